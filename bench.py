@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the VESIS hot path on GB300; prints one JSON line.
+
+A step is one outer VESIS iteration (Sec. 3.3, Steps 2-3) from the fixed
+initial state of the workload: energy density and field on the grid, flip
+rounds to a local minimum of the interface, gradient (grid -> atoms, far
+field, solute-solute), and adaptive-mobility trial steps until one is
+accepted.  The metric is atom-grid pair evaluations per second over the
+whole step.  The default workload is the 2,000-atom protein-like solute on
+the 256^3 grid at h = 0.4 A.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vesis|reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the paper's method has no public implementation to install).
+Multi-GPU runs (torchrun) relax one independent replica per GPU; there is
+no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atom-grid pair-evals/s"
+# FP32 lane operations per energy pair in the inner loop of the pair kernel:
+# dz, r^2, clamp, r^-2, r^-3, r^-6, two LJ FMAs, Q r^-3, three field FMAs
+# (the reciprocal square root runs on the SFU and is not counted).
+OPS_PER_PAIR = 12
+FP32_LANES_PER_SM = 128
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workloads():
+    from paper_2208_05524_gb300 import synth
+    return {
+        "protein2000_grid256": (
+            "2,000-atom protein-like random-walk solute, 256^3 grid, h=0.4 A, seed 0",
+            lambda: synth.protein_like()),
+        "two_atom_grid128": (
+            "two atoms (+1e, -1e) 8 A apart with a bond, 128^3 grid, h=0.2 A",
+            lambda: synth.two_atom(8.0)),
+        "single_ion_grid64": (
+            "one charged LJ atom, 64^3 grid, h=0.25 A, 7 A initial sphere",
+            lambda: synth.single_ion()),
+        "complex20000_grid384": (
+            "two 10,000-atom globules 6 A apart, 384^3 grid, h=0.4 A, seed 2",
+            lambda: synth.two_domain_complex()),
+    }
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample_step(sysd, cells, atoms_idx, grad_pts):
+    """One bounded sample of the step on the host cores: energy-density
+    pairs for `cells` x all atoms and gradient pairs for `atoms_idx` x
+    `grad_pts` solvent points.  Returns the pair count."""
+    import numpy as np
+    import oracle as O
+    p = O.params()
+    pts = O.cell_positions(sysd, cells)
+    O.point_fields(sysd, p, pts)
+    sub = dict(sysd)
+    for k in ("xyz", "sigma_sw", "eps_sw", "q"):
+        sub[k] = np.ascontiguousarray(sysd[k][atoms_idx])
+    P = O.cell_positions(sysd, grad_pts)
+    _, _, E = O.point_fields(sysd, p, P)
+    L = O.lib()
+    g = np.zeros((len(atoms_idx), 3))
+    w = np.full(len(P), sysd["h"] ** 3)
+    L.or_point_grad(len(P), O._p(np.ascontiguousarray(P)), O._p(w), O._p(E),
+                    len(atoms_idx), O._p(sub["xyz"]), O._p(sub["sigma_sw"]),
+                    O._p(sub["eps_sw"]), O._p(sub["q"]), p["rho_w"],
+                    O.cfa_prefactor(p), p["rmin"], O._p(g))
+    N = len(sysd["xyz"])
+    return len(cells) * N + len(grad_pts) * N + len(atoms_idx) * len(grad_pts)
+
+
+def oracle_sample(sysd, target_s=10.0, seed=0):
+    """Times the oracle on a sample sized to about target_s seconds."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    G = int(np.prod(sysd["n"]))
+    N = len(sysd["xyz"])
+
+    def make(m):
+        cells = rng.integers(0, G, m)
+        gp = rng.integers(0, G, max(1, m // 4))
+        ai = np.arange(0, N, max(1, N // 64))[:64]
+        return cells, ai, gp
+
+    m = 2048
+    t0 = time.perf_counter()
+    pairs = oracle_sample_step(sysd, *make(m))
+    dt = time.perf_counter() - t0
+    m = int(min(4_000_000, max(m, m * target_s / max(dt, 1e-3))))
+    args = make(m)
+    t0 = time.perf_counter()
+    pairs = oracle_sample_step(sysd, *args)
+    dt = time.perf_counter() - t0
+    return pairs / dt, dt, m, pairs
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    wl = workloads()[args.workload]
+    sysd = wl[1]()
+    cores = os.cpu_count()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    per = []
+    meta = None
+    for i in range(args.warmup + args.steps):
+        v, dt, m, pairs = oracle_sample(sysd, target_s=args.ref_seconds, seed=i)
+        if i >= args.warmup:
+            per.append((v, dt, pairs))
+        meta = m
+    pairs = sum(p for _, _, p in per)
+    secs = sum(d for _, d, _ in per)
+    value = pairs / secs
+    sample = (f"{meta} random cells x all {len(sysd['xyz'])} atoms (energy density) + "
+              f"64 atoms x {max(1, meta // 4)} cells (gradient) per step, FP64 C oracle")
+    out = {"metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * secs / max(1, len(per)), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "desc": wl[0]},
+           "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "pair-evals/s",
+                   "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU
+
+def run_vesis(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2208_05524_gb300 import vesis
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workloads()[args.workload]
+    sysd = wl[1]()
+    stream = torch.cuda.current_stream()
+    S = vesis.System(sysd, stream=stream)
+    G, N = S.G, S.n_atoms
+    chi0 = torch.empty(G, dtype=torch.uint8, device=dev)
+    S.init_labels(chi0, sysd["init"]["kind"], radius=sysd["init"].get("radius", 0.0))
+    chi = torch.empty_like(chi0)
+    xyz0 = np.ascontiguousarray(sysd["xyz"])
+    opts = dict(max_outer=1)
+
+    def step():
+        chi.copy_(chi0, non_blocking=True)
+        return S.relax(chi, xyz0, **opts)
+
+    for _ in range(args.warmup):
+        r = step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    clk = ClockSampler(local)
+    clk.start()
+    S.set_timing(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    pairs = 0
+    stats = []
+    for _ in range(args.steps):
+        r = step()
+        pairs += r["pair_evals"]
+        stats.append(r)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    tm = S.get_timing()
+    S.set_timing(False)
+    clocks = clk.stop()
+    ms_max = allmax(world, ms)
+    pairs_all = allsum(world, pairs)
+    value = pairs_all / (ms_max * 1e-3)
+
+    # ---- end to end through the API with host buffers
+    chi_host = torch.empty(G, dtype=torch.uint8, pin_memory=True)
+    chi_host.copy_(chi0.cpu())
+    chi_out = torch.empty(G, dtype=torch.uint8, pin_memory=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    epairs = 0
+    for _ in range(args.steps):
+        chi.copy_(chi_host, non_blocking=True)
+        r = S.relax(chi, xyz0, **opts)
+        chi_out.copy_(chi, non_blocking=True)
+        epairs += r["pair_evals"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ems = allmax(world, e0.elapsed_time(e1))
+    e2e_value = allsum(world, epairs) / (ems * 1e-3)
+
+    pk, pk_kind = peaks()
+    f_max = float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = nsm * FP32_LANES_PER_SM * f_max
+    avg_s = tm["pair_energy_ms"] * 1e-3 / max(1, tm["pair_energy_launches"])
+    pairs_per_launch = tm["pair_energy_pairs"] / max(1, tm["pair_energy_launches"])
+    achieved = pairs_per_launch * OPS_PER_PAIR / avg_s
+    sweep = None
+    if tm["sweep_ms"] > 0:
+        gbs = tm["sweep_cells"] * 6.0 / (tm["sweep_ms"] * 1e-3) / 1e9
+        sweep = {"rounds": tm["sweep_rounds"], "ms": tm["sweep_ms"],
+                 "algorithmic_GBps": gbs, "peak_GBps": pk.get("hbm_gbs"),
+                 "frac": gbs / pk.get("hbm_gbs", 6800.0),
+                 "bytes_per_cell_round": 6}
+    force = None
+    if tm["pair_force_launches"]:
+        fs = tm["pair_force_ms"] * 1e-3 / tm["pair_force_launches"]
+        force = {"ms_per_launch": fs * 1e3,
+                 "pairs_per_s": tm["pair_force_pairs"] / tm["pair_force_launches"] / fs}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            v, dt, m, _ = oracle_sample(sysd, target_s=args.ref_seconds)
+            cpu = {"value": v, "unit": "pair-evals/s", "cores": os.cpu_count(),
+                   "kind": "oracle",
+                   "sample": f"{m} random cells x all {N} atoms (energy density) + "
+                             f"64 atoms x {max(1, m // 4)} cells (gradient), "
+                             f"FP64 C oracle, {dt:.1f} s"}
+        last = stats[-1]
+        out = {
+            "metric": METRIC, "value": value, "unit": "pair-evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl[0],
+                       "grid": list(S.shape), "atoms": N,
+                       "step": "one outer VESIS iteration from the initial state",
+                       "l2": "working set (U, E fields %.0f MB) larger than L2"
+                             % (16 * G / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "alu", "kernel": "pair_energy_grid",
+                         "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s (FP32 lane-ops)",
+                         "frac": achieved / peak_ops, "traffic": None,
+                         "ops_per_pair": OPS_PER_PAIR,
+                         "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                       f"{f_max/1e6:.0f} MHz ({pk_kind} max clock)",
+                         "launches": tm["pair_energy_launches"],
+                         "ms_per_launch": avg_s * 1e3},
+            "sweep": sweep, "force": force,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "pair-evals/s",
+                    "h2d_bytes_per_step": G + 24 * N,
+                    "d2h_bytes_per_step": G + 24 * N + 8 * 12},
+            "gpu_launches": tm["kernel_launches"],
+            "cpu_baseline": cpu,
+            "step_detail": {"flip_rounds": last["flip_rounds"], "flips": last["flips"],
+                            "gd_trials": last["gd_trials"],
+                            "pair_evals": last["pair_evals"], "G": last["G"]},
+        }
+        print(json.dumps(out), flush=True)
+    S.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vesis", choices=["vesis", "reference"])
+    ap.add_argument("--workload", default="protein2000_grid256",
+                    choices=list(workloads().keys()))
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_vesis(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * vesis.h - C ABI of the GB300 (sm_103a) VESIS hot path.
+ *
+ * Variational explicit-solute implicit-solvent relaxation of Liu, Zhang,
+ * Cheng and Li (arXiv 2208.05524): the free energy G[Gamma, R] of
+ * Eq. (freeenergyfn) is minimised by alternating the binary level-set
+ * method (Sec. 3.1) at fixed atoms and adaptive-mobility gradient descent
+ * of the atoms (Sec. 3.2) at a fixed interface (Sec. 3.3, Steps 1-5).
+ *
+ * Units: Angstrom, k_B T, elementary charge.  Host arrays are FP64.
+ *
+ * Grid: nx * ny * nz cells of side h; cell (i,j,k) has its centre at
+ * origin + (i + 1/2, j + 1/2, k + 1/2) h and linear index
+ * (i * ny + j) * nz + k (z fastest).  The box is the union of the cells.
+ * Labels chi are uint8, 1 = solute (phi = -1 in the paper), 0 = solvent;
+ * cells outside the box count as solvent.
+ *
+ * Device arrays (suffix _dev) are raw device pointers on the device that
+ * was current when the system was created (for example the data_ptr() of
+ * contiguous CUDA tensors).  The caller owns every array it passes; the
+ * library owns only its internal scratch, released by vesis_destroy.
+ * Work is enqueued on the stream given to vesis_init_system; calls that
+ * return host values synchronise that stream before returning.
+ *
+ * Errors: every call returns a vesis_status.  Negative values are errors
+ * (nothing is guaranteed about outputs), positive values are warnings
+ * (outputs valid).  vesis_last_error() gives a thread-local message for
+ * the last failing call on the calling thread.  No call aborts the process.
+ */
+#ifndef VESIS_H
+#define VESIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VESIS_OK = 0,
+    VESIS_E_ARG = -1,          /* invalid argument or size */
+    VESIS_E_CUDA = -2,         /* CUDA runtime error */
+    VESIS_E_NAN = -3,          /* non-finite energy or gradient */
+    VESIS_E_OUT_OF_BOX = -4,   /* an atom left the box */
+    VESIS_E_ALLOC = -5,        /* device allocation failed */
+    VESIS_W_MAX_ROUNDS = 1,    /* flip rounds hit their cap */
+    VESIS_W_NOT_CONVERGED = 2  /* relaxation hit k_max or the retry cap */
+} vesis_status;
+
+/* Model and discretisation parameters.  vesis_default_params() fills the
+ * paper's Table 1 (T = 298 K, rho_w = 0.0333 A^-3, gamma0 = 0.174 kBT/A^2,
+ * eps_m = 1, eps_w = 80) and the discretisation described below. */
+typedef struct {
+    double gamma0;       /* surface tension, kBT/A^2 (Eq. G_VISM) */
+    double rho_w;        /* solvent number density, A^-3 */
+    double eps_m;        /* solute relative permittivity */
+    double eps_w;        /* solvent relative permittivity */
+    double temperature;  /* K; fixes k_B T and the Bjerrum length */
+    double eps_ss;       /* permittivity of solute-solute Coulomb (Eq. Gss);
+                            default eps_m */
+    int nx, ny, nz;      /* grid cells per axis, each 1..4096 */
+    double h;            /* grid spacing, A */
+    double origin[3];    /* lower box corner, A */
+    double gauss_sigma;  /* surface kernel width, A; <= 0 means 2 h */
+    int trunc_r;         /* kernel half-width in cells, 1..8 (default 6) */
+    double r_min;        /* distance clamp of every pair term, A (0.2) */
+    int far_field;       /* 1: include the integral outside the box */
+    int far_nuv;         /* far-field Gauss points per face axis (16) */
+    int far_nt;          /* far-field Gauss points along rays (8) */
+} vesis_params;
+
+/* Algorithm constants of Step 1 (defaults: k_max = 3000, N*_cnt = 5,
+ * window 100, M = 1, alpha = 1/sqrt(2), delta G* = 5% of |G_old|,
+ * Tol1 = 1e-4, Tol2 = 1e-5) and the caps this implementation adds. */
+typedef struct {
+    int max_outer;        /* k_max */
+    int ncnt_star;        /* N*_cnt */
+    int window;           /* steps the energy test must hold (Step 5) */
+    double M0;            /* initial M */
+    double alpha;         /* shrink factor of M */
+    double dgstar_frac;   /* delta G* = dgstar_frac * |G_old| */
+    double tol_grad;      /* Tol1: max |dG/dr| (Step 3.2) */
+    double tol_energy;    /* Tol2: abs or rel energy change (Step 5) */
+    int max_flip_rounds;  /* cap on flip rounds per interface relaxation */
+    int max_gd_retries;   /* cap on consecutive shrinks of M (Step 3.4) */
+} vesis_relax_opts;
+
+/* Per-run report of vesis_relax. */
+typedef struct {
+    int status;            /* vesis_status of the run */
+    int iterations;        /* accepted outer iterations k */
+    int stop_reason;       /* 0 gradient test, 1 energy test, 2 k_max,
+                              3 retry cap */
+    long long flip_rounds; /* flip rounds over all outer iterations */
+    long long flips;       /* flipped cells over all outer iterations */
+    long long gd_trials;   /* trial positions evaluated (accepts+rejects) */
+    long long pair_evals;  /* atom-point pair evaluations issued */
+    double G;              /* final total free energy, kBT */
+    double terms[6];       /* surface, vdW, CFA, far field, solute-solute,
+                              total at the final state */
+    double M;              /* final mobility factor */
+    double max_grad;       /* max |dG/dr| at the last gradient evaluation */
+} vesis_relax_stats;
+
+typedef struct vesis_system_t *vesis_system;
+
+void vesis_default_params(vesis_params *p);
+void vesis_default_relax_opts(vesis_relax_opts *o);
+
+/* Creates a system: copies the atom data to the device and allocates the
+ * scratch for its grid (about 40 bytes per cell plus per-atom buffers).
+ * Eq. (freeenergyfn), (G_VISM), (LJpotential), (Gss).
+ *   xyz       n_atoms x 3 positions (must lie inside the box)
+ *   sigma_sw, eps_sw  solute-solvent LJ parameters of each atom (A, kBT)
+ *   q         partial charges (e)
+ *   sigma_ss, eps_ss  solute-solute LJ parameters; a pair uses
+ *             (sigma_i + sigma_j)/2 and sqrt(eps_i eps_j)
+ *   bonds     n_bonds x 2 atom indices; harmonic 1/2 A (r - r0)^2 with
+ *             A = bond_k, r0 = bond_r0; bonded pairs are excluded from
+ *             the non-bonded terms (at most 8 bonds per atom)
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default)
+ * n_atoms >= 1, n_bonds >= 0.  On error *out is NULL. */
+int vesis_init_system(const vesis_params *p, int n_atoms, const double *xyz,
+                      const double *sigma_sw, const double *eps_sw,
+                      const double *q, const double *sigma_ss,
+                      const double *eps_ss, int n_bonds, const int *bonds,
+                      const double *bond_k, const double *bond_r0,
+                      void *cuda_stream, vesis_system *out);
+
+/* Replaces the atom positions (n_atoms x 3, host). */
+int vesis_set_positions(vesis_system s, const double *xyz);
+
+/* Copies the current positions (n_atoms x 3) to host memory. */
+int vesis_get_positions(vesis_system s, double *xyz_out);
+
+/* Initial labels (Sec. 3.1, "Initial surfaces"):
+ *   kind 0: loose sphere, chi = 1 where |x - center| < radius;
+ *   kind 1: tight surface, chi = 1 where min_i (|x - r_i| - d_i) < 0 at
+ *           the cell centre, d = n_atoms radii (host; NULL: sigma_sw).
+ * chi_dev: G bytes, written. */
+int vesis_init_labels(vesis_system s, int kind, const double *d,
+                      double radius, const double *center, uint8_t *chi_dev);
+
+/* Energy density and Coulomb field on every cell (Eq. Ur):
+ *   U = rho_w sum_i U_LJ^(i)(r) + C |E|^2,  E = sum_i Q_i d / r^3,
+ *   C = (l_B / 8 pi)(1/eps_w - 1/eps_m),  d = x - r_i,  r = max(|d|, r_min).
+ * xyz_or_null: new positions (host, n_atoms x 3) or NULL for the current.
+ * U_dev: G floats; E_dev: 3 x G floats (Ex block, Ey block, Ez block) or
+ * NULL.  FP32 pair sums.  If chi_dev is not NULL and terms_out is not NULL,
+ * terms_out[0..5] = surface, vdW, CFA, far field, solute-solute, total
+ * (FP64; vdW and CFA need E_dev). */
+int vesis_energy_field(vesis_system s, const double *xyz_or_null,
+                       float *U_dev, float *E_dev, const uint8_t *chi_dev,
+                       double *terms_out);
+
+/* Energy terms of a labelled state from given fields (Eq. 4flip plus the
+ * far field and G_ss at the current positions):
+ *   surface = c sum_j chi_j (1 - w_j),  w = g * chi (Gaussian kernel),
+ *   volume  = h^3 sum_{chi_j = 0} U_j  (split into vdW and CFA if E_dev).
+ * terms_out[6] as for vesis_energy_field. */
+int vesis_energy_terms(vesis_system s, const uint8_t *chi_dev,
+                       const float *U_dev, const float *E_dev,
+                       double *terms_out);
+
+/* Kernel convolution of the labels (Eq. Area with the separable Gaussian):
+ * W_dev[j] = 256^3 w_j, an exact integer (<= 2^24).  G uint32, written. */
+int vesis_surface_weights(vesis_system s, const uint8_t *chi_dev,
+                          uint32_t *W_dev);
+
+/* Flip energies (Eq. dGj1 / dGj2 with the h^3 of the centre-point rule):
+ *   dE_j = c [s_j (1 - 2 w_j) - g0] - s_j h^3 U_j,  s_j = 1 - 2 chi_j,
+ * evaluated in FP64 on candidate cells (a face neighbour with the other
+ * label).  dE_dev: G doubles (0 on non-candidates); cand_dev: G bytes. */
+int vesis_flip_energies(vesis_system s, const uint8_t *chi_dev,
+                        const float *U_dev, double *dE_dev,
+                        uint8_t *cand_dev);
+
+/* Binary level-set relaxation at fixed atoms (Sec. 3.1, Step 2): rounds
+ * of flips until no candidate lowers the energy.  Each round flips every
+ * candidate with dE < 0 whose key (float(dE), then index) is the least in
+ * the cube of half-width trunc_r around it - the data-parallel form of the
+ * min-heap flipping, which always contains the heap's top.
+ *   chi_dev   G bytes, relaxed in place
+ *   U_dev     G floats from vesis_energy_field at the current positions
+ *   E_dev     3 x G floats or NULL (only for the vdW/CFA split of terms)
+ *   max_rounds  > 0
+ * Outputs (each may be NULL): rounds with flips, flipped cells, the sum of
+ * the flipped cells' dE (FP64), terms[6] of the relaxed state.
+ * Returns VESIS_W_MAX_ROUNDS if the cap stopped it. */
+int vesis_blsm_relax(vesis_system s, uint8_t *chi_dev, const float *U_dev,
+                     const float *E_dev, int max_rounds, int *rounds_out,
+                     long long *flips_out, double *dE_sum_out,
+                     double *terms_out);
+
+/* Gradient dG/dr_n of the total free energy with the interface fixed
+ * (Eq. GradientG, taken as the exact derivative of the discrete energy):
+ * grid term -h^3 sum over solvent cells, far-field term and G_ss.
+ *   chi_dev      labels (G bytes)
+ *   xyz_or_null  positions to evaluate at (host) or NULL for the current
+ *   E_dev        3 x G field at those positions, or NULL to compute it
+ *   grad_out     host, n_atoms x 3 FP64
+ *   energy_out   host, total G at that state (may be NULL) */
+int vesis_atom_forces(vesis_system s, const uint8_t *chi_dev,
+                      const double *xyz_or_null, const float *E_dev,
+                      double *grad_out, double *energy_out);
+
+/* Full VESIS relaxation (Sec. 3.3, Steps 1-5) from chi_dev and xyz_inout:
+ * flips to a local minimum (Step 2), gradient test (Step 3.2), forward
+ * Euler step with M_nl = omega M, omega = 1 / max |dG/dr| (Eq. adjustmml),
+ * accept or shrink M (Step 3.4), energy test held for `window` steps
+ * (Steps 4-5).  chi_dev and xyz_inout are updated; stats_out may be NULL.
+ * opts NULL means the defaults. */
+int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
+                const vesis_relax_opts *opts, vesis_relax_stats *stats_out);
+
+/* Device time of the hot kernels, measured with CUDA events recorded on the
+ * system's stream around each launch while timing is enabled. */
+typedef struct {
+    double pair_energy_ms;       /* grid energy-density kernel */
+    long long pair_energy_launches;
+    long long pair_energy_pairs; /* cells x atoms over those launches */
+    double pair_force_ms;        /* grid -> atom gradient kernel */
+    long long pair_force_launches;
+    long long pair_force_pairs;  /* solvent cells x atoms */
+    double sweep_ms;             /* flip-round batches (all round kernels) */
+    long long sweep_rounds;      /* rounds enqueued in those batches */
+    long long sweep_cells;       /* cells x rounds enqueued */
+    long long kernel_launches;   /* library kernels launched (all systems) */
+} vesis_timing;
+
+/* enable != 0 starts recording (and clears the totals); 0 stops. */
+int vesis_set_timing(vesis_system s, int enable);
+
+/* Synchronises the stream and returns the totals since timing was enabled. */
+int vesis_get_timing(vesis_system s, vesis_timing *out);
+
+/* Frees the system's device memory.  NULL is accepted. */
+int vesis_destroy(vesis_system s);
+
+/* Message of the last error on this thread ("" if none). */
+const char *vesis_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VESIS_H */

@@ -466,6 +466,12 @@ def gradient(sysd, p, chi, xyz=None, E=None):
 
 # ------------------------------------------------------------ relaxation
 
+def _inside(sysd, xyz):
+    lo = np.asarray(sysd["origin"], np.float64)
+    hi = lo + np.asarray(sysd["n"], np.float64) * sysd["h"]
+    return bool(np.all((xyz > lo) & (xyz < hi)))
+
+
 def relax(sysd, p, opts, chi=None, xyz=None, log=None):
     """Full VESIS iteration (Steps 1-5): flips to a local minimum of the
     interface at fixed atoms (Step 2), then adaptive-mobility gradient
@@ -476,6 +482,8 @@ def relax(sysd, p, opts, chi=None, xyz=None, log=None):
 
     Readings where the paper is silent: delta G* = frac * |G_old|; the
     energy change of Steps 4-5 is between consecutive accepted iterates;
+    a trial that moves an atom out of the box, or whose energy is not
+    finite, is rejected like an energy increase;
     at most max_gd_retries shrinks per step (then status 2, not
     converged).  Status: 0 gradient converged, 1 energy converged,
     2 not converged (k_max or retry cap)."""
@@ -503,7 +511,8 @@ def relax(sysd, p, opts, chi=None, xyz=None, log=None):
             G_new = energy_terms(sysd, p, chi, x_new, U_n, E_n)["total"]
             dG = G_new - G_old
             dGs = opts["dgstar_frac"] * abs(G_old)
-            if dG > dGs or (ncnt >= opts["ncnt_star"] and 0.0 < dG <= dGs):
+            if (dG > dGs or (ncnt >= opts["ncnt_star"] and 0.0 < dG <= dGs)
+                    or not math.isfinite(G_new) or not _inside(sysd, x_new)):
                 M *= opts["alpha"]
                 ncnt = 0
                 retries += 1

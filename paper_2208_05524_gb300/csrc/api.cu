@@ -1,0 +1,1114 @@
+// C ABI of the VESIS hot path (include/vesis.h): system set-up, orchestration
+// of the kernels on the caller's stream, and the relaxation loop of
+// Sec. 3.3 (Steps 1-5) with its accept/shrink test run on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "vesis.h"
+#include "vesis_internal.cuh"
+
+using namespace vesis;
+
+#include <atomic>
+
+namespace vesis {
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace vesis
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define VCK(call)                                                              \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess)                                                 \
+            return fail(VESIS_E_CUDA, std::string(#call) + ": " +              \
+                                          cudaGetErrorString(e_));             \
+    } while (0)
+
+// Device scalar slots of an energy bank.
+enum {
+    S_SURF = 0, S_VOL = 1, S_CFA = 2, S_NSOL = 3, S_FAR = 4,
+    S_SSB = 5, S_SSLJ = 6, S_SSC = 7, S_TOTAL = 8, S_BANK = 16
+};
+
+struct GdState {
+    double M;
+    int ncnt;
+    int decision;   // 0 accept, 1 reject
+    double dG;
+};
+
+__global__ void k_total(double *bank)
+{
+    bank[S_TOTAL] = bank[S_SURF] + bank[S_VOL] + bank[S_FAR] + bank[S_SSB] +
+                    bank[S_SSLJ] + bank[S_SSC];
+}
+
+// Step 3.4: reject if dG > dG* or (N_cnt >= N*_cnt and 0 < dG <= dG*), with
+// dG* = frac |G_old|; a rejection shrinks M by alpha and resets N_cnt, an
+// acceptance increments N_cnt.  A non-finite trial energy or an atom that
+// left the box is rejected like an energy increase.
+__global__ void k_gd_decide(GdState *s, const double *bank_old,
+                            const double *bank_new, const int *oob,
+                            int ncnt_star, double frac, double alpha)
+{
+    const double Gold = bank_old[S_TOTAL], Gnew = bank_new[S_TOTAL];
+    const double dG = Gnew - Gold;
+    const double dGs = frac * fabs(Gold);
+    bool reject = (dG > dGs) || (s->ncnt >= ncnt_star && dG > 0.0 && dG <= dGs);
+    if (!(Gnew == Gnew) || *oob) reject = true;
+    if (reject) {
+        s->M *= alpha;
+        s->ncnt = 0;
+        s->decision = 1;
+    } else {
+        s->ncnt += 1;
+        s->decision = 0;
+    }
+    s->dG = dG;
+}
+
+__global__ void k_gd_init(GdState *s, double M0)
+{
+    s->M = M0;
+    s->ncnt = 0;
+    s->decision = 0;
+    s->dG = 0.0;
+}
+
+__global__ void k_rs_init(RoundState *rs, int max_rounds)
+{
+    rs->done = 0;
+    rs->round = 0;
+    rs->capped = 0;
+    rs->max_rounds = max_rounds;
+    rs->round_flips = 0;
+    rs->total_flips = 0;
+    rs->round_dE = 0.0;
+    rs->total_dE = 0.0;
+}
+
+// Gauss-Legendre nodes and weights on (-1, 1): Newton iteration on the
+// three-term recurrence of the Legendre polynomials.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) {
+                p0 = 1.0;
+                p1 = z;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+}  // namespace
+
+struct vesis_system_t {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    int nsm = 152;
+    vesis_params p{};
+    int n = 0;
+    GridDesc g{};
+    long long G = 0;
+    KernelW kw{};
+    FlipConst fc{};
+    double c = 0, g0 = 0, h3 = 0, cfa = 0, lB = 0, coul = 0;
+    float rmin2 = 0.f;
+    double centre[3]{}, lo[3]{}, hi[3]{};
+    std::vector<double> sig_sw;
+
+    double *d_xyz = nullptr, *d_xyz_new = nullptr;
+    double *d_sig_sw = nullptr, *d_eps_sw = nullptr, *d_q = nullptr;
+    double *d_sig_ss = nullptr, *d_sqeps_ss = nullptr;
+    double *d_geo = nullptr;   // centre[3], lo[3], hi[3]
+    float4 *d_xyzq = nullptr, *d_fcoef = nullptr, *d_xyzd = nullptr;
+    float2 *d_ab = nullptr;
+    int *d_oob = nullptr;
+    int *d_excl = nullptr, *d_bond_ptr = nullptr, *d_bond_other = nullptr;
+    double *d_bond_k = nullptr, *d_bond_r0 = nullptr;
+
+    uint16_t *d_T1 = nullptr;
+    uint32_t *d_T2 = nullptr, *d_W = nullptr;
+    unsigned long long *d_K0 = nullptr, *d_K1 = nullptr, *d_K2 = nullptr;
+    double *d_dE = nullptr;
+    float *d_U[2] = {nullptr, nullptr}, *d_E[2] = {nullptr, nullptr};
+
+    long long *d_part_s = nullptr;
+    double *d_part_v = nullptr, *d_part_c = nullptr;
+    int nb_terms = 0;
+    ForcePlan fplan{}, fplan_far{};
+    double *d_fpart = nullptr;
+    double *d_grad_solv = nullptr, *d_grad_ss = nullptr, *d_grad = nullptr;
+    unsigned long long *d_gmax = nullptr;
+    unsigned long long *d_fcount = nullptr;   // solvent cells seen by forces
+
+    int nfar = 0;
+    float4 *d_far_pts = nullptr, *d_far_UE = nullptr;
+    double *d_far_w = nullptr, *d_far_part = nullptr;
+    float *d_far_wf = nullptr;
+    int nb_far = 0;
+
+    double *d_ss_part = nullptr;
+    int nb_ss = 0;
+
+    double *d_scal = nullptr;   // two banks of S_BANK doubles
+    RoundState *d_rs = nullptr;
+    GdState *d_gd = nullptr;
+
+    // pinned host mirrors
+    double *h_scal = nullptr;
+    RoundState *h_rs = nullptr;
+    GdState *h_gd = nullptr;
+    int *h_int = nullptr;
+    unsigned long long *h_u64 = nullptr;
+
+    std::vector<void *> allocs;
+
+    // optional event timing of the hot kernels
+    bool timing = false;
+    struct Span {
+        cudaEvent_t a, b;
+        int kind;            // 0 energy, 1 force, 2 sweep batch
+        long long units;     // pairs or cells x rounds
+        long long rounds;
+    };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> ev_pool;
+    vesis_timing tm{};
+    long long launches0 = 0;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(vesis_system s, T **ptr, size_t count)
+{
+    void *p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess)
+        return fail(VESIS_E_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    s->allocs.push_back(p);
+    *ptr = (T *)p;
+    return VESIS_OK;
+}
+
+#define VTRY(x)                  \
+    do {                         \
+        int rc_ = (x);           \
+        if (rc_ != VESIS_OK) {   \
+            return rc_;          \
+        }                        \
+    } while (0)
+
+cudaEvent_t take_event(vesis_system s)
+{
+    if (!s->ev_pool.empty()) {
+        cudaEvent_t e = s->ev_pool.back();
+        s->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Opens a timed span on the stream (no-op unless timing is enabled).
+int span_begin(vesis_system s)
+{
+    if (!s->timing) return -1;
+    vesis_system_t::Span sp{take_event(s), take_event(s), 0, 0, 0};
+    cudaEventRecord(sp.a, s->st);
+    s->spans.push_back(sp);
+    return (int)s->spans.size() - 1;
+}
+
+void span_end(vesis_system s, int id, int kind, long long units, long long rounds)
+{
+    if (id < 0) return;
+    vesis_system_t::Span &sp = s->spans[id];
+    sp.kind = kind;
+    sp.units = units;
+    sp.rounds = rounds;
+    cudaEventRecord(sp.b, s->st);
+}
+
+// Folds completed spans into the totals (the stream must be synchronised).
+void collect_spans(vesis_system s)
+{
+    for (auto &sp : s->spans) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, sp.a, sp.b);
+        if (sp.kind == 0) {
+            s->tm.pair_energy_ms += ms;
+            s->tm.pair_energy_launches += 1;
+            s->tm.pair_energy_pairs += sp.units;
+        } else if (sp.kind == 1) {
+            s->tm.pair_force_ms += ms;
+            s->tm.pair_force_launches += 1;
+            s->tm.pair_force_pairs += sp.units;
+        } else {
+            s->tm.sweep_ms += ms;
+            s->tm.sweep_rounds += sp.rounds;
+            s->tm.sweep_cells += sp.units;
+        }
+        s->ev_pool.push_back(sp.a);
+        s->ev_pool.push_back(sp.b);
+    }
+    s->spans.clear();
+}
+
+AtomsDev atoms_view(vesis_system s)
+{
+    AtomsDev a;
+    a.n = s->n;
+    a.xyzq = s->d_xyzq;
+    a.ab = s->d_ab;
+    a.fcoef = s->d_fcoef;
+    return a;
+}
+
+double *bank(vesis_system s, int b) { return s->d_scal + b * S_BANK; }
+
+void enq_pack(vesis_system s, const double *d_pos)
+{
+    cudaMemsetAsync(s->d_oob, 0, sizeof(int), s->st);
+    launch_pack_atoms(d_pos, s->d_geo, s->d_sig_sw, s->d_eps_sw, s->d_q, s->n,
+                      s->p.rho_w, s->cfa, s->d_xyzq, s->d_ab, s->d_fcoef,
+                      s->d_oob, s->d_geo + 3, s->d_geo + 6, s->st);
+}
+
+// Far-field energy and node fields at the packed positions.
+void enq_far(vesis_system s, double *bk)
+{
+    if (s->nfar > 0) {
+        launch_point_energy(s->d_far_pts, s->d_far_w, s->nfar, atoms_view(s),
+                            (float)s->p.rho_w, (float)s->cfa, s->rmin2,
+                            s->d_far_UE, s->d_far_part, s->st);
+        launch_sum_doubles(s->d_far_part, s->nb_far, bk + S_FAR, 0, s->st);
+    } else {
+        cudaMemsetAsync(bk + S_FAR, 0, sizeof(double), s->st);
+    }
+}
+
+void enq_fields(vesis_system s, float *U, float *E, double *bk)
+{
+    const int sp = span_begin(s);
+    launch_pair_energy_grid(s->g, atoms_view(s), (float)s->p.rho_w,
+                            (float)s->cfa, s->rmin2, U, E, E + s->G,
+                            E + 2 * s->G, s->st);
+    span_end(s, sp, 0, s->G * (long long)s->n, 0);
+    enq_far(s, bk);
+}
+
+void enq_ss(vesis_system s, const double *d_pos, double *bk)
+{
+    launch_ss(d_pos, s->d_sig_ss, s->d_sqeps_ss, s->d_q, s->d_excl,
+              s->d_bond_ptr, s->d_bond_other, s->d_bond_k, s->d_bond_r0, s->n,
+              s->coul, s->d_ss_part, s->d_grad_ss, s->st);
+    launch_ss_final(s->d_ss_part, s->nb_ss, bk + S_SSB, s->st);
+}
+
+void enq_conv(vesis_system s, const uint8_t *chi, uint32_t *W)
+{
+    launch_conv_z(s->g, s->kw, chi, s->d_T1, nullptr, s->st);
+    launch_conv_y(s->g, s->kw, s->d_T1, s->d_T2, nullptr, s->st);
+    launch_conv_x(s->g, s->kw, s->d_T2, W, s->st);
+}
+
+// Surface and volume terms of a labelled state; total with far and ss slots.
+void enq_terms(vesis_system s, const uint8_t *chi, const float *U,
+               const float *E, double *bk)
+{
+    enq_conv(s, chi, s->d_W);
+    launch_terms(s->g, chi, s->d_W, U, E, E ? E + s->G : nullptr,
+                 E ? E + 2 * s->G : nullptr, (float)s->cfa, s->d_part_s,
+                 s->d_part_v, s->d_part_c, s->st);
+    launch_terms_final(s->d_part_s, s->d_part_v, s->d_part_c, s->nb_terms,
+                       s->c, 16777216.0, s->h3, bk, s->st);
+    count_launch();
+    k_total<<<1, 1, 0, s->st>>>(bk);
+}
+
+void enq_round(vesis_system s, uint8_t *chi, const float *U)
+{
+    const int *done = &s->d_rs->done;
+    launch_conv_z(s->g, s->kw, chi, s->d_T1, done, s->st);
+    launch_conv_y(s->g, s->kw, s->d_T1, s->d_T2, done, s->st);
+    launch_conv_x_key(s->g, s->kw, s->d_T2, chi, U, s->fc, s->d_K0, s->d_dE,
+                      done, s->st);
+    launch_min_z(s->g, s->kw.r, s->d_K0, s->d_K1, done, s->st);
+    launch_min_y(s->g, s->kw.r, s->d_K1, s->d_K2, done, s->st);
+    launch_min_x_flip(s->g, s->kw.r, s->d_K0, s->d_K2, s->d_dE, chi, s->d_rs,
+                      s->st);
+    launch_round_end(s->d_rs, s->st);
+}
+
+int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
+             RoundState *out)
+{
+    count_launch();
+    k_rs_init<<<1, 1, 0, s->st>>>(s->d_rs, max_rounds);
+    int batch = 4;
+    for (;;) {
+        const int sp = span_begin(s);
+        for (int b = 0; b < batch; ++b) enq_round(s, chi, U);
+        span_end(s, sp, 2, s->G * (long long)batch, batch);
+        VCK(cudaMemcpyAsync(s->h_rs, s->d_rs, sizeof(RoundState),
+                            cudaMemcpyDeviceToHost, s->st));
+        VCK(cudaStreamSynchronize(s->st));
+        if (s->h_rs->done) break;
+        batch = std::min(batch * 2, 64);
+    }
+    *out = *s->h_rs;
+    return VESIS_OK;
+}
+
+// Gradient at the packed positions; E: the 3 x G field there.  Requires the
+// far-field node fields of the same positions (enq_far).  Writes d_grad and
+// d_gmax, and the solute-solute energies into bk.
+void enq_gradient(vesis_system s, const uint8_t *chi, const float *E,
+                  const double *d_pos, double *bk)
+{
+    const int sp = span_begin(s);
+    launch_pair_force_grid(s->g, s->fplan, chi, E, E + s->G, E + 2 * s->G,
+                           atoms_view(s), s->rmin2, s->d_fpart, s->d_fcount,
+                           s->st);
+    span_end(s, sp, 1, 0, 0);
+    launch_force_reduce(s->d_fpart, s->fplan.nchunk, s->n, s->h3,
+                        s->d_grad_solv, 0, s->st);
+    if (s->nfar > 0) {
+        launch_point_force(s->d_far_pts, s->d_far_wf, s->nfar, s->d_far_UE,
+                           s->fplan_far, atoms_view(s), s->rmin2, s->d_fpart,
+                           s->st);
+        launch_force_reduce(s->d_fpart, s->fplan_far.nchunk, s->n, 1.0,
+                            s->d_grad_solv, 1, s->st);
+    }
+    enq_ss(s, d_pos, bk);
+    launch_grad_combine(s->d_grad_solv, s->d_grad_ss, s->d_grad, 3 * s->n,
+                        s->d_gmax, s->st);
+}
+
+int read_bank(vesis_system s, const double *bk)
+{
+    VCK(cudaMemcpyAsync(s->h_scal, bk, S_BANK * sizeof(double),
+                        cudaMemcpyDeviceToHost, s->st));
+    VCK(cudaStreamSynchronize(s->st));
+    return VESIS_OK;
+}
+
+void fill_terms(const double *hb, bool have_E, double *terms)
+{
+    const double vol = hb[S_VOL];
+    const double cfa = have_E ? hb[S_CFA] : 0.0;
+    terms[0] = hb[S_SURF];
+    terms[1] = vol - cfa;
+    terms[2] = cfa;
+    terms[3] = hb[S_FAR];
+    terms[4] = hb[S_SSB] + hb[S_SSLJ] + hb[S_SSC];
+    terms[5] = hb[S_TOTAL];
+}
+
+int check_oob(vesis_system s)
+{
+    VCK(cudaMemcpyAsync(s->h_int, s->d_oob, sizeof(int), cudaMemcpyDeviceToHost,
+                        s->st));
+    VCK(cudaStreamSynchronize(s->st));
+    if (*s->h_int) return fail(VESIS_E_OUT_OF_BOX, "an atom lies outside the box");
+    return VESIS_OK;
+}
+
+int upload_xyz(vesis_system s, const double *xyz, double *dst)
+{
+    VCK(cudaMemcpyAsync(dst, xyz, 3 * sizeof(double) * s->n,
+                        cudaMemcpyHostToDevice, s->st));
+    // the source may be pageable; make the copy complete before returning
+    VCK(cudaStreamSynchronize(s->st));
+    return VESIS_OK;
+}
+
+int last_launch(const char *what)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(VESIS_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return VESIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void vesis_default_params(vesis_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->gamma0 = 0.174;
+    p->rho_w = 0.0333;
+    p->eps_m = 1.0;
+    p->eps_w = 80.0;
+    p->temperature = 298.0;
+    p->eps_ss = 1.0;
+    p->nx = p->ny = p->nz = 64;
+    p->h = 0.25;
+    p->origin[0] = p->origin[1] = p->origin[2] = -8.0;
+    p->gauss_sigma = 0.0;
+    p->trunc_r = 6;
+    p->r_min = 0.2;
+    p->far_field = 1;
+    p->far_nuv = 16;
+    p->far_nt = 8;
+}
+
+void vesis_default_relax_opts(vesis_relax_opts *o)
+{
+    if (!o) return;
+    o->max_outer = 3000;
+    o->ncnt_star = 5;
+    o->window = 100;
+    o->M0 = 1.0;
+    o->alpha = 1.0 / std::sqrt(2.0);
+    o->dgstar_frac = 0.05;
+    o->tol_grad = 1e-4;
+    o->tol_energy = 1e-5;
+    o->max_flip_rounds = 100000;
+    o->max_gd_retries = 60;
+}
+
+const char *vesis_last_error(void) { return g_err.c_str(); }
+
+int vesis_set_timing(vesis_system s, int enable)
+{
+    if (!s) return fail(VESIS_E_ARG, "NULL system");
+    VCK(cudaStreamSynchronize(s->st));
+    collect_spans(s);
+    s->timing = enable != 0;
+    if (enable) {
+        std::memset(&s->tm, 0, sizeof(s->tm));
+        s->launches0 = launch_count();
+        VCK(cudaMemsetAsync(s->d_fcount, 0, sizeof(unsigned long long), s->st));
+        VCK(cudaStreamSynchronize(s->st));
+    }
+    return VESIS_OK;
+}
+
+int vesis_get_timing(vesis_system s, vesis_timing *out)
+{
+    if (!s || !out) return fail(VESIS_E_ARG, "NULL argument");
+    VCK(cudaMemcpyAsync(s->h_u64, s->d_fcount, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s->st));
+    VCK(cudaStreamSynchronize(s->st));
+    collect_spans(s);
+    *out = s->tm;
+    out->pair_force_pairs = (long long)(*s->h_u64) * s->n;
+    out->kernel_launches = launch_count() - s->launches0;
+    return VESIS_OK;
+}
+
+int vesis_destroy(vesis_system s)
+{
+    if (!s) return VESIS_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(s->dev);
+    cudaStreamSynchronize(s->st);
+    for (auto &sp : s->spans) {
+        cudaEventDestroy(sp.a);
+        cudaEventDestroy(sp.b);
+    }
+    for (auto e : s->ev_pool) cudaEventDestroy(e);
+    for (void *p : s->allocs) cudaFree(p);
+    if (s->h_scal) cudaFreeHost(s->h_scal);
+    if (s->h_rs) cudaFreeHost(s->h_rs);
+    if (s->h_gd) cudaFreeHost(s->h_gd);
+    if (s->h_int) cudaFreeHost(s->h_int);
+    if (s->h_u64) cudaFreeHost(s->h_u64);
+    cudaSetDevice(dev);
+    delete s;
+    return VESIS_OK;
+}
+
+static int init_impl(vesis_system s, const vesis_params *p, int n,
+                     const double *xyz, const double *sigma_sw,
+                     const double *eps_sw, const double *q,
+                     const double *sigma_ss, const double *eps_ss, int nbond,
+                     const int *bonds, const double *bond_k,
+                     const double *bond_r0)
+{
+    s->p = *p;
+    s->n = n;
+    VCK(cudaGetDevice(&s->dev));
+    VCK(cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev));
+    const long long G = (long long)p->nx * p->ny * p->nz;
+    s->G = G;
+    s->g.nx = p->nx;
+    s->g.ny = p->ny;
+    s->g.nz = p->nz;
+    s->g.h = (float)p->h;
+    s->g.cx = 0.5f * (float)(p->nx - 1);
+    s->g.cy = 0.5f * (float)(p->ny - 1);
+    s->g.cz = 0.5f * (float)(p->nz - 1);
+    const int nn[3] = {p->nx, p->ny, p->nz};
+    for (int d = 0; d < 3; ++d) {
+        s->lo[d] = p->origin[d];
+        s->hi[d] = p->origin[d] + nn[d] * p->h;
+        s->centre[d] = p->origin[d] + 0.5 * nn[d] * p->h;
+    }
+
+    // physical constants (CODATA 2018) and the CFA prefactor of Eq. (Ur)
+    const double e = 1.602176634e-19, eps0 = 8.8541878128e-12, kB = 1.380649e-23;
+    s->lB = e * e / (4.0 * M_PI * eps0 * kB * p->temperature) * 1e10;
+    s->cfa = s->lB / (8.0 * M_PI) * (1.0 / p->eps_w - 1.0 / p->eps_m);
+    s->coul = s->lB / p->eps_ss;
+    s->rmin2 = (float)(p->r_min * p->r_min);
+
+    // surface kernel: integer Gaussian weights summing to 256
+    const double h = p->h;
+    const double sig = p->gauss_sigma > 0.0 ? p->gauss_sigma : 2.0 * h;
+    const int r = p->trunc_r;
+    std::vector<double> gw(2 * r + 1);
+    double gs = 0.0;
+    for (int a = -r; a <= r; ++a) {
+        gw[a + r] = std::exp(-(double)(a * a) / (2.0 * (sig / h) * (sig / h)));
+        gs += gw[a + r];
+    }
+    int qsum = 0;
+    s->kw.r = r;
+    for (int a = -r; a <= r; ++a) {
+        if (a == 0) continue;
+        s->kw.q[a + r] = (int)std::nearbyint(256.0 * gw[a + r] / gs);
+        qsum += s->kw.q[a + r];
+    }
+    s->kw.q[r] = 256 - qsum;
+    if (s->kw.q[r] < 0) return fail(VESIS_E_ARG, "surface kernel weights exceed 256");
+    long long S1 = 0;
+    for (int a = 1; a <= r; ++a) S1 += (long long)a * s->kw.q[a + r];
+    if (S1 <= 0) return fail(VESIS_E_ARG, "surface kernel has no first moment");
+    s->c = p->gamma0 * h * h * 256.0 / (double)S1;
+    s->g0 = (double)((long long)s->kw.q[r] * s->kw.q[r] * s->kw.q[r]) / 16777216.0;
+    s->h3 = h * h * h;
+    s->fc.c = s->c;
+    s->fc.g0 = s->g0;
+    s->fc.h3 = s->h3;
+    s->fc.invD3 = 1.0 / 16777216.0;
+
+    // atom data
+    s->sig_sw.assign(sigma_sw, sigma_sw + n);
+    std::vector<double> sqe(n);
+    for (int i = 0; i < n; ++i) sqe[i] = std::sqrt(eps_ss[i]);
+    VTRY(dalloc(s, &s->d_xyz, 3 * n));
+    VTRY(dalloc(s, &s->d_xyz_new, 3 * n));
+    VTRY(dalloc(s, &s->d_sig_sw, n));
+    VTRY(dalloc(s, &s->d_eps_sw, n));
+    VTRY(dalloc(s, &s->d_q, n));
+    VTRY(dalloc(s, &s->d_sig_ss, n));
+    VTRY(dalloc(s, &s->d_sqeps_ss, n));
+    VTRY(dalloc(s, &s->d_geo, 9));
+    VTRY(dalloc(s, &s->d_xyzq, n));
+    VTRY(dalloc(s, &s->d_ab, n));
+    VTRY(dalloc(s, &s->d_fcoef, n));
+    VTRY(dalloc(s, &s->d_xyzd, n));
+    VTRY(dalloc(s, &s->d_oob, 1));
+    double geo[9] = {s->centre[0], s->centre[1], s->centre[2], s->lo[0], s->lo[1],
+                     s->lo[2], s->hi[0], s->hi[1], s->hi[2]};
+    VCK(cudaMemcpy(s->d_geo, geo, sizeof(geo), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_xyz, xyz, 3 * n * sizeof(double), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_sig_sw, sigma_sw, n * sizeof(double), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_eps_sw, eps_sw, n * sizeof(double), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_q, q, n * sizeof(double), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_sig_ss, sigma_ss, n * sizeof(double), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_sqeps_ss, sqe.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+
+    // bonds: per-atom exclusion lists and CSR bond lists
+    constexpr int kMaxExcl = 8;
+    std::vector<int> excl((size_t)n * kMaxExcl, -1), deg(n, 0);
+    std::vector<int> ptr(n + 1, 0);
+    for (int b = 0; b < nbond; ++b) {
+        const int i = bonds[2 * b], j = bonds[2 * b + 1];
+        if (i < 0 || j < 0 || i >= n || j >= n || i == j)
+            return fail(VESIS_E_ARG, "bond index out of range");
+        if (deg[i] >= kMaxExcl || deg[j] >= kMaxExcl)
+            return fail(VESIS_E_ARG, "more than 8 bonds on one atom");
+        excl[(size_t)i * kMaxExcl + deg[i]++] = j;
+        excl[(size_t)j * kMaxExcl + deg[j]++] = i;
+    }
+    for (int i = 0; i < n; ++i) ptr[i + 1] = ptr[i] + deg[i];
+    std::vector<int> other(std::max(1, ptr[n]));
+    std::vector<double> bk(std::max(1, ptr[n])), br(std::max(1, ptr[n]));
+    std::vector<int> fillc(n, 0);
+    for (int b = 0; b < nbond; ++b) {
+        const int i = bonds[2 * b], j = bonds[2 * b + 1];
+        int pi = ptr[i] + fillc[i]++, pj = ptr[j] + fillc[j]++;
+        other[pi] = j; bk[pi] = bond_k[b]; br[pi] = bond_r0[b];
+        other[pj] = i; bk[pj] = bond_k[b]; br[pj] = bond_r0[b];
+    }
+    VTRY(dalloc(s, &s->d_excl, (size_t)n * kMaxExcl));
+    VTRY(dalloc(s, &s->d_bond_ptr, n + 1));
+    VTRY(dalloc(s, &s->d_bond_other, other.size()));
+    VTRY(dalloc(s, &s->d_bond_k, bk.size()));
+    VTRY(dalloc(s, &s->d_bond_r0, br.size()));
+    VCK(cudaMemcpy(s->d_excl, excl.data(), excl.size() * sizeof(int), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_bond_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_bond_other, other.data(), other.size() * sizeof(int), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_bond_k, bk.data(), bk.size() * sizeof(double), cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(s->d_bond_r0, br.data(), br.size() * sizeof(double), cudaMemcpyHostToDevice));
+
+    // grid scratch
+    VTRY(dalloc(s, &s->d_T1, G));
+    VTRY(dalloc(s, &s->d_T2, G));
+    VTRY(dalloc(s, &s->d_W, G));
+    VTRY(dalloc(s, &s->d_K0, G));
+    VTRY(dalloc(s, &s->d_K1, G));
+    VTRY(dalloc(s, &s->d_K2, G));
+    VTRY(dalloc(s, &s->d_dE, G));
+    for (int b = 0; b < 2; ++b) {
+        VTRY(dalloc(s, &s->d_U[b], G));
+        VTRY(dalloc(s, &s->d_E[b], 3 * G));
+    }
+    s->nb_terms = terms_blocks(G);
+    VTRY(dalloc(s, &s->d_part_s, 2 * s->nb_terms));
+    VTRY(dalloc(s, &s->d_part_v, s->nb_terms));
+    VTRY(dalloc(s, &s->d_part_c, s->nb_terms));
+
+    // far-field quadrature: six face pyramids about the box centre,
+    // y = c + s p, s = 1/t >= 1, dV = Lx Ly Lz t^-4 dt du dv
+    if (p->far_field) {
+        std::vector<double> xu, wu, xt, wt;
+        gauss_legendre(p->far_nuv, xu, wu);
+        gauss_legendre(p->far_nt, xt, wt);
+        const double Lh[3] = {0.5 * nn[0] * h, 0.5 * nn[1] * h, 0.5 * nn[2] * h};
+        const double vol = Lh[0] * Lh[1] * Lh[2];
+        std::vector<float4> pts;
+        std::vector<double> w;
+        std::vector<float> wf;
+        for (int axis = 0; axis < 3; ++axis) {
+            int oth[2], m = 0;
+            for (int d = 0; d < 3; ++d)
+                if (d != axis) oth[m++] = d;
+            for (int sg = -1; sg <= 1; sg += 2)
+                for (int iu = 0; iu < p->far_nuv; ++iu)
+                    for (int iv = 0; iv < p->far_nuv; ++iv)
+                        for (int it = 0; it < p->far_nt; ++it) {
+                            const double t = 0.5 * (xt[it] + 1.0);
+                            double f[3];
+                            f[axis] = sg * Lh[axis];
+                            f[oth[0]] = xu[iu] * Lh[oth[0]];
+                            f[oth[1]] = xu[iv] * Lh[oth[1]];
+                            const double ww = wu[iu] * wu[iv] * 0.5 * wt[it] * vol / (t * t * t * t);
+                            pts.push_back(make_float4((float)(f[0] / t), (float)(f[1] / t),
+                                                      (float)(f[2] / t), 0.f));
+                            w.push_back(ww);
+                            wf.push_back((float)ww);
+                        }
+        }
+        s->nfar = (int)pts.size();
+        VTRY(dalloc(s, &s->d_far_pts, s->nfar));
+        VTRY(dalloc(s, &s->d_far_UE, s->nfar));
+        VTRY(dalloc(s, &s->d_far_w, s->nfar));
+        VTRY(dalloc(s, &s->d_far_wf, s->nfar));
+        s->nb_far = point_energy_blocks(s->nfar);
+        VTRY(dalloc(s, &s->d_far_part, s->nb_far));
+        VCK(cudaMemcpy(s->d_far_pts, pts.data(), pts.size() * sizeof(float4), cudaMemcpyHostToDevice));
+        VCK(cudaMemcpy(s->d_far_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+        VCK(cudaMemcpy(s->d_far_wf, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+
+    // gradient partials
+    s->fplan = plan_pair_force(G, n, s->nsm);
+    s->fplan_far = plan_point_force(std::max(1, s->nfar), n, s->nsm);
+    const long long nch = std::max(s->fplan.nchunk, s->fplan_far.nchunk);
+    VTRY(dalloc(s, &s->d_fpart, (size_t)nch * n * 3));
+    VTRY(dalloc(s, &s->d_grad_solv, 3 * n));
+    VTRY(dalloc(s, &s->d_grad_ss, 3 * n));
+    VTRY(dalloc(s, &s->d_grad, 3 * n));
+    VTRY(dalloc(s, &s->d_gmax, 1));
+    VTRY(dalloc(s, &s->d_fcount, 1));
+    VCK(cudaMemset(s->d_fcount, 0, sizeof(unsigned long long)));
+    s->nb_ss = ss_blocks(n);
+    VTRY(dalloc(s, &s->d_ss_part, 3 * s->nb_ss));
+
+    VTRY(dalloc(s, &s->d_scal, 2 * S_BANK));
+    VTRY(dalloc(s, &s->d_rs, 1));
+    VTRY(dalloc(s, &s->d_gd, 1));
+    VCK(cudaMemset(s->d_scal, 0, 2 * S_BANK * sizeof(double)));
+    VCK(cudaMallocHost(&s->h_scal, S_BANK * sizeof(double)));
+    VCK(cudaMallocHost(&s->h_rs, sizeof(RoundState)));
+    VCK(cudaMallocHost(&s->h_gd, sizeof(GdState)));
+    VCK(cudaMallocHost(&s->h_int, sizeof(int)));
+    VCK(cudaMallocHost(&s->h_u64, sizeof(unsigned long long)));
+    VCK(cudaDeviceSynchronize());
+    return VESIS_OK;
+}
+
+int vesis_init_system(const vesis_params *p, int n, const double *xyz,
+                      const double *sigma_sw, const double *eps_sw,
+                      const double *q, const double *sigma_ss,
+                      const double *eps_ss, int nbond, const int *bonds,
+                      const double *bond_k, const double *bond_r0,
+                      void *cuda_stream, vesis_system *out)
+{
+    if (!out) return fail(VESIS_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || !xyz || !sigma_sw || !eps_sw || !q || !sigma_ss || !eps_ss)
+        return fail(VESIS_E_ARG, "NULL parameter or atom array");
+    if (n < 1) return fail(VESIS_E_ARG, "n_atoms must be >= 1");
+    if (nbond < 0 || (nbond > 0 && (!bonds || !bond_k || !bond_r0)))
+        return fail(VESIS_E_ARG, "bad bond arrays");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nx > 4096 || p->ny > 4096 ||
+        p->nz > 4096)
+        return fail(VESIS_E_ARG, "grid dimensions must be in 1..4096");
+    const long long G = (long long)p->nx * p->ny * p->nz;
+    if (G > 2147483647LL) return fail(VESIS_E_ARG, "grid has more than 2^31-1 cells");
+    if (!(p->h > 0.0)) return fail(VESIS_E_ARG, "h must be > 0");
+    if (p->trunc_r < 1 || p->trunc_r > kMaxR)
+        return fail(VESIS_E_ARG, "trunc_r must be in 1..8");
+    if (!(p->r_min > 0.0)) return fail(VESIS_E_ARG, "r_min must be > 0");
+    if (!(p->temperature > 0.0) || !(p->eps_w > 0.0) || !(p->eps_m > 0.0) ||
+        !(p->eps_ss > 0.0))
+        return fail(VESIS_E_ARG, "temperature and permittivities must be > 0");
+    if (p->far_field && (p->far_nuv < 1 || p->far_nt < 1 || p->far_nuv > 64 ||
+                         p->far_nt > 64))
+        return fail(VESIS_E_ARG, "far-field orders must be in 1..64");
+    for (int i = 0; i < 3 * n; ++i)
+        if (!std::isfinite(xyz[i])) return fail(VESIS_E_NAN, "non-finite position");
+    vesis_system s = new vesis_system_t();
+    s->st = (cudaStream_t)cuda_stream;
+    int rc = init_impl(s, p, n, xyz, sigma_sw, eps_sw, q, sigma_ss, eps_ss,
+                       nbond, bonds, bond_k, bond_r0);
+    if (rc == VESIS_OK) {
+        enq_pack(s, s->d_xyz);
+        rc = check_oob(s);
+    }
+    if (rc != VESIS_OK) {
+        std::string keep = g_err;
+        vesis_destroy(s);
+        g_err = keep;
+        return rc;
+    }
+    *out = s;
+    return VESIS_OK;
+}
+
+int vesis_set_positions(vesis_system s, const double *xyz)
+{
+    if (!s || !xyz) return fail(VESIS_E_ARG, "NULL argument");
+    for (int i = 0; i < 3 * s->n; ++i)
+        if (!std::isfinite(xyz[i])) return fail(VESIS_E_NAN, "non-finite position");
+    VTRY(upload_xyz(s, xyz, s->d_xyz));
+    enq_pack(s, s->d_xyz);
+    return check_oob(s);
+}
+
+int vesis_get_positions(vesis_system s, double *xyz_out)
+{
+    if (!s || !xyz_out) return fail(VESIS_E_ARG, "NULL argument");
+    VCK(cudaMemcpyAsync(xyz_out, s->d_xyz, 3 * sizeof(double) * s->n,
+                        cudaMemcpyDeviceToHost, s->st));
+    VCK(cudaStreamSynchronize(s->st));
+    return VESIS_OK;
+}
+
+int vesis_init_labels(vesis_system s, int kind, const double *d, double radius,
+                      const double *center, uint8_t *chi_dev)
+{
+    if (!s || !chi_dev) return fail(VESIS_E_ARG, "NULL argument");
+    if (kind == 0) {
+        const double c0 = center ? center[0] : 0.0, c1 = center ? center[1] : 0.0,
+                     c2 = center ? center[2] : 0.0;
+        launch_init_sphere(s->g, (float)(c0 - s->centre[0]), (float)(c1 - s->centre[1]),
+                           (float)(c2 - s->centre[2]), (float)radius, chi_dev, s->st);
+    } else if (kind == 1) {
+        std::vector<double> xyz(3 * s->n);
+        VCK(cudaMemcpy(xyz.data(), s->d_xyz, xyz.size() * sizeof(double),
+                       cudaMemcpyDeviceToHost));
+        std::vector<float4> a(s->n);
+        for (int i = 0; i < s->n; ++i)
+            a[i] = make_float4((float)(xyz[3 * i] - s->centre[0]),
+                               (float)(xyz[3 * i + 1] - s->centre[1]),
+                               (float)(xyz[3 * i + 2] - s->centre[2]),
+                               (float)(d ? d[i] : s->sig_sw[i]));
+        VCK(cudaMemcpyAsync(s->d_xyzd, a.data(), a.size() * sizeof(float4),
+                            cudaMemcpyHostToDevice, s->st));
+        launch_init_tight(s->g, s->d_xyzd, s->n, chi_dev, s->st);
+        VCK(cudaStreamSynchronize(s->st));
+    } else {
+        return fail(VESIS_E_ARG, "kind must be 0 (sphere) or 1 (tight)");
+    }
+    return last_launch("init_labels");
+}
+
+int vesis_energy_field(vesis_system s, const double *xyz, float *U_dev,
+                       float *E_dev, const uint8_t *chi_dev, double *terms_out)
+{
+    if (!s || !U_dev) return fail(VESIS_E_ARG, "NULL argument");
+    if (xyz) VTRY(vesis_set_positions(s, xyz));
+    else enq_pack(s, s->d_xyz);
+    float *E = E_dev ? E_dev : s->d_E[0];
+    double *bk = bank(s, 0);
+    enq_fields(s, U_dev, E, bk);
+    if (chi_dev && terms_out) {
+        enq_ss(s, s->d_xyz, bk);
+        enq_terms(s, chi_dev, U_dev, E_dev, bk);
+        VTRY(last_launch("energy_field"));
+        VTRY(read_bank(s, bk));
+        fill_terms(s->h_scal, E_dev != nullptr, terms_out);
+    } else {
+        VTRY(last_launch("energy_field"));
+        VCK(cudaStreamSynchronize(s->st));
+    }
+    return VESIS_OK;
+}
+
+int vesis_energy_terms(vesis_system s, const uint8_t *chi_dev, const float *U_dev,
+                       const float *E_dev, double *terms_out)
+{
+    if (!s || !chi_dev || !U_dev || !terms_out) return fail(VESIS_E_ARG, "NULL argument");
+    double *bk = bank(s, 0);
+    enq_pack(s, s->d_xyz);
+    enq_far(s, bk);
+    enq_ss(s, s->d_xyz, bk);
+    enq_terms(s, chi_dev, U_dev, E_dev, bk);
+    VTRY(last_launch("energy_terms"));
+    VTRY(read_bank(s, bk));
+    fill_terms(s->h_scal, E_dev != nullptr, terms_out);
+    return VESIS_OK;
+}
+
+int vesis_surface_weights(vesis_system s, const uint8_t *chi_dev, uint32_t *W_dev)
+{
+    if (!s || !chi_dev || !W_dev) return fail(VESIS_E_ARG, "NULL argument");
+    enq_conv(s, chi_dev, W_dev);
+    VTRY(last_launch("surface_weights"));
+    VCK(cudaStreamSynchronize(s->st));
+    return VESIS_OK;
+}
+
+int vesis_flip_energies(vesis_system s, const uint8_t *chi_dev, const float *U_dev,
+                        double *dE_dev, uint8_t *cand_dev)
+{
+    if (!s || !chi_dev || !U_dev || !dE_dev || !cand_dev)
+        return fail(VESIS_E_ARG, "NULL argument");
+    enq_conv(s, chi_dev, s->d_W);
+    launch_flip_energy(s->g, s->d_W, chi_dev, U_dev, s->fc, dE_dev, cand_dev, s->st);
+    VTRY(last_launch("flip_energies"));
+    VCK(cudaStreamSynchronize(s->st));
+    return VESIS_OK;
+}
+
+int vesis_blsm_relax(vesis_system s, uint8_t *chi_dev, const float *U_dev,
+                     const float *E_dev, int max_rounds, int *rounds_out,
+                     long long *flips_out, double *dE_sum_out, double *terms_out)
+{
+    if (!s || !chi_dev || !U_dev) return fail(VESIS_E_ARG, "NULL argument");
+    if (max_rounds < 1) return fail(VESIS_E_ARG, "max_rounds must be >= 1");
+    RoundState rs;
+    VTRY(run_blsm(s, chi_dev, U_dev, max_rounds, &rs));
+    VTRY(last_launch("blsm_relax"));
+    if (rounds_out) *rounds_out = rs.round;
+    if (flips_out) *flips_out = (long long)rs.total_flips;
+    if (dE_sum_out) *dE_sum_out = rs.total_dE;
+    if (terms_out) VTRY(vesis_energy_terms(s, chi_dev, U_dev, E_dev, terms_out));
+    return rs.capped ? VESIS_W_MAX_ROUNDS : VESIS_OK;
+}
+
+int vesis_atom_forces(vesis_system s, const uint8_t *chi_dev, const double *xyz,
+                      const float *E_dev, double *grad_out, double *energy_out)
+{
+    if (!s || !chi_dev || !grad_out) return fail(VESIS_E_ARG, "NULL argument");
+    if (xyz) VTRY(vesis_set_positions(s, xyz));
+    else enq_pack(s, s->d_xyz);
+    double *bk = bank(s, 0);
+    const float *E = E_dev;
+    if (!E || energy_out) {
+        enq_fields(s, s->d_U[0], s->d_E[0], bk);
+        E = s->d_E[0];
+    } else {
+        enq_far(s, bk);
+    }
+    enq_gradient(s, chi_dev, E, s->d_xyz, bk);
+    if (energy_out) {
+        enq_terms(s, chi_dev, s->d_U[0], s->d_E[0], bk);
+        VTRY(last_launch("atom_forces"));
+        VTRY(read_bank(s, bk));
+        *energy_out = s->h_scal[S_TOTAL];
+    }
+    VTRY(last_launch("atom_forces"));
+    VCK(cudaMemcpyAsync(grad_out, s->d_grad, 3 * sizeof(double) * s->n,
+                        cudaMemcpyDeviceToHost, s->st));
+    VCK(cudaStreamSynchronize(s->st));
+    for (int i = 0; i < 3 * s->n; ++i)
+        if (!std::isfinite(grad_out[i])) return fail(VESIS_E_NAN, "non-finite gradient");
+    return VESIS_OK;
+}
+
+int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
+                const vesis_relax_opts *opts_in, vesis_relax_stats *stats_out)
+{
+    if (!s || !chi_dev || !xyz_inout) return fail(VESIS_E_ARG, "NULL argument");
+    vesis_relax_opts o;
+    if (opts_in) o = *opts_in;
+    else vesis_default_relax_opts(&o);
+    if (o.max_outer < 0 || o.window < 1 || o.max_flip_rounds < 1 ||
+        o.max_gd_retries < 0 || !(o.alpha > 0.0 && o.alpha < 1.0) || !(o.M0 > 0.0))
+        return fail(VESIS_E_ARG, "invalid relax options");
+    vesis_relax_stats st;
+    std::memset(&st, 0, sizeof(st));
+    const long long GN = s->G * (long long)s->n;
+    const long long FN = (long long)s->nfar * s->n;
+    const long long NN = (long long)s->n * s->n;
+
+    VTRY(vesis_set_positions(s, xyz_inout));
+    int cur = 0, trial = 1;
+    enq_fields(s, s->d_U[cur], s->d_E[cur], bank(s, cur));
+    enq_ss(s, s->d_xyz, bank(s, cur));
+    enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur));
+    count_launch();
+    k_gd_init<<<1, 1, 0, s->st>>>(s->d_gd, o.M0);
+    VTRY(last_launch("relax init"));
+    VTRY(read_bank(s, bank(s, cur)));
+    st.pair_evals += GN + FN;
+    double G_prev = s->h_scal[S_TOTAL];
+    if (!std::isfinite(G_prev)) return fail(VESIS_E_NAN, "non-finite initial energy");
+
+    int k = 0, stable = 0, reason = 2, status = VESIS_OK;
+    double gmax = 0.0;
+    while (k < o.max_outer) {
+        RoundState rs;
+        VTRY(run_blsm(s, chi_dev, s->d_U[cur], o.max_flip_rounds, &rs));
+        st.flip_rounds += rs.round;
+        st.flips += (long long)rs.total_flips;
+        // Step 3.1-3.2: gradient and G_old at (Gamma^{k+1}, R^k)
+        enq_gradient(s, chi_dev, s->d_E[cur], s->d_xyz, bank(s, cur));
+        enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur));
+        VTRY(last_launch("relax gradient"));
+        VCK(cudaMemcpyAsync(s->h_u64, s->d_gmax, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s->st));
+        VTRY(read_bank(s, bank(s, cur)));
+        std::memcpy(&gmax, s->h_u64, sizeof(double));
+        st.pair_evals += (s->G - (long long)s->h_scal[S_NSOL]) * s->n + FN + NN;
+        if (!std::isfinite(gmax) || gmax >= 1.0e308) {
+            status = fail(VESIS_E_NAN, "non-finite gradient");
+            break;
+        }
+        if (gmax < o.tol_grad) {
+            reason = 0;
+            break;
+        }
+        // Step 3.3-3.4: trial steps until one is accepted
+        int retries = 0;
+        bool accepted = false;
+        double G_new = 0.0;
+        while (!accepted) {
+            launch_mobility(s->d_xyz, s->d_grad, s->d_gmax, &s->d_gd->M,
+                            s->d_xyz_new, 3 * s->n, s->st);
+            enq_pack(s, s->d_xyz_new);
+            enq_fields(s, s->d_U[trial], s->d_E[trial], bank(s, trial));
+            enq_ss(s, s->d_xyz_new, bank(s, trial));
+            enq_terms(s, chi_dev, s->d_U[trial], s->d_E[trial], bank(s, trial));
+            count_launch();
+            k_gd_decide<<<1, 1, 0, s->st>>>(s->d_gd, bank(s, cur), bank(s, trial),
+                                            s->d_oob, o.ncnt_star, o.dgstar_frac,
+                                            o.alpha);
+            VTRY(last_launch("relax trial"));
+            VCK(cudaMemcpyAsync(s->h_gd, s->d_gd, sizeof(GdState),
+                                cudaMemcpyDeviceToHost, s->st));
+            VTRY(read_bank(s, bank(s, trial)));
+            st.gd_trials += 1;
+            st.pair_evals += GN + FN + NN;
+            if (s->h_gd->decision == 0) {
+                accepted = true;
+                G_new = s->h_scal[S_TOTAL];
+            } else if (++retries > o.max_gd_retries) {
+                break;
+            }
+        }
+        if (!accepted) {
+            enq_pack(s, s->d_xyz);   // keep the packed atoms on R^k
+            reason = 3;
+            status = VESIS_W_NOT_CONVERGED;
+            break;
+        }
+        std::swap(cur, trial);
+        std::swap(s->d_xyz, s->d_xyz_new);
+        ++k;
+        // Steps 4-5: energy change between consecutive accepted iterates
+        const double d_abs = std::fabs(G_new - G_prev);
+        const double d_rel = G_new != 0.0 ? d_abs / std::fabs(G_new) : INFINITY;
+        G_prev = G_new;
+        if (d_abs < o.tol_energy || d_rel < o.tol_energy) {
+            if (++stable >= o.window) {
+                reason = 1;
+                break;
+            }
+        } else {
+            stable = 0;
+        }
+    }
+    if (status == VESIS_OK && reason == 2) status = VESIS_W_NOT_CONVERGED;
+    // final state
+    if (status >= 0) {
+        enq_pack(s, s->d_xyz);
+        enq_far(s, bank(s, cur));
+        enq_ss(s, s->d_xyz, bank(s, cur));
+        enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur));
+        VTRY(last_launch("relax final"));
+        VTRY(read_bank(s, bank(s, cur)));
+        fill_terms(s->h_scal, true, st.terms);
+        st.G = st.terms[5];
+        VCK(cudaMemcpyAsync(s->h_gd, s->d_gd, sizeof(GdState),
+                            cudaMemcpyDeviceToHost, s->st));
+        VCK(cudaMemcpyAsync(xyz_inout, s->d_xyz, 3 * sizeof(double) * s->n,
+                            cudaMemcpyDeviceToHost, s->st));
+        VCK(cudaStreamSynchronize(s->st));
+        st.M = s->h_gd->M;
+    }
+    st.status = status;
+    st.iterations = k;
+    st.stop_reason = reason;
+    st.max_grad = gmax;
+    if (stats_out) *stats_out = st;
+    return status;
+}
+
+}  // extern "C"

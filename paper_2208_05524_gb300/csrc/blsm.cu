@@ -1,0 +1,497 @@
+// Binary level-set sweep kernels (Sec. 3.1, Step 2) for sm_103a.
+//
+// Surface energy with the separable Gaussian kernel g(a,b,c) = q_a q_b q_c /
+// 256^3 (q integer, sum 256): E_s = c sum_j chi_j (1 - w_j), w = g * chi with
+// cells outside the box counted as solvent.  W = 256^3 w is computed in
+// three integer passes (z, y, x), so it is exact: pass 1 <= 256, pass 2
+// <= 2^16, pass 3 <= 2^24.
+//
+// One flip round:
+//   conv_z -> conv_y -> conv_x_key: candidates (a face neighbour with the
+//     other label) get dE = c [s (1 - 2 w) - g0] - s h^3 U (Eq. dGj1/dGj2,
+//     FP64, candidates only) and, if dE < 0, the key
+//     (order-preserving bits of float(dE)) << 32 | index; others get ~0.
+//   min_z -> min_y -> min_x_flip: a cell flips iff its key equals the
+//     minimum key over the cube of half-width r around it.  Selected cells
+//     are more than r apart, so their kernel couplings vanish and the round
+//     lowers the energy by exactly the sum of their dE.
+//   round_end: stops the rounds once a round flips nothing.
+// Every round kernel returns at once when the rounds are done, so a fixed
+// batch of rounds can be enqueued ahead of the host's check.
+#include "vesis_internal.cuh"
+
+namespace vesis {
+
+constexpr int CT = 256;   // threads per block of the cell-parallel kernels
+
+__device__ __forceinline__ bool rounds_done(const int *done)
+{
+    return done != nullptr && *(volatile const int *)done != 0;
+}
+
+static unsigned cell_blocks(const GridDesc &g)
+{
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    return (unsigned)((G + CT - 1) / CT);
+}
+
+__global__ void k_conv_z(GridDesc g, KernelW kw, const uint8_t *__restrict__ chi,
+                         uint16_t *__restrict__ T1, const int *done)
+{
+    if (rounds_done(done)) return;
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int k = (int)(p % g.nz);
+    unsigned s = 0;
+    for (int a = -kw.r; a <= kw.r; ++a) {
+        const int kk = k + a;
+        if (kk >= 0 && kk < g.nz) s += (unsigned)kw.q[a + kw.r] * chi[p + a];
+    }
+    T1[p] = (uint16_t)s;
+}
+
+__global__ void k_conv_y(GridDesc g, KernelW kw, const uint16_t *__restrict__ T1,
+                         uint32_t *__restrict__ T2, const int *done)
+{
+    if (rounds_done(done)) return;
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int j = (int)((p / g.nz) % g.ny);
+    unsigned s = 0;
+    for (int b = -kw.r; b <= kw.r; ++b) {
+        const int jj = j + b;
+        if (jj >= 0 && jj < g.ny) s += (unsigned)kw.q[b + kw.r] * T1[p + (long long)b * g.nz];
+    }
+    T2[p] = s;
+}
+
+__device__ __forceinline__ unsigned conv_x_at(const GridDesc &g, const KernelW &kw,
+                                              const uint32_t *__restrict__ T2,
+                                              long long p, int i, long long nyz)
+{
+    unsigned s = 0;
+    for (int c = -kw.r; c <= kw.r; ++c) {
+        const int ii = i + c;
+        if (ii >= 0 && ii < g.nx) s += (unsigned)kw.q[c + kw.r] * T2[p + (long long)c * nyz];
+    }
+    return s;
+}
+
+__global__ void k_conv_x(GridDesc g, KernelW kw, const uint32_t *__restrict__ T2,
+                         uint32_t *__restrict__ W)
+{
+    const long long nyz = (long long)g.ny * g.nz;
+    const long long G = nyz * g.nx;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int i = (int)(p / nyz);
+    W[p] = conv_x_at(g, kw, T2, p, i, nyz);
+}
+
+// Face neighbour with the other label; outside the box counts as solvent.
+__device__ __forceinline__ bool is_candidate(const GridDesc &g,
+                                             const uint8_t *__restrict__ chi,
+                                             long long p, int i, int j, int k,
+                                             long long nyz)
+{
+    const uint8_t c = chi[p];
+    const uint8_t xm = (i > 0) ? chi[p - nyz] : 0;
+    const uint8_t xp = (i < g.nx - 1) ? chi[p + nyz] : 0;
+    const uint8_t ym = (j > 0) ? chi[p - g.nz] : 0;
+    const uint8_t yp = (j < g.ny - 1) ? chi[p + g.nz] : 0;
+    const uint8_t zm = (k > 0) ? chi[p - 1] : 0;
+    const uint8_t zp = (k < g.nz - 1) ? chi[p + 1] : 0;
+    return (xm != c) | (xp != c) | (ym != c) | (yp != c) | (zm != c) | (zp != c);
+}
+
+// dE of Eq. (dGj1/dGj2) rounded exactly as written: a = s (1 - 2w) - g0 is
+// exact, then c*a and h3*U are rounded products and the difference is
+// rounded once (no contraction).
+__device__ __forceinline__ double flip_dE(uint8_t chi_j, unsigned W, float U,
+                                          const FlipConst &fc)
+{
+    const double w = __dmul_rn((double)W, fc.invD3);
+    const double s = chi_j ? -1.0 : 1.0;
+    const double a = __dsub_rn(__dmul_rn(s, __dsub_rn(1.0, __dmul_rn(2.0, w))), fc.g0);
+    const double t1 = __dmul_rn(fc.c, a);
+    const double t2 = __dmul_rn(fc.h3, (double)U);
+    return __dsub_rn(t1, __dmul_rn(s, t2));
+}
+
+__device__ __forceinline__ unsigned long long flip_key(double dE, long long p)
+{
+    unsigned u = __float_as_uint(__double2float_rn(dE));
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)u << 32) | (unsigned long long)p;
+}
+
+__global__ void k_conv_x_key(GridDesc g, KernelW kw, const uint32_t *__restrict__ T2,
+                             const uint8_t *__restrict__ chi,
+                             const float *__restrict__ U, FlipConst fc,
+                             unsigned long long *__restrict__ K0,
+                             double *__restrict__ dE, const int *done)
+{
+    if (rounds_done(done)) return;
+    const long long nyz = (long long)g.ny * g.nz;
+    const long long G = nyz * g.nx;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int i = (int)(p / nyz);
+    const long long rem = p - (long long)i * nyz;
+    const int j = (int)(rem / g.nz);
+    const int k = (int)(rem - (long long)j * g.nz);
+    unsigned long long key = ~0ull;
+    if (is_candidate(g, chi, p, i, j, k, nyz)) {
+        const unsigned W = conv_x_at(g, kw, T2, p, i, nyz);
+        const double e = flip_dE(chi[p], W, U[p], fc);
+        dE[p] = e;
+        if (e < 0.0) key = flip_key(e, p);
+    }
+    K0[p] = key;
+}
+
+__global__ void k_flip_energy(GridDesc g, const uint32_t *__restrict__ W,
+                              const uint8_t *__restrict__ chi,
+                              const float *__restrict__ U, FlipConst fc,
+                              double *__restrict__ dE, uint8_t *__restrict__ cand)
+{
+    const long long nyz = (long long)g.ny * g.nz;
+    const long long G = nyz * g.nx;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int i = (int)(p / nyz);
+    const long long rem = p - (long long)i * nyz;
+    const int j = (int)(rem / g.nz);
+    const int k = (int)(rem - (long long)j * g.nz);
+    const bool c = is_candidate(g, chi, p, i, j, k, nyz);
+    cand[p] = c;
+    dE[p] = c ? flip_dE(chi[p], W[p], U[p], fc) : 0.0;
+}
+
+__global__ void k_min_z(GridDesc g, int r, const unsigned long long *__restrict__ K0,
+                        unsigned long long *__restrict__ K1, const int *done)
+{
+    if (rounds_done(done)) return;
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int k = (int)(p % g.nz);
+    unsigned long long m = ~0ull;
+    const int lo = max(-r, -k), hi = min(r, g.nz - 1 - k);
+    for (int a = lo; a <= hi; ++a) m = min(m, K0[p + a]);
+    K1[p] = m;
+}
+
+__global__ void k_min_y(GridDesc g, int r, const unsigned long long *__restrict__ K1,
+                        unsigned long long *__restrict__ K2, const int *done)
+{
+    if (rounds_done(done)) return;
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int j = (int)((p / g.nz) % g.ny);
+    unsigned long long m = ~0ull;
+    const int lo = max(-r, -j), hi = min(r, g.ny - 1 - j);
+    for (int b = lo; b <= hi; ++b) m = min(m, K1[p + (long long)b * g.nz]);
+    K2[p] = m;
+}
+
+__global__ void k_min_x_flip(GridDesc g, int r, const unsigned long long *__restrict__ K0,
+                             const unsigned long long *__restrict__ K2,
+                             const double *__restrict__ dE, uint8_t *__restrict__ chi,
+                             RoundState *rs)
+{
+    __shared__ double s_e[CT / 32];
+    __shared__ unsigned s_n[CT / 32];
+    if (rounds_done(&rs->done)) return;
+    const long long nyz = (long long)g.ny * g.nz;
+    const long long G = nyz * g.nx;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    unsigned flip = 0;
+    double e = 0.0;
+    if (p < G) {
+        const unsigned long long key = K0[p];
+        if (key != ~0ull) {
+            const int i = (int)(p / nyz);
+            unsigned long long m = ~0ull;
+            const int lo = max(-r, -i), hi = min(r, g.nx - 1 - i);
+            for (int c = lo; c <= hi; ++c) m = min(m, K2[p + (long long)c * nyz]);
+            if (m == key) {
+                chi[p] ^= 1;
+                flip = 1;
+                e = dE[p];
+            }
+        }
+    }
+    // block totals, one atomic per block
+    unsigned n = flip;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n += __shfl_down_sync(0xffffffffu, n, o);
+        e += __shfl_down_sync(0xffffffffu, e, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        s_n[w] = n;
+        s_e[w] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tn = 0;
+        double te = 0.0;
+        for (int q = 0; q < CT / 32; ++q) {
+            tn += s_n[q];
+            te += s_e[q];
+        }
+        if (tn) {
+            atomicAdd(&rs->round_flips, (unsigned long long)tn);
+            atomicAdd(&rs->round_dE, te);
+        }
+    }
+}
+
+__global__ void k_round_end(RoundState *rs)
+{
+    if (rs->done) return;
+    if (rs->round_flips == 0) {
+        rs->done = 1;
+    } else {
+        rs->round += 1;
+        rs->total_flips += rs->round_flips;
+        rs->total_dE += rs->round_dE;
+        if (rs->round >= rs->max_rounds) {
+            rs->done = 1;
+            rs->capped = 1;
+        }
+    }
+    rs->round_flips = 0;
+    rs->round_dE = 0.0;
+}
+
+// ----------------------------------------------------------------- sums
+int terms_blocks(long long G)
+{
+    long long nb = (G + CT - 1) / CT;
+    return (int)(nb < 1024 ? nb : 1024);
+}
+
+__global__ void __launch_bounds__(CT)
+k_terms(GridDesc g, const uint8_t *__restrict__ chi, const uint32_t *__restrict__ W,
+        const float *__restrict__ U, const float *__restrict__ Ex,
+        const float *__restrict__ Ey, const float *__restrict__ Ez, float cfa,
+        long long *__restrict__ part_s, double *__restrict__ part_v,
+        double *__restrict__ part_c)
+{
+    __shared__ long long s_s[CT / 32], s_n[CT / 32];
+    __shared__ double s_v[CT / 32], s_c[CT / 32];
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    long long S = 0, N = 0;
+    double V = 0.0, Cs = 0.0;
+    const long long stride = (long long)gridDim.x * CT;
+    for (long long p = (long long)blockIdx.x * CT + threadIdx.x; p < G; p += stride) {
+        if (chi[p]) {
+            S += (long long)(16777216u - W[p]);
+            N += 1;
+        } else {
+            V += (double)U[p];
+            if (Ex) {
+                const float ex = Ex[p], ey = Ey[p], ez = Ez[p];
+                Cs += (double)(cfa * fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        S += __shfl_down_sync(0xffffffffu, S, o);
+        N += __shfl_down_sync(0xffffffffu, N, o);
+        V += __shfl_down_sync(0xffffffffu, V, o);
+        Cs += __shfl_down_sync(0xffffffffu, Cs, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        s_s[w] = S;
+        s_n[w] = N;
+        s_v[w] = V;
+        s_c[w] = Cs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long ts = 0, tn = 0;
+        double tv = 0.0, tc = 0.0;
+        for (int q = 0; q < CT / 32; ++q) {
+            ts += s_s[q];
+            tn += s_n[q];
+            tv += s_v[q];
+            tc += s_c[q];
+        }
+        part_s[2 * blockIdx.x] = ts;
+        part_s[2 * blockIdx.x + 1] = tn;
+        part_v[blockIdx.x] = tv;
+        part_c[blockIdx.x] = tc;
+    }
+}
+
+__global__ void k_terms_final(const long long *__restrict__ part_s,
+                              const double *__restrict__ part_v,
+                              const double *__restrict__ part_c, int nb,
+                              double c, double D3, double h3, double *out)
+{
+    // one thread, fixed order: nb <= 1024
+    long long S = 0, N = 0;
+    double V = 0.0, Cs = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        S += part_s[2 * b];
+        N += part_s[2 * b + 1];
+        V += part_v[b];
+        Cs += part_c[b];
+    }
+    out[0] = c * ((double)S / D3);
+    out[1] = h3 * V;
+    out[2] = h3 * Cs;
+    out[3] = (double)N;
+}
+
+// ------------------------------------------------------------- initial chi
+__global__ void k_init_sphere(GridDesc g, float cx, float cy, float cz, float R,
+                              uint8_t *__restrict__ chi)
+{
+    const long long nyz = (long long)g.ny * g.nz;
+    const long long G = nyz * g.nx;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int i = (int)(p / nyz);
+    const long long rem = p - (long long)i * nyz;
+    const int j = (int)(rem / g.nz);
+    const int k = (int)(rem - (long long)j * g.nz);
+    const float dx = cell_pos(i, g.cx, g.h) - cx;
+    const float dy = cell_pos(j, g.cy, g.h) - cy;
+    const float dz = cell_pos(k, g.cz, g.h) - cz;
+    chi[p] = (sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) < R) ? 1 : 0;
+}
+
+constexpr int IT_TILE = 256;
+
+__global__ void __launch_bounds__(CT)
+k_init_tight(GridDesc g, const float4 *__restrict__ xyzd, int n,
+             uint8_t *__restrict__ chi)
+{
+    __shared__ float4 s_a[IT_TILE];
+    const long long nyz = (long long)g.ny * g.nz;
+    const long long G = nyz * g.nx;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    float x = 0.f, y = 0.f, z = 0.f;
+    if (p < G) {
+        const int i = (int)(p / nyz);
+        const long long rem = p - (long long)i * nyz;
+        const int j = (int)(rem / g.nz);
+        const int k = (int)(rem - (long long)j * g.nz);
+        x = cell_pos(i, g.cx, g.h);
+        y = cell_pos(j, g.cy, g.h);
+        z = cell_pos(k, g.cz, g.h);
+    }
+    float phi = 3.0e38f;
+    for (int base = 0; base < n; base += IT_TILE) {
+        const int cnt = min(IT_TILE, n - base);
+        __syncthreads();
+        for (int m = threadIdx.x; m < cnt; m += CT) s_a[m] = xyzd[base + m];
+        __syncthreads();
+        for (int m = 0; m < cnt; ++m) {
+            const float4 A = s_a[m];
+            const float dx = x - A.x, dy = y - A.y, dz = z - A.z;
+            phi = fminf(phi, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - A.w);
+        }
+    }
+    if (p < G) chi[p] = (phi < 0.f) ? 1 : 0;
+}
+
+// ------------------------------------------------------------- launchers
+void launch_conv_z(const GridDesc &g, const KernelW &kw, const uint8_t *chi,
+                   uint16_t *T1, const int *done, cudaStream_t st)
+{
+    count_launch();
+    k_conv_z<<<cell_blocks(g), CT, 0, st>>>(g, kw, chi, T1, done);
+}
+void launch_conv_y(const GridDesc &g, const KernelW &kw, const uint16_t *T1,
+                   uint32_t *T2, const int *done, cudaStream_t st)
+{
+    count_launch();
+    k_conv_y<<<cell_blocks(g), CT, 0, st>>>(g, kw, T1, T2, done);
+}
+void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
+                   uint32_t *W, cudaStream_t st)
+{
+    count_launch();
+    k_conv_x<<<cell_blocks(g), CT, 0, st>>>(g, kw, T2, W);
+}
+void launch_conv_x_key(const GridDesc &g, const KernelW &kw,
+                       const uint32_t *T2, const uint8_t *chi, const float *U,
+                       const FlipConst &fc, unsigned long long *K0,
+                       double *dE, const int *done, cudaStream_t st)
+{
+    count_launch();
+    k_conv_x_key<<<cell_blocks(g), CT, 0, st>>>(g, kw, T2, chi, U, fc, K0, dE, done);
+}
+void launch_flip_energy(const GridDesc &g, const uint32_t *W,
+                        const uint8_t *chi, const float *U, const FlipConst &fc,
+                        double *dE, uint8_t *cand, cudaStream_t st)
+{
+    count_launch();
+    k_flip_energy<<<cell_blocks(g), CT, 0, st>>>(g, W, chi, U, fc, dE, cand);
+}
+void launch_min_z(const GridDesc &g, int r, const unsigned long long *K0,
+                  unsigned long long *K1, const int *done, cudaStream_t st)
+{
+    count_launch();
+    k_min_z<<<cell_blocks(g), CT, 0, st>>>(g, r, K0, K1, done);
+}
+void launch_min_y(const GridDesc &g, int r, const unsigned long long *K1,
+                  unsigned long long *K2, const int *done, cudaStream_t st)
+{
+    count_launch();
+    k_min_y<<<cell_blocks(g), CT, 0, st>>>(g, r, K1, K2, done);
+}
+void launch_min_x_flip(const GridDesc &g, int r, const unsigned long long *K0,
+                       const unsigned long long *K2, const double *dE,
+                       uint8_t *chi, RoundState *rs, cudaStream_t st)
+{
+    count_launch();
+    k_min_x_flip<<<cell_blocks(g), CT, 0, st>>>(g, r, K0, K2, dE, chi, rs);
+}
+void launch_round_end(RoundState *rs, cudaStream_t st)
+{
+    count_launch();
+    k_round_end<<<1, 1, 0, st>>>(rs);
+}
+void launch_terms(const GridDesc &g, const uint8_t *chi, const uint32_t *W,
+                  const float *U, const float *Ex, const float *Ey,
+                  const float *Ez, float cfa, long long *part_s,
+                  double *part_v, double *part_c, cudaStream_t st)
+{
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    count_launch();
+    k_terms<<<terms_blocks(G), CT, 0, st>>>(g, chi, W, U, Ex, Ey, Ez, cfa,
+                                            part_s, part_v, part_c);
+}
+void launch_terms_final(const long long *part_s, const double *part_v,
+                        const double *part_c, int nb, double c, double D3,
+                        double h3, double *out, cudaStream_t st)
+{
+    count_launch();
+    k_terms_final<<<1, 1, 0, st>>>(part_s, part_v, part_c, nb, c, D3, h3, out);
+}
+void launch_init_sphere(const GridDesc &g, float cx, float cy, float cz,
+                        float radius, uint8_t *chi, cudaStream_t st)
+{
+    count_launch();
+    k_init_sphere<<<cell_blocks(g), CT, 0, st>>>(g, cx, cy, cz, radius, chi);
+}
+void launch_init_tight(const GridDesc &g, const float4 *xyzd, int n,
+                       uint8_t *chi, cudaStream_t st)
+{
+    count_launch();
+    k_init_tight<<<cell_blocks(g), CT, 0, st>>>(g, xyzd, n, chi);
+}
+
+}  // namespace vesis

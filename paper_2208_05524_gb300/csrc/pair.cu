@@ -1,0 +1,504 @@
+// Grid x atom pair kernels of the VESIS hot path (sm_103a, FP32 CUDA cores).
+//
+// Energy density (Eq. Ur): U(x) = rho_w sum_i U_LJ^(i)(r) + C |E(x)|^2 with
+// E(x) = sum_i Q_i d / r^3, d = x - r_i, r = max(|d|, r_min).  U_LJ is
+// written A r^-12 - B r^-6 with A = 4 eps sigma^12, B = 4 eps sigma^6.
+//
+// Gradient (exact derivative of the discrete energy, Eq. GradientG):
+//   d/dr_n [rho_w U_LJ] = rho_w r^-8 (12 A r^-6 - 6 B) d
+//   d/dr_n [C |E|^2]    = -2 C Q_n [E r^-3 - 3 (d.E) d r^-5]
+// with the LJ part and the d d^T part dropped where r is clamped.
+//
+// Atom tiles are staged in shared memory and read as warp-wide broadcasts;
+// every thread keeps PE_PTS cells of one z-pencil in registers, so the x/y
+// parts of the distance are formed once per atom and reused.
+#include "vesis_internal.cuh"
+
+namespace vesis {
+
+constexpr int PE_THREADS = 128;
+constexpr int PE_PTS = 8;
+constexpr int PE_TILE = 256;
+
+__global__ void __launch_bounds__(PE_THREADS)
+k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
+                   float *__restrict__ U, float *__restrict__ Ex,
+                   float *__restrict__ Ey, float *__restrict__ Ez)
+{
+    __shared__ float4 s_xyzq[PE_TILE];
+    __shared__ float2 s_ab[PE_TILE];
+    const int cpp = (g.nz + PE_PTS - 1) / PE_PTS;
+    const long long t = (long long)blockIdx.x * PE_THREADS + threadIdx.x;
+    const long long npen = (long long)g.nx * g.ny;
+    const long long pen = t / cpp;
+    const int chunk = (int)(t - pen * cpp);
+    const bool live = pen < npen;
+    const int i = live ? (int)(pen / g.ny) : 0;
+    const int j = live ? (int)(pen - (long long)i * g.ny) : 0;
+    const int k0 = chunk * PE_PTS;
+    const float px = cell_pos(i, g.cx, g.h);
+    const float py = cell_pos(j, g.cy, g.h);
+    float pz[PE_PTS], lj[PE_PTS], ex[PE_PTS], ey[PE_PTS], ez[PE_PTS];
+#pragma unroll
+    for (int p = 0; p < PE_PTS; ++p) {
+        pz[p] = cell_pos(k0 + p, g.cz, g.h);
+        lj[p] = ex[p] = ey[p] = ez[p] = 0.f;
+    }
+    for (int base = 0; base < a.n; base += PE_TILE) {
+        const int cnt = min(PE_TILE, a.n - base);
+        __syncthreads();
+        for (int m = threadIdx.x; m < cnt; m += PE_THREADS) {
+            s_xyzq[m] = a.xyzq[base + m];
+            s_ab[m] = a.ab[base + m];
+        }
+        __syncthreads();
+#pragma unroll 2
+        for (int m = 0; m < cnt; ++m) {
+            const float4 A = s_xyzq[m];
+            const float2 B = s_ab[m];
+            const float dx = px - A.x;
+            const float dy = py - A.y;
+            const float dxy2 = fmaf(dx, dx, dy * dy);
+#pragma unroll
+            for (int p = 0; p < PE_PTS; ++p) {
+                const float dz = pz[p] - A.z;
+                const float r2 = fmaxf(fmaf(dz, dz, dxy2), rmin2);
+                const float ri = rsqrtf(r2);
+                const float ri2 = ri * ri;
+                const float ri3 = ri2 * ri;
+                const float ri6 = ri3 * ri3;
+                const float tl = fmaf(B.x, ri6, -B.y);   // A r^-6 - B
+                lj[p] = fmaf(ri6, tl, lj[p]);
+                const float qr3 = A.w * ri3;
+                ex[p] = fmaf(qr3, dx, ex[p]);
+                ey[p] = fmaf(qr3, dy, ey[p]);
+                ez[p] = fmaf(qr3, dz, ez[p]);
+            }
+        }
+    }
+    if (!live) return;
+    const long long row = pen * g.nz;
+#pragma unroll
+    for (int p = 0; p < PE_PTS; ++p) {
+        const int k = k0 + p;
+        if (k < g.nz) {
+            const long long idx = row + k;
+            const float e2 = fmaf(ex[p], ex[p], fmaf(ey[p], ey[p], ez[p] * ez[p]));
+            U[idx] = fmaf(cfa, e2, rho * lj[p]);
+            Ex[idx] = ex[p];
+            Ey[idx] = ey[p];
+            Ez[idx] = ez[p];
+        }
+    }
+}
+
+void launch_pair_energy_grid(const GridDesc &g, const AtomsDev &a, float rho,
+                             float cfa, float rmin2, float *U, float *Ex,
+                             float *Ey, float *Ez, cudaStream_t st)
+{
+    const long long cpp = (g.nz + PE_PTS - 1) / PE_PTS;
+    const long long threads = (long long)g.nx * g.ny * cpp;
+    const long long blocks = (threads + PE_THREADS - 1) / PE_THREADS;
+    count_launch();
+    k_pair_energy_grid<<<(unsigned)blocks, PE_THREADS, 0, st>>>(
+        g, a, rho, cfa, rmin2, U, Ex, Ey, Ez);
+}
+
+// ------------------------------------------------------------ block sums
+// Fixed-order block reduction of a double (warp tree, then warp 0).
+template <int NT>
+__device__ double block_sum(double v, double *s_red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) s_red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (l < NT / 32) ? s_red[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;   // valid in thread 0
+}
+
+// ----------------------------------------------------- far-field nodes
+constexpr int PT_THREADS = 128;
+
+int point_energy_blocks(int np) { return (np + PT_THREADS - 1) / PT_THREADS; }
+
+__global__ void __launch_bounds__(PT_THREADS)
+k_point_energy(const float4 *__restrict__ pts, const double *__restrict__ w,
+               int np, AtomsDev a, float rho, float cfa, float rmin2,
+               float4 *__restrict__ UE, double *__restrict__ part)
+{
+    __shared__ float4 s_xyzq[PE_TILE];
+    __shared__ float2 s_ab[PE_TILE];
+    __shared__ double s_red[PT_THREADS / 32];
+    const int k = blockIdx.x * PT_THREADS + threadIdx.x;
+    const float4 P = (k < np) ? pts[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float lj = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+    for (int base = 0; base < a.n; base += PE_TILE) {
+        const int cnt = min(PE_TILE, a.n - base);
+        __syncthreads();
+        for (int m = threadIdx.x; m < cnt; m += PT_THREADS) {
+            s_xyzq[m] = a.xyzq[base + m];
+            s_ab[m] = a.ab[base + m];
+        }
+        __syncthreads();
+        for (int m = 0; m < cnt; ++m) {
+            const float4 A = s_xyzq[m];
+            const float2 B = s_ab[m];
+            const float dx = P.x - A.x, dy = P.y - A.y, dz = P.z - A.z;
+            const float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), rmin2);
+            const float ri = rsqrtf(r2);
+            const float ri2 = ri * ri, ri3 = ri2 * ri, ri6 = ri3 * ri3;
+            lj = fmaf(ri6, fmaf(B.x, ri6, -B.y), lj);
+            const float qr3 = A.w * ri3;
+            ex = fmaf(qr3, dx, ex);
+            ey = fmaf(qr3, dy, ey);
+            ez = fmaf(qr3, dz, ez);
+        }
+    }
+    double contrib = 0.0;
+    if (k < np) {
+        const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const float u = fmaf(cfa, e2, rho * lj);
+        UE[k] = make_float4(ex, ey, ez, u);
+        contrib = w[k] * (double)u;
+    }
+    const double s = block_sum<PT_THREADS>(contrib, s_red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+void launch_point_energy(const float4 *pts, const double *w, int np,
+                         const AtomsDev &a, float rho, float cfa, float rmin2,
+                         float4 *UE, double *part, cudaStream_t st)
+{
+    count_launch();
+    k_point_energy<<<point_energy_blocks(np), PT_THREADS, 0, st>>>(
+        pts, w, np, a, rho, cfa, rmin2, UE, part);
+}
+
+// ------------------------------------------------------ grid -> atoms
+constexpr int PF_THREADS = 128;
+constexpr int PF_APT = 2;                    // atoms per thread
+constexpr int PF_ATOMS = PF_THREADS * PF_APT;
+constexpr int PF_STAGE = 256;                // cells staged per pass
+
+ForcePlan plan_pair_force(long long G, int natoms, int nsm)
+{
+    ForcePlan fp;
+    fp.atom_tiles = (natoms + PF_ATOMS - 1) / PF_ATOMS;
+    const long long target = (long long)nsm * 8 * 4;
+    long long nchunk = target / fp.atom_tiles;
+    const long long maxc = (G + PF_STAGE - 1) / PF_STAGE;
+    if (nchunk < 1) nchunk = 1;
+    if (nchunk > maxc) nchunk = maxc;
+    long long len = (G + nchunk - 1) / nchunk;
+    len = (len + PF_STAGE - 1) / PF_STAGE * PF_STAGE;
+    fp.chunk_len = len;
+    fp.nchunk = (int)((G + len - 1) / len);
+    return fp;
+}
+
+// One pair's contribution to the gradient of atom (ax, ay, az) with
+// coefficients c1 = 12 rho A, c2 = -6 rho B, kq = -2 C Q; E is the field at
+// the point, wgt its weight.
+__device__ __forceinline__ void force_pair(float px, float py, float pz,
+                                           const float4 &E, float ax, float ay,
+                                           float az, float c1, float c2,
+                                           float kq, float rmin2, float &fx,
+                                           float &fy, float &fz)
+{
+    const float dx = px - ax, dy = py - ay, dz = pz - az;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const bool un = r2 >= rmin2;                    // not clamped
+    const float msk = un ? 1.f : 0.f;
+    const float m3 = un ? 3.f : 0.f;
+    const float ri = rsqrtf(fmaxf(r2, rmin2));
+    const float ri2 = ri * ri;
+    const float ri3 = ri2 * ri;
+    const float ri6 = ri3 * ri3;
+    const float ri8 = ri6 * ri2;
+    const float glj = fmaf(c1, ri6, c2) * (ri8 * msk);
+    const float dE = fmaf(dx, E.x, fmaf(dy, E.y, dz * E.z));
+    const float am = kq * ri3;
+    const float b = dE * ri2 * m3;
+    const float cd = fmaf(-am, b, glj);
+    fx = fmaf(cd, dx, fmaf(am, E.x, fx));
+    fy = fmaf(cd, dy, fmaf(am, E.y, fy));
+    fz = fmaf(cd, dz, fmaf(am, E.z, fz));
+}
+
+__global__ void __launch_bounds__(PF_THREADS)
+k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
+                  const uint8_t *__restrict__ chi, const float *__restrict__ Ex,
+                  const float *__restrict__ Ey, const float *__restrict__ Ez,
+                  AtomsDev a, float rmin2, double *__restrict__ part,
+                  unsigned long long *__restrict__ nsolvent)
+{
+    __shared__ float4 s_p[PF_STAGE];
+    __shared__ float4 s_e[PF_STAGE];
+    __shared__ int s_wc[2 * PF_THREADS / 32];
+    const int chunk = blockIdx.x;
+    const long long c0 = (long long)chunk * chunk_len;
+    const long long c1 = min(G, c0 + chunk_len);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = PF_THREADS / 32;
+
+    float ax[PF_APT], ay[PF_APT], az[PF_APT], k1[PF_APT], k2[PF_APT], kq[PF_APT];
+    int an[PF_APT];
+#pragma unroll
+    for (int u = 0; u < PF_APT; ++u) {
+        an[u] = blockIdx.y * PF_ATOMS + u * PF_THREADS + threadIdx.x;
+        if (an[u] < a.n) {
+            const float4 A = a.xyzq[an[u]];
+            const float4 F = a.fcoef[an[u]];
+            ax[u] = A.x; ay[u] = A.y; az[u] = A.z;
+            k1[u] = F.x; k2[u] = F.y; kq[u] = F.z;
+        } else {
+            ax[u] = ay[u] = az[u] = 0.f;
+            k1[u] = k2[u] = kq[u] = 0.f;
+        }
+    }
+    double acc[PF_APT][3];
+#pragma unroll
+    for (int u = 0; u < PF_APT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = 0.0;
+
+    const long long nyz = (long long)g.ny * g.nz;
+    unsigned long long seen = 0;
+    for (long long s = c0; s < c1; s += PF_STAGE) {
+        // stage the solvent cells of [s, s + PF_STAGE) in index order
+        bool v[2];
+        float4 P[2], Ev[2];
+#pragma unroll
+        for (int hlf = 0; hlf < 2; ++hlf) {
+            const long long idx = s + hlf * PF_THREADS + threadIdx.x;
+            v[hlf] = (idx < c1) && chi[idx] == 0;
+            if (v[hlf]) {
+                const int i = (int)(idx / nyz);
+                const long long rem = idx - (long long)i * nyz;
+                const int j = (int)(rem / g.nz);
+                const int k = (int)(rem - (long long)j * g.nz);
+                P[hlf] = make_float4(cell_pos(i, g.cx, g.h), cell_pos(j, g.cy, g.h),
+                                     cell_pos(k, g.cz, g.h), 0.f);
+                Ev[hlf] = make_float4(Ex[idx], Ey[idx], Ez[idx], 0.f);
+            }
+        }
+        const unsigned b0 = __ballot_sync(0xffffffffu, v[0]);
+        const unsigned b1 = __ballot_sync(0xffffffffu, v[1]);
+        __syncthreads();   // previous pass finished reading s_p / s_e
+        if (lane == 0) {
+            s_wc[warp] = __popc(b0);
+            s_wc[NW + warp] = __popc(b1);
+        }
+        __syncthreads();
+        int off0 = 0, off1 = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < 2 * NW; ++w) {
+            const int c = s_wc[w];
+            if (w < warp) off0 += c;
+            if (w < NW + warp) off1 += c;
+            tot += c;
+        }
+        const unsigned lt = (1u << lane) - 1u;
+        if (v[0]) {
+            const int pos = off0 + __popc(b0 & lt);
+            s_p[pos] = P[0];
+            s_e[pos] = Ev[0];
+        }
+        if (v[1]) {
+            const int pos = off1 + __popc(b1 & lt);
+            s_p[pos] = P[1];
+            s_e[pos] = Ev[1];
+        }
+        __syncthreads();
+        seen += (unsigned long long)tot;
+        float f[PF_APT][3];
+#pragma unroll
+        for (int u = 0; u < PF_APT; ++u) f[u][0] = f[u][1] = f[u][2] = 0.f;
+#pragma unroll 2
+        for (int p = 0; p < tot; ++p) {
+            const float4 Pp = s_p[p];
+            const float4 Ep = s_e[p];
+#pragma unroll
+            for (int u = 0; u < PF_APT; ++u)
+                force_pair(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
+                           k2[u], kq[u], rmin2, f[u][0], f[u][1], f[u][2]);
+        }
+#pragma unroll
+        for (int u = 0; u < PF_APT; ++u) {
+            acc[u][0] += (double)f[u][0];
+            acc[u][1] += (double)f[u][1];
+            acc[u][2] += (double)f[u][2];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PF_APT; ++u) {
+        if (an[u] < a.n) {
+            double *o = part + ((long long)chunk * a.n + an[u]) * 3;
+            o[0] = acc[u][0];
+            o[1] = acc[u][1];
+            o[2] = acc[u][2];
+        }
+    }
+    if (nsolvent && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(nsolvent, seen);
+}
+
+void launch_pair_force_grid(const GridDesc &g, const ForcePlan &fp,
+                            const uint8_t *chi, const float *Ex,
+                            const float *Ey, const float *Ez,
+                            const AtomsDev &a, float rmin2, double *part,
+                            unsigned long long *nsolvent, cudaStream_t st)
+{
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    dim3 grid(fp.nchunk, fp.atom_tiles);
+    count_launch();
+    k_pair_force_grid<<<grid, PF_THREADS, 0, st>>>(g, G, fp.chunk_len, chi, Ex,
+                                                   Ey, Ez, a, rmin2, part,
+                                                   nsolvent);
+}
+
+// Far-field nodes -> atoms: weighted points, all of them solvent.
+ForcePlan plan_point_force(int np, int natoms, int nsm)
+{
+    ForcePlan fp;
+    fp.atom_tiles = (natoms + PF_ATOMS - 1) / PF_ATOMS;
+    long long nchunk = ((long long)nsm * 8) / fp.atom_tiles;
+    const long long maxc = (np + PF_STAGE - 1) / PF_STAGE;
+    if (nchunk < 1) nchunk = 1;
+    if (nchunk > maxc) nchunk = maxc;
+    long long len = (np + nchunk - 1) / nchunk;
+    len = (len + PF_STAGE - 1) / PF_STAGE * PF_STAGE;
+    fp.chunk_len = len;
+    fp.nchunk = (int)((np + len - 1) / len);
+    return fp;
+}
+
+__global__ void __launch_bounds__(PF_THREADS)
+k_point_force(const float4 *__restrict__ pts, const float *__restrict__ wf,
+              int np, const float4 *__restrict__ UE, long long chunk_len,
+              AtomsDev a, float rmin2, double *__restrict__ part)
+{
+    __shared__ float4 s_p[PF_STAGE];
+    __shared__ float4 s_e[PF_STAGE];
+    const int chunk = blockIdx.x;
+    const long long c0 = (long long)chunk * chunk_len;
+    const long long c1 = min((long long)np, c0 + chunk_len);
+    float ax[PF_APT], ay[PF_APT], az[PF_APT], k1[PF_APT], k2[PF_APT], kq[PF_APT];
+    int an[PF_APT];
+#pragma unroll
+    for (int u = 0; u < PF_APT; ++u) {
+        an[u] = blockIdx.y * PF_ATOMS + u * PF_THREADS + threadIdx.x;
+        if (an[u] < a.n) {
+            const float4 A = a.xyzq[an[u]];
+            const float4 F = a.fcoef[an[u]];
+            ax[u] = A.x; ay[u] = A.y; az[u] = A.z;
+            k1[u] = F.x; k2[u] = F.y; kq[u] = F.z;
+        } else {
+            ax[u] = ay[u] = az[u] = 0.f;
+            k1[u] = k2[u] = kq[u] = 0.f;
+        }
+    }
+    double acc[PF_APT][3];
+#pragma unroll
+    for (int u = 0; u < PF_APT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = 0.0;
+    for (long long s = c0; s < c1; s += PF_STAGE) {
+        const int cnt = (int)min((long long)PF_STAGE, c1 - s);
+        __syncthreads();
+        for (int m = threadIdx.x; m < cnt; m += PF_THREADS) {
+            float4 P = pts[s + m];
+            P.w = wf[s + m];
+            s_p[m] = P;
+            s_e[m] = UE[s + m];
+        }
+        __syncthreads();
+        float f[PF_APT][3];
+#pragma unroll
+        for (int u = 0; u < PF_APT; ++u) f[u][0] = f[u][1] = f[u][2] = 0.f;
+        for (int p = 0; p < cnt; ++p) {
+            const float4 Pp = s_p[p];
+            const float4 Ep = s_e[p];
+#pragma unroll
+            for (int u = 0; u < PF_APT; ++u) {
+                float gx = 0.f, gy = 0.f, gz = 0.f;
+                force_pair(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
+                           k2[u], kq[u], rmin2, gx, gy, gz);
+                f[u][0] = fmaf(Pp.w, gx, f[u][0]);
+                f[u][1] = fmaf(Pp.w, gy, f[u][1]);
+                f[u][2] = fmaf(Pp.w, gz, f[u][2]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PF_APT; ++u) {
+            acc[u][0] += (double)f[u][0];
+            acc[u][1] += (double)f[u][1];
+            acc[u][2] += (double)f[u][2];
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PF_APT; ++u) {
+        if (an[u] < a.n) {
+            double *o = part + ((long long)chunk * a.n + an[u]) * 3;
+            o[0] = acc[u][0];
+            o[1] = acc[u][1];
+            o[2] = acc[u][2];
+        }
+    }
+}
+
+void launch_point_force(const float4 *pts, const float *wf, int np,
+                        const float4 *UE, const ForcePlan &fp,
+                        const AtomsDev &a, float rmin2, double *part,
+                        cudaStream_t st)
+{
+    dim3 grid(fp.nchunk, fp.atom_tiles);
+    count_launch();
+    k_point_force<<<grid, PF_THREADS, 0, st>>>(pts, wf, np, UE, fp.chunk_len,
+                                               a, rmin2, part);
+}
+
+// ------------------------------------------------------ ordered reductions
+__global__ void k_force_reduce(const double *__restrict__ part, int nchunk,
+                               int natoms, double scale, double *__restrict__ out,
+                               int accumulate)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n3 = natoms * 3;
+    if (t >= n3) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += part[(long long)c * n3 + t];
+    s *= scale;
+    out[t] = accumulate ? out[t] + s : s;
+}
+
+void launch_force_reduce(const double *part, int nchunk, int natoms,
+                         double scale, double *out, int accumulate,
+                         cudaStream_t st)
+{
+    const int n3 = natoms * 3;
+    count_launch();
+    k_force_reduce<<<(n3 + 255) / 256, 256, 0, st>>>(part, nchunk, natoms,
+                                                     scale, out, accumulate);
+}
+
+__global__ void __launch_bounds__(1024)
+k_sum_doubles(const double *__restrict__ in, int n, double *out, int accumulate)
+{
+    __shared__ double s_red[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) v += in[i];
+    const double s = block_sum<1024>(v, s_red);
+    if (threadIdx.x == 0) out[0] = accumulate ? out[0] + s : s;
+}
+
+void launch_sum_doubles(const double *in, int n, double *out, int accumulate,
+                        cudaStream_t st)
+{
+    count_launch();
+    k_sum_doubles<<<1, 1024, 0, st>>>(in, n, out, accumulate);
+}
+
+}  // namespace vesis

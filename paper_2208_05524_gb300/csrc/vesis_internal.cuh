@@ -1,0 +1,161 @@
+// Internal declarations of the VESIS CUDA library (sm_103a).
+// Shared by the library's translation units only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vesis {
+
+constexpr int kMaxR = 8;  // largest kernel half-width in cells
+
+// Grid geometry in box-centred FP32 coordinates: the centre of cell i on
+// an axis with n cells is (i - (n - 1)/2) h, exact up to one rounding.
+struct GridDesc {
+    int nx, ny, nz;
+    float h;
+    float cx, cy, cz;  // (n - 1) / 2 per axis
+};
+
+__device__ __forceinline__ float cell_pos(int i, float half, float h) {
+    return ((float)i - half) * h;
+}
+
+// Integer 1-D weights q[a + r], a = -r..r, of the product surface kernel.
+struct KernelW {
+    int r;
+    int q[2 * kMaxR + 1];
+};
+
+// Device views of the atom data (box-centred FP32 coordinates).
+struct AtomsDev {
+    int n;
+    const float4 *xyzq;   // x, y, z, Q
+    const float2 *ab;     // A = 4 eps sigma^12, B = 4 eps sigma^6
+    const float4 *fcoef;  // 12 rho_w A, -6 rho_w B, -2 C Q, 0
+};
+
+// Per-relaxation flip-round state, in device memory.
+struct RoundState {
+    int done;              // 1 once a round flips nothing or the cap is hit
+    int round;             // rounds that flipped cells
+    int capped;            // 1 if max_rounds stopped the rounds
+    int max_rounds;
+    unsigned long long round_flips;   // flips of the round in progress
+    unsigned long long total_flips;
+    double round_dE;       // sum of dE of the round in progress
+    double total_dE;
+};
+
+// Counts kernel launches made by the library (reported by the timing API).
+void count_launch(int n = 1);
+long long launch_count();
+
+// ---------------------------------------------------------------- pair.cu
+void launch_pair_energy_grid(const GridDesc &g, const AtomsDev &a, float rho,
+                             float cfa, float rmin2, float *U, float *Ex,
+                             float *Ey, float *Ez, cudaStream_t st);
+// Far-field nodes: pts[k] = (x, y, z, _); writes U, E per node and the
+// FP64 partial sums of w_k U_k per block into part (nblocks doubles).
+int point_energy_blocks(int np);
+void launch_point_energy(const float4 *pts, const double *w, int np,
+                         const AtomsDev &a, float rho, float cfa, float rmin2,
+                         float4 *UE, double *part, cudaStream_t st);
+// Grid -> atom gradient partials: part[chunk][atom][3] (FP64); the solvent
+// cells visited are added to *nsolvent (may be NULL).
+struct ForcePlan {
+    int nchunk;
+    long long chunk_len;
+    int atom_tiles;
+};
+ForcePlan plan_pair_force(long long G, int natoms, int nsm);
+void launch_pair_force_grid(const GridDesc &g, const ForcePlan &fp,
+                            const uint8_t *chi, const float *Ex,
+                            const float *Ey, const float *Ez,
+                            const AtomsDev &a, float rmin2, double *part,
+                            unsigned long long *nsolvent, cudaStream_t st);
+// Point-list (far-field) gradient partials: part[chunk][atom][3].
+ForcePlan plan_point_force(int np, int natoms, int nsm);
+void launch_point_force(const float4 *pts, const float *wf, int np,
+                        const float4 *UE, const ForcePlan &fp,
+                        const AtomsDev &a, float rmin2, double *part,
+                        cudaStream_t st);
+// Sum of partials in chunk order, scaled: out[n*3+l] (FP64).
+void launch_force_reduce(const double *part, int nchunk, int natoms,
+                         double scale, double *out, int accumulate,
+                         cudaStream_t st);
+// Ordered sum of `n` doubles (single block) into out[0] (optionally added).
+void launch_sum_doubles(const double *in, int n, double *out, int accumulate,
+                        cudaStream_t st);
+
+// ---------------------------------------------------------------- blsm.cu
+void launch_conv_z(const GridDesc &g, const KernelW &kw, const uint8_t *chi,
+                   uint16_t *T1, const int *done, cudaStream_t st);
+void launch_conv_y(const GridDesc &g, const KernelW &kw, const uint16_t *T1,
+                   uint32_t *T2, const int *done, cudaStream_t st);
+void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
+                   uint32_t *W, cudaStream_t st);
+struct FlipConst {
+    double c, g0, h3, invD3;
+};
+void launch_conv_x_key(const GridDesc &g, const KernelW &kw,
+                       const uint32_t *T2, const uint8_t *chi, const float *U,
+                       const FlipConst &fc, unsigned long long *K0,
+                       double *dE, const int *done, cudaStream_t st);
+void launch_flip_energy(const GridDesc &g, const uint32_t *W,
+                        const uint8_t *chi, const float *U, const FlipConst &fc,
+                        double *dE, uint8_t *cand, cudaStream_t st);
+void launch_min_z(const GridDesc &g, int r, const unsigned long long *K0,
+                  unsigned long long *K1, const int *done, cudaStream_t st);
+void launch_min_y(const GridDesc &g, int r, const unsigned long long *K1,
+                  unsigned long long *K2, const int *done, cudaStream_t st);
+void launch_min_x_flip(const GridDesc &g, int r, const unsigned long long *K0,
+                       const unsigned long long *K2, const double *dE,
+                       uint8_t *chi, RoundState *rs, cudaStream_t st);
+void launch_round_end(RoundState *rs, cudaStream_t st);
+// Energy sums over a labelled grid: per-block partials then ordered final.
+int terms_blocks(long long G);
+void launch_terms(const GridDesc &g, const uint8_t *chi, const uint32_t *W,
+                  const float *U, const float *Ex, const float *Ey,
+                  const float *Ez, float cfa, long long *part_s,
+                  double *part_v, double *part_c, cudaStream_t st);
+// out[0] = c * S / D^3, out[1] = h^3 * sum U (solvent), out[2] = h^3 * sum
+// C|E|^2 (solvent), out[3] = number of solute cells.
+void launch_terms_final(const long long *part_s, const double *part_v,
+                        const double *part_c, int nb, double c, double D3,
+                        double h3, double *out, cudaStream_t st);
+void launch_init_sphere(const GridDesc &g, float cx, float cy, float cz,
+                        float radius, uint8_t *chi, cudaStream_t st);
+void launch_init_tight(const GridDesc &g, const float4 *xyzd, int n,
+                       uint8_t *chi, cudaStream_t st);
+
+// --------------------------------------------------------------- atoms.cu
+struct AtomParamsDev {
+    const double *sig_sw, *eps_sw, *q;   // per atom, FP64
+};
+// Packs FP64 positions (relative to the box centre) into the FP32 views.
+void launch_pack_atoms(const double *xyz, const double *centre,
+                       const double *sig, const double *eps, const double *q,
+                       int n, double rho, double cfa, float4 *xyzq,
+                       float2 *ab, float4 *fcoef, int *oob, const double *lo,
+                       const double *hi, cudaStream_t st);
+// Solute-solute energy and gradient in FP64 (Eq. Gss): e_part[block][3]
+// (bond, LJ, Coulomb), grad[n][3] overwritten.
+int ss_blocks(int n);
+void launch_ss(const double *xyz, const double *sig, const double *sqeps,
+               const double *q, const int *excl, const int *bond_ptr,
+               const int *bond_other, const double *bond_k,
+               const double *bond_r0, int n, double coul, double *e_part,
+               double *grad, cudaStream_t st);
+void launch_ss_final(const double *e_part, int nb, double *out3,
+                     cudaStream_t st);
+// grad = a + b (+ c), and the max |component| into *gmax (FP64 bits).
+void launch_grad_combine(const double *a, const double *b, double *grad,
+                         int n3, unsigned long long *gmax_bits,
+                         cudaStream_t st);
+// xyz_new = xyz - (M / gmax) grad (Eq. moveatoms, Eq. adjustmml).
+void launch_mobility(const double *xyz, const double *grad,
+                     const unsigned long long *gmax_bits, const double *M,
+                     double *xyz_new, int n3, cudaStream_t st);
+
+}  // namespace vesis

@@ -1,0 +1,285 @@
+"""ctypes binding of libvesis.so (C ABI in include/vesis.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  Device arrays are torch CUDA tensors (contiguous, on the device
+the system was created on); host arrays are numpy float64.  If the library
+is missing the import of `lib()` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvesis.so")
+
+_d, _i, _p, _ll = C.c_double, C.c_int, C.c_void_p, C.c_longlong
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma0", _d), ("rho_w", _d), ("eps_m", _d), ("eps_w", _d),
+                ("temperature", _d), ("eps_ss", _d), ("nx", _i), ("ny", _i),
+                ("nz", _i), ("h", _d), ("origin", _d * 3),
+                ("gauss_sigma", _d), ("trunc_r", _i), ("r_min", _d),
+                ("far_field", _i), ("far_nuv", _i), ("far_nt", _i)]
+
+
+class RelaxOpts(C.Structure):
+    _fields_ = [("max_outer", _i), ("ncnt_star", _i), ("window", _i),
+                ("M0", _d), ("alpha", _d), ("dgstar_frac", _d),
+                ("tol_grad", _d), ("tol_energy", _d), ("max_flip_rounds", _i),
+                ("max_gd_retries", _i)]
+
+
+class RelaxStats(C.Structure):
+    _fields_ = [("status", _i), ("iterations", _i), ("stop_reason", _i),
+                ("flip_rounds", _ll), ("flips", _ll), ("gd_trials", _ll),
+                ("pair_evals", _ll), ("G", _d), ("terms", _d * 6), ("M", _d),
+                ("max_grad", _d)]
+
+
+class Timing(C.Structure):
+    _fields_ = [("pair_energy_ms", _d), ("pair_energy_launches", _ll),
+                ("pair_energy_pairs", _ll), ("pair_force_ms", _d),
+                ("pair_force_launches", _ll), ("pair_force_pairs", _ll),
+                ("sweep_ms", _d), ("sweep_rounds", _ll), ("sweep_cells", _ll),
+                ("kernel_launches", _ll)]
+
+
+STATUS = {0: "OK", -1: "E_ARG", -2: "E_CUDA", -3: "E_NAN", -4: "E_OUT_OF_BOX",
+          -5: "E_ALLOC", 1: "W_MAX_ROUNDS", 2: "W_NOT_CONVERGED"}
+TERMS = ("surf", "vdw", "cfa", "far", "ss", "total")
+
+
+class VesisError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"vesis {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libvesis.so (built by paper_2208_05524_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libvesis.so is not built; run paper_2208_05524_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        L.vesis_default_params.argtypes = [C.POINTER(Params)]
+        L.vesis_default_params.restype = None
+        L.vesis_default_relax_opts.argtypes = [C.POINTER(RelaxOpts)]
+        L.vesis_default_relax_opts.restype = None
+        L.vesis_init_system.argtypes = [C.POINTER(Params), _i, _p, _p, _p, _p,
+                                        _p, _p, _i, _p, _p, _p, _p,
+                                        C.POINTER(_p)]
+        L.vesis_set_positions.argtypes = [_p, _p]
+        L.vesis_get_positions.argtypes = [_p, _p]
+        L.vesis_init_labels.argtypes = [_p, _i, _p, _d, _p, _p]
+        L.vesis_energy_field.argtypes = [_p, _p, _p, _p, _p, _p]
+        L.vesis_energy_terms.argtypes = [_p, _p, _p, _p, _p]
+        L.vesis_surface_weights.argtypes = [_p, _p, _p]
+        L.vesis_flip_energies.argtypes = [_p, _p, _p, _p, _p]
+        L.vesis_blsm_relax.argtypes = [_p, _p, _p, _p, _i, C.POINTER(_i),
+                                       C.POINTER(_ll), C.POINTER(_d), _p]
+        L.vesis_atom_forces.argtypes = [_p, _p, _p, _p, _p, _p]
+        L.vesis_relax.argtypes = [_p, _p, _p, C.POINTER(RelaxOpts),
+                                  C.POINTER(RelaxStats)]
+        L.vesis_set_timing.argtypes = [_p, _i]
+        L.vesis_get_timing.argtypes = [_p, C.POINTER(Timing)]
+        L.vesis_destroy.argtypes = [_p]
+        L.vesis_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc, allow_warn=True):
+    if rc < 0 or (rc > 0 and not allow_warn):
+        raise VesisError(rc, lib().vesis_last_error().decode())
+    return rc
+
+
+def _np(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a):
+    return a.ctypes.data_as(_p) if a is not None else None
+
+
+def _dp(t, dtype=None, numel=None):
+    """Raw device pointer of a contiguous CUDA tensor (checked)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous CUDA tensors")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"tensor too small: {t.numel()} < {numel}")
+    return _p(t.data_ptr())
+
+
+def default_params(**kw):
+    p = Params()
+    lib().vesis_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "origin":
+            p.origin[:] = [float(x) for x in v]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def default_relax_opts(**kw):
+    o = RelaxOpts()
+    lib().vesis_default_relax_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class System:
+    """One solute system on the current CUDA device.
+
+    sysd: dict from paper_2208_05524_gb300.synth (atoms, grid, bonds).
+    params: overrides of vesis_params fields (gauss_sigma <= 0 means 2 h).
+    stream: torch.cuda.Stream (default: the current stream)."""
+
+    def __init__(self, sysd, stream=None, **params):
+        import torch
+        n = [int(v) for v in sysd["n"]]
+        p = default_params(nx=n[0], ny=n[1], nz=n[2], h=float(sysd["h"]),
+                           origin=sysd["origin"])
+        for k, v in params.items():
+            if k == "origin":
+                p.origin[:] = [float(x) for x in v]
+            else:
+                setattr(p, k, v)
+        self.params = p
+        self.n_atoms = len(sysd["xyz"])
+        self.G = n[0] * n[1] * n[2]
+        self.shape = tuple(n)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._keep = [_np(sysd[k]) for k in ("xyz", "sigma_sw", "eps_sw", "q",
+                                            "sigma_ss", "eps_ss")]
+        bonds = _np(sysd["bonds"], np.int32).reshape(-1, 2)
+        bk, br = _np(sysd["bond_k"]), _np(sysd["bond_r0"])
+        self._keep += [bonds, bk, br]
+        h = _p()
+        _check(lib().vesis_init_system(
+            C.byref(p), self.n_atoms, *[_hp(a) for a in self._keep[:6]],
+            len(bonds), _hp(bonds), _hp(bk), _hp(br),
+            _p(self.stream.cuda_stream), C.byref(h)), allow_warn=False)
+        self.h = h
+
+    # ------------------------------------------------------------- calls
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vesis_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_positions(self, xyz):
+        a = _np(xyz).reshape(-1, 3)
+        _check(lib().vesis_set_positions(self.h, _hp(a)), allow_warn=False)
+
+    def get_positions(self):
+        out = np.zeros((self.n_atoms, 3))
+        _check(lib().vesis_get_positions(self.h, _hp(out)), allow_warn=False)
+        return out
+
+    def init_labels(self, chi, kind="tight", d=None, radius=0.0, center=None):
+        import torch
+        k = {"sphere": 0, "tight": 1}[kind]
+        dd = None if d is None else _np(d)
+        cc = None if center is None else _np(center)
+        _check(lib().vesis_init_labels(self.h, k, _hp(dd), float(radius),
+                                       _hp(cc), _dp(chi, torch.uint8, self.G)))
+
+    def energy_field(self, U, E=None, chi=None, xyz=None, terms=False):
+        import torch
+        out = (_d * 6)() if terms else None
+        x = None if xyz is None else _np(xyz).reshape(-1, 3)
+        _check(lib().vesis_energy_field(
+            self.h, _hp(x), _dp(U, torch.float32, self.G),
+            _dp(E, torch.float32, 3 * self.G) if E is not None else None,
+            _dp(chi, torch.uint8, self.G) if chi is not None else None,
+            C.cast(out, _p) if out is not None else None))
+        return dict(zip(TERMS, list(out))) if out is not None else None
+
+    def energy_terms(self, chi, U, E=None):
+        import torch
+        out = (_d * 6)()
+        _check(lib().vesis_energy_terms(
+            self.h, _dp(chi, torch.uint8, self.G), _dp(U, torch.float32, self.G),
+            _dp(E, torch.float32, 3 * self.G) if E is not None else None,
+            C.cast(out, _p)))
+        return dict(zip(TERMS, list(out)))
+
+    def surface_weights(self, chi, W):
+        import torch
+        _check(lib().vesis_surface_weights(
+            self.h, _dp(chi, torch.uint8, self.G), _dp(W, torch.int32, self.G)))
+
+    def flip_energies(self, chi, U, dE, cand):
+        import torch
+        _check(lib().vesis_flip_energies(
+            self.h, _dp(chi, torch.uint8, self.G), _dp(U, torch.float32, self.G),
+            _dp(dE, torch.float64, self.G), _dp(cand, torch.uint8, self.G)))
+
+    def blsm_relax(self, chi, U, E=None, max_rounds=100000, terms=True):
+        import torch
+        rounds, flips, dsum = _i(0), _ll(0), _d(0.0)
+        out = (_d * 6)() if terms else None
+        rc = _check(lib().vesis_blsm_relax(
+            self.h, _dp(chi, torch.uint8, self.G), _dp(U, torch.float32, self.G),
+            _dp(E, torch.float32, 3 * self.G) if E is not None else None,
+            int(max_rounds), C.byref(rounds), C.byref(flips), C.byref(dsum),
+            C.cast(out, _p) if out is not None else None))
+        r = dict(status=rc, rounds=rounds.value, flips=flips.value,
+                 dE_sum=dsum.value)
+        if out is not None:
+            r["terms"] = dict(zip(TERMS, list(out)))
+        return r
+
+    def atom_forces(self, chi, xyz=None, E=None, energy=False):
+        import torch
+        g = np.zeros((self.n_atoms, 3))
+        e = _d(0.0)
+        x = None if xyz is None else _np(xyz).reshape(-1, 3)
+        _check(lib().vesis_atom_forces(
+            self.h, _dp(chi, torch.uint8, self.G), _hp(x),
+            _dp(E, torch.float32, 3 * self.G) if E is not None else None,
+            _hp(g), C.byref(e) if energy else None))
+        return (g, e.value) if energy else g
+
+    def set_timing(self, enable=True):
+        _check(lib().vesis_set_timing(self.h, int(bool(enable))))
+
+    def get_timing(self):
+        t = Timing()
+        _check(lib().vesis_get_timing(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Timing._fields_}
+
+    def relax(self, chi, xyz, **opts):
+        import torch
+        o = default_relax_opts(**opts)
+        x = _np(xyz).reshape(-1, 3).copy()
+        st = RelaxStats()
+        rc = _check(lib().vesis_relax(self.h, _dp(chi, torch.uint8, self.G),
+                                      _hp(x), C.byref(o), C.byref(st)))
+        res = {f: getattr(st, f) for f, _ in RelaxStats._fields_ if f != "terms"}
+        res["terms"] = dict(zip(TERMS, list(st.terms)))
+        res["status"] = rc
+        res["xyz"] = x
+        return res

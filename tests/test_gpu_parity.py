@@ -1,0 +1,303 @@
+"""CUDA path vs the FP64 CPU oracle, through the C ABI (needs a GPU).
+
+Tolerances (stated once, used below):
+  * fields U, E: FP32 pair sums vs FP64: |gpu - oracle| <= 1e-4 |oracle|
+    + 1e-4 max|oracle| (relative 1e-4 per cell with a floor).
+  * W (kernel convolution), flip energies, candidate masks, labels after a
+    sweep from the same FP32 U: bit-exact.
+  * energy totals: relative 1e-6 (FP64 sums of FP32 cell values).
+  * gradients: |gpu - oracle| <= 1e-4 |oracle| + 1e-4 max|oracle|.
+  * converged positions: 1e-3 A.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2208_05524_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _vs():
+    from paper_2208_05524_gb300 import vesis
+    return vesis
+
+
+def _dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda").to(dtype).contiguous()
+
+
+def _fields_gpu(S, n):
+    G = int(np.prod(n))
+    U = torch.empty(G, dtype=torch.float32, device="cuda")
+    E = torch.empty(3 * G, dtype=torch.float32, device="cuda")
+    return U, E
+
+
+def _close(gpu, ref, rel=1e-4):
+    ref = np.asarray(ref, np.float64)
+    gpu = np.asarray(gpu, np.float64)
+    tol = rel * np.abs(ref) + rel * np.abs(ref).max()
+    bad = np.abs(gpu - ref) > tol
+    return int(bad.sum()), float(np.max(np.abs(gpu - ref) / (tol + 1e-300)))
+
+
+# ------------------------------------------------------------------ fields
+
+@pytest.mark.parametrize("n,h,natoms,seed", [((40, 36, 28), 0.5, 30, 1),
+                                             ((17, 23, 29), 0.9, 300, 2)])
+def test_energy_field_matches_oracle(n, h, natoms, seed):
+    vs = _vs()
+    s = synth.random_cluster(natoms, 8, h, seed=seed, net_charge=-1.0)
+    s["n"] = np.array(n)
+    s["origin"] = -0.5 * np.array(n) * h
+    p = O.params()
+    S = vs.System(s)
+    U, E = _fields_gpu(S, n)
+    S.energy_field(U, E)
+    Uo, _, Eo = O.fields(s, p)
+    nb, worst = _close(U.cpu().numpy(), Uo.reshape(-1))
+    assert nb == 0, worst
+    Eg = E.cpu().numpy().reshape(3, -1).T
+    nb, worst = _close(Eg, Eo.reshape(-1, 3))
+    assert nb == 0, worst
+
+
+def test_energy_field_single_ion_and_terms():
+    vs = _vs()
+    s = synth.single_ion()
+    p = O.params()
+    S = vs.System(s)
+    n = tuple(int(v) for v in s["n"])
+    U, E = _fields_gpu(S, n)
+    chi0 = O.init_labels(s)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    T = S.energy_field(U, E, chi=chi, terms=True)
+    Uo, _, Eo = O.fields(s, p)
+    nb, worst = _close(U.cpu().numpy(), Uo.reshape(-1))
+    assert nb == 0, worst
+    To = O.energy_terms(s, p, chi0, U=Uo, E=Eo)
+    for k in ("surf", "far", "ss"):
+        assert T[k] == pytest.approx(To[k], rel=1e-6, abs=1e-9)
+    assert T["vdw"] + T["cfa"] == pytest.approx(To["vol"], rel=1e-6)
+    assert T["total"] == pytest.approx(To["total"], rel=1e-6)
+
+
+def test_init_labels_match_oracle():
+    vs = _vs()
+    s = synth.random_cluster(60, 8, 0.45, seed=3)
+    s["n"] = np.array([48, 44, 40])
+    s["origin"] = -0.5 * s["n"] * 0.45
+    S = vs.System(s)
+    G = int(np.prod(s["n"]))
+    chi = torch.empty(G, dtype=torch.uint8, device="cuda")
+    S.init_labels(chi, "tight")
+    ref = O.init_labels(s).reshape(-1)
+    got = chi.cpu().numpy()
+    diff = np.nonzero(got != ref)[0]
+    if len(diff):
+        _, phi = O.init_labels_at(s, diff)
+        assert np.all(np.abs(phi) < 1e-4)
+    s2 = synth.single_ion(n=40, h=0.4, r_init=5.3)
+    S2 = vs.System(s2)
+    c2 = torch.empty(40 ** 3, dtype=torch.uint8, device="cuda")
+    S2.init_labels(c2, "sphere", radius=5.3)
+    assert np.array_equal(c2.cpu().numpy(), O.init_labels(s2).reshape(-1))
+
+
+# --------------------------------------------------------------- surface
+
+@pytest.mark.parametrize("n", [(37, 29, 41), (8, 9, 10), (1, 5, 64)])
+def test_surface_weights_exact(n):
+    vs = _vs()
+    s = synth.single_ion(n=8, h=0.3)
+    s["n"] = np.array(n)
+    S = vs.System(s)
+    chi0 = synth.random_labels(n, seed=sum(n), p=0.4)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    W = torch.empty(int(np.prod(n)), dtype=torch.int32, device="cuda")
+    S.surface_weights(chi, W)
+    sc = O.surface_constants(s, O.params())
+    assert np.array_equal(W.cpu().numpy().astype(np.int64), O.conv(chi0, sc["q"]).reshape(-1))
+
+
+def test_flip_energies_bit_exact():
+    vs = _vs()
+    n = (33, 30, 27)
+    s = synth.single_ion(n=8, h=0.35)
+    s["n"] = np.array(n)
+    S = vs.System(s)
+    chi0 = synth.random_labels(n, seed=4, p=0.5)
+    U32 = synth.random_field(n, seed=5, scale=0.3)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    U = _dev(U32.reshape(-1), torch.float32)
+    G = int(np.prod(n))
+    dE = torch.empty(G, dtype=torch.float64, device="cuda")
+    cand = torch.empty(G, dtype=torch.uint8, device="cuda")
+    S.flip_energies(chi, U, dE, cand)
+    sc = O.surface_constants(s, O.params())
+    dEo, co = O.delta_e(chi0, U32.astype(np.float64), sc)
+    assert np.array_equal(cand.cpu().numpy(), co.reshape(-1))
+    assert np.array_equal(dE.cpu().numpy(), dEo.reshape(-1))
+
+
+def _blob(n, seed):
+    """Seeded label field with structure: a union of random balls."""
+    rng = np.random.default_rng(seed)
+    idx = np.indices(n).reshape(3, -1).T.astype(np.float64)
+    chi = np.zeros(int(np.prod(n)), np.uint8)
+    for _ in range(6):
+        c = rng.uniform(0.25, 0.75, 3) * np.array(n)
+        r = rng.uniform(0.1, 0.3) * min(n)
+        chi |= (np.linalg.norm(idx - c, axis=1) < r).astype(np.uint8)
+    return chi.reshape(n)
+
+
+@pytest.mark.parametrize("n,seed", [((30, 28, 26), 1), ((45, 17, 50), 2)])
+def test_blsm_rounds_bit_exact(n, seed):
+    vs = _vs()
+    s = synth.single_ion(n=8, h=0.3)
+    s["n"] = np.array(n)
+    S = vs.System(s)
+    chi0 = _blob(n, seed)
+    U32 = (synth.random_field(n, seed=seed + 10, scale=0.05) - 0.02).astype(np.float32)
+    sc = O.surface_constants(s, O.params())
+    ref = chi0.copy()
+    ro = O.blsm_parallel(ref, U32.astype(np.float64), sc, record_rounds=True)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    U = _dev(U32.reshape(-1), torch.float32)
+    r = S.blsm_relax(chi, U, terms=False)
+    assert r["rounds"] == ro["rounds"]
+    assert r["flips"] == ro["flips"]
+    assert r["dE_sum"] == pytest.approx(ro["dE_sum"], rel=1e-12, abs=1e-12)
+    assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
+    # the same after a capped number of rounds
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    k = max(1, ro["rounds"] // 3)
+    r = S.blsm_relax(chi, U, max_rounds=k, terms=False)
+    ref2 = chi0.copy()
+    O.blsm_parallel(ref2, U32.astype(np.float64), sc, max_rounds=k)
+    assert r["rounds"] == k
+    assert np.array_equal(chi.cpu().numpy(), ref2.reshape(-1))
+
+
+def test_blsm_single_ion_full_size():
+    """64^3 single ion: identical labels and rounds from the same FP32 U;
+    the relaxed radius and energy meet the closed-form sphere minimum."""
+    vs = _vs()
+    s = synth.single_ion()
+    p = O.params()
+    n = tuple(int(v) for v in s["n"])
+    Uo, _, Eo = O.fields(s, p)
+    U32 = Uo.astype(np.float32)
+    sc = O.surface_constants(s, p)
+    chi0 = O.init_labels(s)
+    ref = chi0.copy()
+    ro = O.blsm_parallel(ref, U32.astype(np.float64), sc)
+    S = vs.System(s)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    r = S.blsm_relax(chi, _dev(U32.reshape(-1), torch.float32), terms=False)
+    assert r["rounds"] == ro["rounds"] and r["flips"] == ro["flips"]
+    assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
+    # GPU's own FP32 fields: labels may differ only where the oracle's
+    # |dE| is below 1e-9 kBT; energy at the closed-form minimum
+    U, E = _fields_gpu(S, n)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    S.energy_field(U, E)
+    r = S.blsm_relax(chi, U, E)
+    got = chi.cpu().numpy().reshape(n)
+    mism = np.argwhere(got != ref)
+    if len(mism):
+        dEo, _ = O.delta_e(ref, Uo, sc)
+        assert np.all(np.abs(dEo[tuple(mism.T)]) < 1e-9), len(mism)
+    Rs, Gs = O.sphere_minimum(3.5, s["eps_sw"][0], 1.0, p)
+    R_eq = (3 * got.sum() * sc["h3"] / (4 * math.pi)) ** (1 / 3)
+    assert abs(R_eq - Rs) < s["h"]
+    assert r["terms"]["total"] == pytest.approx(Gs, rel=0.01)
+    To = O.energy_terms(s, p, ref, U=Uo, E=Eo)
+    assert r["terms"]["total"] == pytest.approx(To["total"], rel=1e-6)
+
+
+# ---------------------------------------------------------------- forces
+
+@pytest.mark.parametrize("natoms,n,h", [(7, (30, 26, 34), 0.5), (250, (40, 40, 40), 0.7)])
+def test_atom_forces_match_oracle(natoms, n, h):
+    vs = _vs()
+    s = synth.random_cluster(natoms, 8, h, seed=natoms, net_charge=1.0)
+    s["n"] = np.array(n)
+    s["origin"] = -0.5 * np.array(n) * h
+    p = O.params()
+    chi0 = O.init_labels(s)
+    S = vs.System(s)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    g, e = S.atom_forces(chi, energy=True)
+    go = O.gradient(s, p, chi0)
+    nb, worst = _close(g, go)
+    assert nb == 0, worst
+    To = O.energy_terms(s, p, chi0)
+    assert e == pytest.approx(To["total"], rel=1e-6)
+
+
+# ------------------------------------------------------------ relaxation
+
+def test_relax_two_atom_molecule_matches_oracle():
+    vs = _vs()
+    s = synth.two_atom_molecule(8.0, 7.0, n=32, h=0.5)
+    p = O.params()
+    ro = O.relax(s, p, O.relax_opts())
+    S = vs.System(s)
+    chi0 = O.init_labels(s)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    r = S.relax(chi, s["xyz"])
+    assert r["status"] == 0 and r["stop_reason"] == 1
+    assert np.abs(r["xyz"] - ro["xyz"]).max() < 1e-3
+    assert r["G"] == pytest.approx(ro["G"], rel=1e-4)
+    x = np.sort(r["xyz"][:, 0])
+    assert x[1] - x[0] == pytest.approx(8.0, abs=0.01)
+
+
+# --------------------------------------------------- full-size, sampled
+
+def test_protein_like_full_size_sampled():
+    """2,000-atom protein-like solute on the 256^3 grid (h = 0.4 A) in the
+    launch configuration of the benchmark: fields at sampled cells against
+    the oracle, exact W, tight labels at sampled cells, and the flip sweep's
+    reported energy change against a from-scratch recomputation."""
+    vs = _vs()
+    s = synth.protein_like()
+    p = O.params()
+    n = tuple(int(v) for v in s["n"])
+    G = int(np.prod(n))
+    S = vs.System(s)
+    U, E = _fields_gpu(S, n)
+    chi = torch.empty(G, dtype=torch.uint8, device="cuda")
+    S.init_labels(chi, "tight")
+    T0 = S.energy_field(U, E, chi=chi, terms=True)
+    rng = np.random.default_rng(0)
+    cells = np.concatenate([rng.integers(0, G, 3000),
+                            np.nonzero(chi.cpu().numpy())[0][::997]])
+    pts = O.cell_positions(s, cells)
+    Uo, _, Eo = O.point_fields(s, p, pts)
+    Ug = U.cpu().numpy()[cells]
+    # floor from the solvent cells of the sample
+    chis = chi.cpu().numpy()[cells]
+    floor = 1e-4 * np.abs(Uo[chis == 0]).max()
+    assert np.all(np.abs(Ug - Uo) <= 1e-4 * np.abs(Uo) + floor)
+    Eg = E.cpu().numpy().reshape(3, -1)[:, cells].T
+    fl = 1e-4 * np.abs(Eo).max()
+    assert np.all(np.abs(Eg - Eo) <= 1e-4 * np.abs(Eo) + fl)
+    lab, phi = O.init_labels_at(s, cells)
+    bad = lab != chis
+    assert np.all(np.abs(phi[bad]) < 1e-4)
+    W = torch.empty(G, dtype=torch.int32, device="cuda")
+    S.surface_weights(chi, W)
+    sc = O.surface_constants(s, p)
+    assert np.array_equal(W.cpu().numpy().astype(np.int64),
+                          O.conv(chi.cpu().numpy().reshape(n), sc["q"]).reshape(-1))
+    r = S.blsm_relax(chi, U, E)
+    assert r["status"] == 0 and r["rounds"] > 0
+    assert r["terms"]["total"] - T0["total"] == pytest.approx(r["dE_sum"], rel=1e-6, abs=1e-6)
