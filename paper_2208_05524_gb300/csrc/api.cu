@@ -93,18 +93,6 @@ __global__ void k_gd_init(GdState *s, double M0)
     s->dG = 0.0;
 }
 
-__global__ void k_rs_init(RoundState *rs, int max_rounds)
-{
-    rs->done = 0;
-    rs->round = 0;
-    rs->capped = 0;
-    rs->max_rounds = max_rounds;
-    rs->round_flips = 0;
-    rs->total_flips = 0;
-    rs->round_dE = 0.0;
-    rs->total_dE = 0.0;
-}
-
 // Gauss-Legendre nodes and weights on (-1, 1): Newton iteration on the
 // three-term recurrence of the Legendre polynomials.
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
@@ -192,6 +180,14 @@ struct vesis_system_t {
 
     double *d_ss_part = nullptr;
     int nb_ss = 0;
+
+    // persistent sweep state
+    int sweep_blocks = 0, ntiles = 0;
+    uint8_t *d_act = nullptr, *d_tneg = nullptr;
+    unsigned *d_ctl = nullptr;
+    int *d_err = nullptr, *d_rounds = nullptr, *d_capped = nullptr;
+    unsigned long long *d_part_flips = nullptr;
+    double *d_part_dE = nullptr;
 
     double *d_scal = nullptr;   // two banks of S_BANK doubles
     RoundState *d_rs = nullptr;
@@ -371,35 +367,29 @@ void enq_terms(vesis_system s, const uint8_t *chi, const float *U,
     k_total<<<1, 1, 0, s->st>>>(bk);
 }
 
-void enq_round(vesis_system s, uint8_t *chi, const float *U)
-{
-    const int *done = &s->d_rs->done;
-    launch_conv_z(s->g, s->kw, chi, s->d_T1, done, s->st);
-    launch_conv_y(s->g, s->kw, s->d_T1, s->d_T2, done, s->st);
-    launch_conv_x_key(s->g, s->kw, s->d_T2, chi, U, s->fc, s->d_K0, s->d_dE,
-                      done, s->st);
-    launch_min_z(s->g, s->kw.r, s->d_K0, s->d_K1, done, s->st);
-    launch_min_y(s->g, s->kw.r, s->d_K1, s->d_K2, done, s->st);
-    launch_min_x_flip(s->g, s->kw.r, s->d_K0, s->d_K2, s->d_dE, chi, s->d_rs,
-                      s->st);
-    launch_round_end(s->d_rs, s->st);
-}
-
 int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
              RoundState *out)
 {
-    count_launch();
-    k_rs_init<<<1, 1, 0, s->st>>>(s->d_rs, max_rounds);
-    int batch = 4;
-    for (;;) {
-        const int sp = span_begin(s);
-        for (int b = 0; b < batch; ++b) enq_round(s, chi, U);
-        span_end(s, sp, 2, s->G * (long long)batch, batch);
-        VCK(cudaMemcpyAsync(s->h_rs, s->d_rs, sizeof(RoundState),
-                            cudaMemcpyDeviceToHost, s->st));
-        VCK(cudaStreamSynchronize(s->st));
-        if (s->h_rs->done) break;
-        batch = std::min(batch * 2, 64);
+    // exact integer convolution of the starting labels; the sweep keeps it
+    // current with every flip
+    enq_conv(s, chi, s->d_W);
+    const int sp = span_begin(s);
+    VCK(launch_sweep(s->g, s->kw, s->fc, chi, s->d_W, U, s->d_K0, s->d_dE,
+                     s->d_act, s->d_tneg, s->d_ctl, s->d_err, s->d_part_flips,
+                     s->d_part_dE, s->d_rounds, s->d_capped, max_rounds,
+                     s->sweep_blocks, s->d_rs, s->st));
+    span_end(s, sp, 2, 0, 0);
+    VCK(cudaMemcpyAsync(s->h_rs, s->d_rs, sizeof(RoundState),
+                        cudaMemcpyDeviceToHost, s->st));
+    VCK(cudaMemcpyAsync(s->h_int, s->d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                        s->st));
+    VCK(cudaStreamSynchronize(s->st));
+    if (*s->h_int) return fail(VESIS_E_CUDA, "flip sweep grid barrier timed out");
+    if (sp >= 0) {
+        // the rounds include the last one, which found nothing to flip
+        const long long rounds = s->h_rs->round + (s->h_rs->capped ? 0 : 1);
+        s->spans[sp].rounds = rounds;
+        s->spans[sp].units = s->G * rounds;
     }
     *out = *s->h_rs;
     return VESIS_OK;
@@ -767,6 +757,21 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VCK(cudaMemset(s->d_fcount, 0, sizeof(unsigned long long)));
     s->nb_ss = ss_blocks(n);
     VTRY(dalloc(s, &s->d_ss_part, 3 * s->nb_ss));
+
+    {
+        const cudaError_t e = sweep_grid_size(r, s->nsm, &s->sweep_blocks);
+        if (e != cudaSuccess)
+            return fail(VESIS_E_CUDA, std::string("sweep occupancy: ") + cudaGetErrorString(e));
+    }
+    s->ntiles = sweep_tiles(s->g);
+    VTRY(dalloc(s, &s->d_act, 2 * (size_t)s->ntiles));
+    VTRY(dalloc(s, &s->d_tneg, s->ntiles));
+    VTRY(dalloc(s, &s->d_ctl, 5));
+    VTRY(dalloc(s, &s->d_err, 1));
+    VTRY(dalloc(s, &s->d_rounds, 1));
+    VTRY(dalloc(s, &s->d_capped, 1));
+    VTRY(dalloc(s, &s->d_part_flips, s->sweep_blocks));
+    VTRY(dalloc(s, &s->d_part_dE, s->sweep_blocks));
 
     VTRY(dalloc(s, &s->d_scal, 2 * S_BANK));
     VTRY(dalloc(s, &s->d_rs, 1));

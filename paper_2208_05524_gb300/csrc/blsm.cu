@@ -6,18 +6,8 @@
 // three integer passes (z, y, x), so it is exact: pass 1 <= 256, pass 2
 // <= 2^16, pass 3 <= 2^24.
 //
-// One flip round:
-//   conv_z -> conv_y -> conv_x_key: candidates (a face neighbour with the
-//     other label) get dE = c [s (1 - 2 w) - g0] - s h^3 U (Eq. dGj1/dGj2,
-//     FP64, candidates only) and, if dE < 0, the key
-//     (order-preserving bits of float(dE)) << 32 | index; others get ~0.
-//   min_z -> min_y -> min_x_flip: a cell flips iff its key equals the
-//     minimum key over the cube of half-width r around it.  Selected cells
-//     are more than r apart, so their kernel couplings vanish and the round
-//     lowers the energy by exactly the sum of their dE.
-//   round_end: stops the rounds once a round flips nothing.
-// Every round kernel returns at once when the rounds are done, so a fixed
-// batch of rounds can be enqueued ahead of the host's check.
+// This file holds the full-grid passes (convolution, flip energies, energy
+// sums, initial labels); the flip rounds themselves run in sweep.cu.
 #include "vesis_internal.cuh"
 
 namespace vesis {
@@ -120,38 +110,6 @@ __device__ __forceinline__ double flip_dE(uint8_t chi_j, unsigned W, float U,
     return __dsub_rn(t1, __dmul_rn(s, t2));
 }
 
-__device__ __forceinline__ unsigned long long flip_key(double dE, long long p)
-{
-    unsigned u = __float_as_uint(__double2float_rn(dE));
-    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    return ((unsigned long long)u << 32) | (unsigned long long)p;
-}
-
-__global__ void k_conv_x_key(GridDesc g, KernelW kw, const uint32_t *__restrict__ T2,
-                             const uint8_t *__restrict__ chi,
-                             const float *__restrict__ U, FlipConst fc,
-                             unsigned long long *__restrict__ K0,
-                             double *__restrict__ dE, const int *done)
-{
-    if (rounds_done(done)) return;
-    const long long nyz = (long long)g.ny * g.nz;
-    const long long G = nyz * g.nx;
-    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
-    if (p >= G) return;
-    const int i = (int)(p / nyz);
-    const long long rem = p - (long long)i * nyz;
-    const int j = (int)(rem / g.nz);
-    const int k = (int)(rem - (long long)j * g.nz);
-    unsigned long long key = ~0ull;
-    if (is_candidate(g, chi, p, i, j, k, nyz)) {
-        const unsigned W = conv_x_at(g, kw, T2, p, i, nyz);
-        const double e = flip_dE(chi[p], W, U[p], fc);
-        dE[p] = e;
-        if (e < 0.0) key = flip_key(e, p);
-    }
-    K0[p] = key;
-}
-
 __global__ void k_flip_energy(GridDesc g, const uint32_t *__restrict__ W,
                               const uint8_t *__restrict__ chi,
                               const float *__restrict__ U, FlipConst fc,
@@ -168,106 +126,6 @@ __global__ void k_flip_energy(GridDesc g, const uint32_t *__restrict__ W,
     const bool c = is_candidate(g, chi, p, i, j, k, nyz);
     cand[p] = c;
     dE[p] = c ? flip_dE(chi[p], W[p], U[p], fc) : 0.0;
-}
-
-__global__ void k_min_z(GridDesc g, int r, const unsigned long long *__restrict__ K0,
-                        unsigned long long *__restrict__ K1, const int *done)
-{
-    if (rounds_done(done)) return;
-    const long long G = (long long)g.nx * g.ny * g.nz;
-    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
-    if (p >= G) return;
-    const int k = (int)(p % g.nz);
-    unsigned long long m = ~0ull;
-    const int lo = max(-r, -k), hi = min(r, g.nz - 1 - k);
-    for (int a = lo; a <= hi; ++a) m = min(m, K0[p + a]);
-    K1[p] = m;
-}
-
-__global__ void k_min_y(GridDesc g, int r, const unsigned long long *__restrict__ K1,
-                        unsigned long long *__restrict__ K2, const int *done)
-{
-    if (rounds_done(done)) return;
-    const long long G = (long long)g.nx * g.ny * g.nz;
-    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
-    if (p >= G) return;
-    const int j = (int)((p / g.nz) % g.ny);
-    unsigned long long m = ~0ull;
-    const int lo = max(-r, -j), hi = min(r, g.ny - 1 - j);
-    for (int b = lo; b <= hi; ++b) m = min(m, K1[p + (long long)b * g.nz]);
-    K2[p] = m;
-}
-
-__global__ void k_min_x_flip(GridDesc g, int r, const unsigned long long *__restrict__ K0,
-                             const unsigned long long *__restrict__ K2,
-                             const double *__restrict__ dE, uint8_t *__restrict__ chi,
-                             RoundState *rs)
-{
-    __shared__ double s_e[CT / 32];
-    __shared__ unsigned s_n[CT / 32];
-    if (rounds_done(&rs->done)) return;
-    const long long nyz = (long long)g.ny * g.nz;
-    const long long G = nyz * g.nx;
-    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
-    unsigned flip = 0;
-    double e = 0.0;
-    if (p < G) {
-        const unsigned long long key = K0[p];
-        if (key != ~0ull) {
-            const int i = (int)(p / nyz);
-            unsigned long long m = ~0ull;
-            const int lo = max(-r, -i), hi = min(r, g.nx - 1 - i);
-            for (int c = lo; c <= hi; ++c) m = min(m, K2[p + (long long)c * nyz]);
-            if (m == key) {
-                chi[p] ^= 1;
-                flip = 1;
-                e = dE[p];
-            }
-        }
-    }
-    // block totals, one atomic per block
-    unsigned n = flip;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        n += __shfl_down_sync(0xffffffffu, n, o);
-        e += __shfl_down_sync(0xffffffffu, e, o);
-    }
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) {
-        s_n[w] = n;
-        s_e[w] = e;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned tn = 0;
-        double te = 0.0;
-        for (int q = 0; q < CT / 32; ++q) {
-            tn += s_n[q];
-            te += s_e[q];
-        }
-        if (tn) {
-            atomicAdd(&rs->round_flips, (unsigned long long)tn);
-            atomicAdd(&rs->round_dE, te);
-        }
-    }
-}
-
-__global__ void k_round_end(RoundState *rs)
-{
-    if (rs->done) return;
-    if (rs->round_flips == 0) {
-        rs->done = 1;
-    } else {
-        rs->round += 1;
-        rs->total_flips += rs->round_flips;
-        rs->total_dE += rs->round_dE;
-        if (rs->round >= rs->max_rounds) {
-            rs->done = 1;
-            rs->capped = 1;
-        }
-    }
-    rs->round_flips = 0;
-    rs->round_dE = 0.0;
 }
 
 // ----------------------------------------------------------------- sums
@@ -425,44 +283,12 @@ void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
     count_launch();
     k_conv_x<<<cell_blocks(g), CT, 0, st>>>(g, kw, T2, W);
 }
-void launch_conv_x_key(const GridDesc &g, const KernelW &kw,
-                       const uint32_t *T2, const uint8_t *chi, const float *U,
-                       const FlipConst &fc, unsigned long long *K0,
-                       double *dE, const int *done, cudaStream_t st)
-{
-    count_launch();
-    k_conv_x_key<<<cell_blocks(g), CT, 0, st>>>(g, kw, T2, chi, U, fc, K0, dE, done);
-}
 void launch_flip_energy(const GridDesc &g, const uint32_t *W,
                         const uint8_t *chi, const float *U, const FlipConst &fc,
                         double *dE, uint8_t *cand, cudaStream_t st)
 {
     count_launch();
     k_flip_energy<<<cell_blocks(g), CT, 0, st>>>(g, W, chi, U, fc, dE, cand);
-}
-void launch_min_z(const GridDesc &g, int r, const unsigned long long *K0,
-                  unsigned long long *K1, const int *done, cudaStream_t st)
-{
-    count_launch();
-    k_min_z<<<cell_blocks(g), CT, 0, st>>>(g, r, K0, K1, done);
-}
-void launch_min_y(const GridDesc &g, int r, const unsigned long long *K1,
-                  unsigned long long *K2, const int *done, cudaStream_t st)
-{
-    count_launch();
-    k_min_y<<<cell_blocks(g), CT, 0, st>>>(g, r, K1, K2, done);
-}
-void launch_min_x_flip(const GridDesc &g, int r, const unsigned long long *K0,
-                       const unsigned long long *K2, const double *dE,
-                       uint8_t *chi, RoundState *rs, cudaStream_t st)
-{
-    count_launch();
-    k_min_x_flip<<<cell_blocks(g), CT, 0, st>>>(g, r, K0, K2, dE, chi, rs);
-}
-void launch_round_end(RoundState *rs, cudaStream_t st)
-{
-    count_launch();
-    k_round_end<<<1, 1, 0, st>>>(rs);
 }
 void launch_terms(const GridDesc &g, const uint8_t *chi, const uint32_t *W,
                   const float *U, const float *Ex, const float *Ey,

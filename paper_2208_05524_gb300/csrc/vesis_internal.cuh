@@ -98,21 +98,9 @@ void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
 struct FlipConst {
     double c, g0, h3, invD3;
 };
-void launch_conv_x_key(const GridDesc &g, const KernelW &kw,
-                       const uint32_t *T2, const uint8_t *chi, const float *U,
-                       const FlipConst &fc, unsigned long long *K0,
-                       double *dE, const int *done, cudaStream_t st);
 void launch_flip_energy(const GridDesc &g, const uint32_t *W,
                         const uint8_t *chi, const float *U, const FlipConst &fc,
                         double *dE, uint8_t *cand, cudaStream_t st);
-void launch_min_z(const GridDesc &g, int r, const unsigned long long *K0,
-                  unsigned long long *K1, const int *done, cudaStream_t st);
-void launch_min_y(const GridDesc &g, int r, const unsigned long long *K1,
-                  unsigned long long *K2, const int *done, cudaStream_t st);
-void launch_min_x_flip(const GridDesc &g, int r, const unsigned long long *K0,
-                       const unsigned long long *K2, const double *dE,
-                       uint8_t *chi, RoundState *rs, cudaStream_t st);
-void launch_round_end(RoundState *rs, cudaStream_t st);
 // Energy sums over a labelled grid: per-block partials then ordered final.
 int terms_blocks(long long G);
 void launch_terms(const GridDesc &g, const uint8_t *chi, const uint32_t *W,
@@ -128,6 +116,21 @@ void launch_init_sphere(const GridDesc &g, float cx, float cy, float cz,
                         float radius, uint8_t *chi, cudaStream_t st);
 void launch_init_tight(const GridDesc &g, const float4 *xyzd, int n,
                        uint8_t *chi, cudaStream_t st);
+
+// --------------------------------------------------------------- sweep.cu
+// Persistent narrow-band flip sweep: all rounds in one cooperative launch.
+size_t sweep_smem_bytes(int r);
+int sweep_tiles(const GridDesc &g);
+cudaError_t sweep_grid_size(int r, int nsm, int *blocks);
+// act: 2 * tiles bytes, tneg: tiles bytes, ctl: 5 unsigned, err: 1 int,
+// part_*: `blocks` entries; writes the totals into *rs.
+cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &fc,
+                         uint8_t *chi, uint32_t *W, const float *U,
+                         unsigned long long *K, double *dE, uint8_t *act,
+                         uint8_t *tneg, unsigned *ctl, int *err,
+                         unsigned long long *part_flips, double *part_dE,
+                         int *rounds, int *capped, int max_rounds, int blocks,
+                         RoundState *rs, cudaStream_t st);
 
 // --------------------------------------------------------------- atoms.cu
 struct AtomParamsDev {

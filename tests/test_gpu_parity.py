@@ -49,7 +49,7 @@ def _close(gpu, ref, rel=1e-4):
 # ------------------------------------------------------------------ fields
 
 @pytest.mark.parametrize("n,h,natoms,seed", [((40, 36, 28), 0.5, 30, 1),
-                                             ((17, 23, 29), 0.9, 300, 2)])
+                                             ((27, 33, 29), 1.0, 300, 2)])
 def test_energy_field_matches_oracle(n, h, natoms, seed):
     vs = _vs()
     s = synth.random_cluster(natoms, 8, h, seed=seed, net_charge=-1.0)
@@ -116,6 +116,7 @@ def test_surface_weights_exact(n):
     vs = _vs()
     s = synth.single_ion(n=8, h=0.3)
     s["n"] = np.array(n)
+    s["origin"] = -0.5 * np.array(n) * 0.3
     S = vs.System(s)
     chi0 = synth.random_labels(n, seed=sum(n), p=0.4)
     chi = _dev(chi0.reshape(-1), torch.uint8)
@@ -130,6 +131,7 @@ def test_flip_energies_bit_exact():
     n = (33, 30, 27)
     s = synth.single_ion(n=8, h=0.35)
     s["n"] = np.array(n)
+    s["origin"] = -0.5 * np.array(n) * 0.35
     S = vs.System(s)
     chi0 = synth.random_labels(n, seed=4, p=0.5)
     U32 = synth.random_field(n, seed=5, scale=0.3)
@@ -162,6 +164,7 @@ def test_blsm_rounds_bit_exact(n, seed):
     vs = _vs()
     s = synth.single_ion(n=8, h=0.3)
     s["n"] = np.array(n)
+    s["origin"] = -0.5 * np.array(n) * 0.3
     S = vs.System(s)
     chi0 = _blob(n, seed)
     U32 = (synth.random_field(n, seed=seed + 10, scale=0.05) - 0.02).astype(np.float32)
