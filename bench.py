@@ -32,6 +32,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "atom-grid pair-evals/s"
+# DRAM bytes (read + write) per launch of the pair-energy kernel from one ncu
+# capture (profiles/pair_energy_grid_protein2000_grid256.md), valid only for
+# the source it was taken on: reported as null once pair.cu changes.
+TRAFFIC = {"sha256_16": "ee5aa2625926d2b8", "bytes": 2.68e6 + 208.14e6,
+           "workload": "protein2000_grid256"}
 # FP32 lane operations per energy pair in the inner loop of the pair kernel:
 # dz, r^2, clamp, r^-2, r^-3, r^-6, two LJ FMAs, Q r^-3, three field FMAs
 # (the reciprocal square root runs on the SFU and is not counted).
@@ -56,6 +61,16 @@ def workloads():
             "two 10,000-atom globules 6 A apart, 384^3 grid, h=0.4 A, seed 2",
             lambda: synth.two_domain_complex()),
     }
+
+
+def pair_traffic(workload):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2208_05524_gb300", "csrc", "pair.cu")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    if h == TRAFFIC["sha256_16"] and workload == TRAFFIC["workload"]:
+        return TRAFFIC["bytes"]
+    return None
 
 
 def peaks():
@@ -365,7 +380,8 @@ def run_vesis(args, world, rank, local):
             "roofline": {"bound": "alu", "kernel": "pair_energy_grid",
                          "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Tops/s (FP32 lane-ops)",
-                         "frac": achieved / peak_ops, "traffic": None,
+                         "frac": achieved / peak_ops,
+                         "traffic": pair_traffic(args.workload),
                          "ops_per_pair": OPS_PER_PAIR,
                          "peak_basis": f"{nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                        f"{f_max/1e6:.0f} MHz ({pk_kind} max clock)",

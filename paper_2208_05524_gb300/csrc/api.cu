@@ -182,6 +182,8 @@ struct vesis_system_t {
     int nb_ss = 0;
 
     // persistent sweep state
+    alignas(64) unsigned char tmap[128];
+    int use_tma = 0;
     int sweep_blocks = 0, ntiles = 0;
     uint8_t *d_act = nullptr, *d_tneg = nullptr;
     unsigned *d_ctl = nullptr;
@@ -374,7 +376,8 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
     // current with every flip
     enq_conv(s, chi, s->d_W);
     const int sp = span_begin(s);
-    VCK(launch_sweep(s->g, s->kw, s->fc, chi, s->d_W, U, s->d_K0, s->d_dE,
+    VCK(launch_sweep(s->tmap, s->use_tma, s->g, s->kw, s->fc, chi, s->d_W, U,
+                     reinterpret_cast<uint32_t *>(s->d_K0), s->d_dE,
                      s->d_act, s->d_tneg, s->d_ctl, s->d_err, s->d_part_flips,
                      s->d_part_dE, s->d_rounds, s->d_capped, max_rounds,
                      s->sweep_blocks, s->d_rs, s->st));
@@ -764,6 +767,9 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
             return fail(VESIS_E_CUDA, std::string("sweep occupancy: ") + cudaGetErrorString(e));
     }
     s->ntiles = sweep_tiles(s->g);
+    if (sweep_tmap_bytes() > sizeof(s->tmap))
+        return fail(VESIS_E_ARG, "tensor map larger than its slot");
+    s->use_tma = sweep_make_tmap(s->g, r, reinterpret_cast<uint32_t *>(s->d_K0), s->tmap) ? 1 : 0;
     VTRY(dalloc(s, &s->d_act, 2 * (size_t)s->ntiles));
     VTRY(dalloc(s, &s->d_tneg, s->ntiles));
     VTRY(dalloc(s, &s->d_ctl, 5));

@@ -124,10 +124,13 @@ int sweep_tiles(const GridDesc &g);
 cudaError_t sweep_grid_size(int r, int nsm, int *blocks);
 // act: 2 * tiles bytes, tneg: tiles bytes, ctl: 5 unsigned, err: 1 int,
 // part_*: `blocks` entries; writes the totals into *rs.
-cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &fc,
-                         uint8_t *chi, uint32_t *W, const float *U,
-                         unsigned long long *K, double *dE, uint8_t *act,
-                         uint8_t *tneg, unsigned *ctl, int *err,
+// TMA descriptor of the key volume (false if the grid does not allow one).
+bool sweep_make_tmap(const GridDesc &g, int r, uint32_t *K, void *tmap_out);
+size_t sweep_tmap_bytes();
+cudaError_t launch_sweep(const void *tmap, int use_tma, const GridDesc &g,
+                         const KernelW &kw, const FlipConst &fc, uint8_t *chi,
+                         uint32_t *W, const float *U, uint32_t *K, double *dE,
+                         uint8_t *act, uint8_t *tneg, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
                          int *rounds, int *capped, int max_rounds, int blocks,
                          RoundState *rs, cudaStream_t st);
