@@ -39,7 +39,8 @@ PARITY = {
     "fields": "pinned: Gauss law, LJ zero/minimum, superposition, sphere closed form",
     "conv": "pinned: direct 3-D sum, flat-interface calibration",
     "delta_e": "pinned: from-scratch energy differences of single flips",
-    "blsm_parallel": "pinned: exact energy decrease per round, local minimality",
+    "blsm_parallel": "pinned: exact energy decrease per round, local minimality, "
+                     "separation of flips, contains the cube rule",
     "blsm_heap": "pinned: exact energy decrease per flip, exhaustive minimum",
     "gradient": "pinned: central finite differences of the discrete energy",
     "ss": "pinned: finite differences, two-atom closed form",
@@ -79,6 +80,8 @@ def lib():
             L.or_delta_e.argtypes = [i, i, i, p, p, p, d, d, d, i64, p, p]
             L.or_select.argtypes = [i, i, i, p, p, i, p, p]
             L.or_select.restype = i64
+            L.or_select_cells.argtypes = [i, i, i, p, p, i, p, p]
+            L.or_select_cells.restype = i64
             L.or_energy.argtypes = [i, i, i, p, p, i, p, d, d, i64]
             L.or_energy.restype = d
             L.or_blsm_parallel.argtypes = [i, i, i, p, p, i, p, d, d, d, i64, i,
@@ -342,14 +345,16 @@ def delta_e(chi, U, sc, W=None):
     return dE, cand
 
 
-def select(chi, U, sc):
-    """One round's selection of the parallel rule: (sel mask, keys)."""
+def select(chi, U, sc, rule="bricks"):
+    """One round's selection of the parallel rule: (sel mask, keys).
+    rule "bricks" is the rule the relaxation uses; "cells" the finer cube
+    rule it contains."""
     dE, cand = delta_e(chi, U, sc)
     n = chi.shape
     sel = np.zeros(n, np.uint8)
     keys = np.zeros(n, np.uint64)
-    lib().or_select(n[0], n[1], n[2], _p(cand), _p(dE), sc["r"], _p(sel),
-                    _p(keys))
+    fn = lib().or_select if rule == "bricks" else lib().or_select_cells
+    fn(n[0], n[1], n[2], _p(cand), _p(dE), sc["r"], _p(sel), _p(keys))
     return sel, keys, dE, cand
 
 
@@ -363,7 +368,7 @@ def flip_energy_total(chi, U, sc):
 
 def blsm_parallel(chi, U, sc, max_rounds=100000, verify=False,
                   record_rounds=False):
-    """Parallel window-minimum flipping to a local minimum, in place.
+    """Rounds of the parallel brick-leader rule to a local minimum, in place.
     Returns dict(rounds, flips, dE_sum, verify_err, round_flips)."""
     chi_c = np.ascontiguousarray(chi, np.uint8)
     n = chi_c.shape

@@ -326,13 +326,21 @@ void or_delta_e(int nx, int ny, int nz, const uint8_t *chi, const int64_t *W,
 }
 
 /* ----------------------------------------------------- parallel flip rule
- * Data-parallel form of the min-heap flipping (Sec. 3.1, Step 2.2): in one
- * round every candidate whose flip lowers the energy (dE < 0, FP64) and
- * whose key is the minimum over the cube of Chebyshev radius r around it
- * flips.  key = (order-preserving bits of (float)dE) << 32 | linear index,
- * so equal float values break ties towards the smaller index.  Two selected
- * cells are more than r apart, so the kernel couples none of them and the
- * energy change of the round is exactly the sum of their dE.
+ * Data-parallel form of the min-heap flipping (Sec. 3.1, Step 2.2).  Every
+ * candidate whose flip lowers the energy (dE < 0, FP64) gets the key
+ * (order-preserving bits of (float)dE) << 32 | linear index; a smaller key
+ * comes first in the heap's order (ties of float(dE) go to the smaller
+ * index).  The grid is cut into bricks of edge B (B = 4 when r >= 3, else
+ * 2) aligned at index 0; each brick's leader is its cell with the smallest
+ * key.  A leader flips when no other brick's leader within Chebyshev
+ * distance r has a smaller key.  Two flipped cells are therefore more than
+ * r apart, the kernel couples none of them, and the energy change of the
+ * round is exactly the sum of their dE.  The heap's top (the global
+ * smallest key) always flips.
+ *
+ * or_select_cells is the finer rule "smallest key over the whole cube of
+ * half-width r"; every cell it selects the brick rule selects too.  Tests
+ * use it to check that relation.
  */
 static uint64_t flip_key(double dE, int64_t p)
 {
@@ -343,13 +351,77 @@ static uint64_t flip_key(double dE, int64_t p)
     return ((uint64_t)u << 32) | (uint64_t)p;
 }
 
+int or_brick_edge(int r) { return r >= 3 ? 4 : 2; }
+
+static void make_keys(int64_t G, const uint8_t *cand, const double *dE, uint64_t *keys)
+{
+#pragma omp parallel for
+    for (int64_t p = 0; p < G; ++p)
+        keys[p] = (cand[p] && dE[p] < 0.0) ? flip_key(dE[p], p) : UINT64_MAX;
+}
+
 int64_t or_select(int nx, int ny, int nz, const uint8_t *cand,
                   const double *dE, int r, uint8_t *sel, uint64_t *keys)
 {
     int64_t G = (int64_t)nx * ny * nz;
-#pragma omp parallel for
-    for (int64_t p = 0; p < G; ++p)
-        keys[p] = (cand[p] && dE[p] < 0.0) ? flip_key(dE[p], p) : UINT64_MAX;
+    const int B = or_brick_edge(r);
+    const int bx = (nx + B - 1) / B, by = (ny + B - 1) / B, bz = (nz + B - 1) / B;
+    const int64_t NB = (int64_t)bx * by * bz;
+    uint64_t *lead = (uint64_t *)malloc(sizeof(uint64_t) * NB);
+    make_keys(G, cand, dE, keys);
+    /* leaders: the smallest key of each brick */
+#pragma omp parallel for collapse(2)
+    for (int a = 0; a < bx; ++a)
+        for (int b = 0; b < by; ++b)
+            for (int c = 0; c < bz; ++c) {
+                uint64_t m = UINT64_MAX;
+                for (int i = a * B; i < a * B + B && i < nx; ++i)
+                    for (int j = b * B; j < b * B + B && j < ny; ++j)
+                        for (int k = c * B; k < c * B + B && k < nz; ++k)
+                            if (keys[IDX(i, j, k)] < m) m = keys[IDX(i, j, k)];
+                lead[((int64_t)a * by + b) * bz + c] = m;
+            }
+    for (int64_t p = 0; p < G; ++p) sel[p] = 0;
+    int64_t nsel = 0;
+#pragma omp parallel for collapse(2) reduction(+ : nsel)
+    for (int a = 0; a < bx; ++a)
+        for (int b = 0; b < by; ++b)
+            for (int c = 0; c < bz; ++c) {
+                const uint64_t m = lead[((int64_t)a * by + b) * bz + c];
+                if (m == UINT64_MAX) continue;
+                const int64_t p = (int64_t)(m & 0xffffffffu);
+                const int i = (int)(p / ((int64_t)ny * nz)), j = (int)((p / nz) % ny),
+                          k = (int)(p % nz);
+                int best = 1;
+                /* every brick that holds a cell of the cube around p */
+                for (int a2 = (i - r < 0 ? 0 : i - r) / B; best && a2 <= (i + r < nx ? i + r : nx - 1) / B; ++a2)
+                    for (int b2 = (j - r < 0 ? 0 : j - r) / B; best && b2 <= (j + r < ny ? j + r : ny - 1) / B; ++b2)
+                        for (int c2 = (k - r < 0 ? 0 : k - r) / B; c2 <= (k + r < nz ? k + r : nz - 1) / B; ++c2) {
+                            if (a2 == a && b2 == b && c2 == c) continue;
+                            const uint64_t m2 = lead[((int64_t)a2 * by + b2) * bz + c2];
+                            if (m2 >= m) continue;
+                            const int64_t p2 = (int64_t)(m2 & 0xffffffffu);
+                            const int i2 = (int)(p2 / ((int64_t)ny * nz)),
+                                      j2 = (int)((p2 / nz) % ny), k2 = (int)(p2 % nz);
+                            if (abs(i2 - i) <= r && abs(j2 - j) <= r && abs(k2 - k) <= r) {
+                                best = 0;
+                                break;
+                            }
+                        }
+                if (best) {
+                    sel[p] = 1;
+                    nsel += 1;
+                }
+            }
+    free(lead);
+    return nsel;
+}
+
+int64_t or_select_cells(int nx, int ny, int nz, const uint8_t *cand,
+                        const double *dE, int r, uint8_t *sel, uint64_t *keys)
+{
+    int64_t G = (int64_t)nx * ny * nz;
+    make_keys(G, cand, dE, keys);
     int64_t nsel = 0;
 #pragma omp parallel for collapse(2) reduction(+ : nsel)
     for (int i = 0; i < nx; ++i)

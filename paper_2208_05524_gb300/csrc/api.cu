@@ -159,7 +159,6 @@ struct vesis_system_t {
 
     uint16_t *d_T1 = nullptr;
     uint32_t *d_T2 = nullptr, *d_W = nullptr;
-    unsigned long long *d_K0 = nullptr, *d_K1 = nullptr, *d_K2 = nullptr;
     double *d_dE = nullptr;
     float *d_U[2] = {nullptr, nullptr}, *d_E[2] = {nullptr, nullptr};
 
@@ -178,13 +177,13 @@ struct vesis_system_t {
     float *d_far_wf = nullptr;
     int nb_far = 0;
 
-    double *d_ss_part = nullptr;
+    double *d_ss_part = nullptr, *d_ss_gpart = nullptr;
     int nb_ss = 0;
+    SsPlan ssplan{};
 
     // persistent sweep state
-    alignas(64) unsigned char tmap[128];
-    int use_tma = 0;
     int sweep_blocks = 0, ntiles = 0;
+    unsigned long long *d_PL = nullptr;
     uint8_t *d_act = nullptr, *d_tneg = nullptr;
     unsigned *d_ctl = nullptr;
     int *d_err = nullptr, *d_rounds = nullptr, *d_capped = nullptr;
@@ -342,10 +341,12 @@ void enq_fields(vesis_system s, float *U, float *E, double *bk)
 
 void enq_ss(vesis_system s, const double *d_pos, double *bk)
 {
-    launch_ss(d_pos, s->d_sig_ss, s->d_sqeps_ss, s->d_q, s->d_excl,
+    launch_ss(s->ssplan, d_pos, s->d_sig_ss, s->d_sqeps_ss, s->d_q, s->d_excl,
               s->d_bond_ptr, s->d_bond_other, s->d_bond_k, s->d_bond_r0, s->n,
-              s->coul, s->d_ss_part, s->d_grad_ss, s->st);
+              s->coul, s->d_ss_part, s->d_ss_gpart, s->st);
     launch_ss_final(s->d_ss_part, s->nb_ss, bk + S_SSB, s->st);
+    launch_force_reduce(s->d_ss_gpart, s->ssplan.nchunk, s->n, 1.0, s->d_grad_ss,
+                        0, s->st);
 }
 
 void enq_conv(vesis_system s, const uint8_t *chi, uint32_t *W)
@@ -376,8 +377,7 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
     // current with every flip
     enq_conv(s, chi, s->d_W);
     const int sp = span_begin(s);
-    VCK(launch_sweep(s->tmap, s->use_tma, s->g, s->kw, s->fc, chi, s->d_W, U,
-                     reinterpret_cast<uint32_t *>(s->d_K0), s->d_dE,
+    VCK(launch_sweep(s->g, s->kw, s->fc, chi, s->d_W, U, s->d_dE, s->d_PL,
                      s->d_act, s->d_tneg, s->d_ctl, s->d_err, s->d_part_flips,
                      s->d_part_dE, s->d_rounds, s->d_capped, max_rounds,
                      s->sweep_blocks, s->d_rs, s->st));
@@ -691,9 +691,6 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VTRY(dalloc(s, &s->d_T1, G));
     VTRY(dalloc(s, &s->d_T2, G));
     VTRY(dalloc(s, &s->d_W, G));
-    VTRY(dalloc(s, &s->d_K0, G));
-    VTRY(dalloc(s, &s->d_K1, G));
-    VTRY(dalloc(s, &s->d_K2, G));
     VTRY(dalloc(s, &s->d_dE, G));
     for (int b = 0; b < 2; ++b) {
         VTRY(dalloc(s, &s->d_U[b], G));
@@ -758,21 +755,21 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VTRY(dalloc(s, &s->d_gmax, 1));
     VTRY(dalloc(s, &s->d_fcount, 1));
     VCK(cudaMemset(s->d_fcount, 0, sizeof(unsigned long long)));
-    s->nb_ss = ss_blocks(n);
+    s->ssplan = plan_ss(n, s->nsm);
+    s->nb_ss = s->ssplan.tiles * s->ssplan.nchunk;
     VTRY(dalloc(s, &s->d_ss_part, 3 * s->nb_ss));
+    VTRY(dalloc(s, &s->d_ss_gpart, (size_t)3 * n * s->ssplan.nchunk));
 
     {
-        const cudaError_t e = sweep_grid_size(r, s->nsm, &s->sweep_blocks);
+        const cudaError_t e = sweep_grid_size(s->nsm, &s->sweep_blocks);
         if (e != cudaSuccess)
             return fail(VESIS_E_CUDA, std::string("sweep occupancy: ") + cudaGetErrorString(e));
     }
     s->ntiles = sweep_tiles(s->g);
-    if (sweep_tmap_bytes() > sizeof(s->tmap))
-        return fail(VESIS_E_ARG, "tensor map larger than its slot");
-    s->use_tma = sweep_make_tmap(s->g, r, reinterpret_cast<uint32_t *>(s->d_K0), s->tmap) ? 1 : 0;
-    VTRY(dalloc(s, &s->d_act, 2 * (size_t)s->ntiles));
+    VTRY(dalloc(s, &s->d_PL, sweep_bricks(s->g, r)));
+    VTRY(dalloc(s, &s->d_act, 4 * (size_t)s->ntiles));
     VTRY(dalloc(s, &s->d_tneg, s->ntiles));
-    VTRY(dalloc(s, &s->d_ctl, 5));
+    VTRY(dalloc(s, &s->d_ctl, sweep_ctl_words()));
     VTRY(dalloc(s, &s->d_err, 1));
     VTRY(dalloc(s, &s->d_rounds, 1));
     VTRY(dalloc(s, &s->d_capped, 1));

@@ -42,28 +42,55 @@ void launch_pack_atoms(const double *xyz, const double *centre,
 }
 
 // Solute-solute terms in FP64: harmonic bonds, and LJ plus Coulomb over the
-// pairs not joined by a bond (mixing (s_i + s_j)/2, sqrt(e_i e_j)).  Each
-// thread owns atom i and visits every j, so each pair is counted twice and
-// the energies are halved.  Bonds come from a per-atom list (CSR).
+// pairs not joined by a bond (mixing (s_i + s_j)/2, sqrt(e_i e_j)).  Block
+// (x, y) owns atoms i of tile x and visits the atoms j of chunk y, so each
+// pair is counted twice and the energies are halved; bonds (a per-atom CSR
+// list) are added by chunk 0.  Per-chunk FP64 gradient partials are summed
+// in chunk order afterwards.  1/r comes from an FP32 reciprocal square root
+// refined by two Newton-Raphson steps y <- y (3/2 - r^2 y^2 / 2), which
+// reaches double precision without a double divide or square root.
 constexpr int SS_THREADS = 128;
 constexpr int SS_TILE = 128;
 constexpr int kMaxExcl = 8;
 
-int ss_blocks(int n) { return (n + SS_THREADS - 1) / SS_THREADS; }
+SsPlan plan_ss(int n, int nsm)
+{
+    SsPlan sp;
+    sp.tiles = (n + SS_THREADS - 1) / SS_THREADS;
+    int nchunk = (2 * nsm + sp.tiles - 1) / sp.tiles;
+    const int maxc = (n + 31) / 32;
+    if (nchunk < 1) nchunk = 1;
+    if (nchunk > maxc) nchunk = maxc;
+    int len = (n + nchunk - 1) / nchunk;
+    len = (len + 31) / 32 * 32;
+    sp.chunk_len = len;
+    sp.nchunk = (n + len - 1) / len;
+    return sp;
+}
+
+__device__ __forceinline__ double inv_sqrt_d(double r2)
+{
+    double y = (double)rsqrtf((float)r2);
+    y = y * (1.5 - 0.5 * r2 * y * y);
+    y = y * (1.5 - 0.5 * r2 * y * y);
+    return y;
+}
 
 __global__ void __launch_bounds__(SS_THREADS)
 k_ss(const double *__restrict__ xyz, const double *__restrict__ sig,
      const double *__restrict__ sqeps, const double *__restrict__ q,
      const int *__restrict__ excl, const int *__restrict__ bond_ptr,
      const int *__restrict__ bond_other, const double *__restrict__ bond_k,
-     const double *__restrict__ bond_r0, int n, double coul,
-     double *__restrict__ e_part, double *__restrict__ grad)
+     const double *__restrict__ bond_r0, int n, int chunk_len, double coul,
+     double *__restrict__ e_part, double *__restrict__ g_part)
 {
     __shared__ double s_x[SS_TILE], s_y[SS_TILE], s_z[SS_TILE];
     __shared__ double s_s[SS_TILE], s_e[SS_TILE], s_q[SS_TILE];
     __shared__ double s_red[3][SS_THREADS / 32];
     const int i = blockIdx.x * SS_THREADS + threadIdx.x;
     const bool live = i < n;
+    const int jb = blockIdx.y * chunk_len;
+    const int je = min(n, jb + chunk_len);
     double xi = 0, yi = 0, zi = 0, si = 0, ei = 0, qi = 0;
     int ex[kMaxExcl];
 #pragma unroll
@@ -75,8 +102,8 @@ k_ss(const double *__restrict__ xyz, const double *__restrict__ sig,
         for (int e = 0; e < kMaxExcl; ++e) ex[e] = excl[i * kMaxExcl + e];
     }
     double elj = 0.0, ec = 0.0, eb = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
-    for (int base = 0; base < n; base += SS_TILE) {
-        const int cnt = min(SS_TILE, n - base);
+    for (int base = jb; base < je; base += SS_TILE) {
+        const int cnt = min(SS_TILE, je - base);
         __syncthreads();
         for (int m = threadIdx.x; m < cnt; m += SS_THREADS) {
             const int j = base + m;
@@ -93,8 +120,8 @@ k_ss(const double *__restrict__ xyz, const double *__restrict__ sig,
             if (skip) continue;
             const double dx = xi - s_x[m], dy = yi - s_y[m], dz = zi - s_z[m];
             const double r2 = dx * dx + dy * dy + dz * dz;
-            const double ir2 = 1.0 / r2;
-            const double ir = sqrt(ir2);
+            const double ir = inv_sqrt_d(r2);
+            const double ir2 = ir * ir;
             const double s = 0.5 * (si + s_s[m]);
             const double ep = ei * s_e[m];
             const double sr2 = s * s * ir2;
@@ -110,21 +137,24 @@ k_ss(const double *__restrict__ xyz, const double *__restrict__ sig,
         }
     }
     if (live) {
-        for (int b = bond_ptr[i]; b < bond_ptr[i + 1]; ++b) {
-            const int j = bond_other[b];
-            const double dx = xi - xyz[3 * j], dy = yi - xyz[3 * j + 1],
-                         dz = zi - xyz[3 * j + 2];
-            const double r = sqrt(dx * dx + dy * dy + dz * dz);
-            const double dr = r - bond_r0[b];
-            eb += 0.5 * bond_k[b] * dr * dr;
-            const double f = bond_k[b] * dr / r;
-            gx += f * dx;
-            gy += f * dy;
-            gz += f * dz;
+        if (blockIdx.y == 0) {
+            for (int b = bond_ptr[i]; b < bond_ptr[i + 1]; ++b) {
+                const int j = bond_other[b];
+                const double dx = xi - xyz[3 * j], dy = yi - xyz[3 * j + 1],
+                             dz = zi - xyz[3 * j + 2];
+                const double r = sqrt(dx * dx + dy * dy + dz * dz);
+                const double dr = r - bond_r0[b];
+                eb += 0.5 * bond_k[b] * dr * dr;
+                const double f = bond_k[b] * dr / r;
+                gx += f * dx;
+                gy += f * dy;
+                gz += f * dz;
+            }
         }
-        grad[3 * i] = gx;
-        grad[3 * i + 1] = gy;
-        grad[3 * i + 2] = gz;
+        double *o = g_part + ((long long)blockIdx.y * n + i) * 3;
+        o[0] = gx;
+        o[1] = gy;
+        o[2] = gz;
     }
     double v[3] = {0.5 * eb, 0.5 * elj, 0.5 * ec};
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -136,24 +166,25 @@ k_ss(const double *__restrict__ xyz, const double *__restrict__ sig,
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
         for (int c = 0; c < 3; ++c) {
             double t = 0.0;
             for (int q2 = 0; q2 < SS_THREADS / 32; ++q2) t += s_red[c][q2];
-            e_part[3 * blockIdx.x + c] = t;
+            e_part[3 * blk + c] = t;
         }
     }
 }
 
-void launch_ss(const double *xyz, const double *sig, const double *sqeps,
-               const double *q, const int *excl, const int *bond_ptr,
-               const int *bond_other, const double *bond_k,
+void launch_ss(const SsPlan &sp, const double *xyz, const double *sig,
+               const double *sqeps, const double *q, const int *excl,
+               const int *bond_ptr, const int *bond_other, const double *bond_k,
                const double *bond_r0, int n, double coul, double *e_part,
-               double *grad, cudaStream_t st)
+               double *g_part, cudaStream_t st)
 {
     count_launch();
-    k_ss<<<ss_blocks(n), SS_THREADS, 0, st>>>(xyz, sig, sqeps, q, excl,
-                                             bond_ptr, bond_other, bond_k,
-                                             bond_r0, n, coul, e_part, grad);
+    k_ss<<<dim3(sp.tiles, sp.nchunk), SS_THREADS, 0, st>>>(
+        xyz, sig, sqeps, q, excl, bond_ptr, bond_other, bond_k, bond_r0, n,
+        sp.chunk_len, coul, e_part, g_part);
 }
 
 __global__ void k_ss_final(const double *__restrict__ e_part, int nb, double *out3)

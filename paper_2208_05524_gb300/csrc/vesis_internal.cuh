@@ -119,18 +119,19 @@ void launch_init_tight(const GridDesc &g, const float4 *xyzd, int n,
 
 // --------------------------------------------------------------- sweep.cu
 // Persistent narrow-band flip sweep: all rounds in one cooperative launch.
-size_t sweep_smem_bytes(int r);
 int sweep_tiles(const GridDesc &g);
-cudaError_t sweep_grid_size(int r, int nsm, int *blocks);
-// act: 2 * tiles bytes, tneg: tiles bytes, ctl: 5 unsigned, err: 1 int,
-// part_*: `blocks` entries; writes the totals into *rs.
-// TMA descriptor of the key volume (false if the grid does not allow one).
-bool sweep_make_tmap(const GridDesc &g, int r, uint32_t *K, void *tmap_out);
-size_t sweep_tmap_bytes();
-cudaError_t launch_sweep(const void *tmap, int use_tma, const GridDesc &g,
-                         const KernelW &kw, const FlipConst &fc, uint8_t *chi,
-                         uint32_t *W, const float *U, uint32_t *K, double *dE,
-                         uint8_t *act, uint8_t *tneg, unsigned *ctl, int *err,
+int sweep_brick_edge(int r);
+long long sweep_bricks(const GridDesc &g, int r);
+cudaError_t sweep_grid_size(int nsm, int *blocks);
+int sweep_ctl_words();   // unsigned words of the sweep control block
+// dE: G doubles, PL: sweep_bricks() words, act: 4 * tiles bytes
+// (active and dirty maps, two each), tneg: tiles bytes, ctl:
+// sweep_ctl_words(), err: 1 int, part_*: `blocks` entries; writes the totals
+// into *rs.
+cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &fc,
+                         uint8_t *chi, uint32_t *W, const float *U,
+                         double *dE, unsigned long long *PL, uint8_t *act,
+                         uint8_t *tneg, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
                          int *rounds, int *capped, int max_rounds, int blocks,
                          RoundState *rs, cudaStream_t st);
@@ -145,14 +146,18 @@ void launch_pack_atoms(const double *xyz, const double *centre,
                        int n, double rho, double cfa, float4 *xyzq,
                        float2 *ab, float4 *fcoef, int *oob, const double *lo,
                        const double *hi, cudaStream_t st);
-// Solute-solute energy and gradient in FP64 (Eq. Gss): e_part[block][3]
-// (bond, LJ, Coulomb), grad[n][3] overwritten.
-int ss_blocks(int n);
-void launch_ss(const double *xyz, const double *sig, const double *sqeps,
-               const double *q, const int *excl, const int *bond_ptr,
-               const int *bond_other, const double *bond_k,
+// Solute-solute energy and gradient in FP64 (Eq. Gss) on a 2-D grid of
+// (atom tile, j-chunk) blocks: e_part[block][3] (bond, LJ, Coulomb) and
+// g_part[chunk][n][3] (gradient partials, summed in chunk order later).
+struct SsPlan {
+    int tiles, nchunk, chunk_len;
+};
+SsPlan plan_ss(int n, int nsm);
+void launch_ss(const SsPlan &sp, const double *xyz, const double *sig,
+               const double *sqeps, const double *q, const int *excl,
+               const int *bond_ptr, const int *bond_other, const double *bond_k,
                const double *bond_r0, int n, double coul, double *e_part,
-               double *grad, cudaStream_t st);
+               double *g_part, cudaStream_t st);
 void launch_ss_final(const double *e_part, int nb, double *out3,
                      cudaStream_t st);
 // grad = a + b (+ c), and the max |component| into *gmax (FP64 bits).

@@ -304,3 +304,25 @@ def test_protein_like_full_size_sampled():
     r = S.blsm_relax(chi, U, E)
     assert r["status"] == 0 and r["rounds"] > 0
     assert r["terms"]["total"] - T0["total"] == pytest.approx(r["dE_sum"], rel=1e-6, abs=1e-6)
+
+
+def test_blsm_small_kernel_radius_bit_exact():
+    """r = 2 (bricks of edge 2 in the selection): identical rounds and labels."""
+    vs = _vs()
+    n = (26, 21, 23)
+    h = 0.3
+    s = synth.single_ion(n=8, h=h)
+    s["n"] = np.array(n)
+    s["origin"] = -0.5 * np.array(n) * h
+    p = O.params(trunc_r=2, gauss_sigma=h)
+    S = vs.System(s, trunc_r=2, gauss_sigma=h)
+    chi0 = _blob(n, 7)
+    U32 = (synth.random_field(n, seed=17, scale=0.05) - 0.02).astype(np.float32)
+    sc = O.surface_constants(s, p)
+    ref = chi0.copy()
+    ro = O.blsm_parallel(ref, U32.astype(np.float64), sc)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    r = S.blsm_relax(chi, _dev(U32.reshape(-1), torch.float32), terms=False)
+    assert ro["rounds"] > 0
+    assert r["rounds"] == ro["rounds"] and r["flips"] == ro["flips"]
+    assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))

@@ -326,9 +326,36 @@ def test_parallel_rule_round_exact_and_local_min():
     kmin = keys[neg].min()
     assert sel[np.unravel_index(np.argmin(np.where(neg, keys, np.uint64(2**64 - 1))), chi.shape)]
     assert kmin == keys.min()
+    # every cell the cube rule (smallest key over the whole window) selects,
+    # the brick rule selects as well
+    selc, _, _, _ = O.select(chi, U, sc, rule="cells")
+    assert selc.sum() > 0
+    assert np.all(sel[selc == 1] == 1)
     res = O.blsm_parallel(chi, U, sc, verify=True, record_rounds=True)
     assert res["verify_err"] < 1e-12
     assert res["round_flips"].sum() == res["flips"]
+    dE, cand = O.delta_e(chi, U, sc)
+    assert np.all(dE[cand == 1] >= 0)
+
+
+def test_parallel_rule_small_kernel_radius():
+    # r = 2 uses bricks of edge 2; the same invariants hold
+    sc, chi, U = _small_case(5, n=(13, 11, 12), scale=0.15)
+    U = U - 0.05
+    q = O.surface_kernel(1.0, 2)
+    S1 = int(sum(a * int(q[2 + a]) for a in range(1, 3)))
+    sc = dict(sc, q=q, r=2, S1=S1, c=0.174 * 0.3 * 0.3 * 256.0 / S1,
+              g0=float(int(q[2]) ** 3) / float(256 ** 3))
+    sel, keys, dE, cand = O.select(chi, U, sc)
+    idx = np.argwhere(sel == 1)
+    assert len(idx) > 0
+    for a in range(len(idx)):
+        for b in range(a + 1, len(idx)):
+            assert np.abs(idx[a] - idx[b]).max() > 2
+    selc, _, _, _ = O.select(chi, U, sc, rule="cells")
+    assert np.all(sel[selc == 1] == 1)
+    res = O.blsm_parallel(chi, U, sc, verify=True)
+    assert res["verify_err"] < 1e-12
     dE, cand = O.delta_e(chi, U, sc)
     assert np.all(dE[cand == 1] >= 0)
 
