@@ -234,6 +234,33 @@ int vesis_set_timing(vesis_system s, int enable);
 /* Synchronises the stream and returns the totals since timing was enabled. */
 int vesis_get_timing(vesis_system s, vesis_timing *out);
 
+/* Largest grid (cells) vesis_surface_weights_noalloc accepts. */
+#define VESIS_NOALLOC_MAX_CELLS (1 << 20)
+
+/* The kernel convolution of vesis_surface_weights (W_dev[j] = 256^3 w_j,
+ * exact) for callers that cannot allocate device memory.  The paper has no
+ * counterpart: it is a service of this library.  Creating a vesis_system
+ * calls cudaMalloc; code running while a stream is captured into a CUDA
+ * graph, processes whose device memory belongs to a pool or arena that
+ * forbids other allocations, and loops that must not enter the driver's
+ * allocator cannot do that.  This call needs no system and allocates
+ * nothing: its two intermediate planes live in a fixed array of device
+ * global memory (6 bytes per cell for VESIS_NOALLOC_MAX_CELLS cells, about
+ * 6 MiB) that every GPU holds from the moment the library is loaded until
+ * the process exits.
+ *   p        grid (nx, ny, nz), h, gauss_sigma and trunc_r are used; at most
+ *            VESIS_NOALLOC_MAX_CELLS cells, larger grids return VESIS_E_ARG
+ *   chi_dev  G labels (device), W_dev G uint32 (device, written)
+ *   cuda_stream  stream to enqueue on (NULL = legacy default); the call
+ *            returns once the work is enqueued
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array, and each call writes it in full before
+ * reading it: calls whose work overlaps on the GPU (other streams, other
+ * threads) race and must be serialised by the caller. */
+int vesis_surface_weights_noalloc(const vesis_params *p, const uint8_t *chi_dev,
+                                  uint32_t *W_dev, void *cuda_stream);
+
 /* Frees the system's device memory.  NULL is accepted. */
 int vesis_destroy(vesis_system s);
 

@@ -28,6 +28,15 @@ namespace {
 
 thread_local std::string g_err;
 
+}  // namespace
+
+namespace vesis {
+// The calling thread's error message slot (also used by noalloc.cu).
+std::string *noalloc_last_error() { return &g_err; }
+}  // namespace vesis
+
+namespace {
+
 int fail(int code, const std::string &msg)
 {
     g_err = msg;

@@ -91,6 +91,7 @@ def lib():
                                   C.POINTER(RelaxStats)]
         L.vesis_set_timing.argtypes = [_p, _i]
         L.vesis_get_timing.argtypes = [_p, C.POINTER(Timing)]
+        L.vesis_surface_weights_noalloc.argtypes = [C.POINTER(Params), _p, _p, _p]
         L.vesis_destroy.argtypes = [_p]
         L.vesis_last_error.restype = C.c_char_p
         _lib = L
@@ -141,6 +142,23 @@ def default_relax_opts(**kw):
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+NOALLOC_MAX_CELLS = 1 << 20
+
+
+def surface_weights_noalloc(params, chi, W, stream=None):
+    """vesis_surface_weights_noalloc: the kernel convolution of the labels
+    without any device allocation (for callers that cannot allocate, e.g.
+    inside a stream capture).  params: a Params (grid, h, kernel); chi and W
+    contiguous CUDA tensors of G uint8 / int32.  Calls share one scratch
+    array: do not overlap them on the GPU."""
+    import torch
+    G = params.nx * params.ny * params.nz
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().vesis_surface_weights_noalloc(
+        C.byref(params), _dp(chi, torch.uint8, G), _dp(W, torch.int32, G),
+        _p(st.cuda_stream)))
 
 
 class System:
