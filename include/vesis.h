@@ -176,10 +176,14 @@ int vesis_flip_energies(vesis_system s, const uint8_t *chi_dev,
                         uint8_t *cand_dev);
 
 /* Binary level-set relaxation at fixed atoms (Sec. 3.1, Step 2): rounds
- * of flips until no candidate lowers the energy.  Each round flips every
- * candidate with dE < 0 whose key (float(dE), then index) is the least in
- * the cube of half-width trunc_r around it - the data-parallel form of the
- * min-heap flipping, which always contains the heap's top.
+ * of flips until no candidate lowers the energy - the data-parallel form of
+ * the min-heap flipping.  A candidate with dE < 0 has the key (float(dE),
+ * then index); the grid is cut into bricks of edge 4 (edge 2 when
+ * trunc_r < 3) and a brick's leader is its smallest key; each round flips
+ * every leader that no other leader within Chebyshev distance trunc_r
+ * precedes.  The heap's top always flips, flipped cells are more than
+ * trunc_r apart, and a round lowers the energy by exactly the sum of their
+ * dE.
  *   chi_dev   G bytes, relaxed in place
  *   U_dev     G floats from vesis_energy_field at the current positions
  *   E_dev     3 x G floats or NULL (only for the vdW/CFA split of terms)

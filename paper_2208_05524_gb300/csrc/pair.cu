@@ -20,6 +20,68 @@ constexpr int PE_THREADS = 128;
 constexpr int PE_PTS = 8;
 constexpr int PE_TILE = 256;
 
+// 1/sqrt(x) on the SFU without the subnormal range handling: every argument
+// here is at least r_min^2, so flushing subnormals changes nothing.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Block-wide min and max of three values (all threads must call).
+__device__ __forceinline__ void block_box(float x, float y, float z, float lo[3],
+                                          float hi[3], float *s_box)
+{
+    float v[6] = {x, y, z, -x, -y, -z};
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[c] = fminf(v[c], __shfl_xor_sync(0xffffffffu, v[c], o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) s_box[w * 6 + c] = v[c];
+    __syncthreads();
+    float r[6] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f};
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) r[c] = fminf(r[c], s_box[q * 6 + c]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = r[c];
+        hi[c] = -r[c + 3];
+    }
+}
+
+// One atom against the PE_PTS cells of a thread; CLAMP applies r_min.
+template <bool CLAMP>
+__device__ __forceinline__ void energy_atom(const float4 &A, const float2 &B, float px,
+                                            float py, const float *pz, float rmin2,
+                                            float *lj, float *ex, float *ey, float *ez)
+{
+    const float dx = px - A.x;
+    const float dy = py - A.y;
+    const float dxy2 = fmaf(dx, dx, dy * dy);
+#pragma unroll
+    for (int p = 0; p < PE_PTS; ++p) {
+        const float dz = pz[p] - A.z;
+        float r2 = fmaf(dz, dz, dxy2);
+        if (CLAMP) r2 = fmaxf(r2, rmin2);
+        const float ri = rsqrt_ftz(r2);
+        const float ri2 = ri * ri;
+        const float ri3 = ri2 * ri;
+        const float ri6 = ri3 * ri3;
+        const float tl = fmaf(B.x, ri6, -B.y);   // A r^-6 - B
+        lj[p] = fmaf(ri6, tl, lj[p]);
+        const float qr3 = A.w * ri3;
+        ex[p] = fmaf(qr3, dx, ex[p]);
+        ey[p] = fmaf(qr3, dy, ey[p]);
+        ez[p] = fmaf(qr3, dz, ez[p]);
+    }
+}
+
 __global__ void __launch_bounds__(PE_THREADS)
 k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
                    float *__restrict__ U, float *__restrict__ Ex,
@@ -27,6 +89,7 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
 {
     __shared__ float4 s_xyzq[PE_TILE];
     __shared__ float2 s_ab[PE_TILE];
+    __shared__ float s_box[6 * (PE_THREADS / 32)];
     const int cpp = (g.nz + PE_PTS - 1) / PE_PTS;
     const long long t = (long long)blockIdx.x * PE_THREADS + threadIdx.x;
     const long long npen = (long long)g.nx * g.ny;
@@ -44,36 +107,50 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
         pz[p] = cell_pos(k0 + p, g.cz, g.h);
         lj[p] = ex[p] = ey[p] = ez[p] = 0.f;
     }
+    // bounding box of the block's cells (padding cells included: harmless)
+    float clo[3], chi[3];
+    block_box(px, py, pz[0], clo, chi, s_box);
+    {
+        float lo2[3], hi2[3];
+        block_box(px, py, pz[PE_PTS - 1], lo2, hi2, s_box);
+        clo[2] = fminf(clo[2], lo2[2]);
+        chi[2] = fmaxf(chi[2], hi2[2]);
+    }
     for (int base = 0; base < a.n; base += PE_TILE) {
         const int cnt = min(PE_TILE, a.n - base);
         __syncthreads();
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        bool have = false;
         for (int m = threadIdx.x; m < cnt; m += PE_THREADS) {
-            s_xyzq[m] = a.xyzq[base + m];
+            const float4 A = a.xyzq[base + m];
+            s_xyzq[m] = A;
             s_ab[m] = a.ab[base + m];
+            ax = A.x; ay = A.y; az = A.z;
+            have = true;
+        }
+        if (!have) {   // a thread without atoms repeats the tile's first one
+            const float4 A = a.xyzq[base];
+            ax = A.x; ay = A.y; az = A.z;
+        }
+        // the tile needs the clamp only if its atoms' box comes within r_min
+        // of the block's cells
+        float alo[3], ahi[3];
+        block_box(ax, ay, az, alo, ahi, s_box);
+        float d2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float gap = fmaxf(fmaxf(alo[c] - chi[c], clo[c] - ahi[c]), 0.f);
+            d2 = fmaf(gap, gap, d2);
         }
         __syncthreads();
+        if (d2 > rmin2) {
 #pragma unroll 2
-        for (int m = 0; m < cnt; ++m) {
-            const float4 A = s_xyzq[m];
-            const float2 B = s_ab[m];
-            const float dx = px - A.x;
-            const float dy = py - A.y;
-            const float dxy2 = fmaf(dx, dx, dy * dy);
-#pragma unroll
-            for (int p = 0; p < PE_PTS; ++p) {
-                const float dz = pz[p] - A.z;
-                const float r2 = fmaxf(fmaf(dz, dz, dxy2), rmin2);
-                const float ri = rsqrtf(r2);
-                const float ri2 = ri * ri;
-                const float ri3 = ri2 * ri;
-                const float ri6 = ri3 * ri3;
-                const float tl = fmaf(B.x, ri6, -B.y);   // A r^-6 - B
-                lj[p] = fmaf(ri6, tl, lj[p]);
-                const float qr3 = A.w * ri3;
-                ex[p] = fmaf(qr3, dx, ex[p]);
-                ey[p] = fmaf(qr3, dy, ey[p]);
-                ez[p] = fmaf(qr3, dz, ez[p]);
-            }
+            for (int m = 0; m < cnt; ++m)
+                energy_atom<false>(s_xyzq[m], s_ab[m], px, py, pz, rmin2, lj, ex, ey, ez);
+        } else {
+#pragma unroll 2
+            for (int m = 0; m < cnt; ++m)
+                energy_atom<true>(s_xyzq[m], s_ab[m], px, py, pz, rmin2, lj, ex, ey, ez);
         }
     }
     if (!live) return;
@@ -152,7 +229,7 @@ k_point_energy(const float4 *__restrict__ pts, const double *__restrict__ w,
             const float2 B = s_ab[m];
             const float dx = P.x - A.x, dy = P.y - A.y, dz = P.z - A.z;
             const float r2 = fmaxf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)), rmin2);
-            const float ri = rsqrtf(r2);
+            const float ri = rsqrt_ftz(r2);
             const float ri2 = ri * ri, ri3 = ri2 * ri, ri6 = ri3 * ri3;
             lj = fmaf(ri6, fmaf(B.x, ri6, -B.y), lj);
             const float qr3 = A.w * ri3;
@@ -204,29 +281,37 @@ ForcePlan plan_pair_force(long long G, int natoms, int nsm)
 }
 
 // One pair's contribution to the gradient of atom (ax, ay, az) with
-// coefficients c1 = 12 rho A, c2 = -6 rho B, kq = -2 C Q; E is the field at
-// the point, wgt its weight.
+// coefficients c1 = 12 rho A, c2 = -6 rho B, kq = -2 C Q, kq3 = 3 kq; E is
+// the field at the point.  Without the clamp:
+//   f += [r^-8 (c1 r^-6 + c2) - kq3 r^-5 (d.E)] d + kq r^-3 E.
+// With it, the LJ part and the d d^T part vanish where r < r_min.
+template <bool CLAMP>
 __device__ __forceinline__ void force_pair(float px, float py, float pz,
                                            const float4 &E, float ax, float ay,
                                            float az, float c1, float c2,
-                                           float kq, float rmin2, float &fx,
-                                           float &fy, float &fz)
+                                           float kq, float kq3, float rmin2,
+                                           float &fx, float &fy, float &fz)
 {
     const float dx = px - ax, dy = py - ay, dz = pz - az;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const bool un = r2 >= rmin2;                    // not clamped
-    const float msk = un ? 1.f : 0.f;
-    const float m3 = un ? 3.f : 0.f;
-    const float ri = rsqrtf(fmaxf(r2, rmin2));
+    float ri, c1m = c1, c2m = c2, k3m = kq3;
+    if (CLAMP) {
+        const bool un = r2 >= rmin2;                // not clamped
+        ri = rsqrt_ftz(fmaxf(r2, rmin2));
+        c1m = un ? c1 : 0.f;
+        c2m = un ? c2 : 0.f;
+        k3m = un ? kq3 : 0.f;
+    } else {
+        ri = rsqrt_ftz(r2);
+    }
     const float ri2 = ri * ri;
     const float ri3 = ri2 * ri;
     const float ri6 = ri3 * ri3;
     const float ri8 = ri6 * ri2;
-    const float glj = fmaf(c1, ri6, c2) * (ri8 * msk);
+    const float glj = fmaf(c1m, ri6, c2m) * ri8;
     const float dE = fmaf(dx, E.x, fmaf(dy, E.y, dz * E.z));
     const float am = kq * ri3;
-    const float b = dE * ri2 * m3;
-    const float cd = fmaf(-am, b, glj);
+    const float cd = fmaf(-(k3m * ri3), dE * ri2, glj);
     fx = fmaf(cd, dx, fmaf(am, E.x, fx));
     fy = fmaf(cd, dy, fmaf(am, E.y, fy));
     fz = fmaf(cd, dz, fmaf(am, E.z, fz));
@@ -242,14 +327,17 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
     __shared__ float4 s_p[PF_STAGE];
     __shared__ float4 s_e[PF_STAGE];
     __shared__ int s_wc[2 * PF_THREADS / 32];
+    __shared__ float s_box[6 * (PF_THREADS / 32)];
     const int chunk = blockIdx.x;
     const long long c0 = (long long)chunk * chunk_len;
     const long long c1 = min(G, c0 + chunk_len);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = PF_THREADS / 32;
 
-    float ax[PF_APT], ay[PF_APT], az[PF_APT], k1[PF_APT], k2[PF_APT], kq[PF_APT];
+    float ax[PF_APT], ay[PF_APT], az[PF_APT], k1[PF_APT], k2[PF_APT], kq[PF_APT],
+        kq3[PF_APT];
     int an[PF_APT];
+    const float4 A0 = a.xyzq[blockIdx.y * PF_ATOMS];   // exists: tiles are non-empty
 #pragma unroll
     for (int u = 0; u < PF_APT; ++u) {
         an[u] = blockIdx.y * PF_ATOMS + u * PF_THREADS + threadIdx.x;
@@ -258,9 +346,23 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             const float4 F = a.fcoef[an[u]];
             ax[u] = A.x; ay[u] = A.y; az[u] = A.z;
             k1[u] = F.x; k2[u] = F.y; kq[u] = F.z;
-        } else {
-            ax[u] = ay[u] = az[u] = 0.f;
+        } else {   // idle slot: sits on a real atom and adds nothing
+            ax[u] = A0.x; ay[u] = A0.y; az[u] = A0.z;
             k1[u] = k2[u] = kq[u] = 0.f;
+        }
+        kq3[u] = 3.f * kq[u];
+    }
+    // bounding box of the block's atoms
+    float alo[3], ahi[3];
+    block_box(ax[0], ay[0], az[0], alo, ahi, s_box);
+#pragma unroll
+    for (int u = 1; u < PF_APT; ++u) {
+        float lo2[3], hi2[3];
+        block_box(ax[u], ay[u], az[u], lo2, hi2, s_box);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            alo[c] = fminf(alo[c], lo2[c]);
+            ahi[c] = fmaxf(ahi[c], hi2[c]);
         }
     }
     double acc[PF_APT][3];
@@ -275,18 +377,30 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         float4 P[2], Ev[2];
 #pragma unroll
         for (int hlf = 0; hlf < 2; ++hlf) {
-            const long long idx = s + hlf * PF_THREADS + threadIdx.x;
+            long long idx = s + hlf * PF_THREADS + threadIdx.x;
             v[hlf] = (idx < c1) && chi[idx] == 0;
-            if (v[hlf]) {
-                const int i = (int)(idx / nyz);
-                const long long rem = idx - (long long)i * nyz;
-                const int j = (int)(rem / g.nz);
-                const int k = (int)(rem - (long long)j * g.nz);
-                P[hlf] = make_float4(cell_pos(i, g.cx, g.h), cell_pos(j, g.cy, g.h),
-                                     cell_pos(k, g.cz, g.h), 0.f);
-                Ev[hlf] = make_float4(Ex[idx], Ey[idx], Ez[idx], 0.f);
-            }
+            if (idx >= c1) idx = s;          // position only feeds the box
+            const int i = (int)(idx / nyz);
+            const long long rem = idx - (long long)i * nyz;
+            const int j = (int)(rem / g.nz);
+            const int k = (int)(rem - (long long)j * g.nz);
+            P[hlf] = make_float4(cell_pos(i, g.cx, g.h), cell_pos(j, g.cy, g.h),
+                                 cell_pos(k, g.cz, g.h), 0.f);
+            if (v[hlf]) Ev[hlf] = make_float4(Ex[idx], Ey[idx], Ez[idx], 0.f);
         }
+        // the stage needs the clamp only if its cells' box comes within r_min
+        // of the block's atoms
+        float clo[3], chi3[3], lo2[3], hi2[3];
+        block_box(P[0].x, P[0].y, P[0].z, clo, chi3, s_box);
+        block_box(P[1].x, P[1].y, P[1].z, lo2, hi2, s_box);
+        float d2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float lo = fminf(clo[c], lo2[c]), hi = fmaxf(chi3[c], hi2[c]);
+            const float gap = fmaxf(fmaxf(alo[c] - hi, lo - ahi[c]), 0.f);
+            d2 = fmaf(gap, gap, d2);
+        }
+        const bool clamp = !(d2 > rmin2);
         const unsigned b0 = __ballot_sync(0xffffffffu, v[0]);
         const unsigned b1 = __ballot_sync(0xffffffffu, v[1]);
         __syncthreads();   // previous pass finished reading s_p / s_e
@@ -319,14 +433,26 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         float f[PF_APT][3];
 #pragma unroll
         for (int u = 0; u < PF_APT; ++u) f[u][0] = f[u][1] = f[u][2] = 0.f;
+        if (clamp) {
 #pragma unroll 2
-        for (int p = 0; p < tot; ++p) {
-            const float4 Pp = s_p[p];
-            const float4 Ep = s_e[p];
+            for (int p = 0; p < tot; ++p) {
+                const float4 Pp = s_p[p];
+                const float4 Ep = s_e[p];
 #pragma unroll
-            for (int u = 0; u < PF_APT; ++u)
-                force_pair(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
-                           k2[u], kq[u], rmin2, f[u][0], f[u][1], f[u][2]);
+                for (int u = 0; u < PF_APT; ++u)
+                    force_pair<true>(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
+                                     k2[u], kq[u], kq3[u], rmin2, f[u][0], f[u][1], f[u][2]);
+            }
+        } else {
+#pragma unroll 2
+            for (int p = 0; p < tot; ++p) {
+                const float4 Pp = s_p[p];
+                const float4 Ep = s_e[p];
+#pragma unroll
+                for (int u = 0; u < PF_APT; ++u)
+                    force_pair<false>(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
+                                      k2[u], kq[u], kq3[u], rmin2, f[u][0], f[u][1], f[u][2]);
+            }
         }
 #pragma unroll
         for (int u = 0; u < PF_APT; ++u) {
@@ -424,8 +550,8 @@ k_point_force(const float4 *__restrict__ pts, const float *__restrict__ wf,
 #pragma unroll
             for (int u = 0; u < PF_APT; ++u) {
                 float gx = 0.f, gy = 0.f, gz = 0.f;
-                force_pair(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
-                           k2[u], kq[u], rmin2, gx, gy, gz);
+                force_pair<true>(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
+                                 k2[u], kq[u], 3.f * kq[u], rmin2, gx, gy, gz);
                 f[u][0] = fmaf(Pp.w, gx, f[u][0]);
                 f[u][1] = fmaf(Pp.w, gy, f[u][1]);
                 f[u][2] = fmaf(Pp.w, gz, f[u][2]);
