@@ -192,8 +192,7 @@ struct vesis_system_t {
 
     // persistent sweep state
     int sweep_blocks = 0, ntiles = 0;
-    unsigned long long *d_PL = nullptr;
-    uint8_t *d_act = nullptr, *d_tneg = nullptr;
+    uint8_t *d_sweep = nullptr;
     unsigned *d_ctl = nullptr;
     int *d_err = nullptr, *d_rounds = nullptr, *d_capped = nullptr;
     unsigned long long *d_part_flips = nullptr;
@@ -386,8 +385,8 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
     // current with every flip
     enq_conv(s, chi, s->d_W);
     const int sp = span_begin(s);
-    VCK(launch_sweep(s->g, s->kw, s->fc, chi, s->d_W, U, s->d_dE, s->d_PL,
-                     s->d_act, s->d_tneg, s->d_ctl, s->d_err, s->d_part_flips,
+    VCK(launch_sweep(s->g, s->kw, s->fc, chi, s->d_W, U, s->d_dE, s->d_sweep,
+                     s->d_ctl, s->d_err, s->d_part_flips,
                      s->d_part_dE, s->d_rounds, s->d_capped, max_rounds,
                      s->sweep_blocks, s->d_rs, s->st));
     span_end(s, sp, 2, 0, 0);
@@ -770,14 +769,12 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VTRY(dalloc(s, &s->d_ss_gpart, (size_t)3 * n * s->ssplan.nchunk));
 
     {
-        const cudaError_t e = sweep_grid_size(s->nsm, &s->sweep_blocks);
+        const cudaError_t e = sweep_grid_size(s->nsm, r, &s->sweep_blocks);
         if (e != cudaSuccess)
             return fail(VESIS_E_CUDA, std::string("sweep occupancy: ") + cudaGetErrorString(e));
     }
     s->ntiles = sweep_tiles(s->g);
-    VTRY(dalloc(s, &s->d_PL, sweep_bricks(s->g, r)));
-    VTRY(dalloc(s, &s->d_act, 4 * (size_t)s->ntiles));
-    VTRY(dalloc(s, &s->d_tneg, s->ntiles));
+    VTRY(dalloc(s, &s->d_sweep, sweep_state_bytes(s->g, r)));
     VTRY(dalloc(s, &s->d_ctl, sweep_ctl_words()));
     VTRY(dalloc(s, &s->d_err, 1));
     VTRY(dalloc(s, &s->d_rounds, 1));

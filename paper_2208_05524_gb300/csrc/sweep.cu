@@ -1,37 +1,42 @@
 // Persistent narrow-band flip sweep (Sec. 3.1, Step 2) for sm_103a.
 //
 // All flip rounds of one interface relaxation run in a single cooperative
-// launch.  The grid is cut into 8^3 tiles; only tiles holding candidate
-// cells (a face neighbour with the other label) are active, which is the
-// band around the interface the paper restricts the flips to.
+// launch.  The grid is cut into 8^3 tiles; a round only visits tiles that
+// hold a cell that may flip or lie near one that just flipped, which keeps
+// the work on the band around the interface the paper restricts the flips
+// to.
 //
 // Selection rule (the data-parallel form of the min-heap flipping): every
-// candidate with dE < 0 gets the 32-bit key bits(float(dE)) (the raw bits of
-// a negative float grow as the value falls); other cells get 0.  The grid is
-// cut into bricks of edge B (4 when r >= 3, else 2) aligned at index 0; a
-// brick's leader is its cell with the largest key, the smallest linear index
-// among equal keys, packed as (key << 32) | (2^32 - 1 - index) so that a
-// larger word is a better leader.  A leader flips when no other brick's
-// leader within Chebyshev distance r is better.  The heap's top always
-// flips, flipped cells are more than r apart, the kernel couples none of
-// them, and a round lowers the energy by exactly the sum of their dE.
+// candidate cell (a face neighbour has the other label) whose flip lowers
+// the energy (dE < 0 in FP64, Eqs. dGj1/dGj2) gets the key float(dE); the
+// grid is cut into bricks of edge B (4 when r >= 3, else 2) aligned at
+// index 0, and a brick's leader is its cell with the most negative key, the
+// smaller linear index among equal keys.  A leader flips when no other
+// brick's leader within Chebyshev distance r comes first.  The heap's top
+// always flips, flipped cells are more than r apart, the kernel couples
+// none of them, and a round lowers the energy by exactly the sum of their
+// dE.
 //
-// Per round:
-//   phase A (one warp per active tile that a flip of the previous round
-//     came within r of - the other tiles' keys cannot have changed): the
-//     tile's candidate cells are compacted, their flip energies
-//     dE = c[s(1-2w) - g0] - s h^3 U are evaluated in FP64 (Eq. dGj1/dGj2),
-//     and the tile's brick leaders are written.  A tile without candidates
-//     turns inactive.
+// A leader is one 64-bit word, larger = first:
+//   (magnitude bits of float(dE)) << 33 | (2^32 - 1 - index) << 1 | label,
+// zero for a brick without one (PL, one word per brick).
+//
+// Round k:
+//   decide (one warp per tile holding a leader): the words of the 6^3
+//     bricks around the tile arrive together; each of the tile's leaders is
+//     tested against every other leader within r.  A winner flips its label
+//     and adds its dE, and posts itself to every tile within r of it: a
+//     16-bit entry (cell within its brick, old label) in the slot of its
+//     brick among the 6^3 bricks that tile can see, plus the slot's bit.
 //   grid barrier
-//   phase B (one warp per tile with a negative cell): the packed leaders of
-//     the 6^3 bricks around the tile arrive in shared memory together, and
-//     each brick leader of the tile is tested against them.  Winners
-//     flip; +-q_a q_b q_c is added to W over each winner's window with
-//     integer atomics (W stays the exact convolution); the tiles of the
-//     winner and of its face neighbours are activated and the tiles within
-//     r of it are marked for recomputation.
-//   grid barrier; stop when a round flipped nothing.
+//   update (one warp per tile that received a winner): W of the tile's own
+//     cells gets +-q_a q_b q_c from each posted winner whose window covers
+//     them (W stays the exact convolution, and only the warp visiting the
+//     tile writes its cells), then the tile's candidates, their dE and its
+//     leaders are recomputed.  Tiles no winner reached keep their leaders.
+//   grid barrier
+// The sweep stops when no tile holds a leader or after max_rounds rounds.
+// An opening pass computes every tile's leaders from the starting labels.
 //
 // The grid barrier spins with a bound; on timeout it raises an error flag
 // and every block returns.
@@ -40,18 +45,26 @@
 namespace vesis {
 
 constexpr int TS = 8;             // tile edge
-constexpr int TC = TS * TS * TS;  // cells per tile
 constexpr int SW_THREADS = 256;
 constexpr int NWARP = SW_THREADS / 32;
 constexpr long long kSpinLimit = 1ll << 24;   // polls before the barrier gives up
 constexpr int kLine = 32;         // words per 128-byte line of the control block
 constexpr int kMaxBricksPerTile = 64;         // (8 / 2)^3 for bricks of edge 2
-// Bricks per axis a tile's leaders can see: from brick (tile - ceil(r/B)) to
-// (tile end + ceil(r/B)); 6 for r <= 8 with B = 4 and for r <= 2 with B = 2.
+constexpr int kHaloRows = (TS + 2) * (TS + 2);
+// Bricks per axis a tile can see: the tile's own (8 / B) and ceil(r / B) on
+// each side; 6 for r <= 8 with B = 4 and for r <= 2 with B = 2.  Leaders
+// within r of a tile, and the rivals of a tile's own leaders, all lie there.
 constexpr int kNbh = 6;
-constexpr int kMaxQueue = 512;    // winners per block and round queued for W
+constexpr int kNbh3 = kNbh * kNbh * kNbh;
+// Winners within r of a tile are more than r apart inside a box of edge
+// 8 + 2r: at most ceil((8 + 2r) / (r + 1))^3 <= 125 of them.
+constexpr int kMaxWin = 128;
+// Posting area of a tile: 216 16-bit slots and an 8-word slot bitmap.
+constexpr int kPostBytes = 512;
+constexpr int kPostMaskOff = 448;
 
-// Blocks per SM of the cooperative grid.
+// Blocks per SM of the cooperative grid (upper bound; shared memory and
+// registers may allow fewer).
 #ifndef VESIS_SWEEP_BPS
 #define VESIS_SWEEP_BPS 3
 #endif
@@ -59,17 +72,23 @@ constexpr int kMaxQueue = 512;    // winners per block and round queued for W
 struct SweepArgs {
     GridDesc g;
     KernelW kw;
-    FlipConst fc;
+    double cD;          // c / 2^24 (exact)
+    double h3;
+    int qc3;            // q_0^3 = g0 * 2^24
     uint8_t *chi;
     uint32_t *W;
     const float *U;
     double *dE;
-    unsigned long long *PL;   // packed brick leaders
-    uint8_t *act0, *act1, *dirty0, *dirty1, *tneg;
+    unsigned long long *PL;   // leader word per brick
+    uint8_t *post;            // posting area per tile (kPostBytes)
+    uint8_t *upd;             // tile received a winner this round
+    uint8_t *lead;            // tile holds a leader
     int ntx, nty, ntz;
     int bs, bsh;        // brick edge and its log2
+    int reach;          // ceil(r / B)
     int nbx, nby, nbz;  // bricks per axis
-    unsigned *cnt;      // [3] flips per round, cycled
+    int vec;            // rows of 8 cells may be loaded as vectors
+    unsigned *nlead;    // tiles holding a leader (kept current by the updates)
     unsigned *bar;      // monotonic arrival counter (own 128-byte line)
     int *err;
     unsigned long long *part_flips;   // [gridDim.x]
@@ -77,6 +96,24 @@ struct SweepArgs {
     int *rounds_out;
     int *capped_out;
     int max_rounds;
+};
+
+// Per-warp shared memory; the decide and update phases use it in turn.
+struct WarpMem {
+    union {
+        struct {
+            unsigned long long w[kNbh3];   // leader words of the 6^3 bricks
+            unsigned c[kNbh3];             // their cells, 5 bits per axis
+        } d;
+        struct {
+            unsigned cW[512];              // candidates: W
+            float cU[512];                 //             U
+            unsigned short cP[512];        //             tile cell | label << 9
+            unsigned hr[kHaloRows];        // label bits of the halo rows (bit 0: z = -1)
+            unsigned win[kMaxWin];         // winners: tile coords + 8 (5 bits each) | label << 15
+            unsigned long long bmax[kMaxBricksPerTile];   // new leader per brick
+        } u;
+    };
 };
 
 // Grid barrier on a monotonic arrival counter: barrier number e (1, 2, ...)
@@ -87,13 +124,6 @@ struct SweepArgs {
 // acquire fence; no reset is needed.  The poll is bounded and watches the
 // error flag every 256 polls; a timeout raises the flag and the caller
 // returns.
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
-{
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
 {
     unsigned v;
@@ -125,17 +155,6 @@ __device__ __forceinline__ bool grid_barrier(const SweepArgs &A, unsigned &targe
     return *abort_flag == 0;
 }
 
-__device__ __forceinline__ double flip_dE_s(uint8_t chi_j, unsigned W, float U,
-                                            const FlipConst &fc)
-{
-    const double w = __dmul_rn((double)W, fc.invD3);
-    const double s = chi_j ? -1.0 : 1.0;
-    const double a = __dsub_rn(__dmul_rn(s, __dsub_rn(1.0, __dmul_rn(2.0, w))), fc.g0);
-    const double t1 = __dmul_rn(fc.c, a);
-    const double t2 = __dmul_rn(fc.h3, (double)U);
-    return __dsub_rn(t1, __dmul_rn(s, t2));
-}
-
 __device__ __forceinline__ void tile_origin(const SweepArgs &A, int t, int &i0,
                                             int &j0, int &k0)
 {
@@ -147,326 +166,472 @@ __device__ __forceinline__ void tile_origin(const SweepArgs &A, int t, int &i0,
     k0 = tk * TS;
 }
 
-__device__ __forceinline__ void mark_tile(const SweepArgs &A, uint8_t *act,
-                                          int i, int j, int k)
+// Cell (ci, cj, ck) of the leader word w of brick (bx, by, bz), found from
+// its linear index without a division: the offset from the brick's first
+// cell is di * nyz + dj * nz + dk with 0 <= di, dj, dk < B.
+__device__ __forceinline__ void leader_cell(const SweepArgs &A, unsigned long long w,
+                                            int bx, int by, int bz, int &ci, int &cj,
+                                            int &ck)
 {
-    if (i < 0 || j < 0 || k < 0 || i >= A.g.nx || j >= A.g.ny || k >= A.g.nz) return;
-    act[((i / TS) * A.nty + (j / TS)) * A.ntz + (k / TS)] = 1;
+    const long long nyz = (long long)A.g.ny * A.g.nz;
+    const long long p = (long long)(0xffffffffull - ((w >> 1) & 0xffffffffull));
+    ci = bx << A.bsh;
+    cj = by << A.bsh;
+    ck = bz << A.bsh;
+    long long d = p - ((long long)ci * nyz + (long long)cj * A.g.nz + ck);
+    for (int s = 1; s < A.bs; ++s)
+        if (d >= nyz) {
+            d -= nyz;
+            ++ci;
+        }
+    for (int s = 1; s < A.bs; ++s)
+        if (d >= A.g.nz) {
+            d -= A.g.nz;
+            ++cj;
+        }
+    ck += (int)d;
 }
 
-struct SweepShared {
-    uint8_t chi[NWARP][(TS + 2) * (TS + 2) * (TS + 2)];   // per-warp label halo
-    unsigned long long bmax[NWARP][kMaxBricksPerTile];     // per-warp brick leaders
-    uint16_t cl[NWARP][TC];                                // per-warp candidate list
-    unsigned long long nbh[NWARP][kNbh * kNbh * kNbh];     // per-warp leader neighbourhood
-    long long wl[kMaxQueue];          // this round's winners of the block
-    int nwl;
-    int abort_flag;                   // set when a grid barrier gave up
-    unsigned ncnt;                    // flips of the round, read by thread 0
-    int qw[2 * kMaxR + 1];            // 1-D kernel weights
-    int list[SW_THREADS];
-    int wc[NWARP];
-    double e[NWARP];
-    unsigned nf[NWARP];
-};
-
-// Labels, W, keys, brick leaders and tile flags change under other blocks
-// between rounds: every read of them goes to L2 (ld.global.cg), never to a
-// stale L1 line.
-
-// Phase A for one tile, one warp.
-__device__ __noinline__ void phase_keys_warp(const SweepArgs &A, SweepShared &S, int t,
-                                             uint8_t *act_next)
+// Label bits of 8 consecutive cells (one byte each, non-zero = solute).
+__device__ __forceinline__ unsigned pack8(unsigned long long v)
 {
-    constexpr int E = TS + 2;
-    constexpr int EE = E * E * E;
-    constexpr int PER = TC / 32;
-    constexpr int HB = (EE + 31) / 32;
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    uint8_t *hal = S.chi[wp];
-    unsigned long long *bmax = S.bmax[wp];
-    const int bpt = TS >> A.bsh;                   // bricks per tile edge
+    const unsigned long long lo7 = 0x7f7f7f7f7f7f7f7full;
+    unsigned long long t = ((v & lo7) + lo7) | v;       // bit 7 of a byte: byte != 0
+    t = (t >> 7) & 0x0101010101010101ull;
+    return (unsigned)((t * 0x0102040810204080ull) >> 56);
+}
+
+__device__ __forceinline__ void red_or(unsigned *p, unsigned v)
+{
+    asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Labels, W, dE, leader words, postings and tile flags change under other
+// warps and blocks between phases: every read of them goes to L2
+// (ld.global.cg), never to a stale L1 line.
+
+// Decide phase for tile t (one warp).
+__device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int t,
+                                            double &e_lane, unsigned &n_lane)
+{
+    const int lane = threadIdx.x & 31;
+    const GridDesc &g = A.g;
+    const int r = A.kw.r, bsh = A.bsh, reach = A.reach;
+    const int bpt = TS >> bsh;
     const int nbt = bpt * bpt * bpt;
     int i0, j0, k0;
     tile_origin(A, t, i0, j0, k0);
-    const GridDesc &g = A.g;
-    const long long nyz = (long long)g.ny * g.nz;
-    for (int b = lane; b < nbt; b += 32) bmax[b] = 0ull;
-    // labels of the tile and a one-cell halo: all loads of a lane issued
-    // before the first store
-#pragma unroll
-    for (int half = 0; half < 1; ++half) {
-        constexpr int HH = HB;
-        uint32_t packed[(HH + 3) / 4];
-#pragma unroll
-        for (int u = 0; u < (HH + 3) / 4; ++u) packed[u] = 0u;
-#pragma unroll
-        for (int u = 0; u < HH; ++u) {
-            const int idx = lane + 32 * (half * HH + u);
-            uint32_t v = 0;
-            if (idx < EE) {
-                const int hz = idx % E, hy = (idx / E) % E, hx = idx / (E * E);
-                const int i = i0 - 1 + hx, j = j0 - 1 + hy, k = k0 - 1 + hz;
-                if (i >= 0 && j >= 0 && k >= 0 && i < g.nx && j < g.ny && k < g.nz)
-                    v = __ldcg(A.chi + (long long)i * nyz + (long long)j * g.nz + k);
-            }
-            packed[u >> 2] |= v << (8 * (u & 3));
-        }
-#pragma unroll
-        for (int u = 0; u < HH; ++u) {
-            const int idx = lane + 32 * (half * HH + u);
-            if (idx < EE) hal[idx] = (uint8_t)(packed[u >> 2] >> (8 * (u & 3)));
-        }
-    }
-    __syncwarp();
-    // candidates, compacted into the warp's list (cell order)
-    const unsigned lt = (1u << lane) - 1u;
-    int ncand = 0;
+    const int nbx0 = (i0 >> bsh) - reach, nby0 = (j0 >> bsh) - reach, nbz0 = (k0 >> bsh) - reach;
+    constexpr int PER = (kNbh3 + 31) / 32;
+    unsigned long long v[PER];
+    unsigned cc[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
-        const int c = lane + 32 * u;
-        const int x = c / (TS * TS), y = (c / TS) % TS, z = c % TS;
-        bool cand = false;
-        if (i0 + x < g.nx && j0 + y < g.ny && k0 + z < g.nz) {
-            const int h = ((x + 1) * E + (y + 1)) * E + (z + 1);
-            const uint8_t v = hal[h];
-            cand = (hal[h - E * E] != v) | (hal[h + E * E] != v) | (hal[h - E] != v) |
-                   (hal[h + E] != v) | (hal[h - 1] != v) | (hal[h + 1] != v);
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, cand);
-        if (cand) S.cl[wp][ncand + __popc(b & lt)] = (uint16_t)c;
-        ncand += __popc(b);
-    }
-    __syncwarp();
-    // FP64 flip energies of the candidates, 128 at a time: the W and U loads
-    // of all four per lane are issued before the first use
-    bool neg = false;
-    for (int base = 0; base < ncand; base += 128) {
-        unsigned Wv[4];
-        float Uv[4];
-        long long pv[4];
-        int cv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int q = base + 32 * u + lane;
-            cv[u] = -1;
-            Wv[u] = 0u;
-            Uv[u] = 0.f;
-            pv[u] = 0;
-            if (q < ncand) {
-                const int c = S.cl[wp][q];
-                const int x = c / (TS * TS), y = (c / TS) % TS, z = c % TS;
-                cv[u] = c;
-                pv[u] = (long long)(i0 + x) * nyz + (long long)(j0 + y) * g.nz + (k0 + z);
-                Wv[u] = __ldcg(A.W + pv[u]);
-                Uv[u] = __ldg(A.U + pv[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (cv[u] < 0) continue;
-            const int c = cv[u];
-            const int x = c / (TS * TS), y = (c / TS) % TS, z = c % TS;
-            const uint8_t v = hal[((x + 1) * E + (y + 1)) * E + (z + 1)];
-            const double e = flip_dE_s(v, Wv[u], Uv[u], A.fc);
-            if (e < 0.0) {
-                const uint32_t key = __float_as_uint(__double2float_rn(e));
-                A.dE[pv[u]] = e;
-                neg = true;
-                const unsigned long long pk =
-                    ((unsigned long long)key << 32) | (0xffffffffull - (unsigned long long)pv[u]);
-                const int bb = ((x >> A.bsh) * bpt + (y >> A.bsh)) * bpt + (z >> A.bsh);
-                atomicMax(&bmax[bb], pk);
-            }
-        }
-    }
-    const bool ca = ncand > 0;
-    const bool na = __any_sync(0xffffffffu, neg);
-    __syncwarp();
-    // brick leaders of this tile (bricks lie inside the tile: B divides 8)
-    for (int b = lane; b < nbt; b += 32) {
-        const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
-        const int gi = (i0 >> A.bsh) + bx, gj = (j0 >> A.bsh) + by, gk = (k0 >> A.bsh) + bz;
-        if (gi >= A.nbx || gj >= A.nby || gk >= A.nbz) continue;
-        A.PL[((long long)gi * A.nby + gj) * A.nbz + gk] = bmax[b];
-    }
-    if (lane == 0) {
-        act_next[t] = (uint8_t)ca;
-        A.tneg[t] = (uint8_t)na;
-    }
-    __syncwarp();
-}
-
-// Phase B for one tile (one warp).  The packed leaders of the bricks its
-// leaders' windows can reach are loaded into shared memory with every load
-// in flight at once; lane b then tests the leader of the tile's brick b: it
-// wins unless another brick's leader within Chebyshev distance r is better
-// (a larger packed word).  Returns a bit mask of the winning bricks.
-__device__ unsigned long long tile_winners(const SweepArgs &A, unsigned long long *nbh, int t)
-{
-    constexpr int NN = kNbh * kNbh * kNbh;
-    constexpr int PERL = (NN + 31) / 32;
-    const int lane = threadIdx.x & 31;
-    const GridDesc &g = A.g;
-    const long long nyz = (long long)g.ny * g.nz;
-    const int r = A.kw.r;
-    const int bpt = TS >> A.bsh;
-    const int reach = (r + A.bs - 1) >> A.bsh;          // ceil(r / B) <= 2
-    int i0, j0, k0;
-    tile_origin(A, t, i0, j0, k0);
-    const int bi0 = (i0 >> A.bsh) - reach, bj0 = (j0 >> A.bsh) - reach, bk0 = (k0 >> A.bsh) - reach;
-    unsigned long long v[PERL];
-#pragma unroll
-    for (int u = 0; u < PERL; ++u) {
         const int q = lane + 32 * u;
         v[u] = 0ull;
-        if (q < NN) {
-            const int bi = bi0 + q / (kNbh * kNbh), bj = bj0 + (q / kNbh) % kNbh,
-                      bk = bk0 + q % kNbh;
-            if (bi >= 0 && bj >= 0 && bk >= 0 && bi < A.nbx && bj < A.nby && bk < A.nbz)
-                v[u] = __ldcg(A.PL + ((long long)bi * A.nby + bj) * A.nbz + bk);
+        if (q < kNbh3) {
+            const int bx = nbx0 + q / (kNbh * kNbh), by = nby0 + (q / kNbh) % kNbh,
+                      bz = nbz0 + q % kNbh;
+            if (bx >= 0 && by >= 0 && bz >= 0 && bx < A.nbx && by < A.nby && bz < A.nbz)
+                v[u] = __ldcg(A.PL + ((long long)bx * A.nby + by) * A.nbz + bz);
         }
     }
 #pragma unroll
-    for (int u = 0; u < PERL; ++u) {
+    for (int u = 0; u < PER; ++u) {
         const int q = lane + 32 * u;
-        if (q < NN) nbh[q] = v[u];
+        cc[u] = 0u;
+        if (v[u] != 0ull) {
+            int ci, cj, ck;
+            leader_cell(A, v[u], nbx0 + q / (kNbh * kNbh), nby0 + (q / kNbh) % kNbh,
+                        nbz0 + q % kNbh, ci, cj, ck);
+            cc[u] = (unsigned)(ci - (nbx0 * A.bs)) | ((unsigned)(cj - (nby0 * A.bs)) << 5) |
+                    ((unsigned)(ck - (nbz0 * A.bs)) << 10);
+        }
+        if (q < kNbh3) {
+            M.d.w[q] = v[u];
+            M.d.c[q] = cc[u];
+        }
     }
     __syncwarp();
-    const int nbt = bpt * bpt * bpt;            // 8 (B = 4) or 64 (B = 2)
-    unsigned long long mask = 0ull;
-    for (int b = lane; b < ((nbt + 31) & ~31); b += 32) {
-        bool win = false;
-        if (b < nbt) {
-            const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
-            const unsigned long long pl =
-                nbh[((bx + reach) * kNbh + (by + reach)) * kNbh + (bz + reach)];
-            if (pl != 0ull) {
-                const long long p = (long long)(0xffffffffull - (pl & 0xffffffffull));
-                const int ci = (int)(p / nyz), cj = (int)((p / g.nz) % g.ny), ck = (int)(p % g.nz);
-                // bricks holding a cell of the window, in neighbourhood coordinates
-                const int a0 = (max(ci - r, 0) >> A.bsh) - bi0, a1 = (min(ci + r, g.nx - 1) >> A.bsh) - bi0;
-                const int b0 = (max(cj - r, 0) >> A.bsh) - bj0, b1 = (min(cj + r, g.ny - 1) >> A.bsh) - bj0;
-                const int c0 = (max(ck - r, 0) >> A.bsh) - bk0, c1 = (min(ck + r, g.nz - 1) >> A.bsh) - bk0;
-                win = true;
-                for (int a = a0; a <= a1 && win; ++a)
-                    for (int bb = b0; bb <= b1 && win; ++bb)
-                        for (int c = c0; c <= c1; ++c) {
-                            const unsigned long long m = nbh[(a * kNbh + bb) * kNbh + c];
-                            if (m <= pl) continue;
-                            const long long p2 = (long long)(0xffffffffull - (m & 0xffffffffull));
-                            const int i2 = (int)(p2 / nyz), j2 = (int)((p2 / g.nz) % g.ny),
-                                      k2 = (int)(p2 % g.nz);
-                            if (abs(i2 - ci) <= r && abs(j2 - cj) <= r && abs(k2 - ck) <= r) {
-                                win = false;
-                                break;
-                            }
-                        }
+    // verdicts: a leader of the tile wins unless another within r is better
+    unsigned long long wmask = 0ull;
+    for (int b = 0; b < nbt; ++b) {
+        const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
+        const int o = ((reach + bx) * kNbh + (reach + by)) * kNbh + (reach + bz);
+        const unsigned long long L = M.d.w[o];
+        if (L == 0ull) continue;
+        const unsigned lc = M.d.c[o];
+        const int lx = lc & 31, ly = (lc >> 5) & 31, lz = (lc >> 10) & 31;
+        bool lose = false;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            if (v[u] > L) {
+                const int ox = cc[u] & 31, oy = (cc[u] >> 5) & 31, oz = (cc[u] >> 10) & 31;
+                lose |= abs(ox - lx) <= r && abs(oy - ly) <= r && abs(oz - lz) <= r;
             }
         }
-        const unsigned m32 = __ballot_sync(0xffffffffu, win);
-        mask |= (unsigned long long)m32 << (b - lane);
+        if (!__any_sync(0xffffffffu, lose)) wmask |= 1ull << b;
     }
-    __syncwarp();
-    return mask;
+    if (wmask == 0ull) return;
+    // winners: flip, add dE, post to every tile within r
+    for (int b = lane; b < nbt; b += 32) {
+        if (!((wmask >> b) & 1ull)) continue;
+        const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
+        const int o = ((reach + bx) * kNbh + (reach + by)) * kNbh + (reach + bz);
+        const unsigned long long L = M.d.w[o];
+        const long long p = (long long)(0xffffffffull - ((L >> 1) & 0xffffffffull));
+        A.chi[p] = (uint8_t)(1u - (unsigned)(L & 1ull));
+        e_lane += __ldcg(A.dE + p);
+        n_lane += 1u;
+    }
+    unsigned long long rest = wmask;
+    while (rest) {
+        const int b = __ffsll((long long)rest) - 1;
+        rest &= rest - 1;
+        const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
+        const int o = ((reach + bx) * kNbh + (reach + by)) * kNbh + (reach + bz);
+        const unsigned long long L = M.d.w[o];
+        const unsigned lc = M.d.c[o];
+        const int ci = (nbx0 * A.bs) + (int)(lc & 31), cj = (nby0 * A.bs) + (int)((lc >> 5) & 31),
+                  ck = (nbz0 * A.bs) + (int)((lc >> 10) & 31);
+        const unsigned entry = (unsigned)(ci & (A.bs - 1)) | ((unsigned)(cj & (A.bs - 1)) << 2) |
+                               ((unsigned)(ck & (A.bs - 1)) << 4) | ((unsigned)(L & 1ull) << 6);
+        const int ti0 = max(ci - r, 0) / TS, ti1 = min(ci + r, g.nx - 1) / TS;
+        const int tj0 = max(cj - r, 0) / TS, tj1 = min(cj + r, g.ny - 1) / TS;
+        const int tk0 = max(ck - r, 0) / TS, tk1 = min(ck + r, g.nz - 1) / TS;
+        if (lane < 27) {
+            const int ta = ti0 + lane / 9, tb = tj0 + (lane / 3) % 3, tc = tk0 + lane % 3;
+            if (ta <= ti1 && tb <= tj1 && tc <= tk1) {
+                const int tt = (ta * A.nty + tb) * A.ntz + tc;
+                // the winner's brick among the 6^3 bricks tile tt sees
+                const int sx = (ci >> bsh) - ((ta * TS) >> bsh) + reach;
+                const int sy = (cj >> bsh) - ((tb * TS) >> bsh) + reach;
+                const int sz = (ck >> bsh) - ((tc * TS) >> bsh) + reach;
+                const int slot = (sx * kNbh + sy) * kNbh + sz;
+                uint8_t *pa = A.post + (size_t)tt * kPostBytes;
+                reinterpret_cast<unsigned short *>(pa)[slot] = (unsigned short)entry;
+                red_or(reinterpret_cast<unsigned *>(pa + kPostMaskOff) + (slot >> 5),
+                       1u << (slot & 31));
+                A.upd[tt] = 1;
+            }
+        }
+    }
 }
 
-// W window update of one flipped cell, spread over `nthreads` threads with
-// index `tid`: +-q_a q_b q_c on every in-grid cell of the cube of half-width
-// r around it (integer atomics, so W stays the exact convolution).
-__device__ __forceinline__ void add_window(const SweepArgs &A, const int *qw, long long p,
-                                           int sgn, int tid, int nthreads)
-{
-    const GridDesc &g = A.g;
-    const long long nyz = (long long)g.ny * g.nz;
-    const int r = A.kw.r;
-    const int w = 2 * r + 1;
-    const int i = (int)(p / nyz), j = (int)((p / g.nz) % g.ny), k = (int)(p % g.nz);
-    for (int idx = tid; idx < w * w * w; idx += nthreads) {
-        const int c = idx % w, b = (idx / w) % w, a = idx / (w * w);
-        const int ii = i + a - r, jj = j + b - r, kk = k + c - r;
-        if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nx || jj >= g.ny || kk >= g.nz) continue;
-        atomicAdd(&A.W[(long long)ii * nyz + (long long)jj * g.nz + kk],
-                  (unsigned)(sgn * qw[a] * qw[b] * qw[c]));
-    }
-}
-
-// Flip of a winner by its warp: label, energy, activation of the tiles of
-// the cell and of its face neighbours, recomputation marks for the tiles
-// within r.  The W update is queued for the whole block (done after the
-// phase); if the queue is full the warp does it at once.
-__device__ void flip_winner(const SweepArgs &A, SweepShared &S, long long p,
-                            uint8_t *act_next, uint8_t *dirty_next, double &e_warp,
-                            unsigned &n_warp)
+// Update phase for tile t (one warp).  first: the opening pass (no
+// winners; every tile computes its leaders).
+__device__ __forceinline__ void tile_update(const SweepArgs &A, WarpMem &M, const int *qw,
+                                            int t, bool first)
 {
     const int lane = threadIdx.x & 31;
     const GridDesc &g = A.g;
     const long long nyz = (long long)g.ny * g.nz;
-    const int r = A.kw.r;
-    const int i = (int)(p / nyz), j = (int)((p / g.nz) % g.ny), k = (int)(p % g.nz);
-    const uint8_t old = __ldcg(A.chi + p);
-    int slot = 0;
-    if (lane == 0) {
-        A.chi[p] = (uint8_t)(1 - old);
-        e_warp += __ldcg(A.dE + p);
-        n_warp += 1;
-        slot = atomicAdd(&S.nwl, 1);
-        if (slot < kMaxQueue) S.wl[slot] = old ? -(p + 1) : (p + 1);   // sign: W change
+    const int r = A.kw.r, bsh = A.bsh, reach = A.reach;
+    const int bpt = TS >> bsh;
+    const int nbt = bpt * bpt * bpt;
+    int i0, j0, k0;
+    tile_origin(A, t, i0, j0, k0);
+    const int zlim = min(TS, g.nz - k0);
+    const unsigned zmask = (1u << zlim) - 1u;
+
+    // ---------------------------------------------------------- loads
+    // All of a lane's loads are issued before the first use.  W and U of the
+    // tile's own cells: rows rho = lane + 32 m, (x, y) = (rho >> 3, rho & 7).
+    unsigned Wr[2][TS];
+    float Ur[2][TS];
+    bool rowok[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int rho = lane + 32 * m;
+        const int x = rho >> 3, y = rho & 7;
+        rowok[m] = (i0 + x < g.nx) && (j0 + y < g.ny);
+#pragma unroll
+        for (int z = 0; z < TS; ++z) {
+            Wr[m][z] = 0u;
+            Ur[m][z] = 0.f;
+        }
+        if (rowok[m]) {
+            const long long o = (long long)(i0 + x) * nyz + (long long)(j0 + y) * g.nz + k0;
+            if (A.vec) {
+                const uint4 *wp = reinterpret_cast<const uint4 *>(A.W + o);
+                const float4 *up = reinterpret_cast<const float4 *>(A.U + o);
+                const uint4 w0 = __ldcg(wp), w1 = __ldcg(wp + 1);
+                const float4 u0 = __ldg(up), u1 = __ldg(up + 1);
+                Wr[m][0] = w0.x; Wr[m][1] = w0.y; Wr[m][2] = w0.z; Wr[m][3] = w0.w;
+                Wr[m][4] = w1.x; Wr[m][5] = w1.y; Wr[m][6] = w1.z; Wr[m][7] = w1.w;
+                Ur[m][0] = u0.x; Ur[m][1] = u0.y; Ur[m][2] = u0.z; Ur[m][3] = u0.w;
+                Ur[m][4] = u1.x; Ur[m][5] = u1.y; Ur[m][6] = u1.z; Ur[m][7] = u1.w;
+            } else {
+#pragma unroll
+                for (int z = 0; z < TS; ++z)
+                    if (z < zlim) {
+                        Wr[m][z] = __ldcg(A.W + o + z);
+                        Ur[m][z] = __ldg(A.U + o + z);
+                    }
+            }
+        }
     }
-    slot = __shfl_sync(0xffffffffu, slot, 0);
-    if (slot >= kMaxQueue) add_window(A, S.qw, p, old ? -1 : 1, lane, 32);
-    if (lane < 7) {
-        const int di = (lane == 1) - (lane == 2), dj = (lane == 3) - (lane == 4),
-                  dk = (lane == 5) - (lane == 6);
-        mark_tile(A, act_next, i + di, j + dj, k + dk);
+    // halo label rows: row h = hx * 10 + hy is the cell column
+    // (i0 - 1 + hx, j0 - 1 + hy); bit z + 1 is cell k0 + z, z = -1..8
+    unsigned hb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int h = lane + 32 * u;
+        hb[u] = 0u;
+        if (h < kHaloRows) {
+            const int i = i0 - 1 + h / 10, j = j0 - 1 + h % 10;
+            if (i >= 0 && j >= 0 && i < g.nx && j < g.ny) {
+                const uint8_t *row = A.chi + (long long)i * nyz + (long long)j * g.nz;
+                if (A.vec) {
+                    const unsigned lo = k0 > 0 ? (__ldcg(row + k0 - 1) != 0) : 0u;
+                    const unsigned mid =
+                        pack8(__ldcg(reinterpret_cast<const unsigned long long *>(row + k0)));
+                    const unsigned hi = k0 + TS < g.nz ? (__ldcg(row + k0 + TS) != 0) : 0u;
+                    hb[u] = lo | (mid << 1) | (hi << 9);
+                } else {
+                    unsigned b = 0u;
+                    for (int z = -1; z <= TS; ++z) {
+                        const int k = k0 + z;
+                        if (k >= 0 && k < g.nz && __ldcg(row + k) != 0) b |= 1u << (z + 1);
+                    }
+                    hb[u] = b;
+                }
+            }
+        }
     }
-    // tiles holding a cell within r of the flip: their keys change
+    // posted winners: slot bitmap (lanes 0..7) and the 216 slots (lanes x 4 per u64)
+    uint8_t *pa = A.post + (size_t)t * kPostBytes;
+    unsigned pmask = 0u;
+    unsigned long long pslot[2] = {0ull, 0ull};
+    const uint8_t old_lead = first ? 0 : __ldcg(A.lead + t);
+    if (!first) {
+        if (lane < 8) pmask = __ldcg(reinterpret_cast<const unsigned *>(pa + kPostMaskOff) + lane);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int q = lane + 32 * m;            // u64 q holds slots 4q .. 4q + 3
+            if (q < kNbh3 / 4) pslot[m] = __ldcg(reinterpret_cast<const unsigned long long *>(pa) + q);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int h = lane + 32 * u;
+        if (h < kHaloRows) M.u.hr[h] = hb[u];
+    }
+
+    // ------------------------------------------------- posted winners
+    int nw = 0;
+    if (!first) {
+        // the bitmap is consumed: clear it for the next round's postings
+        if (lane < 8 && pmask) reinterpret_cast<unsigned *>(pa + kPostMaskOff)[lane] = 0u;
+        // slot values to shared memory (reuse the candidate W list as scratch)
+        unsigned short *ps = reinterpret_cast<unsigned short *>(M.u.cW);
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int q = lane + 32 * m;
+            if (q < kNbh3 / 4) reinterpret_cast<unsigned long long *>(ps)[q] = pslot[m];
+        }
+        __syncwarp();
+        // decode the set slots of each bitmap word (lane l < 7 owns word l)
+        const int cnt = __popc(pmask);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        nw = __shfl_sync(0xffffffffu, incl, 7);
+        int pos = incl - cnt;
+        unsigned mm = pmask;
+        while (mm) {
+            const int bit = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const int slot = lane * 32 + bit;
+            const unsigned e = ps[slot];
+            const int sx = slot / (kNbh * kNbh), sy = (slot / kNbh) % kNbh, sz = slot % kNbh;
+            // winner cell relative to the tile origin
+            const int wx = (sx - reach) * A.bs + (int)(e & 3u);
+            const int wy = (sy - reach) * A.bs + (int)((e >> 2) & 3u);
+            const int wz = (sz - reach) * A.bs + (int)((e >> 4) & 3u);
+            if (pos < kMaxWin)
+                M.u.win[pos] = (unsigned)(wx + 8) | ((unsigned)(wy + 8) << 5) |
+                               ((unsigned)(wz + 8) << 10) | (((e >> 6) & 1u) << 15);
+            ++pos;
+        }
+        nw = min(nw, kMaxWin);
+        __syncwarp();
+        // W of the tile's own cells
+        bool changed[2] = {false, false};
+        for (int e = 0; e < nw; ++e) {
+            const unsigned wv = M.u.win[e];
+            const int wx = (int)(wv & 31) - 8, wy = (int)((wv >> 5) & 31) - 8,
+                      wz = (int)((wv >> 10) & 31) - 8;
+            const int sgn = ((wv >> 15) & 1u) ? -1 : 1;   // solute -> solvent lowers W
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int rho = lane + 32 * m;
+                const int ax = (rho >> 3) - wx, ay = (rho & 7) - wy;
+                if (abs(ax) > r || abs(ay) > r) continue;
+                const int qxy = sgn * qw[ax + r] * qw[ay + r];
+                changed[m] = true;
+#pragma unroll
+                for (int z = 0; z < TS; ++z) {
+                    const int az = z - wz;
+                    if (abs(az) <= r) Wr[m][z] += (unsigned)(qxy * qw[az + r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            if (!changed[m] || !rowok[m]) continue;
+            const int rho = lane + 32 * m;
+            const long long o = (long long)(i0 + (rho >> 3)) * nyz +
+                                (long long)(j0 + (rho & 7)) * g.nz + k0;
+            if (A.vec) {
+                uint4 *wp = reinterpret_cast<uint4 *>(A.W + o);
+                wp[0] = make_uint4(Wr[m][0], Wr[m][1], Wr[m][2], Wr[m][3]);
+                wp[1] = make_uint4(Wr[m][4], Wr[m][5], Wr[m][6], Wr[m][7]);
+            } else {
+#pragma unroll
+                for (int z = 0; z < TS; ++z)
+                    if (z < zlim) A.W[o + z] = Wr[m][z];
+            }
+        }
+        __syncwarp();
+    }
+
+    // ------------------------------------ candidates, dE, new leaders
+    for (int b = lane; b < nbt; b += 32) M.u.bmax[b] = 0ull;
+    int ncand = 0;
     {
-        const int ti0 = max(i - r, 0) / TS, ti1 = min(i + r, g.nx - 1) / TS;
-        const int tj0 = max(j - r, 0) / TS, tj1 = min(j + r, g.ny - 1) / TS;
-        const int tk0 = max(k - r, 0) / TS, tk1 = min(k + r, g.nz - 1) / TS;
-        const int mj = tj1 - tj0 + 1, mk = tk1 - tk0 + 1;
-        const int mt = (ti1 - ti0 + 1) * mj * mk;
-        if (lane < mt) {
-            const int ti = ti0 + lane / (mj * mk), tj = tj0 + (lane / mk) % mj, tk = tk0 + lane % mk;
-            dirty_next[(ti * A.nty + tj) * A.ntz + tk] = 1;
+        unsigned cm[2], lab[2];
+        int cnt = 0;
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int rho = lane + 32 * m;
+            const int x = rho >> 3, y = rho & 7;
+            const unsigned c = M.u.hr[(x + 1) * 10 + (y + 1)];
+            const unsigned d = (c ^ M.u.hr[x * 10 + (y + 1)]) |
+                               (c ^ M.u.hr[(x + 2) * 10 + (y + 1)]) |
+                               (c ^ M.u.hr[(x + 1) * 10 + y]) |
+                               (c ^ M.u.hr[(x + 1) * 10 + (y + 2)]) |
+                               (c ^ (c << 1)) | (c ^ (c >> 1));
+            cm[m] = rowok[m] ? (d >> 1) & zmask : 0u;
+            lab[m] = (c >> 1) & 0xffu;
+            cnt += __popc(cm[m]);
+        }
+        int incl = cnt;   // inclusive warp scan of the counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        ncand = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - cnt;
+        __syncwarp();     // the slot scratch in cW is no longer read
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int rho = lane + 32 * m;
+#pragma unroll
+            for (int z = 0; z < TS; ++z) {
+                if ((cm[m] >> z) & 1u) {
+                    M.u.cW[pos] = Wr[m][z];
+                    M.u.cU[pos] = Ur[m][z];
+                    M.u.cP[pos] = (unsigned short)((rho << 3) | z | (((lab[m] >> z) & 1u) << 9));
+                    ++pos;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // dE = c [s (1 - 2w) - g0] - s h^3 U with s = 1 - 2 chi.  With w = W / 2^24
+    // and g0 = q_0^3 / 2^24 the bracket is the integer N = s (2^24 - 2W) - q_0^3
+    // over 2^24, exact in FP64 like every step before the product with c, so
+    // c * bracket = (c / 2^24) * N with the same single rounding.
+    for (int q0 = 0; q0 < ncand; q0 += 32) {
+        const int q = q0 + lane;
+        if (q >= ncand) continue;
+        const unsigned Wv = M.u.cW[q];
+        const float Uv = M.u.cU[q];
+        const unsigned cp = M.u.cP[q];
+        const int x = (cp >> 6) & 7, y = (cp >> 3) & 7, z = cp & 7;
+        const bool solute = (cp >> 9) & 1u;
+        const int base = (1 << 24) - 2 * (int)Wv;
+        const int N = (solute ? -base : base) - A.qc3;
+        const double t1 = __dmul_rn(A.cD, (double)N);
+        const double t2 = __dmul_rn(A.h3, (double)Uv);
+        const double e = __dadd_rn(t1, solute ? t2 : -t2);
+        if (e < 0.0) {
+            const long long p =
+                (long long)(i0 + x) * nyz + (long long)(j0 + y) * g.nz + (k0 + z);
+            A.dE[p] = e;
+            const unsigned key = __float_as_uint(__double2float_rn(e)) & 0x7fffffffu;
+            const unsigned long long w = ((unsigned long long)key << 33) |
+                                         ((0xffffffffull - (unsigned long long)p) << 1) |
+                                         (unsigned long long)solute;
+            atomicMax(&M.u.bmax[((x >> bsh) * bpt + (y >> bsh)) * bpt + (z >> bsh)], w);
+        }
+    }
+    __syncwarp();
+    bool any = false;
+    for (int b = lane; b < nbt; b += 32) {
+        const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
+        const int gx = (i0 >> bsh) + bx, gy = (j0 >> bsh) + by, gz = (k0 >> bsh) + bz;
+        if (gx >= A.nbx || gy >= A.nby || gz >= A.nbz) continue;
+        const unsigned long long w = M.u.bmax[b];
+        A.PL[((long long)gx * A.nby + gy) * A.nbz + gz] = w;
+        any |= w != 0ull;
+    }
+    const bool now = __any_sync(0xffffffffu, any);
+    if (lane == 0) {
+        if (now != (old_lead != 0)) {
+            A.lead[t] = (uint8_t)now;
+            red_add(A.nlead, now ? 1u : 0xffffffffu);
         }
     }
     __syncwarp();
 }
 
+struct SweepShared {
+    int list[SW_THREADS];
+    int wc[NWARP];
+    int qw[2 * kMaxR + 1];
+    double e[NWARP];
+    unsigned nf[NWARP];
+    unsigned ncnt;
+    int abort_flag;
+};
+
 // Collects, in increasing order, this block's tiles t = blockIdx.x + k *
-// gridDim.x (k in [base, base + SW_THREADS)) whose flag is set (and, if
-// `dirty` is given, whose dirty flag is set too); returns the count (list
-// in S.list).  With `nxt` (phase A), own tiles are also prepared for the
-// next round: an inactive tile gets nxt = 0 and tneg = 0, an active tile
-// that needs no recomputation keeps nxt = 1 and its tneg, and the own
-// entries of `clear` (next round's dirty map) are zeroed.
-__device__ int gather_tiles(const SweepArgs &A, SweepShared &S, const uint8_t *flags,
-                            const uint8_t *dirty, int base, int ntiles, uint8_t *nxt,
-                            uint8_t *clear)
+// gridDim.x (k in [base, base + SW_THREADS)) whose flag is set (clearing
+// those flags if `clear`; flags = NULL: every tile); returns the count
+// (list in S.list).  With cntp, thread 0 also reads that counter into
+// S.ncnt.
+__device__ int gather_tiles(SweepShared &S, uint8_t *flags, bool clear, int base,
+                            int ntiles, const unsigned *cntp)
 {
     const int k = base + threadIdx.x;
     const long long t = (long long)blockIdx.x + (long long)k * gridDim.x;
+    unsigned c = 0u;
+    if (cntp && threadIdx.x == 0) c = ld_relaxed_u32(cntp);
     bool fl = false;
     if (t < ntiles) {
-        const bool act = __ldcg(flags + t) != 0;
-        const bool dt = dirty ? (__ldcg(dirty + t) != 0) : true;
-        fl = act && dt;
-        if (nxt) {
-            if (!act) {
-                nxt[t] = 0;
-                A.tneg[t] = 0;
-            } else if (!dt) {
-                nxt[t] = 1;
-            }
-            clear[t] = 0;
+        if (flags) {
+            fl = __ldcg(flags + t) != 0;
+            if (fl && clear) flags[t] = 0;
+        } else {
+            fl = true;
         }
     }
     const unsigned b = __ballot_sync(0xffffffffu, fl);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     __syncthreads();          // the previous list is no longer read
     if (lane == 0) S.wc[wp] = __popc(b);
+    if (cntp && threadIdx.x == 0) S.ncnt = c;
     __syncthreads();
     int off = 0, tot = 0;
 #pragma unroll
@@ -479,101 +644,82 @@ __device__ int gather_tiles(const SweepArgs &A, SweepShared &S, const uint8_t *f
     return tot;
 }
 
-__global__ void __launch_bounds__(SW_THREADS, VESIS_SWEEP_BPS)
+__global__ void __launch_bounds__(SW_THREADS, 2)
 k_sweep(SweepArgs A)
 {
     __shared__ SweepShared S;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    WarpMem *WM = reinterpret_cast<WarpMem *>(dyn);
     const int ntiles = A.ntx * A.nty * A.ntz;
     const int per_block = (ntiles + gridDim.x - 1) / gridDim.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int bpt = TS >> A.bsh;
+    WarpMem &M = WM[wp];
     for (int a = threadIdx.x; a <= 2 * A.kw.r; a += SW_THREADS) S.qw[a] = A.kw.q[a];
     if (threadIdx.x == 0) {
-        S.nwl = 0;
         S.abort_flag = 0;
+        S.ncnt = 1u;
     }
     __syncthreads();
     unsigned target = 0;      // thread 0: arrivals the next barrier waits for
-    unsigned nflip = 0;       // thread 0 only
-    double esum = 0.0;        // thread 0 only
+    double e_lane = 0.0;
+    unsigned n_lane = 0;
     int round = 0, capped = 0;
-    for (;;) {
-        uint8_t *cur = (round & 1) ? A.act1 : A.act0;
-        uint8_t *nxt = (round & 1) ? A.act0 : A.act1;
-        uint8_t *dcur = (round & 1) ? A.dirty1 : A.dirty0;
-        uint8_t *dnxt = (round & 1) ? A.dirty0 : A.dirty1;
-        if (blockIdx.x == 0 && threadIdx.x == 0) A.cnt[(round + 1) % 3] = 0;
-        // phase A: one warp per active tile that needs recomputation
+    // opening pass: leaders of the starting labels
+    for (int base = 0; base < per_block; base += SW_THREADS) {
+        const int n = gather_tiles(S, nullptr, false, base, ntiles, nullptr);
+        for (int q = wp; q < n; q += NWARP) tile_update(A, M, S.qw, S.list[q], true);
+    }
+    if (!grid_barrier(A, target, &S.abort_flag)) return;
+    for (int k = 0;; ++k) {
+        // decide
+        bool stop = false;
         for (int base = 0; base < per_block; base += SW_THREADS) {
-            const int n = gather_tiles(A, S, cur, dcur, base, ntiles, nxt, dnxt);
-            for (int q = wp; q < n; q += NWARP) phase_keys_warp(A, S, S.list[q], nxt);
-        }
-        if (!grid_barrier(A, target, &S.abort_flag)) return;
-        // phase B: one warp per tile with a negative cell
-        double e_warp = 0.0;
-        unsigned n_warp = 0;
-        for (int base = 0; base < per_block; base += SW_THREADS) {
-            const int n = gather_tiles(A, S, A.tneg, nullptr, base, ntiles, nullptr, nullptr);
-            for (int q = wp; q < n; q += NWARP) {
-                const int t = S.list[q];
-                unsigned long long mask = tile_winners(A, S.nbh[wp], t);
-                // winners in brick order (the flips of one tile are > r apart)
-                while (mask) {
-                    const int b = __ffsll((long long)mask) - 1;
-                    mask &= mask - 1;
-                    int i0, j0, k0;
-                    tile_origin(A, t, i0, j0, k0);
-                    const int reach = (A.kw.r + A.bs - 1) >> A.bsh;
-                    const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
-                    const unsigned long long pl =
-                        S.nbh[wp][((bx + reach) * kNbh + (by + reach)) * kNbh + (bz + reach)];
-                    const long long p = (long long)(0xffffffffull - (pl & 0xffffffffull));
-                    flip_winner(A, S, p, nxt, dnxt, e_warp, n_warp);
+            const int n = gather_tiles(S, A.lead, false, base, ntiles,
+                                       base == 0 ? A.nlead : nullptr);
+            if (base == 0) {
+                if (S.ncnt == 0u) {               // no leader left: converged
+                    stop = true;
+                } else if (k >= A.max_rounds) {   // cap reached with leaders left
+                    capped = 1;
+                    stop = true;
                 }
+                if (stop) break;
             }
+            for (int q = wp; q < n; q += NWARP) tile_decide(A, M, S.list[q], e_lane, n_lane);
         }
-        if (lane == 0) {
-            S.e[wp] = e_warp;
-            S.nf[wp] = n_warp;
-        }
-        __syncthreads();
-        // W updates of the queued winners by the whole block
-        {
-            const int nq = min(S.nwl, kMaxQueue);
-            for (int f = 0; f < nq; ++f) {
-                const long long v = S.wl[f];
-                add_window(A, S.qw, (v > 0 ? v : -v) - 1, v > 0 ? 1 : -1, threadIdx.x,
-                           SW_THREADS);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) S.nwl = 0;
-        if (threadIdx.x == 0) {
-            double te = 0.0;
-            unsigned nround = 0;
-            for (int q = 0; q < NWARP; ++q) {
-                te += S.e[q];
-                nround += S.nf[q];
-            }
-            esum += te;
-            nflip += nround;
-            if (nround) atomicAdd(&A.cnt[round % 3], nround);
-        }
-        if (threadIdx.x == 0) S.ncnt = 0;
-        if (!grid_barrier(A, target, &S.abort_flag)) return;
-        if (threadIdx.x == 0) S.ncnt = ld_acquire_u32(&A.cnt[round % 3]);
-        __syncthreads();
-        const unsigned n = S.ncnt;
-        if (n == 0) break;
-        ++round;
-        if (round >= A.max_rounds) {
-            capped = 1;
+        if (stop) {
+            round = k;
             break;
         }
+        if (!grid_barrier(A, target, &S.abort_flag)) return;
+        // update
+        for (int base = 0; base < per_block; base += SW_THREADS) {
+            const int n = gather_tiles(S, A.upd, true, base, ntiles, nullptr);
+            for (int q = wp; q < n; q += NWARP) tile_update(A, M, S.qw, S.list[q], false);
+        }
+        if (!grid_barrier(A, target, &S.abort_flag)) return;
     }
+    // FP64 sums of the flipped cells' dE and their counts: lanes, then warps
+    // in order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e_lane += __shfl_down_sync(0xffffffffu, e_lane, o);
+        n_lane += __shfl_down_sync(0xffffffffu, n_lane, o);
+    }
+    if (lane == 0) {
+        S.e[wp] = e_lane;
+        S.nf[wp] = n_lane;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        A.part_flips[blockIdx.x] = nflip;
-        A.part_dE[blockIdx.x] = esum;
+        double te = 0.0;
+        unsigned long long tf = 0;
+        for (int q = 0; q < NWARP; ++q) {
+            te += S.e[q];
+            tf += S.nf[q];
+        }
+        A.part_flips[blockIdx.x] = tf;
+        A.part_dE[blockIdx.x] = te;
         if (blockIdx.x == 0) {
             *A.rounds_out = round;
             *A.capped_out = capped;
@@ -613,10 +759,24 @@ long long sweep_bricks(const GridDesc &g, int r)
     return (long long)((g.nx + b - 1) / b) * ((g.ny + b - 1) / b) * ((g.nz + b - 1) / b);
 }
 
-cudaError_t sweep_grid_size(int nsm, int *blocks)
+// Sweep state: leader words, then the per-tile posting areas, then the
+// update and leader flags.
+size_t sweep_state_bytes(const GridDesc &g, int r)
 {
+    const size_t nt = (size_t)sweep_tiles(g);
+    return (size_t)sweep_bricks(g, r) * 8 + nt * kPostBytes + 2 * ((nt + 255) / 256 * 256);
+}
+
+constexpr size_t kSweepSmem = NWARP * sizeof(WarpMem);
+
+cudaError_t sweep_grid_size(int nsm, int r, int *blocks)
+{
+    (void)r;
+    cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSweepSmem);
+    if (e != cudaSuccess) return e;
     int per = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep, SW_THREADS, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep, SW_THREADS, kSweepSmem);
     if (e != cudaSuccess) return e;
     per = per > VESIS_SWEEP_BPS ? VESIS_SWEEP_BPS : per;
     *blocks = per * nsm;
@@ -627,8 +787,7 @@ int sweep_ctl_words() { return 3 * kLine; }
 
 cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &fc,
                          uint8_t *chi, uint32_t *W, const float *U,
-                         double *dE, unsigned long long *PL, uint8_t *act,
-                         uint8_t *tneg, unsigned *ctl, int *err,
+                         double *dE, void *state, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
                          int *rounds, int *capped, int max_rounds, int blocks,
                          RoundState *rs, cudaStream_t st)
@@ -636,27 +795,32 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &
     SweepArgs A;
     A.g = g;
     A.kw = kw;
-    A.fc = fc;
+    A.cD = fc.c * fc.invD3;
+    A.h3 = fc.h3;
+    A.qc3 = kw.q[kw.r] * kw.q[kw.r] * kw.q[kw.r];
     A.chi = chi;
     A.W = W;
     A.U = U;
     A.dE = dE;
-    A.PL = PL;
     A.ntx = (g.nx + TS - 1) / TS;
     A.nty = (g.ny + TS - 1) / TS;
     A.ntz = (g.nz + TS - 1) / TS;
     A.bs = sweep_brick_edge(kw.r);
     A.bsh = A.bs == 4 ? 2 : 1;
+    A.reach = (kw.r + A.bs - 1) / A.bs;
     A.nbx = (g.nx + A.bs - 1) / A.bs;
     A.nby = (g.ny + A.bs - 1) / A.bs;
     A.nbz = (g.nz + A.bs - 1) / A.bs;
-    const int ntiles = A.ntx * A.nty * A.ntz;
-    A.act0 = act;
-    A.act1 = act + ntiles;
-    A.dirty0 = act + 2 * (long long)ntiles;
-    A.dirty1 = act + 3 * (long long)ntiles;
-    A.tneg = tneg;
-    A.cnt = ctl;
+    A.vec = (g.nz % TS == 0) && ((uintptr_t)chi % 8 == 0) && ((uintptr_t)W % 16 == 0) &&
+            ((uintptr_t)U % 16 == 0);
+    const size_t nb = (size_t)A.nbx * A.nby * A.nbz;
+    const size_t nt = (size_t)A.ntx * A.nty * A.ntz;
+    uint8_t *base = static_cast<uint8_t *>(state);
+    A.PL = reinterpret_cast<unsigned long long *>(base);
+    A.post = base + nb * 8;
+    A.upd = A.post + nt * kPostBytes;
+    A.lead = A.upd + (nt + 255) / 256 * 256;
+    A.nlead = ctl;
     A.bar = ctl + kLine;
     A.err = err;
     A.part_flips = part_flips;
@@ -664,18 +828,16 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &
     A.rounds_out = rounds;
     A.capped_out = capped;
     A.max_rounds = max_rounds;
-    // every tile starts active and dirty: round 0 is a full pass that finds
-    // the band
-    cudaMemsetAsync(A.act0, 1, ntiles, st);
-    cudaMemsetAsync(A.act1, 0, ntiles, st);
-    cudaMemsetAsync(A.dirty0, 1, ntiles, st);
-    cudaMemsetAsync(A.dirty1, 0, ntiles, st);
+    // leader words are all rewritten by the opening pass; postings start
+    // empty (a slot is only read under its bitmap bit)
+    cudaMemset2DAsync(A.post + kPostMaskOff, kPostBytes, 0, 32, nt, st);
+    cudaMemsetAsync(A.upd, 0, 2 * ((nt + 255) / 256 * 256), st);
     cudaMemsetAsync(ctl, 0, sweep_ctl_words() * sizeof(unsigned), st);
     cudaMemsetAsync(err, 0, sizeof(int), st);
     void *args[] = {&A};
     count_launch();
     cudaError_t e = cudaLaunchCooperativeKernel((void *)k_sweep, dim3(blocks),
-                                                dim3(SW_THREADS), args, 0, st);
+                                                dim3(SW_THREADS), args, kSweepSmem, st);
     if (e != cudaSuccess) return e;
     count_launch();
     k_sweep_final<<<1, 1, 0, st>>>(part_flips, part_dE, blocks, rounds, capped, rs);

@@ -122,16 +122,15 @@ void launch_init_tight(const GridDesc &g, const float4 *xyzd, int n,
 int sweep_tiles(const GridDesc &g);
 int sweep_brick_edge(int r);
 long long sweep_bricks(const GridDesc &g, int r);
-cudaError_t sweep_grid_size(int nsm, int *blocks);
+cudaError_t sweep_grid_size(int nsm, int r, int *blocks);
 int sweep_ctl_words();   // unsigned words of the sweep control block
-// dE: G doubles, PL: sweep_bricks() words, act: 4 * tiles bytes
-// (active and dirty maps, two each), tneg: tiles bytes, ctl:
-// sweep_ctl_words(), err: 1 int, part_*: `blocks` entries; writes the totals
-// into *rs.
+// Bytes of sweep state (leader words, per-tile postings and flags).
+size_t sweep_state_bytes(const GridDesc &g, int r);
+// dE: G doubles, state: sweep_state_bytes(), ctl: sweep_ctl_words(),
+// err: 1 int, part_*: `blocks` entries; writes the totals into *rs.
 cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &fc,
                          uint8_t *chi, uint32_t *W, const float *U,
-                         double *dE, unsigned long long *PL, uint8_t *act,
-                         uint8_t *tneg, unsigned *ctl, int *err,
+                         double *dE, void *state, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
                          int *rounds, int *capped, int max_rounds, int blocks,
                          RoundState *rs, cudaStream_t st);
