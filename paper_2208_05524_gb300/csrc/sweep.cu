@@ -45,7 +45,10 @@
 namespace vesis {
 
 constexpr int TS = 8;             // tile edge
-constexpr int SW_THREADS = 256;
+#ifndef VESIS_SWEEP_THREADS
+#define VESIS_SWEEP_THREADS 512
+#endif
+constexpr int SW_THREADS = VESIS_SWEEP_THREADS;
 constexpr int NWARP = SW_THREADS / 32;
 constexpr long long kSpinLimit = 1ll << 24;   // polls before the barrier gives up
 constexpr int kLine = 32;         // words per 128-byte line of the control block
@@ -66,8 +69,11 @@ constexpr int kPostMaskOff = 448;
 // Blocks per SM of the cooperative grid (upper bound; shared memory and
 // registers may allow fewer).
 #ifndef VESIS_SWEEP_BPS
-#define VESIS_SWEEP_BPS 3
+#define VESIS_SWEEP_BPS 1
 #endif
+// A block keeps one bit per own tile (holds a leader) in shared memory:
+// up to 32768 own tiles, more than a grid of 2^31 cells gives any block.
+constexpr int kOwnWords = 1024;
 
 struct SweepArgs {
     GridDesc g;
@@ -80,14 +86,16 @@ struct SweepArgs {
     const float *U;
     double *dE;
     unsigned long long *PL;   // leader word per brick
+    uint8_t *PO;              // leader cell within its brick: di | dj << 2 | dk << 4
+    unsigned *CB;             // labels, one bit per cell: row (i, j) is nzw words
+    int nzw;
     uint8_t *post;            // posting area per tile (kPostBytes)
     uint8_t *upd;             // tile received a winner this round
-    uint8_t *lead;            // tile holds a leader
     int ntx, nty, ntz;
     int bs, bsh;        // brick edge and its log2
     int reach;          // ceil(r / B)
     int nbx, nby, nbz;  // bricks per axis
-    int vec;            // rows of 8 cells may be loaded as vectors
+    int vec;            // rows of 8 W and U values may be loaded as vectors
     unsigned *nlead;    // tiles holding a leader (kept current by the updates)
     unsigned *bar;      // monotonic arrival counter (own 128-byte line)
     int *err;
@@ -104,6 +112,8 @@ struct WarpMem {
         struct {
             unsigned long long w[kNbh3];   // leader words of the 6^3 bricks
             unsigned c[kNbh3];             // their cells, 5 bits per axis
+            unsigned long long cw[kNbh3];  // the non-zero words, compacted
+            unsigned cc[kNbh3];            // and their cells
         } d;
         struct {
             unsigned cW[512];              // candidates: W
@@ -192,15 +202,6 @@ __device__ __forceinline__ void leader_cell(const SweepArgs &A, unsigned long lo
     ck += (int)d;
 }
 
-// Label bits of 8 consecutive cells (one byte each, non-zero = solute).
-__device__ __forceinline__ unsigned pack8(unsigned long long v)
-{
-    const unsigned long long lo7 = 0x7f7f7f7f7f7f7f7full;
-    unsigned long long t = ((v & lo7) + lo7) | v;       // bit 7 of a byte: byte != 0
-    t = (t >> 7) & 0x0101010101010101ull;
-    return (unsigned)((t * 0x0102040810204080ull) >> 56);
-}
-
 __device__ __forceinline__ void red_or(unsigned *p, unsigned v)
 {
     asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
@@ -229,64 +230,107 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
     const int nbx0 = (i0 >> bsh) - reach, nby0 = (j0 >> bsh) - reach, nbz0 = (k0 >> bsh) - reach;
     constexpr int PER = (kNbh3 + 31) / 32;
     unsigned long long v[PER];
-    unsigned cc[PER];
+    unsigned off[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int q = lane + 32 * u;
         v[u] = 0ull;
+        off[u] = 0u;
         if (q < kNbh3) {
             const int bx = nbx0 + q / (kNbh * kNbh), by = nby0 + (q / kNbh) % kNbh,
                       bz = nbz0 + q % kNbh;
-            if (bx >= 0 && by >= 0 && bz >= 0 && bx < A.nbx && by < A.nby && bz < A.nbz)
-                v[u] = __ldcg(A.PL + ((long long)bx * A.nby + by) * A.nbz + bz);
+            if (bx >= 0 && by >= 0 && bz >= 0 && bx < A.nbx && by < A.nby && bz < A.nbz) {
+                const long long o = ((long long)bx * A.nby + by) * A.nbz + bz;
+                v[u] = __ldcg(A.PL + o);
+                off[u] = __ldcg(A.PO + o);
+            }
         }
     }
+    // leader cells relative to the neighbourhood's first cell; the non-zero
+    // words compacted for the scans below
+    int m = 0;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int q = lane + 32 * u;
-        cc[u] = 0u;
+        unsigned c = 0u;
         if (v[u] != 0ull) {
-            int ci, cj, ck;
-            leader_cell(A, v[u], nbx0 + q / (kNbh * kNbh), nby0 + (q / kNbh) % kNbh,
-                        nbz0 + q % kNbh, ci, cj, ck);
-            cc[u] = (unsigned)(ci - (nbx0 * A.bs)) | ((unsigned)(cj - (nby0 * A.bs)) << 5) |
-                    ((unsigned)(ck - (nbz0 * A.bs)) << 10);
+            const int bx = q / (kNbh * kNbh), by = (q / kNbh) % kNbh, bz = q % kNbh;
+            c = (unsigned)(bx * A.bs + (int)(off[u] & 3u)) |
+                ((unsigned)(by * A.bs + (int)((off[u] >> 2) & 3u)) << 5) |
+                ((unsigned)(bz * A.bs + (int)((off[u] >> 4) & 3u)) << 10);
         }
         if (q < kNbh3) {
             M.d.w[q] = v[u];
-            M.d.c[q] = cc[u];
+            M.d.c[q] = c;
         }
+        const unsigned bm = __ballot_sync(0xffffffffu, v[u] != 0ull);
+        if (v[u] != 0ull) {
+            const int pos = m + __popc(bm & ((1u << lane) - 1u));
+            M.d.cw[pos] = v[u];
+            M.d.cc[pos] = c;
+        }
+        m += __popc(bm);
     }
     __syncwarp();
-    // verdicts: a leader of the tile wins unless another within r is better
+    // verdicts: a leader of the tile wins unless another within r is better.
+    // G lanes share one of the tile's bricks and split the scan of the
+    // compacted words between them.
     unsigned long long wmask = 0ull;
-    for (int b = 0; b < nbt; ++b) {
-        const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
-        const int o = ((reach + bx) * kNbh + (reach + by)) * kNbh + (reach + bz);
-        const unsigned long long L = M.d.w[o];
-        if (L == 0ull) continue;
-        const unsigned lc = M.d.c[o];
-        const int lx = lc & 31, ly = (lc >> 5) & 31, lz = (lc >> 10) & 31;
-        bool lose = false;
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            if (v[u] > L) {
-                const int ox = cc[u] & 31, oy = (cc[u] >> 5) & 31, oz = (cc[u] >> 10) & 31;
-                lose |= abs(ox - lx) <= r && abs(oy - ly) <= r && abs(oz - lz) <= r;
+    {
+        const int G = nbt >= 32 ? 1 : 32 / nbt;      // 4 for 8 bricks
+        const int P = 32 / G;                         // bricks per pass
+        const int gl = lane / G, sub = lane - gl * G;
+        for (int b0 = 0; b0 < nbt; b0 += P) {
+            const int b = b0 + gl;
+            unsigned long long L = 0ull;
+            int lx = 0, ly = 0, lz = 0;
+            if (b < nbt) {
+                const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
+                const int o = ((reach + bx) * kNbh + (reach + by)) * kNbh + (reach + bz);
+                L = M.d.w[o];
+                const unsigned lc = M.d.c[o];
+                lx = lc & 31;
+                ly = (lc >> 5) & 31;
+                lz = (lc >> 10) & 31;
             }
+            bool lose = false;
+            if (L != 0ull) {
+                for (int q = sub; q < m; q += G) {
+                    if (M.d.cw[q] > L) {
+                        const unsigned c = M.d.cc[q];
+                        const int ox = c & 31, oy = (c >> 5) & 31, oz = (c >> 10) & 31;
+                        lose |= abs(ox - lx) <= r && abs(oy - ly) <= r && abs(oz - lz) <= r;
+                    }
+                }
+            }
+            const unsigned lb = __ballot_sync(0xffffffffu, lose);
+            const unsigned gm = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+            const bool win = L != 0ull && sub == 0 && ((lb >> (gl * G)) & gm) == 0u;
+            const unsigned wb = __ballot_sync(0xffffffffu, win);
+            for (int q = 0; q < P && b0 + q < nbt; ++q)
+                if ((wb >> (q * G)) & 1u) wmask |= 1ull << (b0 + q);
         }
-        if (!__any_sync(0xffffffffu, lose)) wmask |= 1ull << b;
     }
     if (wmask == 0ull) return;
-    // winners: flip, add dE, post to every tile within r
-    for (int b = lane; b < nbt; b += 32) {
-        if (!((wmask >> b) & 1ull)) continue;
+    // winners: flip and fetch dE (added at the end), post to every tile
+    // within r
+    double dv[2] = {0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int b = lane + 32 * h;
+        if (b >= nbt || !((wmask >> b) & 1ull)) continue;
         const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
         const int o = ((reach + bx) * kNbh + (reach + by)) * kNbh + (reach + bz);
         const unsigned long long L = M.d.w[o];
+        const unsigned lc = M.d.c[o];
+        const int ci = nbx0 * A.bs + (int)(lc & 31), cj = nby0 * A.bs + (int)((lc >> 5) & 31),
+                  ck = nbz0 * A.bs + (int)((lc >> 10) & 31);
         const long long p = (long long)(0xffffffffull - ((L >> 1) & 0xffffffffull));
         A.chi[p] = (uint8_t)(1u - (unsigned)(L & 1ull));
-        e_lane += __ldcg(A.dE + p);
+        asm volatile("red.relaxed.gpu.global.xor.b32 [%0], %1;"
+                     :: "l"(A.CB + ((long long)ci * g.ny + cj) * A.nzw + (ck >> 5)),
+                        "r"(1u << (ck & 31)) : "memory");
+        dv[h] = __ldcg(A.dE + p);
         n_lane += 1u;
     }
     unsigned long long rest = wmask;
@@ -321,11 +365,13 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
             }
         }
     }
+    e_lane += dv[0];
+    e_lane += dv[1];
 }
 
 // Update phase for tile t (one warp).  first: the opening pass (no
 // winners; every tile computes its leaders).
-__device__ __forceinline__ void tile_update(const SweepArgs &A, WarpMem &M, const int *qw,
+__device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, const int *qw,
                                             int t, bool first)
 {
     const int lane = threadIdx.x & 31;
@@ -376,30 +422,29 @@ __device__ __forceinline__ void tile_update(const SweepArgs &A, WarpMem &M, cons
             }
         }
     }
-    // halo label rows: row h = hx * 10 + hy is the cell column
-    // (i0 - 1 + hx, j0 - 1 + hy); bit z + 1 is cell k0 + z, z = -1..8
+    // halo label rows from the bit copy: row h = hx * 10 + hy is the cell
+    // column (i0 - 1 + hx, j0 - 1 + hy); bit z + 1 is cell k0 + z, z = -1..8.
+    // Cells k0..k0 + 7 share word k0 / 32 (k0 is a multiple of 8); cell k0 - 1
+    // or k0 + 8 sits in the word before or after when k0 % 32 is 0 or 24.
+    // Bits past the end of a row are zero (solvent, as outside the box).
     unsigned hb[4];
+    {
+        const int sh = k0 & 31, wm = k0 >> 5;
+        const bool need_lo = sh == 0 && k0 > 0, need_hi = sh == 24 && k0 + TS < g.nz;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int h = lane + 32 * u;
-        hb[u] = 0u;
-        if (h < kHaloRows) {
-            const int i = i0 - 1 + h / 10, j = j0 - 1 + h % 10;
-            if (i >= 0 && j >= 0 && i < g.nx && j < g.ny) {
-                const uint8_t *row = A.chi + (long long)i * nyz + (long long)j * g.nz;
-                if (A.vec) {
-                    const unsigned lo = k0 > 0 ? (__ldcg(row + k0 - 1) != 0) : 0u;
-                    const unsigned mid =
-                        pack8(__ldcg(reinterpret_cast<const unsigned long long *>(row + k0)));
-                    const unsigned hi = k0 + TS < g.nz ? (__ldcg(row + k0 + TS) != 0) : 0u;
-                    hb[u] = lo | (mid << 1) | (hi << 9);
-                } else {
-                    unsigned b = 0u;
-                    for (int z = -1; z <= TS; ++z) {
-                        const int k = k0 + z;
-                        if (k >= 0 && k < g.nz && __ldcg(row + k) != 0) b |= 1u << (z + 1);
-                    }
-                    hb[u] = b;
+        for (int u = 0; u < 4; ++u) {
+            const int h = lane + 32 * u;
+            hb[u] = 0u;
+            if (h < kHaloRows) {
+                const int i = i0 - 1 + h / 10, j = j0 - 1 + h % 10;
+                if (i >= 0 && j >= 0 && i < g.nx && j < g.ny) {
+                    const unsigned *row = A.CB + ((long long)i * g.ny + j) * A.nzw;
+                    const unsigned vm = __ldcg(row + wm);
+                    const unsigned vl = need_lo ? __ldcg(row + wm - 1) : 0u;
+                    const unsigned vh = need_hi ? __ldcg(row + wm + 1) : 0u;
+                    const unsigned lo = sh == 0 ? (vl >> 31) : ((vm >> (sh - 1)) & 1u);
+                    const unsigned hi = sh == 24 ? (vh & 1u) : ((vm >> (sh + 8)) & 1u);
+                    hb[u] = lo | (((vm >> sh) & 0xffu) << 1) | (hi << 9);
                 }
             }
         }
@@ -408,7 +453,6 @@ __device__ __forceinline__ void tile_update(const SweepArgs &A, WarpMem &M, cons
     uint8_t *pa = A.post + (size_t)t * kPostBytes;
     unsigned pmask = 0u;
     unsigned long long pslot[2] = {0ull, 0ull};
-    const uint8_t old_lead = first ? 0 : __ldcg(A.lead + t);
     if (!first) {
         if (lane < 8) pmask = __ldcg(reinterpret_cast<const unsigned *>(pa + kPostMaskOff) + lane);
 #pragma unroll
@@ -583,20 +627,21 @@ __device__ __forceinline__ void tile_update(const SweepArgs &A, WarpMem &M, cons
         const int gx = (i0 >> bsh) + bx, gy = (j0 >> bsh) + by, gz = (k0 >> bsh) + bz;
         if (gx >= A.nbx || gy >= A.nby || gz >= A.nbz) continue;
         const unsigned long long w = M.u.bmax[b];
-        A.PL[((long long)gx * A.nby + gy) * A.nbz + gz] = w;
+        const long long o = ((long long)gx * A.nby + gy) * A.nbz + gz;
+        A.PL[o] = w;
+        if (w != 0ull) {
+            int ci, cj, ck;
+            leader_cell(A, w, gx, gy, gz, ci, cj, ck);
+            A.PO[o] = (uint8_t)((ci & (A.bs - 1)) | ((cj & (A.bs - 1)) << 2) |
+                                ((ck & (A.bs - 1)) << 4));
+        }
         any |= w != 0ull;
     }
-    const bool now = __any_sync(0xffffffffu, any);
-    if (lane == 0) {
-        if (now != (old_lead != 0)) {
-            A.lead[t] = (uint8_t)now;
-            red_add(A.nlead, now ? 1u : 0xffffffffu);
-        }
-    }
-    __syncwarp();
+    return __any_sync(0xffffffffu, any);
 }
 
 struct SweepShared {
+    unsigned own[kOwnWords];   // own tile j = (t - blockIdx.x) / gridDim.x holds a leader
     int list[SW_THREADS];
     int wc[NWARP];
     int qw[2 * kMaxR + 1];
@@ -644,7 +689,40 @@ __device__ int gather_tiles(SweepShared &S, uint8_t *flags, bool clear, int base
     return tot;
 }
 
-__global__ void __launch_bounds__(SW_THREADS, 2)
+// Same as gather_tiles for the block's own tiles whose bit is set in S.own.
+__device__ int own_list(SweepShared &S, int base, int per_block)
+{
+    const int j = base + threadIdx.x;
+    const bool fl = j < per_block && ((S.own[j >> 5] >> (j & 31)) & 1u);
+    const unsigned b = __ballot_sync(0xffffffffu, fl);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    __syncthreads();          // the previous list is no longer read
+    if (lane == 0) S.wc[wp] = __popc(b);
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < NWARP; ++q) {
+        if (q < wp) off += S.wc[q];
+        tot += S.wc[q];
+    }
+    if (fl) S.list[off + __popc(b & ((1u << lane) - 1u))] = (int)(blockIdx.x + (long long)j * gridDim.x);
+    __syncthreads();
+    return tot;
+}
+
+// Records whether own tile t holds a leader, keeping the global count.
+__device__ __forceinline__ void set_own(const SweepArgs &A, SweepShared &S, int t, bool now)
+{
+    const int j = (int)((t - (int)blockIdx.x) / (int)gridDim.x);
+    const unsigned bit = 1u << (j & 31);
+    const bool old = (S.own[j >> 5] & bit) != 0u;
+    if (now == old) return;
+    if (now) atomicOr(&S.own[j >> 5], bit);
+    else atomicAnd(&S.own[j >> 5], ~bit);
+    red_add(A.nlead, now ? 1u : 0xffffffffu);
+}
+
+__global__ void __launch_bounds__(SW_THREADS, 1)
 k_sweep(SweepArgs A)
 {
     __shared__ SweepShared S;
@@ -655,6 +733,7 @@ k_sweep(SweepArgs A)
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     WarpMem &M = WM[wp];
     for (int a = threadIdx.x; a <= 2 * A.kw.r; a += SW_THREADS) S.qw[a] = A.kw.q[a];
+    for (int a = threadIdx.x; a < kOwnWords; a += SW_THREADS) S.own[a] = 0u;
     if (threadIdx.x == 0) {
         S.abort_flag = 0;
         S.ncnt = 1u;
@@ -667,27 +746,30 @@ k_sweep(SweepArgs A)
     // opening pass: leaders of the starting labels
     for (int base = 0; base < per_block; base += SW_THREADS) {
         const int n = gather_tiles(S, nullptr, false, base, ntiles, nullptr);
-        for (int q = wp; q < n; q += NWARP) tile_update(A, M, S.qw, S.list[q], true);
+        for (int q = wp; q < n; q += NWARP) {
+            const int t = S.list[q];
+            const bool now = tile_update(A, M, S.qw, t, true);
+            if (lane == 0) set_own(A, S, t, now);
+        }
     }
     if (!grid_barrier(A, target, &S.abort_flag)) return;
     for (int k = 0;; ++k) {
-        // decide
-        bool stop = false;
+        if (k >= A.max_rounds) {     // cap reached: capped if leaders are left
+            round = k;
+            capped = -1;
+            break;
+        }
+        // decide (the global leader count is read meanwhile; it only
+        // changes in the update phases)
+        unsigned nl = 1u;
+        if (threadIdx.x == 0) nl = ld_relaxed_u32(A.nlead);
         for (int base = 0; base < per_block; base += SW_THREADS) {
-            const int n = gather_tiles(S, A.lead, false, base, ntiles,
-                                       base == 0 ? A.nlead : nullptr);
-            if (base == 0) {
-                if (S.ncnt == 0u) {               // no leader left: converged
-                    stop = true;
-                } else if (k >= A.max_rounds) {   // cap reached with leaders left
-                    capped = 1;
-                    stop = true;
-                }
-                if (stop) break;
-            }
+            const int n = own_list(S, base, per_block);
             for (int q = wp; q < n; q += NWARP) tile_decide(A, M, S.list[q], e_lane, n_lane);
         }
-        if (stop) {
+        if (threadIdx.x == 0) S.ncnt = nl;
+        __syncthreads();
+        if (S.ncnt == 0u) {          // no leader was left: converged
             round = k;
             break;
         }
@@ -695,7 +777,11 @@ k_sweep(SweepArgs A)
         // update
         for (int base = 0; base < per_block; base += SW_THREADS) {
             const int n = gather_tiles(S, A.upd, true, base, ntiles, nullptr);
-            for (int q = wp; q < n; q += NWARP) tile_update(A, M, S.qw, S.list[q], false);
+            for (int q = wp; q < n; q += NWARP) {
+                const int t = S.list[q];
+                const bool now = tile_update(A, M, S.qw, t, false);
+                if (lane == 0) set_own(A, S, t, now);
+            }
         }
         if (!grid_barrier(A, target, &S.abort_flag)) return;
     }
@@ -722,7 +808,7 @@ k_sweep(SweepArgs A)
         A.part_dE[blockIdx.x] = te;
         if (blockIdx.x == 0) {
             *A.rounds_out = round;
-            *A.capped_out = capped;
+            *A.capped_out = capped < 0 ? (ld_relaxed_u32(A.nlead) != 0u) : 0;
         }
     }
 }
@@ -759,12 +845,33 @@ long long sweep_bricks(const GridDesc &g, int r)
     return (long long)((g.nx + b - 1) / b) * ((g.ny + b - 1) / b) * ((g.nz + b - 1) / b);
 }
 
-// Sweep state: leader words, then the per-tile posting areas, then the
-// update and leader flags.
+static size_t pad256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Sweep state: leader words, leader offsets, the per-tile posting areas,
+// the update flags and the label bits.
 size_t sweep_state_bytes(const GridDesc &g, int r)
 {
     const size_t nt = (size_t)sweep_tiles(g);
-    return (size_t)sweep_bricks(g, r) * 8 + nt * kPostBytes + 2 * ((nt + 255) / 256 * 256);
+    const size_t nb = (size_t)sweep_bricks(g, r);
+    const size_t nzw = ((size_t)g.nz + 31) / 32;
+    return nb * 8 + pad256(nb) + nt * kPostBytes + pad256(nt) +
+           (size_t)g.nx * g.ny * nzw * 4;
+}
+
+// Label bits: word w of row (i, j) holds cells 32 w .. 32 w + 31 of the row
+// (bit = cell - 32 w), zero past the row's end.
+__global__ void k_pack_labels(const uint8_t *__restrict__ chi, int nz, int nzw,
+                              long long nwords, unsigned *__restrict__ CB)
+{
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nwords) return;
+    const long long row = w / nzw;
+    const int k0 = (int)(w - row * nzw) * 32;
+    const uint8_t *src = chi + row * nz + k0;
+    const int n = min(32, nz - k0);
+    unsigned b = 0u;
+    for (int k = 0; k < n; ++k) b |= (src[k] != 0 ? 1u : 0u) << k;
+    CB[w] = b;
 }
 
 constexpr size_t kSweepSmem = NWARP * sizeof(WarpMem);
@@ -811,15 +918,17 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &
     A.nbx = (g.nx + A.bs - 1) / A.bs;
     A.nby = (g.ny + A.bs - 1) / A.bs;
     A.nbz = (g.nz + A.bs - 1) / A.bs;
-    A.vec = (g.nz % TS == 0) && ((uintptr_t)chi % 8 == 0) && ((uintptr_t)W % 16 == 0) &&
-            ((uintptr_t)U % 16 == 0);
+    A.vec = (g.nz % TS == 0) && ((uintptr_t)W % 16 == 0) && ((uintptr_t)U % 16 == 0);
     const size_t nb = (size_t)A.nbx * A.nby * A.nbz;
     const size_t nt = (size_t)A.ntx * A.nty * A.ntz;
+    if ((nt + blocks - 1) / blocks > (size_t)kOwnWords * 32) return cudaErrorInvalidValue;
     uint8_t *base = static_cast<uint8_t *>(state);
     A.PL = reinterpret_cast<unsigned long long *>(base);
-    A.post = base + nb * 8;
+    A.PO = base + nb * 8;
+    A.post = A.PO + pad256(nb);
     A.upd = A.post + nt * kPostBytes;
-    A.lead = A.upd + (nt + 255) / 256 * 256;
+    A.CB = reinterpret_cast<unsigned *>(A.upd + pad256(nt));
+    A.nzw = (g.nz + 31) / 32;
     A.nlead = ctl;
     A.bar = ctl + kLine;
     A.err = err;
@@ -831,9 +940,15 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &
     // leader words are all rewritten by the opening pass; postings start
     // empty (a slot is only read under its bitmap bit)
     cudaMemset2DAsync(A.post + kPostMaskOff, kPostBytes, 0, 32, nt, st);
-    cudaMemsetAsync(A.upd, 0, 2 * ((nt + 255) / 256 * 256), st);
+    cudaMemsetAsync(A.upd, 0, nt, st);
     cudaMemsetAsync(ctl, 0, sweep_ctl_words() * sizeof(unsigned), st);
     cudaMemsetAsync(err, 0, sizeof(int), st);
+    {
+        const long long nwords = (long long)g.nx * g.ny * A.nzw;
+        count_launch();
+        k_pack_labels<<<(unsigned)((nwords + 255) / 256), 256, 0, st>>>(chi, g.nz, A.nzw,
+                                                                       nwords, A.CB);
+    }
     void *args[] = {&A};
     count_launch();
     cudaError_t e = cudaLaunchCooperativeKernel((void *)k_sweep, dim3(blocks),
