@@ -29,6 +29,44 @@ __device__ __forceinline__ float rsqrt_ftz(float x)
     return y;
 }
 
+// Two FP32 values in one 64-bit register, for the packed f32x2 arithmetic
+// of sm_100-class SMs: one instruction performs the same IEEE operation on
+// both halves, so the FP32 pipe is fed with half the issue slots.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk2(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ void upk2(f2 v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Block-wide min and max of three values (all threads must call).
 __device__ __forceinline__ void block_box(float x, float y, float z, float lo[3],
                                           float hi[3], float *s_box)
@@ -55,40 +93,54 @@ __device__ __forceinline__ void block_box(float x, float y, float z, float lo[3]
     }
 }
 
-// One atom against the PE_PTS cells of a thread; CLAMP applies r_min.
+// One staged atom, every value duplicated into both halves of a pair.
+struct AtomPairs {
+    f2 x, y, z, q;   // position, charge
+    f2 a, nb;        // A = 4 eps sigma^12, -B = -4 eps sigma^6
+};
+
+// One atom against the PE_PTS cells of a thread, two cells per packed
+// instruction; CLAMP applies r_min.
 template <bool CLAMP>
-__device__ __forceinline__ void energy_atom(const float4 &A, const float2 &B, float px,
-                                            float py, const float *pz, float rmin2,
-                                            float *lj, float *ex, float *ey, float *ez)
+__device__ __forceinline__ void energy_atom(const AtomPairs &at, f2 px, f2 py, const f2 *pz,
+                                            float rmin2, f2 *lj, f2 *ex, f2 *ey, f2 *ez)
 {
-    const float dx = px - A.x;
-    const float dy = py - A.y;
-    const float dxy2 = fmaf(dx, dx, dy * dy);
+    const f2 dx = sub2(px, at.x);
+    const f2 dy = sub2(py, at.y);
+    const f2 dxy2 = fma2(dx, dx, mul2(dy, dy));
 #pragma unroll
-    for (int p = 0; p < PE_PTS; ++p) {
-        const float dz = pz[p] - A.z;
-        float r2 = fmaf(dz, dz, dxy2);
-        if (CLAMP) r2 = fmaxf(r2, rmin2);
-        const float ri = rsqrt_ftz(r2);
-        const float ri2 = ri * ri;
-        const float ri3 = ri2 * ri;
-        const float ri6 = ri3 * ri3;
-        const float tl = fmaf(B.x, ri6, -B.y);   // A r^-6 - B
-        lj[p] = fmaf(ri6, tl, lj[p]);
-        const float qr3 = A.w * ri3;
-        ex[p] = fmaf(qr3, dx, ex[p]);
-        ey[p] = fmaf(qr3, dy, ey[p]);
-        ez[p] = fmaf(qr3, dz, ez[p]);
+    for (int p = 0; p < PE_PTS / 2; ++p) {
+        const f2 dz = sub2(pz[p], at.z);
+        const f2 r2 = fma2(dz, dz, dxy2);
+        float r2a, r2b;
+        upk2(r2, r2a, r2b);
+        if (CLAMP) {
+            r2a = fmaxf(r2a, rmin2);
+            r2b = fmaxf(r2b, rmin2);
+        }
+        const f2 ri = pk2(rsqrt_ftz(r2a), rsqrt_ftz(r2b));
+        const f2 ri2 = mul2(ri, ri);
+        const f2 ri3 = mul2(ri2, ri);
+        const f2 ri6 = mul2(ri3, ri3);
+        const f2 tl = fma2(at.a, ri6, at.nb);    // A r^-6 - B
+        lj[p] = fma2(ri6, tl, lj[p]);
+        const f2 qr3 = mul2(at.q, ri3);
+        ex[p] = fma2(qr3, dx, ex[p]);
+        ey[p] = fma2(qr3, dy, ey[p]);
+        ez[p] = fma2(qr3, dz, ez[p]);
     }
 }
 
-__global__ void __launch_bounds__(PE_THREADS)
+#ifndef VESIS_PE_MINB
+#define VESIS_PE_MINB 4
+#endif
+
+__global__ void __launch_bounds__(PE_THREADS, VESIS_PE_MINB)
 k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
                    float *__restrict__ U, float *__restrict__ Ex,
                    float *__restrict__ Ey, float *__restrict__ Ez)
 {
-    __shared__ float4 s_xyzq[PE_TILE];
-    __shared__ float2 s_ab[PE_TILE];
+    __shared__ __align__(16) AtomPairs s_at[PE_TILE];
     __shared__ float s_box[6 * (PE_THREADS / 32)];
     const int cpp = (g.nz + PE_PTS - 1) / PE_PTS;
     const long long t = (long long)blockIdx.x * PE_THREADS + threadIdx.x;
@@ -101,18 +153,23 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
     const int k0 = chunk * PE_PTS;
     const float px = cell_pos(i, g.cx, g.h);
     const float py = cell_pos(j, g.cy, g.h);
-    float pz[PE_PTS], lj[PE_PTS], ex[PE_PTS], ey[PE_PTS], ez[PE_PTS];
+    float pzs[PE_PTS];
 #pragma unroll
-    for (int p = 0; p < PE_PTS; ++p) {
-        pz[p] = cell_pos(k0 + p, g.cz, g.h);
-        lj[p] = ex[p] = ey[p] = ez[p] = 0.f;
+    for (int p = 0; p < PE_PTS; ++p) pzs[p] = cell_pos(k0 + p, g.cz, g.h);
+    f2 pz[PE_PTS / 2], lj[PE_PTS / 2], ex[PE_PTS / 2], ey[PE_PTS / 2], ez[PE_PTS / 2];
+    const f2 zero = pk2(0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < PE_PTS / 2; ++p) {
+        pz[p] = pk2(pzs[2 * p], pzs[2 * p + 1]);
+        lj[p] = ex[p] = ey[p] = ez[p] = zero;
     }
+    const f2 px2 = pk2(px, px), py2 = pk2(py, py);
     // bounding box of the block's cells (padding cells included: harmless)
     float clo[3], chi[3];
-    block_box(px, py, pz[0], clo, chi, s_box);
+    block_box(px, py, pzs[0], clo, chi, s_box);
     {
         float lo2[3], hi2[3];
-        block_box(px, py, pz[PE_PTS - 1], lo2, hi2, s_box);
+        block_box(px, py, pzs[PE_PTS - 1], lo2, hi2, s_box);
         clo[2] = fminf(clo[2], lo2[2]);
         chi[2] = fmaxf(chi[2], hi2[2]);
     }
@@ -123,8 +180,15 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
         bool have = false;
         for (int m = threadIdx.x; m < cnt; m += PE_THREADS) {
             const float4 A = a.xyzq[base + m];
-            s_xyzq[m] = A;
-            s_ab[m] = a.ab[base + m];
+            const float2 B = a.ab[base + m];
+            AtomPairs at;
+            at.x = pk2(A.x, A.x);
+            at.y = pk2(A.y, A.y);
+            at.z = pk2(A.z, A.z);
+            at.q = pk2(A.w, A.w);
+            at.a = pk2(B.x, B.x);
+            at.nb = pk2(-B.y, -B.y);
+            s_at[m] = at;
             ax = A.x; ay = A.y; az = A.z;
             have = true;
         }
@@ -146,25 +210,33 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
         if (d2 > rmin2) {
 #pragma unroll 2
             for (int m = 0; m < cnt; ++m)
-                energy_atom<false>(s_xyzq[m], s_ab[m], px, py, pz, rmin2, lj, ex, ey, ez);
+                energy_atom<false>(s_at[m], px2, py2, pz, rmin2, lj, ex, ey, ez);
         } else {
 #pragma unroll 2
             for (int m = 0; m < cnt; ++m)
-                energy_atom<true>(s_xyzq[m], s_ab[m], px, py, pz, rmin2, lj, ex, ey, ez);
+                energy_atom<true>(s_at[m], px2, py2, pz, rmin2, lj, ex, ey, ez);
         }
     }
     if (!live) return;
     const long long row = pen * g.nz;
 #pragma unroll
-    for (int p = 0; p < PE_PTS; ++p) {
-        const int k = k0 + p;
-        if (k < g.nz) {
-            const long long idx = row + k;
-            const float e2 = fmaf(ex[p], ex[p], fmaf(ey[p], ey[p], ez[p] * ez[p]));
-            U[idx] = fmaf(cfa, e2, rho * lj[p]);
-            Ex[idx] = ex[p];
-            Ey[idx] = ey[p];
-            Ez[idx] = ez[p];
+    for (int p = 0; p < PE_PTS / 2; ++p) {
+        float l[2], x[2], y[2], z[2];
+        upk2(lj[p], l[0], l[1]);
+        upk2(ex[p], x[0], x[1]);
+        upk2(ey[p], y[0], y[1]);
+        upk2(ez[p], z[0], z[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = k0 + 2 * p + h;
+            if (k < g.nz) {
+                const long long idx = row + k;
+                const float e2 = fmaf(x[h], x[h], fmaf(y[h], y[h], z[h] * z[h]));
+                U[idx] = fmaf(cfa, e2, rho * l[h]);
+                Ex[idx] = x[h];
+                Ey[idx] = y[h];
+                Ez[idx] = z[h];
+            }
         }
     }
 }
@@ -317,6 +389,49 @@ __device__ __forceinline__ void force_pair(float px, float py, float pz,
     fz = fmaf(cd, dz, fmaf(am, E.z, fz));
 }
 
+// The same for the thread's two atoms at once (packed pairs; nk3 = -3 kq).
+// The clamped form goes through the halves one by one.
+struct CellPairs {
+    f2 x, y, z;      // cell position, duplicated into both halves
+    f2 ex, ey, ez;   // field at the cell, duplicated
+};
+
+template <bool CLAMP>
+__device__ __forceinline__ void force_pair2(const CellPairs &c, f2 ax, f2 ay, f2 az, f2 c1,
+                                            f2 c2, f2 kq, f2 nk3, float rmin2, f2 &fx,
+                                            f2 &fy, f2 &fz)
+{
+    const f2 dx = sub2(c.x, ax), dy = sub2(c.y, ay), dz = sub2(c.z, az);
+    const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    float ra, rb;
+    upk2(r2, ra, rb);
+    f2 ri, c1m = c1, c2m = c2, k3m = nk3;
+    if (CLAMP) {
+        const bool ua = ra >= rmin2, ub = rb >= rmin2;   // not clamped
+        ri = pk2(rsqrt_ftz(fmaxf(ra, rmin2)), rsqrt_ftz(fmaxf(rb, rmin2)));
+        float s0, s1;
+        upk2(c1, s0, s1);
+        c1m = pk2(ua ? s0 : 0.f, ub ? s1 : 0.f);
+        upk2(c2, s0, s1);
+        c2m = pk2(ua ? s0 : 0.f, ub ? s1 : 0.f);
+        upk2(nk3, s0, s1);
+        k3m = pk2(ua ? s0 : 0.f, ub ? s1 : 0.f);
+    } else {
+        ri = pk2(rsqrt_ftz(ra), rsqrt_ftz(rb));
+    }
+    const f2 ri2 = mul2(ri, ri);
+    const f2 ri3 = mul2(ri2, ri);
+    const f2 ri6 = mul2(ri3, ri3);
+    const f2 ri8 = mul2(ri6, ri2);
+    const f2 glj = mul2(fma2(c1m, ri6, c2m), ri8);
+    const f2 dE = fma2(dx, c.ex, fma2(dy, c.ey, mul2(dz, c.ez)));
+    const f2 am = mul2(kq, ri3);
+    const f2 cd = fma2(mul2(k3m, ri3), mul2(dE, ri2), glj);
+    fx = fma2(cd, dx, fma2(am, c.ex, fx));
+    fy = fma2(cd, dy, fma2(am, c.ey, fy));
+    fz = fma2(cd, dz, fma2(am, c.ez, fz));
+}
+
 __global__ void __launch_bounds__(PF_THREADS)
 k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
                   const uint8_t *__restrict__ chi, const float *__restrict__ Ex,
@@ -324,8 +439,8 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
                   AtomsDev a, float rmin2, double *__restrict__ part,
                   unsigned long long *__restrict__ nsolvent)
 {
-    __shared__ float4 s_p[PF_STAGE];
-    __shared__ float4 s_e[PF_STAGE];
+    static_assert(PF_APT == 2, "the two atoms of a thread form one packed pair");
+    __shared__ __align__(16) CellPairs s_c[PF_STAGE];
     __shared__ int s_wc[2 * PF_THREADS / 32];
     __shared__ float s_box[6 * (PF_THREADS / 32)];
     const int chunk = blockIdx.x;
@@ -365,6 +480,10 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             ahi[c] = fmaxf(ahi[c], hi2[c]);
         }
     }
+    const f2 ax2 = pk2(ax[0], ax[1]), ay2 = pk2(ay[0], ay[1]), az2 = pk2(az[0], az[1]);
+    const f2 c12 = pk2(k1[0], k1[1]), c22 = pk2(k2[0], k2[1]), kq2 = pk2(kq[0], kq[1]);
+    const f2 nk32 = pk2(-kq3[0], -kq3[1]);
+    const f2 zero2 = pk2(0.f, 0.f);
     double acc[PF_APT][3];
 #pragma unroll
     for (int u = 0; u < PF_APT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = 0.0;
@@ -418,48 +537,41 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             tot += c;
         }
         const unsigned lt = (1u << lane) - 1u;
-        if (v[0]) {
-            const int pos = off0 + __popc(b0 & lt);
-            s_p[pos] = P[0];
-            s_e[pos] = Ev[0];
-        }
-        if (v[1]) {
-            const int pos = off1 + __popc(b1 & lt);
-            s_p[pos] = P[1];
-            s_e[pos] = Ev[1];
+#pragma unroll
+        for (int hlf = 0; hlf < 2; ++hlf) {
+            if (!v[hlf]) continue;
+            const int pos = (hlf ? off1 + __popc(b1 & lt) : off0 + __popc(b0 & lt));
+            CellPairs cp;
+            cp.x = pk2(P[hlf].x, P[hlf].x);
+            cp.y = pk2(P[hlf].y, P[hlf].y);
+            cp.z = pk2(P[hlf].z, P[hlf].z);
+            cp.ex = pk2(Ev[hlf].x, Ev[hlf].x);
+            cp.ey = pk2(Ev[hlf].y, Ev[hlf].y);
+            cp.ez = pk2(Ev[hlf].z, Ev[hlf].z);
+            s_c[pos] = cp;
         }
         __syncthreads();
         seen += (unsigned long long)tot;
-        float f[PF_APT][3];
-#pragma unroll
-        for (int u = 0; u < PF_APT; ++u) f[u][0] = f[u][1] = f[u][2] = 0.f;
+        f2 fx = zero2, fy = zero2, fz = zero2;
         if (clamp) {
 #pragma unroll 2
-            for (int p = 0; p < tot; ++p) {
-                const float4 Pp = s_p[p];
-                const float4 Ep = s_e[p];
-#pragma unroll
-                for (int u = 0; u < PF_APT; ++u)
-                    force_pair<true>(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
-                                     k2[u], kq[u], kq3[u], rmin2, f[u][0], f[u][1], f[u][2]);
-            }
+            for (int p = 0; p < tot; ++p)
+                force_pair2<true>(s_c[p], ax2, ay2, az2, c12, c22, kq2, nk32, rmin2, fx, fy, fz);
         } else {
 #pragma unroll 2
-            for (int p = 0; p < tot; ++p) {
-                const float4 Pp = s_p[p];
-                const float4 Ep = s_e[p];
-#pragma unroll
-                for (int u = 0; u < PF_APT; ++u)
-                    force_pair<false>(Pp.x, Pp.y, Pp.z, Ep, ax[u], ay[u], az[u], k1[u],
-                                      k2[u], kq[u], kq3[u], rmin2, f[u][0], f[u][1], f[u][2]);
-            }
+            for (int p = 0; p < tot; ++p)
+                force_pair2<false>(s_c[p], ax2, ay2, az2, c12, c22, kq2, nk32, rmin2, fx, fy, fz);
         }
-#pragma unroll
-        for (int u = 0; u < PF_APT; ++u) {
-            acc[u][0] += (double)f[u][0];
-            acc[u][1] += (double)f[u][1];
-            acc[u][2] += (double)f[u][2];
-        }
+        float f0, f1;
+        upk2(fx, f0, f1);
+        acc[0][0] += (double)f0;
+        acc[1][0] += (double)f1;
+        upk2(fy, f0, f1);
+        acc[0][1] += (double)f0;
+        acc[1][1] += (double)f1;
+        upk2(fz, f0, f1);
+        acc[0][2] += (double)f0;
+        acc[1][2] += (double)f1;
     }
 #pragma unroll
     for (int u = 0; u < PF_APT; ++u) {
