@@ -32,15 +32,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "atom-grid pair-evals/s"
-# DRAM bytes (read + write) per launch of the pair-energy kernel from one ncu
-# capture (profiles/pair_energy_grid_protein2000_grid256.md), valid only for
-# the source it was taken on: reported as null once pair.cu changes.
-TRAFFIC = {"sha256_16": "ee5aa2625926d2b8", "bytes": 2.68e6 + 208.14e6,
-           "workload": "protein2000_grid256"}
+# DRAM bytes (read + write) per launch of the pair kernels from one ncu
+# capture (profiles/pair_energy_grid_protein2000_grid256.md and
+# pair_force_grid_protein2000_grid256.md), valid only for the source they
+# were taken on: reported as null once pair.cu changes.
+TRAFFIC = {"sha256_16": "fff7eaaf2fa66493", "workload": "protein2000_grid256",
+           "pair_energy_grid": 762368 + 206455552,
+           "pair_force_grid": 1695993600 + 27971840}
 # FP32 lane operations per energy pair in the inner loop of the pair kernel:
-# dz, r^2, clamp, r^-2, r^-3, r^-6, two LJ FMAs, Q r^-3, three field FMAs
-# (the reciprocal square root runs on the SFU and is not counted).
-OPS_PER_PAIR = 12
+# dz, r^2, r^-2, r^-3, r^-6, two LJ FMAs, Q r^-3, three field FMAs (the
+# reciprocal square root runs on the SFU and is not counted; the x/y parts of
+# the distance are formed once per atom for 8 cells and not counted either).
+OPS_PER_PAIR = 11
+# The same for a gradient pair: d (3), r^2 (3), r^-2, r^-3, r^-6, r^-8, the
+# LJ factor (2), d.E (3), kq r^-3, the d d^T factor (3), six accumulations.
+FORCE_OPS_PER_PAIR = 25
 FP32_LANES_PER_SM = 128
 L2_BYTES = 129 * 1024 * 1024
 
@@ -63,13 +69,13 @@ def workloads():
     }
 
 
-def pair_traffic(workload):
+def pair_traffic(workload, kernel="pair_energy_grid"):
     import hashlib
     src = os.path.join(ROOT, "paper_2208_05524_gb300", "csrc", "pair.cu")
     with open(src, "rb") as f:
         h = hashlib.sha256(f.read()).hexdigest()[:16]
     if h == TRAFFIC["sha256_16"] and workload == TRAFFIC["workload"]:
-        return TRAFFIC["bytes"]
+        return TRAFFIC[kernel]
     return None
 
 
@@ -108,20 +114,29 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self):
+        """Opens the window whose samples stop() keeps (the sampler itself is
+        started earlier, so that its start-up stays out of the timed region)."""
+        self.t0 = time.perf_counter()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        t1 = time.perf_counter()
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        t0 = getattr(self, "t0", 0.0)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if ts < t0 or ts > t1 + 0.25:
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -284,29 +299,30 @@ def run_vesis(args, world, rank, local):
         chi.copy_(chi0, non_blocking=True)
         return S.relax(chi, xyz0, **opts)
 
+    clk = ClockSampler(local)
+    clk.start()
     for _ in range(args.warmup):
         r = step()
     torch.cuda.synchronize()
 
     # ---- device-resident timed region
-    clk = ClockSampler(local)
-    clk.start()
     S.set_timing(True)
     barrier(world)
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    clk.mark()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
     pairs = 0
     stats = []
-    for _ in range(args.steps):
+    for i in range(args.steps):
         r = step()
+        evs[i + 1].record(stream)
         pairs += r["pair_evals"]
         stats.append(r)
-    ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    ms = ev0.elapsed_time(ev1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     tm = S.get_timing()
     S.set_timing(False)
     clocks = clk.stop()
@@ -344,16 +360,26 @@ def run_vesis(args, world, rank, local):
     achieved = pairs_per_launch * OPS_PER_PAIR / avg_s
     sweep = None
     if tm["sweep_ms"] > 0:
+        # a dense sweep reads chi and U and writes chi for every cell in every
+        # round (6 B per cell); the narrow band touches far fewer cells, so
+        # this is the bandwidth a dense sweep would need to keep pace
         gbs = tm["sweep_cells"] * 6.0 / (tm["sweep_ms"] * 1e-3) / 1e9
         sweep = {"rounds": tm["sweep_rounds"], "ms": tm["sweep_ms"],
-                 "algorithmic_GBps": gbs, "peak_GBps": pk.get("hbm_gbs"),
-                 "frac": gbs / pk.get("hbm_gbs", 6800.0),
+                 "us_per_round": 1e3 * tm["sweep_ms"] / max(1, tm["sweep_rounds"]),
+                 "dense_equiv_GBps": gbs, "hbm_peak_GBps": pk.get("hbm_gbs"),
+                 "dense_equiv_frac": gbs / pk.get("hbm_gbs", 6800.0),
                  "bytes_per_cell_round": 6}
     force = None
     if tm["pair_force_launches"]:
         fs = tm["pair_force_ms"] * 1e-3 / tm["pair_force_launches"]
-        force = {"ms_per_launch": fs * 1e3,
-                 "pairs_per_s": tm["pair_force_pairs"] / tm["pair_force_launches"] / fs}
+        fpairs = tm["pair_force_pairs"] / tm["pair_force_launches"]
+        force = {"bound": "alu", "kernel": "pair_force_grid",
+                 "ms_per_launch": fs * 1e3, "pairs_per_s": fpairs / fs,
+                 "achieved": fpairs * FORCE_OPS_PER_PAIR / fs / 1e12,
+                 "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 lane-ops)",
+                 "frac": fpairs * FORCE_OPS_PER_PAIR / fs / peak_ops,
+                 "traffic": pair_traffic(args.workload, "pair_force_grid"),
+                 "ops_per_pair": FORCE_OPS_PER_PAIR}
 
     if rank == 0:
         cpu = None
@@ -369,6 +395,8 @@ def run_vesis(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": "pair-evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
+                        "max": max(step_ms)},
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl[0],
@@ -405,7 +433,7 @@ def run_vesis(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vesis", choices=["vesis", "reference"])
     ap.add_argument("--workload", default="protein2000_grid256",

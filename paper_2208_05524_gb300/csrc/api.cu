@@ -365,10 +365,12 @@ void enq_conv(vesis_system s, const uint8_t *chi, uint32_t *W)
 }
 
 // Surface and volume terms of a labelled state; total with far and ss slots.
+// w_current: d_W already holds the exact convolution of chi (the flip sweep
+// keeps it so), and the three passes are skipped.
 void enq_terms(vesis_system s, const uint8_t *chi, const float *U,
-               const float *E, double *bk)
+               const float *E, double *bk, bool w_current = false)
 {
-    enq_conv(s, chi, s->d_W);
+    if (!w_current) enq_conv(s, chi, s->d_W);
     launch_terms(s->g, chi, s->d_W, U, E, E ? E + s->G : nullptr,
                  E ? E + 2 * s->G : nullptr, (float)s->cfa, s->d_part_s,
                  s->d_part_v, s->d_part_c, s->st);
@@ -379,11 +381,11 @@ void enq_terms(vesis_system s, const uint8_t *chi, const float *U,
 }
 
 int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
-             RoundState *out)
+             RoundState *out, bool w_current = false)
 {
-    // exact integer convolution of the starting labels; the sweep keeps it
-    // current with every flip
-    enq_conv(s, chi, s->d_W);
+    // exact integer convolution of the starting labels (unless d_W holds it
+    // already); the sweep keeps it current with every flip
+    if (!w_current) enq_conv(s, chi, s->d_W);
     const int sp = span_begin(s);
     VCK(launch_sweep(s->g, s->kw, s->fc, chi, s->d_W, U, s->d_dE, s->d_sweep,
                      s->d_ctl, s->d_err, s->d_part_flips,
@@ -1017,6 +1019,8 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     enq_fields(s, s->d_U[cur], s->d_E[cur], bank(s, cur));
     enq_ss(s, s->d_xyz, bank(s, cur));
     enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur));
+    // from here on d_W is the exact convolution of chi_dev: only the sweep
+    // changes the labels in this call, and it keeps d_W current
     count_launch();
     k_gd_init<<<1, 1, 0, s->st>>>(s->d_gd, o.M0);
     VTRY(last_launch("relax init"));
@@ -1029,12 +1033,12 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     double gmax = 0.0;
     while (k < o.max_outer) {
         RoundState rs;
-        VTRY(run_blsm(s, chi_dev, s->d_U[cur], o.max_flip_rounds, &rs));
+        VTRY(run_blsm(s, chi_dev, s->d_U[cur], o.max_flip_rounds, &rs, true));
         st.flip_rounds += rs.round;
         st.flips += (long long)rs.total_flips;
         // Step 3.1-3.2: gradient and G_old at (Gamma^{k+1}, R^k)
         enq_gradient(s, chi_dev, s->d_E[cur], s->d_xyz, bank(s, cur));
-        enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur));
+        enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur), true);
         VTRY(last_launch("relax gradient"));
         VCK(cudaMemcpyAsync(s->h_u64, s->d_gmax, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, s->st));
@@ -1059,7 +1063,7 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
             enq_pack(s, s->d_xyz_new);
             enq_fields(s, s->d_U[trial], s->d_E[trial], bank(s, trial));
             enq_ss(s, s->d_xyz_new, bank(s, trial));
-            enq_terms(s, chi_dev, s->d_U[trial], s->d_E[trial], bank(s, trial));
+            enq_terms(s, chi_dev, s->d_U[trial], s->d_E[trial], bank(s, trial), true);
             count_launch();
             k_gd_decide<<<1, 1, 0, s->st>>>(s->d_gd, bank(s, cur), bank(s, trial),
                                             s->d_oob, o.ncnt_star, o.dgstar_frac,
@@ -1100,12 +1104,10 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
         }
     }
     if (status == VESIS_OK && reason == 2) status = VESIS_W_NOT_CONVERGED;
-    // final state
+    // final state: bank(cur) already holds every term at (chi, R^k) - the
+    // start, the gradient step after the last sweep or the accepted trial
+    // wrote it last - so it is only read back
     if (status >= 0) {
-        enq_pack(s, s->d_xyz);
-        enq_far(s, bank(s, cur));
-        enq_ss(s, s->d_xyz, bank(s, cur));
-        enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur));
         VTRY(last_launch("relax final"));
         VTRY(read_bank(s, bank(s, cur)));
         fill_terms(s->h_scal, true, st.terms);

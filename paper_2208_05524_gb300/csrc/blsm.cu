@@ -191,24 +191,59 @@ k_terms(GridDesc g, const uint8_t *__restrict__ chi, const uint32_t *__restrict_
     }
 }
 
-__global__ void k_terms_final(const long long *__restrict__ part_s,
-                              const double *__restrict__ part_v,
-                              const double *__restrict__ part_c, int nb,
-                              double c, double D3, double h3, double *out)
+// One block of 1024 threads, nb <= 1024 partials: integer sums are exact;
+// the FP64 sums follow a fixed tree (warp shuffles, then warp 0), so the
+// result does not depend on timing.
+__global__ void __launch_bounds__(1024)
+k_terms_final(const long long *__restrict__ part_s, const double *__restrict__ part_v,
+              const double *__restrict__ part_c, int nb, double c, double D3,
+              double h3, double *out)
 {
-    // one thread, fixed order: nb <= 1024
+    __shared__ long long s_S[32], s_N[32];
+    __shared__ double s_V[32], s_C[32];
+    const int b = threadIdx.x, lane = b & 31, w = b >> 5;
     long long S = 0, N = 0;
     double V = 0.0, Cs = 0.0;
-    for (int b = 0; b < nb; ++b) {
-        S += part_s[2 * b];
-        N += part_s[2 * b + 1];
-        V += part_v[b];
-        Cs += part_c[b];
+    if (b < nb) {
+        S = part_s[2 * b];
+        N = part_s[2 * b + 1];
+        V = part_v[b];
+        Cs = part_c[b];
     }
-    out[0] = c * ((double)S / D3);
-    out[1] = h3 * V;
-    out[2] = h3 * Cs;
-    out[3] = (double)N;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        S += __shfl_down_sync(0xffffffffu, S, o);
+        N += __shfl_down_sync(0xffffffffu, N, o);
+        V += __shfl_down_sync(0xffffffffu, V, o);
+        Cs += __shfl_down_sync(0xffffffffu, Cs, o);
+    }
+    if (lane == 0) {
+        s_S[w] = S;
+        s_N[w] = N;
+        s_V[w] = V;
+        s_C[w] = Cs;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        S = lane < nw ? s_S[lane] : 0;
+        N = lane < nw ? s_N[lane] : 0;
+        V = lane < nw ? s_V[lane] : 0.0;
+        Cs = lane < nw ? s_C[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            S += __shfl_down_sync(0xffffffffu, S, o);
+            N += __shfl_down_sync(0xffffffffu, N, o);
+            V += __shfl_down_sync(0xffffffffu, V, o);
+            Cs += __shfl_down_sync(0xffffffffu, Cs, o);
+        }
+        if (lane == 0) {
+            out[0] = c * ((double)S / D3);
+            out[1] = h3 * V;
+            out[2] = h3 * Cs;
+            out[3] = (double)N;
+        }
+    }
 }
 
 // ------------------------------------------------------------- initial chi
@@ -305,7 +340,7 @@ void launch_terms_final(const long long *part_s, const double *part_v,
                         double h3, double *out, cudaStream_t st)
 {
     count_launch();
-    k_terms_final<<<1, 1, 0, st>>>(part_s, part_v, part_c, nb, c, D3, h3, out);
+    k_terms_final<<<1, 1024, 0, st>>>(part_s, part_v, part_c, nb, c, D3, h3, out);
 }
 void launch_init_sphere(const GridDesc &g, float cx, float cy, float cz,
                         float radius, uint8_t *chi, cudaStream_t st)
