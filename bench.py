@@ -369,6 +369,17 @@ def run_vesis(args, world, rank, local):
                  "dense_equiv_GBps": gbs, "hbm_peak_GBps": pk.get("hbm_gbs"),
                  "dense_equiv_frac": gbs / pk.get("hbm_gbs", 6800.0),
                  "bytes_per_cell_round": 6}
+    conv = None
+    if tm.get("conv_launches"):
+        cs = tm["conv_ms"] * 1e-3 / tm["conv_launches"]
+        cells = tm["conv_cells"] / tm["conv_launches"]
+        # z pass: 1 B in, 2 B out; y pass: 2 in, 4 out; x pass: 4 in, 4 out
+        gbs = cells * 17.0 / cs / 1e9
+        conv = {"bound": "hbm", "kernel": "conv_z + conv_y + conv_x",
+                "ms_per_convolution": cs * 1e3, "achieved": gbs,
+                "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_cell": 17,
+                "launches": tm["conv_launches"]}
     force = None
     if tm["pair_force_launches"]:
         fs = tm["pair_force_ms"] * 1e-3 / tm["pair_force_launches"]
@@ -415,7 +426,7 @@ def run_vesis(args, world, rank, local):
                                        f"{f_max/1e6:.0f} MHz ({pk_kind} max clock)",
                          "launches": tm["pair_energy_launches"],
                          "ms_per_launch": avg_s * 1e3},
-            "sweep": sweep, "force": force,
+            "sweep": sweep, "force": force, "conv": conv,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": "pair-evals/s",
                     "h2d_bytes_per_step": G + 24 * N,

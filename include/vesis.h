@@ -230,6 +230,9 @@ typedef struct {
     long long sweep_rounds;      /* rounds enqueued in those batches */
     long long sweep_cells;       /* cells x rounds enqueued */
     long long kernel_launches;   /* library kernels launched (all systems) */
+    double conv_ms;              /* surface-kernel convolutions (three passes each) */
+    long long conv_launches;     /* convolutions timed */
+    long long conv_cells;        /* cells x convolutions */
 } vesis_timing;
 
 /* enable != 0 starts recording (and clears the totals); 0 stops. */

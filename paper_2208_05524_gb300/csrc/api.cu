@@ -293,10 +293,14 @@ void collect_spans(vesis_system s)
             s->tm.pair_force_ms += ms;
             s->tm.pair_force_launches += 1;
             s->tm.pair_force_pairs += sp.units;
-        } else {
+        } else if (sp.kind == 2) {
             s->tm.sweep_ms += ms;
             s->tm.sweep_rounds += sp.rounds;
             s->tm.sweep_cells += sp.units;
+        } else {
+            s->tm.conv_ms += ms;
+            s->tm.conv_launches += 1;
+            s->tm.conv_cells += sp.units;
         }
         s->ev_pool.push_back(sp.a);
         s->ev_pool.push_back(sp.b);
@@ -359,9 +363,11 @@ void enq_ss(vesis_system s, const double *d_pos, double *bk)
 
 void enq_conv(vesis_system s, const uint8_t *chi, uint32_t *W)
 {
-    launch_conv_z(s->g, s->kw, chi, s->d_T1, nullptr, s->st);
-    launch_conv_y(s->g, s->kw, s->d_T1, s->d_T2, nullptr, s->st);
+    const int sp = span_begin(s);
+    launch_conv_z(s->g, s->kw, chi, s->d_T1, s->st);
+    launch_conv_y(s->g, s->kw, s->d_T1, s->d_T2, s->st);
     launch_conv_x(s->g, s->kw, s->d_T2, W, s->st);
+    span_end(s, sp, 3, s->G, 0);
 }
 
 // Surface and volume terms of a labelled state; total with far and ss slots.

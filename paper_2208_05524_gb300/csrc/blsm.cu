@@ -14,70 +14,164 @@ namespace vesis {
 
 constexpr int CT = 256;   // threads per block of the cell-parallel kernels
 
-__device__ __forceinline__ bool rounds_done(const int *done)
-{
-    return done != nullptr && *(volatile const int *)done != 0;
-}
-
 static unsigned cell_blocks(const GridDesc &g)
 {
     const long long G = (long long)g.nx * g.ny * g.nz;
     return (unsigned)((G + CT - 1) / CT);
 }
 
-__global__ void k_conv_z(GridDesc g, KernelW kw, const uint8_t *__restrict__ chi,
-                         uint16_t *__restrict__ T1, const int *done)
+// The 1-D weights centred in 17 entries (q17[8 + a] = q_a, zero for
+// |a| > r), so every pass runs the same 17-tap loop for any r <= 8.
+struct Q17 {
+    int q[2 * kMaxR + 1];
+};
+
+static Q17 centred(const KernelW &kw)
 {
-    if (rounds_done(done)) return;
+    Q17 w{};
+    for (int a = -kw.r; a <= kw.r; ++a) w.q[kMaxR + a] = kw.q[a + kw.r];
+    return w;
+}
+
+// z pass, any layout: one thread per cell.
+__global__ void k_conv_z(GridDesc g, Q17 w, const uint8_t *__restrict__ chi,
+                         uint16_t *__restrict__ T1)
+{
     const long long G = (long long)g.nx * g.ny * g.nz;
     const long long p = (long long)blockIdx.x * CT + threadIdx.x;
     if (p >= G) return;
     const int k = (int)(p % g.nz);
     unsigned s = 0;
-    for (int a = -kw.r; a <= kw.r; ++a) {
+#pragma unroll
+    for (int a = -kMaxR; a <= kMaxR; ++a) {
         const int kk = k + a;
-        if (kk >= 0 && kk < g.nz) s += (unsigned)kw.q[a + kw.r] * chi[p + a];
+        if (kk >= 0 && kk < g.nz) s += (unsigned)w.q[a + kMaxR] * chi[p + a];
     }
     T1[p] = (uint16_t)s;
 }
 
-__global__ void k_conv_y(GridDesc g, KernelW kw, const uint16_t *__restrict__ T1,
-                         uint32_t *__restrict__ T2, const int *done)
+// z pass on rows of whole 8-cell chunks (nz % 8 == 0, chi 8-byte and T1
+// 16-byte aligned): one thread per chunk reads the chunk and its two
+// neighbours as three 8-byte words and writes 8 sums as one 16-byte store.
+__global__ void __launch_bounds__(CT)
+k_conv_z8(Q17 w, const uint8_t *__restrict__ chi, uint16_t *__restrict__ T1, int nz,
+          unsigned nchunk)
 {
-    if (rounds_done(done)) return;
-    const long long G = (long long)g.nx * g.ny * g.nz;
-    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
-    if (p >= G) return;
-    const int j = (int)((p / g.nz) % g.ny);
-    unsigned s = 0;
-    for (int b = -kw.r; b <= kw.r; ++b) {
-        const int jj = j + b;
-        if (jj >= 0 && jj < g.ny) s += (unsigned)kw.q[b + kw.r] * T1[p + (long long)b * g.nz];
+    const unsigned t = blockIdx.x * CT + threadIdx.x;
+    if (t >= nchunk) return;
+    const unsigned cpr = (unsigned)nz / 8u;
+    const unsigned row = t / cpr;
+    const int k0 = (int)(t - row * cpr) * 8;
+    const uint8_t *rp = chi + (long long)row * nz;
+    const unsigned long long lo =
+        k0 >= 8 ? __ldg(reinterpret_cast<const unsigned long long *>(rp + k0 - 8)) : 0ull;
+    const unsigned long long mid = __ldg(reinterpret_cast<const unsigned long long *>(rp + k0));
+    const unsigned long long hi =
+        k0 + 8 < nz ? __ldg(reinterpret_cast<const unsigned long long *>(rp + k0 + 8)) : 0ull;
+    unsigned b[24];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        b[i] = (unsigned)(lo >> (8 * i)) & 0xffu;
+        b[8 + i] = (unsigned)(mid >> (8 * i)) & 0xffu;
+        b[16 + i] = (unsigned)(hi >> (8 * i)) & 0xffu;
     }
-    T2[p] = s;
+    unsigned o[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {     // cell k0 + c: bytes c .. c + 16 are cells k0 + c - 8 .. + 8
+        unsigned s = 0;
+#pragma unroll
+        for (int m = 0; m <= 2 * kMaxR; ++m) s += (unsigned)w.q[m] * b[c + m];
+        o[c] = s;
+    }
+    *reinterpret_cast<uint4 *>(T1 + (long long)row * nz + k0) =
+        make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
+                   o[6] | (o[7] << 16));
 }
 
-__device__ __forceinline__ unsigned conv_x_at(const GridDesc &g, const KernelW &kw,
-                                              const uint32_t *__restrict__ T2,
-                                              long long p, int i, long long nyz)
+// y and x passes: every line along the pass axis (axis stride `as`) is
+// walked by threads that each own KW adjacent z cells of it and a chunk of
+// 32 outputs; 17 inputs sit in a register ring, so each input is loaded once
+// per chunk and the loads of a warp are contiguous along z.  Lines: outer
+// index o (stride os) x z index k; the element at axis position t is
+// o * os + t * as + k.
+template <typename TI>
+__device__ __forceinline__ void ld_kw(const TI *p, unsigned (&v)[1])
 {
-    unsigned s = 0;
-    for (int c = -kw.r; c <= kw.r; ++c) {
-        const int ii = i + c;
-        if (ii >= 0 && ii < g.nx) s += (unsigned)kw.q[c + kw.r] * T2[p + (long long)c * nyz];
-    }
-    return s;
+    v[0] = (unsigned)__ldg(p);
+}
+__device__ __forceinline__ void ld_kw(const uint16_t *p, unsigned (&v)[2])
+{
+    const unsigned x = __ldg(reinterpret_cast<const unsigned *>(p));
+    v[0] = x & 0xffffu;
+    v[1] = x >> 16;
+}
+__device__ __forceinline__ void ld_kw(const uint32_t *p, unsigned (&v)[2])
+{
+    const uint2 x = __ldg(reinterpret_cast<const uint2 *>(p));
+    v[0] = x.x;
+    v[1] = x.y;
+}
+__device__ __forceinline__ void st_kw(uint32_t *p, const unsigned (&v)[1]) { *p = v[0]; }
+__device__ __forceinline__ void st_kw(uint32_t *p, const unsigned (&v)[2])
+{
+    *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
 }
 
-__global__ void k_conv_x(GridDesc g, KernelW kw, const uint32_t *__restrict__ T2,
-                         uint32_t *__restrict__ W)
+constexpr int WALK = 32;   // outputs per thread along the pass axis
+
+template <int KW, typename TI>
+__global__ void __launch_bounds__(CT)
+k_conv_walk(Q17 w, const TI *__restrict__ in, uint32_t *__restrict__ out, int n_axis,
+            long long as, long long os, int nz, unsigned nthreads, unsigned nchunk)
 {
-    const long long nyz = (long long)g.ny * g.nz;
-    const long long G = nyz * g.nx;
-    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
-    if (p >= G) return;
-    const int i = (int)(p / nyz);
-    W[p] = conv_x_at(g, kw, T2, p, i, nyz);
+    const unsigned t = blockIdx.x * CT + threadIdx.x;
+    if (t >= nthreads) return;
+    const unsigned nkq = (unsigned)nz / KW;
+    const unsigned kq = t % nkq;
+    const unsigned rest = t / nkq;
+    const unsigned c = rest % nchunk;
+    const unsigned o = rest / nchunk;
+    const long long base = (long long)o * os + (long long)(kq * KW);
+    const int t0 = (int)c * WALK;
+    unsigned ring[2 * kMaxR + 1][KW];
+#pragma unroll
+    for (int s = 0; s < WALK + 2 * kMaxR; ++s) {
+        const int ta = t0 - kMaxR + s;
+        unsigned v[KW];
+        if (ta >= 0 && ta < n_axis) {
+            ld_kw(in + base + (long long)ta * as, v);
+        } else {
+#pragma unroll
+            for (int e = 0; e < KW; ++e) v[e] = 0u;
+        }
+#pragma unroll
+        for (int e = 0; e < KW; ++e) ring[s % (2 * kMaxR + 1)][e] = v[e];
+        if (s >= 2 * kMaxR) {
+            const int to = t0 + s - 2 * kMaxR;
+            if (to < n_axis) {
+                unsigned acc[KW];
+#pragma unroll
+                for (int e = 0; e < KW; ++e) acc[e] = 0u;
+#pragma unroll
+                for (int m = 0; m <= 2 * kMaxR; ++m)
+#pragma unroll
+                    for (int e = 0; e < KW; ++e)
+                        acc[e] += (unsigned)w.q[m] * ring[(s - 2 * kMaxR + m) % (2 * kMaxR + 1)][e];
+                st_kw(out + base + (long long)to * as, acc);
+            }
+        }
+    }
+}
+
+template <int KW, typename TI>
+static void launch_walk(const Q17 &w, const TI *in, uint32_t *out, int n_axis, long long as,
+                        long long os, int n_outer, int nz, cudaStream_t st)
+{
+    const unsigned nchunk = (unsigned)((n_axis + WALK - 1) / WALK);
+    const unsigned nthreads = (unsigned)n_outer * nchunk * (unsigned)(nz / KW);
+    count_launch();
+    k_conv_walk<KW, TI><<<(nthreads + CT - 1) / CT, CT, 0, st>>>(w, in, out, n_axis, as, os, nz,
+                                                                  nthreads, nchunk);
 }
 
 // Face neighbour with the other label; outside the box counts as solvent.
@@ -301,22 +395,37 @@ k_init_tight(GridDesc g, const float4 *__restrict__ xyzd, int n,
 
 // ------------------------------------------------------------- launchers
 void launch_conv_z(const GridDesc &g, const KernelW &kw, const uint8_t *chi,
-                   uint16_t *T1, const int *done, cudaStream_t st)
+                   uint16_t *T1, cudaStream_t st)
 {
+    const Q17 w = centred(kw);
+    const long long G = (long long)g.nx * g.ny * g.nz;
     count_launch();
-    k_conv_z<<<cell_blocks(g), CT, 0, st>>>(g, kw, chi, T1, done);
+    if (g.nz % 8 == 0 && (uintptr_t)chi % 8 == 0 && (uintptr_t)T1 % 16 == 0) {
+        const unsigned nchunk = (unsigned)(G / 8);
+        k_conv_z8<<<(nchunk + CT - 1) / CT, CT, 0, st>>>(w, chi, T1, g.nz, nchunk);
+    } else {
+        k_conv_z<<<cell_blocks(g), CT, 0, st>>>(g, w, chi, T1);
+    }
 }
 void launch_conv_y(const GridDesc &g, const KernelW &kw, const uint16_t *T1,
-                   uint32_t *T2, const int *done, cudaStream_t st)
+                   uint32_t *T2, cudaStream_t st)
 {
-    count_launch();
-    k_conv_y<<<cell_blocks(g), CT, 0, st>>>(g, kw, T1, T2, done);
+    const Q17 w = centred(kw);
+    const long long nyz = (long long)g.ny * g.nz;
+    if (g.nz % 2 == 0 && (uintptr_t)T1 % 4 == 0 && (uintptr_t)T2 % 8 == 0)
+        launch_walk<2>(w, T1, T2, g.ny, g.nz, nyz, g.nx, g.nz, st);
+    else
+        launch_walk<1>(w, T1, T2, g.ny, g.nz, nyz, g.nx, g.nz, st);
 }
 void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
                    uint32_t *W, cudaStream_t st)
 {
-    count_launch();
-    k_conv_x<<<cell_blocks(g), CT, 0, st>>>(g, kw, T2, W);
+    const Q17 w = centred(kw);
+    const long long nyz = (long long)g.ny * g.nz;
+    if (g.nz % 2 == 0 && (uintptr_t)T2 % 8 == 0 && (uintptr_t)W % 8 == 0)
+        launch_walk<2>(w, T2, W, g.nx, nyz, g.nz, g.ny, g.nz, st);
+    else
+        launch_walk<1>(w, T2, W, g.nx, nyz, g.nz, g.ny, g.nz, st);
 }
 void launch_flip_energy(const GridDesc &g, const uint32_t *W,
                         const uint8_t *chi, const float *U, const FlipConst &fc,

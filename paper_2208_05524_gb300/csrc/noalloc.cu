@@ -112,8 +112,8 @@ extern "C" int vesis_surface_weights_noalloc(const vesis_params *p, const uint8_
     // array has to start at zero
     uint16_t *T1 = reinterpret_cast<uint16_t *>(base);
     uint32_t *T2 = reinterpret_cast<uint32_t *>(base + kPlane1Bytes);
-    launch_conv_z(g, kw, chi_dev, T1, nullptr, st);
-    launch_conv_y(g, kw, T1, T2, nullptr, st);
+    launch_conv_z(g, kw, chi_dev, T1, st);
+    launch_conv_y(g, kw, T1, T2, st);
     launch_conv_x(g, kw, T2, W_dev, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(VESIS_E_CUDA, cudaGetErrorString(e));

@@ -89,10 +89,12 @@ void launch_sum_doubles(const double *in, int n, double *out, int accumulate,
                         cudaStream_t st);
 
 // ---------------------------------------------------------------- blsm.cu
+// Exact integer passes of the separable surface kernel: T1 = z pass of chi
+// (<= 256), T2 = y pass of T1 (<= 2^16), W = x pass of T2 (<= 2^24).
 void launch_conv_z(const GridDesc &g, const KernelW &kw, const uint8_t *chi,
-                   uint16_t *T1, const int *done, cudaStream_t st);
+                   uint16_t *T1, cudaStream_t st);
 void launch_conv_y(const GridDesc &g, const KernelW &kw, const uint16_t *T1,
-                   uint32_t *T2, const int *done, cudaStream_t st);
+                   uint32_t *T2, cudaStream_t st);
 void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
                    uint32_t *W, cudaStream_t st);
 struct FlipConst {

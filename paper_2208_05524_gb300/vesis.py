@@ -45,7 +45,8 @@ class Timing(C.Structure):
                 ("pair_energy_pairs", _ll), ("pair_force_ms", _d),
                 ("pair_force_launches", _ll), ("pair_force_pairs", _ll),
                 ("sweep_ms", _d), ("sweep_rounds", _ll), ("sweep_cells", _ll),
-                ("kernel_launches", _ll)]
+                ("kernel_launches", _ll), ("conv_ms", _d), ("conv_launches", _ll),
+                ("conv_cells", _ll)]
 
 
 STATUS = {0: "OK", -1: "E_ARG", -2: "E_CUDA", -3: "E_NAN", -4: "E_OUT_OF_BOX",

@@ -326,3 +326,43 @@ def test_blsm_small_kernel_radius_bit_exact():
     assert ro["rounds"] > 0
     assert r["rounds"] == ro["rounds"] and r["flips"] == ro["flips"]
     assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
+
+
+@pytest.mark.parametrize("case", ["all_solvent", "all_solute", "tiny", "random", "r1", "r8"])
+def test_blsm_edge_cases_bit_exact(case):
+    """Degenerate label fields, a grid smaller than one tile, a checkerboard-
+    like random start (many candidates per tile), and the smallest and
+    largest kernel radii (bricks of edge 2; the widest 6^3 brick
+    neighbourhood): identical rounds, flips and labels."""
+    vs = _vs()
+    h = 0.3
+    n = (3, 2, 5) if case == "tiny" else (20, 18, 24)
+    s = synth.single_ion(n=8, h=h)
+    s["n"] = np.array(n)
+    s["origin"] = -0.5 * np.array(n) * h
+    kw = {}
+    if case == "r1":
+        kw = dict(trunc_r=1, gauss_sigma=0.5 * h)
+    elif case == "r8":
+        kw = dict(trunc_r=8, gauss_sigma=2.0 * h)
+    p = O.params(**kw)
+    S = vs.System(s, **kw)
+    if case == "all_solvent":
+        chi0 = np.zeros(n, np.uint8)
+    elif case == "all_solute":
+        chi0 = np.ones(n, np.uint8)
+    elif case in ("tiny", "random"):
+        chi0 = synth.random_labels(n, seed=31)
+    else:
+        chi0 = _blob(n, 9)
+    U32 = (synth.random_field(n, seed=23, scale=0.05) - 0.02).astype(np.float32)
+    sc = O.surface_constants(s, p)
+    ref = chi0.copy()
+    ro = O.blsm_parallel(ref, U32.astype(np.float64), sc)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    r = S.blsm_relax(chi, _dev(U32.reshape(-1), torch.float32), terms=False)
+    if case == "all_solvent":
+        assert ro["rounds"] == 0
+    assert r["rounds"] == ro["rounds"] and r["flips"] == ro["flips"]
+    assert r["dE_sum"] == pytest.approx(ro["dE_sum"], rel=1e-12, abs=1e-12)
+    assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
