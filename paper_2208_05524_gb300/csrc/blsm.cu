@@ -14,6 +14,11 @@ namespace vesis {
 
 constexpr int CT = 256;   // threads per block of the cell-parallel kernels
 
+// y and x passes: 1 = shared-memory tiles, 0 = register walks
+#ifndef VESIS_CONV_TILE
+#define VESIS_CONV_TILE 1
+#endif
+
 static unsigned cell_blocks(const GridDesc &g)
 {
     const long long G = (long long)g.nx * g.ny * g.nz;
@@ -81,6 +86,59 @@ k_conv_z8(Q17 w, const uint8_t *__restrict__ chi, uint16_t *__restrict__ T1, int
         unsigned s = 0;
 #pragma unroll
         for (int m = 0; m <= 2 * kMaxR; ++m) s += (unsigned)w.q[m] * b[c + m];
+        o[c] = s;
+    }
+    *reinterpret_cast<uint4 *>(T1 + (long long)row * nz + k0) =
+        make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
+                   o[6] | (o[7] << 16));
+}
+
+// The z pass with byte dot products: the 17 weights, re-packed for each of
+// the 8 byte alignments c of an output inside its chunk, so that output c
+// is the sum over the six 4-byte words j of the chunk's 24-byte window of
+// dp4a(word j, qp[c][j]) (all weights must fit in a byte).
+struct QPack {
+    unsigned qp[8][6];
+};
+
+static bool pack_dp4a(const Q17 &w, QPack *out)
+{
+    for (int m = 0; m <= 2 * kMaxR; ++m)
+        if (w.q[m] < 0 || w.q[m] > 255) return false;
+    for (int c = 0; c < 8; ++c)
+        for (int j = 0; j < 6; ++j) {
+            unsigned v = 0;
+            for (int t = 0; t < 4; ++t) {
+                const int m = 4 * j + t - c;     // window byte 4j + t holds tap m
+                if (m >= 0 && m <= 2 * kMaxR) v |= (unsigned)w.q[m] << (8 * t);
+            }
+            out->qp[c][j] = v;
+        }
+    return true;
+}
+
+__global__ void __launch_bounds__(CT)
+k_conv_z8_dp4a(QPack w, const uint8_t *__restrict__ chi, uint16_t *__restrict__ T1, int nz,
+               unsigned nchunk)
+{
+    const unsigned t = blockIdx.x * CT + threadIdx.x;
+    if (t >= nchunk) return;
+    const unsigned cpr = (unsigned)nz / 8u;
+    const unsigned row = t / cpr;
+    const int k0 = (int)(t - row * cpr) * 8;
+    const uint8_t *rp = chi + (long long)row * nz;
+    const uint2 lo = k0 >= 8 ? __ldg(reinterpret_cast<const uint2 *>(rp + k0 - 8)) : make_uint2(0u, 0u);
+    const uint2 mid = __ldg(reinterpret_cast<const uint2 *>(rp + k0));
+    const uint2 hi = k0 + 8 < nz ? __ldg(reinterpret_cast<const uint2 *>(rp + k0 + 8))
+                                 : make_uint2(0u, 0u);
+    const unsigned wd[6] = {lo.x, lo.y, mid.x, mid.y, hi.x, hi.y};
+    unsigned o[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        unsigned s = 0;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (w.qp[c][j] != 0u) s = __dp4a(wd[j], w.qp[c][j], s);
         o[c] = s;
     }
     *reinterpret_cast<uint4 *>(T1 + (long long)row * nz + k0) =
@@ -161,6 +219,66 @@ k_conv_walk(Q17 w, const TI *__restrict__ in, uint32_t *__restrict__ out, int n_
             }
         }
     }
+}
+
+// y and x passes through shared memory: a block takes 64 z cells of one
+// line bundle and 64 outputs along the pass axis; its 256 threads load the
+// 80 x 64 input tile (16 halo rows) with all loads in flight, then each
+// thread forms 16 outputs of one z column from a 17-entry register ring.
+constexpr int TK = 64, TA = 64, TR = TA + 2 * kMaxR;
+
+template <typename TI>
+__global__ void __launch_bounds__(CT)
+k_conv_tile(Q17 w, const TI *__restrict__ in, uint32_t *__restrict__ out, int n_axis,
+            long long as, long long os, int nz)
+{
+    __shared__ TI tile[TR][TK];
+    const int k0 = blockIdx.x * TK, a0 = blockIdx.y * TA;
+    const long long base = (long long)blockIdx.z * os;
+    constexpr int PER = TR * TK / CT;            // 20 loads per thread
+    TI v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * CT;
+        const int row = e / TK, k = k0 + e % TK;
+        const int ta = a0 - kMaxR + row;
+        v[u] = (ta >= 0 && ta < n_axis && k < nz) ? __ldg(in + base + (long long)ta * as + k)
+                                                  : (TI)0;
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * CT;
+        tile[e / TK][e % TK] = v[u];
+    }
+    __syncthreads();
+    const int kk = threadIdx.x % TK, seg = threadIdx.x / TK;   // 4 segments of 16 outputs
+    const int k = k0 + kk;
+    if (k >= nz) return;
+    unsigned ring[2 * kMaxR + 1];
+#pragma unroll
+    for (int s = 0; s < 16 + 2 * kMaxR; ++s) {
+        ring[s % (2 * kMaxR + 1)] = (unsigned)tile[seg * 16 + s][kk];
+        if (s >= 2 * kMaxR) {
+            const int ta = a0 + seg * 16 + s - 2 * kMaxR;
+            if (ta < n_axis) {
+                unsigned acc = 0u;
+#pragma unroll
+                for (int m = 0; m <= 2 * kMaxR; ++m)
+                    acc += (unsigned)w.q[m] * ring[(s - 2 * kMaxR + m) % (2 * kMaxR + 1)];
+                out[base + (long long)ta * as + k] = acc;
+            }
+        }
+    }
+}
+
+template <typename TI>
+static void launch_tile(const Q17 &w, const TI *in, uint32_t *out, int n_axis, long long as,
+                        long long os, int n_outer, int nz, cudaStream_t st)
+{
+    count_launch();
+    const dim3 grid((unsigned)((nz + TK - 1) / TK), (unsigned)((n_axis + TA - 1) / TA),
+                    (unsigned)n_outer);
+    k_conv_tile<TI><<<grid, CT, 0, st>>>(w, in, out, n_axis, as, os, nz);
 }
 
 template <int KW, typename TI>
@@ -400,9 +518,13 @@ void launch_conv_z(const GridDesc &g, const KernelW &kw, const uint8_t *chi,
     const Q17 w = centred(kw);
     const long long G = (long long)g.nx * g.ny * g.nz;
     count_launch();
+    QPack qp;
     if (g.nz % 8 == 0 && (uintptr_t)chi % 8 == 0 && (uintptr_t)T1 % 16 == 0) {
         const unsigned nchunk = (unsigned)(G / 8);
-        k_conv_z8<<<(nchunk + CT - 1) / CT, CT, 0, st>>>(w, chi, T1, g.nz, nchunk);
+        if (pack_dp4a(w, &qp))
+            k_conv_z8_dp4a<<<(nchunk + CT - 1) / CT, CT, 0, st>>>(qp, chi, T1, g.nz, nchunk);
+        else
+            k_conv_z8<<<(nchunk + CT - 1) / CT, CT, 0, st>>>(w, chi, T1, g.nz, nchunk);
     } else {
         k_conv_z<<<cell_blocks(g), CT, 0, st>>>(g, w, chi, T1);
     }
@@ -412,7 +534,9 @@ void launch_conv_y(const GridDesc &g, const KernelW &kw, const uint16_t *T1,
 {
     const Q17 w = centred(kw);
     const long long nyz = (long long)g.ny * g.nz;
-    if (g.nz % 2 == 0 && (uintptr_t)T1 % 4 == 0 && (uintptr_t)T2 % 8 == 0)
+    if (VESIS_CONV_TILE && g.nx <= 65535)
+        launch_tile(w, T1, T2, g.ny, g.nz, nyz, g.nx, g.nz, st);
+    else if (g.nz % 2 == 0 && (uintptr_t)T1 % 4 == 0 && (uintptr_t)T2 % 8 == 0)
         launch_walk<2>(w, T1, T2, g.ny, g.nz, nyz, g.nx, g.nz, st);
     else
         launch_walk<1>(w, T1, T2, g.ny, g.nz, nyz, g.nx, g.nz, st);
@@ -422,7 +546,9 @@ void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
 {
     const Q17 w = centred(kw);
     const long long nyz = (long long)g.ny * g.nz;
-    if (g.nz % 2 == 0 && (uintptr_t)T2 % 8 == 0 && (uintptr_t)W % 8 == 0)
+    if (VESIS_CONV_TILE && g.ny <= 65535)
+        launch_tile(w, T2, W, g.nx, nyz, g.nz, g.ny, g.nz, st);
+    else if (g.nz % 2 == 0 && (uintptr_t)T2 % 8 == 0 && (uintptr_t)W % 8 == 0)
         launch_walk<2>(w, T2, W, g.nx, nyz, g.nz, g.ny, g.nz, st);
     else
         launch_walk<1>(w, T2, W, g.nx, nyz, g.nz, g.ny, g.nz, st);
