@@ -75,20 +75,21 @@ def lib():
             L.or_point_grad.argtypes = [i64, p, p, p, i, p, p, p, p, d, d, d, p]
             L.or_ss.argtypes = [i, p, p, p, p, i, p, p, p, d, p, p]
             L.or_conv.argtypes = [i, i, i, p, i, p, p]
+            L.or_conv3.argtypes = [i, i, i, p, i, p, p]
             L.or_surface_sum.argtypes = [i64, p, p, i64]
             L.or_surface_sum.restype = i64
-            L.or_delta_e.argtypes = [i, i, i, p, p, p, d, d, d, i64, p, p]
+            L.or_delta_e.argtypes = [i, i, i, p, p, p, d, i64, i64, d, p, p]
             L.or_select.argtypes = [i, i, i, p, p, i, p, p]
             L.or_select.restype = i64
             L.or_select_cells.argtypes = [i, i, i, p, p, i, p, p]
             L.or_select_cells.restype = i64
-            L.or_energy.argtypes = [i, i, i, p, p, i, p, d, d, i64]
+            L.or_energy.argtypes = [i, i, i, p, p, i, p, p, d, i64, d]
             L.or_energy.restype = d
-            L.or_blsm_parallel.argtypes = [i, i, i, p, p, i, p, d, d, d, i64, i,
-                                           p, p, p, i, p]
+            L.or_blsm_parallel.argtypes = [i, i, i, p, p, i, p, p, d, i64, i64, d,
+                                           i, p, p, p, i, p]
             L.or_blsm_parallel.restype = i
-            L.or_blsm_heap.argtypes = [i, i, i, p, p, i, p, d, d, d, i64, i64,
-                                       p, i, p]
+            L.or_blsm_heap.argtypes = [i, i, i, p, p, i, p, p, d, i64, i64, d,
+                                       i64, p, i, p]
             L.or_blsm_heap.restype = i64
             L.or_init_tight.argtypes = [i, i, i, d, p, i, p, p, p]
             L.or_init_tight_at.argtypes = [i64, p, i, i, i, d, p, i, p, p, p, p]
@@ -109,12 +110,15 @@ def _c64(a):
 def params(**kw):
     """Model parameters: Table 1 (T, rho_w, gamma0, eps_m, eps_w) plus the
     discretisation choices of this implementation.  `gauss_sigma` None means
-    2 h; `eps_ss` is the dielectric constant of the solute-solute Coulomb
+    2 h; `kernel` is "gauss" (separable truncated Gaussian) or "sin2" (the
+    paper's sin^2 kernel with radius sin2_lambda sqrt(h), Sec. 3.1); `eps_ss`
+    is the dielectric constant of the solute-solute Coulomb
     term (the paper writes eps_w in Eq. Gss and eps_m in the appendix; eps_m
     is the default here)."""
     p = dict(gamma0=0.174, rho_w=0.0333, eps_m=1.0, eps_w=80.0,
              temperature=298.0, eps_ss=None, gauss_sigma=None, trunc_r=6,
-             rmin=0.2, far_field=True, far_nuv=16, far_nt=8)
+             rmin=0.2, far_field=True, far_nuv=16, far_nt=8,
+             kernel="gauss", sin2_lambda=2.0)
     p.update(kw)
     if p["eps_ss"] is None:
         p["eps_ss"] = p["eps_m"]
@@ -162,24 +166,73 @@ def surface_kernel(sigma_over_h: float, r: int):
     return q.astype(np.int32)
 
 
-def surface_constants(sysd, p):
-    """c (energy per unit of sum chi (1-w)), g0 (self weight), D^3, q.
+SIN2_BITS = 16   # integer sin^2 weights: round(2^16 K)
 
-    c follows from asking a grid-aligned flat interface to cost exactly
-    gamma0 per unit area: per column of cross-section h^2 the plane gives
-    sum_{a>0} a q_a / 256 of kernel mass, so c = gamma0 h^2 256 / S1 with
-    S1 = sum_{a>0} a q_a (the role of C0 h^4 / lambda^4 in Eq. 4flip).
-    Evaluated as ((gamma0 * h) * h * 256) / S1."""
+
+def sin2_c0():
+    """C0 of Sec. 3.1 for K(y) = sin^2(pi |y|) on the unit ball:
+    1 / int_0^1 int_{B(0,1), y3 > s} K(y) dy ds.  The inner double integral
+    is int_{y3 > 0} K(|y|) y3 dy = pi int_0^1 sin^2(pi t) t^3 dt
+    = pi (pi^2 - 3) / (8 pi^2), so C0 = 8 pi / (pi^2 - 3)."""
+    return 8.0 * math.pi / (math.pi * math.pi - 3.0)
+
+
+def sin2_kernel(h: float, lam: float, bits: int = SIN2_BITS):
+    """Integer stencil of the sin^2 kernel (Sec. 3.1): offsets d = (a,b,c)
+    with rho = h |d| <= delta = lam sqrt(h) get round(2^bits sin^2(pi rho /
+    delta)), the others 0.  Returns (k3 of shape (2R+1)^3, R), R = the largest
+    integer with R h <= delta."""
+    delta = lam * math.sqrt(h)
+    R = int(math.floor(delta / h))
+    w = 2 * R + 1
+    k3 = np.zeros((w, w, w), np.int64)
+    for a in range(-R, R + 1):
+        for b in range(-R, R + 1):
+            for c in range(-R, R + 1):
+                rho = h * math.sqrt(float(a * a + b * b + c * c))
+                if rho <= delta:
+                    v = math.sin(math.pi * rho / delta)
+                    k3[a + R, b + R, c + R] = int(round(float(1 << bits) * (v * v)))
+    return k3, R
+
+
+def surface_constants(sysd, p):
+    """Constants of the surface term E_s = c_N sum_j chi_j (S - W_j), W = the
+    integer kernel convolution of chi, S = sum of all kernel weights:
+
+    * "gauss": g(a,b,c) = q_a q_b q_c / 256^3, S = D^3 = 256^3, c = c_N S.
+      c follows from asking a grid-aligned flat interface to cost exactly
+      gamma0 per unit area: per column of cross-section h^2 the plane gives
+      sum_{a>0} a q_a / 256 of kernel mass, so c = gamma0 h^2 256 / S1 with
+      S1 = sum_{a>0} a q_a (the role of C0 h^4 / lambda^4 in Eq. 4flip).
+      Evaluated as ((gamma0 * h) * h * 256) / S1.
+    * "sin2": the paper's double sum gamma0 C0 h^4 / lambda^4 sum_{j in m}
+      sum_{k in w} K_jk (Sec. 3.1) with K_jk = k3 / 2^16, so
+      c_N = gamma0 C0 h^4 / (lambda^4 2^16), evaluated as
+      ((gamma0 * C0) * h^4) / (lambda^4 * 2^16).
+
+    g0 = k0 / S is the kernel's centre weight (0 for sin^2)."""
     h = sysd["h"]
+    h3 = h * h * h
+    if p.get("kernel", "gauss") == "sin2":
+        lam = float(p["sin2_lambda"])
+        k3, R = sin2_kernel(h, lam)
+        S = int(k3.sum())
+        k0 = int(k3[R, R, R])
+        h4 = h * h * h * h
+        cN = ((p["gamma0"] * sin2_c0()) * h4) / (lam * lam * lam * lam * float(1 << SIN2_BITS))
+        return dict(kind="sin2", cN=cN, S=S, k0=k0, k3=k3, q=None, r=R, h3=h3,
+                    c=cN * S, g0=k0 / S, D3=S, lam=lam)
     sig = p["gauss_sigma"] if p["gauss_sigma"] is not None else 2.0 * h
     r = int(p["trunc_r"])
     q = surface_kernel(sig / h, r)
     S1 = int(sum(a * int(q[r + a]) for a in range(1, r + 1)))
     c = p["gamma0"] * h * h * 256.0 / float(S1)
     D3 = 256 ** 3
-    g0 = float(int(q[r]) ** 3) / float(D3)
-    h3 = h * h * h
-    return dict(c=c, g0=g0, D3=D3, q=q, r=r, h3=h3, S1=S1)
+    k0 = int(q[r]) ** 3
+    g0 = float(k0) / float(D3)
+    return dict(kind="gauss", c=c, g0=g0, D3=D3, q=q, r=r, h3=h3, S1=S1,
+                cN=c / D3, S=D3, k0=k0, k3=None)
 
 
 # ----------------------------------------------------------------- fields
@@ -324,24 +377,53 @@ def conv(chi, q):
     return W
 
 
+def conv3(chi, k3):
+    """W = sum over the full integer stencil k3 ((2R+1)^3), exact int64,
+    zero padding."""
+    chi = np.ascontiguousarray(chi, np.uint8)
+    n = chi.shape
+    W = np.zeros(n, np.int64)
+    k3 = np.ascontiguousarray(k3, np.int64)
+    R = (k3.shape[0] - 1) // 2
+    lib().or_conv3(n[0], n[1], n[2], _p(chi), R, _p(k3), _p(W))
+    return W
+
+
+def conv_kernel(chi, sc):
+    """W of the kernel that sc describes (separable Gaussian or stencil)."""
+    return conv(chi, sc["q"]) if sc["k3"] is None else conv3(chi, sc["k3"])
+
+
+def _karrays(sc):
+    """(qw, k3) arrays for the C routines: exactly one is not None.  The
+    caller keeps them alive across the call."""
+    if sc["k3"] is None:
+        return np.ascontiguousarray(sc["q"], np.int32), None
+    return None, np.ascontiguousarray(sc["k3"], np.int64)
+
+
+def _pp(a):
+    return None if a is None else _p(a)
+
+
 def surface_energy(chi, sc):
-    W = conv(chi, sc["q"])
+    W = conv_kernel(chi, sc)
     s = lib().or_surface_sum(chi.size, _p(np.ascontiguousarray(chi)), _p(W),
-                             sc["D3"])
-    return sc["c"] * (s / sc["D3"]), W
+                             sc["S"])
+    return sc["cN"] * s, W
 
 
 def delta_e(chi, U, sc, W=None):
     """dE (Eq. dGj1/dGj2) and the candidate mask."""
     chi = np.ascontiguousarray(chi, np.uint8)
     if W is None:
-        W = conv(chi, sc["q"])
+        W = conv_kernel(chi, sc)
     U = _c64(U)
     n = chi.shape
     dE = np.zeros(n)
     cand = np.zeros(n, np.uint8)
-    lib().or_delta_e(n[0], n[1], n[2], _p(chi), _p(W), _p(U), sc["c"],
-                     sc["g0"], sc["h3"], sc["D3"], _p(dE), _p(cand))
+    lib().or_delta_e(n[0], n[1], n[2], _p(chi), _p(W), _p(U), sc["cN"],
+                     sc["S"], sc["k0"], sc["h3"], _p(dE), _p(cand))
     return dE, cand
 
 
@@ -362,8 +444,9 @@ def flip_energy_total(chi, U, sc):
     """c sum chi (1 - w) + h^3 sum_{solvent} U (Eq. 4flip, first two terms)."""
     chi = np.ascontiguousarray(chi, np.uint8)
     n = chi.shape
+    qw, k3 = _karrays(sc)
     return lib().or_energy(n[0], n[1], n[2], _p(chi), _p(_c64(U)), sc["r"],
-                           _p(sc["q"]), sc["c"], sc["h3"], sc["D3"])
+                           _pp(qw), _pp(k3), sc["cN"], sc["S"], sc["h3"])
 
 
 def blsm_parallel(chi, U, sc, max_rounds=100000, verify=False,
@@ -376,9 +459,11 @@ def blsm_parallel(chi, U, sc, max_rounds=100000, verify=False,
     dsum = C.c_double(0.0)
     verr = C.c_double(0.0)
     rf = np.zeros(max_rounds if record_rounds else 1, np.int64)
+    qw, k3 = _karrays(sc)
+    U64 = _c64(U)
     rounds = lib().or_blsm_parallel(
-        n[0], n[1], n[2], _p(chi_c), _p(_c64(U)), sc["r"], _p(sc["q"]),
-        sc["c"], sc["g0"], sc["h3"], sc["D3"], max_rounds, C.byref(flips),
+        n[0], n[1], n[2], _p(chi_c), _p(U64), sc["r"], _pp(qw), _pp(k3),
+        sc["cN"], sc["S"], sc["k0"], sc["h3"], max_rounds, C.byref(flips),
         C.byref(dsum), _p(rf) if record_rounds else None, int(verify),
         C.byref(verr))
     if chi_c is not chi:
@@ -396,9 +481,11 @@ def blsm_heap(chi, U, sc, max_flips=1 << 40, verify=False):
     n = chi_c.shape
     dsum = C.c_double(0.0)
     verr = C.c_double(0.0)
-    flips = lib().or_blsm_heap(n[0], n[1], n[2], _p(chi_c), _p(_c64(U)),
-                               sc["r"], _p(sc["q"]), sc["c"], sc["g0"],
-                               sc["h3"], sc["D3"], max_flips, C.byref(dsum),
+    qw, k3 = _karrays(sc)
+    U64 = _c64(U)
+    flips = lib().or_blsm_heap(n[0], n[1], n[2], _p(chi_c), _p(U64),
+                               sc["r"], _pp(qw), _pp(k3), sc["cN"], sc["S"], sc["k0"],
+                               sc["h3"], max_flips, C.byref(dsum),
                                int(verify), C.byref(verr))
     if chi_c is not chi:
         chi[...] = chi_c

@@ -266,13 +266,49 @@ void or_conv(int nx, int ny, int nz, const uint8_t *chi, int r, const int *qw,
     free(t2);
 }
 
-/* sum_j chi_j (D^3 - W_j), exact.  E_s = c * this / D^3. */
+/* Direct 3-D convolution with a full integer stencil k3 of (2r+1)^3
+ * weights (offset (a,b,c) at ((a+r)(2r+1) + b+r)(2r+1) + c+r), zero
+ * padding: the sin^2 kernel of Sec. 3.1 is not a product of 1-D factors. */
+void or_conv3(int nx, int ny, int nz, const uint8_t *chi, int r, const int64_t *k3,
+              int64_t *W)
+{
+    const int w = 2 * r + 1;
+#pragma omp parallel for collapse(2)
+    for (int i = 0; i < nx; ++i)
+        for (int j = 0; j < ny; ++j)
+            for (int k = 0; k < nz; ++k) {
+                int64_t s = 0;
+                for (int a = -r; a <= r; ++a) {
+                    if (i + a < 0 || i + a >= nx) continue;
+                    for (int b = -r; b <= r; ++b) {
+                        if (j + b < 0 || j + b >= ny) continue;
+                        for (int c = -r; c <= r; ++c) {
+                            if (k + c < 0 || k + c >= nz) continue;
+                            s += k3[((a + r) * w + (b + r)) * w + (c + r)] *
+                                 chi[IDX(i + a, j + b, k + c)];
+                        }
+                    }
+                }
+                W[IDX(i, j, k)] = s;
+            }
+}
+
+/* W of either kernel: the 1-D factors qw when k3 is NULL, else the stencil. */
+static void conv_any(int nx, int ny, int nz, const uint8_t *chi, int r, const int *qw,
+                     const int64_t *k3, int64_t *W)
+{
+    if (k3) or_conv3(nx, ny, nz, chi, r, k3, W);
+    else or_conv(nx, ny, nz, chi, r, qw, W);
+}
+
+/* sum_j chi_j (S - W_j), exact; S = sum of all kernel weights (D^3 for the
+ * product kernel).  E_s = c_N * this. */
 int64_t or_surface_sum(int64_t G, const uint8_t *chi, const int64_t *W,
-                       int64_t D3)
+                       int64_t S)
 {
     int64_t s = 0;
     for (int64_t p = 0; p < G; ++p)
-        if (chi[p]) s += D3 - W[p];
+        if (chi[p]) s += S - W[p];
     return s;
 }
 
@@ -295,33 +331,35 @@ static int is_candidate(int nx, int ny, int nz, const uint8_t *chi, int i,
 
 /* Energy change of flipping cell j (Eq. dGj1 / dGj2 with the h^3 of the
  * centre-point rule restored):  with s = +1 for solvent -> solute and -1
- * for solute -> solvent,
- *   dE = c [ s (1 - 2 w_j) - g0 ] - s h^3 U_j,    g0 = q0^3 / D^3.
- * Evaluated in exactly this order: a = s (1 - 2w) - g0 is exact; then
- * c*a and h3*U are rounded products and the difference is rounded once. */
-static double flip_energy(uint8_t chi_j, int64_t Wj, double U, double c,
-                          double g0, double h3, double invD3)
+ * for solute -> solvent, w_j = W_j / S and g0 = k0 / S (k0 the kernel's
+ * centre weight),
+ *   dE = c [ s (1 - 2 w_j) - g0 ] - s h^3 U_j.
+ * With c_N = c / S the bracket times c is c_N N for the exact integer
+ * N = s (S - 2 W_j) - k0, so dE = c_N N - s h^3 U: one rounded product for
+ * each term and one rounded difference.  (For the Gaussian, S = 2^24 and
+ * every step of c [s (1 - 2w) - g0] before the product with c is exact, so
+ * the two forms agree bit for bit.) */
+static double flip_energy(uint8_t chi_j, int64_t Wj, double U, double cN, int64_t S,
+                          int64_t k0, double h3)
 {
-    double w = (double)Wj * invD3;
     double s = chi_j ? -1.0 : 1.0;
-    double a = s * (1.0 - 2.0 * w) - g0;
-    double t1 = c * a;
+    int64_t N = (chi_j ? -(S - 2 * Wj) : (S - 2 * Wj)) - k0;
+    double t1 = cN * (double)N;
     double t2 = h3 * U;
     return t1 - s * t2;
 }
 
 void or_delta_e(int nx, int ny, int nz, const uint8_t *chi, const int64_t *W,
-                const double *U, double c, double g0, double h3, int64_t D3,
+                const double *U, double cN, int64_t S, int64_t k0, double h3,
                 double *dE, uint8_t *cand)
 {
-    double invD3 = 1.0 / (double)D3;
 #pragma omp parallel for collapse(2)
     for (int i = 0; i < nx; ++i)
         for (int j = 0; j < ny; ++j)
             for (int k = 0; k < nz; ++k) {
                 int64_t p = IDX(i, j, k);
                 cand[p] = (uint8_t)is_candidate(nx, ny, nz, chi, i, j, k);
-                dE[p] = cand[p] ? flip_energy(chi[p], W[p], U[p], c, g0, h3, invD3) : 0.0;
+                dE[p] = cand[p] ? flip_energy(chi[p], W[p], U[p], cN, S, k0, h3) : 0.0;
             }
 }
 
@@ -449,26 +487,27 @@ int64_t or_select_cells(int nx, int ny, int nz, const uint8_t *cand,
 }
 
 /* Total of the interface-dependent energy of Eq. (4flip):
- * c sum chi (1 - w) + h^3 sum_{solvent} U.  Used by the exactness checks. */
+ * c_N sum chi (S - W) + h^3 sum_{solvent} U.  Used by the exactness checks. */
 static double energy_now(int nx, int ny, int nz, const uint8_t *chi,
-                         const double *U, int r, const int *qw, double c,
-                         double h3, int64_t D3, int64_t *Wtmp)
+                         const double *U, int r, const int *qw, const int64_t *k3,
+                         double cN, int64_t S, double h3, int64_t *Wtmp)
 {
     int64_t G = (int64_t)nx * ny * nz;
-    or_conv(nx, ny, nz, chi, r, qw, Wtmp);
-    int64_t s = or_surface_sum(G, chi, Wtmp, D3);
+    conv_any(nx, ny, nz, chi, r, qw, k3, Wtmp);
+    int64_t s = or_surface_sum(G, chi, Wtmp, S);
     double v = 0.0;
     for (int64_t p = 0; p < G; ++p)
         if (!chi[p]) v += U[p];
-    return c * ((double)s / (double)D3) + h3 * v;
+    return cN * (double)s + h3 * v;
 }
 
 double or_energy(int nx, int ny, int nz, const uint8_t *chi, const double *U,
-                 int r, const int *qw, double c, double h3, int64_t D3)
+                 int r, const int *qw, const int64_t *k3, double cN, int64_t S,
+                 double h3)
 {
     int64_t G = (int64_t)nx * ny * nz;
     int64_t *W = (int64_t *)malloc(sizeof(int64_t) * G);
-    double e = energy_now(nx, ny, nz, chi, U, r, qw, c, h3, D3, W);
+    double e = energy_now(nx, ny, nz, chi, U, r, qw, k3, cN, S, h3, W);
     free(W);
     return e;
 }
@@ -479,8 +518,8 @@ double or_energy(int nx, int ny, int nz, const uint8_t *chi, const double *U,
  * energy is recomputed from scratch around every round and the largest
  * |(E_after - E_before) - sum dE| is returned in *verify_err. */
 int or_blsm_parallel(int nx, int ny, int nz, uint8_t *chi, const double *U,
-                     int r, const int *qw, double c, double g0, double h3,
-                     int64_t D3, int max_rounds, int64_t *flips_out,
+                     int r, const int *qw, const int64_t *k3, double cN, int64_t S,
+                     int64_t k0, double h3, int max_rounds, int64_t *flips_out,
                      double *dEsum_out, int64_t *round_flips, int verify,
                      double *verify_err)
 {
@@ -495,11 +534,11 @@ int or_blsm_parallel(int nx, int ny, int nz, uint8_t *chi, const double *U,
     int64_t flips = 0;
     double dsum = 0.0, verr = 0.0;
     while (rounds < max_rounds) {
-        or_conv(nx, ny, nz, chi, r, qw, W);
-        or_delta_e(nx, ny, nz, chi, W, U, c, g0, h3, D3, dE, cand);
+        conv_any(nx, ny, nz, chi, r, qw, k3, W);
+        or_delta_e(nx, ny, nz, chi, W, U, cN, S, k0, h3, dE, cand);
         int64_t n = or_select(nx, ny, nz, cand, dE, r, sel, keys);
         if (n == 0) break;
-        double e0 = verify ? energy_now(nx, ny, nz, chi, U, r, qw, c, h3, D3, Wt) : 0.0;
+        double e0 = verify ? energy_now(nx, ny, nz, chi, U, r, qw, k3, cN, S, h3, Wt) : 0.0;
         double rs = 0.0;
         for (int64_t p = 0; p < G; ++p)
             if (sel[p]) {
@@ -507,7 +546,7 @@ int or_blsm_parallel(int nx, int ny, int nz, uint8_t *chi, const double *U,
                 rs += dE[p];
             }
         if (verify) {
-            double e1 = energy_now(nx, ny, nz, chi, U, r, qw, c, h3, D3, Wt);
+            double e1 = energy_now(nx, ny, nz, chi, U, r, qw, k3, cN, S, h3, Wt);
             double err = fabs((e1 - e0) - rs);
             if (err > verr) verr = err;
         }
@@ -566,29 +605,29 @@ static hent hpop(hent *h, int64_t *n)
 }
 
 int64_t or_blsm_heap(int nx, int ny, int nz, uint8_t *chi, const double *U,
-                     int r, const int *qw, double c, double g0, double h3,
-                     int64_t D3, int64_t max_flips, double *dEsum_out,
+                     int r, const int *qw, const int64_t *k3, double cN, int64_t S,
+                     int64_t k0, double h3, int64_t max_flips, double *dEsum_out,
                      int verify, double *verify_err)
 {
     int64_t G = (int64_t)nx * ny * nz;
-    double invD3 = 1.0 / (double)D3;
+    const int wd = 2 * r + 1;
     int64_t *W = (int64_t *)malloc(sizeof(int64_t) * G);
     int64_t *Wt = verify ? (int64_t *)malloc(sizeof(int64_t) * G) : NULL;
     uint32_t *ver = (uint32_t *)calloc(G, sizeof(uint32_t));
     int64_t cap = 4 * G + 1024, hn = 0;
     hent *heap = (hent *)malloc(sizeof(hent) * cap);
-    or_conv(nx, ny, nz, chi, r, qw, W);
+    conv_any(nx, ny, nz, chi, r, qw, k3, W);
     for (int i = 0; i < nx; ++i)
         for (int j = 0; j < ny; ++j)
             for (int k = 0; k < nz; ++k) {
                 int64_t p = IDX(i, j, k);
                 if (!is_candidate(nx, ny, nz, chi, i, j, k)) continue;
-                double e = flip_energy(chi[p], W[p], U[p], c, g0, h3, invD3);
+                double e = flip_energy(chi[p], W[p], U[p], cN, S, k0, h3);
                 if (e < 0.0) hpush(heap, &hn, (hent){e, p, ver[p]});
             }
     int64_t flips = 0;
     double dsum = 0.0, verr = 0.0;
-    double ecur = verify ? energy_now(nx, ny, nz, chi, U, r, qw, c, h3, D3, Wt) : 0.0;
+    double ecur = verify ? energy_now(nx, ny, nz, chi, U, r, qw, k3, cN, S, h3, Wt) : 0.0;
     while (hn > 0 && flips < max_flips) {
         hent t = hpop(heap, &hn);
         if (t.v != ver[t.p]) continue;          /* stale entry */
@@ -605,7 +644,9 @@ int64_t or_blsm_heap(int nx, int ny, int nz, uint8_t *chi, const double *U,
                 for (int d = -r; d <= r; ++d) {
                     int ii = i + a, jj = j + b, kk = k + d;
                     if (ii < 0 || ii >= nx || jj < 0 || jj >= ny || kk < 0 || kk >= nz) continue;
-                    W[IDX(ii, jj, kk)] += sgn * (int64_t)qw[a + r] * qw[b + r] * qw[d + r];
+                    const int64_t kw = k3 ? k3[((a + r) * wd + (b + r)) * wd + (d + r)]
+                                          : (int64_t)qw[a + r] * qw[b + r] * qw[d + r];
+                    W[IDX(ii, jj, kk)] += sgn * kw;
                 }
         for (int a = -r; a <= r; ++a)
             for (int b = -r; b <= r; ++b)
@@ -615,7 +656,7 @@ int64_t or_blsm_heap(int nx, int ny, int nz, uint8_t *chi, const double *U,
                     int64_t q = IDX(ii, jj, kk);
                     ver[q]++;
                     if (!is_candidate(nx, ny, nz, chi, ii, jj, kk)) continue;
-                    double e = flip_energy(chi[q], W[q], U[q], c, g0, h3, invD3);
+                    double e = flip_energy(chi[q], W[q], U[q], cN, S, k0, h3);
                     if (e < 0.0) {
                         if (hn >= cap) {
                             cap *= 2;
@@ -625,7 +666,7 @@ int64_t or_blsm_heap(int nx, int ny, int nz, uint8_t *chi, const double *U,
                     }
                 }
         if (verify) {
-            double e1 = energy_now(nx, ny, nz, chi, U, r, qw, c, h3, D3, Wt);
+            double e1 = energy_now(nx, ny, nz, chi, U, r, qw, k3, cN, S, h3, Wt);
             double err = fabs((e1 - ecur) - t.e);
             if (err > verr) verr = err;
             ecur = e1;

@@ -344,8 +344,9 @@ def test_parallel_rule_small_kernel_radius():
     U = U - 0.05
     q = O.surface_kernel(1.0, 2)
     S1 = int(sum(a * int(q[2 + a]) for a in range(1, 3)))
-    sc = dict(sc, q=q, r=2, S1=S1, c=0.174 * 0.3 * 0.3 * 256.0 / S1,
-              g0=float(int(q[2]) ** 3) / float(256 ** 3))
+    c = 0.174 * 0.3 * 0.3 * 256.0 / S1
+    sc = dict(sc, q=q, r=2, S1=S1, c=c, g0=float(int(q[2]) ** 3) / float(256 ** 3),
+              cN=c / 256 ** 3, k0=int(q[2]) ** 3)
     sel, keys, dE, cand = O.select(chi, U, sc)
     idx = np.argwhere(sel == 1)
     assert len(idx) > 0
@@ -581,3 +582,127 @@ def test_two_atom_molecule_reaches_paper_state():
     assert all(b <= a for a, b in zip(Ms, Ms[1:]))
     for h in r["history"]:
         assert h["G"] - h["G_old"] <= 0.05 * abs(h["G_old"]) + 1e-12
+
+
+# ------------------------------------------------- the paper's sin^2 kernel
+
+def test_sin2_c0_from_its_definition():
+    # C0 = 1 / int_0^1 int_{B(0,1), y3 > s} sin^2(pi |y|) dy ds (Sec. 3.1):
+    # at radius rho the cap {y3 > s} of the sphere has area 2 pi rho (rho - s)
+    from scipy import integrate
+    val, _ = integrate.dblquad(
+        lambda rho, s: math.sin(math.pi * rho) ** 2 * 2 * math.pi * rho * (rho - s),
+        0.0, 1.0, lambda s: s, lambda s: 1.0, epsabs=1e-13, epsrel=1e-13)
+    assert O.sin2_c0() == pytest.approx(1.0 / val, rel=1e-10)
+
+
+def test_sin2_stencil_values_and_symmetry():
+    # h = 0.25, lambda = 2: delta = 1 A, R = 4; rho = 0.5 A gives sin^2(pi/2)
+    k3, R = O.sin2_kernel(0.25, 2.0)
+    assert R == 4 and k3.shape == (9, 9, 9)
+    c = R
+    assert k3[c, c, c] == 0                           # K(0) = sin^2(0)
+    for d in (1, 3):
+        assert k3[c + d, c, c] == 32768               # sin^2(pi/4), sin^2(3pi/4)
+    assert k3[c + 2, c, c] == 65536                   # sin^2(pi/2)
+    assert k3[c + 4, c, c] == 0                       # rho = delta: sin^2(pi)
+    idx = np.indices(k3.shape).reshape(3, -1).T - R
+    outside = (idx ** 2).sum(1) * 0.25 ** 2 > 1.0 + 1e-12
+    assert np.all(k3.reshape(-1)[outside] == 0)
+    for perm in ((0, 1, 2), (1, 0, 2), (2, 1, 0), (0, 2, 1)):
+        assert np.array_equal(k3, np.transpose(k3, perm))
+    assert np.array_equal(k3, k3[::-1, :, :]) and np.array_equal(k3, k3[:, ::-1, ::-1])
+
+
+def _sin2_plane_ratio(h, lam=2.0):
+    p = O.params(kernel="sin2", sin2_lambda=lam)
+    sc = O.surface_constants(dict(h=h), p)
+    R = sc["r"]
+    nx, ny = 4 * R + 4, 2 * R + 3
+    chi = np.zeros((nx, ny, ny), np.uint8)
+    chi[: nx // 2] = 1
+    W = O.conv3(chi, sc["k3"])
+    j = ny // 2
+    # solute cells at least R + 1 from the x = 0 face see only the plane
+    inner = sum(int(sc["S"] - W[i, j, j]) for i in range(R + 1, nx // 2))
+    return sc["cN"] * inner / (h * h) / p["gamma0"]
+
+
+def test_sin2_flat_interface_costs_gamma0_to_order_h():
+    # a grid-aligned plane costs gamma0 per unit area up to the O(h) error
+    # of the discretisation (Sec. 3.1): the error shrinks as h does
+    ratios = [_sin2_plane_ratio(h) for h in (0.25, 0.125, 0.0625)]
+    errs = [1.0 - x for x in ratios]
+    assert all(e > 0 for e in errs)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.01
+
+
+def test_sin2_sphere_area():
+    p = O.params(kernel="sin2", sin2_lambda=2.0)
+    h, Rs = 0.125, 3.0
+    n = int(2 * (Rs + 1.5) / h)
+    s = synth.single_ion(n=n, h=h)
+    sc = O.surface_constants(s, p)
+    P = O.grid_positions(s)
+    chi = (np.sqrt((P ** 2).sum(-1)) < Rs).astype(np.uint8)
+    es, _ = O.surface_energy(chi, sc)
+    Req = (3 * chi.sum() * sc["h3"] / (4 * math.pi)) ** (1 / 3)
+    assert es == pytest.approx(4 * math.pi * Req ** 2 * p["gamma0"], rel=0.03)
+
+
+def _sin2_energy_pairs(chi, U, sc):
+    # the paper's double sum, pair by pair: c_N sum_{j solute} sum_{k solvent
+    # or outside the box, within the stencil} k3[k - j] + h^3 sum_solvent U
+    n = chi.shape
+    R = sc["r"]
+    k3 = sc["k3"]
+    offs = [(a, b, c) for a in range(-R, R + 1) for b in range(-R, R + 1)
+            for c in range(-R, R + 1) if k3[a + R, b + R, c + R] != 0]
+    tot = 0
+    for j in zip(*np.nonzero(chi)):
+        for (a, b, c) in offs:
+            i2, j2, k2 = j[0] + a, j[1] + b, j[2] + c
+            out = not (0 <= i2 < n[0] and 0 <= j2 < n[1] and 0 <= k2 < n[2])
+            if out or chi[i2, j2, k2] == 0:
+                tot += int(k3[a + R, b + R, c + R])
+    return sc["cN"] * tot + sc["h3"] * float(U[chi == 0].sum())
+
+
+def _sin2_small_case(seed, n=(7, 8, 6)):
+    s = synth.single_ion(n=8, h=0.25)
+    s["n"] = np.array(n)
+    sc = O.surface_constants(s, O.params(kernel="sin2", sin2_lambda=2.0))
+    rng = np.random.default_rng(seed)
+    chi = (rng.random(n) < 0.5).astype(np.uint8)
+    U = 0.2 * rng.normal(size=n)
+    return sc, chi, U
+
+
+def test_sin2_flip_energies_are_exact_energy_differences():
+    sc, chi, U = _sin2_small_case(3)
+    assert sc["k0"] == 0 and sc["r"] == 4
+    assert O.flip_energy_total(chi, U, sc) == pytest.approx(
+        _sin2_energy_pairs(chi, U, sc), rel=1e-12)
+    dE, cand = O.delta_e(chi, U, sc)
+    e0 = _sin2_energy_pairs(chi, U, sc)
+    for idx in zip(*np.nonzero(cand)):
+        c2 = chi.copy()
+        c2[idx] ^= 1
+        assert dE[idx] == pytest.approx(_sin2_energy_pairs(c2, U, sc) - e0,
+                                        abs=1e-12 * max(1.0, abs(e0)))
+
+
+def test_sin2_parallel_rule_and_heap_exact():
+    sc, chi, U = _sin2_small_case(4, n=(12, 13, 11))
+    U = U - 0.05
+    c1 = chi.copy()
+    res = O.blsm_parallel(c1, U, sc, verify=True, record_rounds=True)
+    assert res["rounds"] > 0 and res["verify_err"] < 1e-12
+    dE, cand = O.delta_e(c1, U, sc)
+    assert np.all(dE[cand == 1] >= 0)
+    c2 = chi.copy()
+    res = O.blsm_heap(c2, U, sc, verify=True)
+    assert res["flips"] > 0 and res["verify_err"] < 1e-12
+    dE, cand = O.delta_e(c2, U, sc)
+    assert np.all(dE[cand == 1] >= 0)
