@@ -67,6 +67,12 @@ typedef struct {
     int far_field;       /* 1: include the integral outside the box */
     int far_nuv;         /* far-field Gauss points per face axis (16) */
     int far_nt;          /* far-field Gauss points along rays (8) */
+    int kernel;          /* surface kernel: 0 = separable truncated Gaussian
+                            (gauss_sigma, trunc_r); 1 = the paper's
+                            K = sin^2(pi |x| / delta) on |x| <= delta =
+                            sin2_lambda sqrt(h) (Sec. 3.1), integer weights
+                            round(2^16 K); delta / h must give 1..8 cells */
+    double sin2_lambda;  /* lambda of delta = lambda sqrt(h) (default 2) */
 } vesis_params;
 
 /* Algorithm constants of Step 1 (defaults: k_max = 3000, N*_cnt = 5,

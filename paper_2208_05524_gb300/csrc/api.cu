@@ -151,6 +151,9 @@ struct vesis_system_t {
     long long G = 0;
     KernelW kw{};
     FlipConst fc{};
+    int *d_k3 = nullptr;        // full stencil of the sin^2 kernel, or NULL
+    long long ksum = 0;         // sum of all kernel weights
+    double terms_c = 0, terms_D = 1;   // E_s = terms_c * sum chi (S - W) / terms_D
     double c = 0, g0 = 0, h3 = 0, cfa = 0, lB = 0, coul = 0;
     float rmin2 = 0.f;
     double centre[3]{}, lo[3]{}, hi[3]{};
@@ -364,9 +367,13 @@ void enq_ss(vesis_system s, const double *d_pos, double *bk)
 void enq_conv(vesis_system s, const uint8_t *chi, uint32_t *W)
 {
     const int sp = span_begin(s);
-    launch_conv_z(s->g, s->kw, chi, s->d_T1, s->st);
-    launch_conv_y(s->g, s->kw, s->d_T1, s->d_T2, s->st);
-    launch_conv_x(s->g, s->kw, s->d_T2, W, s->st);
+    if (s->d_k3) {
+        launch_conv3(s->g, s->kw.r, s->d_k3, chi, W, s->st);
+    } else {
+        launch_conv_z(s->g, s->kw, chi, s->d_T1, s->st);
+        launch_conv_y(s->g, s->kw, s->d_T1, s->d_T2, s->st);
+        launch_conv_x(s->g, s->kw, s->d_T2, W, s->st);
+    }
     span_end(s, sp, 3, s->G, 0);
 }
 
@@ -378,10 +385,10 @@ void enq_terms(vesis_system s, const uint8_t *chi, const float *U,
 {
     if (!w_current) enq_conv(s, chi, s->d_W);
     launch_terms(s->g, chi, s->d_W, U, E, E ? E + s->G : nullptr,
-                 E ? E + 2 * s->G : nullptr, (float)s->cfa, s->d_part_s,
-                 s->d_part_v, s->d_part_c, s->st);
+                 E ? E + 2 * s->G : nullptr, (float)s->cfa, (unsigned)s->ksum,
+                 s->d_part_s, s->d_part_v, s->d_part_c, s->st);
     launch_terms_final(s->d_part_s, s->d_part_v, s->d_part_c, s->nb_terms,
-                       s->c, 16777216.0, s->h3, bk, s->st);
+                       s->terms_c, s->terms_D, s->h3, bk, s->st);
     count_launch();
     k_total<<<1, 1, 0, s->st>>>(bk);
 }
@@ -393,7 +400,7 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
     // already); the sweep keeps it current with every flip
     if (!w_current) enq_conv(s, chi, s->d_W);
     const int sp = span_begin(s);
-    VCK(launch_sweep(s->g, s->kw, s->fc, chi, s->d_W, U, s->d_dE, s->d_sweep,
+    VCK(launch_sweep(s->g, s->kw, s->d_k3, s->fc, chi, s->d_W, U, s->d_dE, s->d_sweep,
                      s->d_ctl, s->d_err, s->d_part_flips,
                      s->d_part_dE, s->d_rounds, s->d_capped, max_rounds,
                      s->sweep_blocks, s->d_rs, s->st));
@@ -508,6 +515,8 @@ void vesis_default_params(vesis_params *p)
     p->far_field = 1;
     p->far_nuv = 16;
     p->far_nt = 8;
+    p->kernel = 0;
+    p->sin2_lambda = 2.0;
 }
 
 void vesis_default_relax_opts(vesis_relax_opts *o)
@@ -612,35 +621,78 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     s->coul = s->lB / p->eps_ss;
     s->rmin2 = (float)(p->r_min * p->r_min);
 
-    // surface kernel: integer Gaussian weights summing to 256
     const double h = p->h;
-    const double sig = p->gauss_sigma > 0.0 ? p->gauss_sigma : 2.0 * h;
-    const int r = p->trunc_r;
-    std::vector<double> gw(2 * r + 1);
-    double gs = 0.0;
-    for (int a = -r; a <= r; ++a) {
-        gw[a + r] = std::exp(-(double)(a * a) / (2.0 * (sig / h) * (sig / h)));
-        gs += gw[a + r];
-    }
-    int qsum = 0;
-    s->kw.r = r;
-    for (int a = -r; a <= r; ++a) {
-        if (a == 0) continue;
-        s->kw.q[a + r] = (int)std::nearbyint(256.0 * gw[a + r] / gs);
-        qsum += s->kw.q[a + r];
-    }
-    s->kw.q[r] = 256 - qsum;
-    if (s->kw.q[r] < 0) return fail(VESIS_E_ARG, "surface kernel weights exceed 256");
-    long long S1 = 0;
-    for (int a = 1; a <= r; ++a) S1 += (long long)a * s->kw.q[a + r];
-    if (S1 <= 0) return fail(VESIS_E_ARG, "surface kernel has no first moment");
-    s->c = p->gamma0 * h * h * 256.0 / (double)S1;
-    s->g0 = (double)((long long)s->kw.q[r] * s->kw.q[r] * s->kw.q[r]) / 16777216.0;
     s->h3 = h * h * h;
-    s->fc.c = s->c;
-    s->fc.g0 = s->g0;
-    s->fc.h3 = s->h3;
-    s->fc.invD3 = 1.0 / 16777216.0;
+    if (p->kernel == 1) {
+        // the paper's sin^2 kernel (Sec. 3.1): weights round(2^16 sin^2(pi
+        // rho / delta)) on the cells with rho = h |d| <= delta = lambda
+        // sqrt(h); E_s = gamma0 C0 h^4 / lambda^4 sum over solute-solvent
+        // pairs, C0 = 8 pi / (pi^2 - 3)
+        const double lam = p->sin2_lambda;
+        const double delta = lam * std::sqrt(h);
+        const int R = (int)std::floor(delta / h);
+        const int w = 2 * R + 1;
+        std::vector<int> k3((size_t)w * w * w, 0);
+        long long S = 0;
+        for (int a = -R; a <= R; ++a)
+            for (int b = -R; b <= R; ++b)
+                for (int c = -R; c <= R; ++c) {
+                    const double rho = h * std::sqrt((double)(a * a + b * b + c * c));
+                    if (rho <= delta) {
+                        const double v = std::sin(M_PI * rho / delta);
+                        const int q = (int)std::nearbyint(65536.0 * (v * v));
+                        k3[((size_t)(a + R) * w + (b + R)) * w + (c + R)] = q;
+                        S += q;
+                    }
+                }
+        const double C0 = 8.0 * M_PI / (M_PI * M_PI - 3.0);
+        const double h4 = h * h * h * h;
+        const double cN = ((p->gamma0 * C0) * h4) / (lam * lam * lam * lam * 65536.0);
+        s->kw.r = R;
+        s->ksum = S;
+        s->fc.cN = cN;
+        s->fc.h3 = s->h3;
+        s->fc.S = (int)S;
+        s->fc.k0 = k3[((size_t)R * w + R) * w + R];
+        s->c = cN * (double)S;
+        s->g0 = (double)s->fc.k0 / (double)S;
+        s->terms_c = cN;
+        s->terms_D = 1.0;
+        VTRY(dalloc(s, &s->d_k3, k3.size()));
+        VCK(cudaMemcpy(s->d_k3, k3.data(), k3.size() * sizeof(int), cudaMemcpyHostToDevice));
+    } else {
+        // separable Gaussian: integer 1-D weights summing to 256
+        const double sig = p->gauss_sigma > 0.0 ? p->gauss_sigma : 2.0 * h;
+        const int r = p->trunc_r;
+        std::vector<double> gw(2 * r + 1);
+        double gs = 0.0;
+        for (int a = -r; a <= r; ++a) {
+            gw[a + r] = std::exp(-(double)(a * a) / (2.0 * (sig / h) * (sig / h)));
+            gs += gw[a + r];
+        }
+        int qsum = 0;
+        s->kw.r = r;
+        for (int a = -r; a <= r; ++a) {
+            if (a == 0) continue;
+            s->kw.q[a + r] = (int)std::nearbyint(256.0 * gw[a + r] / gs);
+            qsum += s->kw.q[a + r];
+        }
+        s->kw.q[r] = 256 - qsum;
+        if (s->kw.q[r] < 0) return fail(VESIS_E_ARG, "surface kernel weights exceed 256");
+        long long S1 = 0;
+        for (int a = 1; a <= r; ++a) S1 += (long long)a * s->kw.q[a + r];
+        if (S1 <= 0) return fail(VESIS_E_ARG, "surface kernel has no first moment");
+        s->c = p->gamma0 * h * h * 256.0 / (double)S1;
+        const long long k0 = (long long)s->kw.q[r] * s->kw.q[r] * s->kw.q[r];
+        s->g0 = (double)k0 / 16777216.0;
+        s->ksum = 16777216;
+        s->fc.cN = s->c / 16777216.0;
+        s->fc.h3 = s->h3;
+        s->fc.S = 16777216;
+        s->fc.k0 = (int)k0;
+        s->terms_c = s->c;
+        s->terms_D = 16777216.0;
+    }
 
     // atom data
     s->sig_sw.assign(sigma_sw, sigma_sw + n);
@@ -777,12 +829,12 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VTRY(dalloc(s, &s->d_ss_gpart, (size_t)3 * n * s->ssplan.nchunk));
 
     {
-        const cudaError_t e = sweep_grid_size(s->nsm, r, &s->sweep_blocks);
+        const cudaError_t e = sweep_grid_size(s->nsm, s->kw.r, &s->sweep_blocks);
         if (e != cudaSuccess)
             return fail(VESIS_E_CUDA, std::string("sweep occupancy: ") + cudaGetErrorString(e));
     }
     s->ntiles = sweep_tiles(s->g);
-    VTRY(dalloc(s, &s->d_sweep, sweep_state_bytes(s->g, r)));
+    VTRY(dalloc(s, &s->d_sweep, sweep_state_bytes(s->g, s->kw.r)));
     VTRY(dalloc(s, &s->d_ctl, sweep_ctl_words()));
     VTRY(dalloc(s, &s->d_err, 1));
     VTRY(dalloc(s, &s->d_rounds, 1));
@@ -823,8 +875,16 @@ int vesis_init_system(const vesis_params *p, int n, const double *xyz,
     const long long G = (long long)p->nx * p->ny * p->nz;
     if (G > 2147483647LL) return fail(VESIS_E_ARG, "grid has more than 2^31-1 cells");
     if (!(p->h > 0.0)) return fail(VESIS_E_ARG, "h must be > 0");
-    if (p->trunc_r < 1 || p->trunc_r > kMaxR)
+    if (p->kernel != 0 && p->kernel != 1) return fail(VESIS_E_ARG, "kernel must be 0 or 1");
+    if (p->kernel == 0 && (p->trunc_r < 1 || p->trunc_r > kMaxR))
         return fail(VESIS_E_ARG, "trunc_r must be in 1..8");
+    if (p->kernel == 1) {
+        if (!(p->sin2_lambda > 0.0)) return fail(VESIS_E_ARG, "sin2_lambda must be > 0");
+        const double cells = p->sin2_lambda * std::sqrt(p->h) / p->h;
+        if (!(cells >= 1.0 && cells < (double)(kMaxR + 1)))
+            return fail(VESIS_E_ARG,
+                        "sin^2 kernel radius lambda sqrt(h) must span 1..8 cells of h");
+    }
     if (!(p->r_min > 0.0)) return fail(VESIS_E_ARG, "r_min must be > 0");
     if (!(p->temperature > 0.0) || !(p->eps_w > 0.0) || !(p->eps_m > 0.0) ||
         !(p->eps_ss > 0.0))

@@ -292,6 +292,102 @@ static void launch_walk(const Q17 &w, const TI *in, uint32_t *out, int n_axis, l
                                                                   nthreads, nchunk);
 }
 
+// Full 3-D stencil (the sin^2 kernel): the (2R+1)^3 weights sit in shared
+// memory.  Rows of whole 8-cell chunks (nz % 8 == 0, aligned): a thread
+// forms 8 sums along z; for each (a, b) row offset it loads the chunk and
+// its two neighbours as three 8-byte words and applies that row's 2R+1
+// weights (rows of all-zero weights are skipped, as are zero weights).
+constexpr int K3MAX = (2 * kMaxR + 1) * (2 * kMaxR + 1) * (2 * kMaxR + 1);
+
+__global__ void __launch_bounds__(CT)
+k_conv3_z8(int nx, int ny, int nz, int R, const int *__restrict__ k3,
+           const uint8_t *__restrict__ chi, uint32_t *__restrict__ W, unsigned nchunk)
+{
+    __shared__ int sk[K3MAX];
+    const int w = 2 * R + 1;
+    for (int e = threadIdx.x; e < w * w * w; e += CT) sk[e] = k3[e];
+    __syncthreads();
+    const unsigned t = blockIdx.x * CT + threadIdx.x;
+    if (t >= nchunk) return;
+    const unsigned cpr = (unsigned)nz / 8u;
+    const unsigned row = t / cpr;
+    const int k0 = (int)(t - row * cpr) * 8;
+    const int i = (int)(row / (unsigned)ny), j = (int)(row - (unsigned)i * (unsigned)ny);
+    unsigned acc[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (int a = -R; a <= R; ++a) {
+        const int ii = i + a;
+        if (ii < 0 || ii >= nx) continue;
+        for (int b = -R; b <= R; ++b) {
+            const int jj = j + b;
+            if (jj < 0 || jj >= ny) continue;
+            const int *wr = sk + ((a + R) * w + (b + R)) * w + R;   // wr[c], c = -R..R
+            bool any = false;
+            for (int c = -R; c <= R; ++c) any |= wr[c] != 0;
+            if (!any) continue;
+            const uint8_t *rp = chi + ((long long)ii * ny + jj) * nz;
+            const unsigned long long lo =
+                k0 >= 8 ? __ldg(reinterpret_cast<const unsigned long long *>(rp + k0 - 8)) : 0ull;
+            const unsigned long long mid =
+                __ldg(reinterpret_cast<const unsigned long long *>(rp + k0));
+            const unsigned long long hi =
+                k0 + 8 < nz ? __ldg(reinterpret_cast<const unsigned long long *>(rp + k0 + 8))
+                            : 0ull;
+            unsigned by[24];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                by[e] = (unsigned)(lo >> (8 * e)) & 0xffu;
+                by[8 + e] = (unsigned)(mid >> (8 * e)) & 0xffu;
+                by[16 + e] = (unsigned)(hi >> (8 * e)) & 0xffu;
+            }
+#pragma unroll
+            for (int m = 0; m <= 2 * kMaxR; ++m) {     // tap c = m - 8
+                const int c = m - kMaxR;
+                if (c < -R || c > R) continue;
+                const unsigned wt = (unsigned)wr[c];
+                if (wt == 0u) continue;
+#pragma unroll
+                for (int o = 0; o < 8; ++o) acc[o] += wt * by[o + m];   // cell k0 + o + c
+            }
+        }
+    }
+    uint32_t *dst = W + (long long)row * nz + k0;
+    reinterpret_cast<uint4 *>(dst)[0] = make_uint4(acc[0], acc[1], acc[2], acc[3]);
+    reinterpret_cast<uint4 *>(dst)[1] = make_uint4(acc[4], acc[5], acc[6], acc[7]);
+}
+
+// Any layout: one thread per cell.
+__global__ void __launch_bounds__(CT)
+k_conv3(GridDesc g, int R, const int *__restrict__ k3, const uint8_t *__restrict__ chi,
+        uint32_t *__restrict__ W)
+{
+    __shared__ int sk[K3MAX];
+    const int w = 2 * R + 1;
+    for (int e = threadIdx.x; e < w * w * w; e += CT) sk[e] = k3[e];
+    __syncthreads();
+    const long long nyz = (long long)g.ny * g.nz;
+    const long long G = nyz * g.nx;
+    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
+    if (p >= G) return;
+    const int i = (int)(p / nyz);
+    const long long rem = p - (long long)i * nyz;
+    const int j = (int)(rem / g.nz);
+    const int k = (int)(rem - (long long)j * g.nz);
+    unsigned s = 0u;
+    for (int a = -R; a <= R; ++a) {
+        if (i + a < 0 || i + a >= g.nx) continue;
+        for (int b = -R; b <= R; ++b) {
+            if (j + b < 0 || j + b >= g.ny) continue;
+            const int *wr = sk + ((a + R) * w + (b + R)) * w + R;
+            const uint8_t *rp = chi + ((long long)(i + a) * g.ny + (j + b)) * g.nz;
+            for (int c = -R; c <= R; ++c) {
+                if (k + c < 0 || k + c >= g.nz || wr[c] == 0) continue;
+                s += (unsigned)wr[c] * rp[k + c];
+            }
+        }
+    }
+    W[p] = s;
+}
+
 // Face neighbour with the other label; outside the box counts as solvent.
 __device__ __forceinline__ bool is_candidate(const GridDesc &g,
                                              const uint8_t *__restrict__ chi,
@@ -308,18 +404,18 @@ __device__ __forceinline__ bool is_candidate(const GridDesc &g,
     return (xm != c) | (xp != c) | (ym != c) | (yp != c) | (zm != c) | (zp != c);
 }
 
-// dE of Eq. (dGj1/dGj2) rounded exactly as written: a = s (1 - 2w) - g0 is
-// exact, then c*a and h3*U are rounded products and the difference is
-// rounded once (no contraction).
+// dE of Eq. (dGj1/dGj2): c [s (1 - 2w) - g0] - s h^3 U with w = W / S and
+// g0 = k0 / S is cN N - s h^3 U for the exact integer N = s (S - 2W) - k0
+// and cN = c / S; both products are rounded once and the sum once (no
+// contraction).
 __device__ __forceinline__ double flip_dE(uint8_t chi_j, unsigned W, float U,
                                           const FlipConst &fc)
 {
-    const double w = __dmul_rn((double)W, fc.invD3);
-    const double s = chi_j ? -1.0 : 1.0;
-    const double a = __dsub_rn(__dmul_rn(s, __dsub_rn(1.0, __dmul_rn(2.0, w))), fc.g0);
-    const double t1 = __dmul_rn(fc.c, a);
+    const int base = fc.S - 2 * (int)W;
+    const int N = (chi_j ? -base : base) - fc.k0;
+    const double t1 = __dmul_rn(fc.cN, (double)N);
     const double t2 = __dmul_rn(fc.h3, (double)U);
-    return __dsub_rn(t1, __dmul_rn(s, t2));
+    return __dadd_rn(t1, chi_j ? t2 : -t2);
 }
 
 __global__ void k_flip_energy(GridDesc g, const uint32_t *__restrict__ W,
@@ -351,7 +447,7 @@ __global__ void __launch_bounds__(CT)
 k_terms(GridDesc g, const uint8_t *__restrict__ chi, const uint32_t *__restrict__ W,
         const float *__restrict__ U, const float *__restrict__ Ex,
         const float *__restrict__ Ey, const float *__restrict__ Ez, float cfa,
-        long long *__restrict__ part_s, double *__restrict__ part_v,
+        unsigned ksum, long long *__restrict__ part_s, double *__restrict__ part_v,
         double *__restrict__ part_c)
 {
     __shared__ long long s_s[CT / 32], s_n[CT / 32];
@@ -362,7 +458,7 @@ k_terms(GridDesc g, const uint8_t *__restrict__ chi, const uint32_t *__restrict_
     const long long stride = (long long)gridDim.x * CT;
     for (long long p = (long long)blockIdx.x * CT + threadIdx.x; p < G; p += stride) {
         if (chi[p]) {
-            S += (long long)(16777216u - W[p]);
+            S += (long long)ksum - (long long)W[p];
             N += 1;
         } else {
             V += (double)U[p];
@@ -553,6 +649,19 @@ void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
     else
         launch_walk<1>(w, T2, W, g.nx, nyz, g.nz, g.ny, g.nz, st);
 }
+void launch_conv3(const GridDesc &g, int R, const int *k3, const uint8_t *chi,
+                  uint32_t *W, cudaStream_t st)
+{
+    const long long G = (long long)g.nx * g.ny * g.nz;
+    count_launch();
+    if (g.nz % 8 == 0 && (uintptr_t)chi % 8 == 0 && (uintptr_t)W % 16 == 0) {
+        const unsigned nchunk = (unsigned)(G / 8);
+        k_conv3_z8<<<(nchunk + CT - 1) / CT, CT, 0, st>>>(g.nx, g.ny, g.nz, R, k3, chi, W,
+                                                            nchunk);
+    } else {
+        k_conv3<<<cell_blocks(g), CT, 0, st>>>(g, R, k3, chi, W);
+    }
+}
 void launch_flip_energy(const GridDesc &g, const uint32_t *W,
                         const uint8_t *chi, const float *U, const FlipConst &fc,
                         double *dE, uint8_t *cand, cudaStream_t st)
@@ -562,12 +671,12 @@ void launch_flip_energy(const GridDesc &g, const uint32_t *W,
 }
 void launch_terms(const GridDesc &g, const uint8_t *chi, const uint32_t *W,
                   const float *U, const float *Ex, const float *Ey,
-                  const float *Ez, float cfa, long long *part_s,
+                  const float *Ez, float cfa, unsigned ksum, long long *part_s,
                   double *part_v, double *part_c, cudaStream_t st)
 {
     const long long G = (long long)g.nx * g.ny * g.nz;
     count_launch();
-    k_terms<<<terms_blocks(G), CT, 0, st>>>(g, chi, W, U, Ex, Ey, Ez, cfa,
+    k_terms<<<terms_blocks(G), CT, 0, st>>>(g, chi, W, U, Ex, Ey, Ez, cfa, ksum,
                                             part_s, part_v, part_c);
 }
 void launch_terms_final(const long long *part_s, const double *part_v,

@@ -78,6 +78,8 @@ extern "C" int vesis_surface_weights_noalloc(const vesis_params *p, const uint8_
         return fail(VESIS_E_ARG,
                     "grid larger than VESIS_NOALLOC_MAX_CELLS cells; use vesis_surface_weights");
     if (!(p->h > 0.0)) return fail(VESIS_E_ARG, "h must be > 0");
+    if (p->kernel != 0)
+        return fail(VESIS_E_ARG, "the no-allocation convolution takes the separable kernel only");
     if (p->trunc_r < 1 || p->trunc_r > kMaxR) return fail(VESIS_E_ARG, "trunc_r must be in 1..8");
     // integer Gaussian weights summing to 256 (same construction as the
     // system's), on the stack

@@ -176,7 +176,8 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
     for (int base = 0; base < a.n; base += PE_TILE) {
         const int cnt = min(PE_TILE, a.n - base);
         __syncthreads();
-        float ax = 0.f, ay = 0.f, az = 0.f;
+        // corners of the box of the atoms this thread stages
+        float tlo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, thi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
         bool have = false;
         for (int m = threadIdx.x; m < cnt; m += PE_THREADS) {
             const float4 A = a.xyzq[base + m];
@@ -189,17 +190,20 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
             at.a = pk2(B.x, B.x);
             at.nb = pk2(-B.y, -B.y);
             s_at[m] = at;
-            ax = A.x; ay = A.y; az = A.z;
+            tlo[0] = fminf(tlo[0], A.x); tlo[1] = fminf(tlo[1], A.y); tlo[2] = fminf(tlo[2], A.z);
+            thi[0] = fmaxf(thi[0], A.x); thi[1] = fmaxf(thi[1], A.y); thi[2] = fmaxf(thi[2], A.z);
             have = true;
         }
         if (!have) {   // a thread without atoms repeats the tile's first one
             const float4 A = a.xyzq[base];
-            ax = A.x; ay = A.y; az = A.z;
+            tlo[0] = thi[0] = A.x; tlo[1] = thi[1] = A.y; tlo[2] = thi[2] = A.z;
         }
-        // the tile needs the clamp only if its atoms' box comes within r_min
-        // of the block's cells
-        float alo[3], ahi[3];
-        block_box(ax, ay, az, alo, ahi, s_box);
+        // the tile needs the clamp only if the box of all its atoms comes
+        // within r_min of the block's cells: the block minimum of the lower
+        // corners and the block maximum of the upper corners
+        float alo[3], ahi[3], unused[3];
+        block_box(tlo[0], tlo[1], tlo[2], alo, unused, s_box);
+        block_box(thi[0], thi[1], thi[2], unused, ahi, s_box);
         float d2 = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {

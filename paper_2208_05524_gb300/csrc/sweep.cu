@@ -78,9 +78,11 @@ constexpr int kOwnWords = 1024;
 struct SweepArgs {
     GridDesc g;
     KernelW kw;
-    double cD;          // c / 2^24 (exact)
+    double cD;          // c_N: dE = c_N N - s h^3 U
     double h3;
-    int qc3;            // q_0^3 = g0 * 2^24
+    int qc3;            // k0, the kernel's centre weight
+    int ksum;           // S, the sum of all kernel weights
+    const int *k3;      // full stencil (device) or NULL for the product kernel
     uint8_t *chi;
     uint32_t *W;
     const float *U;
@@ -372,6 +374,7 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
 // Update phase for tile t (one warp).  first: the opening pass (no
 // winners; every tile computes its leaders).
 __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, const int *qw,
+                                            const int *kt,
                                             int t, bool first)
 {
     const int lane = threadIdx.x & 31;
@@ -520,12 +523,21 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
                 const int rho = lane + 32 * m;
                 const int ax = (rho >> 3) - wx, ay = (rho & 7) - wy;
                 if (abs(ax) > r || abs(ay) > r) continue;
-                const int qxy = sgn * qw[ax + r] * qw[ay + r];
                 changed[m] = true;
+                if (kt) {      // full stencil: the row of weights at (ax, ay)
+                    const int *wr = kt + ((ax + r) * (2 * r + 1) + (ay + r)) * (2 * r + 1) + r;
 #pragma unroll
-                for (int z = 0; z < TS; ++z) {
-                    const int az = z - wz;
-                    if (abs(az) <= r) Wr[m][z] += (unsigned)(qxy * qw[az + r]);
+                    for (int z = 0; z < TS; ++z) {
+                        const int az = z - wz;
+                        if (abs(az) <= r) Wr[m][z] += (unsigned)(sgn * wr[az]);
+                    }
+                } else {
+                    const int qxy = sgn * qw[ax + r] * qw[ay + r];
+#pragma unroll
+                    for (int z = 0; z < TS; ++z) {
+                        const int az = z - wz;
+                        if (abs(az) <= r) Wr[m][z] += (unsigned)(qxy * qw[az + r]);
+                    }
                 }
             }
         }
@@ -592,10 +604,10 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
         }
     }
     __syncwarp();
-    // dE = c [s (1 - 2w) - g0] - s h^3 U with s = 1 - 2 chi.  With w = W / 2^24
-    // and g0 = q_0^3 / 2^24 the bracket is the integer N = s (2^24 - 2W) - q_0^3
-    // over 2^24, exact in FP64 like every step before the product with c, so
-    // c * bracket = (c / 2^24) * N with the same single rounding.
+    // dE = c [s (1 - 2w) - g0] - s h^3 U with s = 1 - 2 chi, w = W / S and
+    // g0 = k0 / S (S the sum of the kernel's weights, k0 its centre weight):
+    // the bracket is the integer N = s (S - 2W) - k0 over S, so
+    // c * bracket = c_N N with c_N = c / S and one rounding.
     for (int q0 = 0; q0 < ncand; q0 += 32) {
         const int q = q0 + lane;
         if (q >= ncand) continue;
@@ -604,7 +616,7 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
         const unsigned cp = M.u.cP[q];
         const int x = (cp >> 6) & 7, y = (cp >> 3) & 7, z = cp & 7;
         const bool solute = (cp >> 9) & 1u;
-        const int base = (1 << 24) - 2 * (int)Wv;
+        const int base = A.ksum - 2 * (int)Wv;
         const int N = (solute ? -base : base) - A.qc3;
         const double t1 = __dmul_rn(A.cD, (double)N);
         const double t2 = __dmul_rn(A.h3, (double)Uv);
@@ -732,6 +744,12 @@ k_sweep(SweepArgs A)
     const int per_block = (ntiles + gridDim.x - 1) / gridDim.x;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     WarpMem &M = WM[wp];
+    // the full stencil, if any, follows the warps' areas
+    int *kt = A.k3 ? reinterpret_cast<int *>(dyn + NWARP * sizeof(WarpMem)) : nullptr;
+    if (kt) {
+        const int w = 2 * A.kw.r + 1;
+        for (int a = threadIdx.x; a < w * w * w; a += SW_THREADS) kt[a] = A.k3[a];
+    }
     for (int a = threadIdx.x; a <= 2 * A.kw.r; a += SW_THREADS) S.qw[a] = A.kw.q[a];
     for (int a = threadIdx.x; a < kOwnWords; a += SW_THREADS) S.own[a] = 0u;
     if (threadIdx.x == 0) {
@@ -748,7 +766,7 @@ k_sweep(SweepArgs A)
         const int n = gather_tiles(S, nullptr, false, base, ntiles, nullptr);
         for (int q = wp; q < n; q += NWARP) {
             const int t = S.list[q];
-            const bool now = tile_update(A, M, S.qw, t, true);
+            const bool now = tile_update(A, M, S.qw, kt, t, true);
             if (lane == 0) set_own(A, S, t, now);
         }
     }
@@ -779,7 +797,7 @@ k_sweep(SweepArgs A)
             const int n = gather_tiles(S, A.upd, true, base, ntiles, nullptr);
             for (int q = wp; q < n; q += NWARP) {
                 const int t = S.list[q];
-                const bool now = tile_update(A, M, S.qw, t, false);
+                const bool now = tile_update(A, M, S.qw, kt, t, false);
                 if (lane == 0) set_own(A, S, t, now);
             }
         }
@@ -874,7 +892,9 @@ __global__ void k_pack_labels(const uint8_t *__restrict__ chi, int nz, int nzw,
     CB[w] = b;
 }
 
-constexpr size_t kSweepSmem = NWARP * sizeof(WarpMem);
+// warps' areas plus room for the largest full stencil ((2 * 8 + 1)^3 ints)
+constexpr size_t kSweepSmem =
+    NWARP * sizeof(WarpMem) + sizeof(int) * (2 * kMaxR + 1) * (2 * kMaxR + 1) * (2 * kMaxR + 1);
 
 cudaError_t sweep_grid_size(int nsm, int r, int *blocks)
 {
@@ -892,7 +912,8 @@ cudaError_t sweep_grid_size(int nsm, int r, int *blocks)
 
 int sweep_ctl_words() { return 3 * kLine; }
 
-cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &fc,
+cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
+                         const FlipConst &fc,
                          uint8_t *chi, uint32_t *W, const float *U,
                          double *dE, void *state, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
@@ -902,9 +923,11 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &
     SweepArgs A;
     A.g = g;
     A.kw = kw;
-    A.cD = fc.c * fc.invD3;
+    A.cD = fc.cN;
     A.h3 = fc.h3;
-    A.qc3 = kw.q[kw.r] * kw.q[kw.r] * kw.q[kw.r];
+    A.qc3 = fc.k0;
+    A.ksum = fc.S;
+    A.k3 = k3;
     A.chi = chi;
     A.W = W;
     A.U = U;

@@ -97,17 +97,26 @@ void launch_conv_y(const GridDesc &g, const KernelW &kw, const uint16_t *T1,
                    uint32_t *T2, cudaStream_t st);
 void launch_conv_x(const GridDesc &g, const KernelW &kw, const uint32_t *T2,
                    uint32_t *W, cudaStream_t st);
+// W = the direct convolution of chi with a full integer stencil k3 of
+// (2R+1)^3 weights (device, centred: offset (a,b,c) at ((a+R)(2R+1) + b+R)
+// (2R+1) + c+R), for the sin^2 kernel that is not a product.
+void launch_conv3(const GridDesc &g, int R, const int *k3, const uint8_t *chi,
+                  uint32_t *W, cudaStream_t st);
+// Flip energy dE = cN N - s h3 U with the exact integer N = s (S - 2W) - k0
+// (S: sum of all kernel weights, k0: centre weight; Eq. dGj1/dGj2).
 struct FlipConst {
-    double c, g0, h3, invD3;
+    double cN, h3;
+    int S, k0;
 };
 void launch_flip_energy(const GridDesc &g, const uint32_t *W,
                         const uint8_t *chi, const float *U, const FlipConst &fc,
                         double *dE, uint8_t *cand, cudaStream_t st);
 // Energy sums over a labelled grid: per-block partials then ordered final.
 int terms_blocks(long long G);
+// ksum: sum of all kernel weights (S above); part_s collects sum chi (S - W).
 void launch_terms(const GridDesc &g, const uint8_t *chi, const uint32_t *W,
                   const float *U, const float *Ex, const float *Ey,
-                  const float *Ez, float cfa, long long *part_s,
+                  const float *Ez, float cfa, unsigned ksum, long long *part_s,
                   double *part_v, double *part_c, cudaStream_t st);
 // out[0] = c * S / D^3, out[1] = h^3 * sum U (solvent), out[2] = h^3 * sum
 // C|E|^2 (solvent), out[3] = number of solute cells.
@@ -129,8 +138,11 @@ int sweep_ctl_words();   // unsigned words of the sweep control block
 // Bytes of sweep state (leader words, per-tile postings and flags).
 size_t sweep_state_bytes(const GridDesc &g, int r);
 // dE: G doubles, state: sweep_state_bytes(), ctl: sweep_ctl_words(),
-// err: 1 int, part_*: `blocks` entries; writes the totals into *rs.
-cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const FlipConst &fc,
+// err: 1 int, part_*: `blocks` entries; k3: the full stencil (device,
+// (2 kw.r + 1)^3, centred) or NULL for the product kernel kw.q; writes the
+// totals into *rs.
+cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
+                         const FlipConst &fc,
                          uint8_t *chi, uint32_t *W, const float *U,
                          double *dE, void *state, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,

@@ -23,7 +23,8 @@ class Params(C.Structure):
                 ("temperature", _d), ("eps_ss", _d), ("nx", _i), ("ny", _i),
                 ("nz", _i), ("h", _d), ("origin", _d * 3),
                 ("gauss_sigma", _d), ("trunc_r", _i), ("r_min", _d),
-                ("far_field", _i), ("far_nuv", _i), ("far_nt", _i)]
+                ("far_field", _i), ("far_nuv", _i), ("far_nt", _i),
+                ("kernel", _i), ("sin2_lambda", _d)]
 
 
 class RelaxOpts(C.Structure):
@@ -177,6 +178,8 @@ class System:
         for k, v in params.items():
             if k == "origin":
                 p.origin[:] = [float(x) for x in v]
+            elif k == "kernel":     # "gauss" / "sin2" (or 0 / 1)
+                p.kernel = {"gauss": 0, "sin2": 1}.get(v, v)
             else:
                 setattr(p, k, v)
         self.params = p
