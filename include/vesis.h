@@ -161,22 +161,28 @@ int vesis_energy_field(vesis_system s, const double *xyz_or_null,
 
 /* Energy terms of a labelled state from given fields (Eq. 4flip plus the
  * far field and G_ss at the current positions):
- *   surface = c sum_j chi_j (1 - w_j),  w = g * chi (Gaussian kernel),
+ *   surface = c sum_j chi_j (1 - w_j) = c_N sum_j chi_j (S - W_j) with W
+ *             the integer kernel convolution of chi and S the sum of the
+ *             kernel's weights (either kernel; see vesis_params.kernel),
  *   volume  = h^3 sum_{chi_j = 0} U_j  (split into vdW and CFA if E_dev).
  * terms_out[6] as for vesis_energy_field. */
 int vesis_energy_terms(vesis_system s, const uint8_t *chi_dev,
                        const float *U_dev, const float *E_dev,
                        double *terms_out);
 
-/* Kernel convolution of the labels (Eq. Area with the separable Gaussian):
- * W_dev[j] = 256^3 w_j, an exact integer (<= 2^24).  G uint32, written. */
+/* Kernel convolution of the labels (Eq. Area), exact integers, cells
+ * outside the box solvent: with the separable Gaussian W_dev[j] = 256^3 w_j
+ * (<= 2^24); with the sin^2 kernel W_dev[j] = sum_k round(2^16 K_jk) chi_k.
+ * G uint32, written. */
 int vesis_surface_weights(vesis_system s, const uint8_t *chi_dev,
                           uint32_t *W_dev);
 
 /* Flip energies (Eq. dGj1 / dGj2 with the h^3 of the centre-point rule):
  *   dE_j = c [s_j (1 - 2 w_j) - g0] - s_j h^3 U_j,  s_j = 1 - 2 chi_j,
- * evaluated in FP64 on candidate cells (a face neighbour with the other
- * label).  dE_dev: G doubles (0 on non-candidates); cand_dev: G bytes. */
+ * w = W / S, g0 = the centre weight / S, evaluated in FP64 on candidate
+ * cells (a face neighbour with the other label) as c_N N_j - s_j h^3 U_j
+ * with the exact integer N_j = s_j (S - 2 W_j) - centre weight.
+ * dE_dev: G doubles (0 on non-candidates); cand_dev: G bytes. */
 int vesis_flip_energies(vesis_system s, const uint8_t *chi_dev,
                         const float *U_dev, double *dE_dev,
                         uint8_t *cand_dev);
@@ -184,12 +190,12 @@ int vesis_flip_energies(vesis_system s, const uint8_t *chi_dev,
 /* Binary level-set relaxation at fixed atoms (Sec. 3.1, Step 2): rounds
  * of flips until no candidate lowers the energy - the data-parallel form of
  * the min-heap flipping.  A candidate with dE < 0 has the key (float(dE),
- * then index); the grid is cut into bricks of edge 4 (edge 2 when
- * trunc_r < 3) and a brick's leader is its smallest key; each round flips
- * every leader that no other leader within Chebyshev distance trunc_r
- * precedes.  The heap's top always flips, flipped cells are more than
- * trunc_r apart, and a round lowers the energy by exactly the sum of their
- * dE.
+ * then index); with r the kernel's half-width in cells (trunc_r, or the
+ * sin^2 kernel's radius), the grid is cut into bricks of edge 4 (edge 2
+ * when r < 3) and a brick's leader is its smallest key; each round flips
+ * every leader that no other leader within Chebyshev distance r precedes.
+ * The heap's top always flips, flipped cells are more than r apart, and a
+ * round lowers the energy by exactly the sum of their dE.
  *   chi_dev   G bytes, relaxed in place
  *   U_dev     G floats from vesis_energy_field at the current positions
  *   E_dev     3 x G floats or NULL (only for the vdW/CFA split of terms)
@@ -250,8 +256,9 @@ int vesis_get_timing(vesis_system s, vesis_timing *out);
 /* Largest grid (cells) vesis_surface_weights_noalloc accepts. */
 #define VESIS_NOALLOC_MAX_CELLS (1 << 20)
 
-/* The kernel convolution of vesis_surface_weights (W_dev[j] = 256^3 w_j,
- * exact) for callers that cannot allocate device memory.  The paper has no
+/* The kernel convolution of vesis_surface_weights for the separable
+ * Gaussian (W_dev[j] = 256^3 w_j, exact; p->kernel must be 0) for callers
+ * that cannot allocate device memory.  The paper has no
  * counterpart: it is a service of this library.  Creating a vesis_system
  * calls cudaMalloc; code running while a stream is captured into a CUDA
  * graph, processes whose device memory belongs to a pool or arena that
