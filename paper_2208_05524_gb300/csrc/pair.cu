@@ -336,7 +336,11 @@ void launch_point_energy(const float4 *pts, const double *w, int np,
 
 // ------------------------------------------------------ grid -> atoms
 constexpr int PF_THREADS = 128;
-constexpr int PF_APT = 2;                    // atoms per thread
+#ifndef VESIS_PF_APT
+#define VESIS_PF_APT 4
+#endif
+constexpr int PF_APT = VESIS_PF_APT;          // atoms per thread (packed in pairs)
+constexpr int PF_PAIRS = PF_APT / 2;
 constexpr int PF_ATOMS = PF_THREADS * PF_APT;
 constexpr int PF_STAGE = 256;                // cells staged per pass
 
@@ -443,7 +447,7 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
                   AtomsDev a, float rmin2, double *__restrict__ part,
                   unsigned long long *__restrict__ nsolvent)
 {
-    static_assert(PF_APT == 2, "the two atoms of a thread form one packed pair");
+    static_assert(PF_APT % 2 == 0, "a thread's atoms form packed pairs");
     __shared__ __align__(16) CellPairs s_c[PF_STAGE];
     __shared__ int s_wc[2 * PF_THREADS / 32];
     __shared__ float s_box[6 * (PF_THREADS / 32)];
@@ -484,9 +488,19 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             ahi[c] = fmaxf(ahi[c], hi2[c]);
         }
     }
-    const f2 ax2 = pk2(ax[0], ax[1]), ay2 = pk2(ay[0], ay[1]), az2 = pk2(az[0], az[1]);
-    const f2 c12 = pk2(k1[0], k1[1]), c22 = pk2(k2[0], k2[1]), kq2 = pk2(kq[0], kq[1]);
-    const f2 nk32 = pk2(-kq3[0], -kq3[1]);
+    f2 ax2[PF_PAIRS], ay2[PF_PAIRS], az2[PF_PAIRS], c12[PF_PAIRS], c22[PF_PAIRS],
+        kq2[PF_PAIRS], nk32[PF_PAIRS];
+#pragma unroll
+    for (int pp = 0; pp < PF_PAIRS; ++pp) {
+        const int u = 2 * pp;
+        ax2[pp] = pk2(ax[u], ax[u + 1]);
+        ay2[pp] = pk2(ay[u], ay[u + 1]);
+        az2[pp] = pk2(az[u], az[u + 1]);
+        c12[pp] = pk2(k1[u], k1[u + 1]);
+        c22[pp] = pk2(k2[u], k2[u + 1]);
+        kq2[pp] = pk2(kq[u], kq[u + 1]);
+        nk32[pp] = pk2(-kq3[u], -kq3[u + 1]);
+    }
     const f2 zero2 = pk2(0.f, 0.f);
     double acc[PF_APT][3];
 #pragma unroll
@@ -556,26 +570,41 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         }
         __syncthreads();
         seen += (unsigned long long)tot;
-        f2 fx = zero2, fy = zero2, fz = zero2;
+        f2 fx[PF_PAIRS], fy[PF_PAIRS], fz[PF_PAIRS];
+#pragma unroll
+        for (int pp = 0; pp < PF_PAIRS; ++pp) fx[pp] = fy[pp] = fz[pp] = zero2;
         if (clamp) {
 #pragma unroll 2
-            for (int p = 0; p < tot; ++p)
-                force_pair2<true>(s_c[p], ax2, ay2, az2, c12, c22, kq2, nk32, rmin2, fx, fy, fz);
+            for (int p = 0; p < tot; ++p) {
+                const CellPairs c = s_c[p];
+#pragma unroll
+                for (int pp = 0; pp < PF_PAIRS; ++pp)
+                    force_pair2<true>(c, ax2[pp], ay2[pp], az2[pp], c12[pp], c22[pp], kq2[pp],
+                                      nk32[pp], rmin2, fx[pp], fy[pp], fz[pp]);
+            }
         } else {
 #pragma unroll 2
-            for (int p = 0; p < tot; ++p)
-                force_pair2<false>(s_c[p], ax2, ay2, az2, c12, c22, kq2, nk32, rmin2, fx, fy, fz);
+            for (int p = 0; p < tot; ++p) {
+                const CellPairs c = s_c[p];
+#pragma unroll
+                for (int pp = 0; pp < PF_PAIRS; ++pp)
+                    force_pair2<false>(c, ax2[pp], ay2[pp], az2[pp], c12[pp], c22[pp], kq2[pp],
+                                       nk32[pp], rmin2, fx[pp], fy[pp], fz[pp]);
+            }
         }
-        float f0, f1;
-        upk2(fx, f0, f1);
-        acc[0][0] += (double)f0;
-        acc[1][0] += (double)f1;
-        upk2(fy, f0, f1);
-        acc[0][1] += (double)f0;
-        acc[1][1] += (double)f1;
-        upk2(fz, f0, f1);
-        acc[0][2] += (double)f0;
-        acc[1][2] += (double)f1;
+#pragma unroll
+        for (int pp = 0; pp < PF_PAIRS; ++pp) {
+            float f0, f1;
+            upk2(fx[pp], f0, f1);
+            acc[2 * pp][0] += (double)f0;
+            acc[2 * pp + 1][0] += (double)f1;
+            upk2(fy[pp], f0, f1);
+            acc[2 * pp][1] += (double)f0;
+            acc[2 * pp + 1][1] += (double)f1;
+            upk2(fz[pp], f0, f1);
+            acc[2 * pp][2] += (double)f0;
+            acc[2 * pp + 1][2] += (double)f1;
+        }
     }
 #pragma unroll
     for (int u = 0; u < PF_APT; ++u) {

@@ -373,6 +373,7 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
 
 // Update phase for tile t (one warp).  first: the opening pass (no
 // winners; every tile computes its leaders).
+template <bool STENCIL>
 __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, const int *qw,
                                             const int *kt,
                                             int t, bool first)
@@ -524,7 +525,7 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
                 const int ax = (rho >> 3) - wx, ay = (rho & 7) - wy;
                 if (abs(ax) > r || abs(ay) > r) continue;
                 changed[m] = true;
-                if (kt) {      // full stencil: the row of weights at (ax, ay)
+                if (STENCIL) {      // full stencil: the row of weights at (ax, ay)
                     const int *wr = kt + ((ax + r) * (2 * r + 1) + (ay + r)) * (2 * r + 1) + r;
 #pragma unroll
                     for (int z = 0; z < TS; ++z) {
@@ -734,6 +735,7 @@ __device__ __forceinline__ void set_own(const SweepArgs &A, SweepShared &S, int 
     red_add(A.nlead, now ? 1u : 0xffffffffu);
 }
 
+template <bool STENCIL>
 __global__ void __launch_bounds__(SW_THREADS, 1)
 k_sweep(SweepArgs A)
 {
@@ -745,8 +747,8 @@ k_sweep(SweepArgs A)
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     WarpMem &M = WM[wp];
     // the full stencil, if any, follows the warps' areas
-    int *kt = A.k3 ? reinterpret_cast<int *>(dyn + NWARP * sizeof(WarpMem)) : nullptr;
-    if (kt) {
+    int *kt = STENCIL ? reinterpret_cast<int *>(dyn + NWARP * sizeof(WarpMem)) : nullptr;
+    if (STENCIL) {
         const int w = 2 * A.kw.r + 1;
         for (int a = threadIdx.x; a < w * w * w; a += SW_THREADS) kt[a] = A.k3[a];
     }
@@ -766,7 +768,7 @@ k_sweep(SweepArgs A)
         const int n = gather_tiles(S, nullptr, false, base, ntiles, nullptr);
         for (int q = wp; q < n; q += NWARP) {
             const int t = S.list[q];
-            const bool now = tile_update(A, M, S.qw, kt, t, true);
+            const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, true);
             if (lane == 0) set_own(A, S, t, now);
         }
     }
@@ -797,7 +799,7 @@ k_sweep(SweepArgs A)
             const int n = gather_tiles(S, A.upd, true, base, ntiles, nullptr);
             for (int q = wp; q < n; q += NWARP) {
                 const int t = S.list[q];
-                const bool now = tile_update(A, M, S.qw, kt, t, false);
+                const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, false);
                 if (lane == 0) set_own(A, S, t, now);
             }
         }
@@ -899,12 +901,21 @@ constexpr size_t kSweepSmem =
 cudaError_t sweep_grid_size(int nsm, int r, int *blocks)
 {
     (void)r;
-    cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSweepSmem);
     if (e != cudaSuccess) return e;
-    int per = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep, SW_THREADS, kSweepSmem);
+    e = cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSweepSmem);
     if (e != cudaSuccess) return e;
+    int per = 0, per2 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<false>, SW_THREADS,
+                                                      kSweepSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_sweep<true>, SW_THREADS,
+                                                      kSweepSmem);
+    if (e != cudaSuccess) return e;
+    per = per2 < per ? per2 : per;
     per = per > VESIS_SWEEP_BPS ? VESIS_SWEEP_BPS : per;
     *blocks = per * nsm;
     return *blocks > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
@@ -974,7 +985,8 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
     }
     void *args[] = {&A};
     count_launch();
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_sweep, dim3(blocks),
+    cudaError_t e = cudaLaunchCooperativeKernel(k3 ? (void *)k_sweep<true> : (void *)k_sweep<false>,
+                                                dim3(blocks),
                                                 dim3(SW_THREADS), args, kSweepSmem, st);
     if (e != cudaSuccess) return e;
     count_launch();
