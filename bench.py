@@ -486,6 +486,90 @@ def run_converge(args, world, rank, local):
     S.close()
 
 
+def run_batch(args, world, rank, local):
+    """The batched form on the host-guest set (64 systems at h = 0.3 A,
+    seed 1): every system relaxed for --max-outer outer iterations (default
+    3) from its tight start, first one after another with vesis_relax and the
+    default tile shapes (the plain GPU form), then all at once with
+    vesis_relax_batch after the autotuner has picked each system's tile
+    shapes.  Both forms must end in identical labels and energies.  Prints
+    one JSON line of its own: seconds per system relaxation of each form."""
+    import numpy as np
+    import torch
+
+    from paper_2208_05524_gb300 import synth, vesis
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    K = args.max_outer or 3
+    t0 = time.perf_counter()
+    sysds = [synth.host_guest(i, seed=1) for i in range(args.batch_systems)]
+    gen_s = time.perf_counter() - t0
+    systems, chis0 = [], []
+    for sd in sysds:
+        S = vesis.System(sd, stream=torch.cuda.Stream(device=dev))
+        c = torch.empty(S.G, dtype=torch.uint8, device=dev)
+        S.init_labels(c, "tight")
+        systems.append(S)
+        chis0.append(c)
+    torch.cuda.synchronize()
+    xyzs = [np.ascontiguousarray(sd["xyz"]) for sd in sysds]
+    # warm-up: one outer iteration of the smallest system loads every kernel
+    small = min(range(len(systems)), key=lambda i: systems[i].G * systems[i].n_atoms)
+    c = chis0[small].clone()
+    systems[small].relax(c, xyzs[small], max_outer=1)
+    vesis.relax_batch([systems[small]], [c], [xyzs[small]], max_outer=1)
+    torch.cuda.synchronize()
+    # plain GPU form: one system after another, default tile shapes
+    chis = [c0.clone() for c0 in chis0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [S.relax(c, x, max_outer=K) for S, c, x in zip(systems, chis, xyzs)]
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    seq_chi = [c.cpu() for c in chis]
+    # batched form: autotuned shapes, all systems at once
+    t0 = time.perf_counter()
+    tuned = [S.autotune(c, reps=2) for S, c in zip(systems, chis0)]
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    chis = [c0.clone() for c0 in chis0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bat = vesis.relax_batch(systems, chis, xyzs, threads=args.batch_threads,
+                            sweep_slots=args.sweep_slots, max_outer=K)
+    torch.cuda.synchronize()
+    bat_s = time.perf_counter() - t0
+    same = all(torch.equal(c.cpu(), c0) for c, c0 in zip(chis, seq_chi)) and \
+        all(a["G"] == b["G"] and np.array_equal(a["xyz"], b["xyz"]) for a, b in zip(seq, bat))
+    pairs = sum(r["pair_evals"] for r in bat)
+    n = len(systems)
+    shapes = {}
+    for t in tuned:
+        k = f'{t["energy_pencil"]}/{t["force_atoms"]}'
+        shapes[k] = shapes.get(k, 0) + 1
+    out = {"metric": f"sec per VESIS relaxation ({K} outer iterations), batched form",
+           "value": bat_s / n, "unit": "s", "higher_is_better": False, "n_gpus": world,
+           "data": "synthetic", "dtype": "f32",
+           "config": {"workload": f"host_guest{n}_h0.3",
+                      "desc": f"{n} host-guest systems (host 150-4,000 atoms log-uniform, "
+                              "guest 20-80, offset 5-15 A, seed 1), grids 160-320^3 at "
+                              "h=0.3 A, tight start",
+                      "threads": args.batch_threads, "sweep_slots": args.sweep_slots},
+           "sequential_s_per_system": seq_s / n, "batched_s_per_system": bat_s / n,
+           "speedup": seq_s / bat_s, "identical_results": bool(same),
+           "autotune_s": tune_s, "tile_shapes": shapes,
+           "pair_evals": pairs, "pair_evals_per_s_batched": pairs / bat_s,
+           "pair_evals_per_s_sequential": sum(r["pair_evals"] for r in seq) / seq_s,
+           "atoms": int(sum(S.n_atoms for S in systems)),
+           "cells": int(sum(S.G for S in systems)),
+           "status": sorted(set(r["status"] for r in bat)), "generate_s": gen_s}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    for S in systems:
+        S.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,9 +583,16 @@ def main():
     ap.add_argument("--converge", action="store_true",
                     help="time one converged relaxation instead of the step benchmark")
     ap.add_argument("--max-outer", type=int, default=0)
+    ap.add_argument("--batch", action="store_true",
+                    help="time the batched form on the host-guest set against the plain form")
+    ap.add_argument("--batch-systems", type=int, default=64)
+    ap.add_argument("--batch-threads", type=int, default=8)
+    ap.add_argument("--sweep-slots", type=int, default=2)
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    if args.converge:
+    if args.batch:
+        run_batch(args, world, rank, local)
+    elif args.converge:
         run_converge(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)

@@ -229,6 +229,44 @@ int vesis_atom_forces(vesis_system s, const uint8_t *chi_dev,
 int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
                 const vesis_relax_opts *opts, vesis_relax_stats *stats_out);
 
+/* Tile shapes of the two pair kernels: cells of a z-pencil per thread of
+ * the energy-density kernel (4 or 8, default 8) and atoms per thread of the
+ * grid-to-atom gradient kernel (2 or 4, default 4).  Every cell sums its
+ * atoms, and every atom its cells, in the same order for all shapes, so
+ * the results are bit-identical; only the time differs.  Waits for the
+ * system's stream.  VESIS_E_ARG for any other value. */
+int vesis_set_tiles(vesis_system s, int energy_pencil, int force_atoms);
+int vesis_get_tiles(vesis_system s, int *energy_pencil, int *force_atoms);
+
+/* Autotuner: times each tile shape of the two pair kernels on the system's
+ * current positions and labels chi_dev (one warm-up and `reps` launches
+ * each, 1..1000, CUDA events on the system's stream) and keeps the fastest
+ * (vesis_set_tiles).  times_ms_out (may be NULL): 4 doubles, the mean
+ * launch time of energy pencil 4, 8 and gradient atoms 2, 4. */
+int vesis_autotune(vesis_system s, const uint8_t *chi_dev, int reps,
+                   double *times_ms_out);
+
+/* Batched relaxation: vesis_relax of every system i on (chi_dev[i],
+ * xyz_inout[i]) with the same opts, run by `threads` host threads (1..256)
+ * that take the systems from a shared queue, largest grid x atoms first.
+ * The paper relaxes one solute at a time; this is a service for many
+ * small solutes.  Each system runs on a private non-blocking stream for
+ * the call (its own stream is drained first and given back afterwards),
+ * so one system's kernels overlap another's host steps and kernel tails.
+ * The flip sweep is one cooperative launch whose blocks must be resident
+ * together: at most `sweep_slots` (1..16) sweeps run at a time, each on
+ * 1 / sweep_slots of the device's sweep blocks.  The results of every
+ * system (labels, positions, stats) equal those of vesis_relax called on
+ * it alone.  The systems must be distinct and on one device.
+ *   stats_out  nsys entries or NULL;  status_out  nsys ints or NULL: each
+ *              system's vesis_status
+ * Returns VESIS_OK, or the first system's error (index in the message)
+ * if any system failed; warnings are only reported in status_out. */
+int vesis_relax_batch(int nsys, vesis_system *systems, uint8_t *const *chi_dev,
+                      double *const *xyz_inout, const vesis_relax_opts *opts,
+                      int threads, int sweep_slots, vesis_relax_stats *stats_out,
+                      int *status_out);
+
 /* Device time of the hot kernels, measured with CUDA events recorded on the
  * system's stream around each launch while timing is enabled. */
 typedef struct {

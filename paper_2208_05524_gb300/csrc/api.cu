@@ -5,9 +5,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <numeric>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -141,6 +145,32 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
 
 }  // namespace
 
+// Admission of flip sweeps while several systems relax at once: each sweep
+// is one cooperative launch whose blocks must all be resident together, so
+// at most `slots` sweeps run at a time and each uses `blocks` blocks, with
+// slots x blocks no more than one wave of the device.  Other kernels always
+// end by themselves, so an admitted sweep only waits for them to drain.
+struct SweepGate {
+    std::mutex m;
+    std::condition_variable cv;
+    int free_slots = 1;
+    int blocks = 1;
+    void acquire()
+    {
+        std::unique_lock<std::mutex> l(m);
+        cv.wait(l, [&] { return free_slots > 0; });
+        --free_slots;
+    }
+    void release()
+    {
+        {
+            std::lock_guard<std::mutex> l(m);
+            ++free_slots;
+        }
+        cv.notify_one();
+    }
+};
+
 struct vesis_system_t {
     int dev = 0;
     cudaStream_t st = nullptr;
@@ -178,6 +208,8 @@ struct vesis_system_t {
     double *d_part_v = nullptr, *d_part_c = nullptr;
     int nb_terms = 0;
     ForcePlan fplan{}, fplan_far{};
+    int pe_pts = 8;             // cells per thread of the energy kernel (4 or 8)
+    SweepGate *gate = nullptr;  // set while a batched relaxation runs
     double *d_fpart = nullptr;
     double *d_grad_solv = nullptr, *d_grad_ss = nullptr, *d_grad = nullptr;
     unsigned long long *d_gmax = nullptr;
@@ -349,7 +381,7 @@ void enq_fields(vesis_system s, float *U, float *E, double *bk)
     const int sp = span_begin(s);
     launch_pair_energy_grid(s->g, atoms_view(s), (float)s->p.rho_w,
                             (float)s->cfa, s->rmin2, U, E, E + s->G,
-                            E + 2 * s->G, s->st);
+                            E + 2 * s->G, s->pe_pts, s->st);
     span_end(s, sp, 0, s->G * (long long)s->n, 0);
     enq_far(s, bk);
 }
@@ -399,11 +431,27 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
     // exact integer convolution of the starting labels (unless d_W holds it
     // already); the sweep keeps it current with every flip
     if (!w_current) enq_conv(s, chi, s->d_W);
+    // batched: the stream is drained first so that an admitted sweep starts
+    // at once, and the slot is held until the sweep has ended
+    struct Hold {
+        SweepGate *g;
+        ~Hold()
+        {
+            if (g) g->release();
+        }
+    } hold{nullptr};
+    int blocks = s->sweep_blocks;
+    if (s->gate) {
+        VCK(cudaStreamSynchronize(s->st));
+        s->gate->acquire();
+        hold.g = s->gate;
+        blocks = std::max(1, std::min(blocks, s->gate->blocks));
+    }
     const int sp = span_begin(s);
     VCK(launch_sweep(s->g, s->kw, s->d_k3, s->fc, chi, s->d_W, U, s->d_dE, s->d_sweep,
                      s->d_ctl, s->d_err, s->d_part_flips,
                      s->d_part_dE, s->d_rounds, s->d_capped, max_rounds,
-                     s->sweep_blocks, s->d_rs, s->st));
+                     blocks, s->d_rs, s->st));
     span_end(s, sp, 2, 0, 0);
     VCK(cudaMemcpyAsync(s->h_rs, s->d_rs, sizeof(RoundState),
                         cudaMemcpyDeviceToHost, s->st));
@@ -813,7 +861,7 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     }
 
     // gradient partials
-    s->fplan = plan_pair_force(G, n, s->nsm);
+    s->fplan = plan_pair_force(G, n, s->nsm, 4);
     s->fplan_far = plan_point_force(std::max(1, s->nfar), n, s->nsm);
     const long long nch = std::max(s->fplan.nchunk, s->fplan_far.nchunk);
     VTRY(dalloc(s, &s->d_fpart, (size_t)nch * n * 3));
@@ -1191,6 +1239,179 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     st.max_grad = gmax;
     if (stats_out) *stats_out = st;
     return status;
+}
+
+int vesis_set_tiles(vesis_system s, int energy_pencil, int force_atoms)
+{
+    if (!s) return fail(VESIS_E_ARG, "NULL system");
+    if (energy_pencil != 4 && energy_pencil != 8)
+        return fail(VESIS_E_ARG, "energy_pencil must be 4 or 8");
+    if (force_atoms != 2 && force_atoms != 4)
+        return fail(VESIS_E_ARG, "force_atoms must be 2 or 4");
+    VCK(cudaStreamSynchronize(s->st));
+    s->pe_pts = energy_pencil;
+    const ForcePlan fp = plan_pair_force(s->G, s->n, s->nsm, force_atoms);
+    // the partial buffer was sized for this chunk count at set-up
+    if (fp.nchunk != s->fplan.nchunk) return fail(VESIS_E_CUDA, "gradient chunk plan changed");
+    s->fplan = fp;
+    return VESIS_OK;
+}
+
+int vesis_get_tiles(vesis_system s, int *energy_pencil, int *force_atoms)
+{
+    if (!s) return fail(VESIS_E_ARG, "NULL system");
+    if (energy_pencil) *energy_pencil = s->pe_pts;
+    if (force_atoms) *force_atoms = s->fplan.apt;
+    return VESIS_OK;
+}
+
+int vesis_autotune(vesis_system s, const uint8_t *chi_dev, int reps, double *times_ms_out)
+{
+    if (!s || !chi_dev) return fail(VESIS_E_ARG, "NULL argument");
+    if (reps < 1 || reps > 1000) return fail(VESIS_E_ARG, "reps must be in 1..1000");
+    static const int kPencil[2] = {4, 8}, kAtoms[2] = {2, 4};
+    double ms[4] = {0, 0, 0, 0};
+    // the trial buffers are scratch between calls; the count of solvent
+    // cells the gradient kernel keeps for the timing report is put back
+    float *U = s->d_U[1], *E = s->d_E[1];
+    VCK(cudaMemcpyAsync(s->h_u64, s->d_fcount, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s->st));
+    VCK(cudaStreamSynchronize(s->st));
+    const unsigned long long fcount = *s->h_u64;
+    struct Events {
+        vesis_system s;
+        cudaEvent_t a, b;
+        ~Events()
+        {
+            s->ev_pool.push_back(a);
+            s->ev_pool.push_back(b);
+        }
+    } ev{s, take_event(s), take_event(s)};
+    cudaEvent_t a = ev.a, b = ev.b;
+    auto timed = [&](auto &&launch, double *out) -> int {
+        launch();   // warm-up
+        VCK(cudaEventRecord(a, s->st));
+        for (int i = 0; i < reps; ++i) launch();
+        VCK(cudaEventRecord(b, s->st));
+        VCK(cudaEventSynchronize(b));
+        float t = 0.f;
+        VCK(cudaEventElapsedTime(&t, a, b));
+        *out = (double)t / reps;
+        return VESIS_OK;
+    };
+    for (int v = 0; v < 2; ++v) {
+        const int P = kPencil[v];
+        VTRY(timed([&] {
+            launch_pair_energy_grid(s->g, atoms_view(s), (float)s->p.rho_w, (float)s->cfa,
+                                    s->rmin2, U, E, E + s->G, E + 2 * s->G, P, s->st);
+        }, &ms[v]));
+    }
+    for (int v = 0; v < 2; ++v) {
+        const ForcePlan fp = plan_pair_force(s->G, s->n, s->nsm, kAtoms[v]);
+        VTRY(timed([&] {
+            launch_pair_force_grid(s->g, fp, chi_dev, E, E + s->G, E + 2 * s->G,
+                                   atoms_view(s), s->rmin2, s->d_fpart, s->d_fcount, s->st);
+        }, &ms[2 + v]));
+    }
+    VTRY(last_launch("autotune"));
+    *s->h_u64 = fcount;
+    VCK(cudaMemcpyAsync(s->d_fcount, s->h_u64, sizeof(unsigned long long),
+                        cudaMemcpyHostToDevice, s->st));
+    if (times_ms_out) std::memcpy(times_ms_out, ms, sizeof(ms));
+    return vesis_set_tiles(s, ms[0] < ms[1] ? 4 : 8, ms[2] < ms[3] ? 2 : 4);
+}
+
+int vesis_relax_batch(int nsys, vesis_system *systems, uint8_t *const *chi_dev,
+                      double *const *xyz_inout, const vesis_relax_opts *opts,
+                      int threads, int sweep_slots, vesis_relax_stats *stats_out,
+                      int *status_out)
+{
+    if (nsys < 0) return fail(VESIS_E_ARG, "nsys must be >= 0");
+    if (nsys == 0) return VESIS_OK;
+    if (!systems || !chi_dev || !xyz_inout) return fail(VESIS_E_ARG, "NULL argument");
+    if (threads < 1 || threads > 256) return fail(VESIS_E_ARG, "threads must be in 1..256");
+    if (sweep_slots < 1 || sweep_slots > 16)
+        return fail(VESIS_E_ARG, "sweep_slots must be in 1..16");
+    int dev = -1;
+    for (int i = 0; i < nsys; ++i) {
+        if (!systems[i] || !chi_dev[i] || !xyz_inout[i])
+            return fail(VESIS_E_ARG, "NULL system or buffer at index " + std::to_string(i));
+        for (int j = 0; j < i; ++j)
+            if (systems[j] == systems[i])
+                return fail(VESIS_E_ARG, "a system appears twice in the batch");
+        if (dev < 0) dev = systems[i]->dev;
+        if (systems[i]->dev != dev) return fail(VESIS_E_ARG, "systems are on different devices");
+    }
+    int dev0 = 0;
+    VCK(cudaGetDevice(&dev0));
+    VCK(cudaSetDevice(dev));
+    // one wave of sweep blocks shared by the admitted sweeps
+    SweepGate gate;
+    int wave = systems[0]->sweep_blocks;
+    for (int i = 1; i < nsys; ++i) wave = std::min(wave, systems[i]->sweep_blocks);
+    gate.free_slots = std::min(sweep_slots, std::max(1, wave));
+    gate.blocks = std::max(1, wave / gate.free_slots);
+    // every system runs on a private non-blocking stream for the call; the
+    // caller's streams are drained first and handed back afterwards
+    std::vector<cudaStream_t> own(nsys, nullptr), prev(nsys, nullptr);
+    int rc = VESIS_OK;
+    for (int i = 0; i < nsys && rc == VESIS_OK; ++i) {
+        if (cudaStreamSynchronize(systems[i]->st) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&own[i], cudaStreamNonBlocking) != cudaSuccess)
+            rc = fail(VESIS_E_CUDA, "batch stream set-up failed");
+    }
+    std::vector<int> status(nsys, VESIS_E_CUDA);
+    std::vector<std::string> msg(nsys);
+    if (rc == VESIS_OK) {
+        for (int i = 0; i < nsys; ++i) {
+            prev[i] = systems[i]->st;
+            systems[i]->st = own[i];
+            systems[i]->gate = &gate;
+        }
+        // largest systems first (longest-processing-time order)
+        std::vector<int> order(nsys);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return systems[x]->G * (long long)systems[x]->n >
+                   systems[y]->G * (long long)systems[y]->n;
+        });
+        std::atomic<int> next{0};
+        auto worker = [&] {
+            cudaSetDevice(dev);
+            for (;;) {
+                const int q = next.fetch_add(1);
+                if (q >= nsys) break;
+                const int i = order[q];
+                vesis_relax_stats st;
+                std::memset(&st, 0, sizeof(st));
+                status[i] = vesis_relax(systems[i], chi_dev[i], xyz_inout[i], opts, &st);
+                if (status[i] < 0) msg[i] = g_err;
+                if (stats_out) stats_out[i] = st;
+            }
+        };
+        const int nt = std::min(threads, nsys);
+        std::vector<std::thread> pool;
+        try {
+            pool.reserve(nt);
+            for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+        } catch (...) {
+            // no more threads: the ones that started drain the queue
+        }
+        if (pool.empty()) worker();
+        for (auto &t : pool) t.join();
+        for (int i = 0; i < nsys; ++i) {
+            cudaStreamSynchronize(own[i]);
+            systems[i]->st = prev[i];
+            systems[i]->gate = nullptr;
+        }
+        for (int i = 0; i < nsys && rc == VESIS_OK; ++i)
+            if (status[i] < 0) rc = fail(status[i], "system " + std::to_string(i) + ": " + msg[i]);
+    }
+    for (int i = 0; i < nsys; ++i)
+        if (own[i]) cudaStreamDestroy(own[i]);
+    if (status_out) std::memcpy(status_out, status.data(), nsys * sizeof(int));
+    cudaSetDevice(dev0);
+    return rc;
 }
 
 }  // extern "C"

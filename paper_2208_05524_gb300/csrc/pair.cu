@@ -10,14 +10,13 @@
 // with the LJ part and the d d^T part dropped where r is clamped.
 //
 // Atom tiles are staged in shared memory and read as warp-wide broadcasts;
-// every thread keeps PE_PTS cells of one z-pencil in registers, so the x/y
+// every thread keeps 4 or 8 cells of one z-pencil in registers, so the x/y
 // parts of the distance are formed once per atom and reused.
 #include "vesis_internal.cuh"
 
 namespace vesis {
 
 constexpr int PE_THREADS = 128;
-constexpr int PE_PTS = 8;
 constexpr int PE_TILE = 256;
 
 // 1/sqrt(x) on the SFU without the subnormal range handling: every argument
@@ -99,9 +98,9 @@ struct AtomPairs {
     f2 a, nb;        // A = 4 eps sigma^12, -B = -4 eps sigma^6
 };
 
-// One atom against the PE_PTS cells of a thread, two cells per packed
+// One atom against the PTS cells of a thread, two cells per packed
 // instruction; CLAMP applies r_min.
-template <bool CLAMP>
+template <bool CLAMP, int PTS>
 __device__ __forceinline__ void energy_atom(const AtomPairs &at, f2 px, f2 py, const f2 *pz,
                                             float rmin2, f2 *lj, f2 *ex, f2 *ey, f2 *ez)
 {
@@ -109,7 +108,7 @@ __device__ __forceinline__ void energy_atom(const AtomPairs &at, f2 px, f2 py, c
     const f2 dy = sub2(py, at.y);
     const f2 dxy2 = fma2(dx, dx, mul2(dy, dy));
 #pragma unroll
-    for (int p = 0; p < PE_PTS / 2; ++p) {
+    for (int p = 0; p < PTS / 2; ++p) {
         const f2 dz = sub2(pz[p], at.z);
         const f2 r2 = fma2(dz, dz, dxy2);
         float r2a, r2b;
@@ -131,18 +130,17 @@ __device__ __forceinline__ void energy_atom(const AtomPairs &at, f2 px, f2 py, c
     }
 }
 
-#ifndef VESIS_PE_MINB
-#define VESIS_PE_MINB 4
-#endif
-
-__global__ void __launch_bounds__(PE_THREADS, VESIS_PE_MINB)
+// PTS (cells of a z-pencil per thread, 4 or 8) is the pencil size the
+// autotuner picks per system; the sums of every cell are the same for both.
+template <int PTS>
+__global__ void __launch_bounds__(PE_THREADS, PTS == 8 ? 4 : 5)
 k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
                    float *__restrict__ U, float *__restrict__ Ex,
                    float *__restrict__ Ey, float *__restrict__ Ez)
 {
     __shared__ __align__(16) AtomPairs s_at[PE_TILE];
     __shared__ float s_box[6 * (PE_THREADS / 32)];
-    const int cpp = (g.nz + PE_PTS - 1) / PE_PTS;
+    const int cpp = (g.nz + PTS - 1) / PTS;
     const long long t = (long long)blockIdx.x * PE_THREADS + threadIdx.x;
     const long long npen = (long long)g.nx * g.ny;
     const long long pen = t / cpp;
@@ -150,16 +148,16 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
     const bool live = pen < npen;
     const int i = live ? (int)(pen / g.ny) : 0;
     const int j = live ? (int)(pen - (long long)i * g.ny) : 0;
-    const int k0 = chunk * PE_PTS;
+    const int k0 = chunk * PTS;
     const float px = cell_pos(i, g.cx, g.h);
     const float py = cell_pos(j, g.cy, g.h);
-    float pzs[PE_PTS];
+    float pzs[PTS];
 #pragma unroll
-    for (int p = 0; p < PE_PTS; ++p) pzs[p] = cell_pos(k0 + p, g.cz, g.h);
-    f2 pz[PE_PTS / 2], lj[PE_PTS / 2], ex[PE_PTS / 2], ey[PE_PTS / 2], ez[PE_PTS / 2];
+    for (int p = 0; p < PTS; ++p) pzs[p] = cell_pos(k0 + p, g.cz, g.h);
+    f2 pz[PTS / 2], lj[PTS / 2], ex[PTS / 2], ey[PTS / 2], ez[PTS / 2];
     const f2 zero = pk2(0.f, 0.f);
 #pragma unroll
-    for (int p = 0; p < PE_PTS / 2; ++p) {
+    for (int p = 0; p < PTS / 2; ++p) {
         pz[p] = pk2(pzs[2 * p], pzs[2 * p + 1]);
         lj[p] = ex[p] = ey[p] = ez[p] = zero;
     }
@@ -169,7 +167,7 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
     block_box(px, py, pzs[0], clo, chi, s_box);
     {
         float lo2[3], hi2[3];
-        block_box(px, py, pzs[PE_PTS - 1], lo2, hi2, s_box);
+        block_box(px, py, pzs[PTS - 1], lo2, hi2, s_box);
         clo[2] = fminf(clo[2], lo2[2]);
         chi[2] = fmaxf(chi[2], hi2[2]);
     }
@@ -214,17 +212,17 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
         if (d2 > rmin2) {
 #pragma unroll 2
             for (int m = 0; m < cnt; ++m)
-                energy_atom<false>(s_at[m], px2, py2, pz, rmin2, lj, ex, ey, ez);
+                energy_atom<false, PTS>(s_at[m], px2, py2, pz, rmin2, lj, ex, ey, ez);
         } else {
 #pragma unroll 2
             for (int m = 0; m < cnt; ++m)
-                energy_atom<true>(s_at[m], px2, py2, pz, rmin2, lj, ex, ey, ez);
+                energy_atom<true, PTS>(s_at[m], px2, py2, pz, rmin2, lj, ex, ey, ez);
         }
     }
     if (!live) return;
     const long long row = pen * g.nz;
 #pragma unroll
-    for (int p = 0; p < PE_PTS / 2; ++p) {
+    for (int p = 0; p < PTS / 2; ++p) {
         float l[2], x[2], y[2], z[2];
         upk2(lj[p], l[0], l[1]);
         upk2(ex[p], x[0], x[1]);
@@ -247,14 +245,19 @@ k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
 
 void launch_pair_energy_grid(const GridDesc &g, const AtomsDev &a, float rho,
                              float cfa, float rmin2, float *U, float *Ex,
-                             float *Ey, float *Ez, cudaStream_t st)
+                             float *Ey, float *Ez, int pts, cudaStream_t st)
 {
-    const long long cpp = (g.nz + PE_PTS - 1) / PE_PTS;
+    const int P = pts == 4 ? 4 : 8;
+    const long long cpp = (g.nz + P - 1) / P;
     const long long threads = (long long)g.nx * g.ny * cpp;
     const long long blocks = (threads + PE_THREADS - 1) / PE_THREADS;
     count_launch();
-    k_pair_energy_grid<<<(unsigned)blocks, PE_THREADS, 0, st>>>(
-        g, a, rho, cfa, rmin2, U, Ex, Ey, Ez);
+    if (P == 4)
+        k_pair_energy_grid<4><<<(unsigned)blocks, PE_THREADS, 0, st>>>(
+            g, a, rho, cfa, rmin2, U, Ex, Ey, Ez);
+    else
+        k_pair_energy_grid<8><<<(unsigned)blocks, PE_THREADS, 0, st>>>(
+            g, a, rho, cfa, rmin2, U, Ex, Ey, Ez);
 }
 
 // ------------------------------------------------------------ block sums
@@ -336,20 +339,21 @@ void launch_point_energy(const float4 *pts, const double *w, int np,
 
 // ------------------------------------------------------ grid -> atoms
 constexpr int PF_THREADS = 128;
-#ifndef VESIS_PF_APT
-#define VESIS_PF_APT 4
-#endif
-constexpr int PF_APT = VESIS_PF_APT;          // atoms per thread (packed in pairs)
-constexpr int PF_PAIRS = PF_APT / 2;
+constexpr int PF_APT = 4;                    // atoms per thread of the point kernel
 constexpr int PF_ATOMS = PF_THREADS * PF_APT;
 constexpr int PF_STAGE = 256;                // cells staged per pass
 
-ForcePlan plan_pair_force(long long G, int natoms, int nsm)
+ForcePlan plan_pair_force(long long G, int natoms, int nsm, int apt)
 {
     ForcePlan fp;
-    fp.atom_tiles = (natoms + PF_ATOMS - 1) / PF_ATOMS;
+    fp.apt = apt == 2 ? 2 : 4;
+    fp.atom_tiles = (natoms + PF_THREADS * fp.apt - 1) / (PF_THREADS * fp.apt);
+    // The cell chunks are sized from the 512-atom tile count whatever the
+    // atom tile, so every atom sums the same stages in the same order and
+    // both variants give bit-identical gradients.
+    const long long tiles512 = (natoms + PF_ATOMS - 1) / PF_ATOMS;
     const long long target = (long long)nsm * 8 * 4;
-    long long nchunk = target / fp.atom_tiles;
+    long long nchunk = target / tiles512;
     const long long maxc = (G + PF_STAGE - 1) / PF_STAGE;
     if (nchunk < 1) nchunk = 1;
     if (nchunk > maxc) nchunk = maxc;
@@ -440,6 +444,9 @@ __device__ __forceinline__ void force_pair2(const CellPairs &c, f2 ax, f2 ay, f2
     fz = fma2(cd, dz, fma2(am, c.ez, fz));
 }
 
+// APT (atoms per thread, 2 or 4, in packed pairs) is the atom tile the
+// autotuner picks per system.
+template <int APT>
 __global__ void __launch_bounds__(PF_THREADS)
 k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
                   const uint8_t *__restrict__ chi, const float *__restrict__ Ex,
@@ -447,7 +454,9 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
                   AtomsDev a, float rmin2, double *__restrict__ part,
                   unsigned long long *__restrict__ nsolvent)
 {
-    static_assert(PF_APT % 2 == 0, "a thread's atoms form packed pairs");
+    static_assert(APT % 2 == 0, "a thread's atoms form packed pairs");
+    constexpr int PAIRS = APT / 2;
+    constexpr int ATOMS = PF_THREADS * APT;
     __shared__ __align__(16) CellPairs s_c[PF_STAGE];
     __shared__ int s_wc[2 * PF_THREADS / 32];
     __shared__ float s_box[6 * (PF_THREADS / 32)];
@@ -457,13 +466,13 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = PF_THREADS / 32;
 
-    float ax[PF_APT], ay[PF_APT], az[PF_APT], k1[PF_APT], k2[PF_APT], kq[PF_APT],
-        kq3[PF_APT];
-    int an[PF_APT];
-    const float4 A0 = a.xyzq[blockIdx.y * PF_ATOMS];   // exists: tiles are non-empty
+    float ax[APT], ay[APT], az[APT], k1[APT], k2[APT], kq[APT],
+        kq3[APT];
+    int an[APT];
+    const float4 A0 = a.xyzq[blockIdx.y * ATOMS];   // exists: tiles are non-empty
 #pragma unroll
-    for (int u = 0; u < PF_APT; ++u) {
-        an[u] = blockIdx.y * PF_ATOMS + u * PF_THREADS + threadIdx.x;
+    for (int u = 0; u < APT; ++u) {
+        an[u] = blockIdx.y * ATOMS + u * PF_THREADS + threadIdx.x;
         if (an[u] < a.n) {
             const float4 A = a.xyzq[an[u]];
             const float4 F = a.fcoef[an[u]];
@@ -479,7 +488,7 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
     float alo[3], ahi[3];
     block_box(ax[0], ay[0], az[0], alo, ahi, s_box);
 #pragma unroll
-    for (int u = 1; u < PF_APT; ++u) {
+    for (int u = 1; u < APT; ++u) {
         float lo2[3], hi2[3];
         block_box(ax[u], ay[u], az[u], lo2, hi2, s_box);
 #pragma unroll
@@ -488,10 +497,10 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             ahi[c] = fmaxf(ahi[c], hi2[c]);
         }
     }
-    f2 ax2[PF_PAIRS], ay2[PF_PAIRS], az2[PF_PAIRS], c12[PF_PAIRS], c22[PF_PAIRS],
-        kq2[PF_PAIRS], nk32[PF_PAIRS];
+    f2 ax2[PAIRS], ay2[PAIRS], az2[PAIRS], c12[PAIRS], c22[PAIRS],
+        kq2[PAIRS], nk32[PAIRS];
 #pragma unroll
-    for (int pp = 0; pp < PF_PAIRS; ++pp) {
+    for (int pp = 0; pp < PAIRS; ++pp) {
         const int u = 2 * pp;
         ax2[pp] = pk2(ax[u], ax[u + 1]);
         ay2[pp] = pk2(ay[u], ay[u + 1]);
@@ -502,9 +511,9 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         nk32[pp] = pk2(-kq3[u], -kq3[u + 1]);
     }
     const f2 zero2 = pk2(0.f, 0.f);
-    double acc[PF_APT][3];
+    double acc[APT][3];
 #pragma unroll
-    for (int u = 0; u < PF_APT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = 0.0;
+    for (int u = 0; u < APT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = 0.0;
 
     const long long nyz = (long long)g.ny * g.nz;
     unsigned long long seen = 0;
@@ -570,15 +579,15 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         }
         __syncthreads();
         seen += (unsigned long long)tot;
-        f2 fx[PF_PAIRS], fy[PF_PAIRS], fz[PF_PAIRS];
+        f2 fx[PAIRS], fy[PAIRS], fz[PAIRS];
 #pragma unroll
-        for (int pp = 0; pp < PF_PAIRS; ++pp) fx[pp] = fy[pp] = fz[pp] = zero2;
+        for (int pp = 0; pp < PAIRS; ++pp) fx[pp] = fy[pp] = fz[pp] = zero2;
         if (clamp) {
 #pragma unroll 2
             for (int p = 0; p < tot; ++p) {
                 const CellPairs c = s_c[p];
 #pragma unroll
-                for (int pp = 0; pp < PF_PAIRS; ++pp)
+                for (int pp = 0; pp < PAIRS; ++pp)
                     force_pair2<true>(c, ax2[pp], ay2[pp], az2[pp], c12[pp], c22[pp], kq2[pp],
                                       nk32[pp], rmin2, fx[pp], fy[pp], fz[pp]);
             }
@@ -587,13 +596,13 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             for (int p = 0; p < tot; ++p) {
                 const CellPairs c = s_c[p];
 #pragma unroll
-                for (int pp = 0; pp < PF_PAIRS; ++pp)
+                for (int pp = 0; pp < PAIRS; ++pp)
                     force_pair2<false>(c, ax2[pp], ay2[pp], az2[pp], c12[pp], c22[pp], kq2[pp],
                                        nk32[pp], rmin2, fx[pp], fy[pp], fz[pp]);
             }
         }
 #pragma unroll
-        for (int pp = 0; pp < PF_PAIRS; ++pp) {
+        for (int pp = 0; pp < PAIRS; ++pp) {
             float f0, f1;
             upk2(fx[pp], f0, f1);
             acc[2 * pp][0] += (double)f0;
@@ -607,7 +616,7 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         }
     }
 #pragma unroll
-    for (int u = 0; u < PF_APT; ++u) {
+    for (int u = 0; u < APT; ++u) {
         if (an[u] < a.n) {
             double *o = part + ((long long)chunk * a.n + an[u]) * 3;
             o[0] = acc[u][0];
@@ -627,9 +636,12 @@ void launch_pair_force_grid(const GridDesc &g, const ForcePlan &fp,
     const long long G = (long long)g.nx * g.ny * g.nz;
     dim3 grid(fp.nchunk, fp.atom_tiles);
     count_launch();
-    k_pair_force_grid<<<grid, PF_THREADS, 0, st>>>(g, G, fp.chunk_len, chi, Ex,
-                                                   Ey, Ez, a, rmin2, part,
-                                                   nsolvent);
+    if (fp.apt == 2)
+        k_pair_force_grid<2><<<grid, PF_THREADS, 0, st>>>(g, G, fp.chunk_len, chi, Ex, Ey, Ez,
+                                                          a, rmin2, part, nsolvent);
+    else
+        k_pair_force_grid<4><<<grid, PF_THREADS, 0, st>>>(g, G, fp.chunk_len, chi, Ex, Ey, Ez,
+                                                          a, rmin2, part, nsolvent);
 }
 
 // Far-field nodes -> atoms: weighted points, all of them solvent.

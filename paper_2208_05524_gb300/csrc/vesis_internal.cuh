@@ -52,9 +52,10 @@ void count_launch(int n = 1);
 long long launch_count();
 
 // ---------------------------------------------------------------- pair.cu
+// pts: cells of a z-pencil per thread (4 or 8; equal sums either way)
 void launch_pair_energy_grid(const GridDesc &g, const AtomsDev &a, float rho,
                              float cfa, float rmin2, float *U, float *Ex,
-                             float *Ey, float *Ez, cudaStream_t st);
+                             float *Ey, float *Ez, int pts, cudaStream_t st);
 // Far-field nodes: pts[k] = (x, y, z, _); writes U, E per node and the
 // FP64 partial sums of w_k U_k per block into part (nblocks doubles).
 int point_energy_blocks(int np);
@@ -67,8 +68,9 @@ struct ForcePlan {
     int nchunk;
     long long chunk_len;
     int atom_tiles;
+    int apt;          // atoms per thread of the grid kernel (2 or 4)
 };
-ForcePlan plan_pair_force(long long G, int natoms, int nsm);
+ForcePlan plan_pair_force(long long G, int natoms, int nsm, int apt);
 void launch_pair_force_grid(const GridDesc &g, const ForcePlan &fp,
                             const uint8_t *chi, const float *Ex,
                             const float *Ey, const float *Ez,

@@ -133,7 +133,11 @@ def _confined_walk(rng, n, step, radius, min_dist, center, tries=100):
     pts[0] = center
     i = 1
     fails = 0
+    budget = 2000 * n + 100000        # regrowths before giving up
     while i < n:
+        budget -= 1
+        if budget < 0:
+            raise RuntimeError("confined walk found no room: the ball is too dense")
         prev = pts[i - 1]
         placed = False
         for _ in range(tries):
@@ -257,6 +261,46 @@ def two_domain_complex(n_per: int = 10000, n: int = 384, h: float = 0.4,
     return _system(xyz, sigma, eps, q, nn, hh, o,
                    {"kind": "tight", "d": sigma.copy()},
                    (bonds, np.full(len(bonds), 800.0), r0))
+
+
+def host_guest(index: int, seed: int = 1, h: float = 0.3, temperature: float = 298.0,
+               density: float = 0.05):
+    """System `index` (0..63) of the batched host-guest set: a host drawn
+    log-uniform in [150, 4000] atoms and a guest in [20, 80] atoms, both
+    confined random walks at the protein-like density; the guest's
+    confinement ball sits in a random direction, U[5, 15] A beyond the
+    host's.  The grid is the smallest multiple of 16 cells, at least 64, at
+    spacing h whose half-width covers every atom plus 8 A.  At h = 0.3 A
+    that is 160-320 cells per axis for indices 0..63 with seed 1 (a 4,000-
+    atom host alone spans about 54 A, and even the smallest pair with its
+    offset spans about 45 A).  Each system draws from its own stream spawned
+    from `seed`; net charge 0, tight initial surface."""
+    ss = np.random.SeedSequence(seed).spawn(index + 1)[index]
+    rng = np.random.Generator(np.random.PCG64(ss))
+    n_host = int(round(math.exp(rng.uniform(math.log(150.0), math.log(4000.0)))))
+    n_guest = int(rng.integers(20, 81))
+    offset = float(rng.uniform(5.0, 15.0))
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    ball = lambda m: max((3.0 * m / (4.0 * math.pi * density)) ** (1.0 / 3.0), 2.0 * 3.8)
+    dist = ball(n_host) + offset + ball(n_guest)
+    hx, hb, hr0, _ = globule(n_host, rng, density=density)
+    gx, gb, gr0, _ = globule(n_guest, rng, center=u * dist, density=density)
+    xyz = np.concatenate([hx, gx], axis=0)
+    lo, hi = xyz.min(axis=0), xyz.max(axis=0)
+    xyz -= 0.5 * (lo + hi)
+    need = float(np.abs(xyz).max()) + 8.0
+    n = 64
+    while 0.5 * n * h < need:
+        n += 16
+    bonds = np.concatenate([hb, gb + n_host], axis=0)
+    r0 = np.concatenate([hr0, gr0])
+    sigma, eps, q = _params(rng, n_host + n_guest, temperature, 0.0)
+    nn, hh, o = cubic_grid(n, h)
+    sysd = _system(xyz, sigma, eps, q, nn, hh, o, {"kind": "tight", "d": sigma.copy()},
+                   (bonds, np.full(len(bonds), 800.0), r0))
+    sysd.update(n_host=n_host, n_guest=n_guest)
+    return sysd
 
 
 def random_cluster(n_atoms: int, n: int, h: float, seed: int,

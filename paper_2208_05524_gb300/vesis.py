@@ -94,6 +94,11 @@ def lib():
         L.vesis_set_timing.argtypes = [_p, _i]
         L.vesis_get_timing.argtypes = [_p, C.POINTER(Timing)]
         L.vesis_surface_weights_noalloc.argtypes = [C.POINTER(Params), _p, _p, _p]
+        L.vesis_set_tiles.argtypes = [_p, _i, _i]
+        L.vesis_get_tiles.argtypes = [_p, C.POINTER(_i), C.POINTER(_i)]
+        L.vesis_autotune.argtypes = [_p, _p, _i, _p]
+        L.vesis_relax_batch.argtypes = [_i, _p, _p, _p, C.POINTER(RelaxOpts), _i, _i,
+                                        _p, _p]
         L.vesis_destroy.argtypes = [_p]
         L.vesis_last_error.restype = C.c_char_p
         _lib = L
@@ -293,6 +298,26 @@ class System:
         _check(lib().vesis_get_timing(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Timing._fields_}
 
+    def set_tiles(self, energy_pencil=8, force_atoms=4):
+        _check(lib().vesis_set_tiles(self.h, int(energy_pencil), int(force_atoms)))
+
+    def get_tiles(self):
+        pe, fa = _i(0), _i(0)
+        _check(lib().vesis_get_tiles(self.h, C.byref(pe), C.byref(fa)))
+        return pe.value, fa.value
+
+    def autotune(self, chi, reps=3):
+        """Times the pair kernels' tile shapes on this system and keeps the
+        fastest; returns the chosen shapes and the four mean times (ms)."""
+        import torch
+        t = (_d * 4)()
+        _check(lib().vesis_autotune(self.h, _dp(chi, torch.uint8, self.G), int(reps),
+                                    C.cast(t, _p)))
+        pe, fa = self.get_tiles()
+        return dict(energy_pencil=pe, force_atoms=fa,
+                    ms={"energy_pencil4": t[0], "energy_pencil8": t[1],
+                        "force_atoms2": t[2], "force_atoms4": t[3]})
+
     def relax(self, chi, xyz, **opts):
         import torch
         o = default_relax_opts(**opts)
@@ -305,3 +330,31 @@ class System:
         res["status"] = rc
         res["xyz"] = x
         return res
+
+
+def relax_batch(systems, chis, xyzs, threads=8, sweep_slots=2, **opts):
+    """vesis_relax_batch: relaxes every (system, chi, xyz) with the same
+    options on `threads` host threads; chi tensors are updated in place.
+    Returns one result dict per system, as System.relax does."""
+    import torch
+    n = len(systems)
+    if not (len(chis) == n and len(xyzs) == n):
+        raise ValueError("systems, chis and xyzs differ in length")
+    o = default_relax_opts(**opts)
+    hs = (_p * n)(*[s.h for s in systems])
+    cs = (_p * n)(*[_dp(c, torch.uint8, s.G) for s, c in zip(systems, chis)])
+    xs = [_np(x).reshape(-1, 3).copy() for x in xyzs]
+    xp = (_p * n)(*[_hp(x) for x in xs])
+    st = (RelaxStats * n)()
+    status = (_i * n)()
+    _check(lib().vesis_relax_batch(n, C.cast(hs, _p), C.cast(cs, _p), C.cast(xp, _p),
+                                   C.byref(o), int(threads), int(sweep_slots),
+                                   C.cast(st, _p), C.cast(status, _p)))
+    out = []
+    for i in range(n):
+        res = {f: getattr(st[i], f) for f, _ in RelaxStats._fields_ if f != "terms"}
+        res["terms"] = dict(zip(TERMS, list(st[i].terms)))
+        res["status"] = status[i]
+        res["xyz"] = xs[i]
+        out.append(res)
+    return out

@@ -115,3 +115,48 @@ def test_synthetic_inputs_are_seeded():
     assert np.all((a["sigma_sw"] >= 3.0) & (a["sigma_sw"] <= 4.0))
     c = synth.protein_like(n_atoms=300, n=32, seed=8)
     assert not np.array_equal(a["xyz"], c["xyz"])
+
+
+def test_batch_and_tile_argument_errors_without_device(built):
+    # checked before any CUDA call
+    from paper_2208_05524_gb300 import vesis
+    L = vesis.lib()
+    o = vesis.default_relax_opts()
+    assert L.vesis_relax_batch(0, None, None, None, C.byref(o), 4, 2, None, None) == 0
+    one = (C.c_void_p * 1)(None)
+    rc = L.vesis_relax_batch(1, C.cast(one, C.c_void_p), C.cast(one, C.c_void_p),
+                             C.cast(one, C.c_void_p), C.byref(o), 4, 2, None, None)
+    assert rc == -1 and b"NULL system" in L.vesis_last_error()
+    rc = L.vesis_relax_batch(1, C.cast(one, C.c_void_p), C.cast(one, C.c_void_p),
+                             C.cast(one, C.c_void_p), C.byref(o), 0, 2, None, None)
+    assert rc == -1 and b"threads" in L.vesis_last_error()
+    rc = L.vesis_relax_batch(1, C.cast(one, C.c_void_p), C.cast(one, C.c_void_p),
+                             C.cast(one, C.c_void_p), C.byref(o), 4, 0, None, None)
+    assert rc == -1 and b"sweep_slots" in L.vesis_last_error()
+    assert L.vesis_relax_batch(-1, None, None, None, None, 1, 1, None, None) == -1
+    assert L.vesis_set_tiles(None, 8, 4) == -1
+    assert L.vesis_get_tiles(None, None, None) == -1
+    assert L.vesis_autotune(None, None, 3, None) == -1
+
+
+def test_host_guest_set_follows_its_recipe():
+    from paper_2208_05524_gb300 import synth
+    a = synth.host_guest(5)
+    b = synth.host_guest(5)
+    for k in ("xyz", "sigma_sw", "q", "bonds"):
+        assert np.array_equal(a[k], b[k])
+    c = synth.host_guest(6)
+    assert not np.array_equal(a["xyz"][:20], c["xyz"][:20])
+    for s in (a, c):
+        assert 150 <= s["n_host"] <= 4000 and 20 <= s["n_guest"] <= 80
+        assert len(s["xyz"]) == s["n_host"] + s["n_guest"]
+        assert s["q"].sum() == pytest.approx(0.0, abs=1e-9)
+        n = int(s["n"][0])
+        assert np.all(s["n"] == n) and n % 16 == 0 and n >= 64
+        # every atom is at least 8 A inside the box
+        half = 0.5 * n * float(s["h"])
+        assert np.abs(s["xyz"]).max() + 8.0 <= half + 1e-9
+        # host and guest do not overlap: the closest pair is a bond apart or more
+        hx, gx = s["xyz"][:s["n_host"]], s["xyz"][s["n_host"]:]
+        d = np.sqrt(((hx[:, None, :] - gx[None, :, :]) ** 2).sum(-1)).min()
+        assert d > 3.0
