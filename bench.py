@@ -36,9 +36,9 @@ METRIC = "atom-grid pair-evals/s"
 # capture (profiles/pair_energy_grid_protein2000_grid256.md and
 # pair_force_grid_protein2000_grid256.md), valid only for the source they
 # were taken on: reported as null once pair.cu changes.
-TRAFFIC = {"sha256_16": "fff7eaaf2fa66493", "workload": "protein2000_grid256",
-           "pair_energy_grid": 762368 + 206455552,
-           "pair_force_grid": 1695993600 + 27971840}
+TRAFFIC = {"sha256_16": "948c03c5a61cc242", "workload": "protein2000_grid256",
+           "pair_energy_grid": 1024256 + 206256640,
+           "pair_force_grid": 855271168 + 52225024}
 # FP32 lane operations per energy pair in the inner loop of the pair kernel:
 # dz, r^2, r^-2, r^-3, r^-6, two LJ FMAs, Q r^-3, three field FMAs (the
 # reciprocal square root runs on the SFU and is not counted; the x/y parts of
@@ -528,9 +528,25 @@ def run_batch(args, world, rank, local):
     torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
     seq_chi = [c.cpu() for c in chis]
-    # batched form: autotuned shapes, all systems at once
+    # batched form: autotuned shapes (one system of median atom count per
+    # grid shape is timed, the others of that shape take its choice), all
+    # systems at once
     t0 = time.perf_counter()
-    tuned = [S.autotune(c, reps=2) for S, c in zip(systems, chis0)]
+    by_shape = {}
+    for i, S in enumerate(systems):
+        by_shape.setdefault(S.shape, []).append(i)
+    tuned = [None] * len(systems)
+    tune_ms = {"default": 0.0, "tuned": 0.0}
+    for shape, idx in by_shape.items():
+        idx = sorted(idx, key=lambda i: systems[i].n_atoms)
+        rep = idx[len(idx) // 2]
+        t = systems[rep].autotune(chis0[rep], reps=1)
+        tune_ms["default"] += t["ms"]["energy_pencil8"] + t["ms"]["force_atoms4"]
+        tune_ms["tuned"] += min(t["ms"]["energy_pencil4"], t["ms"]["energy_pencil8"]) + \
+            min(t["ms"]["force_atoms2"], t["ms"]["force_atoms4"])
+        for i in idx:
+            systems[i].set_tiles(t["energy_pencil"], t["force_atoms"])
+            tuned[i] = t
     torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
     chis = [c0.clone() for c0 in chis0]
@@ -559,6 +575,9 @@ def run_batch(args, world, rank, local):
            "sequential_s_per_system": seq_s / n, "batched_s_per_system": bat_s / n,
            "speedup": seq_s / bat_s, "identical_results": bool(same),
            "autotune_s": tune_s, "tile_shapes": shapes,
+           "autotune_timed_ms": {"default_shapes": tune_ms["default"],
+                                 "chosen_shapes": tune_ms["tuned"],
+                                 "systems_timed": len(by_shape)},
            "pair_evals": pairs, "pair_evals_per_s_batched": pairs / bat_s,
            "pair_evals_per_s_sequential": sum(r["pair_evals"] for r in seq) / seq_s,
            "atoms": int(sum(S.n_atoms for S in systems)),
@@ -568,6 +587,83 @@ def run_batch(args, world, rank, local):
         print(json.dumps(out), flush=True)
     for S in systems:
         S.close()
+
+
+def run_heap(args, world, rank, local):
+    """The paper's literal serial flipping (vesis_blsm_heap) on the single
+    ion (64^3, h = 0.25 A, from the 7 A sphere to the local minimum, U from
+    the GPU energy kernel): flips per second of the GPU form, the parallel
+    rule's time to the same state on the GPU, and the FP64 oracle's heap on
+    the host (the whole run).  Prints one JSON line of its own."""
+    import numpy as np
+    import torch
+
+    from paper_2208_05524_gb300 import synth, vesis
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sysd = synth.single_ion()
+    stream = torch.cuda.current_stream()
+    S = vesis.System(sysd, stream=stream)
+    G = S.G
+    U = torch.empty(G, dtype=torch.float32, device=dev)
+    E = torch.empty(3 * G, dtype=torch.float32, device=dev)
+    chi0 = torch.empty(G, dtype=torch.uint8, device=dev)
+    S.init_labels(chi0, "sphere", radius=sysd["init"]["radius"])
+    S.energy_field(U, E)
+    chi = torch.empty_like(chi0)
+
+    def timed(fn, k):
+        ts = []
+        for _ in range(k):
+            chi.copy_(chi0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts, r
+
+    for _ in range(args.warmup):
+        chi.copy_(chi0)
+        S.blsm_heap(chi, U, terms=False)
+    ts, r = timed(lambda: S.blsm_heap(chi, U, terms=False), args.steps)
+    heap_chi = chi.clone()
+    ts_p, rp = timed(lambda: S.blsm_relax(chi, U, terms=False), max(1, args.steps))
+    same = bool(torch.equal(chi, heap_chi))
+    ms = statistics.median(ts)
+    out = {"metric": "flips/s, literal serial flipping", "value": r["flips"] / (ms * 1e-3),
+           "unit": "flips/s", "higher_is_better": True, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "data": "synthetic", "dtype": "f64",
+           "config": {"workload": "single_ion_grid64",
+                      "desc": "single charged LJ atom, 64^3 grid, h=0.25 A, 7 A sphere start"},
+           "flips": r["flips"], "us_per_flip": ms * 1e3 / max(1, r["flips"]),
+           "roofline": {"bound": "latency", "kernel": "heap_run",
+                        "note": "one block; each flip is five dependent block-wide phases "
+                                "(top of the tournament, flip, window keys, tiles, groups)"},
+           "parallel_rule": {"ms": statistics.median(ts_p), "rounds": rp["rounds"],
+                             "flips": rp["flips"], "same_state_as_heap": same}}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O
+        p = O.params()
+        chi_h = chi0.cpu().numpy().reshape(S.shape)
+        U64 = U.cpu().numpy().astype(np.float64).reshape(S.shape)
+        sc = O.surface_constants(sysd, p)
+        t0 = time.perf_counter()
+        ro = O.blsm_heap(chi_h, U64, sc)
+        secs = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ro["flips"] / secs, "unit": "flips/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"the whole run, {ro['flips']} flips, FP64 C heap, "
+                                         f"{secs:.1f} s",
+                               "identical_labels": bool(np.array_equal(
+                                   chi_h.reshape(-1), heap_chi.cpu().numpy()))}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    S.close()
 
 
 def main():
@@ -583,6 +679,8 @@ def main():
     ap.add_argument("--converge", action="store_true",
                     help="time one converged relaxation instead of the step benchmark")
     ap.add_argument("--max-outer", type=int, default=0)
+    ap.add_argument("--heap", action="store_true",
+                    help="time the literal serial flipping on the single ion")
     ap.add_argument("--batch", action="store_true",
                     help="time the batched form on the host-guest set against the plain form")
     ap.add_argument("--batch-systems", type=int, default=64)
@@ -590,7 +688,9 @@ def main():
     ap.add_argument("--sweep-slots", type=int, default=2)
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    if args.batch:
+    if args.heap:
+        run_heap(args, world, rank, local)
+    elif args.batch:
         run_batch(args, world, rank, local)
     elif args.converge:
         run_converge(args, world, rank, local)

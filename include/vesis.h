@@ -208,6 +208,24 @@ int vesis_blsm_relax(vesis_system s, uint8_t *chi_dev, const float *U_dev,
                      long long *flips_out, double *dE_sum_out,
                      double *terms_out);
 
+/* The paper's literal serial flipping (Sec. 3.1, Steps 2.1-2.2) on the
+ * GPU: of the cells next to the interface (a face neighbour with the other
+ * label) with dE < 0, flip the one with the smallest dE (ties: smaller
+ * linear index), update w and dE in its kernel window and the candidate
+ * set, and repeat until no candidate has dE < 0 or max_flips flips were
+ * made.  The order is the min-heap's; the smallest key is kept in a
+ * tournament of 4^3 tiles and groups of 8^3 tiles, run by one block (the
+ * process is serial, so it runs at one flip every few microseconds, far
+ * slower than vesis_blsm_relax on large grids).  Same arguments as
+ * vesis_blsm_relax; max_flips >= 0.  The call also stops after 16 G + 1024
+ * flips: a guard against a cycle of flips whose FP64 dE rounds below zero.
+ * Outputs (each may be NULL): flips, the FP64 sum of the flipped cells' dE
+ * in flip order, terms[6] of the relaxed state.
+ * Returns VESIS_W_MAX_ROUNDS if max_flips stopped it. */
+int vesis_blsm_heap(vesis_system s, uint8_t *chi_dev, const float *U_dev,
+                    const float *E_dev, long long max_flips, long long *flips_out,
+                    double *dE_sum_out, double *terms_out);
+
 /* Gradient dG/dr_n of the total free energy with the interface fixed
  * (Eq. GradientG, taken as the exact derivative of the discrete energy):
  * grid term -h^3 sum over solvent cells, far-field term and G_ss.

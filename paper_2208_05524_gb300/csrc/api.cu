@@ -228,6 +228,8 @@ struct vesis_system_t {
     // persistent sweep state
     int sweep_blocks = 0, ntiles = 0;
     uint8_t *d_sweep = nullptr;
+    uint8_t *d_heap = nullptr;      // tile and group keys of the serial flipping
+    long long *d_heap_out = nullptr;   // flips, dE sum (as bits), capped
     unsigned *d_ctl = nullptr;
     int *d_err = nullptr, *d_rounds = nullptr, *d_capped = nullptr;
     unsigned long long *d_part_flips = nullptr;
@@ -883,6 +885,8 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     }
     s->ntiles = sweep_tiles(s->g);
     VTRY(dalloc(s, &s->d_sweep, sweep_state_bytes(s->g, s->kw.r)));
+    VTRY(dalloc(s, &s->d_heap, heap_state_bytes(s->g)));
+    VTRY(dalloc(s, &s->d_heap_out, 3));
     VTRY(dalloc(s, &s->d_ctl, sweep_ctl_words()));
     VTRY(dalloc(s, &s->d_err, 1));
     VTRY(dalloc(s, &s->d_rounds, 1));
@@ -1080,6 +1084,34 @@ int vesis_blsm_relax(vesis_system s, uint8_t *chi_dev, const float *U_dev,
     if (dE_sum_out) *dE_sum_out = rs.total_dE;
     if (terms_out) VTRY(vesis_energy_terms(s, chi_dev, U_dev, E_dev, terms_out));
     return rs.capped ? VESIS_W_MAX_ROUNDS : VESIS_OK;
+}
+
+int vesis_blsm_heap(vesis_system s, uint8_t *chi_dev, const float *U_dev,
+                    const float *E_dev, long long max_flips, long long *flips_out,
+                    double *dE_sum_out, double *terms_out)
+{
+    if (!s || !chi_dev || !U_dev) return fail(VESIS_E_ARG, "NULL argument");
+    if (max_flips < 0) return fail(VESIS_E_ARG, "max_flips must be >= 0");
+    // Each flip lowers the energy, so the process ends; the bound only
+    // guards against a cycle of flips whose FP64 dE rounds below zero.
+    const long long hard = 16 * s->G + 1024;
+    enq_conv(s, chi_dev, s->d_W);
+    long long *o = s->d_heap_out;
+    VCK(launch_heap(s->g, s->kw, s->d_k3, s->fc, chi_dev, s->d_W, U_dev, s->d_dE, s->d_heap,
+                    std::min(max_flips, hard), o, reinterpret_cast<double *>(o + 1),
+                    reinterpret_cast<int *>(o + 2), s->st));
+    VCK(cudaMemcpyAsync(s->h_scal, o, 3 * sizeof(long long), cudaMemcpyDeviceToHost, s->st));
+    VCK(cudaStreamSynchronize(s->st));
+    VTRY(last_launch("blsm_heap"));
+    long long h[3];
+    std::memcpy(h, s->h_scal, sizeof(h));
+    double dsum;
+    std::memcpy(&dsum, &h[1], sizeof(double));
+    const int capped = (int)(h[2] & 0xffffffffll);
+    if (flips_out) *flips_out = h[0];
+    if (dE_sum_out) *dE_sum_out = dsum;
+    if (terms_out) VTRY(vesis_energy_terms(s, chi_dev, U_dev, E_dev, terms_out));
+    return capped ? VESIS_W_MAX_ROUNDS : VESIS_OK;
 }
 
 int vesis_atom_forces(vesis_system s, const uint8_t *chi_dev, const double *xyz,

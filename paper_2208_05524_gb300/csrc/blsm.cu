@@ -388,36 +388,6 @@ k_conv3(GridDesc g, int R, const int *__restrict__ k3, const uint8_t *__restrict
     W[p] = s;
 }
 
-// Face neighbour with the other label; outside the box counts as solvent.
-__device__ __forceinline__ bool is_candidate(const GridDesc &g,
-                                             const uint8_t *__restrict__ chi,
-                                             long long p, int i, int j, int k,
-                                             long long nyz)
-{
-    const uint8_t c = chi[p];
-    const uint8_t xm = (i > 0) ? chi[p - nyz] : 0;
-    const uint8_t xp = (i < g.nx - 1) ? chi[p + nyz] : 0;
-    const uint8_t ym = (j > 0) ? chi[p - g.nz] : 0;
-    const uint8_t yp = (j < g.ny - 1) ? chi[p + g.nz] : 0;
-    const uint8_t zm = (k > 0) ? chi[p - 1] : 0;
-    const uint8_t zp = (k < g.nz - 1) ? chi[p + 1] : 0;
-    return (xm != c) | (xp != c) | (ym != c) | (yp != c) | (zm != c) | (zp != c);
-}
-
-// dE of Eq. (dGj1/dGj2): c [s (1 - 2w) - g0] - s h^3 U with w = W / S and
-// g0 = k0 / S is cN N - s h^3 U for the exact integer N = s (S - 2W) - k0
-// and cN = c / S; both products are rounded once and the sum once (no
-// contraction).
-__device__ __forceinline__ double flip_dE(uint8_t chi_j, unsigned W, float U,
-                                          const FlipConst &fc)
-{
-    const int base = fc.S - 2 * (int)W;
-    const int N = (chi_j ? -base : base) - fc.k0;
-    const double t1 = __dmul_rn(fc.cN, (double)N);
-    const double t2 = __dmul_rn(fc.h3, (double)U);
-    return __dadd_rn(t1, chi_j ? t2 : -t2);
-}
-
 __global__ void k_flip_energy(GridDesc g, const uint32_t *__restrict__ W,
                               const uint8_t *__restrict__ chi,
                               const float *__restrict__ U, FlipConst fc,

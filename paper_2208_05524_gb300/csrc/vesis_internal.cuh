@@ -110,6 +110,36 @@ struct FlipConst {
     double cN, h3;
     int S, k0;
 };
+// Face neighbour with the other label; outside the box counts as solvent.
+__device__ __forceinline__ bool is_candidate(const GridDesc &g,
+                                             const uint8_t *__restrict__ chi,
+                                             long long p, int i, int j, int k,
+                                             long long nyz)
+{
+    const uint8_t c = chi[p];
+    const uint8_t xm = (i > 0) ? chi[p - nyz] : 0;
+    const uint8_t xp = (i < g.nx - 1) ? chi[p + nyz] : 0;
+    const uint8_t ym = (j > 0) ? chi[p - g.nz] : 0;
+    const uint8_t yp = (j < g.ny - 1) ? chi[p + g.nz] : 0;
+    const uint8_t zm = (k > 0) ? chi[p - 1] : 0;
+    const uint8_t zp = (k < g.nz - 1) ? chi[p + 1] : 0;
+    return (xm != c) | (xp != c) | (ym != c) | (yp != c) | (zm != c) | (zp != c);
+}
+
+// dE of Eq. (dGj1/dGj2): c [s (1 - 2w) - g0] - s h^3 U with w = W / S and
+// g0 = k0 / S is cN N - s h^3 U for the exact integer N = s (S - 2W) - k0
+// and cN = c / S; both products are rounded once and the sum once (no
+// contraction).
+__device__ __forceinline__ double flip_dE(uint8_t chi_j, unsigned W, float U,
+                                          const FlipConst &fc)
+{
+    const int base = fc.S - 2 * (int)W;
+    const int N = (chi_j ? -base : base) - fc.k0;
+    const double t1 = __dmul_rn(fc.cN, (double)N);
+    const double t2 = __dmul_rn(fc.h3, (double)U);
+    return __dadd_rn(t1, chi_j ? t2 : -t2);
+}
+
 void launch_flip_energy(const GridDesc &g, const uint32_t *W,
                         const uint8_t *chi, const float *U, const FlipConst &fc,
                         double *dE, uint8_t *cand, cudaStream_t st);
@@ -143,6 +173,14 @@ size_t sweep_state_bytes(const GridDesc &g, int r);
 // err: 1 int, part_*: `blocks` entries; k3: the full stencil (device,
 // (2 kw.r + 1)^3, centred) or NULL for the product kernel kw.q; writes the
 // totals into *rs.
+// The literal serial flipping (heap.cu): key = G doubles of scratch,
+// state = heap_state_bytes(g) bytes; the counts land in flips_out,
+// dsum_out and capped_out (device).
+size_t heap_state_bytes(const GridDesc &g);
+cudaError_t launch_heap(const GridDesc &g, const KernelW &kw, const int *k3,
+                        const FlipConst &fc, uint8_t *chi, uint32_t *W, const float *U,
+                        double *key, void *state, long long max_flips, long long *flips_out,
+                        double *dsum_out, int *capped_out, cudaStream_t st);
 cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
                          const FlipConst &fc,
                          uint8_t *chi, uint32_t *W, const float *U,

@@ -89,6 +89,8 @@ def lib():
         L.vesis_blsm_relax.argtypes = [_p, _p, _p, _p, _i, C.POINTER(_i),
                                        C.POINTER(_ll), C.POINTER(_d), _p]
         L.vesis_atom_forces.argtypes = [_p, _p, _p, _p, _p, _p]
+        L.vesis_blsm_heap.argtypes = [_p, _p, _p, _p, _ll, C.POINTER(_ll), C.POINTER(_d),
+                                      _p]
         L.vesis_relax.argtypes = [_p, _p, _p, C.POINTER(RelaxOpts),
                                   C.POINTER(RelaxStats)]
         L.vesis_set_timing.argtypes = [_p, _i]
@@ -275,6 +277,21 @@ class System:
             C.cast(out, _p) if out is not None else None))
         r = dict(status=rc, rounds=rounds.value, flips=flips.value,
                  dE_sum=dsum.value)
+        if out is not None:
+            r["terms"] = dict(zip(TERMS, list(out)))
+        return r
+
+    def blsm_heap(self, chi, U, E=None, max_flips=1 << 62, terms=True):
+        """The literal serial flipping (vesis_blsm_heap)."""
+        import torch
+        flips, dsum = _ll(0), _d(0.0)
+        out = (_d * 6)() if terms else None
+        rc = _check(lib().vesis_blsm_heap(
+            self.h, _dp(chi, torch.uint8, self.G), _dp(U, torch.float32, self.G),
+            _dp(E, torch.float32, 3 * self.G) if E is not None else None,
+            int(max_flips), C.byref(flips), C.byref(dsum),
+            C.cast(out, _p) if out is not None else None))
+        r = dict(status=rc, flips=flips.value, dE_sum=dsum.value)
         if out is not None:
             r["terms"] = dict(zip(TERMS, list(out)))
         return r

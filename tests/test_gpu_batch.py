@@ -29,12 +29,12 @@ def _dev(a, dtype):
 
 
 def _cluster():
-    # 700 atoms: ragged atom tiles for 256 and 512 atoms per block; nz = 29
+    # 700 atoms: ragged atom tiles for 256 and 512 atoms per block; nz = 53
     # leaves a ragged pencil for both 4 and 8 cells per thread
-    s = synth.random_cluster(700, 8, 0.5, seed=11, net_charge=-2.0)
-    n = (40, 36, 29)
+    s = synth.random_cluster(700, 8, 0.7, seed=11, net_charge=-2.0)
+    n = (54, 52, 53)
     s["n"] = np.array(n)
-    s["origin"] = -0.5 * np.array(n) * 0.5
+    s["origin"] = -0.5 * np.array(n) * 0.7
     return s
 
 
