@@ -285,6 +285,65 @@ int vesis_relax_batch(int nsys, vesis_system *systems, uint8_t *const *chi_dev,
                       int threads, int sweep_slots, vesis_relax_stats *stats_out,
                       int *status_out);
 
+/* ------------------------------------------------------------------------
+ * Learned initialiser.  The paper starts the flips from a tight or a loose
+ * surface (Sec. 3.1, "Initial surfaces"); this library can instead start
+ * from the guess of a small 3-D U-Net of the relaxed labels, after which
+ * the unchanged flip sweep finishes (so the sweep is both the fallback and
+ * the measure of the guess's error).  Network: channels 32, 64, 128, 128 on
+ * four levels (full, 1/2, 1/4, 1/8 resolution), one 3x3x3 conv + ReLU per
+ * level and per decoder level, 2x2x2 mean pooling, nearest doubling with
+ * skip concatenation, 1x1x1 head giving the logit of chi = 1; loss the mean
+ * binary cross entropy.  BF16 weights and activations, FP32 accumulation
+ * on the tensor cores; FP32 master weights trained by Adam.
+ *
+ * Features (vesis_features): three FP32 planes of the grid, in this order:
+ * asinh((U - C|E|^2) / scale) (the vdW part of the energy density),
+ * asinh(C|E|^2 / scale) (the CFA part), and the tight-surface labels (the
+ * atom-density indicator: 1 within sigma_i of an atom).
+ *
+ * Parameters: one flat FP32 vector, layer by layer (e0, e1, e2, e3, d2,
+ * d1, d0, head), each W[cout][cin][3][3][3] (1x1x1 for the head) then
+ * b[cout]; cin of e0 = n_features, of d2/d1/d0 = skip + coarse channels. */
+typedef struct vesis_net_t *vesis_net;
+
+/* Creates a network for n_features (1..32) input planes with all
+ * parameters zero; work goes on cuda_stream (NULL = legacy default). */
+int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out);
+int vesis_net_param_count(vesis_net n, long long *count);
+/* Host FP32 parameter vectors (param_count floats); set clears Adam's
+ * moments and step. */
+int vesis_net_set_params(vesis_net n, const float *theta);
+int vesis_net_get_params(vesis_net n, float *theta);
+
+/* Logits of a crop of a grid.  x_dev: n_features FP32 planes of the whole
+ * NX x NY x NZ grid (plane-major, cell index (i*NY + j)*NZ + k).  crop:
+ * {ox, oy, oz, cx, cy, cz} (each cx, cy, cz a positive multiple of 8,
+ * inside the grid) or NULL for the whole grid (then NX, NY, NZ must be
+ * multiples of 8).  logit_dev: cx*cy*cz floats or NULL; chi_dev: the same
+ * number of bytes, the guess chi = [logit > 0], or NULL. */
+int vesis_net_forward(vesis_net n, const float *x_dev, int NX, int NY, int NZ,
+                      const int *crop, float *logit_dev, uint8_t *chi_dev);
+
+/* Loss (mean binary cross entropy against chi_dev, the labels of the whole
+ * grid, read in the crop) and its gradient with respect to the parameters,
+ * kept for vesis_net_adam_step and copied to grad_host (param_count floats)
+ * if it is not NULL. */
+int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
+                        int NX, int NY, int NZ, const int *crop, double *loss_out,
+                        float *grad_host);
+
+/* One Adam step with the last gradient (bias-corrected moments). */
+int vesis_net_adam_step(vesis_net n, double lr, double beta1, double beta2, double eps);
+int vesis_net_destroy(vesis_net n);
+
+/* Features of the learned initialiser for a system: U_dev and E_dev from
+ * vesis_energy_field at the current positions, chi_tight_dev the tight
+ * labels (vesis_init_labels kind 1); x_dev: 3 x G floats, written.
+ * scale > 0 (kBT/A^3). */
+int vesis_features(vesis_system s, const float *U_dev, const float *E_dev,
+                   const uint8_t *chi_tight_dev, double scale, float *x_dev);
+
 /* Device time of the hot kernels, measured with CUDA events recorded on the
  * system's stream around each launch while timing is enabled. */
 typedef struct {

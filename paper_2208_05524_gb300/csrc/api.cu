@@ -1114,6 +1114,17 @@ int vesis_blsm_heap(vesis_system s, uint8_t *chi_dev, const float *U_dev,
     return capped ? VESIS_W_MAX_ROUNDS : VESIS_OK;
 }
 
+int vesis_features(vesis_system s, const float *U_dev, const float *E_dev,
+                   const uint8_t *chi_tight_dev, double scale, float *x_dev)
+{
+    if (!s || !U_dev || !E_dev || !chi_tight_dev || !x_dev) return fail(VESIS_E_ARG, "NULL argument");
+    if (!(scale > 0.0)) return fail(VESIS_E_ARG, "scale must be > 0");
+    launch_features(U_dev, E_dev, s->G, chi_tight_dev, (float)s->cfa, (float)scale, x_dev, s->st);
+    VTRY(last_launch("features"));
+    VCK(cudaStreamSynchronize(s->st));
+    return VESIS_OK;
+}
+
 int vesis_atom_forces(vesis_system s, const uint8_t *chi_dev, const double *xyz,
                       const float *E_dev, double *grad_out, double *energy_out)
 {

@@ -1,0 +1,1049 @@
+// Learned initialiser: a 3-D U-Net that guesses the relaxed labels from
+// atom-density and CFA-field features, so that the flip sweep starts near
+// its end (it always finishes from the guess).  The paper starts from tight
+// or loose surfaces (Sec. 3.1, "Initial surfaces"); this network is an
+// alternative start, trained on label fields that the plain method relaxes.
+//
+// Network (channels 32, 64, 128, 128; grid dimensions multiples of 8):
+//   e0 = relu(conv3(x))            e1 = relu(conv3(pool(e0)))
+//   e2 = relu(conv3(pool(e1)))     e3 = relu(conv3(pool(e2)))
+//   d2 = relu(conv3([e2, up(e3)])) d1 = relu(conv3([e1, up(d2)]))
+//   d0 = relu(conv3([e0, up(d1)])) z  = conv1(d0)
+// with 3x3x3 zero-padded cross-correlations, 2x2x2 mean pooling, nearest
+// doubling (read in place: the coarse input of a decoder conv is indexed at
+// half the fine coordinates) and channel concatenation (two input tensors).
+//
+// Storage: activations channels-last (cell-major, channels contiguous) in
+// bfloat16; weights bfloat16 [tap][cout][cin] for the forward pass and
+// [tap][cin][cout] with flipped taps for the input gradient; FP32 master
+// weights, gradients and Adam moments in one flat vector.  The convolutions
+// are implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16 in, FP32
+// accumulate); the rest are plain elementwise and reduction kernels.
+#include <cuda_bf16.h>
+
+#include "vesis_internal.cuh"
+
+namespace vesis {
+namespace unet {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kLevels = 4;
+constexpr int kCh[kLevels] = {32, 64, 128, 128};
+constexpr int kInPad = 32;       // input features padded to 32 channels
+
+// ------------------------------------------------------------ mma helpers
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4],
+                                         const unsigned (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned ld_s32(const bf16 *p)
+{
+    return *reinterpret_cast<const unsigned *>(p);
+}
+
+// ------------------------------------------------------------ convolution
+// Implicit GEMM: M = cells (64 per block), N = output channels (BN per
+// block), K = 27 taps x input channels in chunks of 32.  The input is the
+// concatenation of A (Ca channels at the output's resolution) and B (Cb
+// channels at half of it, read at half the coordinates).
+struct ConvArgs {
+    int nx, ny, nz;
+    long long V;
+    const bf16 *A;
+    int Ca;
+    const bf16 *B;
+    int Cb;
+    const bf16 *Wt;      // [27][Cout][Cin]
+    const float *bias;   // Cout or NULL
+    int Cout;
+    void *Y;             // bf16 [V][Cout] (relu) or float [V][Cout]
+};
+
+constexpr int CM = 64;          // cells per block
+constexpr int CK = 32;          // input channels per stage
+constexpr int SROW = CK + 8;    // padded smem row (conflict-free fragment loads)
+
+template <int BN, bool RAW>
+__global__ void __launch_bounds__(128) k_conv(ConvArgs P)
+{
+    __shared__ __align__(16) bf16 sA[CM][SROW];
+    __shared__ __align__(16) bf16 sB[BN][SROW];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int g = lane >> 2, tq = lane & 3;
+    const long long v0 = (long long)blockIdx.x * CM;
+    const int co0 = blockIdx.y * BN;
+    const int Cin = P.Ca + P.Cb;
+    const long long nyz = (long long)P.ny * P.nz;
+    const int hy = P.ny >> 1, hz = P.nz >> 1;
+    // the cell this thread stages
+    const int row = t >> 1, half = t & 1;
+    const long long v = v0 + row;
+    int ci = 0, cj = 0, ck = 0;
+    if (v < P.V) {
+        ci = (int)(v / nyz);
+        const long long rem = v - (long long)ci * nyz;
+        cj = (int)(rem / P.nz);
+        ck = (int)(rem - (long long)cj * P.nz);
+    }
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int n = 0; n < BN / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+
+    for (int tap = 0; tap < 27; ++tap) {
+        const int da = tap / 9 - 1, db = (tap / 3) % 3 - 1, dc = tap % 3 - 1;
+        const int ii = ci + da, jj = cj + db, kk = ck + dc;
+        const bool inside = v < P.V && ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny &&
+                            kk >= 0 && kk < P.nz;
+        for (int c0 = 0; c0 < Cin; c0 += CK) {
+            uint4 x0 = make_uint4(0, 0, 0, 0), x1 = x0;
+            if (inside) {
+                const bf16 *src;
+                if (c0 < P.Ca)
+                    src = P.A + ((long long)ii * nyz + (long long)jj * P.nz + kk) * P.Ca + c0;
+                else
+                    src = P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) * P.Cb +
+                          (c0 - P.Ca);
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(src + half * 16);
+                x0 = s4[0];
+                x1 = s4[1];
+            }
+            uint4 *d4 = reinterpret_cast<uint4 *>(&sA[row][half * 16]);
+            d4[0] = x0;
+            d4[1] = x1;
+            if (t < 2 * BN) {
+                const bf16 *src = P.Wt + ((long long)tap * P.Cout + co0 + row) * Cin + c0 + half * 16;
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+                uint4 *e4 = reinterpret_cast<uint4 *>(&sB[row][half * 16]);
+                e4[0] = s4[0];
+                e4[1] = s4[1];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int ks = 0; ks < CK; ks += 16) {
+                unsigned a[4];
+                const int r0 = w * 16 + g;
+                a[0] = ld_s32(&sA[r0][ks + 2 * tq]);
+                a[1] = ld_s32(&sA[r0 + 8][ks + 2 * tq]);
+                a[2] = ld_s32(&sA[r0][ks + 8 + 2 * tq]);
+                a[3] = ld_s32(&sA[r0 + 8][ks + 8 + 2 * tq]);
+#pragma unroll
+                for (int n = 0; n < BN / 8; ++n) {
+                    unsigned b[2];
+                    b[0] = ld_s32(&sB[n * 8 + g][ks + 2 * tq]);
+                    b[1] = ld_s32(&sB[n * 8 + g][ks + 8 + 2 * tq]);
+                    mma_bf16(acc[n], a, b);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // epilogue: rows w*16 + g (+8), columns n*8 + 2 tq (+1)
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const long long vo = v0 + w * 16 + g + hh * 8;
+        if (vo >= P.V) continue;
+#pragma unroll
+        for (int n = 0; n < BN / 8; ++n) {
+            const int co = co0 + n * 8 + 2 * tq;
+            float y0 = acc[n][2 * hh], y1 = acc[n][2 * hh + 1];
+            if (RAW) {
+                float2 *dst = reinterpret_cast<float2 *>(static_cast<float *>(P.Y) + vo * P.Cout + co);
+                *dst = make_float2(y0, y1);
+            } else {
+                y0 = fmaxf(y0 + P.bias[co], 0.f);
+                y1 = fmaxf(y1 + P.bias[co + 1], 0.f);
+                __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(
+                    static_cast<bf16 *>(P.Y) + vo * P.Cout + co);
+                *dst = __floats2bfloat162_rn(y0, y1);
+            }
+        }
+    }
+}
+
+// Weight gradient of a conv3: dW[tap][co][ci] += sum over cells v of
+// dZ[v][co] X[v + tap][ci] (X the concatenated input).  M = co (64 per
+// block), N = ci (32 per block), K = cells in stages of 32, split over
+// blocks of WG_CELLS cells and summed with atomics.
+struct WgradArgs {
+    int nx, ny, nz;
+    long long V;
+    const bf16 *A;
+    int Ca;
+    const bf16 *B;
+    int Cb;
+    const bf16 *dZ;      // [V][Cout]
+    int Cout;
+    float *dW;           // [27][Cout][Cin]
+    long long cells_per_block;
+};
+
+constexpr int WK = 32;           // cells per stage
+constexpr int WROW = WK + 8;
+
+__global__ void __launch_bounds__(128) k_wgrad(WgradArgs P)
+{
+    __shared__ __align__(16) bf16 sZ[64][WROW];   // [co][cell]
+    __shared__ __align__(16) bf16 sX[32][WROW];   // [ci][cell]
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int g = lane >> 2, tq = lane & 3;
+    const int Cin = P.Ca + P.Cb;
+    const int nci = Cin / 32;
+    const int tap = blockIdx.y / nci, ci0 = (blockIdx.y % nci) * 32;
+    const int co0 = blockIdx.z * 64;
+    const int da = tap / 9 - 1, db = (tap / 3) % 3 - 1, dc = tap % 3 - 1;
+    const long long nyz = (long long)P.ny * P.nz;
+    const int hy = P.ny >> 1, hz = P.nz >> 1;
+    const long long vb = (long long)blockIdx.x * P.cells_per_block;
+    const long long ve = min(vb + P.cells_per_block, P.V);
+    float acc[4][4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    const int r = t >> 2, q = t & 3;     // staged cell and quarter
+    for (long long s0 = vb; s0 < ve; s0 += WK) {
+        const long long v = s0 + r;
+        // dZ[v][co0 + 16q .. +16] -> sZ[.][r] (zero beyond Cout when Cout = 32)
+        {
+            __align__(16) bf16 z[16];
+            if (v < ve && co0 + q * 16 < P.Cout) {
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(P.dZ + v * P.Cout + co0 + q * 16);
+                reinterpret_cast<uint4 *>(z)[0] = s4[0];
+                reinterpret_cast<uint4 *>(z)[1] = s4[1];
+            } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) z[e] = __float2bfloat16(0.f);
+            }
+#pragma unroll
+            for (int e = 0; e < 16; ++e) sZ[q * 16 + e][r] = z[e];
+        }
+        // X[v + tap][ci0 + 8q .. +8] -> sX[.][r]
+        {
+            __align__(16) bf16 x[8];
+            bool ok = false;
+            long long src = 0;
+            int ii = 0, jj = 0, kk = 0;
+            if (v < ve) {
+                const int i = (int)(v / nyz);
+                const long long rem = v - (long long)i * nyz;
+                const int j = (int)(rem / P.nz);
+                const int k = (int)(rem - (long long)j * P.nz);
+                ii = i + da;
+                jj = j + db;
+                kk = k + dc;
+                ok = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz;
+            }
+            if (ok) {
+                const int c = ci0 + q * 8;
+                const bf16 *p;
+                if (c < P.Ca) {
+                    src = (long long)ii * nyz + (long long)jj * P.nz + kk;
+                    p = P.A + src * P.Ca + c;
+                } else {
+                    src = ((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1);
+                    p = P.B + src * P.Cb + (c - P.Ca);
+                }
+                reinterpret_cast<uint4 *>(x)[0] = *reinterpret_cast<const uint4 *>(p);
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = __float2bfloat16(0.f);
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sX[q * 8 + e][r] = x[e];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < WK; ks += 16) {
+            unsigned a[4];
+            const int r0 = w * 16 + g;
+            a[0] = ld_s32(&sZ[r0][ks + 2 * tq]);
+            a[1] = ld_s32(&sZ[r0 + 8][ks + 2 * tq]);
+            a[2] = ld_s32(&sZ[r0][ks + 8 + 2 * tq]);
+            a[3] = ld_s32(&sZ[r0 + 8][ks + 8 + 2 * tq]);
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+                unsigned b[2];
+                b[0] = ld_s32(&sX[n * 8 + g][ks + 2 * tq]);
+                b[1] = ld_s32(&sX[n * 8 + g][ks + 8 + 2 * tq]);
+                mma_bf16(acc[n], a, b);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const int co = co0 + w * 16 + g + hh * 8;
+        if (co >= P.Cout) continue;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const int ci = ci0 + n * 8 + 2 * tq;
+            float *d = P.dW + ((long long)tap * P.Cout + co) * Cin + ci;
+            atomicAdd(d, acc[n][2 * hh]);
+            atomicAdd(d + 1, acc[n][2 * hh + 1]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ small kernels
+// x (F planes of the full grid NX x NY x NZ, FP32) cropped at (ox, oy, oz)
+// to nx x ny x nz -> X0 [cell][32] bf16, channels >= F zero.
+__global__ void k_pack_input(const float *__restrict__ x, int F, int NX, int NY, int NZ,
+                             int ox, int oy, int oz, int nx, int ny, int nz,
+                             bf16 *__restrict__ X0)
+{
+    const long long V = (long long)nx * ny * nz;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= V * kInPad) return;
+    const long long v = e / kInPad;
+    const int c = (int)(e - v * kInPad);
+    float val = 0.f;
+    if (c < F) {
+        const int i = (int)(v / ((long long)ny * nz));
+        const int j = (int)((v / nz) % ny);
+        const int k = (int)(v % nz);
+        const long long G = (long long)NX * NY * NZ;
+        val = x[c * G + ((long long)(i + ox) * NY + (j + oy)) * NZ + (k + oz)];
+    }
+    X0[e] = __float2bfloat16(val);
+}
+
+// 2x2x2 mean pooling of [cell][C] bf16 at (nx, ny, nz) -> half resolution.
+__global__ void k_pool(const bf16 *__restrict__ X, int nx, int ny, int nz, int C,
+                       bf16 *__restrict__ Y)
+{
+    const int hx = nx >> 1, hy = ny >> 1, hz = nz >> 1;
+    const long long n = (long long)hx * hy * hz * C;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const long long u = e / C;
+    const int c = (int)(e - u * C);
+    const int i = (int)(u / ((long long)hy * hz)), j = (int)((u / hz) % hy), k = (int)(u % hz);
+    float s = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const long long v = ((long long)(2 * i + (d >> 2)) * ny + 2 * j + ((d >> 1) & 1)) * nz +
+                            2 * k + (d & 1);
+        s += __bfloat162float(X[v * C + c]);
+    }
+    Y[e] = __float2bfloat16(s * 0.125f);
+}
+
+// Head and loss: z = bh + sum_c Wh[c] d0[v][c]; with labels, the binary
+// cross entropy of sigmoid(z) and its gradient dz = (sigmoid(z) - y) / N.
+__global__ void __launch_bounds__(256) k_head(const bf16 *__restrict__ D0, long long V,
+                                              const float *__restrict__ Wh,
+                                              const float *__restrict__ bh,
+                                              const uint8_t *__restrict__ chi, int NX, int NY,
+                                              int NZ, int ox, int oy, int oz, int ny, int nz,
+                                              float *__restrict__ z_out, float *__restrict__ dz,
+                                              double *__restrict__ loss_part)
+{
+    __shared__ double s_l[8];
+    const long long v = (long long)blockIdx.x * 256 + threadIdx.x;
+    double l = 0.0;
+    if (v < V) {
+        float z = *bh;
+        const __nv_bfloat162 *p = reinterpret_cast<const __nv_bfloat162 *>(D0 + v * 32);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float2 f = __bfloat1622float2(p[c]);
+            z = fmaf(Wh[2 * c], f.x, z);
+            z = fmaf(Wh[2 * c + 1], f.y, z);
+        }
+        if (z_out) z_out[v] = z;
+        if (chi) {
+            const int i = (int)(v / ((long long)ny * nz)), j = (int)((v / nz) % ny),
+                      k = (int)(v % nz);
+            const float y = chi[((long long)(i + ox) * NY + (j + oy)) * NZ + (k + oz)] ? 1.f : 0.f;
+            const double zd = z;
+            l = fmax(zd, 0.0) - zd * y + log1p(exp(-fabs(zd)));
+            const float sg = 1.f / (1.f + __expf(-z));
+            dz[v] = (sg - y) / (float)V;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) s_l[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0 && loss_part) {
+        double s = 0.0;
+        for (int q = 0; q < 8; ++q) s += s_l[q];
+        loss_part[blockIdx.x] = s;
+    }
+}
+
+// Head backward: g0[v][c] = Wh[c] dz[v] (FP32), dWh[c] += sum_v d0[v][c] dz[v],
+// dbh += sum_v dz[v].
+__global__ void __launch_bounds__(256) k_head_bwd(const bf16 *__restrict__ D0, long long V,
+                                                  const float *__restrict__ Wh,
+                                                  const float *__restrict__ dz,
+                                                  float *__restrict__ g0, float *__restrict__ dWh)
+{
+    __shared__ float s_w[33][8];
+    const long long v = (long long)blockIdx.x * 256 + threadIdx.x;
+    float pw[33];
+#pragma unroll
+    for (int c = 0; c < 33; ++c) pw[c] = 0.f;
+    if (v < V) {
+        const float d = dz[v];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            g0[v * 32 + c] = Wh[c] * d;
+            pw[c] = __bfloat162float(D0[v * 32 + c]) * d;
+        }
+        pw[32] = d;
+    }
+#pragma unroll
+    for (int c = 0; c < 33; ++c) {
+        float s = pw[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) s_w[c][threadIdx.x >> 5] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 33) {
+        float s = 0.f;
+        for (int q = 0; q < 8; ++q) s += s_w[threadIdx.x][q];
+        atomicAdd(dWh + threadIdx.x, s);
+    }
+}
+
+// dZ = bf16(g * [y > 0]) for a relu layer's output y; db[c] += sum_v dZ.
+__global__ void __launch_bounds__(256) k_relu_bwd(const float *__restrict__ gsum,
+                                                  const bf16 *__restrict__ y, long long V, int C,
+                                                  bf16 *__restrict__ dZ, float *__restrict__ db)
+{
+    // each block covers 256 / C cells x C channels per pass
+    extern __shared__ float s_db[];
+    for (int c = threadIdx.x; c < C; c += 256) s_db[c] = 0.f;
+    __syncthreads();
+    const long long n = V * C;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < n;
+         e += (long long)gridDim.x * 256) {
+        const float yv = __bfloat162float(y[e]);
+        const bf16 d = __float2bfloat16(yv > 0.f ? gsum[e] : 0.f);
+        dZ[e] = d;
+        atomicAdd(&s_db[(int)(e % C)], __bfloat162float(d));
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += 256) atomicAdd(db + c, s_db[c]);
+}
+
+// From the input gradient dX [v][Ca + Cb] (FP32) of a decoder conv: the
+// skip part is added into accA [v][Ca]; the coarse part, summed over the
+// 2x2x2 cells that read each coarse cell, is written to gB [u][Cb].
+__global__ void k_split_skip(const float *__restrict__ dX, long long V, int Ca, int Cb,
+                             float *__restrict__ accA)
+{
+    const long long n = V * Ca;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const long long v = e / Ca;
+    const int c = (int)(e - v * Ca);
+    accA[e] += dX[v * (Ca + Cb) + c];
+}
+
+__global__ void k_split_coarse(const float *__restrict__ dX, int nx, int ny, int nz, int Ca,
+                               int Cb, float *__restrict__ gB)
+{
+    const int hx = nx >> 1, hy = ny >> 1, hz = nz >> 1;
+    const long long n = (long long)hx * hy * hz * Cb;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const long long u = e / Cb;
+    const int c = (int)(e - u * Cb);
+    const int i = (int)(u / ((long long)hy * hz)), j = (int)((u / hz) % hy), k = (int)(u % hz);
+    float s = 0.f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const long long v = ((long long)(2 * i + (d >> 2)) * ny + 2 * j + ((d >> 1) & 1)) * nz +
+                            2 * k + (d & 1);
+        s += dX[v * (Ca + Cb) + Ca + c];
+    }
+    gB[e] = s;
+}
+
+// acc[v][c] += dP[parent(v)][c] / 8 (gradient through mean pooling).
+__global__ void k_pool_bwd(const float *__restrict__ dP, int nx, int ny, int nz, int C,
+                           float *__restrict__ acc)
+{
+    const long long n = (long long)nx * ny * nz * C;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const long long v = e / C;
+    const int c = (int)(e - v * C);
+    const int i = (int)(v / ((long long)ny * nz)), j = (int)((v / nz) % ny), k = (int)(v % nz);
+    const long long u = ((long long)(i >> 1) * (ny >> 1) + (j >> 1)) * (nz >> 1) + (k >> 1);
+    acc[e] += 0.125f * dP[u * C + c];
+}
+
+// Flat FP32 parameters (per layer W[co][ci][3][3][3] then b) -> bf16
+// forward weights Wt[tap][co][cip] and flipped input-gradient weights
+// Wd[tap][ci][co] (cip: ci padded; padded entries zero).
+__global__ void k_pack_weights(const float *__restrict__ W, int co_n, int ci_n, int cip,
+                               bf16 *__restrict__ Wt, bf16 *__restrict__ Wd)
+{
+    const long long n = 27ll * co_n * cip;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int tap = (int)(e / ((long long)co_n * cip));
+    const int co = (int)((e / cip) % co_n);
+    const int ci = (int)(e % cip);
+    const float w = ci < ci_n ? W[((long long)co * ci_n + ci) * 27 + tap] : 0.f;
+    const bf16 b = __float2bfloat16(w);
+    Wt[e] = b;
+    if (Wd) Wd[((long long)(26 - tap) * cip + ci) * co_n + co] = b;
+}
+
+// dW[tap][co][cip] (FP32) -> flat gradient order W[co][ci][3][3][3].
+__global__ void k_unpack_grad(const float *__restrict__ dW, int co_n, int ci_n, int cip,
+                              float *__restrict__ g)
+{
+    const long long n = (long long)co_n * ci_n * 27;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int tap = (int)(e % 27);
+    const int ci = (int)((e / 27) % ci_n);
+    const int co = (int)(e / (27ll * ci_n));
+    g[e] = dW[((long long)tap * co_n + co) * cip + ci];
+}
+
+__global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ s, long long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.f - b1) * gi;
+    const float si = b2 * s[e] + (1.f - b2) * gi * gi;
+    m[e] = mi;
+    s[e] = si;
+    th[e] -= lr * (mi / c1) / (sqrtf(si / c2) + eps);
+}
+
+__global__ void k_threshold(const float *__restrict__ z, long long V, uint8_t *__restrict__ chi)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < V) chi[v] = z[v] > 0.f ? 1 : 0;
+}
+
+// Features of a system: asinh((U - C|E|^2) / s), asinh(C|E|^2 / s) and
+// the tight-surface labels, as three FP32 planes.
+__global__ void k_features(const float *__restrict__ U, const float *__restrict__ Ex,
+                           const float *__restrict__ Ey, const float *__restrict__ Ez,
+                           const uint8_t *__restrict__ chi_t, float cfa, float inv_s, long long G,
+                           float *__restrict__ x)
+{
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= G) return;
+    const float e2 = fmaf(Ex[v], Ex[v], fmaf(Ey[v], Ey[v], Ez[v] * Ez[v]));
+    const float c = cfa * e2;
+    x[v] = asinhf((U[v] - c) * inv_s);
+    x[G + v] = asinhf(c * inv_s);
+    x[2 * G + v] = chi_t[v] ? 1.f : 0.f;
+}
+
+}  // namespace unet
+}  // namespace vesis
+
+// ================================================================ host side
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vesis.h"
+
+namespace vesis {
+namespace unet {
+
+struct Layer {
+    int ci_n, cip, co_n, k;
+    long long w_off, b_off;     // in the flat parameter vector
+    bf16 *Wt = nullptr, *Wd = nullptr;
+    float *dW = nullptr;
+};
+
+enum { L_E0, L_E1, L_E2, L_E3, L_D2, L_D1, L_D0, L_HEAD, L_N };
+
+}  // namespace unet
+}  // namespace vesis
+
+using namespace vesis;
+using namespace vesis::unet;
+
+struct vesis_net_t {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    int F = 0;
+    long long P = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *s = nullptr;
+    Layer L[L_N];
+    long long step = 0;
+    bool packed = false;
+    // activations for the current crop size
+    int nx = 0, ny = 0, nz = 0;
+    bool train = false;
+    bf16 *X0 = nullptr, *e[4] = {}, *p[3] = {}, *d[3] = {};   // d[0] = d0, d[1] = d1, d[2] = d2
+    float *z = nullptr, *dz = nullptr;
+    double *loss_part = nullptr;
+    float *ge[4] = {}, *gd[3] = {}, *dX = nullptr;
+    bf16 *dZ = nullptr;
+    double *h_loss = nullptr;
+    std::vector<void *> act;      // activation allocations
+    std::vector<void *> fixed;    // parameter-sized allocations
+};
+
+namespace vesis {
+std::string *noalloc_last_error();   // the thread's error message (api.cu)
+}
+
+namespace {
+
+std::string *net_err() { return vesis::noalloc_last_error(); }
+
+int nfail(int code, const std::string &msg)
+{
+    *net_err() = msg;
+    return code;
+}
+
+#define NCK(x)                                                                     \
+    do {                                                                           \
+        cudaError_t e_ = (x);                                                      \
+        if (e_ != cudaSuccess) return nfail(VESIS_E_CUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+int nalloc(std::vector<void *> &v, T **p, size_t count)
+{
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess)
+        return nfail(VESIS_E_ALLOC, "device allocation failed");
+    v.push_back(q);
+    *p = static_cast<T *>(q);
+    return VESIS_OK;
+}
+
+void free_act(vesis_net n)
+{
+    for (void *q : n->act) cudaFree(q);
+    n->act.clear();
+    n->nx = n->ny = n->nz = 0;
+}
+
+#define NTRY(x)                      \
+    do {                             \
+        int r_ = (x);                \
+        if (r_ != VESIS_OK) return r_; \
+    } while (0)
+
+int ensure_act(vesis_net n, int nx, int ny, int nz, bool train)
+{
+    if (n->nx == nx && n->ny == ny && n->nz == nz && (n->train || !train)) return VESIS_OK;
+    NCK(cudaStreamSynchronize(n->st));
+    free_act(n);
+    const long long V0 = (long long)nx * ny * nz, V1 = V0 / 8, V2 = V1 / 8, V3 = V2 / 8;
+    const long long V[4] = {V0, V1, V2, V3};
+    auto &A = n->act;
+    NTRY(nalloc(A, &n->X0, V0 * kInPad));
+    for (int l = 0; l < 4; ++l) NTRY(nalloc(A, &n->e[l], V[l] * kCh[l]));
+    for (int l = 0; l < 3; ++l) NTRY(nalloc(A, &n->p[l], V[l + 1] * kCh[l]));
+    NTRY(nalloc(A, &n->d[0], V0 * 32));
+    NTRY(nalloc(A, &n->d[1], V1 * 32));
+    NTRY(nalloc(A, &n->d[2], V2 * 64));
+    NTRY(nalloc(A, &n->z, V0));
+    NTRY(nalloc(A, &n->loss_part, (V0 + 255) / 256));
+    if (train) {
+        NTRY(nalloc(A, &n->dz, V0));
+        for (int l = 0; l < 4; ++l) NTRY(nalloc(A, &n->ge[l], V[l] * kCh[l]));
+        NTRY(nalloc(A, &n->gd[0], V0 * 32));
+        NTRY(nalloc(A, &n->gd[1], V1 * 32));
+        NTRY(nalloc(A, &n->gd[2], V2 * 64));
+        long long mx = V0 * 64;
+        mx = std::max(mx, V1 * 128);
+        mx = std::max(mx, V2 * 256);
+        NTRY(nalloc(A, &n->dX, mx));
+        NTRY(nalloc(A, &n->dZ, V0 * 32 > V2 * 128 ? V0 * 32 : V2 * 128));
+    }
+    n->nx = nx;
+    n->ny = ny;
+    n->nz = nz;
+    n->train = train;
+    return VESIS_OK;
+}
+
+unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
+          const bf16 *Wt, const float *bias, int Cout, void *Y, bool raw)
+{
+    ConvArgs a;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.V = (long long)nx * ny * nz;
+    a.A = A;
+    a.Ca = Ca;
+    a.B = B;
+    a.Cb = Cb;
+    a.Wt = Wt;
+    a.bias = bias;
+    a.Cout = Cout;
+    a.Y = Y;
+    const int BN = Cout >= 64 ? 64 : 32;
+    dim3 grid((unsigned)((a.V + CM - 1) / CM), Cout / BN);
+    count_launch();
+    if (BN == 64) {
+        if (raw) k_conv<64, true><<<grid, 128, 0, n->st>>>(a);
+        else k_conv<64, false><<<grid, 128, 0, n->st>>>(a);
+    } else {
+        if (raw) k_conv<32, true><<<grid, 128, 0, n->st>>>(a);
+        else k_conv<32, false><<<grid, 128, 0, n->st>>>(a);
+    }
+}
+
+void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
+           const bf16 *dZ, int Cout, float *dW)
+{
+    WgradArgs a;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.V = (long long)nx * ny * nz;
+    a.A = A;
+    a.Ca = Ca;
+    a.B = B;
+    a.Cb = Cb;
+    a.dZ = dZ;
+    a.Cout = Cout;
+    a.dW = dW;
+    const int Cin = Ca + Cb;
+    const long long tiles = 27ll * (Cin / 32) * ((Cout + 63) / 64);
+    // about four blocks per SM in all, in multiples of 32 cells
+    long long chunks = std::max(1ll, (152ll * 4) / tiles);
+    long long cpb = (a.V + chunks - 1) / chunks;
+    cpb = std::max(256ll, (cpb + WK - 1) / WK * WK);
+    a.cells_per_block = cpb;
+    chunks = (a.V + cpb - 1) / cpb;
+    dim3 grid((unsigned)chunks, (unsigned)(27 * (Cin / 32)), (unsigned)((Cout + 63) / 64));
+    count_launch();
+    k_wgrad<<<grid, 128, 0, n->st>>>(a);
+}
+
+// Forward pass of a crop; with labels, the loss partials and dz too.
+void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy, int oz,
+             const uint8_t *chi)
+{
+    const int nx = n->nx, ny = n->ny, nz = n->nz;
+    const long long V0 = (long long)nx * ny * nz;
+    const int r[4][3] = {{nx, ny, nz}, {nx / 2, ny / 2, nz / 2}, {nx / 4, ny / 4, nz / 4},
+                         {nx / 8, ny / 8, nz / 8}};
+    Layer *L = n->L;
+    const float *th = n->theta;
+    count_launch();
+    k_pack_input<<<nblk(V0 * kInPad), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny,
+                                                       nz, n->X0);
+    conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, th + L[L_E0].b_off, 32, n->e[0],
+         false);
+    for (int l = 1; l < 4; ++l) {
+        const long long Vc = (long long)r[l][0] * r[l][1] * r[l][2];
+        count_launch();
+        k_pool<<<nblk(Vc * kCh[l - 1]), 256, 0, n->st>>>(n->e[l - 1], r[l - 1][0], r[l - 1][1],
+                                                         r[l - 1][2], kCh[l - 1], n->p[l - 1]);
+        conv(n, r[l][0], r[l][1], r[l][2], n->p[l - 1], kCh[l - 1], nullptr, 0, L[l].Wt,
+             th + L[l].b_off, kCh[l], n->e[l], false);
+    }
+    conv(n, r[2][0], r[2][1], r[2][2], n->e[2], 128, n->e[3], 128, L[L_D2].Wt,
+         th + L[L_D2].b_off, 64, n->d[2], false);
+    conv(n, r[1][0], r[1][1], r[1][2], n->e[1], 64, n->d[2], 64, L[L_D1].Wt,
+         th + L[L_D1].b_off, 32, n->d[1], false);
+    conv(n, nx, ny, nz, n->e[0], 32, n->d[1], 32, L[L_D0].Wt, th + L[L_D0].b_off, 32, n->d[0],
+         false);
+    count_launch();
+    k_head<<<nblk(V0), 256, 0, n->st>>>(n->d[0], V0, th + L[L_HEAD].w_off,
+                                        th + L[L_HEAD].b_off, chi, NX, NY, NZ, ox, oy, oz, ny, nz, n->z,
+                                        chi ? n->dz : nullptr, chi ? n->loss_part : nullptr);
+}
+
+int pack_weights(vesis_net n)
+{
+    for (int l = 0; l < L_HEAD; ++l) {
+        Layer &y = n->L[l];
+        count_launch();
+        k_pack_weights<<<nblk(27ll * y.co_n * y.cip), 256, 0, n->st>>>(
+            n->theta + y.w_off, y.co_n, y.ci_n, y.cip, y.Wt, y.Wd);
+    }
+    n->packed = true;
+    return VESIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out)
+{
+    if (!out) return nfail(VESIS_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_features < 1 || n_features > kInPad)
+        return nfail(VESIS_E_ARG, "n_features must be in 1..32");
+    vesis_net n = new vesis_net_t();
+    n->st = (cudaStream_t)cuda_stream;
+    n->F = n_features;
+    if (cudaGetDevice(&n->dev) != cudaSuccess) {
+        delete n;
+        return nfail(VESIS_E_CUDA, "no CUDA device");
+    }
+    const int ci[L_N] = {n_features, 32, 64, 128, 256, 128, 64, 32};
+    const int cip[L_N] = {kInPad, 32, 64, 128, 256, 128, 64, 32};
+    const int co[L_N] = {32, 64, 128, 128, 64, 32, 32, 1};
+    long long o = 0;
+    for (int l = 0; l < L_N; ++l) {
+        Layer &y = n->L[l];
+        y.ci_n = ci[l];
+        y.cip = cip[l];
+        y.co_n = co[l];
+        y.k = l == L_HEAD ? 1 : 3;
+        y.w_off = o;
+        o += (long long)co[l] * ci[l] * y.k * y.k * y.k;
+        y.b_off = o;
+        o += co[l];
+    }
+    n->P = o;
+    int rc = VESIS_OK;
+    auto &A = n->fixed;
+    if (rc == VESIS_OK) rc = nalloc(A, &n->theta, o);
+    if (rc == VESIS_OK) rc = nalloc(A, &n->grad, o);
+    if (rc == VESIS_OK) rc = nalloc(A, &n->m, o);
+    if (rc == VESIS_OK) rc = nalloc(A, &n->s, o);
+    for (int l = 0; l < L_HEAD && rc == VESIS_OK; ++l) {
+        Layer &y = n->L[l];
+        const long long nw = 27ll * y.co_n * y.cip;
+        rc = nalloc(A, &y.Wt, nw);
+        if (rc == VESIS_OK) rc = nalloc(A, &y.Wd, nw);
+        if (rc == VESIS_OK) rc = nalloc(A, &y.dW, nw);
+    }
+    if (rc == VESIS_OK && cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess)
+        rc = nfail(VESIS_E_ALLOC, "pinned allocation failed");
+    if (rc == VESIS_OK) {
+        cudaMemsetAsync(n->theta, 0, o * sizeof(float), n->st);
+        cudaMemsetAsync(n->m, 0, o * sizeof(float), n->st);
+        cudaMemsetAsync(n->s, 0, o * sizeof(float), n->st);
+        if (cudaStreamSynchronize(n->st) != cudaSuccess)
+            rc = nfail(VESIS_E_CUDA, "stream synchronisation failed");
+    }
+    if (rc != VESIS_OK) {
+        std::string keep = *net_err();
+        vesis_net_destroy(n);
+        *net_err() = keep;
+        return rc;
+    }
+    *out = n;
+    return VESIS_OK;
+}
+
+int vesis_net_param_count(vesis_net n, long long *count)
+{
+    if (!n || !count) return nfail(VESIS_E_ARG, "NULL argument");
+    *count = n->P;
+    return VESIS_OK;
+}
+
+int vesis_net_set_params(vesis_net n, const float *theta)
+{
+    if (!n || !theta) return nfail(VESIS_E_ARG, "NULL argument");
+    for (long long i = 0; i < n->P; ++i)
+        if (!std::isfinite(theta[i])) return nfail(VESIS_E_NAN, "non-finite parameter");
+    NCK(cudaMemcpyAsync(n->theta, theta, n->P * sizeof(float), cudaMemcpyHostToDevice, n->st));
+    NCK(cudaMemsetAsync(n->m, 0, n->P * sizeof(float), n->st));
+    NCK(cudaMemsetAsync(n->s, 0, n->P * sizeof(float), n->st));
+    NCK(cudaStreamSynchronize(n->st));
+    n->step = 0;
+    n->packed = false;
+    return VESIS_OK;
+}
+
+int vesis_net_get_params(vesis_net n, float *theta)
+{
+    if (!n || !theta) return nfail(VESIS_E_ARG, "NULL argument");
+    NCK(cudaMemcpyAsync(theta, n->theta, n->P * sizeof(float), cudaMemcpyDeviceToHost, n->st));
+    NCK(cudaStreamSynchronize(n->st));
+    return VESIS_OK;
+}
+
+static int check_crop(int NX, int NY, int NZ, const int *crop, int c[6])
+{
+    if (NX < 1 || NY < 1 || NZ < 1) return nfail(VESIS_E_ARG, "bad grid dimensions");
+    if (crop) {
+        for (int i = 0; i < 6; ++i) c[i] = crop[i];
+    } else {
+        c[0] = c[1] = c[2] = 0;
+        c[3] = NX;
+        c[4] = NY;
+        c[5] = NZ;
+    }
+    const int N[3] = {NX, NY, NZ};
+    for (int d = 0; d < 3; ++d) {
+        if (c[3 + d] < 8 || c[3 + d] % 8 != 0)
+            return nfail(VESIS_E_ARG, "crop dimensions must be positive multiples of 8");
+        if (c[d] < 0 || c[d] + c[3 + d] > N[d]) return nfail(VESIS_E_ARG, "crop outside the grid");
+    }
+    if ((long long)c[3] * c[4] * c[5] > (1ll << 31) / 64)
+        return nfail(VESIS_E_ARG, "crop too large");
+    return VESIS_OK;
+}
+
+int vesis_net_forward(vesis_net n, const float *x_dev, int NX, int NY, int NZ, const int *crop,
+                      float *logit_dev, uint8_t *chi_dev)
+{
+    if (!n || !x_dev) return nfail(VESIS_E_ARG, "NULL argument");
+    int c[6];
+    NTRY(check_crop(NX, NY, NZ, crop, c));
+    NTRY(ensure_act(n, c[3], c[4], c[5], false));
+    if (!n->packed) pack_weights(n);
+    forward(n, x_dev, NX, NY, NZ, c[0], c[1], c[2], nullptr);
+    const long long V = (long long)c[3] * c[4] * c[5];
+    if (logit_dev)
+        NCK(cudaMemcpyAsync(logit_dev, n->z, V * sizeof(float), cudaMemcpyDeviceToDevice, n->st));
+    if (chi_dev) {
+        count_launch();
+        k_threshold<<<nblk(V), 256, 0, n->st>>>(n->z, V, chi_dev);
+    }
+    NCK(cudaGetLastError());
+    NCK(cudaStreamSynchronize(n->st));
+    return VESIS_OK;
+}
+
+int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev, int NX, int NY,
+                        int NZ, const int *crop, double *loss_out, float *grad_host)
+{
+    if (!n || !x_dev || !chi_dev) return nfail(VESIS_E_ARG, "NULL argument");
+    int c[6];
+    NTRY(check_crop(NX, NY, NZ, crop, c));
+    NTRY(ensure_act(n, c[3], c[4], c[5], true));
+    if (!n->packed) pack_weights(n);
+    const int nx = c[3], ny = c[4], nz = c[5];
+    const int r[4][3] = {{nx, ny, nz}, {nx / 2, ny / 2, nz / 2}, {nx / 4, ny / 4, nz / 4},
+                         {nx / 8, ny / 8, nz / 8}};
+    long long V[4];
+    for (int l = 0; l < 4; ++l) V[l] = (long long)r[l][0] * r[l][1] * r[l][2];
+    forward(n, x_dev, NX, NY, NZ, c[0], c[1], c[2], chi_dev);
+    cudaStream_t st = n->st;
+    Layer *L = n->L;
+    NCK(cudaMemsetAsync(n->grad, 0, n->P * sizeof(float), st));
+    for (int l = 0; l < L_HEAD; ++l)
+        NCK(cudaMemsetAsync(L[l].dW, 0, 27ll * L[l].co_n * L[l].cip * sizeof(float), st));
+    for (int l = 0; l < 3; ++l)      // e3's gradient is written whole
+        NCK(cudaMemsetAsync(n->ge[l], 0, V[l] * kCh[l] * sizeof(float), st));
+    // head
+    count_launch();
+    k_head_bwd<<<nblk(V[0]), 256, 0, st>>>(n->d[0], V[0], n->theta + L[L_HEAD].w_off, n->dz,
+                                           n->gd[0], n->grad + L[L_HEAD].w_off);
+    auto relu_bwd = [&](const float *g, const bf16 *y, long long Vl, int C, float *db) {
+        count_launch();
+        const long long nb = std::min<long long>(nblk(Vl * C), 4 * 152);
+        k_relu_bwd<<<(unsigned)nb, 256, C * sizeof(float), st>>>(g, y, Vl, C, n->dZ, db);
+    };
+    auto unpack = [&](int l) {
+        Layer &y = L[l];
+        count_launch();
+        k_unpack_grad<<<nblk(27ll * y.co_n * y.ci_n), 256, 0, st>>>(y.dW, y.co_n, y.ci_n, y.cip,
+                                                                     n->grad + y.w_off);
+    };
+    // decoder: d0 (R0), d1 (R1), d2 (R2); skip inputs e0, e1, e2; coarse d1, d2, e3
+    struct Dec {
+        int l, lev, Ca, Cb, Cout;
+        bf16 *skip, *coarse, *out;
+        float *gskip, *gout, *gcoarse;
+    } dec[3] = {
+        {L_D0, 0, 32, 32, 32, n->e[0], n->d[1], n->d[0], n->ge[0], n->gd[0], n->gd[1]},
+        {L_D1, 1, 64, 64, 32, n->e[1], n->d[2], n->d[1], n->ge[1], n->gd[1], n->gd[2]},
+        {L_D2, 2, 128, 128, 64, n->e[2], n->e[3], n->d[2], n->ge[2], n->gd[2], n->ge[3]},
+    };
+    for (auto &D : dec) {
+        const int *R = r[D.lev];
+        const long long Vl = V[D.lev];
+        relu_bwd(D.gout, D.out, Vl, D.Cout, n->grad + L[D.l].b_off);
+        wgrad(n, R[0], R[1], R[2], D.skip, D.Ca, D.coarse, D.Cb, n->dZ, D.Cout, L[D.l].dW);
+        unpack(D.l);
+        conv(n, R[0], R[1], R[2], n->dZ, D.Cout, nullptr, 0, L[D.l].Wd, nullptr, D.Ca + D.Cb,
+             n->dX, true);
+        count_launch(2);
+        k_split_skip<<<nblk(Vl * D.Ca), 256, 0, st>>>(n->dX, Vl, D.Ca, D.Cb, D.gskip);
+        k_split_coarse<<<nblk(V[D.lev + 1] * D.Cb), 256, 0, st>>>(n->dX, R[0], R[1], R[2], D.Ca,
+                                                                 D.Cb, D.gcoarse);
+    }
+    // encoder: e3 (R3, input p2), e2 (R2, input p1), e1 (R1, input p0), e0 (R0, input X0)
+    for (int l = 3; l >= 0; --l) {
+        const int *R = r[l];
+        const long long Vl = V[l];
+        const bf16 *in = l == 0 ? n->X0 : n->p[l - 1];
+        const int Cin = l == 0 ? kInPad : kCh[l - 1];
+        relu_bwd(n->ge[l], n->e[l], Vl, kCh[l], n->grad + L[l].b_off);
+        wgrad(n, R[0], R[1], R[2], in, Cin, nullptr, 0, n->dZ, kCh[l], L[l].dW);
+        unpack(l);
+        if (l > 0) {
+            conv(n, R[0], R[1], R[2], n->dZ, kCh[l], nullptr, 0, L[l].Wd, nullptr, Cin, n->dX,
+                 true);
+            count_launch();
+            k_pool_bwd<<<nblk(V[l - 1] * Cin), 256, 0, st>>>(n->dX, r[l - 1][0], r[l - 1][1],
+                                                             r[l - 1][2], Cin, n->ge[l - 1]);
+        }
+    }
+    launch_sum_doubles(n->loss_part, (int)nblk(V[0]), reinterpret_cast<double *>(n->dz), 0, st);
+    NCK(cudaMemcpyAsync(n->h_loss, n->dz, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (grad_host)
+        NCK(cudaMemcpyAsync(grad_host, n->grad, n->P * sizeof(float), cudaMemcpyDeviceToHost, st));
+    NCK(cudaGetLastError());
+    NCK(cudaStreamSynchronize(st));
+    if (loss_out) *loss_out = *n->h_loss / (double)V[0];
+    if (!std::isfinite(*n->h_loss)) return nfail(VESIS_E_NAN, "non-finite loss");
+    return VESIS_OK;
+}
+
+int vesis_net_adam_step(vesis_net n, double lr, double beta1, double beta2, double eps)
+{
+    if (!n) return nfail(VESIS_E_ARG, "NULL net");
+    if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
+        !(eps > 0.0))
+        return nfail(VESIS_E_ARG, "invalid Adam constants");
+    ++n->step;
+    const double c1 = 1.0 - std::pow(beta1, (double)n->step);
+    const double c2 = 1.0 - std::pow(beta2, (double)n->step);
+    count_launch();
+    k_adam<<<nblk(n->P), 256, 0, n->st>>>(n->theta, n->grad, n->m, n->s, n->P, (float)lr,
+                                          (float)beta1, (float)beta2, (float)eps, (float)c1,
+                                          (float)c2);
+    NCK(cudaGetLastError());
+    n->packed = false;
+    return VESIS_OK;
+}
+
+int vesis_net_destroy(vesis_net n)
+{
+    if (!n) return VESIS_OK;
+    cudaStreamSynchronize(n->st);
+    free_act(n);
+    for (void *q : n->fixed) cudaFree(q);
+    if (n->h_loss) cudaFreeHost(n->h_loss);
+    delete n;
+    return VESIS_OK;
+}
+
+}  // extern "C"
+
+namespace vesis {
+void launch_features(const float *U, const float *E, long long G, const uint8_t *chi_t,
+                     float cfa, float scale, float *x, cudaStream_t st)
+{
+    count_launch();
+    unet::k_features<<<(unsigned)((G + 255) / 256), 256, 0, st>>>(
+        U, E, E + G, E + 2 * G, chi_t, cfa, 1.f / scale, G, x);
+}
+}  // namespace vesis

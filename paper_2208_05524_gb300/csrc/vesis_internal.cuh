@@ -173,6 +173,10 @@ size_t sweep_state_bytes(const GridDesc &g, int r);
 // err: 1 int, part_*: `blocks` entries; k3: the full stencil (device,
 // (2 kw.r + 1)^3, centred) or NULL for the product kernel kw.q; writes the
 // totals into *rs.
+// Input features of the learned initialiser (unet.cu): three FP32 planes
+// asinh((U - cfa |E|^2) / scale), asinh(cfa |E|^2 / scale), chi_t.
+void launch_features(const float *U, const float *E, long long G, const uint8_t *chi_t,
+                     float cfa, float scale, float *x, cudaStream_t st);
 // The literal serial flipping (heap.cu): key = G doubles of scratch,
 // state = heap_state_bytes(g) bytes; the counts land in flips_out,
 // dsum_out and capped_out (device).

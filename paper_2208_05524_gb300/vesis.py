@@ -97,6 +97,15 @@ def lib():
         L.vesis_get_timing.argtypes = [_p, C.POINTER(Timing)]
         L.vesis_surface_weights_noalloc.argtypes = [C.POINTER(Params), _p, _p, _p]
         L.vesis_set_tiles.argtypes = [_p, _i, _i]
+        L.vesis_features.argtypes = [_p, _p, _p, _p, _d, _p]
+        L.vesis_net_create.argtypes = [_i, _p, _p]
+        L.vesis_net_param_count.argtypes = [_p, C.POINTER(_ll)]
+        L.vesis_net_set_params.argtypes = [_p, _p]
+        L.vesis_net_get_params.argtypes = [_p, _p]
+        L.vesis_net_forward.argtypes = [_p, _p, _i, _i, _i, _p, _p, _p]
+        L.vesis_net_loss_grad.argtypes = [_p, _p, _p, _i, _i, _i, _p, C.POINTER(_d), _p]
+        L.vesis_net_adam_step.argtypes = [_p, _d, _d, _d, _d]
+        L.vesis_net_destroy.argtypes = [_p]
         L.vesis_get_tiles.argtypes = [_p, C.POINTER(_i), C.POINTER(_i)]
         L.vesis_autotune.argtypes = [_p, _p, _i, _p]
         L.vesis_relax_batch.argtypes = [_i, _p, _p, _p, C.POINTER(RelaxOpts), _i, _i,
@@ -335,6 +344,14 @@ class System:
                     ms={"energy_pencil4": t[0], "energy_pencil8": t[1],
                         "force_atoms2": t[2], "force_atoms4": t[3]})
 
+    def features(self, U, E, chi_tight, x, scale=0.01):
+        """Learned-initialiser input planes (3 x G floats) into x."""
+        import torch
+        _check(lib().vesis_features(self.h, _dp(U, torch.float32, self.G),
+                                    _dp(E, torch.float32, 3 * self.G),
+                                    _dp(chi_tight, torch.uint8, self.G), float(scale),
+                                    _dp(x, torch.float32, 3 * self.G)))
+
     def relax(self, chi, xyz, **opts):
         import torch
         o = default_relax_opts(**opts)
@@ -375,3 +392,73 @@ def relax_batch(systems, chis, xyzs, threads=8, sweep_slots=2, **opts):
         res["xyz"] = xs[i]
         out.append(res)
     return out
+
+
+class Net:
+    """The learned initialiser's network (vesis_net_*): a 3-D U-Net on
+    n_features input planes; parameters in the flat order of the header."""
+
+    def __init__(self, n_features=3, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _p()
+        _check(lib().vesis_net_create(int(n_features), _p(self.stream.cuda_stream),
+                                      C.byref(h)), allow_warn=False)
+        self.h = h
+        self.F = int(n_features)
+        n = _ll(0)
+        _check(lib().vesis_net_param_count(self.h, C.byref(n)))
+        self.P = n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vesis_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, np.float32)
+        if a.size != self.P:
+            raise ValueError(f"expected {self.P} parameters, got {a.size}")
+        _check(lib().vesis_net_set_params(self.h, _hp(a)))
+
+    def get_params(self):
+        out = np.zeros(self.P, np.float32)
+        _check(lib().vesis_net_get_params(self.h, _hp(out)))
+        return out
+
+    @staticmethod
+    def _crop(crop):
+        return None if crop is None else (_i * 6)(*[int(v) for v in crop])
+
+    def forward(self, x, shape, crop=None, logits=None, chi=None):
+        import torch
+        n = [int(v) for v in shape]
+        c = self._crop(crop)
+        V = int(np.prod(crop[3:])) if crop is not None else int(np.prod(n))
+        _check(lib().vesis_net_forward(
+            self.h, _dp(x, torch.float32, self.F * int(np.prod(n))), n[0], n[1], n[2],
+            C.cast(c, _p) if c is not None else None,
+            _dp(logits, torch.float32, V) if logits is not None else None,
+            _dp(chi, torch.uint8, V) if chi is not None else None))
+
+    def loss_grad(self, x, chi, shape, crop=None, grad=False):
+        import torch
+        n = [int(v) for v in shape]
+        G = int(np.prod(n))
+        c = self._crop(crop)
+        loss = _d(0.0)
+        g = np.zeros(self.P, np.float32) if grad else None
+        _check(lib().vesis_net_loss_grad(
+            self.h, _dp(x, torch.float32, self.F * G), _dp(chi, torch.uint8, G), n[0], n[1],
+            n[2], C.cast(c, _p) if c is not None else None, C.byref(loss), _hp(g)))
+        return (loss.value, g) if grad else loss.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().vesis_net_adam_step(self.h, float(lr), float(beta1), float(beta2),
+                                         float(eps)))
