@@ -734,6 +734,60 @@ def run_learned(args, world, rank, local):
     net.close()
 
 
+def run_pmf(args, world, rank, local):
+    """Potential of mean force of two atoms (sigma 3.5 A, charges +1/-1 and
+    +1/+1, no bond) on the 128^3 grid at h = 0.2 A, separations 4-12 A in
+    steps of 0.5 A, both branches (tight and loose starts), by the paper's
+    appendix definition.  Prints one JSON line of its own: the curves and
+    the time per PMF point (fields + flip sweep + terms)."""
+    import numpy as np
+    import torch
+
+    from paper_2208_05524_gb300 import pmf, synth, vesis
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seps = np.arange(4.0, 12.0001, 0.5)
+    curves = {}
+    t_all, points = 0.0, 0
+    for name, charges in (("opposite", (1.0, -1.0)), ("like", (1.0, 1.0))):
+        sd = synth.two_atom(8.0, charges=charges)
+        sd["bonds"] = np.zeros((0, 2), np.int32)
+        sd["bond_k"] = np.zeros(0)
+        sd["bond_r0"] = np.zeros(0)
+        S = vesis.System(sd)
+        S1 = vesis.System(synth.subset(sd, [0]))
+        S2 = vesis.System(synth.subset(sd, [1]))
+        G = S.G
+        bufs = []
+        for _ in range(3):
+            bufs += [torch.empty(G, dtype=torch.float32, device=dev),
+                     torch.empty(3 * G, dtype=torch.float32, device=dev)]
+        chis = [torch.empty(G, dtype=torch.uint8, device=dev) for _ in range(3)]
+        for start in ("tight", "loose"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rows = pmf.two_atom_curve(S, S1, S2, *chis, bufs, seps, start)
+            torch.cuda.synchronize()
+            t_all += time.perf_counter() - t0
+            points += len(rows)
+            curves[f"{name}_{start}"] = rows
+        for x in (S, S1, S2):
+            x.close()
+    out = {"metric": "sec per PMF point (two atoms, 128^3)", "value": t_all / points,
+           "unit": "s", "higher_is_better": False, "n_gpus": world, "data": "synthetic",
+           "dtype": "f32 fields, f64 totals",
+           "config": {"workload": "two_atom_pmf_grid128",
+                      "desc": "two LJ atoms sigma 3.5 A, +1/-1 and +1/+1 e, no bond, 128^3, "
+                              "h=0.2 A, d = 4-12 A step 0.5, tight and loose starts"},
+           "points": points,
+           "curves": {k: [{kk: (round(v, 6) if isinstance(v, float) else v)
+                           for kk, v in r.items()} for r in rows]
+                      for k, rows in curves.items()}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -747,6 +801,8 @@ def main():
     ap.add_argument("--converge", action="store_true",
                     help="time one converged relaxation instead of the step benchmark")
     ap.add_argument("--max-outer", type=int, default=0)
+    ap.add_argument("--pmf", action="store_true",
+                    help="potential of mean force of two atoms, both branches")
     ap.add_argument("--learned", action="store_true",
                     help="train the learned initialiser and apply it to the two-domain complex")
     ap.add_argument("--learn-systems", type=int, default=24)
@@ -760,7 +816,9 @@ def main():
     ap.add_argument("--sweep-slots", type=int, default=2)
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    if args.learned:
+    if args.pmf:
+        run_pmf(args, world, rank, local)
+    elif args.learned:
         run_learned(args, world, rank, local)
     elif args.heap:
         run_heap(args, world, rank, local)

@@ -337,6 +337,12 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
 int vesis_net_adam_step(vesis_net n, double lr, double beta1, double beta2, double eps);
 int vesis_net_destroy(vesis_net n);
 
+/* Solute-solute terms at the current positions (Eq. Gss), FP64: out3[0]
+ * bonds, out3[1] Lennard-Jones, out3[2] Coulomb (their sum is terms[4] of
+ * the energy calls).  The potential of mean force of the paper's appendix
+ * needs the two pair parts apart. */
+int vesis_ss_terms(vesis_system s, double *out3);
+
 /* Features of the learned initialiser for a system: U_dev and E_dev from
  * vesis_energy_field at the current positions, chi_tight_dev the tight
  * labels (vesis_init_labels kind 1); x_dev: 3 x G floats, written.

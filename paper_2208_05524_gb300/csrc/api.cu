@@ -1114,6 +1114,19 @@ int vesis_blsm_heap(vesis_system s, uint8_t *chi_dev, const float *U_dev,
     return capped ? VESIS_W_MAX_ROUNDS : VESIS_OK;
 }
 
+int vesis_ss_terms(vesis_system s, double *out3)
+{
+    if (!s || !out3) return fail(VESIS_E_ARG, "NULL argument");
+    double *bk = bank(s, 1);
+    enq_ss(s, s->d_xyz, bk);
+    VTRY(last_launch("ss_terms"));
+    VTRY(read_bank(s, bk));
+    out3[0] = s->h_scal[S_SSB];
+    out3[1] = s->h_scal[S_SSLJ];
+    out3[2] = s->h_scal[S_SSC];
+    return VESIS_OK;
+}
+
 int vesis_features(vesis_system s, const float *U_dev, const float *E_dev,
                    const uint8_t *chi_tight_dev, double scale, float *x_dev)
 {

@@ -13,9 +13,12 @@
 // block of 1024 threads runs the whole process, so it needs no grid
 // barrier; the flips are as serial as the paper's.
 //
-// Keys are FP64 dE (+inf for a cell that is not a candidate or has
-// dE >= 0); ties go to the smaller linear index; the flipped cells' dE are
-// summed in flip order in FP64.
+// A cell's key is the bit pattern of its FP64 dE when dE < 0 (for negative
+// doubles a larger pattern is a more negative value, so the order of the
+// keys as unsigned integers is the reverse of the order of dE) and 0 for a
+// cell that is not a candidate or has dE >= 0; ties go to the smaller
+// linear index.  Comparisons are integer; the flipped cells' dE are summed
+// in flip order in FP64.
 #include "vesis_internal.cuh"
 
 namespace vesis {
@@ -25,19 +28,19 @@ constexpr int HG = 8;        // tiles per group edge
 constexpr int HB = 1024;     // threads of the flipping block
 constexpr int HW = HB / 32;
 
-__device__ __forceinline__ double key_inf() { return __longlong_as_double(0x7ff0000000000000ll); }
+typedef unsigned long long hkey;
 
-// (e1, i1) comes before (e2, i2)
-__device__ __forceinline__ bool key_less(double e1, int i1, double e2, int i2)
+// (e1, i1) comes before (e2, i2) in the heap's order
+__device__ __forceinline__ bool key_less(hkey e1, int i1, hkey e2, int i2)
 {
-    return e1 < e2 || (e1 == e2 && i1 < i2);
+    return e1 > e2 || (e1 == e2 && i1 < i2);
 }
 
-__device__ __forceinline__ void warp_best(double &e, int &i)
+__device__ __forceinline__ void warp_best(hkey &e, int &i)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double e2 = __shfl_down_sync(0xffffffffu, e, o);
+        const hkey e2 = __shfl_down_sync(0xffffffffu, e, o);
         const int i2 = __shfl_down_sync(0xffffffffu, i, o);
         if (key_less(e2, i2, e, i)) {
             e = e2;
@@ -54,10 +57,10 @@ struct HeapArgs {
     uint8_t *chi;
     uint32_t *W;
     const float *U;
-    double *key;          // per cell
-    double *te;           // per tile
+    hkey *key;            // per cell
+    hkey *te;             // per tile
     int *ti;
-    double *ge;           // per group
+    hkey *ge;             // per group
     int *gi;
     int ntx, nty, ntz;    // tiles per axis
     int ngx, ngy, ngz;    // groups per axis
@@ -83,19 +86,19 @@ __device__ __forceinline__ bool candidate_rw(const GridDesc &g, const uint8_t *c
     return (xm != c) | (xp != c) | (ym != c) | (yp != c) | (zm != c) | (zp != c);
 }
 
-__device__ __forceinline__ double cell_key(const HeapArgs &A, long long p, int i, int j, int k,
-                                           long long nyz)
+__device__ __forceinline__ hkey cell_key(const HeapArgs &A, long long p, int i, int j, int k,
+                                         long long nyz)
 {
-    if (!candidate_rw(A.g, A.chi, p, i, j, k, nyz)) return key_inf();
+    if (!candidate_rw(A.g, A.chi, p, i, j, k, nyz)) return 0ull;
     const double e = flip_dE(A.chi[p], A.W[p], A.U[p], A.fc);
-    return e < 0.0 ? e : key_inf();
+    return e < 0.0 ? (hkey)__double_as_longlong(e) : 0ull;
 }
 
 // Best key of tile t (one warp; two cells per lane).
 __device__ __forceinline__ void tile_best(const HeapArgs &A, int t, int lane, long long nyz)
 {
     const int tz = t % A.ntz, ty = (t / A.ntz) % A.nty, tx = t / (A.ntz * A.nty);
-    double e = key_inf();
+    hkey e = 0ull;
     int idx = 0x7fffffff;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -103,7 +106,7 @@ __device__ __forceinline__ void tile_best(const HeapArgs &A, int t, int lane, lo
         const int i = tx * HT + (c >> 4), j = ty * HT + ((c >> 2) & 3), k = tz * HT + (c & 3);
         if (i < A.g.nx && j < A.g.ny && k < A.g.nz) {
             const long long p = (long long)i * nyz + (long long)j * A.g.nz + k;
-            const double v = A.key[p];
+            const hkey v = A.key[p];
             if (key_less(v, (int)p, e, idx)) {
                 e = v;
                 idx = (int)p;
@@ -121,13 +124,13 @@ __device__ __forceinline__ void tile_best(const HeapArgs &A, int t, int lane, lo
 __device__ __forceinline__ void group_best(const HeapArgs &A, int q, int lane)
 {
     const int gz = q % A.ngz, gy = (q / A.ngz) % A.ngy, gx = q / (A.ngz * A.ngy);
-    double e = key_inf();
+    hkey e = 0ull;
     int idx = 0x7fffffff;
     for (int c = lane; c < HG * HG * HG; c += 32) {
         const int tx = gx * HG + c / (HG * HG), ty = gy * HG + (c / HG) % HG, tz = gz * HG + c % HG;
         if (tx < A.ntx && ty < A.nty && tz < A.ntz) {
             const int t = (tx * A.nty + ty) * A.ntz + tz;
-            const double v = A.te[t];
+            const hkey v = A.te[t];
             const int vi = A.ti[t];
             if (key_less(v, vi, e, idx)) {
                 e = v;
@@ -171,7 +174,7 @@ __global__ void k_heap_groups(HeapArgs A, int ngroups)
 
 __global__ void __launch_bounds__(HB, 1) k_heap_run(HeapArgs A)
 {
-    __shared__ double s_e[HW];
+    __shared__ hkey s_e[HW];
     __shared__ int s_i[HW];
     __shared__ int s_q[7];     // top cell (index, i, j, k), sign, stop
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
@@ -183,10 +186,10 @@ __global__ void __launch_bounds__(HB, 1) k_heap_run(HeapArgs A)
     int capped = 0;
     for (;;) {
         // top of the heap: best over the groups
-        double e = key_inf();
+        hkey e = 0ull;
         int idx = 0x7fffffff;
         for (int q = threadIdx.x; q < ngroups; q += HB) {
-            const double v = A.ge[q];
+            const hkey v = A.ge[q];
             const int vi = A.gi[q];
             if (key_less(v, vi, e, idx)) {
                 e = v;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(HB, 1) k_heap_run(HeapArgs A)
                     idx = s_i[w];
                 }
             int stop = 0;
-            if (!(e < 0.0)) {
+            if (e == 0ull) {
                 stop = 1;                       // no candidate lowers the energy
             } else if (flips >= A.max_flips) {
                 stop = 1;
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(HB, 1) k_heap_run(HeapArgs A)
                 s_q[4] = A.chi[p] ? -1 : 1;     // +1: solvent -> solute
                 A.chi[p] ^= 1;
                 ++flips;
-                dsum += e;
+                dsum += __longlong_as_double((long long)e);
             }
             s_q[5] = stop;
         }
@@ -274,7 +277,7 @@ size_t heap_state_bytes(const GridDesc &g)
                       ((g.nz + HT - 1) / HT);
     const int tx = (g.nx + HT - 1) / HT, ty = (g.ny + HT - 1) / HT, tz = (g.nz + HT - 1) / HT;
     const size_t ng = (size_t)((tx + HG - 1) / HG) * ((ty + HG - 1) / HG) * ((tz + HG - 1) / HG);
-    return (nt + ng) * (sizeof(double) + sizeof(int)) + 256;
+    return (nt + ng) * (sizeof(hkey) + sizeof(int)) + 256;
 }
 
 cudaError_t launch_heap(const GridDesc &g, const KernelW &kw, const int *k3,
@@ -290,7 +293,7 @@ cudaError_t launch_heap(const GridDesc &g, const KernelW &kw, const int *k3,
     A.chi = chi;
     A.W = W;
     A.U = U;
-    A.key = key;
+    A.key = reinterpret_cast<hkey *>(key);
     A.ntx = (g.nx + HT - 1) / HT;
     A.nty = (g.ny + HT - 1) / HT;
     A.ntz = (g.nz + HT - 1) / HT;
@@ -300,7 +303,7 @@ cudaError_t launch_heap(const GridDesc &g, const KernelW &kw, const int *k3,
     const long long nt = (long long)A.ntx * A.nty * A.ntz;
     const long long ng = (long long)A.ngx * A.ngy * A.ngz;
     uint8_t *base = static_cast<uint8_t *>(state);
-    A.te = reinterpret_cast<double *>(base);
+    A.te = reinterpret_cast<hkey *>(base);
     A.ge = A.te + nt;
     A.ti = reinterpret_cast<int *>(A.ge + ng);
     A.gi = A.ti + nt;

@@ -894,8 +894,8 @@ static int check_crop(int NX, int NY, int NZ, const int *crop, int c[6])
             return nfail(VESIS_E_ARG, "crop dimensions must be positive multiples of 8");
         if (c[d] < 0 || c[d] + c[3 + d] > N[d]) return nfail(VESIS_E_ARG, "crop outside the grid");
     }
-    if ((long long)c[3] * c[4] * c[5] > (1ll << 31) / 64)
-        return nfail(VESIS_E_ARG, "crop too large");
+    if ((long long)c[3] * c[4] * c[5] > 2147483647ll)
+        return nfail(VESIS_E_ARG, "crop has more than 2^31-1 cells");
     return VESIS_OK;
 }
 

@@ -303,6 +303,24 @@ def host_guest(index: int, seed: int = 1, h: float = 0.3, temperature: float = 2
     return sysd
 
 
+def subset(sysd, idx):
+    """The atoms `idx` of a system alone on the same grid (bonds between
+    them kept, renumbered)."""
+    idx = np.asarray(idx, np.int64)
+    out = dict(sysd)
+    for k in ("xyz", "sigma_sw", "eps_sw", "q", "sigma_ss", "eps_ss"):
+        out[k] = np.asarray(sysd[k])[idx].copy()
+    where = {int(a): i for i, a in enumerate(idx)}
+    b = np.asarray(sysd["bonds"]).reshape(-1, 2)
+    keep = [m for m in range(len(b)) if int(b[m, 0]) in where and int(b[m, 1]) in where]
+    out["bonds"] = np.array([[where[int(b[m, 0])], where[int(b[m, 1])]] for m in keep],
+                            np.int32).reshape(-1, 2)
+    out["bond_k"] = np.asarray(sysd["bond_k"])[keep].copy()
+    out["bond_r0"] = np.asarray(sysd["bond_r0"])[keep].copy()
+    out["init"] = {"kind": "tight", "d": out["sigma_sw"].copy()}
+    return out
+
+
 def random_cluster(n_atoms: int, n: int, h: float, seed: int,
                    temperature: float = 298.0, net_charge: float = 0.0,
                    density: float = 0.05):

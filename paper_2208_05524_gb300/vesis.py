@@ -98,6 +98,7 @@ def lib():
         L.vesis_surface_weights_noalloc.argtypes = [C.POINTER(Params), _p, _p, _p]
         L.vesis_set_tiles.argtypes = [_p, _i, _i]
         L.vesis_features.argtypes = [_p, _p, _p, _p, _d, _p]
+        L.vesis_ss_terms.argtypes = [_p, _p]
         L.vesis_net_create.argtypes = [_i, _p, _p]
         L.vesis_net_param_count.argtypes = [_p, C.POINTER(_ll)]
         L.vesis_net_set_params.argtypes = [_p, _p]
@@ -200,6 +201,7 @@ class System:
                 setattr(p, k, v)
         self.params = p
         self.n_atoms = len(sysd["xyz"])
+        self.sigma = np.asarray(sysd["sigma_sw"], np.float64).copy()
         self.G = n[0] * n[1] * n[2]
         self.shape = tuple(n)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -343,6 +345,12 @@ class System:
         return dict(energy_pencil=pe, force_atoms=fa,
                     ms={"energy_pencil4": t[0], "energy_pencil8": t[1],
                         "force_atoms2": t[2], "force_atoms4": t[3]})
+
+    def ss_terms(self):
+        """Solute-solute bonds, LJ and Coulomb at the current positions."""
+        out = (_d * 3)()
+        _check(lib().vesis_ss_terms(self.h, C.cast(out, _p)))
+        return dict(bonds=out[0], lj=out[1], coulomb=out[2])
 
     def features(self, U, E, chi_tight, x, scale=0.01):
         """Learned-initialiser input planes (3 x G floats) into x."""

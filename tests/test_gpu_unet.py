@@ -118,7 +118,7 @@ def test_training_lowers_the_loss():
 
 def test_features_match_oracle():
     vs = _vs()
-    s = synth.random_cluster(40, 24, 0.5, seed=4, net_charge=1.0)
+    s = synth.random_cluster(40, 32, 0.5, seed=4, net_charge=1.0)
     S = vs.System(s)
     G = S.G
     U = torch.empty(G, dtype=torch.float32, device="cuda")
