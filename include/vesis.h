@@ -337,11 +337,29 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
 int vesis_net_adam_step(vesis_net n, double lr, double beta1, double beta2, double eps);
 int vesis_net_destroy(vesis_net n);
 
-/* Solute-solute terms at the current positions (Eq. Gss), FP64: out3[0]
- * bonds, out3[1] Lennard-Jones, out3[2] Coulomb (their sum is terms[4] of
- * the energy calls).  The potential of mean force of the paper's appendix
- * needs the two pair parts apart. */
-int vesis_ss_terms(vesis_system s, double *out3);
+/* Solute-solute terms at the current positions (Eq. Gss), FP64: out5[0]
+ * bonds, [1] Lennard-Jones, [2] Coulomb, [3] bends, [4] torsions (their
+ * sum is terms[4] of the energy calls).  The potential of mean force of
+ * the paper's appendix needs the pair parts apart. */
+int vesis_ss_terms(vesis_system s, double *out5);
+
+/* Bending and torsion terms of G_ss (Eq. Gss), replacing any set before
+ * (n_angles = n_torsions = 0 removes them; a new system has none):
+ *   bend (i, j, k):  1/2 B (theta - theta0)^2, theta the angle between
+ *                    r_i - r_j and r_k - r_j; ijk [n_angles][3], B and
+ *                    theta0 (radians, in [0, pi]) n_angles each
+ *   torsion (i, j, k, l): sum_{n=0..6} C_n [1 + cos(n tau - psi_n)], tau
+ *                    the angle between (r_j - r_i) x (r_k - r_j) and
+ *                    (r_k - r_j) x (r_l - r_k); ijkl [n_torsions][4], C and
+ *                    psi [n_torsions][7]; each psi_n 0 or pi (the paper's
+ *                    force formulas of the appendix assume so)
+ * Their energies join terms[4] and their gradients (the appendix's) the
+ * atom gradient.  A bend with sin theta = 0 adds no gradient; a torsion
+ * whose two plane normals has a zero vector adds nothing.  Atoms of a term
+ * must be distinct and in range.  Host arrays, copied. */
+int vesis_set_bonded(vesis_system s, int n_angles, const int *ijk, const double *B,
+                     const double *theta0, int n_torsions, const int *ijkl,
+                     const double *C, const double *psi);
 
 /* Features of the learned initialiser for a system: U_dev and E_dev from
  * vesis_energy_field at the current positions, chi_tight_dev the tight

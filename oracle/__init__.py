@@ -506,6 +506,74 @@ def ss_terms(sysd, p, xyz=None):
     return e, g
 
 
+def bonded_terms(sysd, xyz=None):
+    """Bending and torsion energies of G_ss (Eq. Gss) and their gradient.
+
+    Bend (i, j, k): 1/2 B (theta - theta0)^2, theta the angle between
+    r_i - r_j and r_k - r_j.  Torsion (i, j, k, l): sum over n = 0..6 of
+    C_n [1 + cos(n tau - psi_n)], tau the angle between u = q1 x q2 and
+    v = q2 x q3 with q1 = r_j - r_i, q2 = r_k - r_j, q3 = r_l - r_k.  The
+    gradients follow the appendix ("Force calculations of molecular
+    mechanical interactions"): B (theta - theta0) grad theta, and
+    dW/dLambda grad Lambda with Lambda = cos tau = u.v / (|u| |v|), which
+    holds for phases psi_n of 0 or pi.  A bend with sin theta = 0 adds no
+    gradient; a torsion with u or v of zero length adds nothing."""
+    xyz = _c64(sysd["xyz"] if xyz is None else xyz).reshape(-1, 3)
+    g = np.zeros_like(xyz)
+    eb = 0.0
+    angles = np.asarray(sysd.get("angles", np.zeros((0, 3), int))).reshape(-1, 3)
+    for m, (i, j, k) in enumerate(angles):
+        a = xyz[i] - xyz[j]
+        b = xyz[k] - xyz[j]
+        la, lb = np.linalg.norm(a), np.linalg.norm(b)
+        c = float(np.dot(a, b) / (la * lb))
+        c = min(1.0, max(-1.0, c))
+        th = math.acos(c)
+        d = th - float(sysd["angle_theta0"][m])
+        B = float(sysd["angle_B"][m])
+        eb += 0.5 * B * d * d
+        sn = math.sin(th)
+        if sn < 1e-12:
+            continue
+        dth_da = -(b / (la * lb) - c * a / (la * la)) / sn
+        dth_db = -(a / (la * lb) - c * b / (lb * lb)) / sn
+        g[i] += B * d * dth_da
+        g[k] += B * d * dth_db
+        g[j] -= B * d * (dth_da + dth_db)
+    et = 0.0
+    tors = np.asarray(sysd.get("torsions", np.zeros((0, 4), int))).reshape(-1, 4)
+    for m, (i, j, k, l) in enumerate(tors):
+        q1, q2, q3 = xyz[j] - xyz[i], xyz[k] - xyz[j], xyz[l] - xyz[k]
+        u, v = np.cross(q1, q2), np.cross(q2, q3)
+        lu, lv = np.linalg.norm(u), np.linalg.norm(v)
+        if lu * lv < 1e-24:
+            continue
+        lam = float(np.dot(u, v) / (lu * lv))
+        lam = min(1.0, max(-1.0, lam))
+        tau = math.acos(lam)
+        C = np.asarray(sysd["torsion_C"][m], np.float64)
+        psi = np.asarray(sysd["torsion_psi"][m], np.float64)
+        et += float(np.sum(C * (1.0 + np.cos(np.arange(7) * tau - psi))))
+        cps = np.cos(psi)
+        # dW/dLambda = sum_n C_n cos(psi_n) T_n'(Lambda), written out
+        dW = ((C[1] * cps[1] - 3 * C[3] * cps[3] + 5 * C[5] * cps[5])
+              + lam * (4 * C[2] * cps[2] - 16 * C[4] * cps[4] + 36 * C[6] * cps[6])
+              + lam ** 2 * (12 * C[3] * cps[3] - 60 * C[5] * cps[5])
+              + lam ** 3 * (32 * C[4] * cps[4] - 192 * C[6] * cps[6])
+              + lam ** 4 * (80 * C[5] * cps[5])
+              + lam ** 5 * (192 * C[6] * cps[6]))
+        dL_du = (v * lu * lu - np.dot(u, v) * u) / (lu ** 3 * lv)
+        dL_dv = (u * lv * lv - np.dot(u, v) * v) / (lu * lv ** 3)
+        dL_dq1 = np.cross(q2, dL_du)
+        dL_dq2 = np.cross(dL_du, q1) + np.cross(q3, dL_dv)
+        dL_dq3 = np.cross(dL_dv, q2)
+        g[i] += dW * (-dL_dq1)
+        g[j] += dW * (dL_dq1 - dL_dq2)
+        g[k] += dW * (dL_dq2 - dL_dq3)
+        g[l] += dW * dL_dq3
+    return eb, et, g
+
+
 def energy_terms(sysd, p, chi, xyz=None, U=None, E=None):
     """All terms of G = G_VISM + G_ss (Eq. freeenergyfn, Eq. 4flip):
     surface, vdW, CFA (solvent cells), far field, solute-solute, total."""
@@ -523,7 +591,8 @@ def energy_terms(sysd, p, chi, xyz=None, U=None, E=None):
     cfa = sc["h3"] * float(cfa_pt[solv].sum())
     far = far_field(sysd, p, xyz)[0] if p["far_field"] else 0.0
     ess, _ = ss_terms(sysd, p, xyz)
-    ss = float(ess.sum())
+    e_bend, e_tors, _ = bonded_terms(sysd, xyz)
+    ss = float(ess.sum()) + e_bend + e_tors
     return dict(surf=es, vdw=vol - cfa, cfa=cfa, far=far, ss=ss,
                 total=es + vol + far + ss, vol=vol)
 
@@ -553,7 +622,8 @@ def gradient(sysd, p, chi, xyz=None, E=None):
                         p["rmin"], _p(gf))
         g += gf
     _, gss = ss_terms(sysd, p, xyz)
-    return g + gss
+    _, _, gbt = bonded_terms(sysd, xyz)
+    return g + gss + gbt
 
 
 # ------------------------------------------------------------ relaxation

@@ -58,7 +58,7 @@ int fail(int code, const std::string &msg)
 // Device scalar slots of an energy bank.
 enum {
     S_SURF = 0, S_VOL = 1, S_CFA = 2, S_NSOL = 3, S_FAR = 4,
-    S_SSB = 5, S_SSLJ = 6, S_SSC = 7, S_TOTAL = 8, S_BANK = 16
+    S_SSB = 5, S_SSLJ = 6, S_SSC = 7, S_TOTAL = 8, S_SSA = 9, S_SST = 10, S_BANK = 16
 };
 
 struct GdState {
@@ -71,7 +71,7 @@ struct GdState {
 __global__ void k_total(double *bank)
 {
     bank[S_TOTAL] = bank[S_SURF] + bank[S_VOL] + bank[S_FAR] + bank[S_SSB] +
-                    bank[S_SSLJ] + bank[S_SSC];
+                    bank[S_SSLJ] + bank[S_SSC] + bank[S_SSA] + bank[S_SST];
 }
 
 // Step 3.4: reject if dG > dG* or (N_cnt >= N*_cnt and 0 < dG <= dG*), with
@@ -222,6 +222,9 @@ struct vesis_system_t {
     int nb_far = 0;
 
     double *d_ss_part = nullptr, *d_ss_gpart = nullptr;
+    BondedDev bonded{};               // bends and torsions (none by default)
+    double *d_bonded_part = nullptr;
+    std::vector<void *> bonded_allocs;
     int nb_ss = 0;
     SsPlan ssplan{};
 
@@ -396,6 +399,8 @@ void enq_ss(vesis_system s, const double *d_pos, double *bk)
     launch_ss_final(s->d_ss_part, s->nb_ss, bk + S_SSB, s->st);
     launch_force_reduce(s->d_ss_gpart, s->ssplan.nchunk, s->n, 1.0, s->d_grad_ss,
                         0, s->st);
+    launch_bonded(s->bonded, d_pos, s->n, s->d_bonded_part, bk + S_SSA, bk + S_SST,
+                  s->d_grad_ss, s->st);
 }
 
 void enq_conv(vesis_system s, const uint8_t *chi, uint32_t *W)
@@ -512,7 +517,7 @@ void fill_terms(const double *hb, bool have_E, double *terms)
     terms[1] = vol - cfa;
     terms[2] = cfa;
     terms[3] = hb[S_FAR];
-    terms[4] = hb[S_SSB] + hb[S_SSLJ] + hb[S_SSC];
+    terms[4] = hb[S_SSB] + hb[S_SSLJ] + hb[S_SSC] + hb[S_SSA] + hb[S_SST];
     terms[5] = hb[S_TOTAL];
 }
 
@@ -627,6 +632,7 @@ int vesis_destroy(vesis_system s)
     }
     for (auto e : s->ev_pool) cudaEventDestroy(e);
     for (void *p : s->allocs) cudaFree(p);
+    for (void *p : s->bonded_allocs) cudaFree(p);
     if (s->h_scal) cudaFreeHost(s->h_scal);
     if (s->h_rs) cudaFreeHost(s->h_rs);
     if (s->h_gd) cudaFreeHost(s->h_gd);
@@ -1114,16 +1120,105 @@ int vesis_blsm_heap(vesis_system s, uint8_t *chi_dev, const float *U_dev,
     return capped ? VESIS_W_MAX_ROUNDS : VESIS_OK;
 }
 
-int vesis_ss_terms(vesis_system s, double *out3)
+int vesis_ss_terms(vesis_system s, double *out5)
 {
-    if (!s || !out3) return fail(VESIS_E_ARG, "NULL argument");
+    if (!s || !out5) return fail(VESIS_E_ARG, "NULL argument");
     double *bk = bank(s, 1);
     enq_ss(s, s->d_xyz, bk);
     VTRY(last_launch("ss_terms"));
     VTRY(read_bank(s, bk));
-    out3[0] = s->h_scal[S_SSB];
-    out3[1] = s->h_scal[S_SSLJ];
-    out3[2] = s->h_scal[S_SSC];
+    out5[0] = s->h_scal[S_SSB];
+    out5[1] = s->h_scal[S_SSLJ];
+    out5[2] = s->h_scal[S_SSC];
+    out5[3] = s->h_scal[S_SSA];
+    out5[4] = s->h_scal[S_SST];
+    return VESIS_OK;
+}
+
+int vesis_set_bonded(vesis_system s, int n_angles, const int *ijk, const double *B,
+                     const double *theta0, int n_torsions, const int *ijkl, const double *C,
+                     const double *psi)
+{
+    if (!s) return fail(VESIS_E_ARG, "NULL system");
+    if (n_angles < 0 || n_torsions < 0) return fail(VESIS_E_ARG, "negative term count");
+    if (n_angles > 0 && (!ijk || !B || !theta0)) return fail(VESIS_E_ARG, "NULL angle array");
+    if (n_torsions > 0 && (!ijkl || !C || !psi)) return fail(VESIS_E_ARG, "NULL torsion array");
+    const int n = s->n;
+    for (int m = 0; m < n_angles; ++m) {
+        const int *t = ijk + 3 * m;
+        for (int c = 0; c < 3; ++c)
+            if (t[c] < 0 || t[c] >= n) return fail(VESIS_E_ARG, "angle atom index out of range");
+        if (t[0] == t[1] || t[1] == t[2] || t[0] == t[2])
+            return fail(VESIS_E_ARG, "an angle repeats an atom");
+        if (!std::isfinite(B[m]) || !std::isfinite(theta0[m]) || theta0[m] < 0.0 ||
+            theta0[m] > M_PI)
+            return fail(VESIS_E_ARG, "angle constants must be finite, theta0 in [0, pi]");
+    }
+    for (int m = 0; m < n_torsions; ++m) {
+        const int *t = ijkl + 4 * m;
+        for (int c = 0; c < 4; ++c)
+            if (t[c] < 0 || t[c] >= n) return fail(VESIS_E_ARG, "torsion atom index out of range");
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (t[a] == t[b]) return fail(VESIS_E_ARG, "a torsion repeats an atom");
+        for (int c = 0; c < 7; ++c) {
+            const double ps = psi[7 * m + c];
+            if (!std::isfinite(C[7 * m + c]) ||
+                !(std::fabs(ps) < 1e-9 || std::fabs(ps - M_PI) < 1e-9))
+                return fail(VESIS_E_ARG, "torsion phases must be 0 or pi, constants finite");
+        }
+    }
+    VCK(cudaStreamSynchronize(s->st));
+    for (void *p : s->bonded_allocs) cudaFree(p);
+    s->bonded_allocs.clear();
+    s->bonded = BondedDev{};
+    s->d_bonded_part = nullptr;
+    if (n_angles + n_torsions == 0) return VESIS_OK;
+    // per-atom incidence lists, terms in increasing order
+    std::vector<int> aptr(n + 1, 0), tptr(n + 1, 0);
+    for (int m = 0; m < n_angles; ++m)
+        for (int c = 0; c < 3; ++c) ++aptr[ijk[3 * m + c] + 1];
+    for (int m = 0; m < n_torsions; ++m)
+        for (int c = 0; c < 4; ++c) ++tptr[ijkl[4 * m + c] + 1];
+    for (int a = 0; a < n; ++a) {
+        aptr[a + 1] += aptr[a];
+        tptr[a + 1] += tptr[a];
+    }
+    std::vector<int> ainc(std::max(1, aptr[n])), tinc(std::max(1, tptr[n]));
+    {
+        std::vector<int> fa(aptr.begin(), aptr.end() - 1), ft(tptr.begin(), tptr.end() - 1);
+        for (int m = 0; m < n_angles; ++m)
+            for (int c = 0; c < 3; ++c) ainc[fa[ijk[3 * m + c]]++] = (m << 2) | c;
+        for (int m = 0; m < n_torsions; ++m)
+            for (int c = 0; c < 4; ++c) tinc[ft[ijkl[4 * m + c]]++] = (m << 2) | c;
+    }
+    auto up = [&](const void *src, size_t bytes, void **dst) -> int {
+        void *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess)
+            return fail(VESIS_E_ALLOC, "device allocation failed");
+        s->bonded_allocs.push_back(p);
+        if (bytes && cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(VESIS_E_CUDA, "copy of the bonded terms failed");
+        *dst = p;
+        return VESIS_OK;
+    };
+    BondedDev b;
+    b.nang = n_angles;
+    b.ntor = n_torsions;
+    void *q;
+    VTRY(up(ijk, sizeof(int) * 3 * n_angles, &q)); b.ang = (const int *)q;
+    VTRY(up(B, sizeof(double) * n_angles, &q)); b.angB = (const double *)q;
+    VTRY(up(theta0, sizeof(double) * n_angles, &q)); b.angT0 = (const double *)q;
+    VTRY(up(ijkl, sizeof(int) * 4 * n_torsions, &q)); b.tor = (const int *)q;
+    VTRY(up(C, sizeof(double) * 7 * n_torsions, &q)); b.torC = (const double *)q;
+    VTRY(up(psi, sizeof(double) * 7 * n_torsions, &q)); b.torPsi = (const double *)q;
+    VTRY(up(aptr.data(), sizeof(int) * (n + 1), &q)); b.ang_ptr = (const int *)q;
+    VTRY(up(ainc.data(), sizeof(int) * ainc.size(), &q)); b.ang_inc = (const int *)q;
+    VTRY(up(tptr.data(), sizeof(int) * (n + 1), &q)); b.tor_ptr = (const int *)q;
+    VTRY(up(tinc.data(), sizeof(int) * tinc.size(), &q)); b.tor_inc = (const int *)q;
+    VTRY(up(nullptr, sizeof(double) * (n_angles + n_torsions), &q));
+    s->d_bonded_part = (double *)q;
+    s->bonded = b;
     return VESIS_OK;
 }
 

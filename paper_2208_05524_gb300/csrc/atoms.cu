@@ -257,3 +257,172 @@ void launch_mobility(const double *xyz, const double *grad,
 }
 
 }  // namespace vesis
+
+namespace vesis {
+
+// ------------------------------------------------------ bends and torsions
+// Bend (i, j, k): 1/2 B (theta - theta0)^2 with theta the angle between
+// r_i - r_j and r_k - r_j; torsion (i, j, k, l): sum_n C_n [1 + cos(n tau
+// - psi_n)] with tau the angle between u = q1 x q2 and v = q2 x q3, q1 =
+// r_j - r_i, q2 = r_k - r_j, q3 = r_l - r_k (Eq. Gss).  Gradients as in the
+// paper's appendix: B (theta - theta0) grad theta, and dW/dLambda grad
+// Lambda for Lambda = cos tau (phases 0 or pi).  A bend with sin theta = 0
+// adds no gradient; a torsion whose u or v vanishes adds nothing.
+
+__device__ __forceinline__ void bend_term(const double *x, int i, int j, int k, double B,
+                                          double t0, double &e, double gi[3], double gk[3])
+{
+    double a[3], b[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[c] = x[3 * i + c] - x[3 * j + c];
+        b[c] = x[3 * k + c] - x[3 * j + c];
+    }
+    const double la = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    const double lb = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    double cs = (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / (la * lb);
+    cs = fmin(1.0, fmax(-1.0, cs));
+    const double th = acos(cs);
+    const double d = th - t0;
+    e = 0.5 * B * d * d;
+    const double sn = sin(th);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gi[c] = gk[c] = 0.0;
+    if (sn < 1e-12) return;
+    const double f = B * d / sn;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        gi[c] = -f * (b[c] / (la * lb) - cs * a[c] / (la * la));
+        gk[c] = -f * (a[c] / (la * lb) - cs * b[c] / (lb * lb));
+    }
+}
+
+__device__ __forceinline__ void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Energy and the gradients of the four atoms (g[0..3][3]); false when
+// degenerate.
+__device__ __forceinline__ bool torsion_term(const double *x, const int *ijkl, const double *C,
+                                             const double *psi, double &e, double g[4][3])
+{
+    const int i = ijkl[0], j = ijkl[1], k = ijkl[2], l = ijkl[3];
+    double q1[3], q2[3], q3[3], u[3], v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        q1[c] = x[3 * j + c] - x[3 * i + c];
+        q2[c] = x[3 * k + c] - x[3 * j + c];
+        q3[c] = x[3 * l + c] - x[3 * k + c];
+    }
+    cross3(q1, q2, u);
+    cross3(q2, q3, v);
+    const double lu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double lv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    e = 0.0;
+    if (lu * lv < 1e-24) return false;
+    const double uv = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+    const double lam = fmin(1.0, fmax(-1.0, uv / (lu * lv)));
+    const double tau = acos(lam);
+    double cps[7];
+#pragma unroll
+    for (int n = 0; n < 7; ++n) {
+        e += C[n] * (1.0 + cos(n * tau - psi[n]));
+        cps[n] = cos(psi[n]);
+    }
+    // dW/dLambda = sum_n C_n cos(psi_n) T_n'(Lambda), T_n the Chebyshev
+    // polynomials (cos n tau = T_n(cos tau)), T_n' = n U_{n-1}
+    double dW = 0.0, Um1 = 0.0, U0 = 1.0;     // U_{-1} = 0, U_0 = 1
+#pragma unroll
+    for (int n = 1; n < 7; ++n) {
+        dW += C[n] * cps[n] * n * U0;          // U0 holds U_{n-1}
+        const double U1 = 2.0 * lam * U0 - Um1;
+        Um1 = U0;
+        U0 = U1;
+    }
+    double du[3], dv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        du[c] = (v[c] * lu * lu - uv * u[c]) / (lu * lu * lu * lv);
+        dv[c] = (u[c] * lv * lv - uv * v[c]) / (lu * lv * lv * lv);
+    }
+    double d1[3], d2a[3], d2b[3], d3[3];
+    cross3(q2, du, d1);
+    cross3(du, q1, d2a);
+    cross3(q3, dv, d2b);
+    cross3(dv, q2, d3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double d2 = d2a[c] + d2b[c];
+        g[0][c] = -dW * d1[c];
+        g[1][c] = dW * (d1[c] - d2);
+        g[2][c] = dW * (d2 - d3[c]);
+        g[3][c] = dW * d3[c];
+    }
+    return true;
+}
+
+__global__ void k_bonded_energy(BondedDev b, const double *__restrict__ x,
+                                double *__restrict__ part)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < b.nang) {
+        double e, gi[3], gk[3];
+        bend_term(x, b.ang[3 * m], b.ang[3 * m + 1], b.ang[3 * m + 2], b.angB[m], b.angT0[m], e,
+                  gi, gk);
+        part[m] = e;
+    } else if (m < b.nang + b.ntor) {
+        const int t = m - b.nang;
+        double e, g[4][3];
+        torsion_term(x, b.tor + 4 * t, b.torC + 7 * t, b.torPsi + 7 * t, e, g);
+        part[m] = e;
+    }
+}
+
+// grad[n] += the bend and torsion gradients of atom n, its terms in
+// increasing order (no atomics: the sums are reproducible).
+__global__ void k_bonded_grad(BondedDev b, const double *__restrict__ x, int n,
+                              double *__restrict__ grad)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int e = b.ang_ptr[a]; e < b.ang_ptr[a + 1]; ++e) {
+        const int m = b.ang_inc[e] >> 2, role = b.ang_inc[e] & 3;
+        double en, gi[3], gk[3];
+        bend_term(x, b.ang[3 * m], b.ang[3 * m + 1], b.ang[3 * m + 2], b.angB[m], b.angT0[m],
+                  en, gi, gk);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            s[c] += role == 0 ? gi[c] : role == 2 ? gk[c] : -(gi[c] + gk[c]);
+    }
+    for (int e = b.tor_ptr[a]; e < b.tor_ptr[a + 1]; ++e) {
+        const int t = b.tor_inc[e] >> 2, role = b.tor_inc[e] & 3;
+        double en, g[4][3];
+        if (!torsion_term(x, b.tor + 4 * t, b.torC + 7 * t, b.torPsi + 7 * t, en, g)) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s[c] += g[role][c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) grad[3 * a + c] += s[c];
+}
+
+void launch_bonded(const BondedDev &b, const double *xyz, int n, double *part, double *e_bend,
+                   double *e_tors, double *grad, cudaStream_t st)
+{
+    const int nt = b.nang + b.ntor;
+    if (nt > 0) {
+        count_launch();
+        k_bonded_energy<<<(nt + 127) / 128, 128, 0, st>>>(b, xyz, part);
+    }
+    launch_sum_doubles(part, b.nang, e_bend, 0, st);
+    launch_sum_doubles(part + b.nang, b.ntor, e_tors, 0, st);
+    if (grad && nt > 0) {
+        count_launch();
+        k_bonded_grad<<<(n + 127) / 128, 128, 0, st>>>(b, xyz, n, grad);
+    }
+}
+
+}  // namespace vesis

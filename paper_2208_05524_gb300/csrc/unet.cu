@@ -167,6 +167,132 @@ __global__ void __launch_bounds__(128) k_conv(ConvArgs P)
     }
 }
 
+// The same convolution on bricks of 4 x 4 x 8 cells (grid dimensions
+// multiples of 4, 4, 8): per chunk of CK input channels the block loads the
+// brick's 6 x 6 x 10 halo once and the chunk's weights of all 27 taps, then
+// runs every tap's MMAs from shared memory (the plain kernel reloads the
+// inputs for each tap).  32 output channels per block; each warp owns 32
+// cells (two m16 tiles).
+constexpr int HXB = 4, HYB = 4, HZB = 8;        // brick
+constexpr int HCELLS = (HXB + 2) * (HYB + 2) * (HZB + 2);
+constexpr int HBN = 32;
+
+template <int CK_>
+struct HaloSmem {
+    bf16 h[HCELLS][CK_ + 8];
+    bf16 w[27][HBN][CK_ + 8];
+};
+
+template <int CK_, bool RAW>
+__global__ void __launch_bounds__(128) k_conv_halo(ConvArgs P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    HaloSmem<CK_> &S = *reinterpret_cast<HaloSmem<CK_> *>(smem_raw);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int g = lane >> 2, tq = lane & 3;
+    const int bxn = P.nx / HXB, byn = P.ny / HYB;
+    const int bz = blockIdx.x % (P.nz / HZB);
+    const int by = (blockIdx.x / (P.nz / HZB)) % byn;
+    const int bx = blockIdx.x / ((P.nz / HZB) * byn);
+    (void)bxn;
+    const int i0 = bx * HXB, j0 = by * HYB, k0 = bz * HZB;
+    const int co0 = blockIdx.y * HBN;
+    const int Cin = P.Ca + P.Cb;
+    const long long nyz = (long long)P.ny * P.nz;
+    const int hy = P.ny >> 1, hz = P.nz >> 1;
+    // halo index of the rows this lane reads: cell q = 32 w + 16 m + g (+8)
+    int hrow[2][2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int q = 32 * w + 16 * m + g + 8 * hh;
+            const int cx = q / (HYB * HZB), cy = (q / HZB) % HYB, cz = q % HZB;
+            hrow[m][hh] = ((cx + 1) * (HYB + 2) + (cy + 1)) * (HZB + 2) + (cz + 1);
+        }
+    float acc[2][HBN / 8][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < HBN / 8; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
+    constexpr int V16 = CK_ / 8;   // uint4 per cell row of the chunk
+    for (int c0 = 0; c0 < Cin; c0 += CK_) {
+        // halo of the chunk
+        for (int e = t; e < HCELLS * V16; e += 128) {
+            const int hc = e / V16, part = e % V16;
+            const int hx = hc / ((HYB + 2) * (HZB + 2)), hyy = (hc / (HZB + 2)) % (HYB + 2),
+                      hzz = hc % (HZB + 2);
+            const int ii = i0 + hx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz) {
+                const bf16 *src;
+                if (c0 < P.Ca)
+                    src = P.A + ((long long)ii * nyz + (long long)jj * P.nz + kk) * P.Ca + c0;
+                else
+                    src = P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) * P.Cb +
+                          (c0 - P.Ca);
+                v = reinterpret_cast<const uint4 *>(src)[part];
+            }
+            *reinterpret_cast<uint4 *>(&S.h[hc][part * 8]) = v;
+        }
+        // weights of all taps for the chunk
+        for (int e = t; e < 27 * HBN * V16; e += 128) {
+            const int tap = e / (HBN * V16), co = (e / V16) % HBN, part = e % V16;
+            const bf16 *src = P.Wt + ((long long)tap * P.Cout + co0 + co) * Cin + c0;
+            *reinterpret_cast<uint4 *>(&S.w[tap][co][part * 8]) =
+                reinterpret_cast<const uint4 *>(src)[part];
+        }
+        __syncthreads();
+        for (int tap = 0; tap < 27; ++tap) {
+            const int off = ((tap / 9 - 1) * (HYB + 2) + ((tap / 3) % 3 - 1)) * (HZB + 2) +
+                            (tap % 3 - 1);
+#pragma unroll
+            for (int ks = 0; ks < CK_; ks += 16) {
+                unsigned b[HBN / 8][2];
+#pragma unroll
+                for (int n = 0; n < HBN / 8; ++n) {
+                    b[n][0] = ld_s32(&S.w[tap][n * 8 + g][ks + 2 * tq]);
+                    b[n][1] = ld_s32(&S.w[tap][n * 8 + g][ks + 8 + 2 * tq]);
+                }
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    unsigned a[4];
+                    const int r0 = hrow[m][0] + off, r1 = hrow[m][1] + off;
+                    a[0] = ld_s32(&S.h[r0][ks + 2 * tq]);
+                    a[1] = ld_s32(&S.h[r1][ks + 2 * tq]);
+                    a[2] = ld_s32(&S.h[r0][ks + 8 + 2 * tq]);
+                    a[3] = ld_s32(&S.h[r1][ks + 8 + 2 * tq]);
+#pragma unroll
+                    for (int n = 0; n < HBN / 8; ++n) mma_bf16(acc[m][n], a, b[n]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int q = 32 * w + 16 * m + g + 8 * hh;
+            const int cx = q / (HYB * HZB), cy = (q / HZB) % HYB, cz = q % HZB;
+            const long long vo = (long long)(i0 + cx) * nyz + (long long)(j0 + cy) * P.nz + k0 + cz;
+#pragma unroll
+            for (int n = 0; n < HBN / 8; ++n) {
+                const int co = co0 + n * 8 + 2 * tq;
+                float y0 = acc[m][n][2 * hh], y1 = acc[m][n][2 * hh + 1];
+                if (RAW) {
+                    *reinterpret_cast<float2 *>(static_cast<float *>(P.Y) + vo * P.Cout + co) =
+                        make_float2(y0, y1);
+                } else {
+                    y0 = fmaxf(y0 + P.bias[co], 0.f);
+                    y1 = fmaxf(y1 + P.bias[co + 1], 0.f);
+                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<bf16 *>(P.Y) + vo * P.Cout +
+                                                        co) = __floats2bfloat162_rn(y0, y1);
+                }
+            }
+        }
+}
+
 // Weight gradient of a conv3: dW[tap][co][ci] += sum over cells v of
 // dZ[v][co] X[v + tap][ci] (X the concatenated input).  M = co (64 per
 // block), N = ci (32 per block), K = cells in stages of 32, split over
@@ -696,9 +822,17 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
     a.bias = bias;
     a.Cout = Cout;
     a.Y = Y;
+    count_launch();
+    if (nx % HXB == 0 && ny % HYB == 0 && nz % HZB == 0 && Ca % 32 == 0 && Cb % 32 == 0) {
+        const unsigned bricks = (unsigned)((nx / HXB) * (ny / HYB) * (nz / HZB));
+        dim3 hg(bricks, Cout / HBN);
+        const size_t sm = sizeof(HaloSmem<32>);
+        if (raw) k_conv_halo<32, true><<<hg, 128, sm, n->st>>>(a);
+        else k_conv_halo<32, false><<<hg, 128, sm, n->st>>>(a);
+        return;
+    }
     const int BN = Cout >= 64 ? 64 : 32;
     dim3 grid((unsigned)((a.V + CM - 1) / CM), Cout / BN);
-    count_launch();
     if (BN == 64) {
         if (raw) k_conv<64, true><<<grid, 128, 0, n->st>>>(a);
         else k_conv<64, false><<<grid, 128, 0, n->st>>>(a);
@@ -829,6 +963,12 @@ int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out)
         if (rc == VESIS_OK) rc = nalloc(A, &y.Wd, nw);
         if (rc == VESIS_OK) rc = nalloc(A, &y.dW, nw);
     }
+    if (rc == VESIS_OK &&
+        (cudaFuncSetAttribute(k_conv_halo<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(HaloSmem<32>)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_halo<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(HaloSmem<32>)) != cudaSuccess))
+        rc = nfail(VESIS_E_CUDA, "shared memory attribute of the conv kernel");
     if (rc == VESIS_OK && cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess)
         rc = nfail(VESIS_E_ALLOC, "pinned allocation failed");
     if (rc == VESIS_OK) {

@@ -173,6 +173,22 @@ size_t sweep_state_bytes(const GridDesc &g, int r);
 // err: 1 int, part_*: `blocks` entries; k3: the full stencil (device,
 // (2 kw.r + 1)^3, centred) or NULL for the product kernel kw.q; writes the
 // totals into *rs.
+// Bends and torsions of G_ss (atoms.cu): term lists and, per atom, the
+// terms it takes part in (entry = term << 2 | role, role = its position in
+// the term).
+struct BondedDev {
+    int nang = 0, ntor = 0;
+    const int *ang = nullptr;       // [nang][3]
+    const double *angB = nullptr, *angT0 = nullptr;
+    const int *tor = nullptr;       // [ntor][4]
+    const double *torC = nullptr, *torPsi = nullptr;   // [ntor][7]
+    const int *ang_ptr = nullptr, *ang_inc = nullptr;  // CSR over atoms
+    const int *tor_ptr = nullptr, *tor_inc = nullptr;
+};
+// Energies (ordered sums) into e_bend and e_tors; grad (if not NULL) += the
+// terms' gradient; part: nang + ntor doubles of scratch.
+void launch_bonded(const BondedDev &b, const double *xyz, int n, double *part, double *e_bend,
+                   double *e_tors, double *grad, cudaStream_t st);
 // Input features of the learned initialiser (unet.cu): three FP32 planes
 // asinh((U - cfa |E|^2) / scale), asinh(cfa |E|^2 / scale), chi_t.
 void launch_features(const float *U, const float *E, long long G, const uint8_t *chi_t,

@@ -303,6 +303,51 @@ def host_guest(index: int, seed: int = 1, h: float = 0.3, temperature: float = 2
     return sysd
 
 
+def with_bends_torsions(sysd, B: float = 60.0, C=(0.0, 0.6, 0.2, 0.8, 0.0, 0.0, 0.0),
+                        theta0_shift: float = 0.0):
+    """A copy of a system with bending and torsion terms (Eq. Gss) on its
+    bond graph: a bend for every pair of bonds sharing an atom (theta0 the
+    current angle plus theta0_shift, B in kBT/rad^2), a torsion for every
+    path i-j-k-l of three bonds (constants C_0..C_6 in kBT, phases 0 for odd
+    and pi for even n, the convention the paper describes)."""
+    out = dict(sysd)
+    xyz = np.asarray(sysd["xyz"], np.float64)
+    b = np.asarray(sysd["bonds"]).reshape(-1, 2)
+    nb = [[] for _ in range(len(xyz))]
+    for i, j in b:
+        nb[int(i)].append(int(j))
+        nb[int(j)].append(int(i))
+    angles, th0 = [], []
+    for j in range(len(xyz)):
+        ns = sorted(nb[j])
+        for x in range(len(ns)):
+            for y in range(x + 1, len(ns)):
+                i, k = ns[x], ns[y]
+                u, v = xyz[i] - xyz[j], xyz[k] - xyz[j]
+                c = np.dot(u, v) / (np.linalg.norm(u) * np.linalg.norm(v))
+                angles.append((i, j, k))
+                th0.append(min(math.pi, max(0.0, math.acos(min(1.0, max(-1.0, c))) + theta0_shift)))
+    tors = []
+    for j, k in b:
+        j, k = int(j), int(k)
+        for i in sorted(nb[j]):
+            if i == k:
+                continue
+            for l in sorted(nb[k]):
+                if l in (j, i):
+                    continue
+                tors.append((i, j, k, l))
+    n_t = len(tors)
+    psi = np.array([0.0 if n % 2 else math.pi for n in range(7)])
+    out["angles"] = np.array(angles, np.int32).reshape(-1, 3)
+    out["angle_B"] = np.full(len(angles), float(B))
+    out["angle_theta0"] = np.array(th0, np.float64)
+    out["torsions"] = np.array(tors, np.int32).reshape(-1, 4)
+    out["torsion_C"] = np.tile(np.asarray(C, np.float64), (n_t, 1))
+    out["torsion_psi"] = np.tile(psi, (n_t, 1))
+    return out
+
+
 def subset(sysd, idx):
     """The atoms `idx` of a system alone on the same grid (bonds between
     them kept, renumbered)."""

@@ -99,6 +99,7 @@ def lib():
         L.vesis_set_tiles.argtypes = [_p, _i, _i]
         L.vesis_features.argtypes = [_p, _p, _p, _p, _d, _p]
         L.vesis_ss_terms.argtypes = [_p, _p]
+        L.vesis_set_bonded.argtypes = [_p, _i, _p, _p, _p, _i, _p, _p, _p]
         L.vesis_net_create.argtypes = [_i, _p, _p]
         L.vesis_net_param_count.argtypes = [_p, C.POINTER(_ll)]
         L.vesis_net_set_params.argtypes = [_p, _p]
@@ -216,6 +217,10 @@ class System:
             len(bonds), _hp(bonds), _hp(bk), _hp(br),
             _p(self.stream.cuda_stream), C.byref(h)), allow_warn=False)
         self.h = h
+        if len(sysd.get("angles", ())) or len(sysd.get("torsions", ())):
+            self.set_bonded(sysd.get("angles"), sysd.get("angle_B"), sysd.get("angle_theta0"),
+                            sysd.get("torsions"), sysd.get("torsion_C"),
+                            sysd.get("torsion_psi"))
 
     # ------------------------------------------------------------- calls
     def close(self):
@@ -347,10 +352,24 @@ class System:
                         "force_atoms2": t[2], "force_atoms4": t[3]})
 
     def ss_terms(self):
-        """Solute-solute bonds, LJ and Coulomb at the current positions."""
-        out = (_d * 3)()
+        """Solute-solute bonds, LJ, Coulomb, bends and torsions at the
+        current positions."""
+        out = (_d * 5)()
         _check(lib().vesis_ss_terms(self.h, C.cast(out, _p)))
-        return dict(bonds=out[0], lj=out[1], coulomb=out[2])
+        return dict(bonds=out[0], lj=out[1], coulomb=out[2], bend=out[3], torsion=out[4])
+
+    def set_bonded(self, angles=None, angle_B=None, angle_theta0=None, torsions=None,
+                   torsion_C=None, torsion_psi=None):
+        """Bend and torsion terms (vesis_set_bonded); None clears a kind."""
+        a = np.zeros((0, 3), np.int32) if angles is None else _np(angles, np.int32).reshape(-1, 3)
+        t = np.zeros((0, 4), np.int32) if torsions is None else _np(torsions, np.int32).reshape(-1, 4)
+        B = _np(angle_B if angles is not None else np.zeros(0))
+        T0 = _np(angle_theta0 if angles is not None else np.zeros(0))
+        Cc = _np(torsion_C if torsions is not None else np.zeros((0, 7))).reshape(-1, 7)
+        P = _np(torsion_psi if torsions is not None else np.zeros((0, 7))).reshape(-1, 7)
+        self._bonded = (a, B, T0, t, Cc, P)
+        _check(lib().vesis_set_bonded(self.h, len(a), _hp(a), _hp(B), _hp(T0), len(t), _hp(t),
+                                      _hp(Cc), _hp(P)), allow_warn=False)
 
     def features(self, U, E, chi_tight, x, scale=0.01):
         """Learned-initialiser input planes (3 x G floats) into x."""

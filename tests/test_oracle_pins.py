@@ -706,3 +706,63 @@ def test_sin2_parallel_rule_and_heap_exact():
     assert res["flips"] > 0 and res["verify_err"] < 1e-12
     dE, cand = O.delta_e(c2, U, sc)
     assert np.all(dE[cand == 1] >= 0)
+
+
+# ------------------------------------------------------ bends and torsions
+
+def _bt_system(seed=0, shift=0.25):
+    s = synth.protein_like(n_atoms=40, n=32, seed=seed)
+    return synth.with_bends_torsions(s, theta0_shift=shift)
+
+
+def test_bend_and_torsion_closed_forms():
+    """A right angle with theta0 = pi/3 and a torsion of known dihedral
+    (atoms i = (1,0,0), j = 0, k = (0,0,1), l = (cos phi, sin phi, 1): tau =
+    phi) against the definitions written out by hand."""
+    B = 7.0
+    sd = {"xyz": np.array([[1.0, 0, 0], [0, 0, 0], [0, 2.0, 0]]),
+          "angles": np.array([[0, 1, 2]]), "angle_B": np.array([B]),
+          "angle_theta0": np.array([math.pi / 3])}
+    eb, et, _ = O.bonded_terms(sd)
+    assert eb == pytest.approx(0.5 * B * (math.pi / 2 - math.pi / 3) ** 2, rel=1e-14)
+    assert et == 0.0
+    phi = math.radians(60.0)
+    C = np.array([0.3, 0.6, 0.2, 0.8, 0.1, 0.05, 0.02])
+    psi = np.array([0.0, 0.0, math.pi, 0.0, math.pi, 0.0, math.pi])
+    sd = {"xyz": np.array([[1.0, 0, 0], [0, 0, 0], [0, 0, 1.0],
+                           [math.cos(phi), math.sin(phi), 1.0]]),
+          "torsions": np.array([[0, 1, 2, 3]]), "torsion_C": C[None], "torsion_psi": psi[None]}
+    _, et, _ = O.bonded_terms(sd)
+    ref = sum(C[n] * (1 + math.cos(n * phi - psi[n])) for n in range(7))
+    assert et == pytest.approx(ref, rel=1e-13)
+
+
+def test_bend_and_torsion_gradient_finite_differences():
+    s = _bt_system()
+    assert len(s["angles"]) > 10 and len(s["torsions"]) > 10
+    eb, et, g = O.bonded_terms(s)
+    x0 = s["xyz"].copy()
+    h = 1e-6
+    rng = np.random.default_rng(1)
+    for a in rng.choice(len(x0), 8, replace=False):
+        for c in range(3):
+            xp, xm = x0.copy(), x0.copy()
+            xp[a, c] += h
+            xm[a, c] -= h
+            ep = sum(O.bonded_terms(s, xp)[:2])
+            em = sum(O.bonded_terms(s, xm)[:2])
+            assert g[a, c] == pytest.approx((ep - em) / (2 * h), rel=1e-5, abs=1e-7)
+
+
+def test_bend_and_torsion_invariances():
+    """Energies are invariant under rotation and translation; the gradient
+    has no net force and no net torque."""
+    s = _bt_system(seed=2)
+    eb, et, g = O.bonded_terms(s)
+    assert np.allclose(g.sum(axis=0), 0.0, atol=1e-9)
+    assert np.allclose(np.cross(s["xyz"], g).sum(axis=0), 0.0, atol=1e-8)
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
+    x2 = s["xyz"] @ R.T + np.array([1.0, -2.0, 0.5])
+    eb2, et2, _ = O.bonded_terms(s, x2)
+    assert eb2 == pytest.approx(eb, rel=1e-11) and et2 == pytest.approx(et, rel=1e-11)
