@@ -1197,7 +1197,7 @@ int vesis_set_bonded(vesis_system s, int n_angles, const int *ijk, const double 
         if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess)
             return fail(VESIS_E_ALLOC, "device allocation failed");
         s->bonded_allocs.push_back(p);
-        if (bytes && cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        if (src && bytes && cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(VESIS_E_CUDA, "copy of the bonded terms failed");
         *dst = p;
         return VESIS_OK;

@@ -293,6 +293,217 @@ __global__ void __launch_bounds__(128) k_conv_halo(ConvArgs P)
         }
 }
 
+// ------------------------------------------------------ tcgen05 convolution
+// The same convolution on the 5th-generation tensor cores: one block of 4
+// warps per brick of 1 x 16 x 8 cells (M = 128 rows of the accumulator in
+// tensor memory), NT output channels (N), 32 input channels per stage.  The
+// stage's halo (3 x 18 x 10 cells) and weights sit in shared memory in the
+// canonical K-major layout without swizzle (core matrices of 8 rows x 16
+// bytes), so every tap's A operand is the halo itself seen through a
+// descriptor: a core matrix is 8 cells along z (consecutive 16-byte rows),
+// the next 8 rows of M are the next y column (a fixed stride), the next 8
+// channels of K the next channel plane (another fixed stride).  One thread
+// issues the 54 MMAs of a stage (27 taps x 2 steps of K = 16) and commits
+// them to an mbarrier that guards the buffers of the next stage.
+constexpr int TCY = 16, TCZ = 8;                           // brick (x extent 1)
+constexpr int TC_HX = 3, TC_HY = TCY + 2, TC_HZ = TCZ + 2;
+constexpr int TC_HALO_BYTES = TC_HX * TC_HY * 4 * TC_HZ * 16;   // 34,560
+constexpr long long kTcSpin = 1ll << 22;
+
+__host__ __device__ constexpr int tc_w_bytes(int NT) { return 27 * 4 * NT * 16; }
+__host__ __device__ constexpr int tc_smem_bytes(int NT)
+{
+    return tc_w_bytes(NT) + TC_HALO_BYTES + 64;
+}
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets in 16-byte units, descriptor version 1, no swizzle.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (unsigned long long)((addr >> 4) & 0x3fffu) |
+           ((unsigned long long)((lbo >> 4) & 0x3fffu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D,
+// M = 128, N = NT.
+__host__ __device__ constexpr unsigned tc_idesc(int NT)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NT >> 3) << 17) | (8u << 24);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    for (long long i = 0; i < kTcSpin; ++i) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+        __nanosleep(20);
+    }
+    return false;
+}
+
+template <int NT, bool RAW>
+__global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sw = smem;                                 // weights
+    unsigned char *sh = smem + tc_w_bytes(NT);                // halo
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sh + TC_HALO_BYTES);
+    unsigned *tslot = reinterpret_cast<unsigned *>(sh + TC_HALO_BYTES + 8);
+    int *sfail = reinterpret_cast<int *>(sh + TC_HALO_BYTES + 16);
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
+    const int bz = blockIdx.x % nzb, by = (blockIdx.x / nzb) % nyb, bx = blockIdx.x / (nzb * nyb);
+    const int i0 = bx, j0 = by * TCY, k0 = bz * TCZ;
+    const int co0 = blockIdx.y * NT;
+    const int Cin = P.Ca + P.Cb;
+    const long long nyz = (long long)P.ny * P.nz;
+    const int hy = P.ny >> 1, hz = P.nz >> 1;
+    const unsigned bar = smem_u32(mbar);
+    if (t == 0) {
+        *sfail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(NT) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tslot;
+    const unsigned idesc = tc_idesc(NT);
+    const int nstage = Cin / 32;
+    for (int st = 0; st < nstage; ++st) {
+        const int c0 = st * 32;
+        if (st > 0 && !mbar_wait(bar, (unsigned)((st - 1) & 1))) {
+            *sfail = 1;
+            atomicExch(err, 1);
+        }
+        __syncthreads();
+        if (*sfail) break;
+        // weights of the stage: [tap][kc][co][8 ci]
+        for (int e = t; e < 27 * 4 * NT; e += 128) {
+            const int co = e % NT, kc = (e / NT) % 4, tap = e / (4 * NT);
+            const bf16 *src = P.Wt + ((long long)tap * P.Cout + co0 + co) * Cin + c0 + kc * 8;
+            *reinterpret_cast<uint4 *>(sw + (size_t)e * 16) = *reinterpret_cast<const uint4 *>(src);
+        }
+        // halo of the stage: [hx][hy][kc][hz][8 ci]
+        for (int e = t; e < TC_HX * TC_HY * 4 * TC_HZ; e += 128) {
+            const int hzz = e % TC_HZ, kc = (e / TC_HZ) % 4, hyy = (e / (4 * TC_HZ)) % TC_HY,
+                      hxx = e / (4 * TC_HZ * TC_HY);
+            const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz) {
+                const bf16 *src;
+                if (c0 < P.Ca)
+                    src = P.A + ((long long)ii * nyz + (long long)jj * P.nz + kk) * P.Ca + c0;
+                else
+                    src = P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) * P.Cb +
+                          (c0 - P.Ca);
+                v = *reinterpret_cast<const uint4 *>(src + kc * 8);
+            }
+            *reinterpret_cast<uint4 *>(sh + (size_t)e * 16) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned hbase = smem_u32(sh), wbase = smem_u32(sw);
+            for (int tap = 0; tap < 27; ++tap) {
+                const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;   // halo offsets 0..2
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const unsigned a_addr =
+                        hbase + (unsigned)((((da * TC_HY + db) * 4 + 2 * s2) * TC_HZ + dc) * 16);
+                    const unsigned b_addr = wbase + (unsigned)(((tap * 4 + 2 * s2) * NT) * 16);
+                    const unsigned long long ad = tc_desc(a_addr, TC_HZ * 16, 4 * TC_HZ * 16);
+                    const unsigned long long bd = tc_desc(b_addr, NT * 16, 8 * 16);
+                    const unsigned acc = (st > 0 || tap > 0 || s2 > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                        :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(bar) : "memory");
+        }
+    }
+    const bool failed_before = *sfail != 0;
+    __syncthreads();
+    if (!failed_before && !mbar_wait(bar, (unsigned)((nstage - 1) & 1))) {
+        *sfail = 1;     // every thread that timed out marks it; read after the barrier
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!*sfail) {
+        const int m = 32 * w + lane;             // accumulator row = cell of the brick
+        const long long vo = (long long)i0 * nyz + (long long)(j0 + m / TCZ) * P.nz + k0 + m % TCZ;
+#pragma unroll
+        for (int half = 0; half < NT / 32; ++half) {
+            unsigned r[32];
+            const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(32 * half);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                  "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                  "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                  "=r"(r[30]), "=r"(r[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int cb = co0 + 32 * half;
+            if (RAW) {
+                float *dst = static_cast<float *>(P.Y) + vo * P.Cout + cb;
+#pragma unroll
+                for (int c = 0; c < 32; c += 4)
+                    *reinterpret_cast<float4 *>(dst + c) =
+                        make_float4(__uint_as_float(r[c]), __uint_as_float(r[c + 1]),
+                                    __uint_as_float(r[c + 2]), __uint_as_float(r[c + 3]));
+            } else {
+                bf16 *dst = static_cast<bf16 *>(P.Y) + vo * P.Cout + cb;
+#pragma unroll
+                for (int c = 0; c < 32; c += 8) {
+                    __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        o[q] = __floats2bfloat162_rn(
+                            fmaxf(__uint_as_float(r[c + 2 * q]) + P.bias[cb + c + 2 * q], 0.f),
+                            fmaxf(__uint_as_float(r[c + 2 * q + 1]) + P.bias[cb + c + 2 * q + 1],
+                                  0.f));
+                    *reinterpret_cast<uint4 *>(dst + c) = *reinterpret_cast<const uint4 *>(o);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NT)
+                     : "memory");
+    }
+}
+
 // Weight gradient of a conv3: dW[tap][co][ci] += sum over cells v of
 // dZ[v][co] X[v + tap][ci] (X the concatenated input).  M = co (64 per
 // block), N = ci (32 per block), K = cells in stages of 32, split over
@@ -721,6 +932,9 @@ struct vesis_net_t {
     float *ge[4] = {}, *gd[3] = {}, *dX = nullptr;
     bf16 *dZ = nullptr;
     double *h_loss = nullptr;
+    int conv_kind = 0;            // 0 mma.sync, 1 tcgen05 where the shape allows
+    int *d_err = nullptr;         // timeout flag of the tcgen05 convolution
+    int *h_err = nullptr;
     std::vector<void *> act;      // activation allocations
     std::vector<void *> fixed;    // parameter-sized allocations
 };
@@ -823,6 +1037,20 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
     a.Cout = Cout;
     a.Y = Y;
     count_launch();
+    if (n->conv_kind == 1 && ny % TCY == 0 && nz % TCZ == 0 && Ca % 32 == 0 && Cb % 32 == 0 &&
+        Cout % 32 == 0) {
+        const unsigned bricks = (unsigned)(nx * (ny / TCY) * (nz / TCZ));
+        if (Cout % 64 == 0) {
+            dim3 tg(bricks, Cout / 64);
+            if (raw) k_conv_tc<64, true><<<tg, 128, tc_smem_bytes(64), n->st>>>(a, n->d_err);
+            else k_conv_tc<64, false><<<tg, 128, tc_smem_bytes(64), n->st>>>(a, n->d_err);
+        } else {
+            dim3 tg(bricks, Cout / 32);
+            if (raw) k_conv_tc<32, true><<<tg, 128, tc_smem_bytes(32), n->st>>>(a, n->d_err);
+            else k_conv_tc<32, false><<<tg, 128, tc_smem_bytes(32), n->st>>>(a, n->d_err);
+        }
+        return;
+    }
     if (nx % HXB == 0 && ny % HYB == 0 && nz % HZB == 0 && Ca % 32 == 0 && Cb % 32 == 0) {
         const unsigned bricks = (unsigned)((nx / HXB) * (ny / HYB) * (nz / HZB));
         dim3 hg(bricks, Cout / HBN);
@@ -969,6 +1197,20 @@ int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out)
          cudaFuncSetAttribute(k_conv_halo<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(HaloSmem<32>)) != cudaSuccess))
         rc = nfail(VESIS_E_CUDA, "shared memory attribute of the conv kernel");
+    if (rc == VESIS_OK &&
+        (cudaFuncSetAttribute(k_conv_tc<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc_smem_bytes(32)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tc<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc_smem_bytes(32)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tc<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc_smem_bytes(64)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tc<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc_smem_bytes(64)) != cudaSuccess))
+        rc = nfail(VESIS_E_CUDA, "shared memory attribute of the tensor-core conv kernel");
+    if (rc == VESIS_OK) rc = nalloc(A, &n->d_err, 1);
+    if (rc == VESIS_OK && cudaMallocHost(&n->h_err, sizeof(int)) != cudaSuccess)
+        rc = nfail(VESIS_E_ALLOC, "pinned allocation failed");
+    if (rc == VESIS_OK) cudaMemsetAsync(n->d_err, 0, sizeof(int), n->st);
     if (rc == VESIS_OK && cudaMallocHost(&n->h_loss, sizeof(double)) != cudaSuccess)
         rc = nfail(VESIS_E_ALLOC, "pinned allocation failed");
     if (rc == VESIS_OK) {
@@ -1055,8 +1297,18 @@ int vesis_net_forward(vesis_net n, const float *x_dev, int NX, int NY, int NZ, c
         count_launch();
         k_threshold<<<nblk(V), 256, 0, n->st>>>(n->z, V, chi_dev);
     }
+    NCK(cudaMemcpyAsync(n->h_err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->st));
     NCK(cudaGetLastError());
     NCK(cudaStreamSynchronize(n->st));
+    if (*n->h_err) return nfail(VESIS_E_CUDA, "tensor-core convolution: mbarrier wait timed out");
+    return VESIS_OK;
+}
+
+int vesis_net_set_conv_kernel(vesis_net n, int kind)
+{
+    if (!n) return nfail(VESIS_E_ARG, "NULL net");
+    if (kind != 0 && kind != 1) return nfail(VESIS_E_ARG, "kind must be 0 or 1");
+    n->conv_kind = kind;
     return VESIS_OK;
 }
 
@@ -1140,8 +1392,10 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
     NCK(cudaMemcpyAsync(n->h_loss, n->dz, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (grad_host)
         NCK(cudaMemcpyAsync(grad_host, n->grad, n->P * sizeof(float), cudaMemcpyDeviceToHost, st));
+    NCK(cudaMemcpyAsync(n->h_err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     NCK(cudaGetLastError());
     NCK(cudaStreamSynchronize(st));
+    if (*n->h_err) return nfail(VESIS_E_CUDA, "tensor-core convolution: mbarrier wait timed out");
     if (loss_out) *loss_out = *n->h_loss / (double)V[0];
     if (!std::isfinite(*n->h_loss)) return nfail(VESIS_E_NAN, "non-finite loss");
     return VESIS_OK;
@@ -1172,6 +1426,7 @@ int vesis_net_destroy(vesis_net n)
     free_act(n);
     for (void *q : n->fixed) cudaFree(q);
     if (n->h_loss) cudaFreeHost(n->h_loss);
+    if (n->h_err) cudaFreeHost(n->h_err);
     delete n;
     return VESIS_OK;
 }

@@ -107,6 +107,7 @@ def lib():
         L.vesis_net_forward.argtypes = [_p, _p, _i, _i, _i, _p, _p, _p]
         L.vesis_net_loss_grad.argtypes = [_p, _p, _p, _i, _i, _i, _p, C.POINTER(_d), _p]
         L.vesis_net_adam_step.argtypes = [_p, _d, _d, _d, _d]
+        L.vesis_net_set_conv_kernel.argtypes = [_p, _i]
         L.vesis_net_destroy.argtypes = [_p]
         L.vesis_get_tiles.argtypes = [_p, C.POINTER(_i), C.POINTER(_i)]
         L.vesis_autotune.argtypes = [_p, _p, _i, _p]
@@ -485,6 +486,10 @@ class Net:
             self.h, _dp(x, torch.float32, self.F * G), _dp(chi, torch.uint8, G), n[0], n[1],
             n[2], C.cast(c, _p) if c is not None else None, C.byref(loss), _hp(g)))
         return (loss.value, g) if grad else loss.value
+
+    def set_conv_kernel(self, kind):
+        """0: mma.sync convolutions; 1: tcgen05 where the grid allows."""
+        _check(lib().vesis_net_set_conv_kernel(self.h, {"mma": 0, "tcgen05": 1}.get(kind, kind)))
 
     def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(lib().vesis_net_adam_step(self.h, float(lr), float(beta1), float(beta2),

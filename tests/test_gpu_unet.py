@@ -148,3 +148,34 @@ def test_net_arguments():
         net.forward(x, (8, 8, 12), crop=(0, 0, 8, 8, 8, 8))
     with pytest.raises(vs.VesisError):
         net.set_params(np.full(net.P, np.nan, np.float32))
+
+
+def test_tcgen05_convolutions_match_mma_and_oracle():
+    """The tcgen05 path (grids with ny % 16 == 0 and nz % 8 == 0; the
+    coarser levels here fall back to mma.sync) against the mma.sync path
+    and the oracle: logits, loss and every layer's gradient."""
+    vs = _vs()
+    n = (16, 32, 16)
+    theta, x, y = _problem(n, 7)
+    xd = _dev(x.reshape(3, -1).astype(np.float32), torch.float32)
+    yd = _dev(y.reshape(-1), torch.uint8)
+    out = {}
+    for kind in ("mma", "tcgen05"):
+        net = vs.Net(3)
+        net.set_params(theta)
+        net.set_conv_kernel(kind)
+        z = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
+        net.forward(xd, n, logits=z)
+        loss, g = net.loss_grad(xd, yd, n, grad=True)
+        out[kind] = (z.cpu().numpy(), loss, g)
+    zm, zt = out["mma"][0], out["tcgen05"][0]
+    err, cos = _compare(zt.astype(np.float64), zm.astype(np.float64))
+    assert err < 1e-2 and cos > 0.9999, (err, cos)
+    zo = N.forward(theta, x).reshape(-1)
+    err, cos = _compare(zt.astype(np.float64), zo)
+    assert err < 5e-2 and cos > 0.998, (err, cos)
+    lo, go = N.loss_and_grad(theta, x, y.astype(np.float64))
+    assert out["tcgen05"][1] == pytest.approx(lo, rel=1e-2)
+    for name, sl in _layer_slices(3):
+        err, cos = _compare(out["tcgen05"][2][sl].astype(np.float64), go[sl])
+        assert err < 5e-2 and cos > 0.998, (name, err, cos)
