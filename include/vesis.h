@@ -336,8 +336,8 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
 /* Convolution kernels: kind 0 = mma.sync (BF16 tensor-core instructions
  * issued per warp), kind 1 = tcgen05 (5th-generation tensor cores, FP32
  * accumulators in tensor memory) wherever a level's grid has ny % 16 == 0
- * and nz % 8 == 0, kind 0 elsewhere.  Both give the same sums up to FP32
- * rounding order. */
+ * and nz % 8 == 0, kind 0 elsewhere (the default is 1).  Both give the
+ * same sums up to FP32 rounding order. */
 int vesis_net_set_conv_kernel(vesis_net n, int kind);
 
 /* One Adam step with the last gradient (bias-corrected moments). */

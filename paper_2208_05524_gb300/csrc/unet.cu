@@ -352,6 +352,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
     return false;
 }
 
+// 16-byte asynchronous global -> shared copy (zero fill when !valid): the
+// loads of a stage are all in flight together instead of one round trip
+// per iteration.
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+
 template <int NT, bool RAW>
 __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
 {
@@ -395,28 +404,31 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
         __syncthreads();
         if (*sfail) break;
         // weights of the stage: [tap][kc][co][8 ci]
+        const unsigned swa = smem_u32(sw), sha = smem_u32(sh);
         for (int e = t; e < 27 * 4 * NT; e += 128) {
             const int co = e % NT, kc = (e / NT) % 4, tap = e / (4 * NT);
             const bf16 *src = P.Wt + ((long long)tap * P.Cout + co0 + co) * Cin + c0 + kc * 8;
-            *reinterpret_cast<uint4 *>(sw + (size_t)e * 16) = *reinterpret_cast<const uint4 *>(src);
+            cp_async16(swa + (unsigned)e * 16u, src, true);
         }
-        // halo of the stage: [hx][hy][kc][hz][8 ci]
+        // halo of the stage: [hx][hy][kc][hz][8 ci], zero outside the grid
         for (int e = t; e < TC_HX * TC_HY * 4 * TC_HZ; e += 128) {
             const int hzz = e % TC_HZ, kc = (e / TC_HZ) % 4, hyy = (e / (4 * TC_HZ)) % TC_HY,
                       hxx = e / (4 * TC_HZ * TC_HY);
             const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz) {
-                const bf16 *src;
+            const bool in = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz;
+            const bf16 *src = P.A;     // any valid address when nothing is read
+            if (in) {
                 if (c0 < P.Ca)
-                    src = P.A + ((long long)ii * nyz + (long long)jj * P.nz + kk) * P.Ca + c0;
+                    src = P.A + ((long long)ii * nyz + (long long)jj * P.nz + kk) * P.Ca + c0 +
+                          kc * 8;
                 else
                     src = P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) * P.Cb +
-                          (c0 - P.Ca);
-                v = *reinterpret_cast<const uint4 *>(src + kc * 8);
+                          (c0 - P.Ca) + kc * 8;
             }
-            *reinterpret_cast<uint4 *>(sh + (size_t)e * 16) = v;
+            cp_async16(sha + (unsigned)e * 16u, src, in);
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (t == 0) {
@@ -628,25 +640,26 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs P)
 
 // ------------------------------------------------------------ small kernels
 // x (F planes of the full grid NX x NY x NZ, FP32) cropped at (ox, oy, oz)
-// to nx x ny x nz -> X0 [cell][32] bf16, channels >= F zero.
+// to nx x ny x nz -> X0 [cell][32] bf16, channels >= F zero.  One thread per
+// cell: coalesced plane reads, four 16-byte stores.
 __global__ void k_pack_input(const float *__restrict__ x, int F, int NX, int NY, int NZ,
                              int ox, int oy, int oz, int nx, int ny, int nz,
                              bf16 *__restrict__ X0)
 {
     const long long V = (long long)nx * ny * nz;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= V * kInPad) return;
-    const long long v = e / kInPad;
-    const int c = (int)(e - v * kInPad);
-    float val = 0.f;
-    if (c < F) {
-        const int i = (int)(v / ((long long)ny * nz));
-        const int j = (int)((v / nz) % ny);
-        const int k = (int)(v % nz);
-        const long long G = (long long)NX * NY * NZ;
-        val = x[c * G + ((long long)(i + ox) * NY + (j + oy)) * NZ + (k + oz)];
-    }
-    X0[e] = __float2bfloat16(val);
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int i = (int)(v / ((long long)ny * nz));
+    const int j = (int)((v / nz) % ny);
+    const int k = (int)(v % nz);
+    const long long G = (long long)NX * NY * NZ;
+    const long long src = ((long long)(i + ox) * NY + (j + oy)) * NZ + (k + oz);
+    __align__(16) bf16 c[kInPad];
+#pragma unroll
+    for (int q = 0; q < kInPad; ++q) c[q] = __float2bfloat16(q < F ? x[q * G + src] : 0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(X0 + v * kInPad);
+#pragma unroll
+    for (int q = 0; q < kInPad / 8; ++q) dst[q] = reinterpret_cast<const uint4 *>(c)[q];
 }
 
 // 2x2x2 mean pooling of [cell][C] bf16 at (nx, ny, nz) -> half resolution.
@@ -932,7 +945,7 @@ struct vesis_net_t {
     float *ge[4] = {}, *gd[3] = {}, *dX = nullptr;
     bf16 *dZ = nullptr;
     double *h_loss = nullptr;
-    int conv_kind = 0;            // 0 mma.sync, 1 tcgen05 where the shape allows
+    int conv_kind = 1;            // 0 mma.sync, 1 tcgen05 where the shape allows
     int *d_err = nullptr;         // timeout flag of the tcgen05 convolution
     int *h_err = nullptr;
     std::vector<void *> act;      // activation allocations
@@ -1109,8 +1122,8 @@ void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy
     Layer *L = n->L;
     const float *th = n->theta;
     count_launch();
-    k_pack_input<<<nblk(V0 * kInPad), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny,
-                                                       nz, n->X0);
+    k_pack_input<<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
+                                              n->X0);
     conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, th + L[L_E0].b_off, 32, n->e[0],
          false);
     for (int l = 1; l < 4; ++l) {
