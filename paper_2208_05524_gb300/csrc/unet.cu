@@ -516,6 +516,212 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
     }
 }
 
+// Weight-stationary form: each block takes TCW_NB consecutive bricks and
+// keeps a stage's weights in shared memory for all of them, with one FP32
+// accumulator per brick in tensor memory (TCW_NB x NT columns).  The
+// bricks' halos stream through two buffers: the next brick's halo loads
+// (cp.async) while the tensor cores run the current brick's 54 MMAs; a
+// buffer is refilled once the MMAs that read it have committed.  Stage
+// boundaries wait for the stage's last MMAs before the weights are
+// replaced.
+constexpr int TCW_NB = 8;
+
+__host__ __device__ constexpr int tcw_smem_bytes(int NT)
+{
+    return tc_w_bytes(NT) + 2 * TC_HALO_BYTES + 64;
+}
+
+template <int NT, bool RAW>
+__global__ void __launch_bounds__(128, 1) k_conv_tcw(ConvArgs P, int nbricks, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sw = smem;
+    unsigned char *sh0 = smem + tc_w_bytes(NT);
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sh0 + 2 * TC_HALO_BYTES);
+    unsigned *tslot = reinterpret_cast<unsigned *>(sh0 + 2 * TC_HALO_BYTES + 16);
+    int *sfail = reinterpret_cast<int *>(sh0 + 2 * TC_HALO_BYTES + 20);
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
+    const int b0 = blockIdx.x * TCW_NB;
+    const int nbv = min(TCW_NB, nbricks - b0);          // bricks of this block
+    const int Cin = P.Ca + P.Cb;
+    const int nst = Cin / 32;
+    const int U = nst * nbv;
+    const int co0 = blockIdx.y * NT;
+    const long long nyz = (long long)P.ny * P.nz;
+    const int hy = P.ny >> 1, hz = P.nz >> 1;
+    const unsigned bar0 = smem_u32(mbar), swa = smem_u32(sw), sha0 = smem_u32(sh0);
+    if (t == 0) {
+        *sfail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(TCW_NB * NT) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tslot;
+    const unsigned idesc = tc_idesc(NT);
+
+    // loads of unit u (stage u / nbv, brick u % nbv): its halo into buffer
+    // u & 1, and the stage's weights when it is the stage's first unit
+    auto issue = [&](int u) {
+        const int st = u / nbv, bb = b0 + u % nbv, c0 = st * 32;
+        const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
+        const int i0 = bx, j0 = by * TCY, k0 = bz * TCZ;
+        if (u % nbv == 0) {
+            for (int e = t; e < 27 * 4 * NT; e += 128) {
+                const int co = e % NT, kc = (e / NT) % 4, tap = e / (4 * NT);
+                cp_async16(swa + (unsigned)e * 16u,
+                           P.Wt + ((long long)tap * P.Cout + co0 + co) * Cin + c0 + kc * 8, true);
+            }
+        }
+        const unsigned sha = sha0 + (unsigned)((u & 1) * TC_HALO_BYTES);
+        for (int e = t; e < TC_HX * TC_HY * 4 * TC_HZ; e += 128) {
+            const int hzz = e % TC_HZ, kc = (e / TC_HZ) % 4, hyy = (e / (4 * TC_HZ)) % TC_HY,
+                      hxx = e / (4 * TC_HZ * TC_HY);
+            const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
+            const bool in = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz;
+            const bf16 *src = P.A;
+            if (in) {
+                if (c0 < P.Ca)
+                    src = P.A + ((long long)ii * nyz + (long long)jj * P.nz + kk) * P.Ca + c0 +
+                          kc * 8;
+                else
+                    src = P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) * P.Cb +
+                          (c0 - P.Ca) + kc * 8;
+            }
+            cp_async16(sha + (unsigned)e * 16u, src, in);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // unit v's MMAs have completed (its commit arrived on barrier v & 1)
+    auto done = [&](int v) -> bool {
+        return mbar_wait(bar0 + 8u * (unsigned)(v & 1), (unsigned)((v >> 1) & 1));
+    };
+
+    if (U > 0) issue(0);
+    for (int u = 0; u < U; ++u) {
+        const int nu = u + 1;
+        bool pre = false;
+        if (nu < U && nu % nbv != 0) {
+            if (nu >= 2 && !done(nu - 2)) { *sfail = 1; atomicExch(err, 1); }
+            if (!*sfail) {
+                issue(nu);
+                pre = true;
+            }
+        }
+        if (pre) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (*sfail) break;
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int st = u / nbv, b = u % nbv;
+            const unsigned hbase = sha0 + (unsigned)((u & 1) * TC_HALO_BYTES);
+            const unsigned dcol = tmem + (unsigned)(b * NT);
+            for (int tap = 0; tap < 27; ++tap) {
+                const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const unsigned a_addr =
+                        hbase + (unsigned)((((da * TC_HY + db) * 4 + 2 * s2) * TC_HZ + dc) * 16);
+                    const unsigned b_addr = swa + (unsigned)(((tap * 4 + 2 * s2) * NT) * 16);
+                    const unsigned long long ad = tc_desc(a_addr, TC_HZ * 16, 4 * TC_HZ * 16);
+                    const unsigned long long bd = tc_desc(b_addr, NT * 16, 8 * 16);
+                    const unsigned acc = (st > 0 || tap > 0 || s2 > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                        :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(bar0 + 8u * (unsigned)(u & 1)) : "memory");
+        }
+        if (nu < U && nu % nbv == 0) {
+            // stage boundary: the weights are replaced once every MMA of
+            // the stage (unit u and all before it) has completed
+            if (!done(u)) { *sfail = 1; atomicExch(err, 1); }
+            __syncthreads();
+            if (*sfail) break;
+            issue(nu);
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    const bool failed_before = *sfail != 0;
+    __syncthreads();
+    if (!failed_before && U > 0 && !done(U - 1)) {
+        *sfail = 1;
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!*sfail) {
+        const int m = 32 * w + lane;
+        for (int b = 0; b < nbv; ++b) {
+            const int bb = b0 + b;
+            const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
+            const long long vo = (long long)bx * nyz + (long long)(by * TCY + m / TCZ) * P.nz +
+                                 bz * TCZ + m % TCZ;
+#pragma unroll
+            for (int half = 0; half < NT / 32; ++half) {
+                unsigned r[32];
+                const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(b * NT + 32 * half);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                      "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                      "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                      "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                      "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                      "=r"(r[30]), "=r"(r[31])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int cb = co0 + 32 * half;
+                if (RAW) {
+                    float *dst = static_cast<float *>(P.Y) + vo * P.Cout + cb;
+#pragma unroll
+                    for (int c = 0; c < 32; c += 4)
+                        *reinterpret_cast<float4 *>(dst + c) =
+                            make_float4(__uint_as_float(r[c]), __uint_as_float(r[c + 1]),
+                                        __uint_as_float(r[c + 2]), __uint_as_float(r[c + 3]));
+                } else {
+                    bf16 *dst = static_cast<bf16 *>(P.Y) + vo * P.Cout + cb;
+#pragma unroll
+                    for (int c = 0; c < 32; c += 8) {
+                        __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            o[q] = __floats2bfloat162_rn(
+                                fmaxf(__uint_as_float(r[c + 2 * q]) + P.bias[cb + c + 2 * q], 0.f),
+                                fmaxf(__uint_as_float(r[c + 2 * q + 1]) + P.bias[cb + c + 2 * q + 1],
+                                      0.f));
+                        *reinterpret_cast<uint4 *>(dst + c) = *reinterpret_cast<const uint4 *>(o);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"(TCW_NB * NT) : "memory");
+    }
+}
+
 // Weight gradient of a conv3: dW[tap][co][ci] += sum over cells v of
 // dZ[v][co] X[v + tap][ci] (X the concatenated input).  M = co (64 per
 // block), N = ci (32 per block), K = cells in stages of 32, split over
@@ -1053,6 +1259,19 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
     if (n->conv_kind == 1 && ny % TCY == 0 && nz % TCZ == 0 && Ca % 32 == 0 && Cb % 32 == 0 &&
         Cout % 32 == 0) {
         const unsigned bricks = (unsigned)(nx * (ny / TCY) * (nz / TCZ));
+        if (bricks >= 152u * TCW_NB) {    // enough bricks for weight-stationary blocks
+            const unsigned nb = (bricks + TCW_NB - 1) / TCW_NB;
+            if (Cout % 64 == 0) {
+                dim3 tg(nb, Cout / 64);
+                if (raw) k_conv_tcw<64, true><<<tg, 128, tcw_smem_bytes(64), n->st>>>(a, (int)bricks, n->d_err);
+                else k_conv_tcw<64, false><<<tg, 128, tcw_smem_bytes(64), n->st>>>(a, (int)bricks, n->d_err);
+            } else {
+                dim3 tg(nb, Cout / 32);
+                if (raw) k_conv_tcw<32, true><<<tg, 128, tcw_smem_bytes(32), n->st>>>(a, (int)bricks, n->d_err);
+                else k_conv_tcw<32, false><<<tg, 128, tcw_smem_bytes(32), n->st>>>(a, (int)bricks, n->d_err);
+            }
+            return;
+        }
         if (Cout % 64 == 0) {
             dim3 tg(bricks, Cout / 64);
             if (raw) k_conv_tc<64, true><<<tg, 128, tc_smem_bytes(64), n->st>>>(a, n->d_err);
@@ -1218,7 +1437,15 @@ int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out)
          cudaFuncSetAttribute(k_conv_tc<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               tc_smem_bytes(64)) != cudaSuccess ||
          cudaFuncSetAttribute(k_conv_tc<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tc_smem_bytes(64)) != cudaSuccess))
+                              tc_smem_bytes(64)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tcw<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tcw_smem_bytes(32)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tcw<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tcw_smem_bytes(32)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tcw<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tcw_smem_bytes(64)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tcw<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tcw_smem_bytes(64)) != cudaSuccess))
         rc = nfail(VESIS_E_CUDA, "shared memory attribute of the tensor-core conv kernel");
     if (rc == VESIS_OK) rc = nalloc(A, &n->d_err, 1);
     if (rc == VESIS_OK && cudaMallocHost(&n->h_err, sizeof(int)) != cudaSuccess)

@@ -179,3 +179,30 @@ def test_tcgen05_convolutions_match_mma_and_oracle():
     for name, sl in _layer_slices(3):
         err, cos = _compare(out["tcgen05"][2][sl].astype(np.float64), go[sl])
         assert err < 5e-2 and cos > 0.998, (name, err, cos)
+
+
+def test_weight_stationary_tcgen05_matches_mma():
+    """A 64^3 grid: its full-resolution levels have enough 16 x 8 bricks for
+    the weight-stationary tcgen05 kernel (8 bricks per block sharing one
+    weight load, accumulators in tensor memory); logits and gradients
+    against the mma.sync path."""
+    vs = _vs()
+    n = (64, 64, 64)
+    theta, x, y = _problem(n, 9)
+    xd = _dev(x.reshape(3, -1).astype(np.float32), torch.float32)
+    yd = _dev(y.reshape(-1), torch.uint8)
+    out = {}
+    for kind in ("mma", "tcgen05"):
+        net = vs.Net(3)
+        net.set_params(theta)
+        net.set_conv_kernel(kind)
+        z = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
+        net.forward(xd, n, logits=z)
+        loss, g = net.loss_grad(xd, yd, n, grad=True)
+        out[kind] = (z.cpu().numpy().astype(np.float64), loss, g.astype(np.float64))
+    err, cos = _compare(out["tcgen05"][0], out["mma"][0])
+    assert err < 1e-2 and cos > 0.9999, (err, cos)
+    assert out["tcgen05"][1] == pytest.approx(out["mma"][1], rel=1e-3)
+    for name, sl in _layer_slices(3):
+        err, cos = _compare(out["tcgen05"][2][sl], out["mma"][2][sl])
+        assert err < 2e-2 and cos > 0.9998, (name, err, cos)
