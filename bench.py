@@ -696,12 +696,15 @@ def run_learned(args, world, rank, local):
                  for i in range(args.learn_systems)]
     data_s = time.perf_counter() - t0
     net = vesis.Net(3)
+    net.set_conv_kernel(args.conv_kernel)
     learned.init_params(net, seed=0)
     train_s, losses = timed(lambda: learned.train(net, train_set, steps=args.learn_steps,
                                                   crop=64, lr=1e-3, seed=1))
     cells_trained = args.learn_steps * 64 ** 3
     del train_set
-    cx = learned.example(synth.two_domain_complex(), keep_system=True)
+    target = synth.two_domain_complex() if args.learn_target == "complex" else \
+        synth.protein_like(n_atoms=500, n=128, h=0.4, seed=4)
+    cx = learned.example(target, keep_system=True)
     S = cx["system"]
     chi = cx["chi_t"].clone()
     cold_s, rc = timed(lambda: S.blsm_relax(chi, cx["U"], cx["E"]))
@@ -713,10 +716,14 @@ def run_learned(args, world, rank, local):
     out = {"metric": "sec per interface relaxation, learned guess + sweep vs tight start",
            "value": guess_s + sweep_s, "unit": "s", "higher_is_better": False,
            "n_gpus": world, "data": "synthetic", "dtype": "bf16 net, f32 fields",
-           "config": {"workload": "two_domain_complex_20000_grid384",
-                      "desc": "two 10,000-atom random-walk globules 6 A apart, 384^3 grid, "
-                              "h=0.4 A, seed 2; net trained on host-guest systems "
-                              "(seed 3, h=0.4 A)"},
+           "config": ({"workload": "two_domain_complex_20000_grid384",
+                       "desc": "two 10,000-atom random-walk globules 6 A apart, 384^3 grid, "
+                               "h=0.4 A, seed 2; net trained on host-guest systems "
+                               "(seed 3, h=0.4 A)"}
+                      if args.learn_target == "complex" else
+                      {"workload": "protein500_grid128",
+                       "desc": "500-atom protein-like solute, 128^3 grid, h=0.4 A, seed 4 "
+                               "(small case for profiling)"}),
            "tight_start": {"s": cold_s, "rounds": rc["rounds"], "flips": rc["flips"],
                            "G": rc["terms"]["total"], "label_mismatches": miss_tight},
            "learned_start": {"guess_s": guess_s, "sweep_s": sweep_s, "rounds": rg["rounds"],
@@ -807,6 +814,8 @@ def main():
                     help="train the learned initialiser and apply it to the two-domain complex")
     ap.add_argument("--learn-systems", type=int, default=24)
     ap.add_argument("--learn-steps", type=int, default=600)
+    ap.add_argument("--learn-target", default="complex", choices=["complex", "protein128"])
+    ap.add_argument("--conv-kernel", default="tcgen05", choices=["tcgen05", "mma"])
     ap.add_argument("--heap", action="store_true",
                     help="time the literal serial flipping on the single ion")
     ap.add_argument("--batch", action="store_true",

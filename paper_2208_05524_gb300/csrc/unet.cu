@@ -525,6 +525,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
 // boundaries wait for the stage's last MMAs before the weights are
 // replaced.
 constexpr int TCW_NB = 8;
+constexpr int TCW_T = 512;      // 16 warps: the stage copies are address-bound, not bandwidth-bound
 
 __host__ __device__ constexpr int tcw_smem_bytes(int NT)
 {
@@ -532,7 +533,7 @@ __host__ __device__ constexpr int tcw_smem_bytes(int NT)
 }
 
 template <int NT, bool RAW>
-__global__ void __launch_bounds__(128, 1) k_conv_tcw(ConvArgs P, int nbricks, int *err)
+__global__ void __launch_bounds__(TCW_T, 1) k_conv_tcw(ConvArgs P, int nbricks, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sw = smem;
@@ -575,14 +576,14 @@ __global__ void __launch_bounds__(128, 1) k_conv_tcw(ConvArgs P, int nbricks, in
         const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
         const int i0 = bx, j0 = by * TCY, k0 = bz * TCZ;
         if (u % nbv == 0) {
-            for (int e = t; e < 27 * 4 * NT; e += 128) {
+            for (int e = t; e < 27 * 4 * NT; e += TCW_T) {
                 const int co = e % NT, kc = (e / NT) % 4, tap = e / (4 * NT);
                 cp_async16(swa + (unsigned)e * 16u,
                            P.Wt + ((long long)tap * P.Cout + co0 + co) * Cin + c0 + kc * 8, true);
             }
         }
         const unsigned sha = sha0 + (unsigned)((u & 1) * TC_HALO_BYTES);
-        for (int e = t; e < TC_HX * TC_HY * 4 * TC_HZ; e += 128) {
+        for (int e = t; e < TC_HX * TC_HY * 4 * TC_HZ; e += TCW_T) {
             const int hzz = e % TC_HZ, kc = (e / TC_HZ) % 4, hyy = (e / (4 * TC_HZ)) % TC_HY,
                       hxx = e / (4 * TC_HZ * TC_HY);
             const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
@@ -666,8 +667,11 @@ __global__ void __launch_bounds__(128, 1) k_conv_tcw(ConvArgs P, int nbricks, in
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!*sfail) {
-        const int m = 32 * w + lane;
-        for (int b = 0; b < nbv; ++b) {
+        // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane
+        // quarter) of the bricks w / 4, w / 4 + TCW_T / 128, ...
+        const int lq = w & 3;
+        const int m = 32 * lq + lane;
+        for (int b = w >> 2; b < nbv; b += TCW_T / 128) {
             const int bb = b0 + b;
             const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
             const long long vo = (long long)bx * nyz + (long long)(by * TCY + m / TCZ) * P.nz +
@@ -675,7 +679,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_tcw(ConvArgs P, int nbricks, in
 #pragma unroll
             for (int half = 0; half < NT / 32; ++half) {
                 unsigned r[32];
-                const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(b * NT + 32 * half);
+                const unsigned ta = tmem + ((unsigned)(32 * lq) << 16) + (unsigned)(b * NT + 32 * half);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -1263,12 +1267,12 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
             const unsigned nb = (bricks + TCW_NB - 1) / TCW_NB;
             if (Cout % 64 == 0) {
                 dim3 tg(nb, Cout / 64);
-                if (raw) k_conv_tcw<64, true><<<tg, 128, tcw_smem_bytes(64), n->st>>>(a, (int)bricks, n->d_err);
-                else k_conv_tcw<64, false><<<tg, 128, tcw_smem_bytes(64), n->st>>>(a, (int)bricks, n->d_err);
+                if (raw) k_conv_tcw<64, true><<<tg, TCW_T, tcw_smem_bytes(64), n->st>>>(a, (int)bricks, n->d_err);
+                else k_conv_tcw<64, false><<<tg, TCW_T, tcw_smem_bytes(64), n->st>>>(a, (int)bricks, n->d_err);
             } else {
                 dim3 tg(nb, Cout / 32);
-                if (raw) k_conv_tcw<32, true><<<tg, 128, tcw_smem_bytes(32), n->st>>>(a, (int)bricks, n->d_err);
-                else k_conv_tcw<32, false><<<tg, 128, tcw_smem_bytes(32), n->st>>>(a, (int)bricks, n->d_err);
+                if (raw) k_conv_tcw<32, true><<<tg, TCW_T, tcw_smem_bytes(32), n->st>>>(a, (int)bricks, n->d_err);
+                else k_conv_tcw<32, false><<<tg, TCW_T, tcw_smem_bytes(32), n->st>>>(a, (int)bricks, n->d_err);
             }
             return;
         }
