@@ -19,6 +19,7 @@
 // weights, gradients and Adam moments in one flat vector.  The convolutions
 // are implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16 in, FP32
 // accumulate); the rest are plain elementwise and reduction kernels.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "vesis_internal.cuh"
@@ -516,46 +517,65 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
     }
 }
 
-// Weight-stationary form: each block takes TCW_NB consecutive bricks and
+// Weight-stationary blocks: each block takes TCW_NB consecutive bricks and
 // keeps a stage's weights in shared memory for all of them, with one FP32
 // accumulator per brick in tensor memory (TCW_NB x NT columns).  The
 // bricks' halos stream through two buffers: the next brick's halo loads
-// (cp.async) while the tensor cores run the current brick's 54 MMAs; a
-// buffer is refilled once the MMAs that read it have committed.  Stage
-// boundaries wait for the stage's last MMAs before the weights are
-// replaced.
+// while the tensor cores run the current brick's 54 MMAs; a buffer is
+// refilled once the MMAs that read it have committed.  Stage boundaries
+// wait for the stage's last MMAs before the weights are replaced.
 constexpr int TCW_NB = 8;
-constexpr int TCW_T = 512;      // 16 warps: the stage copies are address-bound, not bandwidth-bound
+constexpr int TCW_T = 512;      // 16 warps: the copies of a coarse-input stage
 
-__host__ __device__ constexpr int tcw_smem_bytes(int NT)
+// TMA form of the weight-stationary convolution.  The stage's weights come
+// pre-arranged in global memory (one contiguous block per stage and tile of
+// output channels) and arrive by one bulk copy; the halo of a skip-input
+// stage arrives as four tensor-map box loads (8 channels x 10 z x 18 y x 3
+// x each, cells outside the grid zero-filled by the copy engine); the
+// halo of a coarse-input stage (read at half coordinates) is gathered with
+// cp.async.  Both complete on an mbarrier with a transaction count.  Halo
+// layout: [8-channel plane][x][y][z][8 ch], planes 128-byte aligned.
+constexpr int TMA_PLANE = 8704;                         // 540 x 16 B padded to 128 B
+constexpr int TMA_HALO = 4 * TMA_PLANE;
+
+__host__ __device__ constexpr int tma_smem_bytes(int NT)
 {
-    return tc_w_bytes(NT) + 2 * TC_HALO_BYTES + 64;
+    return tc_w_bytes(NT) + 2 * TMA_HALO + 64 + 128;
 }
 
 template <int NT, bool RAW>
-__global__ void __launch_bounds__(TCW_T, 1) k_conv_tcw(ConvArgs P, int nbricks, int *err)
+__global__ void __launch_bounds__(TCW_T, 1)
+k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__restrict__ Wtc,
+           int nbricks, int *err)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_tma[];
+    // 128-byte aligned base for the copy engine's destinations
+    const unsigned raw0 = smem_u32(smem_tma);
+    const unsigned pad = ((raw0 + 127u) & ~127u) - raw0;
+    unsigned char *smem = smem_tma + pad;
     unsigned char *sw = smem;
     unsigned char *sh0 = smem + tc_w_bytes(NT);
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sh0 + 2 * TC_HALO_BYTES);
-    unsigned *tslot = reinterpret_cast<unsigned *>(sh0 + 2 * TC_HALO_BYTES + 16);
-    int *sfail = reinterpret_cast<int *>(sh0 + 2 * TC_HALO_BYTES + 20);
+    unsigned char *tail = sh0 + 2 * TMA_HALO;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tail);   // 2 MMA + 2 load
+    unsigned *tslot = reinterpret_cast<unsigned *>(tail + 32);
+    int *sfail = reinterpret_cast<int *>(tail + 36);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
     const int b0 = blockIdx.x * TCW_NB;
-    const int nbv = min(TCW_NB, nbricks - b0);          // bricks of this block
+    const int nbv = min(TCW_NB, nbricks - b0);
     const int Cin = P.Ca + P.Cb;
     const int nst = Cin / 32;
     const int U = nst * nbv;
+    const int nnt = P.Cout / NT;
     const int co0 = blockIdx.y * NT;
-    const long long nyz = (long long)P.ny * P.nz;
     const int hy = P.ny >> 1, hz = P.nz >> 1;
-    const unsigned bar0 = smem_u32(mbar), swa = smem_u32(sw), sha0 = smem_u32(sh0);
+    const unsigned mbar0 = smem_u32(mbar), ldbar0 = mbar0 + 16u;
+    const unsigned swa = smem_u32(sw), sha0 = smem_u32(sh0);
     if (t == 0) {
         *sfail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0 + 8) : "memory");
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar0 + 8u * q) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (w == 0) {
@@ -569,41 +589,57 @@ __global__ void __launch_bounds__(TCW_T, 1) k_conv_tcw(ConvArgs P, int nbricks, 
     const unsigned tmem = *tslot;
     const unsigned idesc = tc_idesc(NT);
 
-    // loads of unit u (stage u / nbv, brick u % nbv): its halo into buffer
-    // u & 1, and the stage's weights when it is the stage's first unit
     auto issue = [&](int u) {
         const int st = u / nbv, bb = b0 + u % nbv, c0 = st * 32;
         const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
         const int i0 = bx, j0 = by * TCY, k0 = bz * TCZ;
-        if (u % nbv == 0) {
-            for (int e = t; e < 27 * 4 * NT; e += TCW_T) {
-                const int co = e % NT, kc = (e / NT) % 4, tap = e / (4 * NT);
-                cp_async16(swa + (unsigned)e * 16u,
-                           P.Wt + ((long long)tap * P.Cout + co0 + co) * Cin + c0 + kc * 8, true);
+        const unsigned sha = sha0 + (unsigned)((u & 1) * TMA_HALO);
+        const unsigned lb = ldbar0 + 8u * (unsigned)(u & 1);
+        const bool a_stage = c0 < P.Ca, wload = (u % nbv) == 0;
+        if (t == 0) {
+            const unsigned tx = (a_stage ? 4u * 540u * 16u : 0u) + (wload ? (unsigned)tc_w_bytes(NT) : 0u);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(lb), "r"(tx) : "memory");
+            if (wload) {
+                const bf16 *src = Wtc + (size_t)(st * nnt + blockIdx.y) * (4 * 27 * NT * 8);
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                    :: "r"(swa), "l"(src), "r"((unsigned)tc_w_bytes(NT)), "r"(lb) : "memory");
+            }
+            if (a_stage) {
+#pragma unroll
+                for (int kc = 0; kc < 4; ++kc)
+                    asm volatile(
+                        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                        :: "r"(sha + (unsigned)(kc * TMA_PLANE)),
+                           "l"(reinterpret_cast<unsigned long long>(&tmA)),
+                           "r"(c0 + 8 * kc), "r"(k0 - 1), "r"(j0 - 1), "r"(i0 - 1), "r"(lb)
+                        : "memory");
             }
         }
-        const unsigned sha = sha0 + (unsigned)((u & 1) * TC_HALO_BYTES);
-        for (int e = t; e < TC_HX * TC_HY * 4 * TC_HZ; e += TCW_T) {
-            const int hzz = e % TC_HZ, kc = (e / TC_HZ) % 4, hyy = (e / (4 * TC_HZ)) % TC_HY,
-                      hxx = e / (4 * TC_HZ * TC_HY);
-            const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
-            const bool in = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz;
-            const bf16 *src = P.A;
-            if (in) {
-                if (c0 < P.Ca)
-                    src = P.A + ((long long)ii * nyz + (long long)jj * P.nz + kk) * P.Ca + c0 +
-                          kc * 8;
-                else
-                    src = P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) * P.Cb +
-                          (c0 - P.Ca) + kc * 8;
+        if (!a_stage) {
+            // coarse input: cell (x, y, z) of the halo reads the coarse cell
+            // at half its grid coordinates; four threads per cell, one per
+            // 8-channel plane
+            for (int e = t; e < TC_HX * TC_HY * TC_HZ * 4; e += TCW_T) {
+                const int kc = e & 3, cell = e >> 2;
+                const int hzz = cell % TC_HZ, hyy = (cell / TC_HZ) % TC_HY, hxx = cell / (TC_HZ * TC_HY);
+                const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
+                const bool in = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz;
+                const bf16 *src = in ? P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) *
+                                               P.Cb + (c0 - P.Ca) + kc * 8
+                                     : P.B;
+                cp_async16(sha + (unsigned)(kc * TMA_PLANE + cell * 16), src, in);
             }
-            cp_async16(sha + (unsigned)e * 16u, src, in);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    // unit v's MMAs have completed (its commit arrived on barrier v & 1)
+    auto loaded = [&](int u) -> bool {
+        return mbar_wait(ldbar0 + 8u * (unsigned)(u & 1), (unsigned)((u >> 1) & 1));
+    };
     auto done = [&](int v) -> bool {
-        return mbar_wait(bar0 + 8u * (unsigned)(v & 1), (unsigned)((v >> 1) & 1));
+        return mbar_wait(mbar0 + 8u * (unsigned)(v & 1), (unsigned)((v >> 1) & 1));
     };
 
     if (U > 0) issue(0);
@@ -619,24 +655,26 @@ __global__ void __launch_bounds__(TCW_T, 1) k_conv_tcw(ConvArgs P, int nbricks, 
         }
         if (pre) asm volatile("cp.async.wait_group 1;" ::: "memory");
         else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        if (!loaded(u)) { *sfail = 1; atomicExch(err, 1); }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (*sfail) break;
         if (t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int st = u / nbv, b = u % nbv;
-            const unsigned hbase = sha0 + (unsigned)((u & 1) * TC_HALO_BYTES);
+            (void)st;
+            const unsigned hbase = sha0 + (unsigned)((u & 1) * TMA_HALO);
             const unsigned dcol = tmem + (unsigned)(b * NT);
             for (int tap = 0; tap < 27; ++tap) {
                 const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
 #pragma unroll
                 for (int s2 = 0; s2 < 2; ++s2) {
-                    const unsigned a_addr =
-                        hbase + (unsigned)((((da * TC_HY + db) * 4 + 2 * s2) * TC_HZ + dc) * 16);
-                    const unsigned b_addr = swa + (unsigned)(((tap * 4 + 2 * s2) * NT) * 16);
-                    const unsigned long long ad = tc_desc(a_addr, TC_HZ * 16, 4 * TC_HZ * 16);
-                    const unsigned long long bd = tc_desc(b_addr, NT * 16, 8 * 16);
-                    const unsigned acc = (st > 0 || tap > 0 || s2 > 0) ? 1u : 0u;
+                    const unsigned a_addr = hbase + (unsigned)(2 * s2 * TMA_PLANE) +
+                                            (unsigned)(((da * TC_HY + db) * TC_HZ + dc) * 16);
+                    const unsigned b_addr = swa + (unsigned)(((2 * s2 * 27 + tap) * NT) * 16);
+                    const unsigned long long ad = tc_desc(a_addr, TMA_PLANE, TC_HZ * 16);
+                    const unsigned long long bd = tc_desc(b_addr, 27 * NT * 16, 8 * 16);
+                    const unsigned acc = (u >= nbv || tap > 0 || s2 > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"
@@ -645,11 +683,9 @@ __global__ void __launch_bounds__(TCW_T, 1) k_conv_tcw(ConvArgs P, int nbricks, 
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(bar0 + 8u * (unsigned)(u & 1)) : "memory");
+                         :: "r"(mbar0 + 8u * (unsigned)(u & 1)) : "memory");
         }
         if (nu < U && nu % nbv == 0) {
-            // stage boundary: the weights are replaced once every MMA of
-            // the stage (unit u and all before it) has completed
             if (!done(u)) { *sfail = 1; atomicExch(err, 1); }
             __syncthreads();
             if (*sfail) break;
@@ -667,8 +703,7 @@ __global__ void __launch_bounds__(TCW_T, 1) k_conv_tcw(ConvArgs P, int nbricks, 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!*sfail) {
-        // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane
-        // quarter) of the bricks w / 4, w / 4 + TCW_T / 128, ...
+        const long long nyz = (long long)P.ny * P.nz;
         const int lq = w & 3;
         const int m = 32 * lq + lane;
         for (int b = w >> 2; b < nbv; b += TCW_T / 128) {
@@ -724,6 +759,22 @@ __global__ void __launch_bounds__(TCW_T, 1) k_conv_tcw(ConvArgs P, int nbricks, 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      :: "r"(tmem), "r"(TCW_NB * NT) : "memory");
     }
+}
+
+// Weights [27][Cout][Cin] -> the TMA form's layout: per stage of 32 input
+// channels and tile of NT output channels, [8-channel plane][tap][co][8].
+__global__ void k_pack_tc(const bf16 *__restrict__ W, int Cout, int Cin, int NT,
+                          bf16 *__restrict__ out)
+{
+    const long long n = 27ll * Cout * Cin;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int tap = (int)(e / ((long long)Cout * Cin));
+    const int co = (int)((e / Cin) % Cout);
+    const int ci = (int)(e % Cin);
+    const int st = ci / 32, kc = (ci % 32) / 8, j = ci % 8;
+    const int nt = co / NT, col = co % NT, nnt = Cout / NT;
+    out[((((long long)(st * nnt + nt) * 4 + kc) * 27 + tap) * NT + col) * 8 + j] = W[e];
 }
 
 // Weight gradient of a conv3: dW[tap][co][ci] += sum over cells v of
@@ -1111,9 +1162,12 @@ __global__ void k_features(const float *__restrict__ U, const float *__restrict_
 }  // namespace vesis
 
 // ================================================================ host side
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1126,8 +1180,44 @@ struct Layer {
     int ci_n, cip, co_n, k;
     long long w_off, b_off;     // in the flat parameter vector
     bf16 *Wt = nullptr, *Wd = nullptr;
+    bf16 *Wtc = nullptr, *Wdc = nullptr;   // the same in the TMA kernel's layout
     float *dW = nullptr;
 };
+
+int tc_tile(int c) { return c % 64 == 0 ? 64 : 32; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of a channels-last activation [nx][ny][nz][C] bf16 with the
+// halo box {8 ch, 10 z, 18 y, 3 x}; out-of-range cells read as zero.
+bool encode_halo_map(CUtensorMap *m, const bf16 *base, int C, int nx, int ny, int nz)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)nx};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * nz,
+                                   (cuuint64_t)C * 2 * nz * ny};
+    const cuuint32_t box[4] = {8, (cuuint32_t)TC_HZ, (cuuint32_t)TC_HY, (cuuint32_t)TC_HX};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims, strides, box,
+              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 enum { L_E0, L_E1, L_E2, L_E3, L_D2, L_D1, L_D0, L_HEAD, L_N };
 
@@ -1244,7 +1334,7 @@ int ensure_act(vesis_net n, int nx, int ny, int nz, bool train)
 unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
-          const bf16 *Wt, const float *bias, int Cout, void *Y, bool raw)
+          const bf16 *Wt, const bf16 *Wtc, const float *bias, int Cout, void *Y, bool raw)
 {
     ConvArgs a;
     a.nx = nx;
@@ -1263,16 +1353,18 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
     if (n->conv_kind == 1 && ny % TCY == 0 && nz % TCZ == 0 && Ca % 32 == 0 && Cb % 32 == 0 &&
         Cout % 32 == 0) {
         const unsigned bricks = (unsigned)(nx * (ny / TCY) * (nz / TCZ));
-        if (bricks >= 152u * TCW_NB) {    // enough bricks for weight-stationary blocks
+        CUtensorMap tm;
+        if (bricks >= 152u * TCW_NB && Wtc && encode_halo_map(&tm, A, Ca, nx, ny, nz)) {
+            // enough bricks for weight-stationary blocks: TMA and bulk copies
             const unsigned nb = (bricks + TCW_NB - 1) / TCW_NB;
-            if (Cout % 64 == 0) {
+            if (tc_tile(Cout) == 64) {
                 dim3 tg(nb, Cout / 64);
-                if (raw) k_conv_tcw<64, true><<<tg, TCW_T, tcw_smem_bytes(64), n->st>>>(a, (int)bricks, n->d_err);
-                else k_conv_tcw<64, false><<<tg, TCW_T, tcw_smem_bytes(64), n->st>>>(a, (int)bricks, n->d_err);
+                if (raw) k_conv_tma<64, true><<<tg, TCW_T, tma_smem_bytes(64), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
+                else k_conv_tma<64, false><<<tg, TCW_T, tma_smem_bytes(64), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
             } else {
                 dim3 tg(nb, Cout / 32);
-                if (raw) k_conv_tcw<32, true><<<tg, TCW_T, tcw_smem_bytes(32), n->st>>>(a, (int)bricks, n->d_err);
-                else k_conv_tcw<32, false><<<tg, TCW_T, tcw_smem_bytes(32), n->st>>>(a, (int)bricks, n->d_err);
+                if (raw) k_conv_tma<32, true><<<tg, TCW_T, tma_smem_bytes(32), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
+                else k_conv_tma<32, false><<<tg, TCW_T, tma_smem_bytes(32), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
             }
             return;
         }
@@ -1347,22 +1439,22 @@ void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy
     count_launch();
     k_pack_input<<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
                                               n->X0);
-    conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, th + L[L_E0].b_off, 32, n->e[0],
-         false);
+    conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, L[L_E0].Wtc, th + L[L_E0].b_off, 32,
+         n->e[0], false);
     for (int l = 1; l < 4; ++l) {
         const long long Vc = (long long)r[l][0] * r[l][1] * r[l][2];
         count_launch();
         k_pool<<<nblk(Vc * kCh[l - 1]), 256, 0, n->st>>>(n->e[l - 1], r[l - 1][0], r[l - 1][1],
                                                          r[l - 1][2], kCh[l - 1], n->p[l - 1]);
-        conv(n, r[l][0], r[l][1], r[l][2], n->p[l - 1], kCh[l - 1], nullptr, 0, L[l].Wt,
+        conv(n, r[l][0], r[l][1], r[l][2], n->p[l - 1], kCh[l - 1], nullptr, 0, L[l].Wt, L[l].Wtc,
              th + L[l].b_off, kCh[l], n->e[l], false);
     }
-    conv(n, r[2][0], r[2][1], r[2][2], n->e[2], 128, n->e[3], 128, L[L_D2].Wt,
+    conv(n, r[2][0], r[2][1], r[2][2], n->e[2], 128, n->e[3], 128, L[L_D2].Wt, L[L_D2].Wtc,
          th + L[L_D2].b_off, 64, n->d[2], false);
-    conv(n, r[1][0], r[1][1], r[1][2], n->e[1], 64, n->d[2], 64, L[L_D1].Wt,
+    conv(n, r[1][0], r[1][1], r[1][2], n->e[1], 64, n->d[2], 64, L[L_D1].Wt, L[L_D1].Wtc,
          th + L[L_D1].b_off, 32, n->d[1], false);
-    conv(n, nx, ny, nz, n->e[0], 32, n->d[1], 32, L[L_D0].Wt, th + L[L_D0].b_off, 32, n->d[0],
-         false);
+    conv(n, nx, ny, nz, n->e[0], 32, n->d[1], 32, L[L_D0].Wt, L[L_D0].Wtc, th + L[L_D0].b_off, 32,
+         n->d[0], false);
     count_launch();
     k_head<<<nblk(V0), 256, 0, n->st>>>(n->d[0], V0, th + L[L_HEAD].w_off,
                                         th + L[L_HEAD].b_off, chi, NX, NY, NZ, ox, oy, oz, ny, nz, n->z,
@@ -1376,6 +1468,11 @@ int pack_weights(vesis_net n)
         count_launch();
         k_pack_weights<<<nblk(27ll * y.co_n * y.cip), 256, 0, n->st>>>(
             n->theta + y.w_off, y.co_n, y.ci_n, y.cip, y.Wt, y.Wd);
+        count_launch(2);
+        k_pack_tc<<<nblk(27ll * y.co_n * y.cip), 256, 0, n->st>>>(y.Wt, y.co_n, y.cip,
+                                                                 tc_tile(y.co_n), y.Wtc);
+        k_pack_tc<<<nblk(27ll * y.co_n * y.cip), 256, 0, n->st>>>(y.Wd, y.cip, y.co_n,
+                                                                 tc_tile(y.cip), y.Wdc);
     }
     n->packed = true;
     return VESIS_OK;
@@ -1425,6 +1522,8 @@ int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out)
         const long long nw = 27ll * y.co_n * y.cip;
         rc = nalloc(A, &y.Wt, nw);
         if (rc == VESIS_OK) rc = nalloc(A, &y.Wd, nw);
+        if (rc == VESIS_OK) rc = nalloc(A, &y.Wtc, nw);
+        if (rc == VESIS_OK) rc = nalloc(A, &y.Wdc, nw);
         if (rc == VESIS_OK) rc = nalloc(A, &y.dW, nw);
     }
     if (rc == VESIS_OK &&
@@ -1442,14 +1541,14 @@ int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out)
                               tc_smem_bytes(64)) != cudaSuccess ||
          cudaFuncSetAttribute(k_conv_tc<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               tc_smem_bytes(64)) != cudaSuccess ||
-         cudaFuncSetAttribute(k_conv_tcw<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tcw_smem_bytes(32)) != cudaSuccess ||
-         cudaFuncSetAttribute(k_conv_tcw<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tcw_smem_bytes(32)) != cudaSuccess ||
-         cudaFuncSetAttribute(k_conv_tcw<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tcw_smem_bytes(64)) != cudaSuccess ||
-         cudaFuncSetAttribute(k_conv_tcw<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tcw_smem_bytes(64)) != cudaSuccess))
+         cudaFuncSetAttribute(k_conv_tma<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tma_smem_bytes(32)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tma<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tma_smem_bytes(32)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tma<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tma_smem_bytes(64)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_conv_tma<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tma_smem_bytes(64)) != cudaSuccess))
         rc = nfail(VESIS_E_CUDA, "shared memory attribute of the tensor-core conv kernel");
     if (rc == VESIS_OK) rc = nalloc(A, &n->d_err, 1);
     if (rc == VESIS_OK && cudaMallocHost(&n->h_err, sizeof(int)) != cudaSuccess)
@@ -1608,8 +1707,8 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
         relu_bwd(D.gout, D.out, Vl, D.Cout, n->grad + L[D.l].b_off);
         wgrad(n, R[0], R[1], R[2], D.skip, D.Ca, D.coarse, D.Cb, n->dZ, D.Cout, L[D.l].dW);
         unpack(D.l);
-        conv(n, R[0], R[1], R[2], n->dZ, D.Cout, nullptr, 0, L[D.l].Wd, nullptr, D.Ca + D.Cb,
-             n->dX, true);
+        conv(n, R[0], R[1], R[2], n->dZ, D.Cout, nullptr, 0, L[D.l].Wd, L[D.l].Wdc, nullptr,
+             D.Ca + D.Cb, n->dX, true);
         count_launch(2);
         k_split_skip<<<nblk(Vl * D.Ca), 256, 0, st>>>(n->dX, Vl, D.Ca, D.Cb, D.gskip);
         k_split_coarse<<<nblk(V[D.lev + 1] * D.Cb), 256, 0, st>>>(n->dX, R[0], R[1], R[2], D.Ca,
@@ -1625,8 +1724,8 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
         wgrad(n, R[0], R[1], R[2], in, Cin, nullptr, 0, n->dZ, kCh[l], L[l].dW);
         unpack(l);
         if (l > 0) {
-            conv(n, R[0], R[1], R[2], n->dZ, kCh[l], nullptr, 0, L[l].Wd, nullptr, Cin, n->dX,
-                 true);
+            conv(n, R[0], R[1], R[2], n->dZ, kCh[l], nullptr, 0, L[l].Wd, L[l].Wdc, nullptr, Cin,
+                 n->dX, true);
             count_launch();
             k_pool_bwd<<<nblk(V[l - 1] * Cin), 256, 0, st>>>(n->dX, r[l - 1][0], r[l - 1][1],
                                                              r[l - 1][2], Cin, n->ge[l - 1]);
