@@ -65,6 +65,8 @@ struct ConvArgs {
     const float *bias;   // Cout or NULL
     int Cout;
     void *Y;             // bf16 [V][Cout] (relu) or float [V][Cout]
+    int k16 = 2;         // halves of each 32-channel stage that hold data (the
+                         // input layer's 3 features fill only the first)
 };
 
 constexpr int CM = 64;          // cells per block
@@ -597,7 +599,8 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
         const unsigned lb = ldbar0 + 8u * (unsigned)(u & 1);
         const bool a_stage = c0 < P.Ca, wload = (u % nbv) == 0;
         if (t == 0) {
-            const unsigned tx = (a_stage ? 4u * 540u * 16u : 0u) + (wload ? (unsigned)tc_w_bytes(NT) : 0u);
+            const unsigned tx = (a_stage ? 2u * (unsigned)P.k16 * 540u * 16u : 0u) +
+                                (wload ? (unsigned)tc_w_bytes(NT) : 0u);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          :: "r"(lb), "r"(tx) : "memory");
             if (wload) {
@@ -607,8 +610,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
                     :: "r"(swa), "l"(src), "r"((unsigned)tc_w_bytes(NT)), "r"(lb) : "memory");
             }
             if (a_stage) {
-#pragma unroll
-                for (int kc = 0; kc < 4; ++kc)
+                for (int kc = 0; kc < 2 * P.k16; ++kc)
                     asm volatile(
                         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                         " [%0], [%1, {%2, %3, %4, %5}], [%6];"
@@ -667,8 +669,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
             const unsigned dcol = tmem + (unsigned)(b * NT);
             for (int tap = 0; tap < 27; ++tap) {
                 const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
-#pragma unroll
-                for (int s2 = 0; s2 < 2; ++s2) {
+                for (int s2 = 0; s2 < P.k16; ++s2) {
                     const unsigned a_addr = hbase + (unsigned)(2 * s2 * TMA_PLANE) +
                                             (unsigned)(((da * TC_HY + db) * TC_HZ + dc) * 16);
                     const unsigned b_addr = swa + (unsigned)(((2 * s2 * 27 + tap) * NT) * 16);
@@ -1334,7 +1335,8 @@ int ensure_act(vesis_net n, int nx, int ny, int nz, bool train)
 unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
-          const bf16 *Wt, const bf16 *Wtc, const float *bias, int Cout, void *Y, bool raw)
+          const bf16 *Wt, const bf16 *Wtc, const float *bias, int Cout, void *Y, bool raw,
+          int k16 = 2)
 {
     ConvArgs a;
     a.nx = nx;
@@ -1349,6 +1351,7 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
     a.bias = bias;
     a.Cout = Cout;
     a.Y = Y;
+    a.k16 = k16;
     count_launch();
     if (n->conv_kind == 1 && ny % TCY == 0 && nz % TCZ == 0 && Ca % 32 == 0 && Cb % 32 == 0 &&
         Cout % 32 == 0) {
@@ -1440,7 +1443,7 @@ void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy
     k_pack_input<<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
                                               n->X0);
     conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, L[L_E0].Wtc, th + L[L_E0].b_off, 32,
-         n->e[0], false);
+         n->e[0], false, (n->F + 15) / 16);
     for (int l = 1; l < 4; ++l) {
         const long long Vc = (long long)r[l][0] * r[l][1] * r[l][2];
         count_launch();
