@@ -1357,8 +1357,10 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
         Cout % 32 == 0) {
         const unsigned bricks = (unsigned)(nx * (ny / TCY) * (nz / TCZ));
         CUtensorMap tm;
-        if (bricks >= 152u * TCW_NB && Wtc && encode_halo_map(&tm, A, Ca, nx, ny, nz)) {
-            // enough bricks for weight-stationary blocks: TMA and bulk copies
+        if (Cb == 0 && bricks >= 152u * TCW_NB && Wtc && encode_halo_map(&tm, A, Ca, nx, ny, nz)) {
+            // one input at full resolution and enough bricks for weight-
+            // stationary blocks: TMA and bulk copies (measured faster there;
+            // with a coarse input the per-brick kernel below is)
             const unsigned nb = (bricks + TCW_NB - 1) / TCW_NB;
             if (tc_tile(Cout) == 64) {
                 dim3 tg(nb, Cout / 64);
