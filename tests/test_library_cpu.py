@@ -160,3 +160,50 @@ def test_host_guest_set_follows_its_recipe():
         hx, gx = s["xyz"][:s["n_host"]], s["xyz"][s["n_host"]:]
         d = np.sqrt(((hx[:, None, :] - gx[None, :, :]) ** 2).sum(-1)).min()
         assert d > 3.0
+
+
+def test_pmf_combination_follows_the_appendix_definition():
+    from paper_2208_05524_gb300 import pmf
+    pair = dict(geom=10.0, vdw=-4.0, elec=-30.0, far=-2.0, lj=0.5, coulomb=-46.0)
+    a1 = dict(geom=6.0, vdw=-2.5, elec=-20.0, far=-1.0, lj=0.0, coulomb=0.0)
+    a2 = dict(geom=5.0, vdw=-2.0, elec=-15.0, far=-1.5, lj=0.0, coulomb=0.0)
+    r = pmf.combine(pair, [a1, a2])
+    assert r["geom"] == pytest.approx(10.0 - 11.0)
+    assert r["vdw"] == pytest.approx(-4.0 + 4.5 + 0.5)        # plus the cross LJ
+    assert r["elec"] == pytest.approx(-30.0 + 35.0 - 46.0)    # plus the cross Coulomb
+    assert r["far"] == pytest.approx(-2.0 + 2.5)
+    assert r["total"] == pytest.approx(r["geom"] + r["vdw"] + r["elec"] + r["far"])
+
+
+def test_random_crops_stay_inside_and_on_the_8_cell_lattice():
+    from paper_2208_05524_gb300 import learned
+    rng = np.random.default_rng(0)
+    for shape in [(64, 64, 64), (80, 96, 112), (40, 200, 16)]:
+        for _ in range(50):
+            c = learned.random_crop(shape, 64, rng)
+            for d in range(3):
+                assert c[d] % 8 == 0 and c[3 + d] % 8 == 0 and c[3 + d] >= 8
+                assert c[d] + c[3 + d] <= shape[d]
+
+
+def test_bend_torsion_lists_from_a_bond_graph():
+    from paper_2208_05524_gb300 import synth
+    # a 5-atom chain 0-1-2-3-4 with a branch 2-5: angles at 1 (0-1-2), at 2
+    # (1-2-3, 1-2-5, 3-2-5), at 3 (2-3-4); torsions along 3-bond paths
+    s = synth.single_ion(n=16, h=0.5)
+    s["xyz"] = np.array([[0, 0, 0], [1.5, 0, 0], [2, 1.4, 0], [3.5, 1.5, 0.3],
+                         [4, 2.9, 0.2], [1.6, 2.2, 1.2]], float)
+    for k in ("sigma_sw", "eps_sw", "q", "sigma_ss", "eps_ss"):
+        s[k] = np.full(6, float(np.asarray(s[k])[0]))
+    s["bonds"] = np.array([[0, 1], [1, 2], [2, 3], [3, 4], [2, 5]], np.int32)
+    s["bond_k"] = np.full(5, 800.0)
+    s["bond_r0"] = np.full(5, 1.5)
+    t = synth.with_bends_torsions(s)
+    ang = {tuple(a) for a in t["angles"]}
+    assert ang == {(0, 1, 2), (1, 2, 3), (1, 2, 5), (3, 2, 5), (2, 3, 4)}
+    tor = {tuple(x) for x in t["torsions"]}
+    # every path i-j-k-l over three bonds, listed once per middle bond direction
+    assert {(0, 1, 2, 3), (0, 1, 2, 5), (1, 2, 3, 4), (5, 2, 3, 4)} <= tor | {tuple(x[::-1]) for x in tor}
+    assert np.allclose(t["torsion_psi"][0], [np.pi, 0, np.pi, 0, np.pi, 0, np.pi])
+    sub = synth.subset(t, [1, 2, 3])
+    assert sub["bonds"].tolist() == [[0, 1], [1, 2]]
