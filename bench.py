@@ -542,7 +542,8 @@ def run_batch(args, world, rank, local):
         rep = idx[len(idx) // 2]
         t = systems[rep].autotune(chis0[rep], reps=1)
         tune_ms["default"] += t["ms"]["energy_pencil8"] + t["ms"]["force_atoms4"]
-        tune_ms["tuned"] += min(t["ms"]["energy_pencil4"], t["ms"]["energy_pencil8"]) + \
+        tune_ms["tuned"] += min(t["ms"]["energy_pencil4"], t["ms"]["energy_pencil8"],
+                                t["ms"]["energy_pencil16"]) + \
             min(t["ms"]["force_atoms2"], t["ms"]["force_atoms4"])
         for i in idx:
             systems[i].set_tiles(t["energy_pencil"], t["force_atoms"])

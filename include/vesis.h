@@ -248,7 +248,7 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
                 const vesis_relax_opts *opts, vesis_relax_stats *stats_out);
 
 /* Tile shapes of the two pair kernels: cells of a z-pencil per thread of
- * the energy-density kernel (4 or 8, default 8) and atoms per thread of the
+ * the energy-density kernel (4, 8 or 16, default 8) and atoms per thread of the
  * grid-to-atom gradient kernel (2 or 4, default 4).  Every cell sums its
  * atoms, and every atom its cells, in the same order for all shapes, so
  * the results are bit-identical; only the time differs.  Waits for the
@@ -259,8 +259,8 @@ int vesis_get_tiles(vesis_system s, int *energy_pencil, int *force_atoms);
 /* Autotuner: times each tile shape of the two pair kernels on the system's
  * current positions and labels chi_dev (one warm-up and `reps` launches
  * each, 1..1000, CUDA events on the system's stream) and keeps the fastest
- * (vesis_set_tiles).  times_ms_out (may be NULL): 4 doubles, the mean
- * launch time of energy pencil 4, 8 and gradient atoms 2, 4. */
+ * (vesis_set_tiles).  times_ms_out (may be NULL): 5 doubles, the mean
+ * launch time of energy pencil 4, 8, 16 and gradient atoms 2, 4. */
 int vesis_autotune(vesis_system s, const uint8_t *chi_dev, int reps,
                    double *times_ms_out);
 

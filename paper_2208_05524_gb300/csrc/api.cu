@@ -1395,8 +1395,8 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
 int vesis_set_tiles(vesis_system s, int energy_pencil, int force_atoms)
 {
     if (!s) return fail(VESIS_E_ARG, "NULL system");
-    if (energy_pencil != 4 && energy_pencil != 8)
-        return fail(VESIS_E_ARG, "energy_pencil must be 4 or 8");
+    if (energy_pencil != 4 && energy_pencil != 8 && energy_pencil != 16)
+        return fail(VESIS_E_ARG, "energy_pencil must be 4, 8 or 16");
     if (force_atoms != 2 && force_atoms != 4)
         return fail(VESIS_E_ARG, "force_atoms must be 2 or 4");
     VCK(cudaStreamSynchronize(s->st));
@@ -1420,8 +1420,8 @@ int vesis_autotune(vesis_system s, const uint8_t *chi_dev, int reps, double *tim
 {
     if (!s || !chi_dev) return fail(VESIS_E_ARG, "NULL argument");
     if (reps < 1 || reps > 1000) return fail(VESIS_E_ARG, "reps must be in 1..1000");
-    static const int kPencil[2] = {4, 8}, kAtoms[2] = {2, 4};
-    double ms[4] = {0, 0, 0, 0};
+    static const int kPencil[3] = {4, 8, 16}, kAtoms[2] = {2, 4};
+    double ms[5] = {0, 0, 0, 0, 0};
     // the trial buffers are scratch between calls; the count of solvent
     // cells the gradient kernel keeps for the timing report is put back
     float *U = s->d_U[1], *E = s->d_E[1];
@@ -1450,7 +1450,7 @@ int vesis_autotune(vesis_system s, const uint8_t *chi_dev, int reps, double *tim
         *out = (double)t / reps;
         return VESIS_OK;
     };
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < 3; ++v) {
         const int P = kPencil[v];
         VTRY(timed([&] {
             launch_pair_energy_grid(s->g, atoms_view(s), (float)s->p.rho_w, (float)s->cfa,
@@ -1462,14 +1462,17 @@ int vesis_autotune(vesis_system s, const uint8_t *chi_dev, int reps, double *tim
         VTRY(timed([&] {
             launch_pair_force_grid(s->g, fp, chi_dev, E, E + s->G, E + 2 * s->G,
                                    atoms_view(s), s->rmin2, s->d_fpart, s->d_fcount, s->st);
-        }, &ms[2 + v]));
+        }, &ms[3 + v]));
     }
     VTRY(last_launch("autotune"));
     *s->h_u64 = fcount;
     VCK(cudaMemcpyAsync(s->d_fcount, s->h_u64, sizeof(unsigned long long),
                         cudaMemcpyHostToDevice, s->st));
     if (times_ms_out) std::memcpy(times_ms_out, ms, sizeof(ms));
-    return vesis_set_tiles(s, ms[0] < ms[1] ? 4 : 8, ms[2] < ms[3] ? 2 : 4);
+    int best = 1;
+    for (int v = 0; v < 3; ++v)
+        if (ms[v] < ms[best]) best = v;
+    return vesis_set_tiles(s, kPencil[best], ms[3] < ms[4] ? 2 : 4);
 }
 
 int vesis_relax_batch(int nsys, vesis_system *systems, uint8_t *const *chi_dev,

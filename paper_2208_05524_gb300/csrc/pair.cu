@@ -133,7 +133,7 @@ __device__ __forceinline__ void energy_atom(const AtomPairs &at, f2 px, f2 py, c
 // PTS (cells of a z-pencil per thread, 4 or 8) is the pencil size the
 // autotuner picks per system; the sums of every cell are the same for both.
 template <int PTS>
-__global__ void __launch_bounds__(PE_THREADS, PTS == 8 ? 4 : 5)
+__global__ void __launch_bounds__(PE_THREADS, PTS == 16 ? 3 : PTS == 8 ? 4 : 5)
 k_pair_energy_grid(GridDesc g, AtomsDev a, float rho, float cfa, float rmin2,
                    float *__restrict__ U, float *__restrict__ Ex,
                    float *__restrict__ Ey, float *__restrict__ Ez)
@@ -247,13 +247,16 @@ void launch_pair_energy_grid(const GridDesc &g, const AtomsDev &a, float rho,
                              float cfa, float rmin2, float *U, float *Ex,
                              float *Ey, float *Ez, int pts, cudaStream_t st)
 {
-    const int P = pts == 4 ? 4 : 8;
+    const int P = pts == 4 ? 4 : pts == 16 ? 16 : 8;
     const long long cpp = (g.nz + P - 1) / P;
     const long long threads = (long long)g.nx * g.ny * cpp;
     const long long blocks = (threads + PE_THREADS - 1) / PE_THREADS;
     count_launch();
     if (P == 4)
         k_pair_energy_grid<4><<<(unsigned)blocks, PE_THREADS, 0, st>>>(
+            g, a, rho, cfa, rmin2, U, Ex, Ey, Ez);
+    else if (P == 16)
+        k_pair_energy_grid<16><<<(unsigned)blocks, PE_THREADS, 0, st>>>(
             g, a, rho, cfa, rmin2, U, Ex, Ey, Ez);
     else
         k_pair_energy_grid<8><<<(unsigned)blocks, PE_THREADS, 0, st>>>(

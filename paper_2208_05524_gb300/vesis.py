@@ -344,13 +344,13 @@ class System:
         """Times the pair kernels' tile shapes on this system and keeps the
         fastest; returns the chosen shapes and the four mean times (ms)."""
         import torch
-        t = (_d * 4)()
+        t = (_d * 5)()
         _check(lib().vesis_autotune(self.h, _dp(chi, torch.uint8, self.G), int(reps),
                                     C.cast(t, _p)))
         pe, fa = self.get_tiles()
         return dict(energy_pencil=pe, force_atoms=fa,
-                    ms={"energy_pencil4": t[0], "energy_pencil8": t[1],
-                        "force_atoms2": t[2], "force_atoms4": t[3]})
+                    ms={"energy_pencil4": t[0], "energy_pencil8": t[1], "energy_pencil16": t[2],
+                        "force_atoms2": t[3], "force_atoms4": t[4]})
 
     def ss_terms(self):
         """Solute-solute bonds, LJ, Coulomb, bends and torsions at the

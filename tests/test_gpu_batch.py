@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-SHAPES = [(4, 2), (4, 4), (8, 2), (8, 4)]
+SHAPES = [(4, 2), (4, 4), (8, 2), (8, 4), (16, 2), (16, 4)]
 
 
 def _vs():
@@ -90,7 +90,8 @@ def test_autotune_keeps_a_valid_shape_and_results():
     r = S.autotune(chi, reps=2)
     assert (r["energy_pencil"], r["force_atoms"]) in SHAPES
     assert all(v > 0.0 for v in r["ms"].values())
-    assert r["energy_pencil"] == (4 if r["ms"]["energy_pencil4"] < r["ms"]["energy_pencil8"] else 8)
+    pe = {4: r["ms"]["energy_pencil4"], 8: r["ms"]["energy_pencil8"], 16: r["ms"]["energy_pencil16"]}
+    assert pe[r["energy_pencil"]] == min(pe.values())
     assert r["force_atoms"] == (2 if r["ms"]["force_atoms2"] < r["ms"]["force_atoms4"] else 4)
     # the autotuner's launches are not counted as gradient work
     assert S.get_timing()["pair_force_pairs"] == 0
