@@ -527,58 +527,56 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
 // refilled once the MMAs that read it have committed.  Stage boundaries
 // wait for the stage's last MMAs before the weights are replaced.
 constexpr int TCW_NB = 8;
-constexpr int TCW_T = 512;      // 16 warps: the copies of a coarse-input stage
 
-// TMA form of the weight-stationary convolution.  The stage's weights come
-// pre-arranged in global memory (one contiguous block per stage and tile of
-// output channels) and arrive by one bulk copy; the halo of a skip-input
-// stage arrives as four tensor-map box loads (8 channels x 10 z x 18 y x 3
-// x each, cells outside the grid zero-filled by the copy engine); the
-// halo of a coarse-input stage (read at half coordinates) is gathered with
-// cp.async.  Both complete on an mbarrier with a transaction count.  Halo
-// layout: [8-channel plane][x][y][z][8 ch], planes 128-byte aligned.
+// TMA form of the weight-stationary convolution, for a single input at the
+// output's resolution.  The stage's weights come pre-arranged in global
+// memory (one contiguous block per stage and tile of output channels) and
+// arrive by one bulk copy; a brick's halo arrives as tensor-map box loads
+// (8 channels x 10 z x 18 y x 3 x each, cells outside the grid zero-filled
+// by the copy engine).  Copies and MMAs complete on mbarriers, so one
+// thread runs the whole producer/consumer loop: it keeps the copies of the
+// next NBUF - 1 bricks in flight while the tensor cores work, and the
+// other warps only join for the epilogue.  Halo layout: [8-channel plane]
+// [x][y][z][8 ch], planes 128-byte aligned.
 constexpr int TMA_PLANE = 8704;                         // 540 x 16 B padded to 128 B
 constexpr int TMA_HALO = 4 * TMA_PLANE;
 
+__host__ __device__ constexpr int tma_nbuf(int NT) { return NT == 32 ? 4 : 3; }
 __host__ __device__ constexpr int tma_smem_bytes(int NT)
 {
-    return tc_w_bytes(NT) + 2 * TMA_HALO + 64 + 128;
+    return tc_w_bytes(NT) + tma_nbuf(NT) * TMA_HALO + 128 + 128;
 }
 
 template <int NT, bool RAW>
-__global__ void __launch_bounds__(TCW_T, 1)
+__global__ void __launch_bounds__(128, 1)
 k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__restrict__ Wtc,
            int nbricks, int *err)
 {
+    constexpr int NBUF = tma_nbuf(NT);
     extern __shared__ __align__(1024) unsigned char smem_tma[];
-    // 128-byte aligned base for the copy engine's destinations
     const unsigned raw0 = smem_u32(smem_tma);
     const unsigned pad = ((raw0 + 127u) & ~127u) - raw0;
     unsigned char *smem = smem_tma + pad;
-    unsigned char *sw = smem;
-    unsigned char *sh0 = smem + tc_w_bytes(NT);
-    unsigned char *tail = sh0 + 2 * TMA_HALO;
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(tail);   // 2 MMA + 2 load
-    unsigned *tslot = reinterpret_cast<unsigned *>(tail + 32);
-    int *sfail = reinterpret_cast<int *>(tail + 36);
+    unsigned char *tail = smem + tc_w_bytes(NT) + NBUF * TMA_HALO;
+    unsigned *tslot = reinterpret_cast<unsigned *>(tail + 16 * NBUF);
+    int *sfail = reinterpret_cast<int *>(tail + 16 * NBUF + 4);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
     const int b0 = blockIdx.x * TCW_NB;
     const int nbv = min(TCW_NB, nbricks - b0);
-    const int Cin = P.Ca + P.Cb;
-    const int nst = Cin / 32;
+    const int nst = P.Ca / 32;
     const int U = nst * nbv;
     const int nnt = P.Cout / NT;
     const int co0 = blockIdx.y * NT;
-    const int hy = P.ny >> 1, hz = P.nz >> 1;
-    const unsigned mbar0 = smem_u32(mbar), ldbar0 = mbar0 + 16u;
-    const unsigned swa = smem_u32(sw), sha0 = smem_u32(sh0);
+    const unsigned swa = smem_u32(smem), sha0 = swa + (unsigned)tc_w_bytes(NT);
+    const unsigned ldb0 = smem_u32(tail), mmb0 = ldb0 + 8u * NBUF;   // NBUF load + NBUF MMA barriers
     if (t == 0) {
         *sfail = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar0 + 8u * q) : "memory");
+        for (int q = 0; q < 2 * NBUF; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(ldb0 + 8u * q) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];"
+                     :: "l"(reinterpret_cast<unsigned long long>(&tmA)) : "memory");
     }
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -589,17 +587,19 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tslot;
-    const unsigned idesc = tc_idesc(NT);
 
-    auto issue = [&](int u) {
-        const int st = u / nbv, bb = b0 + u % nbv, c0 = st * 32;
-        const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
-        const int i0 = bx, j0 = by * TCY, k0 = bz * TCZ;
-        const unsigned sha = sha0 + (unsigned)((u & 1) * TMA_HALO);
-        const unsigned lb = ldbar0 + 8u * (unsigned)(u & 1);
-        const bool a_stage = c0 < P.Ca, wload = (u % nbv) == 0;
-        if (t == 0) {
-            const unsigned tx = (a_stage ? 2u * (unsigned)P.k16 * 540u * 16u : 0u) +
+    if (t == 0) {
+        const unsigned idesc = tc_idesc(NT);
+        // unit u: stage u / nbv, brick u % nbv, buffer u % NBUF (its k-th
+        // use, k = u / NBUF, completes phase k of that buffer's barriers)
+        auto issue = [&](int u) {
+            const int st = u / nbv, bb = b0 + u % nbv, c0 = st * 32;
+            const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
+            const unsigned buf = (unsigned)(u % NBUF);
+            const unsigned lb = ldb0 + 8u * buf;
+            const unsigned sha = sha0 + buf * (unsigned)TMA_HALO;
+            const bool wload = (u % nbv) == 0;
+            const unsigned tx = 2u * (unsigned)P.k16 * 540u * 16u +
                                 (wload ? (unsigned)tc_w_bytes(NT) : 0u);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          :: "r"(lb), "r"(tx) : "memory");
@@ -609,64 +609,34 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                     :: "r"(swa), "l"(src), "r"((unsigned)tc_w_bytes(NT)), "r"(lb) : "memory");
             }
-            if (a_stage) {
-                for (int kc = 0; kc < 2 * P.k16; ++kc)
-                    asm volatile(
-                        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
-                        :: "r"(sha + (unsigned)(kc * TMA_PLANE)),
-                           "l"(reinterpret_cast<unsigned long long>(&tmA)),
-                           "r"(c0 + 8 * kc), "r"(k0 - 1), "r"(j0 - 1), "r"(i0 - 1), "r"(lb)
-                        : "memory");
+            for (int kc = 0; kc < 2 * P.k16; ++kc)
+                asm volatile(
+                    "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                    :: "r"(sha + (unsigned)(kc * TMA_PLANE)),
+                       "l"(reinterpret_cast<unsigned long long>(&tmA)),
+                       "r"(c0 + 8 * kc), "r"(bz * TCZ - 1), "r"(by * TCY - 1), "r"(bx - 1), "r"(lb)
+                    : "memory");
+        };
+        auto wait_bar = [&](unsigned base, int u) -> bool {
+            return mbar_wait(base + 8u * (unsigned)(u % NBUF), (unsigned)((u / NBUF) & 1));
+        };
+        bool ok = true;
+        // prologue: the first stage's first NBUF - 1 bricks
+        for (int v = 0; v < NBUF - 1 && v < nbv && v < U; ++v) issue(v);
+        for (int u = 0; u < U && ok; ++u) {
+            const int st = u / nbv;
+            // keep NBUF - 1 bricks of this stage in flight; buffer (u + NBUF - 1)
+            // % NBUF was last read by unit u - 1
+            const int v = u + NBUF - 1;
+            if (v < U && v / nbv == st) {
+                if (v >= NBUF && !wait_bar(mmb0, v - NBUF)) { ok = false; break; }
+                issue(v);
             }
-        }
-        if (!a_stage) {
-            // coarse input: cell (x, y, z) of the halo reads the coarse cell
-            // at half its grid coordinates; four threads per cell, one per
-            // 8-channel plane
-            for (int e = t; e < TC_HX * TC_HY * TC_HZ * 4; e += TCW_T) {
-                const int kc = e & 3, cell = e >> 2;
-                const int hzz = cell % TC_HZ, hyy = (cell / TC_HZ) % TC_HY, hxx = cell / (TC_HZ * TC_HY);
-                const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
-                const bool in = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz;
-                const bf16 *src = in ? P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) *
-                                               P.Cb + (c0 - P.Ca) + kc * 8
-                                     : P.B;
-                cp_async16(sha + (unsigned)(kc * TMA_PLANE + cell * 16), src, in);
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    auto loaded = [&](int u) -> bool {
-        return mbar_wait(ldbar0 + 8u * (unsigned)(u & 1), (unsigned)((u >> 1) & 1));
-    };
-    auto done = [&](int v) -> bool {
-        return mbar_wait(mbar0 + 8u * (unsigned)(v & 1), (unsigned)((v >> 1) & 1));
-    };
-
-    if (U > 0) issue(0);
-    for (int u = 0; u < U; ++u) {
-        const int nu = u + 1;
-        bool pre = false;
-        if (nu < U && nu % nbv != 0) {
-            if (nu >= 2 && !done(nu - 2)) { *sfail = 1; atomicExch(err, 1); }
-            if (!*sfail) {
-                issue(nu);
-                pre = true;
-            }
-        }
-        if (pre) asm volatile("cp.async.wait_group 1;" ::: "memory");
-        else asm volatile("cp.async.wait_group 0;" ::: "memory");
-        if (!loaded(u)) { *sfail = 1; atomicExch(err, 1); }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (*sfail) break;
-        if (t == 0) {
+            if (!wait_bar(ldb0, u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int st = u / nbv, b = u % nbv;
-            (void)st;
-            const unsigned hbase = sha0 + (unsigned)((u & 1) * TMA_HALO);
-            const unsigned dcol = tmem + (unsigned)(b * NT);
+            const unsigned hbase = sha0 + (unsigned)(u % NBUF) * (unsigned)TMA_HALO;
+            const unsigned dcol = tmem + (unsigned)((u % nbv) * NT);
             for (int tap = 0; tap < 27; ++tap) {
                 const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
                 for (int s2 = 0; s2 < P.k16; ++s2) {
@@ -675,7 +645,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
                     const unsigned b_addr = swa + (unsigned)(((2 * s2 * 27 + tap) * NT) * 16);
                     const unsigned long long ad = tc_desc(a_addr, TMA_PLANE, TC_HZ * 16);
                     const unsigned long long bd = tc_desc(b_addr, 27 * NT * 16, 8 * 16);
-                    const unsigned acc = (u >= nbv || tap > 0 || s2 > 0) ? 1u : 0u;
+                    const unsigned acc = (st > 0 || tap > 0 || s2 > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"
@@ -684,30 +654,28 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(mbar0 + 8u * (unsigned)(u & 1)) : "memory");
+                         :: "r"(mmb0 + 8u * (unsigned)(u % NBUF)) : "memory");
+            // stage boundary: replace the weights once every MMA of the stage
+            // has completed, then refill the pipeline
+            if (u + 1 < U && (u + 1) % nbv == 0) {
+                if (!wait_bar(mmb0, u)) { ok = false; break; }
+                for (int q = u + 1; q < u + NBUF && q < U && q / nbv == (u + 1) / nbv; ++q)
+                    issue(q);
+            }
         }
-        if (nu < U && nu % nbv == 0) {
-            if (!done(u)) { *sfail = 1; atomicExch(err, 1); }
-            __syncthreads();
-            if (*sfail) break;
-            issue(nu);
+        if (ok && U > 0 && !wait_bar(mmb0, U - 1)) ok = false;
+        if (!ok) {
+            *sfail = 1;
+            atomicExch(err, 1);
         }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    const bool failed_before = *sfail != 0;
-    __syncthreads();
-    if (!failed_before && U > 0 && !done(U - 1)) {
-        *sfail = 1;
-        atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!*sfail) {
         const long long nyz = (long long)P.ny * P.nz;
-        const int lq = w & 3;
-        const int m = 32 * lq + lane;
-        for (int b = w >> 2; b < nbv; b += TCW_T / 128) {
+        const int m = 32 * w + lane;                 // 4 warps: lane quarter = warp
+        for (int b = 0; b < nbv; ++b) {
             const int bb = b0 + b;
             const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
             const long long vo = (long long)bx * nyz + (long long)(by * TCY + m / TCZ) * P.nz +
@@ -715,7 +683,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
 #pragma unroll
             for (int half = 0; half < NT / 32; ++half) {
                 unsigned r[32];
-                const unsigned ta = tmem + ((unsigned)(32 * lq) << 16) + (unsigned)(b * NT + 32 * half);
+                const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(b * NT + 32 * half);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -1364,12 +1332,12 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
             const unsigned nb = (bricks + TCW_NB - 1) / TCW_NB;
             if (tc_tile(Cout) == 64) {
                 dim3 tg(nb, Cout / 64);
-                if (raw) k_conv_tma<64, true><<<tg, TCW_T, tma_smem_bytes(64), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
-                else k_conv_tma<64, false><<<tg, TCW_T, tma_smem_bytes(64), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
+                if (raw) k_conv_tma<64, true><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
+                else k_conv_tma<64, false><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
             } else {
                 dim3 tg(nb, Cout / 32);
-                if (raw) k_conv_tma<32, true><<<tg, TCW_T, tma_smem_bytes(32), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
-                else k_conv_tma<32, false><<<tg, TCW_T, tma_smem_bytes(32), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
+                if (raw) k_conv_tma<32, true><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
+                else k_conv_tma<32, false><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
             }
             return;
         }
