@@ -312,6 +312,10 @@ constexpr int TCY = 16, TCZ = 8;                           // brick (x extent 1)
 constexpr int TC_HX = 3, TC_HY = TCY + 2, TC_HZ = TCZ + 2;
 constexpr int TC_HALO_BYTES = TC_HX * TC_HY * 4 * TC_HZ * 16;   // 34,560
 constexpr long long kTcSpin = 1ll << 22;
+// MMAs into one accumulator run one after another; the taps are dealt over
+// TC_CHAINS accumulators (summed in the epilogue) so that independent MMAs
+// keep the tensor pipe busy.
+constexpr int TC_CHAINS = 4;
 
 __host__ __device__ constexpr int tc_w_bytes(int NT) { return 27 * 4 * NT * 16; }
 __host__ __device__ constexpr int tc_smem_bytes(int NT)
@@ -389,7 +393,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
     }
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(NT) : "memory");
+                     :: "r"(smem_u32(tslot)), "r"(TC_CHAINS * NT) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -446,12 +450,13 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
                     const unsigned b_addr = wbase + (unsigned)(((tap * 4 + 2 * s2) * NT) * 16);
                     const unsigned long long ad = tc_desc(a_addr, TC_HZ * 16, 4 * TC_HZ * 16);
                     const unsigned long long bd = tc_desc(b_addr, NT * 16, 8 * 16);
-                    const unsigned acc = (st > 0 || tap > 0 || s2 > 0) ? 1u : 0u;
+                    const unsigned acc = (st > 0 || tap >= TC_CHAINS || s2 > 0) ? 1u : 0u;
+                    const unsigned dcol = tmem + (unsigned)((tap % TC_CHAINS) * NT);
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"
                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                        :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                        :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -473,7 +478,11 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
 #pragma unroll
         for (int half = 0; half < NT / 32; ++half) {
             unsigned r[32];
-            const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(32 * half);
+            float sum[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) sum[c] = 0.f;
+            for (int ch = 0; ch < TC_CHAINS; ++ch) {
+            const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(ch * NT + 32 * half);
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -486,6 +495,11 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
                   "=r"(r[30]), "=r"(r[31])
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < 32; ++c) sum[c] += __uint_as_float(r[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 32; ++c) r[c] = __float_as_uint(sum[c]);
             const int cb = co0 + 32 * half;
             if (RAW) {
                 float *dst = static_cast<float *>(P.Y) + vo * P.Cout + cb;
@@ -514,8 +528,8 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
     __syncthreads();
     if (w == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NT)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"(TC_CHAINS * NT) : "memory");
     }
 }
 
@@ -526,7 +540,8 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
 // while the tensor cores run the current brick's 54 MMAs; a buffer is
 // refilled once the MMAs that read it have committed.  Stage boundaries
 // wait for the stage's last MMAs before the weights are replaced.
-constexpr int TCW_NB = 8;
+constexpr int TCW_NB = 4;
+__host__ __device__ constexpr int tma_chains(int NT) { return 512 / (TCW_NB * NT); }
 
 // TMA form of the weight-stationary convolution, for a single input at the
 // output's resolution.  The stage's weights come pre-arranged in global
@@ -580,13 +595,14 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
     }
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(tslot)), "r"(TCW_NB * NT) : "memory");
+                     :: "r"(smem_u32(tslot)), "r"(512) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tslot;
+    constexpr int CH = tma_chains(NT);
 
     if (t == 0) {
         const unsigned idesc = tc_idesc(NT);
@@ -636,16 +652,16 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
             if (!wait_bar(ldb0, u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned hbase = sha0 + (unsigned)(u % NBUF) * (unsigned)TMA_HALO;
-            const unsigned dcol = tmem + (unsigned)((u % nbv) * NT);
             for (int tap = 0; tap < 27; ++tap) {
                 const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
+                const unsigned dcol = tmem + (unsigned)((((u % nbv) * CH) + tap % CH) * NT);
                 for (int s2 = 0; s2 < P.k16; ++s2) {
                     const unsigned a_addr = hbase + (unsigned)(2 * s2 * TMA_PLANE) +
                                             (unsigned)(((da * TC_HY + db) * TC_HZ + dc) * 16);
                     const unsigned b_addr = swa + (unsigned)(((2 * s2 * 27 + tap) * NT) * 16);
                     const unsigned long long ad = tc_desc(a_addr, TMA_PLANE, TC_HZ * 16);
                     const unsigned long long bd = tc_desc(b_addr, 27 * NT * 16, 8 * 16);
-                    const unsigned acc = (st > 0 || tap > 0 || s2 > 0) ? 1u : 0u;
+                    const unsigned acc = (st > 0 || tap >= CH || s2 > 0) ? 1u : 0u;
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "setp.ne.b32 p, %4, 0;\n\t"
@@ -683,7 +699,12 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
 #pragma unroll
             for (int half = 0; half < NT / 32; ++half) {
                 unsigned r[32];
-                const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(b * NT + 32 * half);
+                float sum[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) sum[c] = 0.f;
+                for (int ch = 0; ch < CH; ++ch) {
+                const unsigned ta = tmem + ((unsigned)(32 * w) << 16) +
+                                    (unsigned)((b * CH + ch) * NT + 32 * half);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -696,6 +717,11 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
                       "=r"(r[30]), "=r"(r[31])
                     : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int c = 0; c < 32; ++c) sum[c] += __uint_as_float(r[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) r[c] = __float_as_uint(sum[c]);
                 const int cb = co0 + 32 * half;
                 if (RAW) {
                     float *dst = static_cast<float *>(P.Y) + vo * P.Cout + cb;
@@ -726,7 +752,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
     if (w == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                     :: "r"(tmem), "r"(TCW_NB * NT) : "memory");
+                     :: "r"(tmem), "r"(512) : "memory");
     }
 }
 
