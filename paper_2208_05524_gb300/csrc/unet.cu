@@ -368,6 +368,16 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool v
                  :: "r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
 
+__device__ __forceinline__ void tc_mma(unsigned dcol, unsigned long long ad, unsigned long long bd,
+                                       unsigned idesc, unsigned acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+}
+
 template <int NT, bool RAW>
 __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
 {
@@ -440,23 +450,20 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
         __syncthreads();
         if (t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned hbase = smem_u32(sh), wbase = smem_u32(sw);
+            // descriptors of tap 0, step 0; the others differ only in the
+            // start address field (16-byte units), so they are one add away
+            const unsigned long long ad0 = tc_desc(smem_u32(sh), TC_HZ * 16, 4 * TC_HZ * 16);
+            const unsigned long long bd0 = tc_desc(smem_u32(sw), NT * 16, 8 * 16);
+#pragma unroll
             for (int tap = 0; tap < 27; ++tap) {
                 const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;   // halo offsets 0..2
 #pragma unroll
                 for (int s2 = 0; s2 < 2; ++s2) {
-                    const unsigned a_addr =
-                        hbase + (unsigned)((((da * TC_HY + db) * 4 + 2 * s2) * TC_HZ + dc) * 16);
-                    const unsigned b_addr = wbase + (unsigned)(((tap * 4 + 2 * s2) * NT) * 16);
-                    const unsigned long long ad = tc_desc(a_addr, TC_HZ * 16, 4 * TC_HZ * 16);
-                    const unsigned long long bd = tc_desc(b_addr, NT * 16, 8 * 16);
+                    const unsigned long long ad =
+                        ad0 + (unsigned long long)(((da * TC_HY + db) * 4 + 2 * s2) * TC_HZ + dc);
+                    const unsigned long long bd = bd0 + (unsigned long long)((tap * 4 + 2 * s2) * NT);
                     const unsigned acc = (st > 0 || tap >= TC_CHAINS || s2 > 0) ? 1u : 0u;
-                    const unsigned dcol = tmem + (unsigned)((tap % TC_CHAINS) * NT);
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\t"
-                        "setp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                        :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                    tc_mma(tmem + (unsigned)((tap % TC_CHAINS) * NT), ad, bd, idesc, acc);
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -652,21 +659,30 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
             if (!wait_bar(ldb0, u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned hbase = sha0 + (unsigned)(u % NBUF) * (unsigned)TMA_HALO;
-            for (int tap = 0; tap < 27; ++tap) {
-                const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
-                const unsigned dcol = tmem + (unsigned)((((u % nbv) * CH) + tap % CH) * NT);
-                for (int s2 = 0; s2 < P.k16; ++s2) {
-                    const unsigned a_addr = hbase + (unsigned)(2 * s2 * TMA_PLANE) +
-                                            (unsigned)(((da * TC_HY + db) * TC_HZ + dc) * 16);
-                    const unsigned b_addr = swa + (unsigned)(((2 * s2 * 27 + tap) * NT) * 16);
-                    const unsigned long long ad = tc_desc(a_addr, TMA_PLANE, TC_HZ * 16);
-                    const unsigned long long bd = tc_desc(b_addr, 27 * NT * 16, 8 * 16);
-                    const unsigned acc = (st > 0 || tap >= CH || s2 > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n\t.reg .pred p;\n\t"
-                        "setp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                        :: "r"(dcol), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+            const unsigned long long ad0 = tc_desc(hbase, TMA_PLANE, TC_HZ * 16);
+            const unsigned long long bd0 = tc_desc(swa, 27 * NT * 16, 8 * 16);
+            const unsigned dbase = tmem + (unsigned)((u % nbv) * CH * NT);
+            const bool first = st == 0;
+            if (P.k16 == 2) {
+#pragma unroll
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
+                    const unsigned long long ao = (unsigned long long)((da * TC_HY + db) * TC_HZ + dc);
+#pragma unroll
+                    for (int s2 = 0; s2 < 2; ++s2)
+                        tc_mma(dbase + (unsigned)((tap % CH) * NT),
+                               ad0 + ao + (unsigned long long)(2 * s2 * (TMA_PLANE / 16)),
+                               bd0 + (unsigned long long)((2 * s2 * 27 + tap) * NT), idesc,
+                               (!first || tap >= CH || s2 > 0) ? 1u : 0u);
+                }
+            } else {
+#pragma unroll
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
+                    const unsigned long long ao = (unsigned long long)((da * TC_HY + db) * TC_HZ + dc);
+                    tc_mma(dbase + (unsigned)((tap % CH) * NT), ad0 + ao,
+                           bd0 + (unsigned long long)(tap * NT), idesc,
+                           (!first || tap >= CH) ? 1u : 0u);
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
