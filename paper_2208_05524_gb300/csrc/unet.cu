@@ -571,8 +571,9 @@ __host__ __device__ constexpr int tma_smem_bytes(int NT)
 
 template <int NT, bool RAW>
 __global__ void __launch_bounds__(128, 1)
-k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__restrict__ Wtc,
-           int nbricks, int *err)
+k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
+           const __grid_constant__ CUtensorMap tmB, const bf16 *__restrict__ Wtc, int nbricks,
+           int *err)
 {
     constexpr int NBUF = tma_nbuf(NT);
     extern __shared__ __align__(1024) unsigned char smem_tma[];
@@ -586,7 +587,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
     const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
     const int b0 = blockIdx.x * TCW_NB;
     const int nbv = min(TCW_NB, nbricks - b0);
-    const int nst = P.Ca / 32;
+    const int nst = (P.Ca + P.Cb) / 32;     // stages of the first input, then of the second
     const int U = nst * nbv;
     const int nnt = P.Cout / NT;
     const int co0 = blockIdx.y * NT;
@@ -599,6 +600,9 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];"
                      :: "l"(reinterpret_cast<unsigned long long>(&tmA)) : "memory");
+        if (P.Cb > 0)
+            asm volatile("prefetch.tensormap [%0];"
+                         :: "l"(reinterpret_cast<unsigned long long>(&tmB)) : "memory");
     }
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -632,13 +636,15 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                     :: "r"(swa), "l"(src), "r"((unsigned)tc_w_bytes(NT)), "r"(lb) : "memory");
             }
+            const bool first_input = c0 < P.Ca;
+            const unsigned long long map = reinterpret_cast<unsigned long long>(first_input ? &tmA : &tmB);
+            const int cc = first_input ? c0 : c0 - P.Ca;
             for (int kc = 0; kc < 2 * P.k16; ++kc)
                 asm volatile(
                     "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                     " [%0], [%1, {%2, %3, %4, %5}], [%6];"
-                    :: "r"(sha + (unsigned)(kc * TMA_PLANE)),
-                       "l"(reinterpret_cast<unsigned long long>(&tmA)),
-                       "r"(c0 + 8 * kc), "r"(bz * TCZ - 1), "r"(by * TCY - 1), "r"(bx - 1), "r"(lb)
+                    :: "r"(sha + (unsigned)(kc * TMA_PLANE)), "l"(map),
+                       "r"(cc + 8 * kc), "r"(bz * TCZ - 1), "r"(by * TCY - 1), "r"(bx - 1), "r"(lb)
                     : "memory");
         };
         auto wait_bar = [&](unsigned base, int u) -> bool {
@@ -770,6 +776,22 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA, const bf16 *__re
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      :: "r"(tmem), "r"(512) : "memory");
     }
+}
+
+// Nearest doubling: Y[v][c] = X[parent(v)][c] for a fine grid nx x ny x nz
+// (16-byte copies; C a multiple of 8).
+__global__ void k_upsample(const bf16 *__restrict__ X, int nx, int ny, int nz, int C,
+                           bf16 *__restrict__ Y)
+{
+    const int q = C / 8;
+    const long long n = (long long)nx * ny * nz * q;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const long long v = e / q;
+    const int part = (int)(e - v * q);
+    const int i = (int)(v / ((long long)ny * nz)), j = (int)((v / nz) % ny), k = (int)(v % nz);
+    const long long u = ((long long)(i >> 1) * (ny >> 1) + (j >> 1)) * (nz >> 1) + (k >> 1);
+    reinterpret_cast<uint4 *>(Y)[e] = reinterpret_cast<const uint4 *>(X + u * C)[part];
 }
 
 // Weights [27][Cout][Cin] -> the TMA form's layout: per stage of 32 input
@@ -1257,6 +1279,8 @@ struct vesis_net_t {
     bf16 *dZ = nullptr;
     double *h_loss = nullptr;
     int conv_kind = 1;            // 0 mma.sync, 1 tcgen05 where the shape allows
+    bf16 *up = nullptr;           // a decoder's coarse input doubled to its resolution
+    long long up_cap = 0;
     int *d_err = nullptr;         // timeout flag of the tcgen05 convolution
     int *h_err = nullptr;
     std::vector<void *> act;      // activation allocations
@@ -1298,6 +1322,8 @@ void free_act(vesis_net n)
 {
     for (void *q : n->act) cudaFree(q);
     n->act.clear();
+    n->up = nullptr;
+    n->up_cap = 0;
     n->nx = n->ny = n->nz = 0;
 }
 
@@ -1322,6 +1348,8 @@ int ensure_act(vesis_net n, int nx, int ny, int nz, bool train)
     NTRY(nalloc(A, &n->d[1], V1 * 32));
     NTRY(nalloc(A, &n->d[2], V2 * 64));
     NTRY(nalloc(A, &n->z, V0));
+    NTRY(nalloc(A, &n->up, V0 * 32));    // the largest doubled coarse input (d0's)
+    n->up_cap = V0 * 32;
     NTRY(nalloc(A, &n->loss_part, (V0 + 255) / 256));
     if (train) {
         NTRY(nalloc(A, &n->dz, V0));
@@ -1366,20 +1394,32 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
     if (n->conv_kind == 1 && ny % TCY == 0 && nz % TCZ == 0 && Ca % 32 == 0 && Cb % 32 == 0 &&
         Cout % 32 == 0) {
         const unsigned bricks = (unsigned)(nx * (ny / TCY) * (nz / TCZ));
-        CUtensorMap tm;
-        if (Cb == 0 && bricks >= 152u * TCW_NB && Wtc && encode_halo_map(&tm, A, Ca, nx, ny, nz)) {
-            // one input at full resolution and enough bricks for weight-
-            // stationary blocks: TMA and bulk copies (measured faster there;
-            // with a coarse input the per-brick kernel below is)
+        CUtensorMap tm, tmb;
+        bool tma_ok = bricks >= 152u * TCW_NB && Wtc && encode_halo_map(&tm, A, Ca, nx, ny, nz);
+        if (tma_ok && Cb > 0) {
+            // the coarse input doubled to the output's resolution, so that
+            // both inputs arrive by tensor-map boxes
+            tma_ok = n->up && (long long)nx * ny * nz * Cb <= n->up_cap &&
+                     encode_halo_map(&tmb, n->up, Cb, nx, ny, nz);
+            if (tma_ok) {
+                count_launch();
+                k_upsample<<<nblk((long long)nx * ny * nz * (Cb / 8)), 256, 0, n->st>>>(
+                    B, nx, ny, nz, Cb, n->up);
+            }
+        } else {
+            tmb = tm;
+        }
+        if (tma_ok) {
+            // enough bricks for weight-stationary blocks: TMA and bulk copies
             const unsigned nb = (bricks + TCW_NB - 1) / TCW_NB;
             if (tc_tile(Cout) == 64) {
                 dim3 tg(nb, Cout / 64);
-                if (raw) k_conv_tma<64, true><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
-                else k_conv_tma<64, false><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
+                if (raw) k_conv_tma<64, true><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
+                else k_conv_tma<64, false><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
             } else {
                 dim3 tg(nb, Cout / 32);
-                if (raw) k_conv_tma<32, true><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
-                else k_conv_tma<32, false><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, Wtc, (int)bricks, n->d_err);
+                if (raw) k_conv_tma<32, true><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
+                else k_conv_tma<32, false><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
             }
             return;
         }
