@@ -287,7 +287,7 @@ def run_vesis(args, world, rank, local):
     wl = workloads()[args.workload]
     sysd = wl[1]()
     stream = torch.cuda.current_stream()
-    S = vesis.System(sysd, stream=stream)
+    S = vesis.System(sysd, stream=stream, kernel=args.surface_kernel)
     G, N = S.G, S.n_atoms
     chi0 = torch.empty(G, dtype=torch.uint8, device=dev)
     S.init_labels(chi0, sysd["init"]["kind"], radius=sysd["init"].get("radius", 0.0))
@@ -373,13 +373,21 @@ def run_vesis(args, world, rank, local):
     if tm.get("conv_launches"):
         cs = tm["conv_ms"] * 1e-3 / tm["conv_launches"]
         cells = tm["conv_cells"] / tm["conv_launches"]
-        # z pass: 1 B in, 2 B out; y pass: 2 in, 4 out; x pass: 4 in, 4 out
-        gbs = cells * 17.0 / cs / 1e9
-        conv = {"bound": "hbm", "kernel": "conv_z + conv_y + conv_x",
-                "ms_per_convolution": cs * 1e3, "achieved": gbs,
-                "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_cell": 17,
-                "launches": tm["conv_launches"]}
+        if args.surface_kernel == "sin2":
+            # the paper's kernel is not separable: one integer stencil pass
+            # (labels in, W out: 5 B per cell at least)
+            conv = {"bound": "alu", "kernel": "conv3 (sin^2 stencil)",
+                    "ms_per_convolution": cs * 1e3, "cells_per_s": cells / cs,
+                    "achieved_GBps": cells * 5.0 / cs / 1e9,
+                    "launches": tm["conv_launches"]}
+        else:
+            # z pass: 1 B in, 2 B out; y pass: 2 in, 4 out; x pass: 4 in, 4 out
+            gbs = cells * 17.0 / cs / 1e9
+            conv = {"bound": "hbm", "kernel": "conv_z + conv_y + conv_x",
+                    "ms_per_convolution": cs * 1e3, "achieved": gbs,
+                    "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": gbs / pk.get("hbm_gbs", 6800.0), "bytes_per_cell": 17,
+                    "launches": tm["conv_launches"]}
     force = None
     if tm["pair_force_launches"]:
         fs = tm["pair_force_ms"] * 1e-3 / tm["pair_force_launches"]
@@ -410,7 +418,9 @@ def run_vesis(args, world, rank, local):
                         "max": max(step_ms)},
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl[0],
+            "config": {"workload": args.workload + ("" if args.surface_kernel == "gauss"
+                                                    else "_sin2"),
+                       "desc": wl[0], "surface_kernel": args.surface_kernel,
                        "grid": list(S.shape), "atoms": N,
                        "step": "one outer VESIS iteration from the initial state",
                        "l2": "working set (U, E fields %.0f MB) larger than L2"
@@ -805,6 +815,8 @@ def main():
     ap.add_argument("--workload", default="protein2000_grid256",
                     choices=list(workloads().keys()))
     ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--surface-kernel", default="gauss", choices=["gauss", "sin2"],
+                    help="surface kernel: separable Gaussian (default) or the paper's sin^2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--converge", action="store_true",
                     help="time one converged relaxation instead of the step benchmark")
