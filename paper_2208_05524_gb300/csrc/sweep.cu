@@ -220,7 +220,7 @@ __device__ __forceinline__ void red_add(unsigned *p, unsigned v)
 
 // Decide phase for tile t (one warp).
 __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int t,
-                                            double &e_lane, unsigned &n_lane, int half)
+                                            double &e_lane, unsigned &n_lane)
 {
     const int lane = threadIdx.x & 31;
     const GridDesc &g = A.g;
@@ -274,17 +274,16 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
         m += __popc(bm);
     }
     __syncwarp();
-    // verdicts on the leaders of the warp's half of the tile (bricks
-    // [hb0, hb0 + nbh)): a leader wins unless another within r is better.
-    // G lanes share one brick and split the scan of the compacted words.
+    // verdicts: a leader of the tile wins unless another within r is better.
+    // G lanes share one of the tile's bricks and split the scan of the
+    // compacted words between them.
     unsigned long long wmask = 0ull;
     {
-        const int nbh = nbt / 2, hb0 = half * nbh;
-        const int G = nbh >= 32 ? 1 : 32 / nbh;      // 8 for 4 bricks
+        const int G = nbt >= 32 ? 1 : 32 / nbt;      // 4 for 8 bricks
         const int P = 32 / G;                         // bricks per pass
         const int gl = lane / G, sub = lane - gl * G;
-        for (int b0 = 0; b0 < nbh; b0 += P) {
-            const int b = b0 + gl < nbh ? hb0 + b0 + gl : nbt;
+        for (int b0 = 0; b0 < nbt; b0 += P) {
+            const int b = b0 + gl;
             unsigned long long L = 0ull;
             int lx = 0, ly = 0, lz = 0;
             if (b < nbt) {
@@ -310,8 +309,8 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
             const unsigned gm = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
             const bool win = L != 0ull && sub == 0 && ((lb >> (gl * G)) & gm) == 0u;
             const unsigned wb = __ballot_sync(0xffffffffu, win);
-            for (int q = 0; q < P && b0 + q < nbh; ++q)
-                if ((wb >> (q * G)) & 1u) wmask |= 1ull << (hb0 + b0 + q);
+            for (int q = 0; q < P && b0 + q < nbt; ++q)
+                if ((wb >> (q * G)) & 1u) wmask |= 1ull << (b0 + q);
         }
     }
     if (wmask == 0ull) return;
@@ -377,7 +376,7 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
 template <bool STENCIL>
 __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, const int *qw,
                                             const int *kt,
-                                            int t, bool first, int half)
+                                            int t, bool first)
 {
     const int lane = threadIdx.x & 31;
     const GridDesc &g = A.g;
@@ -391,15 +390,14 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
     const unsigned zmask = (1u << zlim) - 1u;
 
     // ---------------------------------------------------------- loads
-    // All of a lane's loads are issued before the first use.  The warp owns
-    // half of the tile, x in [4 half, 4 half + 4): its cells' W and U, row
-    // rho = lane + 32 half, (x, y) = (rho >> 3, rho & 7).
-    unsigned Wr[1][TS];
-    float Ur[1][TS];
-    bool rowok[1];
+    // All of a lane's loads are issued before the first use.  W and U of the
+    // tile's own cells: rows rho = lane + 32 m, (x, y) = (rho >> 3, rho & 7).
+    unsigned Wr[2][TS];
+    float Ur[2][TS];
+    bool rowok[2];
 #pragma unroll
-    for (int m = 0; m < 1; ++m) {
-        const int rho = lane + 32 * half;
+    for (int m = 0; m < 2; ++m) {
+        const int rho = lane + 32 * m;
         const int x = rho >> 3, y = rho & 7;
         rowok[m] = (i0 + x < g.nx) && (j0 + y < g.ny);
 #pragma unroll
@@ -476,7 +474,8 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
     // ------------------------------------------------- posted winners
     int nw = 0;
     if (!first) {
-        // (the bitmap is cleared after both halves of the tile have read it)
+        // the bitmap is consumed: clear it for the next round's postings
+        if (lane < 8 && pmask) reinterpret_cast<unsigned *>(pa + kPostMaskOff)[lane] = 0u;
         // slot values to shared memory (reuse the candidate W list as scratch)
         unsigned short *ps = reinterpret_cast<unsigned short *>(M.u.cW);
 #pragma unroll
@@ -513,16 +512,16 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
         }
         nw = min(nw, kMaxWin);
         __syncwarp();
-        // W of the half's cells
-        bool changed[1] = {false};
+        // W of the tile's own cells
+        bool changed[2] = {false, false};
         for (int e = 0; e < nw; ++e) {
             const unsigned wv = M.u.win[e];
             const int wx = (int)(wv & 31) - 8, wy = (int)((wv >> 5) & 31) - 8,
                       wz = (int)((wv >> 10) & 31) - 8;
             const int sgn = ((wv >> 15) & 1u) ? -1 : 1;   // solute -> solvent lowers W
 #pragma unroll
-            for (int m = 0; m < 1; ++m) {
-                const int rho = lane + 32 * half;
+            for (int m = 0; m < 2; ++m) {
+                const int rho = lane + 32 * m;
                 const int ax = (rho >> 3) - wx, ay = (rho & 7) - wy;
                 if (abs(ax) > r || abs(ay) > r) continue;
                 changed[m] = true;
@@ -544,9 +543,9 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
             }
         }
 #pragma unroll
-        for (int m = 0; m < 1; ++m) {
+        for (int m = 0; m < 2; ++m) {
             if (!changed[m] || !rowok[m]) continue;
-            const int rho = lane + 32 * half;
+            const int rho = lane + 32 * m;
             const long long o = (long long)(i0 + (rho >> 3)) * nyz +
                                 (long long)(j0 + (rho & 7)) * g.nz + k0;
             if (A.vec) {
@@ -566,11 +565,11 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
     for (int b = lane; b < nbt; b += 32) M.u.bmax[b] = 0ull;
     int ncand = 0;
     {
-        unsigned cm[1], lab[1];
+        unsigned cm[2], lab[2];
         int cnt = 0;
 #pragma unroll
-        for (int m = 0; m < 1; ++m) {
-            const int rho = lane + 32 * half;
+        for (int m = 0; m < 2; ++m) {
+            const int rho = lane + 32 * m;
             const int x = rho >> 3, y = rho & 7;
             const unsigned c = M.u.hr[(x + 1) * 10 + (y + 1)];
             const unsigned d = (c ^ M.u.hr[x * 10 + (y + 1)]) |
@@ -592,8 +591,8 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
         int pos = incl - cnt;
         __syncwarp();     // the slot scratch in cW is no longer read
 #pragma unroll
-        for (int m = 0; m < 1; ++m) {
-            const int rho = lane + 32 * half;
+        for (int m = 0; m < 2; ++m) {
+            const int rho = lane + 32 * m;
 #pragma unroll
             for (int z = 0; z < TS; ++z) {
                 if ((cm[m] >> z) & 1u) {
@@ -636,9 +635,7 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
     }
     __syncwarp();
     bool any = false;
-    // the half's bricks: x in [4 half, 4 half + 4) is brick rows
-    // [half bpt / 2, (half + 1) bpt / 2), the indices [half nbt / 2, ...)
-    for (int b = half * (nbt / 2) + lane; b < (half + 1) * (nbt / 2); b += 32) {
+    for (int b = lane; b < nbt; b += 32) {
         const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
         const int gx = (i0 >> bsh) + bx, gy = (j0 >> bsh) + by, gz = (k0 >> bsh) + bz;
         if (gx >= A.nbx || gy >= A.nby || gz >= A.nbz) continue;
@@ -665,7 +662,6 @@ struct SweepShared {
     unsigned nf[NWARP];
     unsigned ncnt;
     int abort_flag;
-    unsigned char hl[2 * SW_THREADS];   // a half tile holds a leader
 };
 
 // Collects, in increasing order, this block's tiles t = blockIdx.x + k *
@@ -768,17 +764,13 @@ k_sweep(SweepArgs A)
     unsigned n_lane = 0;
     int round = 0, capped = 0;
     // opening pass: leaders of the starting labels
-    // (each tile is two tasks, one per half; a tile holds a leader if
-    // either half does)
     for (int base = 0; base < per_block; base += SW_THREADS) {
         const int n = gather_tiles(S, nullptr, false, base, ntiles, nullptr);
-        for (int q = wp; q < 2 * n; q += NWARP) {
-            const bool now = tile_update<STENCIL>(A, M, S.qw, kt, S.list[q >> 1], true, q & 1);
-            if (lane == 0) S.hl[q] = now;
+        for (int q = wp; q < n; q += NWARP) {
+            const int t = S.list[q];
+            const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, true);
+            if (lane == 0) set_own(A, S, t, now);
         }
-        __syncthreads();
-        for (int q = threadIdx.x; q < n; q += SW_THREADS)
-            set_own(A, S, S.list[q], (S.hl[2 * q] | S.hl[2 * q + 1]) != 0);
     }
     if (!grid_barrier(A, target, &S.abort_flag)) return;
     for (int k = 0;; ++k) {
@@ -793,8 +785,7 @@ k_sweep(SweepArgs A)
         if (threadIdx.x == 0) nl = ld_relaxed_u32(A.nlead);
         for (int base = 0; base < per_block; base += SW_THREADS) {
             const int n = own_list(S, base, per_block);
-            for (int q = wp; q < 2 * n; q += NWARP)
-                tile_decide(A, M, S.list[q >> 1], e_lane, n_lane, q & 1);
+            for (int q = wp; q < n; q += NWARP) tile_decide(A, M, S.list[q], e_lane, n_lane);
         }
         if (threadIdx.x == 0) S.ncnt = nl;
         __syncthreads();
@@ -806,18 +797,11 @@ k_sweep(SweepArgs A)
         // update
         for (int base = 0; base < per_block; base += SW_THREADS) {
             const int n = gather_tiles(S, A.upd, true, base, ntiles, nullptr);
-            for (int q = wp; q < 2 * n; q += NWARP) {
-                const bool now = tile_update<STENCIL>(A, M, S.qw, kt, S.list[q >> 1], false,
-                                                      q & 1);
-                if (lane == 0) S.hl[q] = now;
+            for (int q = wp; q < n; q += NWARP) {
+                const int t = S.list[q];
+                const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, false);
+                if (lane == 0) set_own(A, S, t, now);
             }
-            __syncthreads();
-            // both halves have read the postings: clear the slot bitmaps
-            for (int q = threadIdx.x; q < 8 * n; q += SW_THREADS)
-                reinterpret_cast<unsigned *>(A.post + (size_t)S.list[q >> 3] * kPostBytes +
-                                             kPostMaskOff)[q & 7] = 0u;
-            for (int q = threadIdx.x; q < n; q += SW_THREADS)
-                set_own(A, S, S.list[q], (S.hl[2 * q] | S.hl[2 * q + 1]) != 0);
         }
         if (!grid_barrier(A, target, &S.abort_flag)) return;
     }
