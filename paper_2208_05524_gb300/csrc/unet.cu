@@ -655,13 +655,6 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
         for (int v = 0; v < NBUF - 1 && v < nbv && v < U; ++v) issue(v);
         for (int u = 0; u < U && ok; ++u) {
             const int st = u / nbv;
-            // keep NBUF - 1 bricks of this stage in flight; buffer (u + NBUF - 1)
-            // % NBUF was last read by unit u - 1
-            const int v = u + NBUF - 1;
-            if (v < U && v / nbv == st) {
-                if (v >= NBUF && !wait_bar(mmb0, v - NBUF)) { ok = false; break; }
-                issue(v);
-            }
             if (!wait_bar(ldb0, u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned hbase = sha0 + (unsigned)(u % NBUF) * (unsigned)TMA_HALO;
@@ -693,6 +686,14 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(mmb0 + 8u * (unsigned)(u % NBUF)) : "memory");
+            // with this brick's MMAs queued, refill the buffer the previous
+            // brick read (unit u + NBUF - 1 of the same stage): the tensor
+            // cores never wait for the issuing thread
+            const int v = u + NBUF - 1;
+            if (v < U && v / nbv == st) {
+                if (v >= NBUF && !wait_bar(mmb0, v - NBUF)) { ok = false; break; }
+                issue(v);
+            }
             // stage boundary: replace the weights once every MMA of the stage
             // has completed, then refill the pipeline
             if (u + 1 < U && (u + 1) % nbv == 0) {
