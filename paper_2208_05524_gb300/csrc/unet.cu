@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(128) k_conv_halo(ConvArgs P)
 constexpr int TCY = 16, TCZ = 8;                           // brick (x extent 1)
 constexpr int TC_HX = 3, TC_HY = TCY + 2, TC_HZ = TCZ + 2;
 constexpr int TC_HALO_BYTES = TC_HX * TC_HY * 4 * TC_HZ * 16;   // 34,560
-constexpr long long kTcSpin = 1ll << 22;
+constexpr unsigned long long kTcWaitNs = 2000000000ull;   // 2 s bound on one wait
 // MMAs into one accumulator run one after another; the taps are dealt over
 // TC_CHAINS accumulators (summed in the epilogue) so that independent MMAs
 // keep the tensor pipe busy.
@@ -344,9 +344,13 @@ __device__ __forceinline__ unsigned smem_u32(const void *p)
     return (unsigned)__cvta_generic_to_shared(p);
 }
 
+// try_wait suspends the thread until the phase completes or a short
+// hardware time limit passes, so the loop polls without sleeping; the
+// global timer, read every 64 misses, bounds the whole wait.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
 {
-    for (long long i = 0; i < kTcSpin; ++i) {
+    unsigned long long t0 = 0;
+    for (unsigned i = 0;; ++i) {
         unsigned ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -354,9 +358,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
         if (ok) return true;
-        __nanosleep(20);
+        if ((i & 63u) == 0) {
+            unsigned long long now;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            if (i == 0) t0 = now;
+            else if (now - t0 > kTcWaitNs) return false;
+        }
     }
-    return false;
 }
 
 // 16-byte asynchronous global -> shared copy (zero fill when !valid): the
