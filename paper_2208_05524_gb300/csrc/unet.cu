@@ -67,6 +67,11 @@ struct ConvArgs {
     void *Y;             // bf16 [V][Cout] (relu) or float [V][Cout]
     int k16 = 2;         // halves of each 32-channel stage that hold data (the
                          // input layer's 3 features fill only the first)
+    // 1x1 head fused into a 32-channel layer's epilogue (TMA kernel only):
+    // hz[v] = hb + sum_c hw[c] y_c of the BF16-rounded outputs y, which are
+    // then not stored
+    const float *hw = nullptr, *hb = nullptr;
+    float *hz = nullptr;
 };
 
 constexpr int CM = 64;          // cells per block
@@ -763,6 +768,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
                                         __uint_as_float(r[c + 2]), __uint_as_float(r[c + 3]));
                 } else {
                     bf16 *dst = static_cast<bf16 *>(P.Y) + vo * P.Cout + cb;
+                    float hzv = P.hz ? *P.hb : 0.f;
 #pragma unroll
                     for (int c = 0; c < 32; c += 8) {
                         __align__(16) __nv_bfloat162 o[4];
@@ -772,8 +778,18 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
                                 fmaxf(__uint_as_float(r[c + 2 * q]) + P.bias[cb + c + 2 * q], 0.f),
                                 fmaxf(__uint_as_float(r[c + 2 * q + 1]) + P.bias[cb + c + 2 * q + 1],
                                       0.f));
-                        *reinterpret_cast<uint4 *>(dst + c) = *reinterpret_cast<const uint4 *>(o);
+                        if (P.hz) {      // the head's sum, in channel order
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                const float2 f = __bfloat1622float2(o[q]);
+                                hzv = fmaf(P.hw[c + 2 * q], f.x, hzv);
+                                hzv = fmaf(P.hw[c + 2 * q + 1], f.y, hzv);
+                            }
+                        } else {
+                            *reinterpret_cast<uint4 *>(dst + c) = *reinterpret_cast<const uint4 *>(o);
+                        }
                     }
+                    if (P.hz) P.hz[vo] = hzv;
                 }
             }
         }
@@ -1381,9 +1397,12 @@ int ensure_act(vesis_net n, int nx, int ny, int nz, bool train)
 
 unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
-void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
+// Returns true when the 1x1 head (hw, hb -> hz, a 32-channel layer's
+// outputs) was fused into the convolution, whose outputs were then not
+// stored; only the TMA kernel fuses it.
+bool conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
           const bf16 *Wt, const bf16 *Wtc, const float *bias, int Cout, void *Y, bool raw,
-          int k16 = 2)
+          int k16 = 2, const float *hw = nullptr, const float *hb = nullptr, float *hz = nullptr)
 {
     ConvArgs a;
     a.nx = nx;
@@ -1421,6 +1440,12 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
         if (tma_ok) {
             // enough bricks for weight-stationary blocks: TMA and bulk copies
             const unsigned nb = (bricks + TCW_NB - 1) / TCW_NB;
+            const bool fuse = hz && !raw && Cout == 32;
+            if (fuse) {
+                a.hw = hw;
+                a.hb = hb;
+                a.hz = hz;
+            }
             if (tc_tile(Cout) == 64) {
                 dim3 tg(nb, Cout / 64);
                 if (raw) k_conv_tma<64, true><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
@@ -1430,7 +1455,7 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
                 if (raw) k_conv_tma<32, true><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
                 else k_conv_tma<32, false><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
             }
-            return;
+            return fuse;
         }
         if (Cout % 64 == 0) {
             dim3 tg(bricks, Cout / 64);
@@ -1441,7 +1466,7 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
             if (raw) k_conv_tc<32, true><<<tg, 128, tc_smem_bytes(32), n->st>>>(a, n->d_err);
             else k_conv_tc<32, false><<<tg, 128, tc_smem_bytes(32), n->st>>>(a, n->d_err);
         }
-        return;
+        return false;
     }
     if (nx % HXB == 0 && ny % HYB == 0 && nz % HZB == 0 && Ca % 32 == 0 && Cb % 32 == 0) {
         const unsigned bricks = (unsigned)((nx / HXB) * (ny / HYB) * (nz / HZB));
@@ -1449,7 +1474,7 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
         const size_t sm = sizeof(HaloSmem<32>);
         if (raw) k_conv_halo<32, true><<<hg, 128, sm, n->st>>>(a);
         else k_conv_halo<32, false><<<hg, 128, sm, n->st>>>(a);
-        return;
+        return false;
     }
     const int BN = Cout >= 64 ? 64 : 32;
     dim3 grid((unsigned)((a.V + CM - 1) / CM), Cout / BN);
@@ -1460,6 +1485,7 @@ void conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
         if (raw) k_conv<32, true><<<grid, 128, 0, n->st>>>(a);
         else k_conv<32, false><<<grid, 128, 0, n->st>>>(a);
     }
+    return false;
 }
 
 void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
@@ -1517,8 +1543,11 @@ void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy
          th + L[L_D2].b_off, 64, n->d[2], false);
     conv(n, r[1][0], r[1][1], r[1][2], n->e[1], 64, n->d[2], 64, L[L_D1].Wt, L[L_D1].Wtc,
          th + L[L_D1].b_off, 32, n->d[1], false);
-    conv(n, nx, ny, nz, n->e[0], 32, n->d[1], 32, L[L_D0].Wt, L[L_D0].Wtc, th + L[L_D0].b_off, 32,
-         n->d[0], false);
+    // without targets (inference) the head may run in d0's epilogue
+    const bool fused = conv(n, nx, ny, nz, n->e[0], 32, n->d[1], 32, L[L_D0].Wt, L[L_D0].Wtc,
+                            th + L[L_D0].b_off, 32, n->d[0], false, 2, th + L[L_HEAD].w_off,
+                            th + L[L_HEAD].b_off, chi ? nullptr : n->z);
+    if (fused) return;
     count_launch();
     k_head<<<nblk(V0), 256, 0, n->st>>>(n->d[0], V0, th + L[L_HEAD].w_off,
                                         th + L[L_HEAD].b_off, chi, NX, NY, NZ, ox, oy, oz, ny, nz, n->z,
