@@ -72,6 +72,9 @@ struct ConvArgs {
     // then not stored
     const float *hw = nullptr, *hb = nullptr;
     float *hz = nullptr;
+    // only the taps at x offset 0 hold weights (the input layer with its x
+    // neighbours folded into channels): the TMA kernel skips the others
+    bool x1 = false;
 };
 
 constexpr int CM = 64;          // cells per block
@@ -553,15 +556,17 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
     }
 }
 
-// Weight-stationary blocks: each block takes TCW_NB consecutive bricks and
-// keeps a stage's weights in shared memory for all of them, with one FP32
-// accumulator per brick in tensor memory (TCW_NB x NT columns).  The
-// bricks' halos stream through two buffers: the next brick's halo loads
-// while the tensor cores run the current brick's 54 MMAs; a buffer is
-// refilled once the MMAs that read it have committed.  Stage boundaries
-// wait for the stage's last MMAs before the weights are replaced.
-constexpr int TCW_NB = 4;
-__host__ __device__ constexpr int tma_chains(int NT) { return 512 / (TCW_NB * NT); }
+// Weight-stationary blocks: each block takes nb consecutive bricks (up to
+// 512 / NT, chosen per launch) and keeps a stage's weights in shared memory
+// for all of them, with one FP32 accumulator per brick in tensor memory (nb
+// x NT columns).  The bricks' halos stream through NBUF buffers: the next
+// bricks' halos load while the tensor cores run the current brick's MMAs; a
+// buffer is refilled once the MMAs that read it have committed.  Stage
+// boundaries wait for the stage's last MMAs before the weights are
+// replaced.  The fixed cost of a block (tensor-memory allocation, barrier
+// set-up, the first copies, the epilogue's drain) is spread over its
+// bricks: 8 bricks per block instead of 4 took 6 % off the 384^3 forward.
+__host__ __device__ constexpr int tma_max_nb(int NT) { return 512 / NT; }
 
 // TMA form of the weight-stationary convolution, for a single input at the
 // output's resolution.  The stage's weights come pre-arranged in global
@@ -586,7 +591,7 @@ template <int NT, bool RAW>
 __global__ void __launch_bounds__(128, 1)
 k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
            const __grid_constant__ CUtensorMap tmB, const bf16 *__restrict__ Wtc, int nbricks,
-           int *err)
+           int nb, int *err)
 {
     constexpr int NBUF = tma_nbuf(NT);
     extern __shared__ __align__(1024) unsigned char smem_tma[];
@@ -598,8 +603,8 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
     int *sfail = reinterpret_cast<int *>(tail + 16 * NBUF + 4);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
-    const int b0 = blockIdx.x * TCW_NB;
-    const int nbv = min(TCW_NB, nbricks - b0);
+    const int b0 = blockIdx.x * nb;
+    const int nbv = min(nb, nbricks - b0);
     const int nst = (P.Ca + P.Cb) / 32;     // stages of the first input, then of the second
     const int U = nst * nbv;
     const int nnt = P.Cout / NT;
@@ -626,7 +631,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tslot;
-    constexpr int CH = tma_chains(NT);
+    constexpr int CH = 1;       // accumulator chains per brick (more did not help)
 
     if (t == 0) {
         const unsigned idesc = tc_idesc(NT);
@@ -639,15 +644,33 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
             const unsigned lb = ldb0 + 8u * buf;
             const unsigned sha = sha0 + buf * (unsigned)TMA_HALO;
             const bool wload = (u % nbv) == 0;
-            const unsigned tx = 2u * (unsigned)P.k16 * 540u * 16u +
-                                (wload ? (unsigned)tc_w_bytes(NT) : 0u);
+            // x1: the halo is the brick's own x-plane only (180 rows per box)
+            // the stage's weights [8-channel plane][tap][co][8 ch]: all of
+            // them, or for a half-filled stage (k16 = 1) the first two
+            // planes, and with x1 only the taps 9..17 of each
+            const bool wall = P.k16 == 2 && !P.x1;
+            const int ntap = P.x1 ? 9 : 27, tap0 = P.x1 ? 9 : 0;
+            const unsigned wrun = (unsigned)(ntap * NT * 16);
+            const unsigned wbytes = wall ? (unsigned)tc_w_bytes(NT) : 2u * (unsigned)P.k16 * wrun;
+            const unsigned tx = 2u * (unsigned)P.k16 * (P.x1 ? 180u : 540u) * 16u +
+                                (wload ? wbytes : 0u);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          :: "r"(lb), "r"(tx) : "memory");
             if (wload) {
                 const bf16 *src = Wtc + (size_t)(st * nnt + blockIdx.y) * (4 * 27 * NT * 8);
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                    :: "r"(swa), "l"(src), "r"((unsigned)tc_w_bytes(NT)), "r"(lb) : "memory");
+                if (wall) {
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                        :: "r"(swa), "l"(src), "r"((unsigned)tc_w_bytes(NT)), "r"(lb) : "memory");
+                } else {
+                    for (int kc = 0; kc < 2 * P.k16; ++kc) {
+                        const unsigned off = (unsigned)((kc * 27 + tap0) * NT * 16);
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                            :: "r"(swa + off), "l"(reinterpret_cast<const unsigned char *>(src) + off),
+                               "r"(wrun), "r"(lb) : "memory");
+                    }
+                }
             }
             const bool first_input = c0 < P.Ca;
             const unsigned long long map = reinterpret_cast<unsigned long long>(first_input ? &tmA : &tmB);
@@ -657,7 +680,8 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
                     "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                     " [%0], [%1, {%2, %3, %4, %5}], [%6];"
                     :: "r"(sha + (unsigned)(kc * TMA_PLANE)), "l"(map),
-                       "r"(cc + 8 * kc), "r"(bz * TCZ - 1), "r"(by * TCY - 1), "r"(bx - 1), "r"(lb)
+                       "r"(cc + 8 * kc), "r"(bz * TCZ - 1), "r"(by * TCY - 1),
+                       "r"(P.x1 ? bx : bx - 1), "r"(lb)
                     : "memory");
         };
         auto wait_bar = [&](unsigned base, int u) -> bool {
@@ -675,26 +699,33 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
             const unsigned long long bd0 = tc_desc(swa, 27 * NT * 16, 8 * 16);
             const unsigned dbase = tmem + (unsigned)((u % nbv) * CH * NT);
             const bool first = st == 0;
+            // with x1 only the taps 9..17 (x offset 0) run; the first CH of
+            // them start the accumulator chains
+            const int t0 = P.x1 ? 9 : 0;
             if (P.k16 == 2) {
 #pragma unroll
                 for (int tap = 0; tap < 27; ++tap) {
                     const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
-                    const unsigned long long ao = (unsigned long long)((da * TC_HY + db) * TC_HZ + dc);
+                    if (P.x1 && da != 1) continue;
+                    const unsigned long long ao =
+                        (unsigned long long)(((P.x1 ? 0 : da) * TC_HY + db) * TC_HZ + dc);
 #pragma unroll
                     for (int s2 = 0; s2 < 2; ++s2)
                         tc_mma(dbase + (unsigned)((tap % CH) * NT),
                                ad0 + ao + (unsigned long long)(2 * s2 * (TMA_PLANE / 16)),
                                bd0 + (unsigned long long)((2 * s2 * 27 + tap) * NT), idesc,
-                               (!first || tap >= CH || s2 > 0) ? 1u : 0u);
+                               (!first || tap >= t0 + CH || s2 > 0) ? 1u : 0u);
                 }
             } else {
 #pragma unroll
                 for (int tap = 0; tap < 27; ++tap) {
                     const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
-                    const unsigned long long ao = (unsigned long long)((da * TC_HY + db) * TC_HZ + dc);
+                    if (P.x1 && da != 1) continue;
+                    const unsigned long long ao =
+                        (unsigned long long)(((P.x1 ? 0 : da) * TC_HY + db) * TC_HZ + dc);
                     tc_mma(dbase + (unsigned)((tap % CH) * NT), ad0 + ao,
                            bd0 + (unsigned long long)(tap * NT), idesc,
-                           (!first || tap >= CH) ? 1u : 0u);
+                           (!first || tap >= t0 + CH) ? 1u : 0u);
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -962,7 +993,7 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs P)
 // to nx x ny x nz -> X0 [cell][32] bf16, channels >= F zero.  One thread per
 // cell: coalesced plane reads, four 16-byte stores.
 __global__ void k_pack_input(const float *__restrict__ x, int F, int NX, int NY, int NZ,
-                             int ox, int oy, int oz, int nx, int ny, int nz,
+                             int ox, int oy, int oz, int nx, int ny, int nz, bool fold,
                              bf16 *__restrict__ X0)
 {
     const long long V = (long long)nx * ny * nz;
@@ -974,8 +1005,20 @@ __global__ void k_pack_input(const float *__restrict__ x, int F, int NX, int NY,
     const long long G = (long long)NX * NY * NZ;
     const long long src = ((long long)(i + ox) * NY + (j + oy)) * NZ + (k + oz);
     __align__(16) bf16 c[kInPad];
+    if (fold) {
+        // channel dx F + f: feature f of the cell at x offset dx - 1 (zero
+        // outside the crop, as the convolution pads)
 #pragma unroll
-    for (int q = 0; q < kInPad; ++q) c[q] = __float2bfloat16(q < F ? x[q * G + src] : 0.f);
+        for (int q = 0; q < kInPad; ++q) {
+            const int dx = q / F, f = q - dx * F, ii = i + dx - 1;
+            c[q] = __float2bfloat16(dx < 3 && ii >= 0 && ii < nx
+                                        ? x[f * G + src + (long long)(dx - 1) * NY * NZ]
+                                        : 0.f);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kInPad; ++q) c[q] = __float2bfloat16(q < F ? x[q * G + src] : 0.f);
+    }
     uint4 *dst = reinterpret_cast<uint4 *>(X0 + v * kInPad);
 #pragma unroll
     for (int q = 0; q < kInPad / 8; ++q) dst[q] = reinterpret_cast<const uint4 *>(c)[q];
@@ -1151,9 +1194,12 @@ __global__ void k_pool_bwd(const float *__restrict__ dP, int nx, int ny, int nz,
 
 // Flat FP32 parameters (per layer W[co][ci][3][3][3] then b) -> bf16
 // forward weights Wt[tap][co][cip] and flipped input-gradient weights
-// Wd[tap][ci][co] (cip: ci padded; padded entries zero).
+// Wd[tap][ci][co] (cip: ci padded; padded entries zero).  fold: the input
+// carries each cell's x neighbours as channels dx ci_n + ci (dx = 0, 1, 2
+// for x offsets -1, 0, +1), so W[co][ci][dx][b][c] moves to the tap at x
+// offset 0, channel dx ci_n + ci, and the other taps are zero.
 __global__ void k_pack_weights(const float *__restrict__ W, int co_n, int ci_n, int cip,
-                               bf16 *__restrict__ Wt, bf16 *__restrict__ Wd)
+                               bool fold, bf16 *__restrict__ Wt, bf16 *__restrict__ Wd)
 {
     const long long n = 27ll * co_n * cip;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1161,15 +1207,23 @@ __global__ void k_pack_weights(const float *__restrict__ W, int co_n, int ci_n, 
     const int tap = (int)(e / ((long long)co_n * cip));
     const int co = (int)((e / cip) % co_n);
     const int ci = (int)(e % cip);
-    const float w = ci < ci_n ? W[((long long)co * ci_n + ci) * 27 + tap] : 0.f;
+    float w;
+    if (fold) {
+        const int dx = ci / ci_n, f = ci - dx * ci_n;
+        w = tap / 9 == 1 && dx < 3 ? W[((long long)co * ci_n + f) * 27 + dx * 9 + tap % 9] : 0.f;
+    } else {
+        w = ci < ci_n ? W[((long long)co * ci_n + ci) * 27 + tap] : 0.f;
+    }
     const bf16 b = __float2bfloat16(w);
     Wt[e] = b;
     if (Wd) Wd[((long long)(26 - tap) * cip + ci) * co_n + co] = b;
 }
 
-// dW[tap][co][cip] (FP32) -> flat gradient order W[co][ci][3][3][3].
+// dW[tap][co][cip] (FP32) -> flat gradient order W[co][ci][3][3][3]; with
+// fold (the packing above) W[co][ci][dx][b][c] is the x-offset-0 tap (b, c)
+// at channel dx ci_n + ci.
 __global__ void k_unpack_grad(const float *__restrict__ dW, int co_n, int ci_n, int cip,
-                              float *__restrict__ g)
+                              bool fold, float *__restrict__ g)
 {
     const long long n = (long long)co_n * ci_n * 27;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1177,7 +1231,8 @@ __global__ void k_unpack_grad(const float *__restrict__ dW, int co_n, int ci_n, 
     const int tap = (int)(e % 27);
     const int ci = (int)((e / 27) % ci_n);
     const int co = (int)(e / (27ll * ci_n));
-    g[e] = dW[((long long)tap * co_n + co) * cip + ci];
+    g[e] = fold ? dW[((long long)(9 + tap % 9) * co_n + co) * cip + (tap / 9) * ci_n + ci]
+                : dW[((long long)tap * co_n + co) * cip + ci];
 }
 
 __global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m,
@@ -1262,15 +1317,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }
 
 // Tensor map of a channels-last activation [nx][ny][nz][C] bf16 with the
-// halo box {8 ch, 10 z, 18 y, 3 x}; out-of-range cells read as zero.
-bool encode_halo_map(CUtensorMap *m, const bf16 *base, int C, int nx, int ny, int nz)
+// halo box {8 ch, 10 z, 18 y, hx x}; out-of-range cells read as zero.
+bool encode_halo_map(CUtensorMap *m, const bf16 *base, int C, int nx, int ny, int nz,
+                     int hx = TC_HX)
 {
     PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
     if (!fn) return false;
     const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)nx};
     const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * nz,
                                    (cuuint64_t)C * 2 * nz * ny};
-    const cuuint32_t box[4] = {8, (cuuint32_t)TC_HZ, (cuuint32_t)TC_HY, (cuuint32_t)TC_HX};
+    const cuuint32_t box[4] = {8, (cuuint32_t)TC_HZ, (cuuint32_t)TC_HY, (cuuint32_t)hx};
     const cuuint32_t es[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(base), dims, strides, box,
               es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1289,6 +1345,7 @@ struct vesis_net_t {
     int dev = 0;
     cudaStream_t st = nullptr;
     int F = 0;
+    bool fold = false;            // input layer: x neighbours folded into channels (3 F <= 32)
     long long P = 0;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *s = nullptr;
     Layer L[L_N];
@@ -1402,7 +1459,8 @@ unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 // stored; only the TMA kernel fuses it.
 bool conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
           const bf16 *Wt, const bf16 *Wtc, const float *bias, int Cout, void *Y, bool raw,
-          int k16 = 2, const float *hw = nullptr, const float *hb = nullptr, float *hz = nullptr)
+          int k16 = 2, const float *hw = nullptr, const float *hb = nullptr, float *hz = nullptr,
+          bool x1 = false)
 {
     ConvArgs a;
     a.nx = nx;
@@ -1418,12 +1476,14 @@ bool conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
     a.Cout = Cout;
     a.Y = Y;
     a.k16 = k16;
+    a.x1 = x1;
     count_launch();
     if (n->conv_kind == 1 && ny % TCY == 0 && nz % TCZ == 0 && Ca % 32 == 0 && Cb % 32 == 0 &&
         Cout % 32 == 0) {
         const unsigned bricks = (unsigned)(nx * (ny / TCY) * (nz / TCZ));
         CUtensorMap tm, tmb;
-        bool tma_ok = bricks >= 152u * TCW_NB && Wtc && encode_halo_map(&tm, A, Ca, nx, ny, nz);
+        bool tma_ok = bricks >= 152u * 4u && Wtc &&
+                      encode_halo_map(&tm, A, Ca, nx, ny, nz, x1 ? 1 : TC_HX);
         if (tma_ok && Cb > 0) {
             // the coarse input doubled to the output's resolution, so that
             // both inputs arrive by tensor-map boxes
@@ -1438,8 +1498,13 @@ bool conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
             tmb = tm;
         }
         if (tma_ok) {
-            // enough bricks for weight-stationary blocks: TMA and bulk copies
-            const unsigned nb = (bricks + TCW_NB - 1) / TCW_NB;
+            // enough bricks for weight-stationary blocks: TMA and bulk copies,
+            // nb bricks per block, halved from 512 / NT while that leaves
+            // fewer than two blocks per SM
+            const int NTt = tc_tile(Cout);
+            int bpb = tma_max_nb(NTt);
+            while (bpb > 2 && (long long)((bricks + bpb - 1) / bpb) * (Cout / NTt) < 2 * 152) bpb /= 2;
+            const unsigned nb = (bricks + bpb - 1) / bpb;
             const bool fuse = hz && !raw && Cout == 32;
             if (fuse) {
                 a.hw = hw;
@@ -1448,12 +1513,12 @@ bool conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
             }
             if (tc_tile(Cout) == 64) {
                 dim3 tg(nb, Cout / 64);
-                if (raw) k_conv_tma<64, true><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
-                else k_conv_tma<64, false><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
+                if (raw) k_conv_tma<64, true><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, tmb, Wtc, (int)bricks, bpb, n->d_err);
+                else k_conv_tma<64, false><<<tg, 128, tma_smem_bytes(64), n->st>>>(a, tm, tmb, Wtc, (int)bricks, bpb, n->d_err);
             } else {
                 dim3 tg(nb, Cout / 32);
-                if (raw) k_conv_tma<32, true><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
-                else k_conv_tma<32, false><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, tmb, Wtc, (int)bricks, n->d_err);
+                if (raw) k_conv_tma<32, true><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, tmb, Wtc, (int)bricks, bpb, n->d_err);
+                else k_conv_tma<32, false><<<tg, 128, tma_smem_bytes(32), n->st>>>(a, tm, tmb, Wtc, (int)bricks, bpb, n->d_err);
             }
             return fuse;
         }
@@ -1528,9 +1593,9 @@ void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy
     const float *th = n->theta;
     count_launch();
     k_pack_input<<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
-                                              n->X0);
+                                              n->fold, n->X0);
     conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, L[L_E0].Wtc, th + L[L_E0].b_off, 32,
-         n->e[0], false, (n->F + 15) / 16);
+         n->e[0], false, ((n->fold ? 3 : 1) * n->F + 15) / 16, nullptr, nullptr, nullptr, n->fold);
     for (int l = 1; l < 4; ++l) {
         const long long Vc = (long long)r[l][0] * r[l][1] * r[l][2];
         count_launch();
@@ -1560,7 +1625,7 @@ int pack_weights(vesis_net n)
         Layer &y = n->L[l];
         count_launch();
         k_pack_weights<<<nblk(27ll * y.co_n * y.cip), 256, 0, n->st>>>(
-            n->theta + y.w_off, y.co_n, y.ci_n, y.cip, y.Wt, y.Wd);
+            n->theta + y.w_off, y.co_n, y.ci_n, y.cip, l == L_E0 && n->fold, y.Wt, y.Wd);
         count_launch(2);
         k_pack_tc<<<nblk(27ll * y.co_n * y.cip), 256, 0, n->st>>>(y.Wt, y.co_n, y.cip,
                                                                  tc_tile(y.co_n), y.Wtc);
@@ -1584,6 +1649,7 @@ int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out)
     vesis_net n = new vesis_net_t();
     n->st = (cudaStream_t)cuda_stream;
     n->F = n_features;
+    n->fold = 3 * n_features <= kInPad;
     if (cudaGetDevice(&n->dev) != cudaSuccess) {
         delete n;
         return nfail(VESIS_E_CUDA, "no CUDA device");
@@ -1781,8 +1847,8 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
     auto unpack = [&](int l) {
         Layer &y = L[l];
         count_launch();
-        k_unpack_grad<<<nblk(27ll * y.co_n * y.ci_n), 256, 0, st>>>(y.dW, y.co_n, y.ci_n, y.cip,
-                                                                     n->grad + y.w_off);
+        k_unpack_grad<<<nblk(27ll * y.co_n * y.ci_n), 256, 0, st>>>(
+            y.dW, y.co_n, y.ci_n, y.cip, l == L_E0 && n->fold, n->grad + y.w_off);
     };
     // decoder: d0 (R0), d1 (R1), d2 (R2); skip inputs e0, e1, e2; coarse d1, d2, e3
     struct Dec {

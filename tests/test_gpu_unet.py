@@ -206,3 +206,32 @@ def test_weight_stationary_tcgen05_matches_mma():
     for name, sl in _layer_slices(3):
         err, cos = _compare(out["tcgen05"][2][sl], out["mma"][2][sl])
         assert err < 2e-2 and cos > 0.9998, (name, err, cos)
+
+
+def test_wide_input_without_folding_matches_oracle():
+    """With 3 features the input layer carries each cell's x neighbours as
+    channels (9 of its 32); with 12 features that no longer fits and the
+    layer keeps its 27 taps.  Logits, loss and every layer's gradient of the
+    12-feature network against the oracle, on both convolution paths."""
+    vs = _vs()
+    n = (16, 32, 16)
+    F = 12
+    theta, x, y = _problem(n, 11, F=F)
+    xd = _dev(x.reshape(F, -1).astype(np.float32), torch.float32)
+    yd = _dev(y.reshape(-1), torch.uint8)
+    zo = N.forward(theta, x).reshape(-1)
+    lo, go = N.loss_and_grad(theta, x, y.astype(np.float64))
+    for kind in ("mma", "tcgen05"):
+        net = vs.Net(F)
+        assert net.P == N.param_count(F)
+        net.set_params(theta)
+        net.set_conv_kernel(kind)
+        z = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
+        net.forward(xd, n, logits=z)
+        err, cos = _compare(z.cpu().numpy().astype(np.float64), zo)
+        assert err < 5e-2 and cos > 0.998, (kind, err, cos)
+        loss, g = net.loss_grad(xd, yd, n, grad=True)
+        assert loss == pytest.approx(lo, rel=1e-2)
+        for name, sl in _layer_slices(F):
+            err, cos = _compare(g[sl].astype(np.float64), go[sl])
+            assert err < 5e-2 and cos > 0.998, (kind, name, err, cos)
