@@ -581,10 +581,15 @@ __host__ __device__ constexpr int tma_max_nb(int NT) { return 512 / NT; }
 constexpr int TMA_PLANE = 8704;                         // 540 x 16 B padded to 128 B
 constexpr int TMA_HALO = 4 * TMA_PLANE;
 
+// The halo area holds tma_nbuf(NT) full buffers; a stage that loads fewer
+// planes (k16 = 1) or one x-plane (x1) cuts it into more, smaller buffers
+// (up to TMA_MAXBUF), so that more bricks' copies are in flight.
 __host__ __device__ constexpr int tma_nbuf(int NT) { return NT == 32 ? 4 : 3; }
+constexpr int TMA_MAXBUF = 16;
+constexpr int TMA_PLANE_X1 = 2944;                      // 180 x 16 B padded to 128 B
 __host__ __device__ constexpr int tma_smem_bytes(int NT)
 {
-    return tc_w_bytes(NT) + tma_nbuf(NT) * TMA_HALO + 128 + 128;
+    return tc_w_bytes(NT) + tma_nbuf(NT) * TMA_HALO + 16 * TMA_MAXBUF + 128 + 128;
 }
 
 template <int NT, bool RAW>
@@ -593,14 +598,17 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
            const __grid_constant__ CUtensorMap tmB, const bf16 *__restrict__ Wtc, int nbricks,
            int nb, int *err)
 {
-    constexpr int NBUF = tma_nbuf(NT);
+    // plane stride, buffer size and buffer count of this launch
+    const int PLs = P.x1 ? TMA_PLANE_X1 : TMA_PLANE;
+    const int HB = 2 * P.k16 * PLs;
+    const int NBUF = min(TMA_MAXBUF, tma_nbuf(NT) * TMA_HALO / HB);
     extern __shared__ __align__(1024) unsigned char smem_tma[];
     const unsigned raw0 = smem_u32(smem_tma);
     const unsigned pad = ((raw0 + 127u) & ~127u) - raw0;
     unsigned char *smem = smem_tma + pad;
-    unsigned char *tail = smem + tc_w_bytes(NT) + NBUF * TMA_HALO;
-    unsigned *tslot = reinterpret_cast<unsigned *>(tail + 16 * NBUF);
-    int *sfail = reinterpret_cast<int *>(tail + 16 * NBUF + 4);
+    unsigned char *tail = smem + tc_w_bytes(NT) + tma_nbuf(NT) * TMA_HALO;
+    unsigned *tslot = reinterpret_cast<unsigned *>(tail + 16 * TMA_MAXBUF);
+    int *sfail = reinterpret_cast<int *>(tail + 16 * TMA_MAXBUF + 4);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
     const int b0 = blockIdx.x * nb;
@@ -642,7 +650,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
             const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
             const unsigned buf = (unsigned)(u % NBUF);
             const unsigned lb = ldb0 + 8u * buf;
-            const unsigned sha = sha0 + buf * (unsigned)TMA_HALO;
+            const unsigned sha = sha0 + buf * (unsigned)HB;
             const bool wload = (u % nbv) == 0;
             // x1: the halo is the brick's own x-plane only (180 rows per box)
             // the stage's weights [8-channel plane][tap][co][8 ch]: all of
@@ -679,7 +687,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
                 asm volatile(
                     "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                     " [%0], [%1, {%2, %3, %4, %5}], [%6];"
-                    :: "r"(sha + (unsigned)(kc * TMA_PLANE)), "l"(map),
+                    :: "r"(sha + (unsigned)(kc * PLs)), "l"(map),
                        "r"(cc + 8 * kc), "r"(bz * TCZ - 1), "r"(by * TCY - 1),
                        "r"(P.x1 ? bx : bx - 1), "r"(lb)
                     : "memory");
@@ -694,8 +702,8 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
             const int st = u / nbv;
             if (!wait_bar(ldb0, u)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned hbase = sha0 + (unsigned)(u % NBUF) * (unsigned)TMA_HALO;
-            const unsigned long long ad0 = tc_desc(hbase, TMA_PLANE, TC_HZ * 16);
+            const unsigned hbase = sha0 + (unsigned)(u % NBUF) * (unsigned)HB;
+            const unsigned long long ad0 = tc_desc(hbase, (unsigned)PLs, TC_HZ * 16);
             const unsigned long long bd0 = tc_desc(swa, 27 * NT * 16, 8 * 16);
             const unsigned dbase = tmem + (unsigned)((u % nbv) * CH * NT);
             const bool first = st == 0;
@@ -712,7 +720,7 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
 #pragma unroll
                     for (int s2 = 0; s2 < 2; ++s2)
                         tc_mma(dbase + (unsigned)((tap % CH) * NT),
-                               ad0 + ao + (unsigned long long)(2 * s2 * (TMA_PLANE / 16)),
+                               ad0 + ao + (unsigned long long)(2 * s2 * (PLs / 16)),
                                bd0 + (unsigned long long)((2 * s2 * 27 + tap) * NT), idesc,
                                (!first || tap >= t0 + CH || s2 > 0) ? 1u : 0u);
                 }
@@ -756,22 +764,25 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!*sfail) {
+        // Each warp holds 32 cells of a brick: one y row of 8 z cells per 8
+        // lanes.  A cell's outputs pass through the (now idle) halo buffers
+        // so that each store instruction writes whole 64- or 128-byte cell
+        // rows instead of one 16-byte piece of 32 cells.  Chunk slots are
+        // XOR-swizzled so that neither side has bank conflicts.
         const long long nyz = (long long)P.ny * P.nz;
-        const int m = 32 * w + lane;                 // 4 warps: lane quarter = warp
+        uint4 *stg = reinterpret_cast<uint4 *>(smem + tc_w_bytes(NT)) + w * 256;   // 4 KB per warp
         for (int b = 0; b < nbv; ++b) {
             const int bb = b0 + b;
             const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
-            const long long vo = (long long)bx * nyz + (long long)(by * TCY + m / TCZ) * P.nz +
-                                 bz * TCZ + m % TCZ;
+            // cell of warp-local index c: row c >> 3 (y), z = c & 7
+            const long long vrow = (long long)bx * nyz + (long long)(by * TCY + 4 * w) * P.nz +
+                                   bz * TCZ;
+            const long long vo = vrow + (long long)(lane >> 3) * P.nz + (lane & 7);
 #pragma unroll
             for (int half = 0; half < NT / 32; ++half) {
                 unsigned r[32];
-                float sum[32];
-#pragma unroll
-                for (int c = 0; c < 32; ++c) sum[c] = 0.f;
-                for (int ch = 0; ch < CH; ++ch) {
                 const unsigned ta = tmem + ((unsigned)(32 * w) << 16) +
-                                    (unsigned)((b * CH + ch) * NT + 32 * half);
+                                    (unsigned)(b * CH * NT + 32 * half);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -784,43 +795,53 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
                       "=r"(r[30]), "=r"(r[31])
                     : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int c = 0; c < 32; ++c) sum[c] += __uint_as_float(r[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < 32; ++c) r[c] = __float_as_uint(sum[c]);
                 const int cb = co0 + 32 * half;
                 if (RAW) {
-                    float *dst = static_cast<float *>(P.Y) + vo * P.Cout + cb;
+                    // FP32: 8 chunks of 16 bytes per cell
 #pragma unroll
-                    for (int c = 0; c < 32; c += 4)
-                        *reinterpret_cast<float4 *>(dst + c) =
-                            make_float4(__uint_as_float(r[c]), __uint_as_float(r[c + 1]),
-                                        __uint_as_float(r[c + 2]), __uint_as_float(r[c + 3]));
-                } else {
-                    bf16 *dst = static_cast<bf16 *>(P.Y) + vo * P.Cout + cb;
-                    float hzv = P.hz ? *P.hb : 0.f;
+                    for (int q = 0; q < 8; ++q)
+                        stg[lane * 8 + (q ^ (lane & 7))] =
+                            make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+                    __syncwarp();
 #pragma unroll
-                    for (int c = 0; c < 32; c += 8) {
-                        __align__(16) __nv_bfloat162 o[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            o[q] = __floats2bfloat162_rn(
-                                fmaxf(__uint_as_float(r[c + 2 * q]) + P.bias[cb + c + 2 * q], 0.f),
-                                fmaxf(__uint_as_float(r[c + 2 * q + 1]) + P.bias[cb + c + 2 * q + 1],
-                                      0.f));
-                        if (P.hz) {      // the head's sum, in channel order
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float2 f = __bfloat1622float2(o[q]);
-                                hzv = fmaf(P.hw[c + 2 * q], f.x, hzv);
-                                hzv = fmaf(P.hw[c + 2 * q + 1], f.y, hzv);
-                            }
-                        } else {
-                            *reinterpret_cast<uint4 *>(dst + c) = *reinterpret_cast<const uint4 *>(o);
-                        }
+                    for (int s = 0; s < 8; ++s) {
+                        const int c = 4 * s + (lane >> 3), q = lane & 7;
+                        float *dst = static_cast<float *>(P.Y) +
+                                     (vrow + (long long)(c >> 3) * P.nz + (c & 7)) * P.Cout + cb + 4 * q;
+                        *reinterpret_cast<uint4 *>(dst) = stg[c * 8 + (q ^ (c & 7))];
                     }
-                    if (P.hz) P.hz[vo] = hzv;
+                    __syncwarp();
+                } else {
+                    float hzv = P.hz ? *P.hb : 0.f;
+                    __align__(16) __nv_bfloat162 o[16];
+#pragma unroll
+                    for (int c = 0; c < 32; c += 2)
+                        o[c / 2] = __floats2bfloat162_rn(
+                            fmaxf(__uint_as_float(r[c]) + P.bias[cb + c], 0.f),
+                            fmaxf(__uint_as_float(r[c + 1]) + P.bias[cb + c + 1], 0.f));
+                    if (P.hz) {      // the head's sum, in channel order
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const float2 f = __bfloat1622float2(o[c]);
+                            hzv = fmaf(P.hw[2 * c], f.x, hzv);
+                            hzv = fmaf(P.hw[2 * c + 1], f.y, hzv);
+                        }
+                        P.hz[vo] = hzv;
+                    } else {
+                        // BF16: 4 chunks of 16 bytes per cell
+                        const uint4 *ov = reinterpret_cast<const uint4 *>(o);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) stg[lane * 4 + (q ^ ((lane >> 1) & 3))] = ov[q];
+                        __syncwarp();
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) {
+                            const int c = 8 * s + (lane >> 2), q = lane & 3;
+                            bf16 *dst = static_cast<bf16 *>(P.Y) +
+                                        (vrow + (long long)(c >> 3) * P.nz + (c & 7)) * P.Cout + cb + 8 * q;
+                            *reinterpret_cast<uint4 *>(dst) = stg[c * 4 + (q ^ ((c >> 1) & 3))];
+                        }
+                        __syncwarp();
+                    }
                 }
             }
         }
@@ -992,10 +1013,12 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs P)
 // x (F planes of the full grid NX x NY x NZ, FP32) cropped at (ox, oy, oz)
 // to nx x ny x nz -> X0 [cell][32] bf16, channels >= F zero.  One thread per
 // cell: coalesced plane reads, four 16-byte stores.
-__global__ void k_pack_input(const float *__restrict__ x, int F, int NX, int NY, int NZ,
+template <int FF>     // FF > 0: F = FF known at compile time (the fold's indices fold away)
+__global__ void k_pack_input(const float *__restrict__ x, int Frt, int NX, int NY, int NZ,
                              int ox, int oy, int oz, int nx, int ny, int nz, bool fold,
                              bf16 *__restrict__ X0)
 {
+    const int F = FF > 0 ? FF : Frt;
     const long long V = (long long)nx * ny * nz;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
@@ -1592,8 +1615,12 @@ void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy
     Layer *L = n->L;
     const float *th = n->theta;
     count_launch();
-    k_pack_input<<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
-                                              n->fold, n->X0);
+    if (n->F == 3)
+        k_pack_input<3><<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
+                                                     n->fold, n->X0);
+    else
+        k_pack_input<0><<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
+                                                     n->fold, n->X0);
     conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, L[L_E0].Wtc, th + L[L_E0].b_off, 32,
          n->e[0], false, ((n->fold ? 3 : 1) * n->F + 15) / 16, nullptr, nullptr, nullptr, n->fold);
     for (int l = 1; l < 4; ++l) {
