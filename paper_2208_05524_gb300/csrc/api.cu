@@ -201,7 +201,7 @@ struct vesis_system_t {
 
     uint16_t *d_T1 = nullptr;
     uint32_t *d_T2 = nullptr, *d_W = nullptr;
-    double *d_dE = nullptr;         // dE per cell: serial flipping only, allocated on first use
+    double *d_dE = nullptr;
     float *d_U[2] = {nullptr, nullptr}, *d_E[2] = {nullptr, nullptr};
 
     long long *d_part_s = nullptr;
@@ -455,7 +455,7 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
         blocks = std::max(1, std::min(blocks, s->gate->blocks));
     }
     const int sp = span_begin(s);
-    VCK(launch_sweep(s->g, s->kw, s->d_k3, s->fc, chi, s->d_W, U, s->d_sweep,
+    VCK(launch_sweep(s->g, s->kw, s->d_k3, s->fc, chi, s->d_W, U, s->d_dE, s->d_sweep,
                      s->d_ctl, s->d_err, s->d_part_flips,
                      s->d_part_dE, s->d_rounds, s->d_capped, max_rounds,
                      blocks, s->d_rs, s->st));
@@ -815,6 +815,7 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VTRY(dalloc(s, &s->d_T1, G));
     VTRY(dalloc(s, &s->d_T2, G));
     VTRY(dalloc(s, &s->d_W, G));
+    VTRY(dalloc(s, &s->d_dE, G));
     for (int b = 0; b < 2; ++b) {
         VTRY(dalloc(s, &s->d_U[b], G));
         VTRY(dalloc(s, &s->d_E[b], 3 * G));
@@ -890,6 +891,8 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     }
     s->ntiles = sweep_tiles(s->g);
     VTRY(dalloc(s, &s->d_sweep, sweep_state_bytes(s->g, s->kw.r)));
+    VTRY(dalloc(s, &s->d_heap, heap_state_bytes(s->g)));
+    VTRY(dalloc(s, &s->d_heap_out, 3));
     VTRY(dalloc(s, &s->d_ctl, sweep_ctl_words()));
     VTRY(dalloc(s, &s->d_err, 1));
     VTRY(dalloc(s, &s->d_rounds, 1));
@@ -1098,14 +1101,6 @@ int vesis_blsm_heap(vesis_system s, uint8_t *chi_dev, const float *U_dev,
     // Each flip lowers the energy, so the process ends; the bound only
     // guards against a cycle of flips whose FP64 dE rounds below zero.
     const long long hard = 16 * s->G + 1024;
-    // the serial flipping's scratch (dE per cell, tile and group keys) is
-    // only allocated by its first use
-    if (!s->d_heap) {
-        VCK(cudaStreamSynchronize(s->st));
-        VTRY(dalloc(s, &s->d_dE, s->G));
-        VTRY(dalloc(s, &s->d_heap, heap_state_bytes(s->g)));
-        VTRY(dalloc(s, &s->d_heap_out, 3));
-    }
     enq_conv(s, chi_dev, s->d_W);
     long long *o = s->d_heap_out;
     VCK(launch_heap(s->g, s->kw, s->d_k3, s->fc, chi_dev, s->d_W, U_dev, s->d_dE, s->d_heap,

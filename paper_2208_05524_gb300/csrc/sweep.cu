@@ -86,8 +86,8 @@ struct SweepArgs {
     uint8_t *chi;
     uint32_t *W;
     const float *U;
+    double *dE;
     unsigned long long *PL;   // leader word per brick
-    double *PD;               // FP64 dE of the brick's leader (where PL is non-zero)
     uint8_t *PO;              // leader cell within its brick: di | dj << 2 | dk << 4
     unsigned *CB;             // labels, one bit per cell: row (i, j) is nzw words
     int nzw;
@@ -124,7 +124,6 @@ struct WarpMem {
             unsigned hr[kHaloRows];        // label bits of the halo rows (bit 0: z = -1)
             unsigned win[kMaxWin];         // winners: tile coords + 8 (5 bits each) | label << 15
             unsigned long long bmax[kMaxBricksPerTile];   // new leader per brick
-            unsigned short cq[512];        // tile cell -> its candidate's position
         } u;
     };
 };
@@ -249,19 +248,6 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
             }
         }
     }
-    // FP64 dE of the tile's own bricks' leaders (brick b = lane + 32 h), in
-    // flight with the words: a winner's dE needs no second round trip
-    double pdv[2] = {0.0, 0.0};
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int b = lane + 32 * h;
-        if (b < nbt) {
-            const int gx = (i0 >> bsh) + b / (bpt * bpt), gy = (j0 >> bsh) + (b / bpt) % bpt,
-                      gz = (k0 >> bsh) + b % bpt;
-            if (gx < A.nbx && gy < A.nby && gz < A.nbz)
-                pdv[h] = __ldcg(A.PD + ((long long)gx * A.nby + gy) * A.nbz + gz);
-        }
-    }
     // leader cells relative to the neighbourhood's first cell; the non-zero
     // words compacted for the scans below
     int m = 0;
@@ -346,7 +332,7 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
         asm volatile("red.relaxed.gpu.global.xor.b32 [%0], %1;"
                      :: "l"(A.CB + ((long long)ci * g.ny + cj) * A.nzw + (ck >> 5)),
                         "r"(1u << (ck & 31)) : "memory");
-        dv[h] = pdv[h];
+        dv[h] = __ldcg(A.dE + p);
         n_lane += 1u;
     }
     unsigned long long rest = wmask;
@@ -383,18 +369,6 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
     }
     e_lane += dv[0];
     e_lane += dv[1];
-}
-
-// dE = c [s (1 - 2w) - g0] - s h^3 U of a candidate with W, U and label
-// (solute = 1): the bracket is the integer N = s (S - 2W) - k0 over S, so
-// c * bracket = c_N N with c_N = c / S and one rounding.
-__device__ __forceinline__ double cand_dE(const SweepArgs &A, unsigned Wv, float Uv, bool solute)
-{
-    const int base = A.ksum - 2 * (int)Wv;
-    const int N = (solute ? -base : base) - A.qc3;
-    const double t1 = __dmul_rn(A.cD, (double)N);
-    const double t2 = __dmul_rn(A.h3, (double)Uv);
-    return __dadd_rn(t1, solute ? t2 : -t2);
 }
 
 // Update phase for tile t (one warp).  first: the opening pass (no
@@ -625,24 +599,33 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
                     M.u.cW[pos] = Wr[m][z];
                     M.u.cU[pos] = Ur[m][z];
                     M.u.cP[pos] = (unsigned short)((rho << 3) | z | (((lab[m] >> z) & 1u) << 9));
-                    M.u.cq[(rho << 3) | z] = (unsigned short)pos;
                     ++pos;
                 }
             }
         }
     }
     __syncwarp();
-    // dE of every candidate; the most negative of each brick is its leader
+    // dE = c [s (1 - 2w) - g0] - s h^3 U with s = 1 - 2 chi, w = W / S and
+    // g0 = k0 / S (S the sum of the kernel's weights, k0 its centre weight):
+    // the bracket is the integer N = s (S - 2W) - k0 over S, so
+    // c * bracket = c_N N with c_N = c / S and one rounding.
     for (int q0 = 0; q0 < ncand; q0 += 32) {
         const int q = q0 + lane;
         if (q >= ncand) continue;
+        const unsigned Wv = M.u.cW[q];
+        const float Uv = M.u.cU[q];
         const unsigned cp = M.u.cP[q];
         const int x = (cp >> 6) & 7, y = (cp >> 3) & 7, z = cp & 7;
         const bool solute = (cp >> 9) & 1u;
-        const double e = cand_dE(A, M.u.cW[q], M.u.cU[q], solute);
+        const int base = A.ksum - 2 * (int)Wv;
+        const int N = (solute ? -base : base) - A.qc3;
+        const double t1 = __dmul_rn(A.cD, (double)N);
+        const double t2 = __dmul_rn(A.h3, (double)Uv);
+        const double e = __dadd_rn(t1, solute ? t2 : -t2);
         if (e < 0.0) {
             const long long p =
                 (long long)(i0 + x) * nyz + (long long)(j0 + y) * g.nz + (k0 + z);
+            A.dE[p] = e;
             const unsigned key = __float_as_uint(__double2float_rn(e)) & 0x7fffffffu;
             const unsigned long long w = ((unsigned long long)key << 33) |
                                          ((0xffffffffull - (unsigned long long)p) << 1) |
@@ -664,9 +647,6 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
             leader_cell(A, w, gx, gy, gz, ci, cj, ck);
             A.PO[o] = (uint8_t)((ci & (A.bs - 1)) | ((cj & (A.bs - 1)) << 2) |
                                 ((ck & (A.bs - 1)) << 4));
-            // the leader's dE once more, by the same operations
-            const int q = M.u.cq[(((ci - i0) * TS + (cj - j0)) << 3) | (ck - k0)];
-            A.PD[o] = cand_dE(A, M.u.cW[q], M.u.cU[q], (w & 1ull) != 0ull);
         }
         any |= w != 0ull;
     }
@@ -894,7 +874,7 @@ size_t sweep_state_bytes(const GridDesc &g, int r)
     const size_t nt = (size_t)sweep_tiles(g);
     const size_t nb = (size_t)sweep_bricks(g, r);
     const size_t nzw = ((size_t)g.nz + 31) / 32;
-    return nb * 16 + pad256(nb) + nt * kPostBytes + pad256(nt) +
+    return nb * 8 + pad256(nb) + nt * kPostBytes + pad256(nt) +
            (size_t)g.nx * g.ny * nzw * 4;
 }
 
@@ -946,7 +926,7 @@ int sweep_ctl_words() { return 3 * kLine; }
 cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
                          const FlipConst &fc,
                          uint8_t *chi, uint32_t *W, const float *U,
-                         void *state, unsigned *ctl, int *err,
+                         double *dE, void *state, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
                          int *rounds, int *capped, int max_rounds, int blocks,
                          RoundState *rs, cudaStream_t st)
@@ -962,6 +942,7 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
     A.chi = chi;
     A.W = W;
     A.U = U;
+    A.dE = dE;
     A.ntx = (g.nx + TS - 1) / TS;
     A.nty = (g.ny + TS - 1) / TS;
     A.ntz = (g.nz + TS - 1) / TS;
@@ -977,8 +958,7 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
     if ((nt + blocks - 1) / blocks > (size_t)kOwnWords * 32) return cudaErrorInvalidValue;
     uint8_t *base = static_cast<uint8_t *>(state);
     A.PL = reinterpret_cast<unsigned long long *>(base);
-    A.PD = reinterpret_cast<double *>(base + nb * 8);
-    A.PO = base + nb * 16;
+    A.PO = base + nb * 8;
     A.post = A.PO + pad256(nb);
     A.upd = A.post + nt * kPostBytes;
     A.CB = reinterpret_cast<unsigned *>(A.upd + pad256(nt));

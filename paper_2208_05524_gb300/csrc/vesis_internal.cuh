@@ -167,10 +167,9 @@ int sweep_brick_edge(int r);
 long long sweep_bricks(const GridDesc &g, int r);
 cudaError_t sweep_grid_size(int nsm, int r, int *blocks);
 int sweep_ctl_words();   // unsigned words of the sweep control block
-// Bytes of sweep state (leader words and their dE per brick, per-tile
-// postings and flags, label bits).
+// Bytes of sweep state (leader words, per-tile postings and flags).
 size_t sweep_state_bytes(const GridDesc &g, int r);
-// state: sweep_state_bytes(), ctl: sweep_ctl_words(),
+// dE: G doubles, state: sweep_state_bytes(), ctl: sweep_ctl_words(),
 // err: 1 int, part_*: `blocks` entries; k3: the full stencil (device,
 // (2 kw.r + 1)^3, centred) or NULL for the product kernel kw.q; writes the
 // totals into *rs.
@@ -205,7 +204,7 @@ cudaError_t launch_heap(const GridDesc &g, const KernelW &kw, const int *k3,
 cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
                          const FlipConst &fc,
                          uint8_t *chi, uint32_t *W, const float *U,
-                         void *state, unsigned *ctl, int *err,
+                         double *dE, void *state, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
                          int *rounds, int *capped, int max_rounds, int blocks,
                          RoundState *rs, cudaStream_t st);
