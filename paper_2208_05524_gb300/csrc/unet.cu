@@ -568,12 +568,13 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs P, int *err)
 // bricks: 8 bricks per block instead of 4 took 6 % off the 384^3 forward.
 __host__ __device__ constexpr int tma_max_nb(int NT) { return 512 / NT; }
 
-// TMA form of the weight-stationary convolution, for a single input at the
-// output's resolution.  The stage's weights come pre-arranged in global
-// memory (one contiguous block per stage and tile of output channels) and
-// arrive by one bulk copy; a brick's halo arrives as tensor-map box loads
-// (8 channels x 10 z x 18 y x 3 x each, cells outside the grid zero-filled
-// by the copy engine).  Copies and MMAs complete on mbarriers, so one
+// TMA form of the weight-stationary convolution, for inputs at the
+// output's resolution (a decoder's coarse input is doubled first).  The
+// stage's weights come pre-arranged in global memory (one contiguous block
+// per stage and tile of output channels) and arrive by bulk copies (only
+// the planes and taps the stage uses); a brick's halo arrives as
+// tensor-map box loads (8 channels x 10 z x 18 y x 3 x each, or 1 x for
+// x1, cells outside the grid zero-filled by the copy engine).  Copies and MMAs complete on mbarriers, so one
 // thread runs the whole producer/consumer loop: it keeps the copies of the
 // next NBUF - 1 bricks in flight while the tensor cores work, and the
 // other warps only join for the epilogue.  Halo layout: [8-channel plane]
@@ -1011,8 +1012,10 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs P)
 
 // ------------------------------------------------------------ small kernels
 // x (F planes of the full grid NX x NY x NZ, FP32) cropped at (ox, oy, oz)
-// to nx x ny x nz -> X0 [cell][32] bf16, channels >= F zero.  One thread per
-// cell: coalesced plane reads, four 16-byte stores.
+// to nx x ny x nz -> X0 [cell][32] bf16: channel f = feature f, or with
+// fold channel dx F + f = feature f of the x neighbour dx - 1; unused
+// channels zero.  One thread per cell: coalesced plane reads, four 16-byte
+// stores.
 template <int FF>     // FF > 0: F = FF known at compile time (the fold's indices fold away)
 __global__ void k_pack_input(const float *__restrict__ x, int Frt, int NX, int NY, int NZ,
                              int ox, int oy, int oz, int nx, int ny, int nz, bool fold,
