@@ -36,9 +36,9 @@ METRIC = "atom-grid pair-evals/s"
 # capture (profiles/pair_energy_grid_protein2000_grid256.md and
 # pair_force_grid_protein2000_grid256.md), valid only for the source they
 # were taken on: reported as null once pair.cu changes.
-TRAFFIC = {"sha256_16": "948c03c5a61cc242", "workload": "protein2000_grid256",
-           "pair_energy_grid": 1024256 + 206256640,
-           "pair_force_grid": 855271168 + 52225024}
+TRAFFIC = {"sha256_16": "12418c4a9abb3a56", "workload": "protein2000_grid256",
+           "pair_energy_grid": 829440 + 206576640,
+           "pair_force_grid": 854342400 + 51791616}
 # FP32 lane operations per energy pair in the inner loop of the pair kernel:
 # dz, r^2, r^-2, r^-3, r^-6, two LJ FMAs, Q r^-3, three field FMAs (the
 # reciprocal square root runs on the SFU and is not counted; the x/y parts of
