@@ -857,19 +857,19 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
 }
 
 // Nearest doubling: Y[v][c] = X[parent(v)][c] for a fine grid nx x ny x nz
-// (16-byte copies; C a multiple of 8).
-__global__ void k_upsample(const bf16 *__restrict__ X, int nx, int ny, int nz, int C,
+// (16-byte copies; C / 8 = 2^qs groups of 8 channels): fine row (i, j) on
+// blockIdx.x, (k, group) on blockIdx.y x blockDim.x.
+__global__ void k_upsample(const bf16 *__restrict__ X, int nx, int ny, int nz, int C, int qs,
                            bf16 *__restrict__ Y)
 {
-    const int q = C / 8;
-    const long long n = (long long)nx * ny * nz * q;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const long long v = e / q;
-    const int part = (int)(e - v * q);
-    const int i = (int)(v / ((long long)ny * nz)), j = (int)((v / nz) % ny), k = (int)(v % nz);
+    const int q = C >> 3;
+    const int row = blockIdx.x, i = row / ny, j = row - i * ny;
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= nz * q) return;
+    const int k = e >> qs, part = e & (q - 1);
     const long long u = ((long long)(i >> 1) * (ny >> 1) + (j >> 1)) * (nz >> 1) + (k >> 1);
-    reinterpret_cast<uint4 *>(Y)[e] = reinterpret_cast<const uint4 *>(X + u * C)[part];
+    reinterpret_cast<uint4 *>(Y + ((long long)row * nz + k) * C)[part] =
+        reinterpret_cast<const uint4 *>(X + u * C)[part];
 }
 
 // Weights [27][Cout][Cin] -> the TMA form's layout: per stage of 32 input
@@ -1022,12 +1022,11 @@ __global__ void k_pack_input(const float *__restrict__ x, int Frt, int NX, int N
                              bf16 *__restrict__ X0)
 {
     const int F = FF > 0 ? FF : Frt;
-    const long long V = (long long)nx * ny * nz;
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    const int i = (int)(v / ((long long)ny * nz));
-    const int j = (int)((v / nz) % ny);
-    const int k = (int)(v % nz);
+    // row (i, j) on blockIdx.x, z on blockIdx.y x blockDim.x
+    const int row = blockIdx.x, i = row / ny, j = row - i * ny;
+    const int k = blockIdx.y * blockDim.x + threadIdx.x;
+    if (k >= nz) return;
+    const long long v = (long long)row * nz + k;
     const long long G = (long long)NX * NY * NZ;
     const long long src = ((long long)(i + ox) * NY + (j + oy)) * NZ + (k + oz);
     __align__(16) bf16 c[kInPad];
@@ -1051,24 +1050,39 @@ __global__ void k_pack_input(const float *__restrict__ x, int Frt, int NX, int N
 }
 
 // 2x2x2 mean pooling of [cell][C] bf16 at (nx, ny, nz) -> half resolution.
-__global__ void k_pool(const bf16 *__restrict__ X, int nx, int ny, int nz, int C,
+// One thread per coarse cell and group of 8 channels (C / 8 = 2^qs groups):
+// output row (i, j) on blockIdx.x, (k, group) on blockIdx.y x blockDim.x.
+// Each channel sums its 8 children in the same order as before, then
+// scales by 1/8.
+__global__ void k_pool(const bf16 *__restrict__ X, int nx, int ny, int nz, int C, int qs,
                        bf16 *__restrict__ Y)
 {
-    const int hx = nx >> 1, hy = ny >> 1, hz = nz >> 1;
-    const long long n = (long long)hx * hy * hz * C;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const long long u = e / C;
-    const int c = (int)(e - u * C);
-    const int i = (int)(u / ((long long)hy * hz)), j = (int)((u / hz) % hy), k = (int)(u % hz);
-    float s = 0.f;
+    const int hy = ny >> 1, hz = nz >> 1, q = C >> 3;
+    const int row = blockIdx.x, i = row / hy, j = row - i * hy;
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    if (e >= hz * q) return;
+    const int k = e >> qs, part = e & (q - 1);
+    float s[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s[c] = 0.f;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const long long v = ((long long)(2 * i + (d >> 2)) * ny + 2 * j + ((d >> 1) & 1)) * nz +
                             2 * k + (d & 1);
-        s += __bfloat162float(X[v * C + c]);
+        const uint4 w = reinterpret_cast<const uint4 *>(X + v * C)[part];
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&w);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float2 f = __bfloat1622float2(h[c]);
+            s[2 * c] += f.x;
+            s[2 * c + 1] += f.y;
+        }
     }
-    Y[e] = __float2bfloat16(s * 0.125f);
+    __align__(16) __nv_bfloat162 o[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[c] = __floats2bfloat162_rn(s[2 * c] * 0.125f, s[2 * c + 1] * 0.125f);
+    reinterpret_cast<uint4 *>(Y + ((long long)row * hz + k) * C)[part] =
+        *reinterpret_cast<const uint4 *>(o);
 }
 
 // Head and loss: z = bh + sum_c Wh[c] d0[v][c]; with labels, the binary
@@ -1480,6 +1494,21 @@ int ensure_act(vesis_net n, int nx, int ny, int nz, bool train)
 
 unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Launch shape of the row-indexed kernels: rows (i, j) of an nx x ny x nz
+// grid on x, per_row items of a row on y in blocks of t threads.
+dim3 row_grid(int nx, int ny, long long per_row, int t = 128)
+{
+    return dim3((unsigned)((long long)nx * ny), (unsigned)((per_row + t - 1) / t));
+}
+
+// log2 of the number of 8-channel groups of C channels (C / 8 a power of two).
+int log2_groups(int C)
+{
+    int g = C / 8, s = 0;
+    while ((1 << s) < g) ++s;
+    return s;
+}
+
 // Returns true when the 1x1 head (hw, hb -> hz, a 32-channel layer's
 // outputs) was fused into the convolution, whose outputs were then not
 // stored; only the TMA kernel fuses it.
@@ -1517,8 +1546,8 @@ bool conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
                      encode_halo_map(&tmb, n->up, Cb, nx, ny, nz);
             if (tma_ok) {
                 count_launch();
-                k_upsample<<<nblk((long long)nx * ny * nz * (Cb / 8)), 256, 0, n->st>>>(
-                    B, nx, ny, nz, Cb, n->up);
+                k_upsample<<<row_grid(nx, ny, (long long)nz * (Cb / 8)), 128, 0, n->st>>>(
+                    B, nx, ny, nz, Cb, log2_groups(Cb), n->up);
             }
         } else {
             tmb = tm;
@@ -1619,18 +1648,19 @@ void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy
     const float *th = n->theta;
     count_launch();
     if (n->F == 3)
-        k_pack_input<3><<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
+        k_pack_input<3><<<row_grid(nx, ny, nz), 128, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
                                                      n->fold, n->X0);
     else
-        k_pack_input<0><<<nblk(V0), 256, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
+        k_pack_input<0><<<row_grid(nx, ny, nz), 128, 0, n->st>>>(x, n->F, NX, NY, NZ, ox, oy, oz, nx, ny, nz,
                                                      n->fold, n->X0);
     conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, L[L_E0].Wtc, th + L[L_E0].b_off, 32,
          n->e[0], false, ((n->fold ? 3 : 1) * n->F + 15) / 16, nullptr, nullptr, nullptr, n->fold);
     for (int l = 1; l < 4; ++l) {
         const long long Vc = (long long)r[l][0] * r[l][1] * r[l][2];
         count_launch();
-        k_pool<<<nblk(Vc * kCh[l - 1]), 256, 0, n->st>>>(n->e[l - 1], r[l - 1][0], r[l - 1][1],
-                                                         r[l - 1][2], kCh[l - 1], n->p[l - 1]);
+        k_pool<<<row_grid(r[l][0], r[l][1], (long long)r[l][2] * (kCh[l - 1] / 8)), 128, 0, n->st>>>(
+            n->e[l - 1], r[l - 1][0], r[l - 1][1], r[l - 1][2], kCh[l - 1], log2_groups(kCh[l - 1]),
+            n->p[l - 1]);
         conv(n, r[l][0], r[l][1], r[l][2], n->p[l - 1], kCh[l - 1], nullptr, 0, L[l].Wt, L[l].Wtc,
              th + L[l].b_off, kCh[l], n->e[l], false);
     }
