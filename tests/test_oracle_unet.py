@@ -146,3 +146,33 @@ def test_backward_matches_finite_differences():
         tm[i] -= h
         fd = (N.loss_and_grad(tp, x, y)[0] - N.loss_and_grad(tm, x, y)[0]) / (2 * h)
         assert g[i] == pytest.approx(fd, rel=2e-4, abs=1e-8), i
+
+
+def test_folding_x_neighbours_into_channels_is_exact():
+    """The input layer's reading on the GPU: each cell carries the features
+    of its x neighbours (offsets -1, 0, +1) as channels dx F + f, zero
+    outside the grid, and the 3 x 3 x 3 convolution becomes one over the
+    taps at x offset 0 with weights W'[co, dx F + f, 1, b, c] =
+    W[co, f, dx, b, c] (all other taps zero).  Both the output and the
+    weight gradient must agree with the unfolded layer to rounding."""
+    rng = np.random.default_rng(7)
+    F, co = 3, 5
+    n = (5, 4, 6)
+    X = rng.normal(size=(F,) + n)
+    W = rng.normal(size=(co, F, 3, 3, 3))
+    b = rng.normal(size=co)
+    Xf = np.zeros((3 * F,) + n)
+    for dx in range(3):
+        for i in range(n[0]):
+            ii = i + dx - 1
+            if 0 <= ii < n[0]:
+                Xf[dx * F:(dx + 1) * F, i] = X[:, ii]
+    Wf = np.zeros((co, 3 * F, 3, 3, 3))
+    for dx in range(3):
+        Wf[:, dx * F:(dx + 1) * F, 1] = W[:, :, dx]
+    assert np.allclose(N.conv(Xf, Wf, b), N.conv(X, W, b), rtol=1e-12, atol=1e-12)
+    dY = rng.normal(size=(co,) + n)
+    _, dW, _ = N.conv_backward(X, W, dY)
+    _, dWf, _ = N.conv_backward(Xf, Wf, dY)
+    for dx in range(3):
+        assert np.allclose(dWf[:, dx * F:(dx + 1) * F, 1], dW[:, :, dx], rtol=1e-12, atol=1e-12)
