@@ -1656,7 +1656,6 @@ void forward(vesis_net n, const float *x, int NX, int NY, int NZ, int ox, int oy
     conv(n, nx, ny, nz, n->X0, kInPad, nullptr, 0, L[L_E0].Wt, L[L_E0].Wtc, th + L[L_E0].b_off, 32,
          n->e[0], false, ((n->fold ? 3 : 1) * n->F + 15) / 16, nullptr, nullptr, nullptr, n->fold);
     for (int l = 1; l < 4; ++l) {
-        const long long Vc = (long long)r[l][0] * r[l][1] * r[l][2];
         count_launch();
         k_pool<<<row_grid(r[l][0], r[l][1], (long long)r[l][2] * (kCh[l - 1] / 8)), 128, 0, n->st>>>(
             n->e[l - 1], r[l - 1][0], r[l - 1][1], r[l - 1][2], kCh[l - 1], log2_groups(kCh[l - 1]),
