@@ -646,7 +646,9 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
         const unsigned idesc = tc_idesc(NT);
         // unit u: stage u / nbv, brick u % nbv, buffer u % NBUF (its k-th
         // use, k = u / NBUF, completes phase k of that buffer's barriers)
+        int issued = 0;      // units whose copies have been issued (in order)
         auto issue = [&](int u) {
+            issued = u + 1;
             const int st = u / nbv, bb = b0 + u % nbv, c0 = st * 32;
             const int bz = bb % nzb, by = (bb / nzb) % nyb, bx = bb / (nzb * nyb);
             const unsigned buf = (unsigned)(u % NBUF);
@@ -759,6 +761,9 @@ k_conv_tma(ConvArgs P, const __grid_constant__ CUtensorMap tmA,
         if (!ok) {
             *sfail = 1;
             atomicExch(err, 1);
+            // copies still in flight target this block's shared memory:
+            // wait (bounded) for the last one of each buffer
+            for (int q = max(0, issued - NBUF); q < issued; ++q) wait_bar(ldb0, q);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
