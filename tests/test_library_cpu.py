@@ -207,3 +207,27 @@ def test_bend_torsion_lists_from_a_bond_graph():
     assert np.allclose(t["torsion_psi"][0], [np.pi, 0, np.pi, 0, np.pi, 0, np.pi])
     sub = synth.subset(t, [1, 2, 3])
     assert sub["bonds"].tolist() == [[0, 1], [1, 2]]
+
+
+def test_network_and_extension_argument_errors_without_device(built):
+    # the learned initialiser's and the f-rows' entry points check their
+    # arguments before any CUDA call
+    from paper_2208_05524_gb300 import vesis
+    L = vesis.lib()
+    h = C.c_void_p()
+    assert L.vesis_net_create(3, None, None) == -1
+    assert L.vesis_net_create(0, None, C.byref(h)) == -1
+    assert b"n_features" in L.vesis_last_error()
+    assert L.vesis_net_create(33, None, C.byref(h)) == -1
+    n = C.c_longlong()
+    assert L.vesis_net_param_count(None, C.byref(n)) == -1
+    assert L.vesis_net_set_params(None, None) == -1
+    assert L.vesis_net_forward(None, None, 8, 8, 8, None, None, None) == -1
+    assert L.vesis_net_loss_grad(None, None, None, 8, 8, 8, None, None, None) == -1
+    assert L.vesis_net_adam_step(None, 1e-3, 0.9, 0.999, 1e-8) == -1
+    assert L.vesis_net_set_conv_kernel(None, 1) == -1
+    assert L.vesis_net_destroy(None) == 0
+    out = (C.c_double * 5)()
+    assert L.vesis_ss_terms(None, out) == -1
+    assert L.vesis_blsm_heap(None, None, None, None, 10, None, None, None) == -1
+    assert L.vesis_features(None, None, None, None, 0.01, None) == -1
