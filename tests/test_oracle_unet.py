@@ -176,3 +176,23 @@ def test_folding_x_neighbours_into_channels_is_exact():
     _, dWf, _ = N.conv_backward(Xf, Wf, dY)
     for dx in range(3):
         assert np.allclose(dWf[:, dx * F:(dx + 1) * F, 1], dW[:, :, dx], rtol=1e-12, atol=1e-12)
+
+
+def test_features_invert_to_the_energy_parts():
+    """Channel 0 is asinh of the vdW part U - C|E|^2 over the scale, channel
+    1 asinh of the CFA part C|E|^2, channel 2 the tight labels: energy
+    densities built as scale * sinh(a) + scale * sinh(b) come back as a and
+    b (a swapped channel or a missed subtraction fails)."""
+    rng = np.random.default_rng(11)
+    n = (3, 4, 5)
+    a = rng.normal(size=n) * 3.0
+    b = rng.normal(size=n) * 3.0
+    scale = 0.01
+    cfa = scale * np.sinh(b)
+    U = scale * np.sinh(a) + cfa
+    chi = (rng.random(n) > 0.5).astype(np.uint8)
+    x = N.features(U, cfa, chi, scale=scale)
+    assert x.shape == (3,) + n
+    assert np.allclose(x[0], a, rtol=1e-12, atol=1e-12)
+    assert np.allclose(x[1], b, rtol=1e-12, atol=1e-12)
+    assert np.array_equal(x[2], chi.astype(np.float64))
