@@ -766,3 +766,24 @@ def test_bend_and_torsion_invariances():
     x2 = s["xyz"] @ R.T + np.array([1.0, -2.0, 0.5])
     eb2, et2, _ = O.bonded_terms(s, x2)
     assert eb2 == pytest.approx(eb, rel=1e-11) and et2 == pytest.approx(et, rel=1e-11)
+
+
+def test_sampled_positions_and_tight_labels_match_full_grid_and_brute_force():
+    """The sampled forms used by the full-size parity tests: cell centres at
+    listed cells equal the full grid's, and the tight labels there (with
+    phi = min_i |x - r_i| - d_i) equal both the full-grid labels and a
+    brute-force distance check written here."""
+    from paper_2208_05524_gb300 import synth
+    s = synth.protein_like(n_atoms=120, n=24, seed=5)
+    n = O.grid_shape(s)
+    rng = np.random.default_rng(3)
+    cells = rng.choice(int(np.prod(n)), 400, replace=False)
+    P = O.grid_positions(s).reshape(-1, 3)
+    assert np.array_equal(O.cell_positions(s, cells), P[cells])
+    chi_full = O.init_labels(s).reshape(-1)
+    lab, phi = O.init_labels_at(s, cells)
+    assert np.array_equal(lab, chi_full[cells])
+    d = np.asarray(s["init"]["d"], np.float64)
+    dist = np.linalg.norm(P[cells][:, None, :] - s["xyz"][None, :, :], axis=-1) - d[None, :]
+    assert np.allclose(phi, dist.min(axis=1), rtol=0, atol=1e-12)
+    assert np.array_equal(lab, (dist.min(axis=1) < 0).astype(np.uint8))
