@@ -23,7 +23,8 @@ def built():
 
 
 def _declared():
-    src = open(HEADER).read()
+    with open(HEADER) as f:
+        src = f.read()
     return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(vesis_\w+)\s*\(",
                                  src, flags=re.M)))
 
@@ -44,7 +45,8 @@ def test_library_exports_every_declared_symbol(built):
 
 def test_binding_declares_every_symbol(built):
     from paper_2208_05524_gb300 import vesis
-    src = open(vesis.__file__).read()
+    with open(vesis.__file__) as f:
+        src = f.read()
     for n in _declared():
         assert n in src, n
 
