@@ -33,9 +33,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "atom-grid pair-evals/s"
 # DRAM bytes (read + write) per launch of the pair kernels from one ncu
-# capture (profiles/pair_energy_grid_protein2000_grid256.md and
-# pair_force_grid_protein2000_grid256.md), valid only for the source they
-# were taken on: reported as null once pair.cu changes.
+# capture of the default workload (dram__bytes_read.sum and
+# dram__bytes_write.sum), valid only for the source they were taken on:
+# reported as null once pair.cu changes.
 TRAFFIC = {"sha256_16": "12418c4a9abb3a56", "workload": "protein2000_grid256",
            "pair_energy_grid": 829440 + 206576640,
            "pair_force_grid": 854342400 + 51791616}
