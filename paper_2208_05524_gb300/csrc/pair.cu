@@ -463,7 +463,10 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
     __shared__ __align__(16) CellPairs s_c[PF_STAGE];
     __shared__ int s_wc[2 * PF_THREADS / 32];
     __shared__ float s_box[6 * (PF_THREADS / 32)];
-    const int chunk = blockIdx.x;
+    // the atom tile varies fastest in launch order: the blocks of one cell
+    // chunk run together and its labels and field come from DRAM once
+    const int chunk = blockIdx.y;
+    const int tile = blockIdx.x;
     const long long c0 = (long long)chunk * chunk_len;
     const long long c1 = min(G, c0 + chunk_len);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -472,10 +475,10 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
     float ax[APT], ay[APT], az[APT], k1[APT], k2[APT], kq[APT],
         kq3[APT];
     int an[APT];
-    const float4 A0 = a.xyzq[blockIdx.y * ATOMS];   // exists: tiles are non-empty
+    const float4 A0 = a.xyzq[tile * ATOMS];   // exists: tiles are non-empty
 #pragma unroll
     for (int u = 0; u < APT; ++u) {
-        an[u] = blockIdx.y * ATOMS + u * PF_THREADS + threadIdx.x;
+        an[u] = tile * ATOMS + u * PF_THREADS + threadIdx.x;
         if (an[u] < a.n) {
             const float4 A = a.xyzq[an[u]];
             const float4 F = a.fcoef[an[u]];
@@ -627,7 +630,7 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             o[2] = acc[u][2];
         }
     }
-    if (nsolvent && blockIdx.y == 0 && threadIdx.x == 0) atomicAdd(nsolvent, seen);
+    if (nsolvent && tile == 0 && threadIdx.x == 0) atomicAdd(nsolvent, seen);
 }
 
 void launch_pair_force_grid(const GridDesc &g, const ForcePlan &fp,
@@ -637,7 +640,7 @@ void launch_pair_force_grid(const GridDesc &g, const ForcePlan &fp,
                             unsigned long long *nsolvent, cudaStream_t st)
 {
     const long long G = (long long)g.nx * g.ny * g.nz;
-    dim3 grid(fp.nchunk, fp.atom_tiles);
+    dim3 grid(fp.atom_tiles, fp.nchunk);
     count_launch();
     if (fp.apt == 2)
         k_pair_force_grid<2><<<grid, PF_THREADS, 0, st>>>(g, G, fp.chunk_len, chi, Ex, Ey, Ez,
@@ -670,14 +673,15 @@ k_point_force(const float4 *__restrict__ pts, const float *__restrict__ wf,
 {
     __shared__ float4 s_p[PF_STAGE];
     __shared__ float4 s_e[PF_STAGE];
-    const int chunk = blockIdx.x;
+    const int chunk = blockIdx.y;   // atom tiles fastest, as in k_pair_force_grid
+    const int tile = blockIdx.x;
     const long long c0 = (long long)chunk * chunk_len;
     const long long c1 = min((long long)np, c0 + chunk_len);
     float ax[PF_APT], ay[PF_APT], az[PF_APT], k1[PF_APT], k2[PF_APT], kq[PF_APT];
     int an[PF_APT];
 #pragma unroll
     for (int u = 0; u < PF_APT; ++u) {
-        an[u] = blockIdx.y * PF_ATOMS + u * PF_THREADS + threadIdx.x;
+        an[u] = tile * PF_ATOMS + u * PF_THREADS + threadIdx.x;
         if (an[u] < a.n) {
             const float4 A = a.xyzq[an[u]];
             const float4 F = a.fcoef[an[u]];
@@ -740,7 +744,7 @@ void launch_point_force(const float4 *pts, const float *wf, int np,
                         const AtomsDev &a, float rmin2, double *part,
                         cudaStream_t st)
 {
-    dim3 grid(fp.nchunk, fp.atom_tiles);
+    dim3 grid(fp.atom_tiles, fp.nchunk);
     count_launch();
     k_point_force<<<grid, PF_THREADS, 0, st>>>(pts, wf, np, UE, fp.chunk_len,
                                                a, rmin2, part);
