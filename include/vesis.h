@@ -247,6 +247,21 @@ int vesis_atom_forces(vesis_system s, const uint8_t *chi_dev,
 int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
                 const vesis_relax_opts *opts, vesis_relax_stats *stats_out);
 
+/* Bound on the flip sweep's device-side waits.  The sweep (the rounds of
+ * vesis_blsm_relax and of the interface relaxations inside vesis_relax)
+ * runs as one cooperative launch whose blocks meet at a grid barrier twice
+ * per round.  A block that has polled the barrier `polls` times without
+ * seeing it complete (each poll an L2 load plus a 32 ns sleep) raises the
+ * sweep's error flag and returns, and so does every other block at its
+ * next barrier; the call then returns VESIS_E_CUDA with the message "flip
+ * sweep grid barrier timed out".  The labels passed in are then partly
+ * relaxed and must be reset by the caller; the system stays usable, and
+ * the next call starts its sweep state afresh.  Default 2^24 polls (seconds
+ * of waiting: only a hung block reaches it).  polls >= 0; 0 gives up at the
+ * first poll that finds the barrier still open, which makes the failure
+ * path testable without any fault.  VESIS_E_ARG for polls < 0. */
+int vesis_set_wait_limit(vesis_system s, long long polls);
+
 /* Tile shapes of the two pair kernels: cells of a z-pencil per thread of
  * the energy-density kernel (4, 8 or 16, default 8) and atoms per thread of the
  * grid-to-atom gradient kernel (2 or 4, default 4).  Every cell sums its
@@ -391,6 +406,10 @@ typedef struct {
     double conv_ms;              /* surface-kernel convolutions (three passes each) */
     long long conv_launches;     /* convolutions timed */
     long long conv_cells;        /* cells x convolutions */
+    long long sweep_tiles_decide;   /* 8^3 tiles visited by the sweeps' decide
+                                       phases (a tile holding a leader, per round) */
+    long long sweep_tiles_update;   /* and by their update phases (a tile a
+                                       winner reached, per round) */
 } vesis_timing;
 
 /* enable != 0 starts recording (and clears the totals); 0 stops. */

@@ -230,6 +230,7 @@ struct vesis_system_t {
 
     // persistent sweep state
     int sweep_blocks = 0, ntiles = 0;
+    long long spin_limit = kSweepSpinLimit;   // polls of a sweep barrier wait
     uint8_t *d_sweep = nullptr;
     uint8_t *d_heap = nullptr;      // tile and group keys of the serial flipping
     long long *d_heap_out = nullptr;   // flips, dE sum (as bits), capped
@@ -237,6 +238,7 @@ struct vesis_system_t {
     int *d_err = nullptr, *d_rounds = nullptr, *d_capped = nullptr;
     unsigned long long *d_part_flips = nullptr;
     double *d_part_dE = nullptr;
+    unsigned long long *d_part_tiles = nullptr;
 
     double *d_scal = nullptr;   // two banks of S_BANK doubles
     RoundState *d_rs = nullptr;
@@ -258,6 +260,7 @@ struct vesis_system_t {
         int kind;            // 0 energy, 1 force, 2 sweep batch
         long long units;     // pairs or cells x rounds
         long long rounds;
+        long long tiles_decide, tiles_update;   // sweep: tiles visited per phase
     };
     std::vector<Span> spans;
     std::vector<cudaEvent_t> ev_pool;
@@ -303,7 +306,7 @@ cudaEvent_t take_event(vesis_system s)
 int span_begin(vesis_system s)
 {
     if (!s->timing) return -1;
-    vesis_system_t::Span sp{take_event(s), take_event(s), 0, 0, 0};
+    vesis_system_t::Span sp{take_event(s), take_event(s), 0, 0, 0, 0, 0};
     cudaEventRecord(sp.a, s->st);
     s->spans.push_back(sp);
     return (int)s->spans.size() - 1;
@@ -337,6 +340,8 @@ void collect_spans(vesis_system s)
             s->tm.sweep_ms += ms;
             s->tm.sweep_rounds += sp.rounds;
             s->tm.sweep_cells += sp.units;
+            s->tm.sweep_tiles_decide += sp.tiles_decide;
+            s->tm.sweep_tiles_update += sp.tiles_update;
         } else {
             s->tm.conv_ms += ms;
             s->tm.conv_launches += 1;
@@ -457,8 +462,8 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
     const int sp = span_begin(s);
     VCK(launch_sweep(s->g, s->kw, s->d_k3, s->fc, chi, s->d_W, U, s->d_dE, s->d_sweep,
                      s->d_ctl, s->d_err, s->d_part_flips,
-                     s->d_part_dE, s->d_rounds, s->d_capped, max_rounds,
-                     blocks, s->d_rs, s->st));
+                     s->d_part_dE, s->d_part_tiles, s->d_rounds, s->d_capped, max_rounds,
+                     blocks, s->spin_limit, s->d_rs, s->st));
     span_end(s, sp, 2, 0, 0);
     VCK(cudaMemcpyAsync(s->h_rs, s->d_rs, sizeof(RoundState),
                         cudaMemcpyDeviceToHost, s->st));
@@ -471,6 +476,8 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
         const long long rounds = s->h_rs->round + (s->h_rs->capped ? 0 : 1);
         s->spans[sp].rounds = rounds;
         s->spans[sp].units = s->G * rounds;
+        s->spans[sp].tiles_decide = (long long)s->h_rs->tiles_decide;
+        s->spans[sp].tiles_update = (long long)s->h_rs->tiles_update;
     }
     *out = *s->h_rs;
     return VESIS_OK;
@@ -899,6 +906,7 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VTRY(dalloc(s, &s->d_capped, 1));
     VTRY(dalloc(s, &s->d_part_flips, s->sweep_blocks));
     VTRY(dalloc(s, &s->d_part_dE, s->sweep_blocks));
+    VTRY(dalloc(s, &s->d_part_tiles, 2 * (size_t)s->sweep_blocks));
 
     VTRY(dalloc(s, &s->d_scal, 2 * S_BANK));
     VTRY(dalloc(s, &s->d_rs, 1));
@@ -1390,6 +1398,14 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     st.max_grad = gmax;
     if (stats_out) *stats_out = st;
     return status;
+}
+
+int vesis_set_wait_limit(vesis_system s, long long polls)
+{
+    if (!s) return fail(VESIS_E_ARG, "NULL system");
+    if (polls < 0) return fail(VESIS_E_ARG, "polls must be >= 0");
+    s->spin_limit = polls;
+    return VESIS_OK;
 }
 
 int vesis_set_tiles(vesis_system s, int energy_pencil, int force_atoms)

@@ -50,7 +50,6 @@ constexpr int TS = 8;             // tile edge
 #endif
 constexpr int SW_THREADS = VESIS_SWEEP_THREADS;
 constexpr int NWARP = SW_THREADS / 32;
-constexpr long long kSpinLimit = 1ll << 24;   // polls before the barrier gives up
 constexpr int kLine = 32;         // words per 128-byte line of the control block
 constexpr int kMaxBricksPerTile = 64;         // (8 / 2)^3 for bricks of edge 2
 constexpr int kHaloRows = (TS + 2) * (TS + 2);
@@ -103,9 +102,11 @@ struct SweepArgs {
     int *err;
     unsigned long long *part_flips;   // [gridDim.x]
     double *part_dE;                  // [gridDim.x]
+    unsigned long long *part_tiles;   // [2][gridDim.x]: tiles decided, tiles updated
     int *rounds_out;
     int *capped_out;
     int max_rounds;
+    long long spin_limit;     // polls before a barrier wait gives up
 };
 
 // Per-warp shared memory; the decide and update phases use it in turn.
@@ -133,9 +134,10 @@ struct WarpMem {
 // reduction (it orders the block's earlier writes, which bar.sync has made
 // visible to thread 0), the wait a relaxed poll (an acquire load per poll
 // would discard the SM's L1 under the blocks still working) closed by one
-// acquire fence; no reset is needed.  The poll is bounded and watches the
-// error flag every 256 polls; a timeout raises the flag and the caller
-// returns.
+// acquire fence; no reset is needed.  The poll is bounded (A.spin_limit
+// polls; 0 gives up at the first poll that finds the barrier open) and
+// watches the error flag every 256 polls; a timeout raises the flag and the
+// caller returns.
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
 {
     unsigned v;
@@ -153,8 +155,8 @@ __device__ __forceinline__ bool grid_barrier(const SweepArgs &A, unsigned &targe
                      : "memory");
         long long spins = 0;
         while ((int)(ld_relaxed_u32(A.bar) - target) < 0) {
-            if ((++spins & 255) == 0 &&
-                (spins > kSpinLimit || *(volatile int *)A.err)) {
+            if (++spins > A.spin_limit ||
+                ((spins & 255) == 0 && *(volatile int *)A.err)) {
                 atomicExch(A.err, 1);
                 *abort_flag = 1;
                 break;
@@ -762,6 +764,7 @@ k_sweep(SweepArgs A)
     unsigned target = 0;      // thread 0: arrivals the next barrier waits for
     double e_lane = 0.0;
     unsigned n_lane = 0;
+    unsigned long long t_dec = 0, t_upd = 0;   // thread 0: tiles visited per phase
     int round = 0, capped = 0;
     // opening pass: leaders of the starting labels
     for (int base = 0; base < per_block; base += SW_THREADS) {
@@ -785,6 +788,7 @@ k_sweep(SweepArgs A)
         if (threadIdx.x == 0) nl = ld_relaxed_u32(A.nlead);
         for (int base = 0; base < per_block; base += SW_THREADS) {
             const int n = own_list(S, base, per_block);
+            t_dec += (unsigned long long)n;
             for (int q = wp; q < n; q += NWARP) tile_decide(A, M, S.list[q], e_lane, n_lane);
         }
         if (threadIdx.x == 0) S.ncnt = nl;
@@ -797,6 +801,7 @@ k_sweep(SweepArgs A)
         // update
         for (int base = 0; base < per_block; base += SW_THREADS) {
             const int n = gather_tiles(S, A.upd, true, base, ntiles, nullptr);
+            t_upd += (unsigned long long)n;
             for (int q = wp; q < n; q += NWARP) {
                 const int t = S.list[q];
                 const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, false);
@@ -826,6 +831,8 @@ k_sweep(SweepArgs A)
         }
         A.part_flips[blockIdx.x] = tf;
         A.part_dE[blockIdx.x] = te;
+        A.part_tiles[blockIdx.x] = t_dec;
+        A.part_tiles[gridDim.x + blockIdx.x] = t_upd;
         if (blockIdx.x == 0) {
             *A.rounds_out = round;
             *A.capped_out = capped < 0 ? (ld_relaxed_u32(A.nlead) != 0u) : 0;
@@ -834,15 +841,19 @@ k_sweep(SweepArgs A)
 }
 
 __global__ void k_sweep_final(const unsigned long long *part_flips,
-                              const double *part_dE, int nb, const int *rounds,
-                              const int *capped, RoundState *rs)
+                              const double *part_dE, const unsigned long long *part_tiles,
+                              int nb, const int *rounds, const int *capped, RoundState *rs)
 {
-    unsigned long long f = 0;
+    unsigned long long f = 0, td = 0, tu = 0;
     double e = 0.0;
     for (int b = 0; b < nb; ++b) {
         f += part_flips[b];
         e += part_dE[b];
+        td += part_tiles[b];
+        tu += part_tiles[nb + b];
     }
+    rs->tiles_decide = td;
+    rs->tiles_update = tu;
     rs->done = 1;
     rs->round = *rounds;
     rs->capped = *capped;
@@ -928,8 +939,9 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
                          uint8_t *chi, uint32_t *W, const float *U,
                          double *dE, void *state, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
+                         unsigned long long *part_tiles,
                          int *rounds, int *capped, int max_rounds, int blocks,
-                         RoundState *rs, cudaStream_t st)
+                         long long spin_limit, RoundState *rs, cudaStream_t st)
 {
     SweepArgs A;
     A.g = g;
@@ -968,9 +980,11 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
     A.err = err;
     A.part_flips = part_flips;
     A.part_dE = part_dE;
+    A.part_tiles = part_tiles;
     A.rounds_out = rounds;
     A.capped_out = capped;
     A.max_rounds = max_rounds;
+    A.spin_limit = spin_limit;
     // leader words are all rewritten by the opening pass; postings start
     // empty (a slot is only read under its bitmap bit)
     cudaMemset2DAsync(A.post + kPostMaskOff, kPostBytes, 0, 32, nt, st);
@@ -990,7 +1004,7 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
                                                 dim3(SW_THREADS), args, kSweepSmem, st);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_sweep_final<<<1, 1, 0, st>>>(part_flips, part_dE, blocks, rounds, capped, rs);
+    k_sweep_final<<<1, 1, 0, st>>>(part_flips, part_dE, part_tiles, blocks, rounds, capped, rs);
     return cudaGetLastError();
 }
 

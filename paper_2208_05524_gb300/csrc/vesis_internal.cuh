@@ -45,6 +45,8 @@ struct RoundState {
     unsigned long long total_flips;
     double round_dE;       // sum of dE of the round in progress
     double total_dE;
+    unsigned long long tiles_decide;   // 8^3 tiles visited by the decide phases
+    unsigned long long tiles_update;   // and by the update phases
 };
 
 // Counts kernel launches made by the library (reported by the timing API).
@@ -170,7 +172,8 @@ int sweep_ctl_words();   // unsigned words of the sweep control block
 // Bytes of sweep state (leader words, per-tile postings and flags).
 size_t sweep_state_bytes(const GridDesc &g, int r);
 // dE: G doubles, state: sweep_state_bytes(), ctl: sweep_ctl_words(),
-// err: 1 int, part_*: `blocks` entries; k3: the full stencil (device,
+// err: 1 int, part_flips and part_dE: `blocks` entries, part_tiles: 2 x
+// `blocks` (tiles visited by the decide and update phases); k3: the full stencil (device,
 // (2 kw.r + 1)^3, centred) or NULL for the product kernel kw.q; writes the
 // totals into *rs.
 // Bends and torsions of G_ss (atoms.cu): term lists and, per atom, the
@@ -206,8 +209,12 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
                          uint8_t *chi, uint32_t *W, const float *U,
                          double *dE, void *state, unsigned *ctl, int *err,
                          unsigned long long *part_flips, double *part_dE,
+                         unsigned long long *part_tiles,
                          int *rounds, int *capped, int max_rounds, int blocks,
-                         RoundState *rs, cudaStream_t st);
+                         long long spin_limit, RoundState *rs, cudaStream_t st);
+// Default bound on a sweep block's polls of its grid barrier (several
+// seconds of waiting).
+constexpr long long kSweepSpinLimit = 1ll << 24;
 
 // --------------------------------------------------------------- atoms.cu
 struct AtomParamsDev {

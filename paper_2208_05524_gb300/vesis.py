@@ -47,7 +47,8 @@ class Timing(C.Structure):
                 ("pair_force_launches", _ll), ("pair_force_pairs", _ll),
                 ("sweep_ms", _d), ("sweep_rounds", _ll), ("sweep_cells", _ll),
                 ("kernel_launches", _ll), ("conv_ms", _d), ("conv_launches", _ll),
-                ("conv_cells", _ll)]
+                ("conv_cells", _ll), ("sweep_tiles_decide", _ll),
+                ("sweep_tiles_update", _ll)]
 
 
 STATUS = {0: "OK", -1: "E_ARG", -2: "E_CUDA", -3: "E_NAN", -4: "E_OUT_OF_BOX",
@@ -97,6 +98,7 @@ def lib():
         L.vesis_get_timing.argtypes = [_p, C.POINTER(Timing)]
         L.vesis_surface_weights_noalloc.argtypes = [C.POINTER(Params), _p, _p, _p]
         L.vesis_set_tiles.argtypes = [_p, _i, _i]
+        L.vesis_set_wait_limit.argtypes = [_p, _ll]
         L.vesis_features.argtypes = [_p, _p, _p, _p, _d, _p]
         L.vesis_ss_terms.argtypes = [_p, _p]
         L.vesis_set_bonded.argtypes = [_p, _i, _p, _p, _p, _i, _p, _p, _p]
@@ -331,6 +333,11 @@ class System:
         t = Timing()
         _check(lib().vesis_get_timing(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Timing._fields_}
+
+    def set_wait_limit(self, polls=1 << 24):
+        """Polls a flip-sweep block makes at a grid barrier before the sweep
+        gives up with VESIS_E_CUDA (vesis_set_wait_limit)."""
+        _check(lib().vesis_set_wait_limit(self.h, int(polls)))
 
     def set_tiles(self, energy_pencil=8, force_atoms=4):
         _check(lib().vesis_set_tiles(self.h, int(energy_pencil), int(force_atoms)))
