@@ -30,6 +30,16 @@ channel concatenation.  Arrays are channels-first (C, nx, ny, nz) here.
 Every function is written out from these definitions; the backward pass is
 the chain rule of the same definitions, pinned by central finite differences
 of the loss.
+
+Storage precision.  The network keeps its weights and the tensors it
+passes between layers in bfloat16 (8 significant bits) and accumulates in
+FP32.  forward() and loss_and_grad() take `store`, the rounding applied to
+every tensor the network keeps: the activations after each ReLU, the pooled
+activations and, in the backward pass, each layer's ReLU-masked output
+gradient (the tensor its weight and input gradients are built from).
+store=None keeps everything in FP64 (the exact function of the bfloat16
+weights and inputs); store=bf16_round gives the network at its defined
+storage precision, with FP64 arithmetic everywhere else.
 """
 from __future__ import annotations
 
@@ -125,7 +135,7 @@ def conv(X, W, b):
         for bb in range(k):
             for c in range(k):
                 Xs = _shift(X, a - r, bb - r, c - r)
-                Y += np.einsum("oi,ixyz->oxyz", W[:, :, a, bb, c], Xs)
+                Y += np.tensordot(W[:, :, a, bb, c], Xs, axes=(1, 0))
     return Y
 
 
@@ -139,9 +149,9 @@ def conv_backward(X, W, dY):
         for bb in range(k):
             for c in range(k):
                 Xs = _shift(X, a - r, bb - r, c - r)
-                dW[:, :, a, bb, c] = np.einsum("oxyz,ixyz->oi", dY, Xs)
+                dW[:, :, a, bb, c] = np.tensordot(dY, Xs, axes=([1, 2, 3], [1, 2, 3]))
                 # X[ci, q] feeds Y[co, q - t + r]
-                dX += _shift(np.einsum("oi,oxyz->ixyz", W[:, :, a, bb, c], dY),
+                dX += _shift(np.tensordot(W[:, :, a, bb, c], dY, axes=(0, 0)),
                              -(a - r), -(bb - r), -(c - r))
     db = dY.sum(axis=(1, 2, 3))
     return dX, dW, db
@@ -177,33 +187,41 @@ def bce_with_logits(z, y):
 
 # ---------------------------------------------------------------- network
 
-def forward(theta, x, F=None, keep=False):
-    """Logits z (nx, ny, nz) of features x (F, nx, ny, nz)."""
+def _store(store):
+    return (lambda v: v) if store is None else store
+
+
+def forward(theta, x, F=None, keep=False, store=None):
+    """Logits z (nx, ny, nz) of features x (F, nx, ny, nz); `store` rounds
+    every kept activation (see the module notes)."""
     F = x.shape[0] if F is None else F
     P = unpack(theta, F)
+    q = _store(store)
     relu = lambda v: np.maximum(v, 0.0)
     a = {}
-    a["e0"] = relu(conv(x, *P["e0"]))
-    a["p0"] = pool(a["e0"])
-    a["e1"] = relu(conv(a["p0"], *P["e1"]))
-    a["p1"] = pool(a["e1"])
-    a["e2"] = relu(conv(a["p1"], *P["e2"]))
-    a["p2"] = pool(a["e2"])
-    a["e3"] = relu(conv(a["p2"], *P["e3"]))
+    a["e0"] = q(relu(conv(x, *P["e0"])))
+    a["p0"] = q(pool(a["e0"]))
+    a["e1"] = q(relu(conv(a["p0"], *P["e1"])))
+    a["p1"] = q(pool(a["e1"]))
+    a["e2"] = q(relu(conv(a["p1"], *P["e2"])))
+    a["p2"] = q(pool(a["e2"]))
+    a["e3"] = q(relu(conv(a["p2"], *P["e3"])))
     a["c2"] = np.concatenate([a["e2"], up(a["e3"])])
-    a["d2"] = relu(conv(a["c2"], *P["d2"]))
+    a["d2"] = q(relu(conv(a["c2"], *P["d2"])))
     a["c1"] = np.concatenate([a["e1"], up(a["d2"])])
-    a["d1"] = relu(conv(a["c1"], *P["d1"]))
+    a["d1"] = q(relu(conv(a["c1"], *P["d1"])))
     a["c0"] = np.concatenate([a["e0"], up(a["d1"])])
-    a["d0"] = relu(conv(a["c0"], *P["d0"]))
+    a["d0"] = q(relu(conv(a["c0"], *P["d0"])))
     z = conv(a["d0"], *P["head"])[0]
     return (z, a, P) if keep else z
 
 
-def loss_and_grad(theta, x, y):
-    """Loss and its gradient with respect to the flat parameters."""
+def loss_and_grad(theta, x, y, store=None):
+    """Loss and its gradient with respect to the flat parameters; `store`
+    rounds the kept activations and the masked output gradients."""
     F = x.shape[0]
-    z, a, P = forward(theta, x, F, keep=True)
+    q = _store(store)
+    z, a, P = forward(theta, x, F, keep=True, store=store)
     loss, dz = bce_with_logits(z, y)
     g = {}
     _, g_hW, g_hb = conv_backward(a["d0"], P["head"][0], dz[None])
@@ -211,7 +229,7 @@ def loss_and_grad(theta, x, y):
     g["head"] = (g_hW, g_hb)
 
     def block(name, inp, out, dout):
-        dpre = dout * (out > 0)
+        dpre = q(dout * (out > 0))
         dinp, dW, db = conv_backward(inp, P[name][0], dpre)
         g[name] = (dW, db)
         return dinp

@@ -196,3 +196,40 @@ def test_features_invert_to_the_energy_parts():
     assert np.allclose(x[0], a, rtol=1e-12, atol=1e-12)
     assert np.allclose(x[1], b, rtol=1e-12, atol=1e-12)
     assert np.array_equal(x[2], chi.astype(np.float64))
+
+
+def test_bfloat16_storage_only_rounds_the_kept_tensors():
+    """store=None is the FP64 network; store=bf16_round keeps every stored
+    activation bfloat16-exact and stays within the bfloat16 rounding error
+    of the FP64 network, for the logits and for every gradient."""
+    rng = np.random.default_rng(7)
+    F = 3
+    n = (8, 16, 16)
+    theta = N.init_params(F, seed=8)
+    P = N.unpack(theta, F)
+    for name in P:
+        P[name] = (P[name][0], N.bf16_round(rng.normal(0.0, 0.05, P[name][1].shape)))
+    theta = N.pack(P, F)
+    x = N.bf16_round(rng.normal(size=(F,) + n))
+    y = (rng.random(n) > 0.5).astype(np.float64)
+    z64 = N.forward(theta, x)
+    assert np.array_equal(N.forward(theta, x, store=None), z64)
+    zq, a, _ = N.forward(theta, x, keep=True, store=N.bf16_round)
+    for name in ("e0", "p0", "e1", "p1", "e2", "p2", "e3", "d2", "d1", "d0"):
+        assert np.array_equal(N.bf16_round(a[name]), a[name]), name
+    # seven stored layers, each rounding to 8 significant bits (2^-8 relative)
+    err = np.linalg.norm(zq - z64) / np.linalg.norm(z64)
+    assert 0.0 < err < 7 * 2.0 ** -8, err
+    l64, g64 = N.loss_and_grad(theta, x, y)
+    lq, gq = N.loss_and_grad(theta, x, y, store=N.bf16_round)
+    assert lq == pytest.approx(l64, rel=7 * 2.0 ** -8)
+    # the gradients go through ReLU masks that the roundings can move on the
+    # coarse levels (32 cells at 1/4 resolution here), so they are compared
+    # by direction: a dropped term or a transposed operand has cosine ~0
+    o = 0
+    for name, ci, co, k in N.layer_shapes(F):
+        nw = co * ci * k ** 3 + co
+        u, v = gq[o:o + nw], g64[o:o + nw]
+        cos = float(np.dot(u, v) / (np.linalg.norm(u) * np.linalg.norm(v)))
+        assert cos > 0.99, (name, cos)
+        o += nw
