@@ -634,7 +634,7 @@ def _inside(sysd, xyz):
     return bool(np.all((xyz > lo) & (xyz < hi)))
 
 
-def relax(sysd, p, opts, chi=None, xyz=None, log=None):
+def relax(sysd, p, opts, chi=None, xyz=None, log=None, fields_fp32=False):
     """Full VESIS iteration (Steps 1-5): flips to a local minimum of the
     interface at fixed atoms (Step 2), then adaptive-mobility gradient
     steps of the atoms at fixed interface (Step 3, Eq. moveatoms with
@@ -648,11 +648,24 @@ def relax(sysd, p, opts, chi=None, xyz=None, log=None):
     finite, is rejected like an energy increase;
     at most max_gd_retries shrinks per step (then status 2, not
     converged).  Status: 0 gradient converged, 1 energy converged,
-    2 not converged (k_max or retry cap)."""
+    2 not converged (k_max or retry cap).
+
+    fields_fp32: the energy density U and the field E on the grid are
+    rounded to FP32 where they are stored (computed in FP64, then kept as
+    FP32 values, "FP32 fields, FP64 totals"); every sum, flip energy,
+    gradient and the accept test stay FP64."""
     xyz = _c64(sysd["xyz"] if xyz is None else xyz).copy()
     chi = init_labels(sysd) if chi is None else np.array(chi, np.uint8)
     sc = surface_constants(sysd, p)
-    U, _, E = fields(sysd, p, xyz)
+
+    def fields_stored(x):
+        U, _, E = fields(sysd, p, x)
+        if fields_fp32:
+            U = U.astype(np.float32).astype(np.float64)
+            E = E.astype(np.float32).astype(np.float64)
+        return U, E
+
+    U, E = fields_stored(xyz)
     G_prev = energy_terms(sysd, p, chi, xyz, U, E)["total"]
     M, ncnt, stable, k = opts["M0"], 0, 0, 0
     status = 2
@@ -669,7 +682,7 @@ def relax(sysd, p, opts, chi=None, xyz=None, log=None):
         retries = 0
         while True:
             x_new = xyz - omega * M * grad
-            U_n, _, E_n = fields(sysd, p, x_new)
+            U_n, E_n = fields_stored(x_new)
             G_new = energy_terms(sysd, p, chi, x_new, U_n, E_n)["total"]
             dG = G_new - G_old
             dGs = opts["dgstar_frac"] * abs(G_old)

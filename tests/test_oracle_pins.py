@@ -787,3 +787,19 @@ def test_sampled_positions_and_tight_labels_match_full_grid_and_brute_force():
     dist = np.linalg.norm(P[cells][:, None, :] - s["xyz"][None, :, :], axis=-1) - d[None, :]
     assert np.allclose(phi, dist.min(axis=1), rtol=0, atol=1e-12)
     assert np.array_equal(lab, (dist.min(axis=1) < 0).astype(np.uint8))
+
+
+def test_relax_with_fp32_fields_only_rounds_the_stored_fields():
+    """fields_fp32 stores U and E as FP32 values and changes nothing else:
+    the first interface relaxation and gradient step of a charged cluster
+    give the same accepted trials and M, and energies within the FP32
+    rounding of the fields (2^-24 relative per cell, summed)."""
+    s = synth.random_cluster(12, 24, 0.5, seed=3, net_charge=1.0)
+    p = O.params()
+    a = O.relax(s, p, O.relax_opts(max_outer=2))
+    b = O.relax(s, p, O.relax_opts(max_outer=2), fields_fp32=True)
+    assert a["iters"] == b["iters"] == 2
+    for ha, hb in zip(a["history"], b["history"]):
+        assert (ha["retries"], ha["M"], ha["ncnt"]) == (hb["retries"], hb["M"], hb["ncnt"])
+        assert hb["G"] == pytest.approx(ha["G"], rel=1e-6)
+    assert np.abs(a["xyz"] - b["xyz"]).max() < 1e-6
