@@ -485,9 +485,11 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
 
 // Gradient at the packed positions; E: the 3 x G field there.  Requires the
 // far-field node fields of the same positions (enq_far).  Writes d_grad and
-// d_gmax, and the solute-solute energies into bk.
+// d_gmax, and the solute-solute energies into bk.  ss_current: the last
+// enq_ss ran at d_pos into bk (its gradient is still in d_grad_ss), so the
+// solute-solute terms are not evaluated again.
 void enq_gradient(vesis_system s, const uint8_t *chi, const float *E,
-                  const double *d_pos, double *bk)
+                  const double *d_pos, double *bk, bool ss_current = false)
 {
     const int sp = span_begin(s);
     launch_pair_force_grid(s->g, s->fplan, chi, E, E + s->G, E + 2 * s->G,
@@ -503,7 +505,7 @@ void enq_gradient(vesis_system s, const uint8_t *chi, const float *E,
         launch_force_reduce(s->d_fpart, s->fplan_far.nchunk, s->n, 1.0,
                             s->d_grad_solv, 1, s->st);
     }
-    enq_ss(s, d_pos, bk);
+    if (!ss_current) enq_ss(s, d_pos, bk);
     launch_grad_combine(s->d_grad_solv, s->d_grad_ss, s->d_grad, 3 * s->n,
                         s->d_gmax, s->st);
 }
@@ -1298,7 +1300,7 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     k_gd_init<<<1, 1, 0, s->st>>>(s->d_gd, o.M0);
     VTRY(last_launch("relax init"));
     VTRY(read_bank(s, bank(s, cur)));
-    st.pair_evals += GN + FN;
+    st.pair_evals += GN + FN + NN;
     double G_prev = s->h_scal[S_TOTAL];
     if (!std::isfinite(G_prev)) return fail(VESIS_E_NAN, "non-finite initial energy");
 
@@ -1309,15 +1311,17 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
         VTRY(run_blsm(s, chi_dev, s->d_U[cur], o.max_flip_rounds, &rs, true));
         st.flip_rounds += rs.round;
         st.flips += (long long)rs.total_flips;
-        // Step 3.1-3.2: gradient and G_old at (Gamma^{k+1}, R^k)
-        enq_gradient(s, chi_dev, s->d_E[cur], s->d_xyz, bank(s, cur));
+        // Step 3.1-3.2: gradient and G_old at (Gamma^{k+1}, R^k); the
+        // solute-solute terms at R^k are current (the start or the accepted
+        // trial evaluated them last)
+        enq_gradient(s, chi_dev, s->d_E[cur], s->d_xyz, bank(s, cur), true);
         enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur), true);
         VTRY(last_launch("relax gradient"));
         VCK(cudaMemcpyAsync(s->h_u64, s->d_gmax, sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, s->st));
         VTRY(read_bank(s, bank(s, cur)));
         std::memcpy(&gmax, s->h_u64, sizeof(double));
-        st.pair_evals += (s->G - (long long)s->h_scal[S_NSOL]) * s->n + FN + NN;
+        st.pair_evals += (s->G - (long long)s->h_scal[S_NSOL]) * s->n + FN;
         if (!std::isfinite(gmax) || gmax >= 1.0e308) {
             status = fail(VESIS_E_NAN, "non-finite gradient");
             break;

@@ -263,6 +263,36 @@ def test_relax_two_atom_molecule_matches_oracle():
     assert x[1] - x[0] == pytest.approx(8.0, abs=0.01)
 
 
+def test_relax_charged_multi_atom_lock_step_matches_oracle():
+    """A charged 48-atom protein-like solute (net -3 e) on 48^3 at h = 0.5 A,
+    five outer iterations of Sec. 3.3 (Step 2 sweep, Step 3.1 gradient,
+    Eq. moveatoms with Eq. adjustmml, the accept/shrink rule of Step 3.4)
+    on the GPU and in the oracle, the oracle's fields stored in FP32 like
+    the GPU's.  The two take the same accepted and rejected trials, flip
+    rounds and flips, and end with the same M, the same labels, positions
+    within 1e-3 A and G within 1e-6."""
+    vs = _vs()
+    s = synth.protein_like(n_atoms=48, n=48, h=0.5, seed=5)
+    p = O.params()
+    ro = O.relax(s, p, O.relax_opts(max_outer=5), fields_fp32=True)
+    assert ro["iters"] == 5
+    hist = ro["history"]
+    assert any(h["retries"] > 0 for h in hist)        # rejected trials occur
+    S = vs.System(s)
+    chi0 = O.init_labels(s)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    r = S.relax(chi, s["xyz"], max_outer=5)
+    assert r["iterations"] == 5
+    assert r["gd_trials"] == sum(h["retries"] + 1 for h in hist)
+    assert r["flip_rounds"] == sum(h["rounds"] for h in hist)
+    assert r["flips"] == sum(h["flips"] for h in hist)
+    assert r["M"] == hist[-1]["M"]
+    mism = int((chi.cpu().numpy() != ro["chi"].reshape(-1)).sum())
+    assert mism == 0, mism
+    assert np.abs(r["xyz"] - ro["xyz"]).max() < 1e-3
+    assert r["G"] == pytest.approx(ro["G"], rel=1e-6)
+
+
 # --------------------------------------------------- full-size, sampled
 
 def test_protein_like_full_size_sampled():
