@@ -429,17 +429,24 @@ int vesis_get_timing(vesis_system s, vesis_timing *out);
  * graph, processes whose device memory belongs to a pool or arena that
  * forbids other allocations, and loops that must not enter the driver's
  * allocator cannot do that.  This call needs no system and allocates
- * nothing: its two intermediate planes live in a fixed array of device
- * global memory (6 bytes per cell for VESIS_NOALLOC_MAX_CELLS cells, about
- * 6 MiB) that every GPU holds from the moment the library is loaded until
- * the process exits.
+ * nothing itself: its two intermediate planes live in a fixed array of
+ * device global memory (6 bytes per cell for VESIS_NOALLOC_MAX_CELLS
+ * cells, about 6 MiB) that a GPU reserves when it loads the library's
+ * module and holds until the process exits.  Under CUDA's default lazy
+ * module loading that happens at the first call on the device (with
+ * CUDA_MODULE_LOADING=EAGER, when the library is loaded), so callers whose
+ * memory a pool or arena takes over must make that first call before it
+ * does.
  *   p        grid (nx, ny, nz), h, gauss_sigma and trunc_r are used; at most
  *            VESIS_NOALLOC_MAX_CELLS cells, larger grids return VESIS_E_ARG
  *   chi_dev  G labels (device), W_dev G uint32 (device, written)
  *   cuda_stream  stream to enqueue on (NULL = legacy default); the call
  *            returns once the work is enqueued
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * Each call whose stream is not being captured looks up the array's device
+ * address (with that device current); during a capture the address from
+ * the last such call on the device is used, so the first call on a device
+ * must come before any stream capture (one made during a capture returns
+ * VESIS_E_ARG).
  * All calls share the one array, and each call writes it in full before
  * reading it: calls whose work overlaps on the GPU (other streams, other
  * threads) race and must be serialised by the caller. */

@@ -9,7 +9,8 @@
 // not hit the driver's allocator.  For them this file provides
 // vesis_surface_weights_noalloc: the same three integer passes, with the
 // two intermediate planes placed in a fixed array in device global memory
-// that the library reserves when it is loaded.
+// that a device reserves when it loads the library's module (at the first
+// call on that device under CUDA's default lazy module loading).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,7 +32,8 @@ constexpr long long kNoallocMaxCells = VESIS_NOALLOC_MAX_CELLS;
 constexpr size_t kPlane1Bytes = ((size_t)kNoallocMaxCells * 2 + 255) / 256 * 256;
 constexpr size_t kScratchBytes = kPlane1Bytes + (size_t)kNoallocMaxCells * 4;
 
-// Every GPU that loads the library holds this array until the process exits.
+// Every GPU that loads the library's module holds this array until the
+// process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -44,16 +46,26 @@ int fail(int code, const char *msg)
     return code;
 }
 
-// Device address of the scratch array on the current device, looked up
-// once per device (the name g_noalloc_scratch is only a host-side stand-in
-// and must not be passed to a kernel).
-int scratch_address(unsigned char **out)
+// Device address of the scratch array on the current device (the name
+// g_noalloc_scratch is only a host-side stand-in and must not be passed to
+// a kernel).  Looked up again on every call whose stream is not being
+// captured, so that a module loaded anew (after a device reset, say) is
+// seen; while a capture is in progress the address from the last call on
+// that device is used.
+int scratch_address(cudaStream_t st, unsigned char **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(VESIS_E_CUDA, "cudaGetDevice failed");
     if (dev < 0 || dev >= kMaxDevices) return fail(VESIS_E_ARG, "device index out of range");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess)
+        return fail(VESIS_E_CUDA, "cudaStreamIsCapturing failed");
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
+    if (cs == cudaStreamCaptureStatusNone || g_scratch_addr[dev] == nullptr) {
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(VESIS_E_ARG,
+                        "first call on this device made during a stream capture; "
+                        "call once before capturing");
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr)
@@ -101,15 +113,15 @@ extern "C" int vesis_surface_weights_noalloc(const vesis_params *p, const uint8_
     }
     kw.q[r] = 256 - qsum;
     if (kw.q[r] < 0) return fail(VESIS_E_ARG, "surface kernel weights exceed 256");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
     unsigned char *base = nullptr;
-    const int rc = scratch_address(&base);
+    const int rc = scratch_address(st, &base);
     if (rc != VESIS_OK) return rc;
     GridDesc g{};
     g.nx = p->nx;
     g.ny = p->ny;
     g.nz = p->nz;
     g.h = (float)p->h;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     // both planes are written in full before they are read: nothing in the
     // array has to start at zero
     uint16_t *T1 = reinterpret_cast<uint16_t *>(base);

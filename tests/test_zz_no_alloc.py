@@ -15,15 +15,18 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_noalloc_matches_system_path_on_two_calls():
+@pytest.mark.parametrize("n", [(40, 44, 48),      # z in rows of 8: the vector z pass
+                               (33, 35, 37),      # nz % 8 != 0: the per-cell z pass
+                               (64, 128, 128)])   # exactly VESIS_NOALLOC_MAX_CELLS cells
+def test_noalloc_matches_system_path_on_two_calls(n):
     from paper_2208_05524_gb300 import vesis
-    n = (40, 44, 48)
     h = 0.3
     s = synth.single_ion(n=8, h=h)
     s["n"] = np.array(n)
     s["origin"] = -0.5 * np.array(n) * h
     S = vesis.System(s)
     G = int(np.prod(n))
+    assert G <= vesis.NOALLOC_MAX_CELLS
     for call, seed in enumerate((3, 4)):
         chi0 = synth.random_labels(n, seed=seed, p=0.45)
         chi = torch.from_numpy(chi0.reshape(-1)).cuda()
