@@ -1,10 +1,33 @@
-"""GPU checks of the learned initialiser's kernels against the FP64 oracle
-(oracle/unet.py): logits, loss and the gradient of every layer from the
-same bfloat16 weights and inputs, through the C ABI.  The GPU stores
-activations and the ReLU-masked gradients in bfloat16, so agreement is
-judged on each tensor as a whole: relative L2 error below 5e-2 and cosine
-above 0.998 (a transposed weight, a wrong tap or a missing term gives
-errors of order one)."""
+"""GPU checks of the learned initialiser's kernels against the oracle
+(oracle/unet.py), through the C ABI: logits, loss and the gradient of every
+layer from the same bfloat16 weights and inputs, element by element.
+
+The oracle keeps the tensors the network stores (activations, pooled
+activations, ReLU-masked output gradients) in bfloat16 like the library
+(store=bf16_round) and computes everything else in FP64.  Tolerance, for
+each compared tensor T (the logits, one layer's weight or bias gradient)
+and each element:
+
+  |T_gpu - T_o| <= 2^-4 |T_o| + 2^-6 max|T_o|,
+
+and for the logits also
+
+  |z_gpu - z_o| <= 2^-7 |z_o| + 2^-9 max|z_o|   (one bfloat16 ulp)
+
+for all but 1 % of the cells.  Why no tighter: the GPU accumulates in FP32
+and the oracle in FP64, so a stored value next to a bfloat16 rounding
+boundary can round to the other neighbour (one ulp, 2^-7 relative); the
+next layer sums 27 C_in such values and its own stored values then cross
+boundaries too, so the stored tensors differ by about an ulp in most
+elements after a few layers.  A tensor reached through n stored roundings
+(the logits through the 7 of the forward pass, the input layer's weight
+gradient through those and the 7 masked gradients of the backward pass)
+carries about sqrt(n) ulps, a few times that in its largest elements: the
+bound above is 8 ulps relative plus 2 ulps of the tensor's largest entry,
+about twice the largest difference measured.  A wrong tap, a transposed
+weight, a dropped term or wrong cells at a grid face change the affected
+elements by far more, and a face of any test grid holds more than 1 % of
+its cells.  The loss agrees to relative 1e-4."""
 import numpy as np
 import pytest
 
@@ -41,10 +64,54 @@ def _problem(n, seed, F=3):
     return theta, x, y
 
 
-def _compare(g, go):
-    err = np.linalg.norm(g - go) / max(np.linalg.norm(go), 1e-30)
-    cos = float(np.dot(g, go) / max(np.linalg.norm(g) * np.linalg.norm(go), 1e-30))
-    return err, cos
+BOUND = (2.0 ** -4, 2.0 ** -6)
+ULP = (2.0 ** -7, 2.0 ** -9)
+ULP_SHARE = 1e-2
+
+
+def _elementwise(g, go, what, ulp_share=None):
+    """The element-wise bound above; with ulp_share, also the one-ulp bound
+    for all but that share of the elements."""
+    g = np.asarray(g, np.float64).ravel()
+    go = np.asarray(go, np.float64).ravel()
+    d = np.abs(g - go)
+    m = np.abs(go).max()
+    worst = float((d / np.maximum(BOUND[0] * np.abs(go) + BOUND[1] * m, 1e-300)).max())
+    over = int((d > ULP[0] * np.abs(go) + ULP[1] * m).sum())
+    ok = worst <= 1.0 and (ulp_share is None or over <= ulp_share * g.size)
+    assert ok, (what, worst, over, g.size)
+
+
+def _compare(z, zo, g, go, loss, lo, F, what):
+    _elementwise(z, zo, what + " logits", ULP_SHARE)
+    assert loss == pytest.approx(lo, rel=1e-4), what
+    for name, sl in _layer_slices(F):
+        _elementwise(g[sl], go[sl], what + " " + name)
+
+
+def _oracle(theta, x, y):
+    """Logits (inference) and loss and gradient of the network with its
+    stored tensors in bfloat16."""
+    zo = N.forward(theta, x, store=N.bf16_round)
+    lo, go = N.loss_and_grad(theta, x, y.astype(np.float64), store=N.bf16_round)
+    return zo, lo, go
+
+
+def _gpu(theta, x, y, n, kind="tcgen05", F=3):
+    vs = _vs()
+    net = vs.Net(F)
+    net.set_params(theta)
+    net.set_conv_kernel(kind)
+    xd = _dev(x.reshape(F, -1).astype(np.float32), torch.float32)
+    yd = _dev(y.reshape(-1), torch.uint8)
+    z = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
+    chi = torch.empty(int(np.prod(n)), dtype=torch.uint8, device="cuda")
+    net.forward(xd, n, logits=z, chi=chi)
+    zg = z.cpu().numpy().astype(np.float64)
+    assert np.array_equal(chi.cpu().numpy(), (zg > 0).astype(np.uint8))
+    loss, g = net.loss_grad(xd, yd, n, grad=True)
+    net.close()
+    return zg, loss, g.astype(np.float64)
 
 
 def _layer_slices(F):
@@ -65,22 +132,10 @@ def test_forward_and_gradients_match_oracle():
     assert net.P == N.param_count(3)
     net.set_params(theta)
     assert np.array_equal(net.get_params().astype(np.float64), theta)
-    xd = _dev(x.reshape(3, -1).astype(np.float32), torch.float32)
-    yd = _dev(y.reshape(-1), torch.uint8)
-    z = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
-    chi = torch.empty(int(np.prod(n)), dtype=torch.uint8, device="cuda")
-    net.forward(xd, n, logits=z, chi=chi)
-    zo = N.forward(theta, x)
-    zg = z.cpu().numpy().reshape(n)
-    err, cos = _compare(zg.reshape(-1), zo.reshape(-1))
-    assert err < 5e-2 and cos > 0.998, (err, cos)
-    assert np.array_equal(chi.cpu().numpy().reshape(n), (zg > 0).astype(np.uint8))
-    loss, g = net.loss_grad(xd, yd, n, grad=True)
-    lo, go = N.loss_and_grad(theta, x, y.astype(np.float64))
-    assert loss == pytest.approx(lo, rel=1e-2)
-    for name, sl in _layer_slices(3):
-        err, cos = _compare(g[sl].astype(np.float64), go[sl])
-        assert err < 5e-2 and cos > 0.998, (name, err, cos)
+    net.close()
+    zo, lo, go = _oracle(theta, x, y)
+    z, loss, g = _gpu(theta, x, y, n)
+    _compare(z, zo.reshape(-1), g, go, loss, lo, 3, "16x16x24")
 
 
 def test_crop_reads_the_right_window():
@@ -94,10 +149,10 @@ def test_crop_reads_the_right_window():
     xd = _dev(x.reshape(3, -1).astype(np.float32), torch.float32)
     yd = _dev(y.reshape(-1), torch.uint8)
     loss, g = net.loss_grad(xd, yd, full, crop=crop, grad=True)
-    lo, go = N.loss_and_grad(theta, x[(slice(None),) + sl], y[sl].astype(np.float64))
-    assert loss == pytest.approx(lo, rel=1e-2)
-    err, cos = _compare(g.astype(np.float64), go)
-    assert err < 5e-2 and cos > 0.998, (err, cos)
+    z = torch.empty(16 * 24 * 16, dtype=torch.float32, device="cuda")
+    net.forward(xd, full, crop=crop, logits=z)
+    zo, lo, go = _oracle(theta, x[(slice(None),) + sl], y[sl])
+    _compare(z.cpu().numpy(), zo.reshape(-1), g, go, loss, lo, 3, "crop")
 
 
 def test_training_lowers_the_loss():
@@ -114,6 +169,31 @@ def test_training_lowers_the_loss():
         net.adam_step(lr=2e-3)
     l1 = net.loss_grad(xd, yd, n)
     assert l1 < 0.5 * l0, (l0, l1)
+
+
+def test_training_is_deterministic():
+    """The same training steps twice give bit-identical losses and
+    parameters on both convolution paths: every gradient is summed in a
+    fixed order (per-block partials added in block order, no atomics)."""
+    vs = _vs()
+    n = (32, 32, 32)
+    theta, x, y = _problem(n, 3)
+    xd = _dev(x.reshape(3, -1).astype(np.float32), torch.float32)
+    yd = _dev(y.reshape(-1), torch.uint8)
+    for kind in ("tcgen05", "mma"):
+        runs = []
+        for _ in range(2):
+            net = vs.Net(3)
+            net.set_params(theta)
+            net.set_conv_kernel(kind)
+            losses = []
+            for _ in range(6):
+                losses.append(net.loss_grad(xd, yd, n))
+                net.adam_step(lr=2e-3)
+            runs.append((losses, net.get_params()))
+            net.close()
+        assert runs[0][0] == runs[1][0], kind
+        assert np.array_equal(runs[0][1], runs[1][1]), kind
 
 
 def test_features_match_oracle():
@@ -150,62 +230,45 @@ def test_net_arguments():
         net.set_params(np.full(net.P, np.nan, np.float32))
 
 
-def test_tcgen05_convolutions_match_mma_and_oracle():
-    """The tcgen05 path (grids with ny % 16 == 0 and nz % 8 == 0; the
-    coarser levels here fall back to mma.sync) against the mma.sync path
-    and the oracle: logits, loss and every layer's gradient."""
-    vs = _vs()
+def test_tcgen05_convolutions_match_oracle():
+    """The tcgen05 path on a grid with ny % 16 == 0 and nz % 8 == 0 (one
+    brick per block, k_conv_tc, at full resolution; the coarser levels fall
+    back to mma.sync) and the mma.sync path, each against the oracle."""
     n = (16, 32, 16)
     theta, x, y = _problem(n, 7)
-    xd = _dev(x.reshape(3, -1).astype(np.float32), torch.float32)
-    yd = _dev(y.reshape(-1), torch.uint8)
-    out = {}
+    zo, lo, go = _oracle(theta, x, y)
     for kind in ("mma", "tcgen05"):
-        net = vs.Net(3)
-        net.set_params(theta)
-        net.set_conv_kernel(kind)
-        z = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
-        net.forward(xd, n, logits=z)
-        loss, g = net.loss_grad(xd, yd, n, grad=True)
-        out[kind] = (z.cpu().numpy(), loss, g)
-    zm, zt = out["mma"][0], out["tcgen05"][0]
-    err, cos = _compare(zt.astype(np.float64), zm.astype(np.float64))
-    assert err < 1e-2 and cos > 0.9999, (err, cos)
-    zo = N.forward(theta, x).reshape(-1)
-    err, cos = _compare(zt.astype(np.float64), zo)
-    assert err < 5e-2 and cos > 0.998, (err, cos)
-    lo, go = N.loss_and_grad(theta, x, y.astype(np.float64))
-    assert out["tcgen05"][1] == pytest.approx(lo, rel=1e-2)
-    for name, sl in _layer_slices(3):
-        err, cos = _compare(out["tcgen05"][2][sl].astype(np.float64), go[sl])
-        assert err < 5e-2 and cos > 0.998, (name, err, cos)
+        z, loss, g = _gpu(theta, x, y, n, kind)
+        _compare(z, zo.reshape(-1), g, go, loss, lo, 3, "16x32x16 " + kind)
 
 
-def test_weight_stationary_tcgen05_matches_mma():
-    """A 64^3 grid: its full-resolution levels have enough 16 x 8 bricks for
-    the weight-stationary tcgen05 kernel (8 bricks per block sharing one
-    weight load, accumulators in tensor memory); logits and gradients
-    against the mma.sync path."""
-    vs = _vs()
+def test_tma_convolutions_match_oracle():
+    """32 x 64 x 48 cells: the full-resolution level has 768 bricks of
+    1 x 16 x 8 cells (at least 608), so its convolutions run on the TMA
+    kernel k_conv_tma: e0 with its x taps folded into channels, d0 with the
+    1 x 1 head fused into its epilogue for inference, and both layers' input
+    gradients; the half-resolution level (96 bricks) runs k_conv_tc.
+    Logits of the fused-head inference, loss and every gradient against the
+    oracle."""
+    n = (32, 64, 48)
+    theta, x, y = _problem(n, 21)
+    zo, lo, go = _oracle(theta, x, y)
+    z, loss, g = _gpu(theta, x, y, n)
+    _compare(z, zo.reshape(-1), g, go, loss, lo, 3, "32x64x48")
+
+
+def test_weight_stationary_tcgen05_matches_oracle_and_mma():
+    """A 64^3 grid: the TMA kernel at full resolution, k_conv_tc at half
+    resolution (256 bricks).  Against the oracle; and, as an extra, against
+    the mma.sync path with the same element-wise tolerance."""
     n = (64, 64, 64)
     theta, x, y = _problem(n, 9)
-    xd = _dev(x.reshape(3, -1).astype(np.float32), torch.float32)
-    yd = _dev(y.reshape(-1), torch.uint8)
-    out = {}
-    for kind in ("mma", "tcgen05"):
-        net = vs.Net(3)
-        net.set_params(theta)
-        net.set_conv_kernel(kind)
-        z = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
-        net.forward(xd, n, logits=z)
-        loss, g = net.loss_grad(xd, yd, n, grad=True)
-        out[kind] = (z.cpu().numpy().astype(np.float64), loss, g.astype(np.float64))
-    err, cos = _compare(out["tcgen05"][0], out["mma"][0])
-    assert err < 1e-2 and cos > 0.9999, (err, cos)
-    assert out["tcgen05"][1] == pytest.approx(out["mma"][1], rel=1e-3)
-    for name, sl in _layer_slices(3):
-        err, cos = _compare(out["tcgen05"][2][sl], out["mma"][2][sl])
-        assert err < 2e-2 and cos > 0.9998, (name, err, cos)
+    zo, lo, go = _oracle(theta, x, y)
+    out = {kind: _gpu(theta, x, y, n, kind) for kind in ("tcgen05", "mma")}
+    z, loss, g = out["tcgen05"]
+    _compare(z, zo.reshape(-1), g, go, loss, lo, 3, "64^3 tcgen05")
+    zm, lm, gm = out["mma"]
+    _compare(z, zm, g, gm, loss, lm, 3, "64^3 tcgen05 vs mma")
 
 
 def test_wide_input_without_folding_matches_oracle():
@@ -213,25 +276,11 @@ def test_wide_input_without_folding_matches_oracle():
     channels (9 of its 32); with 12 features that no longer fits and the
     layer keeps its 27 taps.  Logits, loss and every layer's gradient of the
     12-feature network against the oracle, on both convolution paths."""
-    vs = _vs()
     n = (16, 32, 16)
     F = 12
     theta, x, y = _problem(n, 11, F=F)
-    xd = _dev(x.reshape(F, -1).astype(np.float32), torch.float32)
-    yd = _dev(y.reshape(-1), torch.uint8)
-    zo = N.forward(theta, x).reshape(-1)
-    lo, go = N.loss_and_grad(theta, x, y.astype(np.float64))
+    assert _vs().Net(F).P == N.param_count(F)
+    zo, lo, go = _oracle(theta, x, y)
     for kind in ("mma", "tcgen05"):
-        net = vs.Net(F)
-        assert net.P == N.param_count(F)
-        net.set_params(theta)
-        net.set_conv_kernel(kind)
-        z = torch.empty(int(np.prod(n)), dtype=torch.float32, device="cuda")
-        net.forward(xd, n, logits=z)
-        err, cos = _compare(z.cpu().numpy().astype(np.float64), zo)
-        assert err < 5e-2 and cos > 0.998, (kind, err, cos)
-        loss, g = net.loss_grad(xd, yd, n, grad=True)
-        assert loss == pytest.approx(lo, rel=1e-2)
-        for name, sl in _layer_slices(F):
-            err, cos = _compare(g[sl].astype(np.float64), go[sl])
-            assert err < 5e-2 and cos > 0.998, (kind, name, err, cos)
+        z, loss, g = _gpu(theta, x, y, n, kind, F=F)
+        _compare(z, zo.reshape(-1), g, go, loss, lo, F, "F=12 " + kind)
