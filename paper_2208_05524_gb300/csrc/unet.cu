@@ -893,10 +893,12 @@ __global__ void k_pack_tc(const bf16 *__restrict__ W, int Cout, int Cin, int NT,
     out[((((long long)(st * nnt + nt) * 4 + kc) * 27 + tap) * NT + col) * 8 + j] = W[e];
 }
 
-// Weight gradient of a conv3: dW[tap][co][ci] += sum over cells v of
+// Weight gradient of a conv3: dW[tap][co][ci] = sum over cells v of
 // dZ[v][co] X[v + tap][ci] (X the concatenated input).  M = co (64 per
 // block), N = ci (32 per block), K = cells in stages of 32, split over
-// blocks of WG_CELLS cells and summed with atomics.
+// chunks of cells_per_block cells; each chunk writes its own partial
+// dW (part[chunk][tap][co][ci]) and k_sum_parts adds the chunks in order,
+// so the result does not depend on the order the blocks run in.
 struct WgradArgs {
     int nx, ny, nz;
     long long V;
@@ -906,7 +908,7 @@ struct WgradArgs {
     int Cb;
     const bf16 *dZ;      // [V][Cout]
     int Cout;
-    float *dW;           // [27][Cout][Cin]
+    float *part;         // [chunks][27][Cout][Cin]
     long long cells_per_block;
 };
 
@@ -1008,11 +1010,23 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs P)
 #pragma unroll
         for (int n = 0; n < 4; ++n) {
             const int ci = ci0 + n * 8 + 2 * tq;
-            float *d = P.dW + ((long long)tap * P.Cout + co) * Cin + ci;
-            atomicAdd(d, acc[n][2 * hh]);
-            atomicAdd(d + 1, acc[n][2 * hh + 1]);
+            float *d = P.part + (((long long)blockIdx.x * 27 + tap) * P.Cout + co) * Cin + ci;
+            d[0] = acc[n][2 * hh];
+            d[1] = acc[n][2 * hh + 1];
         }
     }
+}
+
+// out[i] = sum over b = 0, 1, ... of part[b][i], in that order (n entries
+// per part): the fixed-order reduction of per-block partial gradients.
+__global__ void k_sum_parts(const float *__restrict__ part, int nparts, long long n,
+                            float *__restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int b = 0; b < nparts; ++b) s += part[(long long)b * n + i];
+    out[i] = s;
 }
 
 // ------------------------------------------------------------ small kernels
@@ -1133,12 +1147,13 @@ __global__ void __launch_bounds__(256) k_head(const bf16 *__restrict__ D0, long 
     }
 }
 
-// Head backward: g0[v][c] = Wh[c] dz[v] (FP32), dWh[c] += sum_v d0[v][c] dz[v],
-// dbh += sum_v dz[v].
+// Head backward: g0[v][c] = Wh[c] dz[v] (FP32); the block's sums of
+// d0[v][c] dz[v] (c < 32) and of dz[v] (entry 32) go to part[block][33]
+// (summed over blocks in order afterwards into dWh and dbh).
 __global__ void __launch_bounds__(256) k_head_bwd(const bf16 *__restrict__ D0, long long V,
                                                   const float *__restrict__ Wh,
                                                   const float *__restrict__ dz,
-                                                  float *__restrict__ g0, float *__restrict__ dWh)
+                                                  float *__restrict__ g0, float *__restrict__ part)
 {
     __shared__ float s_w[33][8];
     const long long v = (long long)blockIdx.x * 256 + threadIdx.x;
@@ -1164,29 +1179,36 @@ __global__ void __launch_bounds__(256) k_head_bwd(const bf16 *__restrict__ D0, l
     if (threadIdx.x < 33) {
         float s = 0.f;
         for (int q = 0; q < 8; ++q) s += s_w[threadIdx.x][q];
-        atomicAdd(dWh + threadIdx.x, s);
+        part[(long long)blockIdx.x * 33 + threadIdx.x] = s;
     }
 }
 
-// dZ = bf16(g * [y > 0]) for a relu layer's output y; db[c] += sum_v dZ.
+// dZ = bf16(g * [y > 0]) for a relu layer's output y; the block's sums of
+// dZ per channel go to part[block][C] (summed over blocks in order
+// afterwards into db).  C divides 256, so thread t only ever sees channel
+// t % C: it sums its elements in order, then the threads of a channel are
+// added in thread order.
 __global__ void __launch_bounds__(256) k_relu_bwd(const float *__restrict__ gsum,
                                                   const bf16 *__restrict__ y, long long V, int C,
-                                                  bf16 *__restrict__ dZ, float *__restrict__ db)
+                                                  bf16 *__restrict__ dZ, float *__restrict__ part)
 {
-    // each block covers 256 / C cells x C channels per pass
-    extern __shared__ float s_db[];
-    for (int c = threadIdx.x; c < C; c += 256) s_db[c] = 0.f;
-    __syncthreads();
+    __shared__ float s_db[256];
     const long long n = V * C;
+    float acc = 0.f;
     for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < n;
          e += (long long)gridDim.x * 256) {
         const float yv = __bfloat162float(y[e]);
         const bf16 d = __float2bfloat16(yv > 0.f ? gsum[e] : 0.f);
         dZ[e] = d;
-        atomicAdd(&s_db[(int)(e % C)], __bfloat162float(d));
+        acc += __bfloat162float(d);
     }
+    s_db[threadIdx.x] = acc;
     __syncthreads();
-    for (int c = threadIdx.x; c < C; c += 256) atomicAdd(db + c, s_db[c]);
+    if (threadIdx.x < C) {
+        float t = 0.f;
+        for (int k = threadIdx.x; k < 256; k += C) t += s_db[k];
+        part[(long long)blockIdx.x * C + threadIdx.x] = t;
+    }
 }
 
 // From the input gradient dX [v][Ca + Cb] (FP32) of a decoder conv: the
@@ -1404,6 +1426,8 @@ struct vesis_net_t {
     double *loss_part = nullptr;
     float *ge[4] = {}, *gd[3] = {}, *dX = nullptr;
     bf16 *dZ = nullptr;
+    float *part = nullptr;        // per-block partial gradients, summed in order
+    long long part_cap = 0;       // floats
     double *h_loss = nullptr;
     int conv_kind = 1;            // 0 mma.sync, 1 tcgen05 where the shape allows
     bf16 *up = nullptr;           // a decoder's coarse input doubled to its resolution
@@ -1489,6 +1513,14 @@ int ensure_act(vesis_net n, int nx, int ny, int nz, bool train)
         mx = std::max(mx, V2 * 256);
         NTRY(nalloc(A, &n->dX, mx));
         NTRY(nalloc(A, &n->dZ, V0 * 32 > V2 * 128 ? V0 * 32 : V2 * 128));
+        // partial gradients: the weight gradient's chunks (at most 608 + 27 x
+        // 8 x 2 blocks of 64 x 32 entries), the ReLU layers' 608 x 128 and
+        // the head's blocks x 33
+        long long pc = (608ll + 27 * 8 * 2) * 64 * 32;
+        pc = std::max(pc, 608ll * 128);
+        pc = std::max(pc, (V0 + 255) / 256 * 33);
+        NTRY(nalloc(A, &n->part, pc));
+        n->part_cap = pc;
     }
     n->nx = nx;
     n->ny = ny;
@@ -1616,6 +1648,7 @@ bool conv(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16
 void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf16 *B, int Cb,
            const bf16 *dZ, int Cout, float *dW)
 {
+    // chunk partials in n->part, then one ordered sum into dW
     WgradArgs a;
     a.nx = nx;
     a.ny = ny;
@@ -1627,7 +1660,7 @@ void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf1
     a.Cb = Cb;
     a.dZ = dZ;
     a.Cout = Cout;
-    a.dW = dW;
+    a.part = n->part;
     const int Cin = Ca + Cb;
     const long long tiles = 27ll * (Cin / 32) * ((Cout + 63) / 64);
     // about four blocks per SM in all, in multiples of 32 cells
@@ -1637,8 +1670,10 @@ void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf1
     a.cells_per_block = cpb;
     chunks = (a.V + cpb - 1) / cpb;
     dim3 grid((unsigned)chunks, (unsigned)(27 * (Cin / 32)), (unsigned)((Cout + 63) / 64));
-    count_launch();
+    const long long nw = 27ll * Cout * Cin;
+    count_launch(2);
     k_wgrad<<<grid, 128, 0, n->st>>>(a);
+    k_sum_parts<<<nblk(nw), 256, 0, n->st>>>(n->part, (int)chunks, nw, dW);
 }
 
 // Forward pass of a crop; with labels, the loss partials and dz too.
@@ -1902,11 +1937,14 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
     // head
     count_launch();
     k_head_bwd<<<nblk(V[0]), 256, 0, st>>>(n->d[0], V[0], n->theta + L[L_HEAD].w_off, n->dz,
-                                           n->gd[0], n->grad + L[L_HEAD].w_off);
+                                           n->gd[0], n->part);
+    count_launch();
+    k_sum_parts<<<1, 64, 0, st>>>(n->part, (int)nblk(V[0]), 33, n->grad + L[L_HEAD].w_off);
     auto relu_bwd = [&](const float *g, const bf16 *y, long long Vl, int C, float *db) {
-        count_launch();
+        count_launch(2);
         const long long nb = std::min<long long>(nblk(Vl * C), 4 * 152);
-        k_relu_bwd<<<(unsigned)nb, 256, C * sizeof(float), st>>>(g, y, Vl, C, n->dZ, db);
+        k_relu_bwd<<<(unsigned)nb, 256, 0, st>>>(g, y, Vl, C, n->dZ, n->part);
+        k_sum_parts<<<1, 128, 0, st>>>(n->part, (int)nb, C, db);
     };
     auto unpack = [&](int l) {
         Layer &y = L[l];
