@@ -608,6 +608,124 @@ def run_batch(args, world, rank, local):
         S.close()
 
 
+def run_converge_set(args, world, rank, local):
+    """Seconds per converged VESIS relaxation (Steps 1-5 with the paper's
+    stopping tests of Steps 3.2 and 5 and k_max = 3,000) on a set of small
+    protein-like solutes (synth.small_protein, seed 5), three ways:
+    (i) the plain GPU form: vesis_relax of one solute after another from the
+    tight start; (ii) the batched form from the same starts
+    (vesis_relax_batch; identical results per solute); (iii) the learned
+    start + batched form: a network trained by the library on plain
+    relaxations of solutes of the same set generator (seed 6) guesses every
+    solute's relaxed labels, and the batch relaxes from the guesses.
+    Prints one JSON line of its own: seconds per relaxation of each form,
+    the ratio of (i) to (iii), and the final energies' largest relative
+    difference between (i) and (iii)."""
+    import numpy as np
+    import torch
+
+    from paper_2208_05524_gb300 import learned, synth, vesis
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.set_systems
+    opts = dict(max_outer=args.max_outer) if args.max_outer else {}
+    sysds = [synth.small_protein(i, seed=5) for i in range(n)]
+    systems, chis0 = [], []
+    for sd in sysds:
+        S = vesis.System(sd, stream=torch.cuda.Stream(device=dev))
+        c = torch.empty(S.G, dtype=torch.uint8, device=dev)
+        S.init_labels(c, "tight")
+        systems.append(S)
+        chis0.append(c)
+    xyzs = [np.ascontiguousarray(sd["xyz"]) for sd in sysds]
+    torch.cuda.synchronize()
+    # warm-up: one outer iteration of one solute, alone and batched
+    c = chis0[0].clone()
+    systems[0].relax(c, xyzs[0], max_outer=1)
+    vesis.relax_batch([systems[0]], [c], [xyzs[0]], max_outer=1)
+    torch.cuda.synchronize()
+    # (i) plain GPU form
+    chis = [c0.clone() for c0 in chis0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [S.relax(c, x, **opts) for S, c, x in zip(systems, chis, xyzs)]
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_chi = [c.clone() for c in chis]
+    # (ii) batched, tight start
+    chis = [c0.clone() for c0 in chis0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bat = vesis.relax_batch(systems, chis, xyzs, threads=args.batch_threads,
+                            sweep_slots=args.sweep_slots, **opts)
+    torch.cuda.synchronize()
+    bat_s = time.perf_counter() - t0
+    same = all(torch.equal(a, b) for a, b in zip(chis, plain_chi)) and \
+        all(a["G"] == b["G"] for a, b in zip(plain, bat))
+    # (iii) learned start + batched: train, guess, relax
+    t0 = time.perf_counter()
+    bank = learned.crop_bank((synth.small_protein(i, seed=6) for i in range(args.set_fields)),
+                             args.set_fields, 6, crop=64)
+    net = vesis.Net(3)
+    learned.init_params(net, seed=0)
+    losses = learned.train_bank(net, bank, args.set_steps, lr=1e-3, seed=1)
+    del bank
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    feats = []
+    for S in systems:
+        U = torch.empty(S.G, dtype=torch.float32, device=dev)
+        E = torch.empty(3 * S.G, dtype=torch.float32, device=dev)
+        ct = torch.empty(S.G, dtype=torch.uint8, device=dev)
+        x = torch.empty(3 * S.G, dtype=torch.float32, device=dev)
+        feats.append((U, E, ct, x))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for S, (U, E, ct, x) in zip(systems, feats):
+        S.energy_field(U, E)
+        S.init_labels(ct, "tight")
+        S.features(U, E, ct, x, scale=learned.FEATURE_SCALE)
+    torch.cuda.synchronize()     # features come from the solutes' own streams
+    chis = [learned.guess(net, x, S.shape) for S, (_, _, _, x) in zip(systems, feats)]
+    torch.cuda.synchronize()
+    lrn = vesis.relax_batch(systems, chis, xyzs, threads=args.batch_threads,
+                            sweep_slots=args.sweep_slots, **opts)
+    torch.cuda.synchronize()
+    lrn_s = time.perf_counter() - t0
+    dG = max(abs(a["G"] - b["G"]) / abs(a["G"]) for a, b in zip(plain, lrn))
+    stops = {}
+    for r in plain:
+        k = {0: "gradient test", 1: "energy test", 2: "k_max", 3: "shrink cap"}[r["stop_reason"]]
+        stops[k] = stops.get(k, 0) + 1
+    out = {"metric": "sec per converged VESIS relaxation, learned start + batched vs plain GPU form",
+           "value": lrn_s / n, "unit": "s", "higher_is_better": False, "n_gpus": world,
+           "data": "synthetic", "dtype": "f32 fields, f64 totals",
+           "config": {"workload": f"small_protein{n}_h0.4",
+                      "desc": f"{n} protein-like solutes of 60-400 atoms (log-uniform, seed 5), "
+                              "80-112^3 grids at h=0.4 A, tight start; stopping tests of "
+                              "Steps 3.2 and 5, k_max 3000",
+                      "threads": args.batch_threads, "sweep_slots": args.sweep_slots},
+           "plain_s_per_relaxation": plain_s / n,
+           "batched_s_per_relaxation": bat_s / n,
+           "learned_batched_s_per_relaxation": lrn_s / n,
+           "speedup_batched": plain_s / bat_s,
+           "speedup_learned_batched": plain_s / lrn_s,
+           "batched_identical_to_plain": bool(same),
+           "max_rel_G_difference_learned": dG,
+           "plain_stop_reasons": stops,
+           "iterations": sorted(r["iterations"] for r in plain),
+           "flip_rounds_plain": int(sum(r["flip_rounds"] for r in plain)),
+           "flip_rounds_learned": int(sum(r["flip_rounds"] for r in lrn)),
+           "training": {"fields": args.set_fields, "steps": args.set_steps, "seconds": train_s,
+                        "loss_last100": float(np.mean(losses[-100:]))}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    for S in systems:
+        S.close()
+    net.close()
+
+
 def run_heap(args, world, rank, local):
     """The paper's literal serial flipping (vesis_blsm_heap) on the single
     ion (64^3, h = 0.25 A, from the 7 A sphere to the local minimum, U from
@@ -687,12 +805,19 @@ def run_heap(args, world, rank, local):
 
 def run_learned(args, world, rank, local):
     """The learned initialiser on the 20,000-atom two-domain complex (384^3,
-    h = 0.4 A): a network trained by the library's kernels on label fields
-    the flip sweep relaxed from tight starts (host-guest systems at the same
-    spacing, seed 3) guesses the complex's relaxed labels; the unchanged
-    sweep finishes from the guess.  Reports the sweep from the tight start
-    against guess + sweep: rounds, flips, seconds, label mismatches and the
-    final energies.  Prints one JSON line of its own."""
+    h = 0.4 A).  Training data: --learn-fields plain relaxations in the style
+    of the protein-like workload (random-walk solutes of 500-4,000 atoms,
+    log-uniform, on 256^3 at h = 0.4 A, seeded per solute), each relaxed by
+    the flip sweep from its tight start at fixed atoms, one 64^3 crop of
+    features and relaxed labels kept per solute.  The network is trained
+    twice from the same start, bank and seed (the two must agree bit for
+    bit), then guesses the complex's relaxed labels and the unchanged sweep
+    finishes from the guess.  Reports the sweep from the tight start against
+    guess + sweep: rounds, flips, seconds, label mismatches and the final
+    energies.  Prints one JSON line of its own."""
+    import functools
+    import multiprocessing as mp
+
     import numpy as np
     import torch
 
@@ -711,16 +836,27 @@ def run_learned(args, world, rank, local):
         return a.elapsed_time(b) * 1e-3, r
 
     t0 = time.perf_counter()
-    train_set = [learned.example(synth.host_guest(i, seed=3, h=0.4))
-                 for i in range(args.learn_systems)]
+    nf = args.learn_fields
+    gen = functools.partial(learned.protein_field, seed=args.learn_seed)
+    workers = max(1, (os.cpu_count() or 2) - 1)
+    with mp.get_context("spawn").Pool(workers) as pool:
+        bank = learned.crop_bank(pool.imap(gen, range(nf), chunksize=4), nf,
+                                 args.learn_seed, crop=64)
     data_s = time.perf_counter() - t0
-    net = vesis.Net(3)
-    net.set_conv_kernel(args.conv_kernel)
-    learned.init_params(net, seed=0)
-    train_s, losses = timed(lambda: learned.train(net, train_set, steps=args.learn_steps,
-                                                  crop=64, lr=1e-3, seed=1))
+    runs = []
+    for _ in range(2):
+        net = vesis.Net(3)
+        net.set_conv_kernel(args.conv_kernel)
+        learned.init_params(net, seed=0)
+        train_s, losses = timed(lambda: learned.train_bank(net, bank, args.learn_steps,
+                                                           lr=1e-3, seed=1))
+        runs.append((net, losses, train_s))
+    net, losses, train_s = runs[0]
+    reproducible = bool(runs[0][1] == runs[1][1] and
+                        np.array_equal(runs[0][0].get_params(), runs[1][0].get_params()))
+    runs[1][0].close()
     cells_trained = args.learn_steps * 64 ** 3
-    del train_set
+    del bank
     target = synth.two_domain_complex() if args.learn_target == "complex" else \
         synth.protein_like(n_atoms=500, n=128, h=0.4, seed=4)
     cx = learned.example(target, keep_system=True)
@@ -737,8 +873,7 @@ def run_learned(args, world, rank, local):
            "n_gpus": world, "data": "synthetic", "dtype": "bf16 net, f32 fields",
            "config": ({"workload": "two_domain_complex_20000_grid384",
                        "desc": "two 10,000-atom random-walk globules 6 A apart, 384^3 grid, "
-                               "h=0.4 A, seed 2; net trained on host-guest systems "
-                               "(seed 3, h=0.4 A)"}
+                               "h=0.4 A, seed 2"}
                       if args.learn_target == "complex" else
                       {"workload": "protein500_grid128",
                        "desc": "500-atom protein-like solute, 128^3 grid, h=0.4 A, seed 4 "
@@ -749,11 +884,16 @@ def run_learned(args, world, rank, local):
                              "flips": rg["flips"], "G": rg["terms"]["total"],
                              "label_mismatches_of_guess": miss_guess,
                              "final_label_mismatches": int((chi_g != chi_cold).sum())},
-           "training": {"systems": args.learn_systems, "steps": args.learn_steps,
-                        "crop": 64, "seconds": train_s, "data_seconds": data_s,
-                        "loss_first20": float(np.mean(losses[:20])),
-                        "loss_last20": float(np.mean(losses[-20:])),
-                        "cells_per_s": cells_trained / train_s}}
+           "training": {"fields": nf, "seed": args.learn_seed,
+                        "fields_desc": "protein-like random-walk solutes, 500-4,000 atoms "
+                                       "log-uniform, 256^3 at h=0.4 A, relaxed by the flip "
+                                       "sweep from the tight start; one 64^3 crop each",
+                        "steps": args.learn_steps, "crop": 64, "seconds": train_s,
+                        "data_seconds": data_s, "data_workers": workers,
+                        "loss_first100": float(np.mean(losses[:100])),
+                        "loss_last100": float(np.mean(losses[-100:])),
+                        "cells_per_s": cells_trained / train_s,
+                        "reproducible": reproducible}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     S.close()
@@ -834,8 +974,10 @@ def main():
                     help="potential of mean force of two atoms, both branches")
     ap.add_argument("--learned", action="store_true",
                     help="train the learned initialiser and apply it to the two-domain complex")
-    ap.add_argument("--learn-systems", type=int, default=24)
-    ap.add_argument("--learn-steps", type=int, default=600)
+    ap.add_argument("--learn-fields", type=int, default=5000,
+                    help="plain relaxations the learned initialiser is trained on")
+    ap.add_argument("--learn-seed", type=int, default=3)
+    ap.add_argument("--learn-steps", type=int, default=4000)
     ap.add_argument("--learn-target", default="complex", choices=["complex", "protein128"])
     ap.add_argument("--conv-kernel", default="tcgen05", choices=["tcgen05", "mma"])
     ap.add_argument("--heap", action="store_true",
@@ -843,6 +985,12 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="time the batched form on the host-guest set against the plain form")
     ap.add_argument("--batch-systems", type=int, default=64)
+    ap.add_argument("--converge-set", action="store_true",
+                    help="seconds per converged relaxation of a set of small solutes: plain, "
+                         "batched, learned start + batched")
+    ap.add_argument("--set-systems", type=int, default=16)
+    ap.add_argument("--set-fields", type=int, default=200)
+    ap.add_argument("--set-steps", type=int, default=1500)
     ap.add_argument("--batch-threads", type=int, default=8)
     ap.add_argument("--sweep-slots", type=int, default=2)
     args = ap.parse_args()
@@ -855,6 +1003,8 @@ def main():
         run_heap(args, world, rank, local)
     elif args.batch:
         run_batch(args, world, rank, local)
+    elif args.converge_set:
+        run_converge_set(args, world, rank, local)
     elif args.converge:
         run_converge(args, world, rank, local)
     elif args.impl == "reference":

@@ -82,6 +82,67 @@ def train(net, examples, steps, crop=64, lr=1e-3, seed=0, log_every=0):
     return losses
 
 
+def protein_field(index, seed, atoms=(500, 4000), n=256, h=0.4):
+    """The `index`-th training solute of a seeded set in the style of the
+    protein-like workload: a random-walk globule whose atom count is drawn
+    log-uniform in `atoms`, with that workload's parameter distributions,
+    on an n^3 grid at spacing h.  Each solute has its own seed, drawn from
+    the set's seed, so any one of them can be rebuilt alone."""
+    from . import synth
+    rng = np.random.default_rng([seed, index])
+    na = int(round(np.exp(rng.uniform(np.log(atoms[0]), np.log(atoms[1])))))
+    return synth.protein_like(n_atoms=na, n=n, h=h, seed=int(rng.integers(1 << 31)))
+
+
+def crop_bank(systems, n_fields, seed, crop=64, stream=None, log_every=0):
+    """Training crops from plain relaxations: for each of the n_fields
+    solutes that `systems` yields (protein_field(i, seed) for i = 0, 1, ...,
+    built here or by worker processes), the tight start relaxed by the flip
+    sweep at fixed atoms (the plain method), and one crop^3 window of its
+    features and relaxed labels, centred on a randomly chosen atom (so that
+    it holds solute, interface and solvent) and kept inside the grid on the
+    8-cell lattice.  Returns the crops as device tensors x
+    [n_fields][3][crop^3] and chi [n_fields][crop^3], with the sweeps'
+    rounds and flips."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    V = crop ** 3
+    X = torch.empty((n_fields, 3, V), dtype=torch.float32, device=dev)
+    Y = torch.empty((n_fields, V), dtype=torch.uint8, device=dev)
+    rounds = flips = 0
+    for i, sd in zip(range(n_fields), systems):
+        e = example(sd, stream=stream)
+        rng = np.random.default_rng([seed, i, 1])
+        a = sd["xyz"][int(rng.integers(len(sd["xyz"])))]
+        cell = np.floor((a - np.asarray(sd["origin"])) / sd["h"]).astype(int)
+        o = [int(np.clip((c - crop // 2) // 8 * 8, 0, d - crop))
+             for c, d in zip(cell, e["shape"])]
+        sl = tuple(slice(oo, oo + crop) for oo in o)
+        nx, ny, nz = e["shape"]
+        X[i] = e["x"].view(3, nx, ny, nz)[(slice(None),) + sl].reshape(3, V)
+        Y[i] = e["chi"].view(nx, ny, nz)[sl].reshape(V)
+        rounds += e["rounds"]
+        flips += e["flips"]
+        del e
+        if log_every and (i + 1) % log_every == 0:
+            print(f"field {i + 1}/{n_fields}", flush=True)
+    return dict(x=X, chi=Y, crop=crop, rounds=rounds, flips=flips)
+
+
+def train_bank(net, bank, steps, lr=1e-3, seed=0):
+    """Adam, one crop of the bank per step, drawn with a seeded generator;
+    returns the losses.  Every gradient is summed in a fixed order, so the
+    same bank, seed and start give the same parameters."""
+    rng = np.random.default_rng(seed)
+    c = bank["crop"]
+    losses = []
+    for _ in range(steps):
+        i = int(rng.integers(bank["x"].shape[0]))
+        losses.append(net.loss_grad(bank["x"][i], bank["chi"][i], (c, c, c)))
+        net.adam_step(lr=lr)
+    return losses
+
+
 def guess(net, x, shape):
     """The network's labels chi = [logit > 0] of a whole grid (dimensions
     multiples of 8)."""

@@ -236,6 +236,22 @@ def protein_like(n_atoms: int = 2000, n: int = 256, h: float = 0.4,
                    (bonds, np.full(len(bonds), 800.0), r0))
 
 
+def small_protein(index: int, seed: int = 5, atoms=(60, 400), h: float = 0.4,
+                  margin: float = 8.0):
+    """The `index`-th solute of a seeded set of small protein-like solutes
+    (the many-solute service the batched form is for): atom count
+    log-uniform in `atoms`, the protein-like parameter distributions, and
+    the smallest cubic grid at spacing h whose side is a multiple of 16
+    cells and holds every atom `margin` A inside the box."""
+    rng = np.random.default_rng([seed, index])
+    na = int(round(np.exp(rng.uniform(np.log(atoms[0]), np.log(atoms[1])))))
+    s = int(rng.integers(1 << 31))
+    sd = protein_like(n_atoms=na, n=16, h=h, seed=s)
+    ext = float(np.abs(sd["xyz"]).max()) + margin
+    n = 16 * int(math.ceil(2.0 * ext / (16.0 * h)))
+    return protein_like(n_atoms=na, n=n, h=h, seed=s)
+
+
 def two_domain_complex(n_per: int = 10000, n: int = 384, h: float = 0.4,
                        seed: int = 2, gap: float = 6.0,
                        temperature: float = 298.0):
