@@ -89,7 +89,25 @@ typedef struct {
     double tol_energy;    /* Tol2: abs or rel energy change (Step 5) */
     int max_flip_rounds;  /* cap on flip rounds per interface relaxation */
     int max_gd_retries;   /* cap on consecutive shrinks of M (Step 3.4) */
+    int resume;           /* 0: start afresh (k = 0, M = M0, N_cnt = 0);
+                             1: continue from the system's relaxation state
+                             (vesis_get_state / vesis_set_state), with
+                             max_outer the cap on the total k */
 } vesis_relax_opts;
+
+/* Where a relaxation stands between two outer iterations (Sec. 3.3): with
+ * the labels and positions it ended at, enough to continue it exactly as
+ * if it had not stopped.  Plain data: save it beside chi and xyz to
+ * checkpoint a relaxation, load it into any system of the same solute to
+ * resume. */
+typedef struct {
+    int k;            /* accepted outer iterations so far */
+    int ncnt;         /* N_cnt, accepted steps since M last shrank (Step 3.4) */
+    int stable;       /* consecutive steps the energy test of Step 5 has held */
+    int valid;        /* 1 once a relaxation has ended normally or by a cap */
+    double M;         /* the mobility factor M (Eq. adjustmml) */
+    double G_prev;    /* total G at the last accepted iterate (Steps 4-5) */
+} vesis_relax_state;
 
 /* Per-run report of vesis_relax. */
 typedef struct {
@@ -208,6 +226,32 @@ int vesis_blsm_relax(vesis_system s, uint8_t *chi_dev, const float *U_dev,
                      long long *flips_out, double *dE_sum_out,
                      double *terms_out);
 
+/* vesis_blsm_relax of many systems in one persistent launch: the flip
+ * rounds of every system run in the same cooperative kernel, whose blocks
+ * serve the 8^3 tiles of all systems round-robin, with one grid barrier
+ * per phase for all of them.  Each system goes through exactly the rounds
+ * it would go through alone (same labels, rounds and flips; the FP64 sum of
+ * its flipped dE is added in another fixed order, so it may differ from
+ * vesis_blsm_relax's in the last bits), and its W is left as the exact
+ * convolution of its relaxed labels.  The paper relaxes one solute at a
+ * time (Sec. 3.3); this serves many solutes, for example the plain
+ * relaxations a learned initialiser is trained on.
+ *   nsys       1..64 distinct systems on one device with the same surface
+ *              kernel (kind, half-width and weights; for the sin^2 kernel
+ *              the same h and lambda)
+ *   chi_dev[i] system i's labels, relaxed in place; U_dev[i] its energy
+ *              density (vesis_energy_field)
+ *   max_rounds > 0, the cap on the rounds of the launch
+ * Outputs (each may be NULL, else nsys entries): each system's rounds with
+ * flips, flipped cells and FP64 sum of their dE.  Every system's stream is
+ * waited for; the work runs on systems[0]'s stream, and the call returns
+ * when it is done.  Returns VESIS_W_MAX_ROUNDS if the cap stopped any
+ * system.  Device scratch for the launch (about 300 bytes per system) is
+ * allocated and freed by the call. */
+int vesis_blsm_relax_batch(int nsys, vesis_system *systems, uint8_t *const *chi_dev,
+                           const float *const *U_dev, int max_rounds, int *rounds_out,
+                           long long *flips_out, double *dE_sum_out);
+
 /* The paper's literal serial flipping (Sec. 3.1, Steps 2.1-2.2) on the
  * GPU: of the cells next to the interface (a face neighbour with the other
  * label) with dE < 0, flip the one with the smallest dE (ties: smaller
@@ -261,6 +305,14 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
  * first poll that finds the barrier still open, which makes the failure
  * path testable without any fault.  VESIS_E_ARG for polls < 0. */
 int vesis_set_wait_limit(vesis_system s, long long polls);
+
+/* The system's relaxation state: written by every vesis_relax that ends
+ * with status >= 0 (cleared to valid = 0 by one that fails), read by
+ * vesis_relax with opts.resume = 1.  set checks that k, ncnt and stable
+ * are >= 0 and M, G_prev finite with M > 0 (VESIS_E_ARG otherwise); a
+ * state with valid = 0 is stored as given and makes a resume fail. */
+int vesis_get_state(vesis_system s, vesis_relax_state *out);
+int vesis_set_state(vesis_system s, const vesis_relax_state *st);
 
 /* Tile shapes of the two pair kernels: cells of a z-pencil per thread of
  * the energy-density kernel (4, 8 or 16, default 8) and atoms per thread of the

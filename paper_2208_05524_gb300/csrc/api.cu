@@ -98,10 +98,10 @@ __global__ void k_gd_decide(GdState *s, const double *bank_old,
     s->dG = dG;
 }
 
-__global__ void k_gd_init(GdState *s, double M0)
+__global__ void k_gd_init(GdState *s, double M0, int ncnt0)
 {
     s->M = M0;
-    s->ncnt = 0;
+    s->ncnt = ncnt0;
     s->decision = 0;
     s->dG = 0.0;
 }
@@ -239,10 +239,13 @@ struct vesis_system_t {
     unsigned long long *d_part_flips = nullptr;
     double *d_part_dE = nullptr;
     unsigned long long *d_part_tiles = nullptr;
+    double *d_tile_dE = nullptr;      // multi-system sweep: per-tile dE sums
+    unsigned *d_tile_nf = nullptr;    // and flip counts
 
     double *d_scal = nullptr;   // two banks of S_BANK doubles
     RoundState *d_rs = nullptr;
     GdState *d_gd = nullptr;
+    vesis_relax_state rstate{};   // where the last relaxation stopped
 
     // pinned host mirrors
     double *h_scal = nullptr;
@@ -596,6 +599,7 @@ void vesis_default_relax_opts(vesis_relax_opts *o)
     o->tol_energy = 1e-5;
     o->max_flip_rounds = 100000;
     o->max_gd_retries = 60;
+    o->resume = 0;
 }
 
 const char *vesis_last_error(void) { return g_err.c_str(); }
@@ -909,6 +913,8 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VTRY(dalloc(s, &s->d_part_flips, s->sweep_blocks));
     VTRY(dalloc(s, &s->d_part_dE, s->sweep_blocks));
     VTRY(dalloc(s, &s->d_part_tiles, 2 * (size_t)s->sweep_blocks));
+    VTRY(dalloc(s, &s->d_tile_dE, (size_t)s->ntiles));
+    VTRY(dalloc(s, &s->d_tile_nf, (size_t)s->ntiles));
 
     VTRY(dalloc(s, &s->d_scal, 2 * S_BANK));
     VTRY(dalloc(s, &s->d_rs, 1));
@@ -1102,6 +1108,78 @@ int vesis_blsm_relax(vesis_system s, uint8_t *chi_dev, const float *U_dev,
     return rs.capped ? VESIS_W_MAX_ROUNDS : VESIS_OK;
 }
 
+int vesis_blsm_relax_batch(int nsys, vesis_system *systems, uint8_t *const *chi_dev,
+                           const float *const *U_dev, int max_rounds, int *rounds_out,
+                           long long *flips_out, double *dE_sum_out)
+{
+    if (nsys < 1 || nsys > kMaxSweepSys)
+        return fail(VESIS_E_ARG, "nsys must be in 1.." + std::to_string(kMaxSweepSys));
+    if (!systems || !chi_dev || !U_dev) return fail(VESIS_E_ARG, "NULL argument");
+    if (max_rounds < 1) return fail(VESIS_E_ARG, "max_rounds must be >= 1");
+    vesis_system s0 = systems[0];
+    for (int i = 0; i < nsys; ++i) {
+        vesis_system s = systems[i];
+        if (!s || !chi_dev[i] || !U_dev[i])
+            return fail(VESIS_E_ARG, "NULL system or buffer at index " + std::to_string(i));
+        for (int j = 0; j < i; ++j)
+            if (systems[j] == s) return fail(VESIS_E_ARG, "a system appears twice in the batch");
+        if (s->dev != s0->dev) return fail(VESIS_E_ARG, "systems are on different devices");
+        bool same = s->kw.r == s0->kw.r && (s->d_k3 != nullptr) == (s0->d_k3 != nullptr);
+        for (int a = 0; same && a <= 2 * s->kw.r; ++a) same = s->kw.q[a] == s0->kw.q[a];
+        if (same && s->d_k3)
+            same = s->p.h == s0->p.h && s->p.sin2_lambda == s0->p.sin2_lambda;
+        if (!same) return fail(VESIS_E_ARG, "the systems' surface kernels differ");
+    }
+    int dev0 = 0;
+    VCK(cudaGetDevice(&dev0));
+    VCK(cudaSetDevice(s0->dev));
+    struct Restore {
+        int d;
+        ~Restore() { cudaSetDevice(d); }
+    } restore{dev0};
+    std::vector<SweepSys> ys((size_t)nsys);
+    for (int i = 0; i < nsys; ++i) {
+        vesis_system s = systems[i];
+        enq_conv(s, chi_dev[i], s->d_W);
+        SweepSys &y = ys[i];
+        y.g = s->g;
+        y.fc = s->fc;
+        y.chi = chi_dev[i];
+        y.W = s->d_W;
+        y.U = U_dev[i];
+        y.dE = s->d_dE;
+        y.state = s->d_sweep;
+        y.ctl = s->d_ctl;
+        y.err = s->d_err;
+        y.tile_dE = s->d_tile_dE;
+        y.tile_nf = s->d_tile_nf;
+        y.rs = s->d_rs;
+        y.st = s->st;
+    }
+    void *scratch = nullptr;
+    VCK(cudaMalloc(&scratch, sweep_multi_scratch_bytes(nsys)));
+    struct Free {
+        void *p;
+        ~Free() { cudaFree(p); }
+    } free_scratch{scratch};
+    cudaStream_t st = s0->st;
+    VCK(launch_sweep_multi(nsys, ys.data(), s0->kw, s0->d_k3, max_rounds, s0->sweep_blocks,
+                           s0->spin_limit, scratch, s0->h_int, st));
+    VCK(cudaStreamSynchronize(st));
+    if (*s0->h_int) return fail(VESIS_E_CUDA, "flip sweep grid barrier timed out");
+    int rc = VESIS_OK;
+    for (int i = 0; i < nsys; ++i) {
+        vesis_system s = systems[i];
+        VCK(cudaMemcpy(s->h_rs, s->d_rs, sizeof(RoundState), cudaMemcpyDeviceToHost));
+        if (rounds_out) rounds_out[i] = s->h_rs->round;
+        if (flips_out) flips_out[i] = (long long)s->h_rs->total_flips;
+        if (dE_sum_out) dE_sum_out[i] = s->h_rs->total_dE;
+        if (s->h_rs->capped) rc = VESIS_W_MAX_ROUNDS;
+    }
+    VTRY(last_launch("blsm_relax_batch"));
+    return rc;
+}
+
 int vesis_blsm_heap(vesis_system s, uint8_t *chi_dev, const float *U_dev,
                     const float *E_dev, long long max_flips, long long *flips_out,
                     double *dE_sum_out, double *terms_out)
@@ -1281,8 +1359,13 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     if (opts_in) o = *opts_in;
     else vesis_default_relax_opts(&o);
     if (o.max_outer < 0 || o.window < 1 || o.max_flip_rounds < 1 ||
-        o.max_gd_retries < 0 || !(o.alpha > 0.0 && o.alpha < 1.0) || !(o.M0 > 0.0))
+        o.max_gd_retries < 0 || !(o.alpha > 0.0 && o.alpha < 1.0) || !(o.M0 > 0.0) ||
+        (o.resume != 0 && o.resume != 1))
         return fail(VESIS_E_ARG, "invalid relax options");
+    if (o.resume && !s->rstate.valid)
+        return fail(VESIS_E_ARG, "no relaxation state to resume");
+    const vesis_relax_state from = s->rstate;
+    s->rstate.valid = 0;     // written again when this call ends normally
     vesis_relax_stats st;
     std::memset(&st, 0, sizeof(st));
     const long long GN = s->G * (long long)s->n;
@@ -1297,14 +1380,16 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     // from here on d_W is the exact convolution of chi_dev: only the sweep
     // changes the labels in this call, and it keeps d_W current
     count_launch();
-    k_gd_init<<<1, 1, 0, s->st>>>(s->d_gd, o.M0);
+    k_gd_init<<<1, 1, 0, s->st>>>(s->d_gd, o.resume ? from.M : o.M0, o.resume ? from.ncnt : 0);
     VTRY(last_launch("relax init"));
     VTRY(read_bank(s, bank(s, cur)));
     st.pair_evals += GN + FN + NN;
-    double G_prev = s->h_scal[S_TOTAL];
-    if (!std::isfinite(G_prev)) return fail(VESIS_E_NAN, "non-finite initial energy");
+    double G_prev = o.resume ? from.G_prev : s->h_scal[S_TOTAL];
+    if (!std::isfinite(s->h_scal[S_TOTAL]))
+        return fail(VESIS_E_NAN, "non-finite initial energy");
 
-    int k = 0, stable = 0, reason = 2, status = VESIS_OK;
+    int k = o.resume ? from.k : 0, stable = o.resume ? from.stable : 0;
+    int reason = 2, status = VESIS_OK;
     double gmax = 0.0;
     while (k < o.max_outer) {
         RoundState rs;
@@ -1395,6 +1480,12 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
                             cudaMemcpyDeviceToHost, s->st));
         VCK(cudaStreamSynchronize(s->st));
         st.M = s->h_gd->M;
+        s->rstate.k = k;
+        s->rstate.ncnt = s->h_gd->ncnt;
+        s->rstate.stable = stable;
+        s->rstate.M = s->h_gd->M;
+        s->rstate.G_prev = G_prev;
+        s->rstate.valid = 1;
     }
     st.status = status;
     st.iterations = k;
@@ -1402,6 +1493,24 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     st.max_grad = gmax;
     if (stats_out) *stats_out = st;
     return status;
+}
+
+int vesis_get_state(vesis_system s, vesis_relax_state *out)
+{
+    if (!s || !out) return fail(VESIS_E_ARG, "NULL argument");
+    *out = s->rstate;
+    return VESIS_OK;
+}
+
+int vesis_set_state(vesis_system s, const vesis_relax_state *in)
+{
+    if (!s || !in) return fail(VESIS_E_ARG, "NULL argument");
+    if (in->k < 0 || in->ncnt < 0 || in->stable < 0 || !(in->M > 0.0) ||
+        !std::isfinite(in->M) || !std::isfinite(in->G_prev) ||
+        (in->valid != 0 && in->valid != 1))
+        return fail(VESIS_E_ARG, "invalid relaxation state");
+    s->rstate = *in;
+    return VESIS_OK;
 }
 
 int vesis_set_wait_limit(vesis_system s, long long polls)

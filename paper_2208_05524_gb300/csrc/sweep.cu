@@ -40,6 +40,8 @@
 //
 // The grid barrier spins with a bound; on timeout it raises an error flag
 // and every block returns.
+#include <vector>
+
 #include "vesis_internal.cuh"
 
 namespace vesis {
@@ -107,6 +109,9 @@ struct SweepArgs {
     int *capped_out;
     int max_rounds;
     long long spin_limit;     // polls before a barrier wait gives up
+    RoundState *rs;           // this system's totals (multi-system sweep)
+    double *tile_dE;          // per tile: its winners' dE, summed over rounds (multi)
+    unsigned *tile_nf;        // per tile: its flips (multi)
 };
 
 // Per-warp shared memory; the decide and update phases use it in turn.
@@ -145,19 +150,19 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
     return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(const SweepArgs &A, unsigned &target,
-                                             int *abort_flag)
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, long long spin_limit,
+                                             unsigned &target, int *abort_flag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x;
-        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(A.bar), "r"(1u)
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(bar), "r"(1u)
                      : "memory");
         long long spins = 0;
-        while ((int)(ld_relaxed_u32(A.bar) - target) < 0) {
-            if (++spins > A.spin_limit ||
-                ((spins & 255) == 0 && *(volatile int *)A.err)) {
-                atomicExch(A.err, 1);
+        while ((int)(ld_relaxed_u32(bar) - target) < 0) {
+            if (++spins > spin_limit ||
+                ((spins & 255) == 0 && *(volatile int *)err)) {
+                atomicExch(err, 1);
                 *abort_flag = 1;
                 break;
             }
@@ -775,7 +780,7 @@ k_sweep(SweepArgs A)
             if (lane == 0) set_own(A, S, t, now);
         }
     }
-    if (!grid_barrier(A, target, &S.abort_flag)) return;
+    if (!grid_barrier(A.bar, A.err, A.spin_limit, target, &S.abort_flag)) return;
     for (int k = 0;; ++k) {
         if (k >= A.max_rounds) {     // cap reached: capped if leaders are left
             round = k;
@@ -797,7 +802,7 @@ k_sweep(SweepArgs A)
             round = k;
             break;
         }
-        if (!grid_barrier(A, target, &S.abort_flag)) return;
+        if (!grid_barrier(A.bar, A.err, A.spin_limit, target, &S.abort_flag)) return;
         // update
         for (int base = 0; base < per_block; base += SW_THREADS) {
             const int n = gather_tiles(S, A.upd, true, base, ntiles, nullptr);
@@ -808,7 +813,7 @@ k_sweep(SweepArgs A)
                 if (lane == 0) set_own(A, S, t, now);
             }
         }
-        if (!grid_barrier(A, target, &S.abort_flag)) return;
+        if (!grid_barrier(A.bar, A.err, A.spin_limit, target, &S.abort_flag)) return;
     }
     // FP64 sums of the flipped cells' dE and their counts: lanes, then warps
     // in order
@@ -934,14 +939,13 @@ cudaError_t sweep_grid_size(int nsm, int r, int *blocks)
 
 int sweep_ctl_words() { return 3 * kLine; }
 
-cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
-                         const FlipConst &fc,
-                         uint8_t *chi, uint32_t *W, const float *U,
-                         double *dE, void *state, unsigned *ctl, int *err,
-                         unsigned long long *part_flips, double *part_dE,
-                         unsigned long long *part_tiles,
-                         int *rounds, int *capped, int max_rounds, int blocks,
-                         long long spin_limit, RoundState *rs, cudaStream_t st)
+// Arguments of one system's sweep, with its set-up enqueued on st: the
+// posting bitmaps, update flags and control words cleared and the label
+// bits packed (leader words are all rewritten by the opening pass).
+static SweepArgs sweep_setup(const GridDesc &g, const KernelW &kw, const int *k3,
+                             const FlipConst &fc, uint8_t *chi, uint32_t *W, const float *U,
+                             double *dE, void *state, unsigned *ctl, int *err, int max_rounds,
+                             long long spin_limit, cudaStream_t st)
 {
     SweepArgs A;
     A.g = g;
@@ -967,7 +971,6 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
     A.vec = (g.nz % TS == 0) && ((uintptr_t)W % 16 == 0) && ((uintptr_t)U % 16 == 0);
     const size_t nb = (size_t)A.nbx * A.nby * A.nbz;
     const size_t nt = (size_t)A.ntx * A.nty * A.ntz;
-    if ((nt + blocks - 1) / blocks > (size_t)kOwnWords * 32) return cudaErrorInvalidValue;
     uint8_t *base = static_cast<uint8_t *>(state);
     A.PL = reinterpret_cast<unsigned long long *>(base);
     A.PO = base + nb * 8;
@@ -978,15 +981,17 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
     A.nlead = ctl;
     A.bar = ctl + kLine;
     A.err = err;
-    A.part_flips = part_flips;
-    A.part_dE = part_dE;
-    A.part_tiles = part_tiles;
-    A.rounds_out = rounds;
-    A.capped_out = capped;
+    A.part_flips = nullptr;
+    A.part_dE = nullptr;
+    A.part_tiles = nullptr;
+    A.rounds_out = nullptr;
+    A.capped_out = nullptr;
     A.max_rounds = max_rounds;
     A.spin_limit = spin_limit;
-    // leader words are all rewritten by the opening pass; postings start
-    // empty (a slot is only read under its bitmap bit)
+    A.rs = nullptr;
+    A.tile_dE = nullptr;
+    A.tile_nf = nullptr;
+    // postings start empty (a slot is only read under its bitmap bit)
     cudaMemset2DAsync(A.post + kPostMaskOff, kPostBytes, 0, 32, nt, st);
     cudaMemsetAsync(A.upd, 0, nt, st);
     cudaMemsetAsync(ctl, 0, sweep_ctl_words() * sizeof(unsigned), st);
@@ -997,6 +1002,29 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
         k_pack_labels<<<(unsigned)((nwords + 255) / 256), 256, 0, st>>>(chi, g.nz, A.nzw,
                                                                        nwords, A.CB);
     }
+    return A;
+}
+
+cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
+                         const FlipConst &fc,
+                         uint8_t *chi, uint32_t *W, const float *U,
+                         double *dE, void *state, unsigned *ctl, int *err,
+                         unsigned long long *part_flips, double *part_dE,
+                         unsigned long long *part_tiles,
+                         int *rounds, int *capped, int max_rounds, int blocks,
+                         long long spin_limit, RoundState *rs, cudaStream_t st)
+{
+    {
+        const size_t nt = (size_t)sweep_tiles(g);
+        if ((nt + blocks - 1) / blocks > (size_t)kOwnWords * 32) return cudaErrorInvalidValue;
+    }
+    SweepArgs A = sweep_setup(g, kw, k3, fc, chi, W, U, dE, state, ctl, err, max_rounds,
+                              spin_limit, st);
+    A.part_flips = part_flips;
+    A.part_dE = part_dE;
+    A.part_tiles = part_tiles;
+    A.rounds_out = rounds;
+    A.capped_out = capped;
     void *args[] = {&A};
     count_launch();
     cudaError_t e = cudaLaunchCooperativeKernel(k3 ? (void *)k_sweep<true> : (void *)k_sweep<false>,
@@ -1005,6 +1033,322 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
     if (e != cudaSuccess) return e;
     count_launch();
     k_sweep_final<<<1, 1, 0, st>>>(part_flips, part_dE, part_tiles, blocks, rounds, capped, rs);
+    return cudaGetLastError();
+}
+
+
+// ------------------------------------------------- many systems at once
+// The same rounds for up to kMaxSweepSys systems in one cooperative launch:
+// the systems' tiles are numbered one after another and dealt round-robin
+// over the blocks, each round's decide and update phases serve the tiles of
+// every system, and one grid barrier closes each phase for all of them.
+// Every system's leaders, postings, labels and W live in its own state
+// exactly as in the single-system sweep, so each system goes through the
+// same rounds as alone.  A system whose leaders are gone contributes no
+// tiles; the launch ends when no system has any.  The FP64 sum of a tile's
+// flipped dE is kept per tile (the tile's warp adds it, round after round)
+// and summed over the system's tiles in tile order at the end.
+
+// dynamic shared memory offset of the systems' arguments (16-byte aligned)
+constexpr size_t kSweepSysOff = (kSweepSmem + 15) / 16 * 16;
+
+struct MultiArgs {
+    const SweepArgs *sys;     // [nsys] (device)
+    const long long *toff;    // [nsys + 1]: first global tile of each system
+    int nsys;
+    int ntiles;
+    unsigned *nlead;          // tiles holding a leader, all systems (own line)
+    unsigned *bar;            // grid barrier arrivals (own line)
+    int *err;
+    int *rounds;              // [nsys]
+    int *capped;              // [nsys]
+    int max_rounds;
+    long long spin_limit;
+    KernelW kw;
+    const int *k3;
+};
+
+__device__ __forceinline__ int sys_of(const long long *toff, int nsys, long long tg)
+{
+    int lo = 0, hi = nsys;    // toff[lo] <= tg < toff[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (toff[mid] <= tg) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// gather_tiles over the global tile numbers, each flag read (and cleared)
+// in its own system's update flags.
+__device__ int gather_tiles_multi(SweepShared &S, const SweepArgs *sys, const long long *toff,
+                                  int nsys, int base, int ntiles)
+{
+    const int k = base + threadIdx.x;
+    const long long t = (long long)blockIdx.x + (long long)k * gridDim.x;
+    bool fl = false;
+    if (t < ntiles) {
+        const int q = sys_of(toff, nsys, t);
+        uint8_t *f = sys[q].upd + (t - toff[q]);
+        fl = __ldcg(f) != 0;
+        if (fl) *f = 0;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, fl);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    __syncthreads();          // the previous list is no longer read
+    if (lane == 0) S.wc[wp] = __popc(b);
+    __syncthreads();
+    int off = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < NWARP; ++q) {
+        if (q < wp) off += S.wc[q];
+        tot += S.wc[q];
+    }
+    if (fl) S.list[off + __popc(b & ((1u << lane) - 1u))] = (int)t;
+    __syncthreads();
+    return tot;
+}
+
+__device__ __forceinline__ void set_own_multi(SweepShared &S, long long tg, bool now,
+                                              unsigned *nlead_all, unsigned *nlead_sys)
+{
+    const int j = (int)((tg - (long long)blockIdx.x) / (long long)gridDim.x);
+    const unsigned bit = 1u << (j & 31);
+    const bool old = (S.own[j >> 5] & bit) != 0u;
+    if (now == old) return;
+    if (now) atomicOr(&S.own[j >> 5], bit);
+    else atomicAnd(&S.own[j >> 5], ~bit);
+    red_add(nlead_all, now ? 1u : 0xffffffffu);
+    red_add(nlead_sys, now ? 1u : 0xffffffffu);
+}
+
+template <bool STENCIL>
+__global__ void __launch_bounds__(SW_THREADS, 1)
+k_sweep_multi(MultiArgs P)
+{
+    __shared__ SweepShared S;
+    __shared__ long long s_toff[kMaxSweepSys + 1];
+    __shared__ int s_rounds[kMaxSweepSys];
+    extern __shared__ __align__(16) unsigned char dyn[];
+    WarpMem *WM = reinterpret_cast<WarpMem *>(dyn);
+    // after the warps' areas and the stencil: the systems' arguments
+    SweepArgs *s_sys = reinterpret_cast<SweepArgs *>(dyn + kSweepSysOff);
+    const int ntiles = P.ntiles, nsys = P.nsys;
+    const int per_block = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    WarpMem &M = WM[wp];
+    int *kt = STENCIL ? reinterpret_cast<int *>(dyn + NWARP * sizeof(WarpMem)) : nullptr;
+    if (STENCIL) {
+        const int w = 2 * P.kw.r + 1;
+        for (int a = threadIdx.x; a < w * w * w; a += SW_THREADS) kt[a] = P.k3[a];
+    }
+    {
+        const int words = nsys * (int)(sizeof(SweepArgs) / 4);
+        const unsigned *src = reinterpret_cast<const unsigned *>(P.sys);
+        unsigned *dst = reinterpret_cast<unsigned *>(s_sys);
+        for (int a = threadIdx.x; a < words; a += SW_THREADS) dst[a] = src[a];
+    }
+    for (int a = threadIdx.x; a <= 2 * P.kw.r; a += SW_THREADS) S.qw[a] = P.kw.q[a];
+    for (int a = threadIdx.x; a < kOwnWords; a += SW_THREADS) S.own[a] = 0u;
+    for (int a = threadIdx.x; a <= nsys; a += SW_THREADS) s_toff[a] = P.toff[a];
+    for (int a = threadIdx.x; a < nsys; a += SW_THREADS) s_rounds[a] = 0;
+    if (threadIdx.x == 0) {
+        S.abort_flag = 0;
+        S.ncnt = 1u;
+    }
+    __syncthreads();
+    unsigned target = 0;
+    int capped = 0;
+    // opening pass: leaders of every system's starting labels
+    for (int base = 0; base < per_block; base += SW_THREADS) {
+        const int n = gather_tiles(S, nullptr, false, base, ntiles, nullptr);
+        for (int q = wp; q < n; q += NWARP) {
+            const int tg = S.list[q];
+            const int sq = sys_of(s_toff, nsys, tg);
+            const SweepArgs &A = s_sys[sq];
+            const bool now = tile_update<STENCIL>(A, M, S.qw, kt, (int)(tg - s_toff[sq]), true);
+            if (lane == 0) set_own_multi(S, tg, now, P.nlead, A.nlead);
+        }
+    }
+    if (!grid_barrier(P.bar, P.err, P.spin_limit, target, &S.abort_flag)) return;
+    for (int k = 0;; ++k) {
+        if (k >= P.max_rounds) {
+            capped = 1;
+            break;
+        }
+        unsigned nl = 1u;
+        if (threadIdx.x == 0) nl = ld_relaxed_u32(P.nlead);
+        if (blockIdx.x == 0)         // rounds of each system that still had leaders
+            for (int q = threadIdx.x; q < nsys; q += SW_THREADS)
+                if (ld_relaxed_u32(s_sys[q].nlead) != 0u) s_rounds[q] = k + 1;
+        for (int base = 0; base < per_block; base += SW_THREADS) {
+            const int n = own_list(S, base, per_block);
+            for (int q = wp; q < n; q += NWARP) {
+                const int tg = S.list[q];
+                const int sq = sys_of(s_toff, nsys, tg);
+                const SweepArgs &A = s_sys[sq];
+                const int t = (int)(tg - s_toff[sq]);
+                double e = 0.0;
+                unsigned nf = 0;
+                tile_decide(A, M, t, e, nf);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    e += __shfl_down_sync(0xffffffffu, e, o);
+                    nf += __shfl_down_sync(0xffffffffu, nf, o);
+                }
+                if (lane == 0 && nf) {
+                    A.tile_dE[t] += e;
+                    A.tile_nf[t] += nf;
+                }
+            }
+        }
+        if (threadIdx.x == 0) S.ncnt = nl;
+        __syncthreads();
+        if (S.ncnt == 0u) break;
+        if (!grid_barrier(P.bar, P.err, P.spin_limit, target, &S.abort_flag)) return;
+        for (int base = 0; base < per_block; base += SW_THREADS) {
+            const int n = gather_tiles_multi(S, s_sys, s_toff, nsys, base, ntiles);
+            for (int q = wp; q < n; q += NWARP) {
+                const int tg = S.list[q];
+                const int sq = sys_of(s_toff, nsys, tg);
+                const SweepArgs &A = s_sys[sq];
+                const bool now =
+                    tile_update<STENCIL>(A, M, S.qw, kt, (int)(tg - s_toff[sq]), false);
+                if (lane == 0) set_own_multi(S, tg, now, P.nlead, A.nlead);
+            }
+        }
+        if (!grid_barrier(P.bar, P.err, P.spin_limit, target, &S.abort_flag)) return;
+    }
+    if (blockIdx.x == 0) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < nsys; q += SW_THREADS) {
+            P.rounds[q] = s_rounds[q];
+            P.capped[q] = capped && ld_relaxed_u32(s_sys[q].nlead) != 0u;
+        }
+    }
+}
+
+// Totals of system blockIdx.x: its tiles' flip counts and dE sums added in
+// a fixed order (strided per thread, then a tree over the threads).
+__global__ void __launch_bounds__(256) k_sweep_multi_final(const SweepArgs *sys,
+                                                           const int *rounds, const int *capped)
+{
+    __shared__ double se[256];
+    __shared__ unsigned long long sf[256];
+    const SweepArgs &A = sys[blockIdx.x];
+    const int nt = A.ntx * A.nty * A.ntz;
+    double e = 0.0;
+    unsigned long long f = 0;
+    for (int t = threadIdx.x; t < nt; t += 256) {
+        e += A.tile_dE[t];
+        f += A.tile_nf[t];
+    }
+    se[threadIdx.x] = e;
+    sf[threadIdx.x] = f;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            se[threadIdx.x] += se[threadIdx.x + w];
+            sf[threadIdx.x] += sf[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        RoundState *rs = A.rs;
+        rs->done = 1;
+        rs->round = rounds[blockIdx.x];
+        rs->capped = capped[blockIdx.x];
+        rs->round_flips = 0;
+        rs->total_flips = sf[0];
+        rs->round_dE = 0.0;
+        rs->total_dE = se[0];
+        rs->tiles_decide = 0;
+        rs->tiles_update = 0;
+    }
+}
+
+static size_t pad256z(size_t x) { return (x + 255) / 256 * 256; }
+
+size_t sweep_multi_scratch_bytes(int nsys)
+{
+    return pad256z((size_t)nsys * sizeof(SweepArgs)) + pad256z((size_t)(nsys + 1) * 8) +
+           pad256z(3 * kLine * sizeof(unsigned)) + pad256z(sizeof(int)) +
+           2 * pad256z((size_t)nsys * sizeof(int));
+}
+
+cudaError_t launch_sweep_multi(int nsys, const SweepSys *sys, const KernelW &kw, const int *k3,
+                               int max_rounds, int blocks, long long spin_limit, void *scratch,
+                               int *err_out, cudaStream_t st)
+{
+    if (nsys < 1 || nsys > kMaxSweepSys) return cudaErrorInvalidValue;
+    std::vector<SweepArgs> As((size_t)nsys);
+    std::vector<long long> toff((size_t)nsys + 1, 0);
+    for (int q = 0; q < nsys; ++q) {
+        const SweepSys &y = sys[q];
+        const int nt = sweep_tiles(y.g);
+        toff[q + 1] = toff[q] + nt;
+        As[q] = sweep_setup(y.g, kw, k3, y.fc, y.chi, y.W, y.U, y.dE, y.state, y.ctl, y.err,
+                            max_rounds, spin_limit, y.st);
+        As[q].rs = y.rs;
+        As[q].tile_dE = y.tile_dE;
+        As[q].tile_nf = y.tile_nf;
+        cudaMemsetAsync(y.tile_dE, 0, (size_t)nt * sizeof(double), y.st);
+        cudaMemsetAsync(y.tile_nf, 0, (size_t)nt * sizeof(unsigned), y.st);
+    }
+    if (toff[nsys] > 0x7fffffffll ||
+        (toff[nsys] + blocks - 1) / blocks > (long long)kOwnWords * 32)
+        return cudaErrorInvalidValue;
+    // the systems' set-up ran on their own streams: st waits for all of it
+    for (int q = 0; q < nsys; ++q) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        cudaEventRecord(ev, sys[q].st);
+        cudaStreamWaitEvent(st, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    uint8_t *b = static_cast<uint8_t *>(scratch);
+    SweepArgs *d_sys = reinterpret_cast<SweepArgs *>(b);
+    b += pad256z((size_t)nsys * sizeof(SweepArgs));
+    long long *d_toff = reinterpret_cast<long long *>(b);
+    b += pad256z((size_t)(nsys + 1) * 8);
+    unsigned *d_ctl = reinterpret_cast<unsigned *>(b);
+    b += pad256z(3 * kLine * sizeof(unsigned));
+    int *d_err = reinterpret_cast<int *>(b);
+    b += pad256z(sizeof(int));
+    int *d_rounds = reinterpret_cast<int *>(b);
+    b += pad256z((size_t)nsys * sizeof(int));
+    int *d_capped = reinterpret_cast<int *>(b);
+    cudaMemcpyAsync(d_sys, As.data(), (size_t)nsys * sizeof(SweepArgs), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(d_toff, toff.data(), (size_t)(nsys + 1) * 8, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(d_ctl, 0, 3 * kLine * sizeof(unsigned), st);
+    cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    MultiArgs P;
+    P.sys = d_sys;
+    P.toff = d_toff;
+    P.nsys = nsys;
+    P.ntiles = (int)toff[nsys];
+    P.nlead = d_ctl;
+    P.bar = d_ctl + kLine;
+    P.err = d_err;
+    P.rounds = d_rounds;
+    P.capped = d_capped;
+    P.max_rounds = max_rounds;
+    P.spin_limit = spin_limit;
+    P.kw = kw;
+    P.k3 = k3;
+    const size_t smem = kSweepSysOff + (size_t)nsys * sizeof(SweepArgs);
+    void *fn = k3 ? (void *)k_sweep_multi<true> : (void *)k_sweep_multi<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kSweepSysOff + kMaxSweepSys * sizeof(SweepArgs)));
+    if (e != cudaSuccess) return e;
+    void *args[] = {&P};
+    count_launch();
+    e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(SW_THREADS), args, smem, st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_sweep_multi_final<<<nsys, 256, 0, st>>>(d_sys, d_rounds, d_capped);
+    if (err_out) cudaMemcpyAsync(err_out, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     return cudaGetLastError();
 }
 

@@ -215,6 +215,34 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
 // Default bound on a sweep block's polls of its grid barrier (several
 // seconds of waiting).
 constexpr long long kSweepSpinLimit = 1ll << 24;
+// Multi-system sweep: the rounds of up to kMaxSweepSys systems (same
+// surface kernel) in one cooperative launch.  Per system: its grid, flip
+// constants, labels, W, U, dE scratch, sweep state, control words and
+// error flag (as for launch_sweep), a per-tile FP64 dE sum and flip count
+// (sweep_tiles(g) entries each), its RoundState and the stream its
+// set-up is enqueued on.  scratch: sweep_multi_scratch_bytes(nsys) bytes
+// of device memory; err_out (pinned host, may be NULL) receives the
+// launch's error flag.  Everything else is enqueued on st.
+constexpr int kMaxSweepSys = 64;
+struct SweepSys {
+    GridDesc g;
+    FlipConst fc;
+    uint8_t *chi;
+    uint32_t *W;
+    const float *U;
+    double *dE;
+    void *state;
+    unsigned *ctl;
+    int *err;
+    double *tile_dE;
+    unsigned *tile_nf;
+    RoundState *rs;
+    cudaStream_t st;
+};
+size_t sweep_multi_scratch_bytes(int nsys);
+cudaError_t launch_sweep_multi(int nsys, const SweepSys *sys, const KernelW &kw, const int *k3,
+                               int max_rounds, int blocks, long long spin_limit, void *scratch,
+                               int *err_out, cudaStream_t st);
 
 // --------------------------------------------------------------- atoms.cu
 struct AtomParamsDev {

@@ -31,7 +31,12 @@ class RelaxOpts(C.Structure):
     _fields_ = [("max_outer", _i), ("ncnt_star", _i), ("window", _i),
                 ("M0", _d), ("alpha", _d), ("dgstar_frac", _d),
                 ("tol_grad", _d), ("tol_energy", _d), ("max_flip_rounds", _i),
-                ("max_gd_retries", _i)]
+                ("max_gd_retries", _i), ("resume", _i)]
+
+
+class RelaxState(C.Structure):
+    _fields_ = [("k", _i), ("ncnt", _i), ("stable", _i), ("valid", _i), ("M", _d),
+                ("G_prev", _d)]
 
 
 class RelaxStats(C.Structure):
@@ -99,6 +104,9 @@ def lib():
         L.vesis_surface_weights_noalloc.argtypes = [C.POINTER(Params), _p, _p, _p]
         L.vesis_set_tiles.argtypes = [_p, _i, _i]
         L.vesis_set_wait_limit.argtypes = [_p, _ll]
+        L.vesis_get_state.argtypes = [_p, C.POINTER(RelaxState)]
+        L.vesis_blsm_relax_batch.argtypes = [_i, _p, _p, _p, _i, _p, _p, _p]
+        L.vesis_set_state.argtypes = [_p, C.POINTER(RelaxState)]
         L.vesis_features.argtypes = [_p, _p, _p, _p, _d, _p]
         L.vesis_ss_terms.argtypes = [_p, _p]
         L.vesis_set_bonded.argtypes = [_p, _i, _p, _p, _p, _i, _p, _p, _p]
@@ -334,6 +342,18 @@ class System:
         _check(lib().vesis_get_timing(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Timing._fields_}
 
+    def get_state(self):
+        """Where the last relaxation stopped (vesis_get_state), as a dict."""
+        st = RelaxState()
+        _check(lib().vesis_get_state(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in RelaxState._fields_}
+
+    def set_state(self, state):
+        """Loads a saved relaxation state (vesis_set_state); relax(...,
+        resume=1) then continues from it."""
+        st = RelaxState(**{f: state[f] for f, _ in RelaxState._fields_})
+        _check(lib().vesis_set_state(self.h, C.byref(st)))
+
     def set_wait_limit(self, polls=1 << 24):
         """Polls a flip-sweep block makes at a grid barrier before the sweep
         gives up with VESIS_E_CUDA (vesis_set_wait_limit)."""
@@ -399,6 +419,26 @@ class System:
         res["status"] = rc
         res["xyz"] = x
         return res
+
+
+def blsm_relax_batch(systems, chis, Us, max_rounds=100000):
+    """vesis_blsm_relax_batch: the flip rounds of every (system, chi, U) in
+    one persistent launch; chi tensors are relaxed in place.  Returns one
+    dict per system (status of the call, rounds, flips, dE_sum)."""
+    import torch
+    n = len(systems)
+    if not (len(chis) == n and len(Us) == n):
+        raise ValueError("systems, chis and Us differ in length")
+    hs = (_p * n)(*[s.h for s in systems])
+    cs = (_p * n)(*[_dp(c, torch.uint8, s.G) for s, c in zip(systems, chis)])
+    us = (_p * n)(*[_dp(u, torch.float32, s.G) for s, u in zip(systems, Us)])
+    rounds = (_i * n)()
+    flips = (_ll * n)()
+    dsum = (_d * n)()
+    rc = _check(lib().vesis_blsm_relax_batch(n, C.cast(hs, _p), C.cast(cs, _p), C.cast(us, _p),
+                                             int(max_rounds), C.cast(rounds, _p),
+                                             C.cast(flips, _p), C.cast(dsum, _p)))
+    return [dict(status=rc, rounds=rounds[i], flips=flips[i], dE_sum=dsum[i]) for i in range(n)]
 
 
 def relax_batch(systems, chis, xyzs, threads=8, sweep_slots=2, **opts):

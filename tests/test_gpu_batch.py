@@ -160,3 +160,64 @@ def test_relax_batch_rejects_a_repeated_system():
     with pytest.raises(vs.VesisError, match="twice"):
         vs.relax_batch([S, S], [c, c.clone()], [s["xyz"], s["xyz"]], max_outer=1)
     assert vs.relax_batch([], [], []) == []
+
+
+def _sweep_inputs(s):
+    """The oracle's tight labels and its energy density rounded to FP32."""
+    p = O.params()
+    Uo = O.fields(s, p)[0].astype(np.float32)
+    return O.init_labels(s), Uo
+
+
+@pytest.mark.parametrize("kernel", ["gauss", "sin2"])
+def test_multi_system_sweep_matches_single_sweeps_and_oracle(kernel):
+    """vesis_blsm_relax_batch: the flip rounds of six systems of different
+    grids (ragged, one already relaxed, one all solvent) in one cooperative
+    launch give every system the labels, rounds and flips of
+    vesis_blsm_relax alone, and the oracle's parallel rule on two of them."""
+    vs = _vs()
+    # the sin^2 stencil depends on h, so that batch keeps h = 0.5 A; the
+    # Gaussian's weights do not, and its batch takes the h = 0.7 A cluster
+    sds = [synth.random_cluster(30, 40, 0.5, seed=1, net_charge=1.0),
+           synth.random_cluster(60, 44, 0.5, seed=2, net_charge=-1.0),
+           synth.protein_like(n_atoms=48, n=48, h=0.5, seed=5),
+           _cluster() if kernel == "gauss" else synth.random_cluster(90, 37, 0.5, seed=6),
+           synth.random_cluster(20, 40, 0.5, seed=3),
+           synth.random_cluster(20, 40, 0.5, seed=4)]
+    kw = {} if kernel == "gauss" else {"kernel": "sin2"}
+    systems = [vs.System(sd, **kw) for sd in sds]
+    starts, Us = [], []
+    for k, sd in enumerate(sds):
+        chi0, Uo = _sweep_inputs(sd)
+        if k == 5:
+            chi0 = np.zeros_like(chi0)            # all solvent: nothing to flip
+        starts.append(chi0)
+        Us.append(_dev(Uo.reshape(-1), torch.float32))
+    single = []
+    for S, chi0, U in zip(systems, starts, Us):
+        c = _dev(chi0.reshape(-1), torch.uint8)
+        r = S.blsm_relax(c, U, terms=False)
+        single.append((c.cpu().numpy(), r))
+    # system 4 starts from its relaxed labels: no rounds at all
+    starts[4] = single[4][0].reshape(starts[4].shape)
+    single[4] = (single[4][0], dict(rounds=0, flips=0, dE_sum=0.0))
+    chis = [_dev(c.reshape(-1), torch.uint8) for c in starts]
+    res = vs.blsm_relax_batch(systems, chis, Us)
+    for k, (c, r, (cs, rs)) in enumerate(zip(chis, res, single)):
+        assert np.array_equal(c.cpu().numpy(), cs), k
+        assert (r["rounds"], r["flips"]) == (rs["rounds"], rs["flips"]), k
+        assert r["dE_sum"] == pytest.approx(rs["dE_sum"], rel=1e-12, abs=1e-12), k
+    assert single[5][1]["flips"] == 0 and res[5]["flips"] == 0
+    p = O.params(kernel=kernel)
+    for k in (0, 2):
+        sc = O.surface_constants(sds[k], p)
+        ref = _sweep_inputs(sds[k])[0].copy()
+        ro = O.blsm_parallel(ref, Us[k].cpu().numpy().astype(np.float64).reshape(ref.shape), sc)
+        assert np.array_equal(chis[k].cpu().numpy(), ref.reshape(-1)), k
+        assert res[k]["rounds"] == ro["rounds"], k
+    # a cap on the rounds stops the batch with the warning
+    chis = [_dev(c.reshape(-1), torch.uint8) for c in starts]
+    res = vs.blsm_relax_batch(systems, chis, Us, max_rounds=2)
+    assert res[0]["status"] == 1
+    for S in systems:
+        S.close()

@@ -293,6 +293,45 @@ def test_relax_charged_multi_atom_lock_step_matches_oracle():
     assert r["G"] == pytest.approx(ro["G"], rel=1e-6)
 
 
+def test_relax_resumes_bit_identically_from_a_saved_state():
+    """Checkpoint and resume: ten outer iterations of a charged solute in one
+    call, against four iterations, the state saved (labels, positions,
+    vesis_get_state), a new system loaded with it (vesis_set_state) and
+    the relaxation continued to k = 10 (opts.resume): identical labels,
+    positions, energy, M and counts."""
+    vs = _vs()
+    s = synth.protein_like(n_atoms=48, n=48, h=0.5, seed=5)
+    chi0 = O.init_labels(s)
+    A = vs.System(s)
+    chi_a = _dev(chi0.reshape(-1), torch.uint8)
+    ra = A.relax(chi_a, s["xyz"], max_outer=10)
+    st_a = A.get_state()
+    assert st_a["valid"] == 1 and st_a["k"] == ra["iterations"] == 10
+    B = vs.System(s)
+    chi_b = _dev(chi0.reshape(-1), torch.uint8)
+    rb1 = B.relax(chi_b, s["xyz"], max_outer=4)
+    saved = (chi_b.cpu().numpy().copy(), rb1["xyz"].copy(), B.get_state())
+    assert saved[2]["k"] == 4
+    B.close()
+    C_ = vs.System(s)
+    with pytest.raises(vs.VesisError):      # nothing to resume yet
+        C_.relax(_dev(saved[0], torch.uint8), saved[1], max_outer=10, resume=1)
+    C_.set_state(saved[2])
+    chi_c = _dev(saved[0], torch.uint8)
+    rb2 = C_.relax(chi_c, saved[1], max_outer=10, resume=1)
+    assert rb2["iterations"] == 10
+    assert torch.equal(chi_c, chi_a)
+    assert np.array_equal(rb2["xyz"], ra["xyz"])
+    assert rb2["G"] == ra["G"] and rb2["M"] == ra["M"]
+    for key in ("gd_trials", "flip_rounds", "flips"):
+        assert rb1[key] + rb2[key] == ra[key], key
+    assert C_.get_state() == st_a
+    with pytest.raises(vs.VesisError):
+        C_.set_state(dict(st_a, M=-1.0))
+    A.close()
+    C_.close()
+
+
 # --------------------------------------------------- full-size, sampled
 
 def test_protein_like_full_size_sampled():

@@ -63,7 +63,8 @@ def _c_layout(struct, fields):
 @pytest.mark.parametrize("cname,pyname", [("vesis_params", "Params"),
                                           ("vesis_relax_opts", "RelaxOpts"),
                                           ("vesis_relax_stats", "RelaxStats"),
-                                          ("vesis_timing", "Timing")])
+                                          ("vesis_timing", "Timing"),
+                                          ("vesis_relax_state", "RelaxState")])
 def test_struct_layouts_match_header(tmp_path, built, cname, pyname):
     from paper_2208_05524_gb300 import vesis
     cls = getattr(vesis, pyname)
