@@ -1017,6 +1017,220 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs P)
     }
 }
 
+// ------------------------------------------------ tcgen05 weight gradient
+// dW[tap][co][ci] = sum over cells v of dZ[v][co] X[v + tap][ci] on the
+// 5th-generation tensor cores, for levels that tile by bricks of 1 x 16 x 8
+// cells.  Per tap this is D[m][n] += sum over cells of P[cell][m] Q[cell][n]
+// (K = cells): one operand gives the 128 rows of D (M, zero channels pad it
+// to 128), the other its N columns.  Both operands sit in shared memory
+// MN-major without swizzle - a core matrix is 8 cells along z (16-byte
+// rows) by 8 channels - so the tiles keep the activations' channels-last
+// layout and nothing is transposed.  The dZ brick is [y][channel group][z][8]
+// and the input's halo [hx][hy][channel group][hz][8], as in the forward
+// kernel, so every tap's operand is the same halo seen from another start
+// address.  Rows are output channels when Cout >= Cin (encoder layers), else
+// a 128-channel tile of the input (decoder layers, whose input is the skip
+// and the doubled coarse tensor).  A block takes a chunk of consecutive
+// bricks and a group of taps whose accumulators fill the tensor memory (512
+// / N taps of N columns); one thread issues each brick's MMAs (8 per tap, K
+// = 16 cells = two z-columns of the brick) once its tiles are staged, and
+// the block writes its partial dW of those taps at the end, summed over the
+// chunks in order afterwards.
+constexpr int WT_KCM = 16;                                   // 128 M channels
+constexpr int WT_DZ_BYTES = TCY * WT_KCM * TCZ * 16;          // 32,768
+constexpr int WT_HALO_BYTES = TC_HX * TC_HY * WT_KCM * TC_HZ * 16;   // 138,240
+// the operands' largest start address plus extent stays inside the
+// allocation for either assignment of the descriptor's two strides
+constexpr int WT_SMEM = 212992;
+static_assert(WT_DZ_BYTES + WT_HALO_BYTES + 64 <= WT_SMEM, "wgrad smem layout");
+
+struct WgradTcArgs {
+    int nx, ny, nz;
+    const bf16 *A;       // input, skip part [V][Ca]
+    int Ca;
+    const bf16 *B;       // coarse part at half resolution [V / 8][Cb], or NULL
+    int Cb;
+    const bf16 *dZ;      // [V][Cout]
+    int Cout;
+    float *part;         // [chunks][27][Cout][Cin]
+    int rows_co;         // 1: rows of D are output channels; 0: input channels
+    int N;               // columns of D per tap
+    int taps;            // taps per block (tap group)
+    int bricks_per_chunk;
+    int nbricks;
+};
+
+// Instruction descriptor of kind::f16 with both operands MN-major: BF16 A
+// and B, FP32 D, M = 128, N.
+__host__ __device__ constexpr unsigned wt_idesc(int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+           ((unsigned)(N >> 3) << 17) | (8u << 24);
+}
+
+__global__ void __launch_bounds__(128, 1) k_wgrad_tc(WgradTcArgs P, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sz = smem;                            // dZ brick
+    unsigned char *sh = smem + WT_DZ_BYTES;              // halo
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sh + WT_HALO_BYTES);
+    unsigned *tslot = reinterpret_cast<unsigned *>(sh + WT_HALO_BYTES + 8);
+    int *sfail = reinterpret_cast<int *>(sh + WT_HALO_BYTES + 16);
+    const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+    const int Cin = P.Ca + P.Cb;
+    const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
+    const long long nyz = (long long)P.ny * P.nz;
+    const int hy = P.ny >> 1, hz = P.nz >> 1;
+    const int chunk = blockIdx.x;
+    const int tap0 = blockIdx.y * P.taps;
+    const int ntap = min(P.taps, 27 - tap0);
+    const int ci0 = P.rows_co ? 0 : blockIdx.z * 128;   // first input channel of the rows
+    // channel groups staged: dZ (rows: 16 padded; columns: Cout / 8), halo
+    // (columns: Cin / 8; rows: 16 padded, starting at ci0)
+    const int kcz = P.rows_co ? WT_KCM : P.Cout / 8;
+    const int kch = P.rows_co ? Cin / 8 : WT_KCM;
+    const int b0 = chunk * P.bricks_per_chunk;
+    const int b1 = min(P.nbricks, b0 + P.bricks_per_chunk);
+    const unsigned bar = smem_u32(mbar);
+    if (t == 0) {
+        *sfail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (w == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(512) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned tmem = *tslot;
+    const unsigned idesc = wt_idesc(P.N);
+    const unsigned sza = smem_u32(sz), sha = smem_u32(sh);
+    int issued = 0;
+    for (int b = b0; b < b1; ++b) {
+        if (issued > 0 && !mbar_wait(bar, (unsigned)((issued - 1) & 1))) {
+            *sfail = 1;
+            atomicExch(err, 1);
+        }
+        __syncthreads();
+        if (*sfail) break;
+        const int bz = b % nzb, by = (b / nzb) % nyb, bx = b / (nzb * nyb);
+        const int i0 = bx, j0 = by * TCY, k0 = bz * TCZ;
+        // dZ brick: [y][group][z][8 channels], zero past Cout
+        for (int e = t; e < TCY * kcz * TCZ; e += 128) {
+            const int z = e % TCZ, g = (e / TCZ) % kcz, y = e / (TCZ * kcz);
+            const bool in = g * 8 < P.Cout;
+            const bf16 *src = P.dZ;
+            if (in)
+                src = P.dZ + ((long long)i0 * nyz + (long long)(j0 + y) * P.nz + k0 + z) * P.Cout +
+                      g * 8;
+            cp_async16(sza + (unsigned)e * 16u, src, in);
+        }
+        // halo: [hx][hy][group][hz][8 channels], zero outside the grid and
+        // past the input's channels
+        for (int e = t; e < TC_HX * TC_HY * kch * TC_HZ; e += 128) {
+            const int hzz = e % TC_HZ, g = (e / TC_HZ) % kch, hyy = (e / (TC_HZ * kch)) % TC_HY,
+                      hxx = e / (TC_HZ * kch * TC_HY);
+            const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
+            const int c = ci0 + g * 8;
+            const bool in = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 &&
+                            kk < P.nz && c < Cin;
+            const bf16 *src = P.A;
+            if (in) {
+                if (c < P.Ca)
+                    src = P.A + ((long long)ii * nyz + (long long)jj * P.nz + kk) * P.Ca + c;
+                else
+                    src = P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) * P.Cb +
+                          (c - P.Ca);
+            }
+            cp_async16(sha + (unsigned)e * 16u, src, in);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // MN stride (SBO) between channel groups, K stride (LBO) between
+            // the two z-columns of a K step
+            const unsigned long long dz0 = tc_desc(sza, kcz * TCZ * 16, TCZ * 16);
+            const unsigned long long dh0 = tc_desc(sha, kch * TC_HZ * 16, TC_HZ * 16);
+            for (int j = 0; j < ntap; ++j) {
+                const int tap = tap0 + j;
+                const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
+                for (int s2 = 0; s2 < TCY / 2; ++s2) {
+                    // start addresses in 16-byte units
+                    const unsigned long long oz = (unsigned long long)(2 * s2 * kcz * TCZ);
+                    const unsigned long long oh =
+                        (unsigned long long)(((da * TC_HY + 2 * s2 + db) * kch) * TC_HZ + dc);
+                    const unsigned long long ad = P.rows_co ? dz0 + oz : dh0 + oh;
+                    const unsigned long long bd = P.rows_co ? dh0 + oh : dz0 + oz;
+                    const unsigned acc = (b > b0 || s2 > 0) ? 1u : 0u;
+                    tc_mma(tmem + (unsigned)(j * P.N), ad, bd, idesc, acc);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(bar) : "memory");
+        }
+        ++issued;
+    }
+    const bool failed_before = *sfail != 0;
+    __syncthreads();
+    if (!failed_before && issued > 0 && !mbar_wait(bar, (unsigned)((issued - 1) & 1))) {
+        *sfail = 1;
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!*sfail && issued > 0) {
+        const int m = 32 * w + lane;                    // row of D
+        for (int j = 0; j < ntap; ++j) {
+            const int tap = tap0 + j;
+            for (int n0 = 0; n0 < P.N; n0 += 32) {
+                unsigned r[32];
+                const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(j * P.N + n0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                    "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                      "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                      "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                      "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                      "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                      "=r"(r[30]), "=r"(r[31])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float *base = P.part + ((long long)chunk * 27 + tap) * P.Cout * Cin;
+                if (P.rows_co) {
+                    if (m < P.Cout) {
+                        float4 *d = reinterpret_cast<float4 *>(base + (long long)m * Cin + n0);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            d[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                               __uint_as_float(r[4 * q + 2]),
+                                               __uint_as_float(r[4 * q + 3]));
+                    }
+                } else if (ci0 + m < Cin) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        base[(long long)(n0 + q) * Cin + ci0 + m] = __uint_as_float(r[q]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"(512) : "memory");
+    }
+}
+
 // out[i] = sum over b = 0, 1, ... of part[b][i], in that order (n entries
 // per part): the fixed-order reduction of per-block partial gradients.
 __global__ void k_sum_parts(const float *__restrict__ part, int nparts, long long n,
@@ -1516,7 +1730,8 @@ int ensure_act(vesis_net n, int nx, int ny, int nz, bool train)
         // partial gradients: the weight gradient's chunks (at most 608 + 27 x
         // 8 x 2 blocks of 64 x 32 entries), the ReLU layers' 608 x 128 and
         // the head's blocks x 33
-        long long pc = (608ll + 27 * 8 * 2) * 64 * 32;
+        long long pc = 16ll << 20;        // at least 16 M floats: the tcgen05 chunks
+        pc = std::max(pc, (608ll + 27 * 8 * 2) * 64 * 32);
         pc = std::max(pc, 608ll * 128);
         pc = std::max(pc, (V0 + 255) / 256 * 33);
         NTRY(nalloc(A, &n->part, pc));
@@ -1649,6 +1864,38 @@ void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf1
            const bf16 *dZ, int Cout, float *dW)
 {
     // chunk partials in n->part, then one ordered sum into dW
+    const int Cin_ = Ca + Cb;
+    const long long nw_ = 27ll * Cout * Cin_;
+    if (n->conv_kind == 1 && ny % TCY == 0 && nz % TCZ == 0 && Ca % 32 == 0 && Cb % 32 == 0 &&
+        Cout % 32 == 0 && (Cout >= Cin_ ? Cin_ : Cout) <= 128) {
+        WgradTcArgs t;
+        t.nx = nx;
+        t.ny = ny;
+        t.nz = nz;
+        t.A = A;
+        t.Ca = Ca;
+        t.B = B;
+        t.Cb = Cb;
+        t.dZ = dZ;
+        t.Cout = Cout;
+        t.part = n->part;
+        t.rows_co = Cout >= Cin_ ? 1 : 0;
+        t.N = t.rows_co ? Cin_ : Cout;
+        t.taps = std::min(27, 512 / t.N);
+        const int groups = (27 + t.taps - 1) / t.taps;
+        const int mt = t.rows_co ? 1 : (Cin_ + 127) / 128;
+        t.nbricks = nx * (ny / TCY) * (nz / TCZ);
+        long long chunks = std::max(1, (2 * 152) / (groups * mt));
+        chunks = std::min<long long>(chunks, t.nbricks);
+        chunks = std::min<long long>(chunks, std::max(1ll, n->part_cap / nw_));
+        t.bricks_per_chunk = (int)((t.nbricks + chunks - 1) / chunks);
+        chunks = (t.nbricks + t.bricks_per_chunk - 1) / t.bricks_per_chunk;
+        count_launch(2);
+        k_wgrad_tc<<<dim3((unsigned)chunks, (unsigned)groups, (unsigned)mt), 128, WT_SMEM,
+                     n->st>>>(t, n->d_err);
+        k_sum_parts<<<nblk(nw_), 256, 0, n->st>>>(n->part, (int)chunks, nw_, dW);
+        return;
+    }
     WgradArgs a;
     a.nx = nx;
     a.ny = ny;
@@ -1806,7 +2053,9 @@ int vesis_net_create(int n_features, void *cuda_stream, vesis_net *out)
          cudaFuncSetAttribute(k_conv_tma<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               tma_smem_bytes(64)) != cudaSuccess ||
          cudaFuncSetAttribute(k_conv_tma<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              tma_smem_bytes(64)) != cudaSuccess))
+                              tma_smem_bytes(64)) != cudaSuccess ||
+         cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              WT_SMEM) != cudaSuccess))
         rc = nfail(VESIS_E_CUDA, "shared memory attribute of the tensor-core conv kernel");
     if (rc == VESIS_OK) rc = nalloc(A, &n->d_err, 1);
     if (rc == VESIS_OK && cudaMallocHost(&n->h_err, sizeof(int)) != cudaSuccess)
