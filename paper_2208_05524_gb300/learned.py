@@ -94,14 +94,15 @@ def protein_field(index, seed, atoms=(500, 4000), n=256, h=0.4):
     return synth.protein_like(n_atoms=na, n=n, h=h, seed=int(rng.integers(1 << 31)))
 
 
-def crop_bank(systems, n_fields, seed, crop=64, stream=None, log_every=0):
+def crop_bank(systems, n_fields, seed, crop=64, group=8, log_every=0):
     """Training crops from plain relaxations: for each of the n_fields
     solutes that `systems` yields (protein_field(i, seed) for i = 0, 1, ...,
     built here or by worker processes), the tight start relaxed by the flip
-    sweep at fixed atoms (the plain method), and one crop^3 window of its
-    features and relaxed labels, centred on a randomly chosen atom (so that
-    it holds solute, interface and solvent) and kept inside the grid on the
-    8-cell lattice.  Returns the crops as device tensors x
+    sweep at fixed atoms (the plain method; `group` solutes at a time in one
+    multi-system sweep, vesis_blsm_relax_batch), and one crop^3 window of
+    its features and relaxed labels, centred on a randomly chosen atom (so
+    that it holds solute, interface and solvent) and kept inside the grid on
+    the 8-cell lattice.  Returns the crops as device tensors x
     [n_fields][3][crop^3] and chi [n_fields][crop^3], with the sweeps'
     rounds and flips."""
     import torch
@@ -110,23 +111,52 @@ def crop_bank(systems, n_fields, seed, crop=64, stream=None, log_every=0):
     X = torch.empty((n_fields, 3, V), dtype=torch.float32, device=dev)
     Y = torch.empty((n_fields, V), dtype=torch.uint8, device=dev)
     rounds = flips = 0
-    for i, sd in zip(range(n_fields), systems):
-        e = example(sd, stream=stream)
-        rng = np.random.default_rng([seed, i, 1])
-        a = sd["xyz"][int(rng.integers(len(sd["xyz"])))]
-        cell = np.floor((a - np.asarray(sd["origin"])) / sd["h"]).astype(int)
-        o = [int(np.clip((c - crop // 2) // 8 * 8, 0, d - crop))
-             for c, d in zip(cell, e["shape"])]
-        sl = tuple(slice(oo, oo + crop) for oo in o)
-        nx, ny, nz = e["shape"]
-        X[i] = e["x"].view(3, nx, ny, nz)[(slice(None),) + sl].reshape(3, V)
-        Y[i] = e["chi"].view(nx, ny, nz)[sl].reshape(V)
-        rounds += e["rounds"]
-        flips += e["flips"]
-        del e
-        if log_every and (i + 1) % log_every == 0:
-            print(f"field {i + 1}/{n_fields}", flush=True)
+    it = iter(zip(range(n_fields), systems))
+    while True:
+        batch = []
+        for _ in range(group):
+            nxt = next(it, None)
+            if nxt is None:
+                break
+            i, sd = nxt
+            S = vesis.System(sd)
+            U = torch.empty(S.G, dtype=torch.float32, device=dev)
+            E = torch.empty(3 * S.G, dtype=torch.float32, device=dev)
+            S.energy_field(U, E)
+            chi = torch.empty(S.G, dtype=torch.uint8, device=dev)
+            S.init_labels(chi, "tight")
+            x = torch.empty(3 * S.G, dtype=torch.float32, device=dev)
+            S.features(U, E, chi, x, scale=FEATURE_SCALE)
+            batch.append((i, sd, S, U, chi, x))
+        if not batch:
+            break
+        res = vesis.blsm_relax_batch([b[2] for b in batch], [b[4] for b in batch],
+                                     [b[3] for b in batch])
+        for (i, sd, S, U, chi, x), r in zip(batch, res):
+            e = dict(shape=S.shape, x=x, chi=chi, rounds=r["rounds"], flips=r["flips"])
+            S.close()
+            _crop_into(X, Y, i, e, sd, seed, crop)
+            rounds += e["rounds"]
+            flips += e["flips"]
+        done = batch[-1][0] + 1
+        if log_every and (done // log_every) != ((done - len(batch)) // log_every):
+            print(f"field {done}/{n_fields}", flush=True)
     return dict(x=X, chi=Y, crop=crop, rounds=rounds, flips=flips)
+
+
+def _crop_into(X, Y, i, e, sd, seed, crop):
+    """Copies the crop^3 window of example e (features x, relaxed labels
+    chi) around an atom of sd chosen with the generator of (seed, i) into
+    X[i] and Y[i]."""
+    V = crop ** 3
+    rng = np.random.default_rng([seed, i, 1])
+    a = sd["xyz"][int(rng.integers(len(sd["xyz"])))]
+    cell = np.floor((a - np.asarray(sd["origin"])) / sd["h"]).astype(int)
+    o = [int(np.clip((c - crop // 2) // 8 * 8, 0, d - crop)) for c, d in zip(cell, e["shape"])]
+    sl = tuple(slice(oo, oo + crop) for oo in o)
+    nx, ny, nz = e["shape"]
+    X[i] = e["x"].view(3, nx, ny, nz)[(slice(None),) + sl].reshape(3, V)
+    Y[i] = e["chi"].view(nx, ny, nz)[sl].reshape(V)
 
 
 def train_bank(net, bank, steps, lr=1e-3, seed=0):
