@@ -361,6 +361,57 @@ def test_parallel_rule_small_kernel_radius():
     assert np.all(dE[cand == 1] >= 0)
 
 
+def _brick_rule_by_definition(dE, cand, r):
+    """The brick-leader rule restated from its definition with numpy and
+    plain loops: the key of a cell with a negative flip energy is
+    (float32(dE), linear index), compared lexicographically; bricks of edge
+    4 (2 when r < 3) aligned at index 0; a brick's leader is its smallest
+    key; a leader is selected when no other brick's leader within Chebyshev
+    distance r has a smaller key."""
+    n = dE.shape
+    B = 4 if r >= 3 else 2
+    f = np.where((cand == 1) & (dE < 0.0), dE.astype(np.float32), np.float32(np.inf))
+    lin = np.arange(dE.size).reshape(n)
+    leaders = []
+    for a in range(0, n[0], B):
+        for b in range(0, n[1], B):
+            for c in range(0, n[2], B):
+                kf = f[a:a + B, b:b + B, c:c + B].ravel()
+                ki = lin[a:a + B, b:b + B, c:c + B].ravel()
+                if not np.isfinite(kf).any():
+                    continue
+                j = np.lexsort((ki, kf))[0]
+                leaders.append((float(kf[j]), int(ki[j])))
+    pos = [np.array(np.unravel_index(p, n)) for _, p in leaders]
+    sel = np.zeros(dE.size, np.uint8)
+    for k, key in enumerate(leaders):
+        if not any(np.abs(pos[m] - pos[k]).max() <= r and leaders[m] < key
+                   for m in range(len(leaders)) if m != k):
+            sel[key[1]] = 1
+    return sel.reshape(n)
+
+
+@pytest.mark.parametrize("r, seed", [(1, 11), (2, 12), (6, 13), (6, 14)])
+def test_brick_rule_matches_its_restatement(r, seed):
+    """The oracle's selection (C, or_select) against the rule written out
+    independently above, on random labels and energy densities with many
+    negative candidates, for bricks of edge 2 (r = 1, 2) and 4 (r = 6)."""
+    rng = np.random.default_rng(seed)
+    n = (13, 10, 15)
+    sc, chi, U = _small_case(seed, n=n, scale=0.15)
+    if r != sc["r"]:
+        q = O.surface_kernel(1.0 if r < 3 else 2.0, r)
+        S1 = int(sum(a * int(q[r + a]) for a in range(1, r + 1)))
+        c = 0.174 * 0.3 * 0.3 * 256.0 / S1
+        sc = dict(sc, q=q, r=r, S1=S1, c=c, g0=float(int(q[r]) ** 3) / float(256 ** 3),
+                  cN=c / 256 ** 3, k0=int(q[r]) ** 3)
+    U = U - rng.uniform(0.0, 0.1)
+    sel, _, dE, cand = O.select(chi, U, sc)
+    ref = _brick_rule_by_definition(dE, cand, r)
+    assert ref.sum() > 1
+    assert np.array_equal(sel, ref)
+
+
 # ------------------------------------------------------------ sphere pins
 
 def test_sphere_closed_form_values():
