@@ -897,7 +897,7 @@ __global__ void k_pack_tc(const bf16 *__restrict__ W, int Cout, int Cin, int NT,
 // dZ[v][co] X[v + tap][ci] (X the concatenated input).  M = co (64 per
 // block), N = ci (32 per block), K = cells in stages of 32, split over
 // chunks of cells_per_block cells; each chunk writes its own partial
-// dW (part[chunk][tap][co][ci]) and k_sum_parts adds the chunks in order,
+// dW (part[chunk][tap][co][ci]) and k_sum_parts4 adds the chunks in order,
 // so the result does not depend on the order the blocks run in.
 struct WgradArgs {
     int nx, ny, nz;
@@ -1039,10 +1039,9 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradArgs P)
 constexpr int WT_KCM = 16;                                   // 128 M channels
 constexpr int WT_DZ_BYTES = TCY * WT_KCM * TCZ * 16;          // 32,768
 constexpr int WT_HALO_BYTES = TC_HX * TC_HY * WT_KCM * TC_HZ * 16;   // 138,240
-// the operands' largest start address plus extent stays inside the
-// allocation for either assignment of the descriptor's two strides
-constexpr int WT_SMEM = 212992;
-static_assert(WT_DZ_BYTES + WT_HALO_BYTES + 64 <= WT_SMEM, "wgrad smem layout");
+// buffer sets (one or two, as they fit) and the barriers in the last 64 bytes
+constexpr int WT_SMEM = 227 * 1024;
+static_assert(WT_DZ_BYTES + WT_HALO_BYTES + 1024 <= WT_SMEM, "wgrad smem layout");
 
 struct WgradTcArgs {
     int nx, ny, nz;
@@ -1068,14 +1067,14 @@ __host__ __device__ constexpr unsigned wt_idesc(int N)
            ((unsigned)(N >> 3) << 17) | (8u << 24);
 }
 
+__device__ __forceinline__ int ilog2(int v)
+{
+    return 31 - __clz(v);
+}
+
 __global__ void __launch_bounds__(128, 1) k_wgrad_tc(WgradTcArgs P, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sz = smem;                            // dZ brick
-    unsigned char *sh = smem + WT_DZ_BYTES;              // halo
-    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sh + WT_HALO_BYTES);
-    unsigned *tslot = reinterpret_cast<unsigned *>(sh + WT_HALO_BYTES + 8);
-    int *sfail = reinterpret_cast<int *>(sh + WT_HALO_BYTES + 16);
     const int t = threadIdx.x, w = t >> 5, lane = t & 31;
     const int Cin = P.Ca + P.Cb;
     const int nyb = P.ny / TCY, nzb = P.nz / TCZ;
@@ -1085,17 +1084,40 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(WgradTcArgs P, int *err)
     const int tap0 = blockIdx.y * P.taps;
     const int ntap = min(P.taps, 27 - tap0);
     const int ci0 = P.rows_co ? 0 : blockIdx.z * 128;   // first input channel of the rows
-    // channel groups staged: dZ (rows: 16 padded; columns: Cout / 8), halo
-    // (columns: Cin / 8; rows: 16 padded, starting at ci0)
+    // channel groups (8 channels) in the layout and staged: the operand that
+    // gives the 128 rows of D is laid out with 16 groups, the ones past its
+    // channels zero (written once); the other has exactly its channels
     const int kcz = P.rows_co ? WT_KCM : P.Cout / 8;
     const int kch = P.rows_co ? Cin / 8 : WT_KCM;
+    const int gz = P.Cout / 8;
+    const int gh = P.rows_co ? Cin / 8 : min(WT_KCM, (Cin - ci0) / 8);
+    const int lgz = ilog2(gz), lgh = ilog2(gh);          // both powers of two
+    const int dz_bytes = TCY * kcz * TCZ * 16;
+    const int h_bytes = TC_HX * TC_HY * kch * TC_HZ * 16;
+    const int set_bytes = (dz_bytes + h_bytes + 1023) & ~1023;
+    const int nbuf = 2 * set_bytes + 1024 <= WT_SMEM ? 2 : 1;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(smem + WT_SMEM - 64);
+    unsigned *tslot = reinterpret_cast<unsigned *>(smem + WT_SMEM - 32);
+    int *sfail = reinterpret_cast<int *>(smem + WT_SMEM - 28);
     const int b0 = chunk * P.bricks_per_chunk;
     const int b1 = min(P.nbricks, b0 + P.bricks_per_chunk);
-    const unsigned bar = smem_u32(mbar);
+    const int nb = b1 - b0;
     if (t == 0) {
         *sfail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+        for (int q = 0; q < 2; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + q)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // zero the padding groups of every buffer set once
+    for (int q = 0; q < nbuf; ++q) {
+        uint4 *sz = reinterpret_cast<uint4 *>(smem + q * set_bytes);
+        uint4 *sh = reinterpret_cast<uint4 *>(smem + q * set_bytes + dz_bytes);
+        if (gz < kcz)
+            for (int e = t; e < TCY * kcz * TCZ; e += 128)
+                if (((e / TCZ) % kcz) >= gz) sz[e] = make_uint4(0u, 0u, 0u, 0u);
+        if (gh < kch)
+            for (int e = t; e < TC_HX * TC_HY * kch * TC_HZ; e += 128)
+                if (((e / TC_HZ) % kch) >= gh) sh[e] = make_uint4(0u, 0u, 0u, 0u);
     }
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -1107,36 +1129,28 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(WgradTcArgs P, int *err)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tslot;
     const unsigned idesc = wt_idesc(P.N);
-    const unsigned sza = smem_u32(sz), sha = smem_u32(sh);
-    int issued = 0;
-    for (int b = b0; b < b1; ++b) {
-        if (issued > 0 && !mbar_wait(bar, (unsigned)((issued - 1) & 1))) {
-            *sfail = 1;
-            atomicExch(err, 1);
-        }
-        __syncthreads();
-        if (*sfail) break;
+
+    // stages brick b into buffer set q (cp.async, one group committed)
+    auto stage = [&](int b, int q) {
         const int bz = b % nzb, by = (b / nzb) % nyb, bx = b / (nzb * nyb);
         const int i0 = bx, j0 = by * TCY, k0 = bz * TCZ;
-        // dZ brick: [y][group][z][8 channels], zero past Cout
-        for (int e = t; e < TCY * kcz * TCZ; e += 128) {
-            const int z = e % TCZ, g = (e / TCZ) % kcz, y = e / (TCZ * kcz);
-            const bool in = g * 8 < P.Cout;
-            const bf16 *src = P.dZ;
-            if (in)
-                src = P.dZ + ((long long)i0 * nyz + (long long)(j0 + y) * P.nz + k0 + z) * P.Cout +
-                      g * 8;
-            cp_async16(sza + (unsigned)e * 16u, src, in);
+        const unsigned sza = smem_u32(smem + q * set_bytes), sha = sza + (unsigned)dz_bytes;
+        // dZ brick: [y][group][z][8 channels]; item e = ((y * gz) + g) * 8 + z
+        for (int e = t; e < TCY * gz * TCZ; e += 128) {
+            const int z = e & 7, g = (e >> 3) & (gz - 1), y = e >> (3 + lgz);
+            const bf16 *src = P.dZ + ((long long)i0 * nyz + (long long)(j0 + y) * P.nz + k0 + z) *
+                                         P.Cout + g * 8;
+            cp_async16(sza + (unsigned)(((y * kcz + g) * TCZ + z) * 16), src, true);
         }
-        // halo: [hx][hy][group][hz][8 channels], zero outside the grid and
-        // past the input's channels
-        for (int e = t; e < TC_HX * TC_HY * kch * TC_HZ; e += 128) {
-            const int hzz = e % TC_HZ, g = (e / TC_HZ) % kch, hyy = (e / (TC_HZ * kch)) % TC_HY,
-                      hxx = e / (TC_HZ * kch * TC_HY);
+        // halo: [hx][hy][group][hz][8 channels], zero outside the grid;
+        // item e = ((row * gh) + g) * 10 + hz with row = hx * 18 + hy
+        for (int e = t; e < TC_HX * TC_HY * gh * TC_HZ; e += 128) {
+            const int hzz = e % TC_HZ, rest = e / TC_HZ;
+            const int g = rest & (gh - 1), row = rest >> lgh;
+            const int hyy = row % TC_HY, hxx = row / TC_HY;
             const int ii = i0 + hxx - 1, jj = j0 + hyy - 1, kk = k0 + hzz - 1;
             const int c = ci0 + g * 8;
-            const bool in = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 &&
-                            kk < P.nz && c < Cin;
+            const bool in = ii >= 0 && ii < P.nx && jj >= 0 && jj < P.ny && kk >= 0 && kk < P.nz;
             const bf16 *src = P.A;
             if (in) {
                 if (c < P.Ca)
@@ -1145,21 +1159,48 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(WgradTcArgs P, int *err)
                     src = P.B + (((long long)(ii >> 1) * hy + (jj >> 1)) * hz + (kk >> 1)) * P.Cb +
                           (c - P.Ca);
             }
-            cp_async16(sha + (unsigned)e * 16u, src, in);
+            cp_async16(sha + (unsigned)((((row * kch) + g) * TC_HZ + hzz) * 16), src, in);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
+    };
+    // brick j of the chunk uses buffer set j % nbuf; its MMAs commit to
+    // mbarrier j % 2 (the j / 2-th completion of that barrier)
+    auto wait_mma = [&](int j) -> bool {
+        return mbar_wait(smem_u32(mbar + (j & 1)), (unsigned)((j >> 1) & 1));
+    };
+    if (nb > 0) stage(b0, 0);
+    for (int j = 0; j < nb; ++j) {
+        const int q = j % nbuf;
+        if (nbuf == 2) {
+            // the other set is free once brick j - 1's MMAs have completed
+            if (j >= 1 && !wait_mma(j - 1)) {
+                *sfail = 1;
+                atomicExch(err, 1);
+            }
+            __syncthreads();
+            if (*sfail) break;
+            if (j + 1 < nb) {
+                stage(b0 + j + 1, (j + 1) % 2);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (t == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned sza = smem_u32(smem + q * set_bytes), sha = sza + (unsigned)dz_bytes;
             // MN stride (SBO) between channel groups, K stride (LBO) between
             // the two z-columns of a K step
             const unsigned long long dz0 = tc_desc(sza, kcz * TCZ * 16, TCZ * 16);
             const unsigned long long dh0 = tc_desc(sha, kch * TC_HZ * 16, TC_HZ * 16);
-            for (int j = 0; j < ntap; ++j) {
-                const int tap = tap0 + j;
+            for (int jt = 0; jt < ntap; ++jt) {
+                const int tap = tap0 + jt;
                 const int da = tap / 9, db = (tap / 3) % 3, dc = tap % 3;
+#pragma unroll
                 for (int s2 = 0; s2 < TCY / 2; ++s2) {
                     // start addresses in 16-byte units
                     const unsigned long long oz = (unsigned long long)(2 * s2 * kcz * TCZ);
@@ -1167,31 +1208,41 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(WgradTcArgs P, int *err)
                         (unsigned long long)(((da * TC_HY + 2 * s2 + db) * kch) * TC_HZ + dc);
                     const unsigned long long ad = P.rows_co ? dz0 + oz : dh0 + oh;
                     const unsigned long long bd = P.rows_co ? dh0 + oh : dz0 + oz;
-                    const unsigned acc = (b > b0 || s2 > 0) ? 1u : 0u;
-                    tc_mma(tmem + (unsigned)(j * P.N), ad, bd, idesc, acc);
+                    const unsigned acc = (j > 0 || s2 > 0) ? 1u : 0u;
+                    tc_mma(tmem + (unsigned)(jt * P.N), ad, bd, idesc, acc);
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(bar) : "memory");
+                         :: "r"(smem_u32(mbar + (j & 1))) : "memory");
         }
-        ++issued;
+        if (nbuf == 1) {
+            // one buffer set: the next brick's copies wait for these MMAs
+            if (!wait_mma(j)) {
+                *sfail = 1;
+                atomicExch(err, 1);
+            }
+            __syncthreads();
+            if (*sfail) break;
+            if (j + 1 < nb) stage(b0 + j + 1, 0);
+        }
     }
     const bool failed_before = *sfail != 0;
     __syncthreads();
-    if (!failed_before && issued > 0 && !mbar_wait(bar, (unsigned)((issued - 1) & 1))) {
+    if (!failed_before && nb > 0 && nbuf == 2 && !wait_mma(nb - 1)) {
         *sfail = 1;
         atomicExch(err, 1);
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!*sfail && issued > 0) {
+    if (!*sfail && nb > 0) {
         const int m = 32 * w + lane;                    // row of D
-        for (int j = 0; j < ntap; ++j) {
-            const int tap = tap0 + j;
+        for (int jt = 0; jt < ntap; ++jt) {
+            const int tap = tap0 + jt;
             for (int n0 = 0; n0 < P.N; n0 += 32) {
                 unsigned r[32];
-                const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(j * P.N + n0);
+                const unsigned ta = tmem + ((unsigned)(32 * w) << 16) + (unsigned)(jt * P.N + n0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                     "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -1231,15 +1282,59 @@ __global__ void __launch_bounds__(128, 1) k_wgrad_tc(WgradTcArgs P, int *err)
     }
 }
 
-// out[i] = sum over b = 0, 1, ... of part[b][i], in that order (n entries
-// per part): the fixed-order reduction of per-block partial gradients.
-__global__ void k_sum_parts(const float *__restrict__ part, int nparts, long long n,
-                            float *__restrict__ out)
+// Fixed-order reductions of per-block partial gradients: out[i] = the sum
+// over b = 0, 1, ... of part[b][i] (n entries per part), always added in
+// the same order, so the result does not depend on how the blocks ran.
+
+// Few entries and many parts: block i sums entry i, each
+// thread the parts t, t + 256, ... in that order, then the threads in a
+// fixed tree.
+__global__ void __launch_bounds__(256) k_sum_parts_tree(const float *__restrict__ part,
+                                                        int nparts, int n,
+                                                        float *__restrict__ out)
+{
+    __shared__ float s_p[256];
+    const int i = blockIdx.x;
+    float s = 0.f;
+    for (int b = threadIdx.x; b < nparts; b += 256) s += part[(long long)b * n + i];
+    s_p[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s_p[threadIdx.x] += s_p[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = s_p[0];
+}
+
+// Many entries: n4 groups of 4 (n = 4 n4), 16-byte loads, eight
+// parts' loads in flight at a time, each entry's sum still taken in part
+// order.
+__global__ void k_sum_parts4(const float4 *__restrict__ part, int nparts, long long n4,
+                             float4 *__restrict__ out)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float s = 0.f;
-    for (int b = 0; b < nparts; ++b) s += part[(long long)b * n + i];
+    if (i >= n4) return;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    int b = 0;
+    for (; b + 8 <= nparts; b += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldg(part + (long long)(b + q) * n4 + i);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            s.x += v[q].x;
+            s.y += v[q].y;
+            s.z += v[q].z;
+            s.w += v[q].w;
+        }
+    }
+    for (; b < nparts; ++b) {
+        const float4 v = __ldg(part + (long long)b * n4 + i);
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+    }
     out[i] = s;
 }
 
@@ -1885,7 +1980,7 @@ void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf1
         const int groups = (27 + t.taps - 1) / t.taps;
         const int mt = t.rows_co ? 1 : (Cin_ + 127) / 128;
         t.nbricks = nx * (ny / TCY) * (nz / TCZ);
-        long long chunks = std::max(1, (2 * 152) / (groups * mt));
+        long long chunks = std::max(1, 152 / (groups * mt));     // one wave
         chunks = std::min<long long>(chunks, t.nbricks);
         chunks = std::min<long long>(chunks, std::max(1ll, n->part_cap / nw_));
         t.bricks_per_chunk = (int)((t.nbricks + chunks - 1) / chunks);
@@ -1893,7 +1988,9 @@ void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf1
         count_launch(2);
         k_wgrad_tc<<<dim3((unsigned)chunks, (unsigned)groups, (unsigned)mt), 128, WT_SMEM,
                      n->st>>>(t, n->d_err);
-        k_sum_parts<<<nblk(nw_), 256, 0, n->st>>>(n->part, (int)chunks, nw_, dW);
+        k_sum_parts4<<<nblk(nw_ / 4), 256, 0, n->st>>>(reinterpret_cast<const float4 *>(n->part),
+                                                        (int)chunks, nw_ / 4,
+                                                        reinterpret_cast<float4 *>(dW));
         return;
     }
     WgradArgs a;
@@ -1920,7 +2017,9 @@ void wgrad(vesis_net n, int nx, int ny, int nz, const bf16 *A, int Ca, const bf1
     const long long nw = 27ll * Cout * Cin;
     count_launch(2);
     k_wgrad<<<grid, 128, 0, n->st>>>(a);
-    k_sum_parts<<<nblk(nw), 256, 0, n->st>>>(n->part, (int)chunks, nw, dW);
+    k_sum_parts4<<<nblk(nw / 4), 256, 0, n->st>>>(reinterpret_cast<const float4 *>(n->part),
+                                                  (int)chunks, nw / 4,
+                                                  reinterpret_cast<float4 *>(dW));
 }
 
 // Forward pass of a crop; with labels, the loss partials and dz too.
@@ -2188,12 +2287,12 @@ int vesis_net_loss_grad(vesis_net n, const float *x_dev, const uint8_t *chi_dev,
     k_head_bwd<<<nblk(V[0]), 256, 0, st>>>(n->d[0], V[0], n->theta + L[L_HEAD].w_off, n->dz,
                                            n->gd[0], n->part);
     count_launch();
-    k_sum_parts<<<1, 64, 0, st>>>(n->part, (int)nblk(V[0]), 33, n->grad + L[L_HEAD].w_off);
+    k_sum_parts_tree<<<33, 256, 0, st>>>(n->part, (int)nblk(V[0]), 33, n->grad + L[L_HEAD].w_off);
     auto relu_bwd = [&](const float *g, const bf16 *y, long long Vl, int C, float *db) {
         count_launch(2);
         const long long nb = std::min<long long>(nblk(Vl * C), 4 * 152);
         k_relu_bwd<<<(unsigned)nb, 256, 0, st>>>(g, y, Vl, C, n->dZ, n->part);
-        k_sum_parts<<<1, 128, 0, st>>>(n->part, (int)nb, C, db);
+        k_sum_parts_tree<<<C, 256, 0, st>>>(n->part, (int)nb, C, db);
     };
     auto unpack = [&](int l) {
         Layer &y = L[l];
