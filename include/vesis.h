@@ -124,7 +124,21 @@ typedef struct {
                               total at the final state */
     double M;              /* final mobility factor */
     double max_grad;       /* max |dG/dr| at the last gradient evaluation */
+    int records;           /* per-iteration records written (vesis_set_history) */
 } vesis_relax_stats;
+
+/* One accepted outer iteration of vesis_relax (Sec. 3.3, Steps 2-4). */
+typedef struct {
+    int k;              /* the iterate's number (1, 2, ...; continues on resume) */
+    int rounds;         /* flip rounds of the iteration's interface relaxation */
+    long long flips;    /* cells flipped by it */
+    int trials;         /* trial positions evaluated: rejections + the accept */
+    int ncnt;           /* N_cnt after the accept */
+    double G;           /* total G at the accepted iterate (Gamma^{k}, R^{k}) */
+    double G_old;       /* total G at (Gamma^{k}, R^{k-1}), before the step */
+    double M;           /* mobility factor after the step */
+    double max_grad;    /* max |dG/dr| that set the step (Eq. adjustmml) */
+} vesis_iter_record;
 
 typedef struct vesis_system_t *vesis_system;
 
@@ -305,6 +319,14 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
  * first poll that finds the barrier still open, which makes the failure
  * path testable without any fault.  VESIS_E_ARG for polls < 0. */
 int vesis_set_wait_limit(vesis_system s, long long polls);
+
+/* Per-iteration log: every later vesis_relax on the system writes one
+ * record per accepted outer iteration into records (host memory, kept by
+ * the caller until the log is replaced or the system destroyed), the
+ * first `capacity` of them; stats->records counts those written by a
+ * call.  records = NULL or capacity = 0 turns the log off.  VESIS_E_ARG
+ * for capacity < 0. */
+int vesis_set_history(vesis_system s, vesis_iter_record *records, int capacity);
 
 /* The system's relaxation state: written by every vesis_relax that ends
  * with status >= 0 (cleared to valid = 0 by one that fails), read by

@@ -15,10 +15,21 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "vesis.h"
 #include "vesis_internal.cuh"
 
 using namespace vesis;
+
+namespace {
+// NVTX range over a scope: the phases of a relaxation show up by name in a
+// profiler's timeline (no cost without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 #include <atomic>
 
@@ -246,6 +257,8 @@ struct vesis_system_t {
     RoundState *d_rs = nullptr;
     GdState *d_gd = nullptr;
     vesis_relax_state rstate{};   // where the last relaxation stopped
+    vesis_iter_record *hist = nullptr;   // caller's per-iteration log (host)
+    int hist_cap = 0;
 
     // pinned host mirrors
     double *h_scal = nullptr;
@@ -1393,18 +1406,25 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     double gmax = 0.0;
     while (k < o.max_outer) {
         RoundState rs;
-        VTRY(run_blsm(s, chi_dev, s->d_U[cur], o.max_flip_rounds, &rs, true));
+        {
+            NvtxRange range("vesis: flip sweep");
+            VTRY(run_blsm(s, chi_dev, s->d_U[cur], o.max_flip_rounds, &rs, true));
+        }
         st.flip_rounds += rs.round;
         st.flips += (long long)rs.total_flips;
         // Step 3.1-3.2: gradient and G_old at (Gamma^{k+1}, R^k); the
         // solute-solute terms at R^k are current (the start or the accepted
         // trial evaluated them last)
-        enq_gradient(s, chi_dev, s->d_E[cur], s->d_xyz, bank(s, cur), true);
-        enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur), true);
-        VTRY(last_launch("relax gradient"));
-        VCK(cudaMemcpyAsync(s->h_u64, s->d_gmax, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, s->st));
-        VTRY(read_bank(s, bank(s, cur)));
+        {
+            NvtxRange range("vesis: gradient");
+            enq_gradient(s, chi_dev, s->d_E[cur], s->d_xyz, bank(s, cur), true);
+            enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur), true);
+            VTRY(last_launch("relax gradient"));
+            VCK(cudaMemcpyAsync(s->h_u64, s->d_gmax, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, s->st));
+            VTRY(read_bank(s, bank(s, cur)));
+        }
+        const double G_old = s->h_scal[S_TOTAL];
         std::memcpy(&gmax, s->h_u64, sizeof(double));
         st.pair_evals += (s->G - (long long)s->h_scal[S_NSOL]) * s->n + FN;
         if (!std::isfinite(gmax) || gmax >= 1.0e308) {
@@ -1419,28 +1439,31 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
         int retries = 0;
         bool accepted = false;
         double G_new = 0.0;
-        while (!accepted) {
-            launch_mobility(s->d_xyz, s->d_grad, s->d_gmax, &s->d_gd->M,
-                            s->d_xyz_new, 3 * s->n, s->st);
-            enq_pack(s, s->d_xyz_new);
-            enq_fields(s, s->d_U[trial], s->d_E[trial], bank(s, trial));
-            enq_ss(s, s->d_xyz_new, bank(s, trial));
-            enq_terms(s, chi_dev, s->d_U[trial], s->d_E[trial], bank(s, trial), true);
-            count_launch();
-            k_gd_decide<<<1, 1, 0, s->st>>>(s->d_gd, bank(s, cur), bank(s, trial),
-                                            s->d_oob, o.ncnt_star, o.dgstar_frac,
-                                            o.alpha);
-            VTRY(last_launch("relax trial"));
-            VCK(cudaMemcpyAsync(s->h_gd, s->d_gd, sizeof(GdState),
-                                cudaMemcpyDeviceToHost, s->st));
-            VTRY(read_bank(s, bank(s, trial)));
-            st.gd_trials += 1;
-            st.pair_evals += GN + FN + NN;
-            if (s->h_gd->decision == 0) {
-                accepted = true;
-                G_new = s->h_scal[S_TOTAL];
-            } else if (++retries > o.max_gd_retries) {
-                break;
+        {
+            NvtxRange range("vesis: trial steps");
+            while (!accepted) {
+                launch_mobility(s->d_xyz, s->d_grad, s->d_gmax, &s->d_gd->M,
+                                s->d_xyz_new, 3 * s->n, s->st);
+                enq_pack(s, s->d_xyz_new);
+                enq_fields(s, s->d_U[trial], s->d_E[trial], bank(s, trial));
+                enq_ss(s, s->d_xyz_new, bank(s, trial));
+                enq_terms(s, chi_dev, s->d_U[trial], s->d_E[trial], bank(s, trial), true);
+                count_launch();
+                k_gd_decide<<<1, 1, 0, s->st>>>(s->d_gd, bank(s, cur), bank(s, trial),
+                                                s->d_oob, o.ncnt_star, o.dgstar_frac,
+                                                o.alpha);
+                VTRY(last_launch("relax trial"));
+                VCK(cudaMemcpyAsync(s->h_gd, s->d_gd, sizeof(GdState),
+                                    cudaMemcpyDeviceToHost, s->st));
+                VTRY(read_bank(s, bank(s, trial)));
+                st.gd_trials += 1;
+                st.pair_evals += GN + FN + NN;
+                if (s->h_gd->decision == 0) {
+                    accepted = true;
+                    G_new = s->h_scal[S_TOTAL];
+                } else if (++retries > o.max_gd_retries) {
+                    break;
+                }
             }
         }
         if (!accepted) {
@@ -1452,6 +1475,18 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
         std::swap(cur, trial);
         std::swap(s->d_xyz, s->d_xyz_new);
         ++k;
+        if (s->hist && st.records < s->hist_cap) {
+            vesis_iter_record &rec = s->hist[st.records++];
+            rec.k = k;
+            rec.rounds = rs.round;
+            rec.flips = (long long)rs.total_flips;
+            rec.trials = retries + 1;
+            rec.ncnt = s->h_gd->ncnt;
+            rec.G = G_new;
+            rec.G_old = G_old;
+            rec.M = s->h_gd->M;
+            rec.max_grad = gmax;
+        }
         // Steps 4-5: energy change between consecutive accepted iterates
         const double d_abs = std::fabs(G_new - G_prev);
         const double d_rel = G_new != 0.0 ? d_abs / std::fabs(G_new) : INFINITY;
@@ -1493,6 +1528,15 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     st.max_grad = gmax;
     if (stats_out) *stats_out = st;
     return status;
+}
+
+int vesis_set_history(vesis_system s, vesis_iter_record *records, int capacity)
+{
+    if (!s) return fail(VESIS_E_ARG, "NULL system");
+    if (capacity < 0) return fail(VESIS_E_ARG, "capacity must be >= 0");
+    s->hist = capacity > 0 ? records : nullptr;
+    s->hist_cap = records ? capacity : 0;
+    return VESIS_OK;
 }
 
 int vesis_get_state(vesis_system s, vesis_relax_state *out)

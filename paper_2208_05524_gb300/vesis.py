@@ -43,7 +43,12 @@ class RelaxStats(C.Structure):
     _fields_ = [("status", _i), ("iterations", _i), ("stop_reason", _i),
                 ("flip_rounds", _ll), ("flips", _ll), ("gd_trials", _ll),
                 ("pair_evals", _ll), ("G", _d), ("terms", _d * 6), ("M", _d),
-                ("max_grad", _d)]
+                ("max_grad", _d), ("records", _i)]
+
+
+class IterRecord(C.Structure):
+    _fields_ = [("k", _i), ("rounds", _i), ("flips", _ll), ("trials", _i), ("ncnt", _i),
+                ("G", _d), ("G_old", _d), ("M", _d), ("max_grad", _d)]
 
 
 class Timing(C.Structure):
@@ -106,6 +111,7 @@ def lib():
         L.vesis_set_wait_limit.argtypes = [_p, _ll]
         L.vesis_get_state.argtypes = [_p, C.POINTER(RelaxState)]
         L.vesis_blsm_relax_batch.argtypes = [_i, _p, _p, _p, _i, _p, _p, _p]
+        L.vesis_set_history.argtypes = [_p, _p, _i]
         L.vesis_set_state.argtypes = [_p, C.POINTER(RelaxState)]
         L.vesis_features.argtypes = [_p, _p, _p, _p, _d, _p]
         L.vesis_ss_terms.argtypes = [_p, _p]
@@ -342,6 +348,14 @@ class System:
         _check(lib().vesis_get_timing(self.h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in Timing._fields_}
 
+    def set_history(self, capacity):
+        """Per-iteration log of later relax calls (vesis_set_history): up to
+        `capacity` records, returned by relax() as res["history"]; 0 turns
+        it off."""
+        self._hist = (IterRecord * capacity)() if capacity > 0 else None
+        _check(lib().vesis_set_history(self.h, C.cast(self._hist, _p) if capacity else None,
+                                       int(capacity)))
+
     def get_state(self):
         """Where the last relaxation stopped (vesis_get_state), as a dict."""
         st = RelaxState()
@@ -418,6 +432,9 @@ class System:
         res["terms"] = dict(zip(TERMS, list(st.terms)))
         res["status"] = rc
         res["xyz"] = x
+        if getattr(self, "_hist", None) is not None:
+            res["history"] = [{f: getattr(r, f) for f, _ in IterRecord._fields_}
+                              for r in self._hist[:st.records]]
         return res
 
 

@@ -279,10 +279,20 @@ def test_relax_charged_multi_atom_lock_step_matches_oracle():
     hist = ro["history"]
     assert any(h["retries"] > 0 for h in hist)        # rejected trials occur
     S = vs.System(s)
+    S.set_history(8)
     chi0 = O.init_labels(s)
     chi = _dev(chi0.reshape(-1), torch.uint8)
     r = S.relax(chi, s["xyz"], max_outer=5)
-    assert r["iterations"] == 5
+    assert r["iterations"] == 5 and r["records"] == 5
+    # iteration by iteration: the sweep, the step that set the mobility, the
+    # trials, N_cnt, M and the energies before and after the step
+    for a, b in zip(r["history"], hist):
+        assert (a["k"], a["rounds"], a["flips"], a["trials"], a["ncnt"]) == \
+            (b["k"], b["rounds"], b["flips"], b["retries"] + 1, b["ncnt"])
+        assert a["M"] == b["M"]
+        assert a["G"] == pytest.approx(b["G"], rel=1e-6)
+        assert a["G_old"] == pytest.approx(b["G_old"], rel=1e-6)
+        assert a["max_grad"] == pytest.approx(b["gmax"], rel=1e-4)
     assert r["gd_trials"] == sum(h["retries"] + 1 for h in hist)
     assert r["flip_rounds"] == sum(h["rounds"] for h in hist)
     assert r["flips"] == sum(h["flips"] for h in hist)

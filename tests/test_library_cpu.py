@@ -64,7 +64,8 @@ def _c_layout(struct, fields):
                                           ("vesis_relax_opts", "RelaxOpts"),
                                           ("vesis_relax_stats", "RelaxStats"),
                                           ("vesis_timing", "Timing"),
-                                          ("vesis_relax_state", "RelaxState")])
+                                          ("vesis_relax_state", "RelaxState"),
+                                          ("vesis_iter_record", "IterRecord")])
 def test_struct_layouts_match_header(tmp_path, built, cname, pyname):
     from paper_2208_05524_gb300 import vesis
     cls = getattr(vesis, pyname)
