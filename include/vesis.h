@@ -320,6 +320,21 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
  * path testable without any fault.  VESIS_E_ARG for polls < 0. */
 int vesis_set_wait_limit(vesis_system s, long long polls);
 
+/* Which tiles a round of the flip sweep decides.  A leader's verdict (Sec.
+ * 3.1, Step 2, in the brick-leader form) depends only on the leader words
+ * within r of it, so a tile none of whose 27 neighbouring tiles changed a
+ * leader word in the previous round keeps its previous verdict (it lost)
+ * and need not be decided again; the updates stamp the tiles whose
+ * neighbourhood changed.  mode -1 (the default): stamps are written while
+ * the tiles holding a leader outnumber the sweep's warps, and read by a
+ * block whose own leader tiles outnumber its warps; 0: never (every tile
+ * holding a leader is decided every round); 1: always.  The rounds,
+ * flips, labels and energies are identical in every mode; only the time
+ * differs.  Applies to later vesis_blsm_relax, vesis_relax and (through
+ * the first system) vesis_blsm_relax_batch calls.  VESIS_E_ARG for another
+ * mode or a NULL system. */
+int vesis_set_sweep_stamps(vesis_system s, int mode);
+
 /* Per-iteration log: every later vesis_relax on the system writes one
  * record per accepted outer iteration into records (host memory, kept by
  * the caller until the log is replaced or the system destroyed), the

@@ -242,6 +242,7 @@ struct vesis_system_t {
     // persistent sweep state
     int sweep_blocks = 0, ntiles = 0;
     long long spin_limit = kSweepSpinLimit;   // polls of a sweep barrier wait
+    int sweep_stamps = -1;                    // decide stamps of the sweep (-1, 0, 1)
     uint8_t *d_sweep = nullptr;
     uint8_t *d_heap = nullptr;      // tile and group keys of the serial flipping
     long long *d_heap_out = nullptr;   // flips, dE sum (as bits), capped
@@ -479,7 +480,7 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
     VCK(launch_sweep(s->g, s->kw, s->d_k3, s->fc, chi, s->d_W, U, s->d_dE, s->d_sweep,
                      s->d_ctl, s->d_err, s->d_part_flips,
                      s->d_part_dE, s->d_part_tiles, s->d_rounds, s->d_capped, max_rounds,
-                     blocks, s->spin_limit, s->d_rs, s->st));
+                     blocks, s->spin_limit, s->sweep_stamps, s->d_rs, s->st));
     span_end(s, sp, 2, 0, 0);
     VCK(cudaMemcpyAsync(s->h_rs, s->d_rs, sizeof(RoundState),
                         cudaMemcpyDeviceToHost, s->st));
@@ -1177,7 +1178,7 @@ int vesis_blsm_relax_batch(int nsys, vesis_system *systems, uint8_t *const *chi_
     } free_scratch{scratch};
     cudaStream_t st = s0->st;
     VCK(launch_sweep_multi(nsys, ys.data(), s0->kw, s0->d_k3, max_rounds, s0->sweep_blocks,
-                           s0->spin_limit, scratch, s0->h_int, st));
+                           s0->spin_limit, s0->sweep_stamps, scratch, s0->h_int, st));
     VCK(cudaStreamSynchronize(st));
     if (*s0->h_int) return fail(VESIS_E_CUDA, "flip sweep grid barrier timed out");
     int rc = VESIS_OK;
@@ -1562,6 +1563,14 @@ int vesis_set_wait_limit(vesis_system s, long long polls)
     if (!s) return fail(VESIS_E_ARG, "NULL system");
     if (polls < 0) return fail(VESIS_E_ARG, "polls must be >= 0");
     s->spin_limit = polls;
+    return VESIS_OK;
+}
+
+int vesis_set_sweep_stamps(vesis_system s, int mode)
+{
+    if (!s) return fail(VESIS_E_ARG, "NULL system");
+    if (mode < -1 || mode > 1) return fail(VESIS_E_ARG, "mode must be -1, 0 or 1");
+    s->sweep_stamps = mode;
     return VESIS_OK;
 }
 

@@ -38,6 +38,20 @@
 // The sweep stops when no tile holds a leader or after max_rounds rounds.
 // An opening pass computes every tile's leaders from the starting labels.
 //
+// Only tiles whose verdict can change are decided: a leader's verdict is a
+// function of the leader words within r of it, all inside the 27 tiles
+// around its own, so a tile none of whose 27 neighbours (itself included)
+// changed a leader word in the last update keeps its last verdict - it
+// lost (a winner changes its own tile's words) - and is skipped.  Every
+// update that changes one of the tile's words stamps its 27 neighbours with
+// the next round; round 0 decides every tile.  The winners, and so the
+// rounds and labels, are those of deciding every tile every round.  The
+// stamps only pay where warps have several tiles: the updates write them
+// while the tiles holding a leader outnumber the grid's warps (a count all
+// blocks read alike), and a block reads them only after such an update and
+// when its own leader tiles outnumber its warps (deciding an unstamped tile
+// is harmless).
+//
 // The grid barrier spins with a bound; on timeout it raises an error flag
 // and every block returns.
 #include <vector>
@@ -63,6 +77,10 @@ constexpr int kNbh3 = kNbh * kNbh * kNbh;
 // Winners within r of a tile are more than r apart inside a box of edge
 // 8 + 2r: at most ceil((8 + 2r) / (r + 1))^3 <= 125 of them.
 constexpr int kMaxWin = 128;
+// Tiles a thread examines per pass when a block lists its tiles: one pass
+// lists up to SW_THREADS * kGatherPer of them.
+constexpr int kGatherPer = 4;
+constexpr int kListCap = SW_THREADS * kGatherPer;
 // Posting area of a tile: 216 16-bit slots and an 8-word slot bitmap.
 constexpr int kPostBytes = 512;
 constexpr int kPostMaskOff = 448;
@@ -94,6 +112,7 @@ struct SweepArgs {
     int nzw;
     uint8_t *post;            // posting area per tile (kPostBytes)
     uint8_t *upd;             // tile received a winner this round
+    int *dirty;               // per tile: the round whose decide must visit it
     int ntx, nty, ntz;
     int bs, bsh;        // brick edge and its log2
     int reach;          // ceil(r / B)
@@ -109,6 +128,7 @@ struct SweepArgs {
     int *capped_out;
     int max_rounds;
     long long spin_limit;     // polls before a barrier wait gives up
+    int stamps;               // decide stamps: -1 by the leader count, 0 never, 1 always
     RoundState *rs;           // this system's totals (multi-system sweep)
     double *tile_dE;          // per tile: its winners' dE, summed over rounds (multi)
     unsigned *tile_nf;        // per tile: its flips (multi)
@@ -379,11 +399,13 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
 }
 
 // Update phase for tile t (one warp).  first: the opening pass (no
-// winners; every tile computes its leaders).
+// winners; every tile computes its leaders).  mark >= 0: if a leader word
+// of the tile changes, the 27 tiles around it (itself included) are
+// stamped with mark, the round whose decide must visit them.
 template <bool STENCIL>
 __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, const int *qw,
                                             const int *kt,
-                                            int t, bool first)
+                                            int t, bool first, int mark)
 {
     const int lane = threadIdx.x & 31;
     const GridDesc &g = A.g;
@@ -458,6 +480,19 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
                     hb[u] = lo | (((vm >> sh) & 0xffu) << 1) | (hi << 9);
                 }
             }
+        }
+    }
+    // the tile's leader words before this update (brick b = lane + 32 h)
+    unsigned long long oldw[2] = {0ull, 0ull};
+    if (mark >= 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int b = lane + 32 * h;
+            if (b >= nbt) continue;
+            const int gx = (i0 >> bsh) + b / (bpt * bpt), gy = (j0 >> bsh) + (b / bpt) % bpt,
+                      gz = (k0 >> bsh) + b % bpt;
+            if (gx < A.nbx && gy < A.nby && gz < A.nbz)
+                oldw[h] = __ldcg(A.PL + ((long long)gx * A.nby + gy) * A.nbz + gz);
         }
     }
     // posted winners: slot bitmap (lanes 0..7) and the 216 slots (lanes x 4 per u64)
@@ -641,13 +676,17 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
         }
     }
     __syncwarp();
-    bool any = false;
-    for (int b = lane; b < nbt; b += 32) {
+    bool any = false, changed = false;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int b = lane + 32 * h;
+        if (b >= nbt) continue;
         const int bx = b / (bpt * bpt), by = (b / bpt) % bpt, bz = b % bpt;
         const int gx = (i0 >> bsh) + bx, gy = (j0 >> bsh) + by, gz = (k0 >> bsh) + bz;
         if (gx >= A.nbx || gy >= A.nby || gz >= A.nbz) continue;
         const unsigned long long w = M.u.bmax[b];
         const long long o = ((long long)gx * A.nby + gy) * A.nbz + gz;
+        changed |= w != oldw[h];
         A.PL[o] = w;
         if (w != 0ull) {
             int ci, cj, ck;
@@ -657,46 +696,70 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
         }
         any |= w != 0ull;
     }
+    if (mark >= 0 && __any_sync(0xffffffffu, changed) && lane < 27) {
+        const int tk = t % A.ntz, tj = (t / A.ntz) % A.nty, ti = t / (A.ntz * A.nty);
+        const int a = ti + lane / 9 - 1, b = tj + (lane / 3) % 3 - 1, c = tk + lane % 3 - 1;
+        if (a >= 0 && b >= 0 && c >= 0 && a < A.ntx && b < A.nty && c < A.ntz)
+            A.dirty[(a * A.nty + b) * A.ntz + c] = mark;
+    }
     return __any_sync(0xffffffffu, any);
 }
 
 struct SweepShared {
     unsigned own[kOwnWords];   // own tile j = (t - blockIdx.x) / gridDim.x holds a leader
-    int list[SW_THREADS];
+    int list[kListCap];
     int wc[NWARP];
     int qw[2 * kMaxR + 1];
     double e[NWARP];
     unsigned nf[NWARP];
     unsigned ncnt;
+    int nown;                  // own tiles holding a leader
     int abort_flag;
 };
 
-// Collects, in increasing order, this block's tiles t = blockIdx.x + k *
-// gridDim.x (k in [base, base + SW_THREADS)) whose flag is set (clearing
-// those flags if `clear`; flags = NULL: every tile); returns the count
-// (list in S.list).  With cntp, thread 0 also reads that counter into
-// S.ncnt.
-__device__ int gather_tiles(SweepShared &S, uint8_t *flags, bool clear, int base,
-                            int ntiles, const unsigned *cntp)
+// Lists this block's tiles t = blockIdx.x + j * gridDim.x, j in [base,
+// base + kListCap), for which pick(j, t) holds, in a fixed order (thread i
+// examines j = base + i + c * SW_THREADS, c < kGatherPer, and its picks
+// follow those of threads i' < i); returns the count (list in S.list).
+// pick is called once per j < limit with t < ntiles; it may clear a flag.
+template <class Pick>
+__device__ int list_tiles(SweepShared &S, int base, int limit, long long ntiles, Pick pick)
 {
-    const int k = base + threadIdx.x;
-    const long long t = (long long)blockIdx.x + (long long)k * gridDim.x;
-    unsigned c = 0u;
-    if (cntp && threadIdx.x == 0) c = ld_relaxed_u32(cntp);
-    bool fl = false;
-    if (t < ntiles) {
-        if (flags) {
-            fl = __ldcg(flags + t) != 0;
-            if (fl && clear) flags[t] = 0;
-        } else {
-            fl = true;
-        }
-    }
-    const unsigned b = __ballot_sync(0xffffffffu, fl);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (limit - base <= SW_THREADS) {    // one tile per thread: a ballot orders them
+        const int j = base + threadIdx.x;
+        const long long t = (long long)blockIdx.x + (long long)j * gridDim.x;
+        const bool fl = j < limit && t < ntiles && pick(j, (int)t);
+        const unsigned b = __ballot_sync(0xffffffffu, fl);
+        __syncthreads();      // the previous list is no longer read
+        if (lane == 0) S.wc[wp] = __popc(b);
+        __syncthreads();
+        int off = 0, tot = 0;
+#pragma unroll
+        for (int q = 0; q < NWARP; ++q) {
+            if (q < wp) off += S.wc[q];
+            tot += S.wc[q];
+        }
+        if (fl) S.list[off + __popc(b & ((1u << lane) - 1u))] = (int)t;
+        __syncthreads();
+        return tot;
+    }
+    unsigned m = 0u;
+#pragma unroll
+    for (int c = 0; c < kGatherPer; ++c) {
+        const int j = base + threadIdx.x + c * SW_THREADS;
+        const long long t = (long long)blockIdx.x + (long long)j * gridDim.x;
+        if (j < limit && t < ntiles && pick(j, (int)t)) m |= 1u << c;
+    }
+    const int cnt = __popc(m);
+    int incl = cnt;   // inclusive warp scan of the counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
     __syncthreads();          // the previous list is no longer read
-    if (lane == 0) S.wc[wp] = __popc(b);
-    if (cntp && threadIdx.x == 0) S.ncnt = c;
+    if (lane == 31) S.wc[wp] = incl;
     __syncthreads();
     int off = 0, tot = 0;
 #pragma unroll
@@ -704,30 +767,20 @@ __device__ int gather_tiles(SweepShared &S, uint8_t *flags, bool clear, int base
         if (q < wp) off += S.wc[q];
         tot += S.wc[q];
     }
-    if (fl) S.list[off + __popc(b & ((1u << lane) - 1u))] = (int)t;
+    int pos = off + incl - cnt;
+#pragma unroll
+    for (int c = 0; c < kGatherPer; ++c)
+        if ((m >> c) & 1u)
+            S.list[pos++] = (int)(blockIdx.x + (long long)(base + threadIdx.x + c * SW_THREADS) *
+                                                   gridDim.x);
     __syncthreads();
     return tot;
 }
 
-// Same as gather_tiles for the block's own tiles whose bit is set in S.own.
-__device__ int own_list(SweepShared &S, int base, int per_block)
+// Whether own tile j holds a leader.
+__device__ __forceinline__ bool own_bit(const SweepShared &S, int j)
 {
-    const int j = base + threadIdx.x;
-    const bool fl = j < per_block && ((S.own[j >> 5] >> (j & 31)) & 1u);
-    const unsigned b = __ballot_sync(0xffffffffu, fl);
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    __syncthreads();          // the previous list is no longer read
-    if (lane == 0) S.wc[wp] = __popc(b);
-    __syncthreads();
-    int off = 0, tot = 0;
-#pragma unroll
-    for (int q = 0; q < NWARP; ++q) {
-        if (q < wp) off += S.wc[q];
-        tot += S.wc[q];
-    }
-    if (fl) S.list[off + __popc(b & ((1u << lane) - 1u))] = (int)(blockIdx.x + (long long)j * gridDim.x);
-    __syncthreads();
-    return tot;
+    return (S.own[j >> 5] >> (j & 31)) & 1u;
 }
 
 // Records whether own tile t holds a leader, keeping the global count.
@@ -739,6 +792,7 @@ __device__ __forceinline__ void set_own(const SweepArgs &A, SweepShared &S, int 
     if (now == old) return;
     if (now) atomicOr(&S.own[j >> 5], bit);
     else atomicAnd(&S.own[j >> 5], ~bit);
+    atomicAdd(&S.nown, now ? 1 : -1);
     red_add(A.nlead, now ? 1u : 0xffffffffu);
 }
 
@@ -764,6 +818,7 @@ k_sweep(SweepArgs A)
     if (threadIdx.x == 0) {
         S.abort_flag = 0;
         S.ncnt = 1u;
+        S.nown = 0;
     }
     __syncthreads();
     unsigned target = 0;      // thread 0: arrivals the next barrier waits for
@@ -771,12 +826,13 @@ k_sweep(SweepArgs A)
     unsigned n_lane = 0;
     unsigned long long t_dec = 0, t_upd = 0;   // thread 0: tiles visited per phase
     int round = 0, capped = 0;
+    bool marked = false;      // the last update stamped the tiles to decide
     // opening pass: leaders of the starting labels
-    for (int base = 0; base < per_block; base += SW_THREADS) {
-        const int n = gather_tiles(S, nullptr, false, base, ntiles, nullptr);
+    for (int base = 0; base < per_block; base += kListCap) {
+        const int n = list_tiles(S, base, per_block, ntiles, [](int, int) { return true; });
         for (int q = wp; q < n; q += NWARP) {
             const int t = S.list[q];
-            const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, true);
+            const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, true, -1);
             if (lane == 0) set_own(A, S, t, now);
         }
     }
@@ -791,8 +847,11 @@ k_sweep(SweepArgs A)
         // changes in the update phases)
         unsigned nl = 1u;
         if (threadIdx.x == 0) nl = ld_relaxed_u32(A.nlead);
-        for (int base = 0; base < per_block; base += SW_THREADS) {
-            const int n = own_list(S, base, per_block);
+        const bool stamped = marked && (A.stamps > 0 || S.nown > NWARP);
+        for (int base = 0; base < per_block; base += kListCap) {
+            const int n = list_tiles(S, base, per_block, ntiles, [&](int j, int t) {
+                return own_bit(S, j) && (!stamped || __ldcg(A.dirty + t) == k);
+            });
             t_dec += (unsigned long long)n;
             for (int q = wp; q < n; q += NWARP) tile_decide(A, M, S.list[q], e_lane, n_lane);
         }
@@ -803,13 +862,19 @@ k_sweep(SweepArgs A)
             break;
         }
         if (!grid_barrier(A.bar, A.err, A.spin_limit, target, &S.abort_flag)) return;
-        // update
-        for (int base = 0; base < per_block; base += SW_THREADS) {
-            const int n = gather_tiles(S, A.upd, true, base, ntiles, nullptr);
+        // update (S.ncnt: the leader tiles of this round, alike in every block)
+        marked = A.stamps > 0 || (A.stamps < 0 && S.ncnt > (unsigned)(NWARP * gridDim.x));
+        const int mark = marked ? k + 1 : -1;
+        for (int base = 0; base < per_block; base += kListCap) {
+            const int n = list_tiles(S, base, per_block, ntiles, [&](int, int t) {
+                const bool f = __ldcg(A.upd + t) != 0;
+                if (f) A.upd[t] = 0;
+                return f;
+            });
             t_upd += (unsigned long long)n;
             for (int q = wp; q < n; q += NWARP) {
                 const int t = S.list[q];
-                const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, false);
+                const bool now = tile_update<STENCIL>(A, M, S.qw, kt, t, false, mark);
                 if (lane == 0) set_own(A, S, t, now);
             }
         }
@@ -884,13 +949,13 @@ long long sweep_bricks(const GridDesc &g, int r)
 static size_t pad256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Sweep state: leader words, leader offsets, the per-tile posting areas,
-// the update flags and the label bits.
+// the update flags, the decide stamps and the label bits.
 size_t sweep_state_bytes(const GridDesc &g, int r)
 {
     const size_t nt = (size_t)sweep_tiles(g);
     const size_t nb = (size_t)sweep_bricks(g, r);
     const size_t nzw = ((size_t)g.nz + 31) / 32;
-    return nb * 8 + pad256(nb) + nt * kPostBytes + pad256(nt) +
+    return nb * 8 + pad256(nb) + nt * kPostBytes + pad256(nt) + pad256(nt * 4) +
            (size_t)g.nx * g.ny * nzw * 4;
 }
 
@@ -976,7 +1041,8 @@ static SweepArgs sweep_setup(const GridDesc &g, const KernelW &kw, const int *k3
     A.PO = base + nb * 8;
     A.post = A.PO + pad256(nb);
     A.upd = A.post + nt * kPostBytes;
-    A.CB = reinterpret_cast<unsigned *>(A.upd + pad256(nt));
+    A.dirty = reinterpret_cast<int *>(A.upd + pad256(nt));
+    A.CB = reinterpret_cast<unsigned *>(A.upd + pad256(nt) + pad256(nt * 4));
     A.nzw = (g.nz + 31) / 32;
     A.nlead = ctl;
     A.bar = ctl + kLine;
@@ -988,12 +1054,14 @@ static SweepArgs sweep_setup(const GridDesc &g, const KernelW &kw, const int *k3
     A.capped_out = nullptr;
     A.max_rounds = max_rounds;
     A.spin_limit = spin_limit;
+    A.stamps = -1;
     A.rs = nullptr;
     A.tile_dE = nullptr;
     A.tile_nf = nullptr;
     // postings start empty (a slot is only read under its bitmap bit)
     cudaMemset2DAsync(A.post + kPostMaskOff, kPostBytes, 0, 32, nt, st);
     cudaMemsetAsync(A.upd, 0, nt, st);
+    cudaMemsetAsync(A.dirty, 0, nt * 4, st);
     cudaMemsetAsync(ctl, 0, sweep_ctl_words() * sizeof(unsigned), st);
     cudaMemsetAsync(err, 0, sizeof(int), st);
     {
@@ -1012,7 +1080,7 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
                          unsigned long long *part_flips, double *part_dE,
                          unsigned long long *part_tiles,
                          int *rounds, int *capped, int max_rounds, int blocks,
-                         long long spin_limit, RoundState *rs, cudaStream_t st)
+                         long long spin_limit, int stamps, RoundState *rs, cudaStream_t st)
 {
     {
         const size_t nt = (size_t)sweep_tiles(g);
@@ -1025,6 +1093,7 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
     A.part_tiles = part_tiles;
     A.rounds_out = rounds;
     A.capped_out = capped;
+    A.stamps = stamps;
     void *args[] = {&A};
     count_launch();
     cudaError_t e = cudaLaunchCooperativeKernel(k3 ? (void *)k_sweep<true> : (void *)k_sweep<false>,
@@ -1064,6 +1133,7 @@ struct MultiArgs {
     int *capped;              // [nsys]
     int max_rounds;
     long long spin_limit;
+    int stamps;               // as SweepArgs::stamps, for all systems
     KernelW kw;
     const int *k3;
 };
@@ -1079,34 +1149,18 @@ __device__ __forceinline__ int sys_of(const long long *toff, int nsys, long long
     return lo;
 }
 
-// gather_tiles over the global tile numbers, each flag read (and cleared)
-// in its own system's update flags.
+// The block's tiles that received a winner, over the global tile numbers,
+// each flag read (and cleared) in its own system's update flags.
 __device__ int gather_tiles_multi(SweepShared &S, const SweepArgs *sys, const long long *toff,
-                                  int nsys, int base, int ntiles)
+                                  int nsys, int base, int per_block, int ntiles)
 {
-    const int k = base + threadIdx.x;
-    const long long t = (long long)blockIdx.x + (long long)k * gridDim.x;
-    bool fl = false;
-    if (t < ntiles) {
+    return list_tiles(S, base, per_block, ntiles, [&](int, int t) {
         const int q = sys_of(toff, nsys, t);
         uint8_t *f = sys[q].upd + (t - toff[q]);
-        fl = __ldcg(f) != 0;
+        const bool fl = __ldcg(f) != 0;
         if (fl) *f = 0;
-    }
-    const unsigned b = __ballot_sync(0xffffffffu, fl);
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    __syncthreads();          // the previous list is no longer read
-    if (lane == 0) S.wc[wp] = __popc(b);
-    __syncthreads();
-    int off = 0, tot = 0;
-#pragma unroll
-    for (int q = 0; q < NWARP; ++q) {
-        if (q < wp) off += S.wc[q];
-        tot += S.wc[q];
-    }
-    if (fl) S.list[off + __popc(b & ((1u << lane) - 1u))] = (int)t;
-    __syncthreads();
-    return tot;
+        return fl;
+    });
 }
 
 __device__ __forceinline__ void set_own_multi(SweepShared &S, long long tg, bool now,
@@ -1118,6 +1172,7 @@ __device__ __forceinline__ void set_own_multi(SweepShared &S, long long tg, bool
     if (now == old) return;
     if (now) atomicOr(&S.own[j >> 5], bit);
     else atomicAnd(&S.own[j >> 5], ~bit);
+    atomicAdd(&S.nown, now ? 1 : -1);
     red_add(nlead_all, now ? 1u : 0xffffffffu);
     red_add(nlead_sys, now ? 1u : 0xffffffffu);
 }
@@ -1155,18 +1210,21 @@ k_sweep_multi(MultiArgs P)
     if (threadIdx.x == 0) {
         S.abort_flag = 0;
         S.ncnt = 1u;
+        S.nown = 0;
     }
     __syncthreads();
     unsigned target = 0;
     int capped = 0;
+    bool marked = false;
     // opening pass: leaders of every system's starting labels
-    for (int base = 0; base < per_block; base += SW_THREADS) {
-        const int n = gather_tiles(S, nullptr, false, base, ntiles, nullptr);
+    for (int base = 0; base < per_block; base += kListCap) {
+        const int n = list_tiles(S, base, per_block, ntiles, [](int, int) { return true; });
         for (int q = wp; q < n; q += NWARP) {
             const int tg = S.list[q];
             const int sq = sys_of(s_toff, nsys, tg);
             const SweepArgs &A = s_sys[sq];
-            const bool now = tile_update<STENCIL>(A, M, S.qw, kt, (int)(tg - s_toff[sq]), true);
+            const bool now =
+                tile_update<STENCIL>(A, M, S.qw, kt, (int)(tg - s_toff[sq]), true, -1);
             if (lane == 0) set_own_multi(S, tg, now, P.nlead, A.nlead);
         }
     }
@@ -1181,8 +1239,14 @@ k_sweep_multi(MultiArgs P)
         if (blockIdx.x == 0)         // rounds of each system that still had leaders
             for (int q = threadIdx.x; q < nsys; q += SW_THREADS)
                 if (ld_relaxed_u32(s_sys[q].nlead) != 0u) s_rounds[q] = k + 1;
-        for (int base = 0; base < per_block; base += SW_THREADS) {
-            const int n = own_list(S, base, per_block);
+        const bool stamped = marked && (P.stamps > 0 || S.nown > NWARP);
+        for (int base = 0; base < per_block; base += kListCap) {
+            const int n = list_tiles(S, base, per_block, ntiles, [&](int j, int tg) {
+                if (!own_bit(S, j)) return false;
+                if (!stamped) return true;
+                const int sq = sys_of(s_toff, nsys, tg);
+                return __ldcg(s_sys[sq].dirty + (tg - s_toff[sq])) == k;
+            });
             for (int q = wp; q < n; q += NWARP) {
                 const int tg = S.list[q];
                 const int sq = sys_of(s_toff, nsys, tg);
@@ -1206,14 +1270,16 @@ k_sweep_multi(MultiArgs P)
         __syncthreads();
         if (S.ncnt == 0u) break;
         if (!grid_barrier(P.bar, P.err, P.spin_limit, target, &S.abort_flag)) return;
-        for (int base = 0; base < per_block; base += SW_THREADS) {
-            const int n = gather_tiles_multi(S, s_sys, s_toff, nsys, base, ntiles);
+        marked = P.stamps > 0 || (P.stamps < 0 && S.ncnt > (unsigned)(NWARP * gridDim.x));
+        const int mark = marked ? k + 1 : -1;
+        for (int base = 0; base < per_block; base += kListCap) {
+            const int n = gather_tiles_multi(S, s_sys, s_toff, nsys, base, per_block, ntiles);
             for (int q = wp; q < n; q += NWARP) {
                 const int tg = S.list[q];
                 const int sq = sys_of(s_toff, nsys, tg);
                 const SweepArgs &A = s_sys[sq];
                 const bool now =
-                    tile_update<STENCIL>(A, M, S.qw, kt, (int)(tg - s_toff[sq]), false);
+                    tile_update<STENCIL>(A, M, S.qw, kt, (int)(tg - s_toff[sq]), false, mark);
                 if (lane == 0) set_own_multi(S, tg, now, P.nlead, A.nlead);
             }
         }
@@ -1277,8 +1343,8 @@ size_t sweep_multi_scratch_bytes(int nsys)
 }
 
 cudaError_t launch_sweep_multi(int nsys, const SweepSys *sys, const KernelW &kw, const int *k3,
-                               int max_rounds, int blocks, long long spin_limit, void *scratch,
-                               int *err_out, cudaStream_t st)
+                               int max_rounds, int blocks, long long spin_limit, int stamps,
+                               void *scratch, int *err_out, cudaStream_t st)
 {
     if (nsys < 1 || nsys > kMaxSweepSys) return cudaErrorInvalidValue;
     std::vector<SweepArgs> As((size_t)nsys);
@@ -1335,6 +1401,7 @@ cudaError_t launch_sweep_multi(int nsys, const SweepSys *sys, const KernelW &kw,
     P.capped = d_capped;
     P.max_rounds = max_rounds;
     P.spin_limit = spin_limit;
+    P.stamps = stamps;
     P.kw = kw;
     P.k3 = k3;
     const size_t smem = kSweepSysOff + (size_t)nsys * sizeof(SweepArgs);

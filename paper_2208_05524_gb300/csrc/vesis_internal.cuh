@@ -211,7 +211,11 @@ cudaError_t launch_sweep(const GridDesc &g, const KernelW &kw, const int *k3,
                          unsigned long long *part_flips, double *part_dE,
                          unsigned long long *part_tiles,
                          int *rounds, int *capped, int max_rounds, int blocks,
-                         long long spin_limit, RoundState *rs, cudaStream_t st);
+                         long long spin_limit, int stamps, RoundState *rs, cudaStream_t st);
+// Decide stamps of the sweep (which tiles a round's decide visits): -1
+// while the leader tiles outnumber the grid's warps, 0 never (every leader
+// tile is decided every round), 1 always.  The rounds and labels are the
+// same in every mode.
 // Default bound on a sweep block's polls of its grid barrier (several
 // seconds of waiting).
 constexpr long long kSweepSpinLimit = 1ll << 24;
@@ -241,8 +245,8 @@ struct SweepSys {
 };
 size_t sweep_multi_scratch_bytes(int nsys);
 cudaError_t launch_sweep_multi(int nsys, const SweepSys *sys, const KernelW &kw, const int *k3,
-                               int max_rounds, int blocks, long long spin_limit, void *scratch,
-                               int *err_out, cudaStream_t st);
+                               int max_rounds, int blocks, long long spin_limit, int stamps,
+                               void *scratch, int *err_out, cudaStream_t st);
 
 // --------------------------------------------------------------- atoms.cu
 struct AtomParamsDev {

@@ -109,6 +109,7 @@ def lib():
         L.vesis_surface_weights_noalloc.argtypes = [C.POINTER(Params), _p, _p, _p]
         L.vesis_set_tiles.argtypes = [_p, _i, _i]
         L.vesis_set_wait_limit.argtypes = [_p, _ll]
+        L.vesis_set_sweep_stamps.argtypes = [_p, _i]
         L.vesis_get_state.argtypes = [_p, C.POINTER(RelaxState)]
         L.vesis_blsm_relax_batch.argtypes = [_i, _p, _p, _p, _i, _p, _p, _p]
         L.vesis_set_history.argtypes = [_p, _p, _i]
@@ -372,6 +373,12 @@ class System:
         """Polls a flip-sweep block makes at a grid barrier before the sweep
         gives up with VESIS_E_CUDA (vesis_set_wait_limit)."""
         _check(lib().vesis_set_wait_limit(self.h, int(polls)))
+
+    def set_sweep_stamps(self, mode=-1):
+        """Which tiles a flip-sweep round decides (vesis_set_sweep_stamps):
+        -1 by the leader count, 0 every leader tile, 1 only the stamped ones.
+        Results are identical in every mode."""
+        _check(lib().vesis_set_sweep_stamps(self.h, int(mode)))
 
     def set_tiles(self, energy_pencil=8, force_atoms=4):
         _check(lib().vesis_set_tiles(self.h, int(energy_pencil), int(force_atoms)))

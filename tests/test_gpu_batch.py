@@ -215,6 +215,15 @@ def test_multi_system_sweep_matches_single_sweeps_and_oracle(kernel):
         ro = O.blsm_parallel(ref, Us[k].cpu().numpy().astype(np.float64).reshape(ref.shape), sc)
         assert np.array_equal(chis[k].cpu().numpy(), ref.reshape(-1)), k
         assert res[k]["rounds"] == ro["rounds"], k
+    # the same with the decide stamps always on (the first system's mode
+    # applies to the batch)
+    systems[0].set_sweep_stamps(1)
+    chis = [_dev(c.reshape(-1), torch.uint8) for c in starts]
+    res1 = vs.blsm_relax_batch(systems, chis, Us)
+    for k, (c, r, (cs, rs)) in enumerate(zip(chis, res1, single)):
+        assert np.array_equal(c.cpu().numpy(), cs), k
+        assert (r["rounds"], r["flips"]) == (rs["rounds"], rs["flips"]), k
+    systems[0].set_sweep_stamps(-1)
     # a cap on the rounds stops the batch with the warning
     chis = [_dev(c.reshape(-1), torch.uint8) for c in starts]
     res = vs.blsm_relax_batch(systems, chis, Us, max_rounds=2)

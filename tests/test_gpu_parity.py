@@ -147,6 +147,19 @@ def test_flip_energies_bit_exact():
     assert np.array_equal(dE.cpu().numpy(), dEo.reshape(-1))
 
 
+def _check_stamp_modes(S, chi0, U, ref, ro, **kw):
+    """The sweep decides only stamped tiles (mode 1), every leader tile
+    (mode 0) or chooses by the leader count (-1): the rounds, flips and
+    labels of every mode are the oracle's."""
+    for mode in (1, 0, -1):
+        S.set_sweep_stamps(mode)
+        chi = _dev(chi0.reshape(-1), torch.uint8)
+        r = S.blsm_relax(chi, U, terms=False, **kw)
+        assert (r["rounds"], r["flips"]) == (ro["rounds"], ro["flips"]), mode
+        assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1)), mode
+    S.set_sweep_stamps(-1)
+
+
 def _blob(n, seed):
     """Seeded label field with structure: a union of random balls."""
     rng = np.random.default_rng(seed)
@@ -178,6 +191,7 @@ def test_blsm_rounds_bit_exact(n, seed):
     assert r["flips"] == ro["flips"]
     assert r["dE_sum"] == pytest.approx(ro["dE_sum"], rel=1e-12, abs=1e-12)
     assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
+    _check_stamp_modes(S, chi0, U, ref, ro)
     # the same after a capped number of rounds
     chi = _dev(chi0.reshape(-1), torch.uint8)
     k = max(1, ro["rounds"] // 3)
@@ -206,6 +220,7 @@ def test_blsm_single_ion_full_size():
     r = S.blsm_relax(chi, _dev(U32.reshape(-1), torch.float32), terms=False)
     assert r["rounds"] == ro["rounds"] and r["flips"] == ro["flips"]
     assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
+    _check_stamp_modes(S, chi0, _dev(U32.reshape(-1), torch.float32), ref, ro)
     # GPU's own FP32 fields: labels may differ only where the oracle's
     # |dE| is below 1e-9 kBT; energy at the closed-form minimum
     U, E = _fields_gpu(S, n)
@@ -405,6 +420,7 @@ def test_blsm_small_kernel_radius_bit_exact():
     assert ro["rounds"] > 0
     assert r["rounds"] == ro["rounds"] and r["flips"] == ro["flips"]
     assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
+    _check_stamp_modes(S, chi0, _dev(U32.reshape(-1), torch.float32), ref, ro)
 
 
 @pytest.mark.parametrize("case", ["all_solvent", "all_solute", "tiny", "random", "r1", "r8"])
@@ -445,6 +461,7 @@ def test_blsm_edge_cases_bit_exact(case):
     assert r["rounds"] == ro["rounds"] and r["flips"] == ro["flips"]
     assert r["dE_sum"] == pytest.approx(ro["dE_sum"], rel=1e-12, abs=1e-12)
     assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
+    _check_stamp_modes(S, chi0, _dev(U32.reshape(-1), torch.float32), ref, ro)
 
 
 def test_two_domain_complex_full_size_sampled():
@@ -528,6 +545,7 @@ def test_sin2_kernel_bit_exact(n):
     assert ro["rounds"] > 0
     assert r["rounds"] == ro["rounds"] and r["flips"] == ro["flips"]
     assert np.array_equal(chi.cpu().numpy(), ref.reshape(-1))
+    _check_stamp_modes(S, chi0, U, ref, ro)
     E = torch.zeros(3 * G, dtype=torch.float32, device="cuda")
     t = S.energy_terms(chi, U, E)
     es, _ = O.surface_energy(ref, sc)

@@ -139,6 +139,7 @@ def test_batch_and_tile_argument_errors_without_device(built):
     assert rc == -1 and b"sweep_slots" in L.vesis_last_error()
     assert L.vesis_relax_batch(-1, None, None, None, None, 1, 1, None, None) == -1
     assert L.vesis_set_tiles(None, 8, 4) == -1
+    assert L.vesis_set_sweep_stamps(None, 1) == -1
     assert L.vesis_get_tiles(None, None, None) == -1
     assert L.vesis_autotune(None, None, 3, None) == -1
 
