@@ -448,7 +448,8 @@ int vesis_net_set_conv_kernel(vesis_net n, int kind);
 int vesis_net_adam_step(vesis_net n, double lr, double beta1, double beta2, double eps);
 int vesis_net_destroy(vesis_net n);
 
-/* Solute-solute terms at the current positions (Eq. Gss), FP64: out5[0]
+/* Solute-solute terms at the current positions (Eq. Gss), to FP64
+ * accuracy (pair terms in double-float arithmetic, sums in FP64): out5[0]
  * bonds, [1] Lennard-Jones, [2] Coulomb, [3] bends, [4] torsions (their
  * sum is terms[4] of the energy calls).  The potential of mean force of
  * the paper's appendix needs the pair parts apart. */

@@ -41,14 +41,23 @@ void launch_pack_atoms(const double *xyz, const double *centre,
                                                   oob, lo, hi);
 }
 
-// Solute-solute terms in FP64: harmonic bonds, and LJ plus Coulomb over the
-// pairs not joined by a bond (mixing (s_i + s_j)/2, sqrt(e_i e_j)).  Block
-// (x, y) owns atoms i of tile x and visits the atoms j of chunk y, so each
-// pair is counted twice and the energies are halved; bonds (a per-atom CSR
-// list) are added by chunk 0.  Per-chunk FP64 gradient partials are summed
-// in chunk order afterwards.  1/r comes from an FP32 reciprocal square root
-// refined by two Newton-Raphson steps y <- y (3/2 - r^2 y^2 / 2), which
-// reaches double precision without a double divide or square root.
+// Solute-solute terms (Eq. Gss): harmonic bonds, and LJ plus Coulomb over
+// the pairs not joined by a bond (mixing (s_i + s_j)/2, sqrt(e_i e_j)).
+// Block (x, y) owns atoms i of tile x and visits the atoms j of chunk y, so
+// each pair is counted twice and the energies are halved; bonds (a
+// per-atom CSR list) are added by chunk 0 in FP64.  Per-chunk FP64 gradient
+// partials are summed in chunk order afterwards.
+//
+// The pair terms run in double-float arithmetic: a value is the unevaluated
+// sum hi + lo of two FP32 numbers (about 48 significant bits), built from
+// the error-free transformations of Knuth (TwoSum) and Dekker (FastTwoSum,
+// and the product's error recovered with one FMA).  The FP32 pipes do the
+// work that FP64 would do at a small fraction of their rate.  Differences
+// of coordinates use the accurate sum (error relative to the result), all
+// other sums the short one (error relative to the operands); 1/r is FP32
+// rsqrt refined by one Newton step whose residual 1 - r^2 y^2 is formed in
+// double-float (relative error about 1.5 (2^-23)^2).  Each 128-atom stage's
+// sums are added into FP64 accumulators, so the long sums stay in FP64.
 constexpr int SS_THREADS = 128;
 constexpr int SS_TILE = 128;
 constexpr int kMaxExcl = 8;
@@ -57,7 +66,7 @@ SsPlan plan_ss(int n, int nsm)
 {
     SsPlan sp;
     sp.tiles = (n + SS_THREADS - 1) / SS_THREADS;
-    int nchunk = (2 * nsm + sp.tiles - 1) / sp.tiles;
+    int nchunk = (8 * nsm + sp.tiles - 1) / sp.tiles;   // about 8 blocks per SM
     const int maxc = (n + 31) / 32;
     if (nchunk < 1) nchunk = 1;
     if (nchunk > maxc) nchunk = maxc;
@@ -68,12 +77,87 @@ SsPlan plan_ss(int n, int nsm)
     return sp;
 }
 
-__device__ __forceinline__ double inv_sqrt_d(double r2)
+struct dfl {
+    float h, l;     // value = h + l, |l| <= ulp(h) / 2
+};
+
+__device__ __forceinline__ dfl df_of(double x)
 {
-    double y = (double)rsqrtf((float)r2);
-    y = y * (1.5 - 0.5 * r2 * y * y);
-    y = y * (1.5 - 0.5 * r2 * y * y);
-    return y;
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+
+__device__ __forceinline__ double df_val(dfl a) { return (double)a.h + (double)a.l; }
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ dfl two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker)
+__device__ __forceinline__ dfl fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a + b with an error relative to |a| + |b|
+__device__ __forceinline__ dfl df_add(dfl a, dfl b)
+{
+    const dfl s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+
+// a - b with an error relative to |a - b|
+__device__ __forceinline__ dfl df_sub_acc(dfl a, dfl b)
+{
+    dfl s = two_sum(a.h, -b.h);
+    const dfl t = two_sum(a.l, -b.l);
+    s = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+    return fast_two_sum(s.h, __fadd_rn(s.l, t.l));
+}
+
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfl df_mulf(dfl a, float f)
+{
+    const float p = __fmul_rn(a.h, f);
+    float e = __fmaf_rn(a.h, f, -p);
+    e = __fmaf_rn(a.l, f, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfl df_sqr(dfl a)
+{
+    const float p = __fmul_rn(a.h, a.h);
+    float e = __fmaf_rn(a.h, a.h, -p);
+    e = __fmaf_rn(__fadd_rn(a.h, a.h), a.l, e);
+    return fast_two_sum(p, e);
+}
+
+// exact scaling by a power of two
+__device__ __forceinline__ dfl df_scale(dfl a, float p2) { return {a.h * p2, a.l * p2}; }
+
+// 1 / sqrt(x): y0 = rsqrt(x.h), then y0 (1 + h / 2) with h = 1 - x y0^2
+// formed in double-float (1 - t.h is exact, t.h being within a few ulp of 1)
+__device__ __forceinline__ dfl df_rsqrt(dfl x)
+{
+    const float y = rsqrtf(x.h);
+    const dfl t = df_mulf(df_mulf(x, y), y);
+    const float h = __fsub_rn(__fsub_rn(1.0f, t.h), t.l);
+    return fast_two_sum(y, __fmul_rn(__fmul_rn(y, h), 0.5f));
 }
 
 __global__ void __launch_bounds__(SS_THREADS)
@@ -84,20 +168,24 @@ k_ss(const double *__restrict__ xyz, const double *__restrict__ sig,
      const double *__restrict__ bond_r0, int n, int chunk_len, double coul,
      double *__restrict__ e_part, double *__restrict__ g_part)
 {
-    __shared__ double s_x[SS_TILE], s_y[SS_TILE], s_z[SS_TILE];
-    __shared__ double s_s[SS_TILE], s_e[SS_TILE], s_q[SS_TILE];
+    // staged atoms j as double-float: x, y, z, sigma / 2, sqrt(eps), q
+    __shared__ __align__(16) dfl s_a[SS_TILE][6];
     __shared__ double s_red[3][SS_THREADS / 32];
     const int i = blockIdx.x * SS_THREADS + threadIdx.x;
     const bool live = i < n;
     const int jb = blockIdx.y * chunk_len;
     const int je = min(n, jb + chunk_len);
-    double xi = 0, yi = 0, zi = 0, si = 0, ei = 0, qi = 0;
+    double xi = 0, yi = 0, zi = 0;
+    dfl Xi = {0.f, 0.f}, Yi = Xi, Zi = Xi, Si = Xi, Ei = Xi, Qi = Xi;
     int ex[kMaxExcl];
 #pragma unroll
     for (int e = 0; e < kMaxExcl; ++e) ex[e] = -1;
     if (live) {
         xi = xyz[3 * i]; yi = xyz[3 * i + 1]; zi = xyz[3 * i + 2];
-        si = sig[i]; ei = sqeps[i]; qi = q[i];
+        Xi = df_of(xi); Yi = df_of(yi); Zi = df_of(zi);
+        Si = df_of(0.5 * sig[i]);
+        Ei = df_scale(df_of(sqeps[i]), 4.0f);     // 4 sqrt(eps_i): 4 eps_ij in one product
+        Qi = df_of(coul * q[i]);
 #pragma unroll
         for (int e = 0; e < kMaxExcl; ++e) ex[e] = excl[i * kMaxExcl + e];
     }
@@ -107,34 +195,51 @@ k_ss(const double *__restrict__ xyz, const double *__restrict__ sig,
         __syncthreads();
         for (int m = threadIdx.x; m < cnt; m += SS_THREADS) {
             const int j = base + m;
-            s_x[m] = xyz[3 * j]; s_y[m] = xyz[3 * j + 1]; s_z[m] = xyz[3 * j + 2];
-            s_s[m] = sig[j]; s_e[m] = sqeps[j]; s_q[m] = q[j];
+            s_a[m][0] = df_of(xyz[3 * j]);
+            s_a[m][1] = df_of(xyz[3 * j + 1]);
+            s_a[m][2] = df_of(xyz[3 * j + 2]);
+            s_a[m][3] = df_of(0.5 * sig[j]);
+            s_a[m][4] = df_of(sqeps[j]);
+            s_a[m][5] = df_of(q[j]);
         }
         __syncthreads();
         if (!live) continue;
+        const dfl z0 = {0.f, 0.f};
+        dfl sl = z0, sc = z0, sx = z0, sy = z0, sz = z0;   // this stage's sums
         for (int m = 0; m < cnt; ++m) {
             const int j = base + m;
             bool skip = (j == i);
 #pragma unroll
             for (int e = 0; e < kMaxExcl; ++e) skip |= (ex[e] == j);
             if (skip) continue;
-            const double dx = xi - s_x[m], dy = yi - s_y[m], dz = zi - s_z[m];
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const double ir = inv_sqrt_d(r2);
-            const double ir2 = ir * ir;
-            const double s = 0.5 * (si + s_s[m]);
-            const double ep = ei * s_e[m];
-            const double sr2 = s * s * ir2;
-            const double sr6 = sr2 * sr2 * sr2;
-            const double cq = coul * qi * s_q[m] * ir;
-            elj += 4.0 * ep * (sr6 * sr6 - sr6);
-            ec += cq;
-            // (dU/dr)/r
-            const double f = (4.0 * ep * (-12.0 * sr6 * sr6 + 6.0 * sr6) - cq) * ir2;
-            gx += f * dx;
-            gy += f * dy;
-            gz += f * dz;
+            const dfl dx = df_sub_acc(Xi, s_a[m][0]);
+            const dfl dy = df_sub_acc(Yi, s_a[m][1]);
+            const dfl dz = df_sub_acc(Zi, s_a[m][2]);
+            const dfl r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+            const dfl ir = df_rsqrt(r2);
+            const dfl ir2 = df_sqr(ir);
+            const dfl sg = df_add(Si, s_a[m][3]);
+            const dfl ep4 = df_mul(Ei, s_a[m][4]);
+            const dfl sr2 = df_mul(df_sqr(sg), ir2);
+            const dfl sr6 = df_mul(df_sqr(sr2), sr2);
+            const dfl sr12 = df_sqr(sr6);
+            const dfl cq = df_mul(df_mul(Qi, s_a[m][5]), ir);
+            sl = df_add(sl, df_mul(ep4, df_add(sr12, df_neg(sr6))));
+            sc = df_add(sc, cq);
+            // (dU/dr) / r = (4 eps (6 sr6 - 12 sr12) - cq) / r^2
+            const dfl f = df_mul(df_add(df_mul(ep4, df_add(df_mulf(sr6, 6.0f),
+                                                          df_mulf(sr12, -12.0f))),
+                                        df_neg(cq)),
+                                 ir2);
+            sx = df_add(sx, df_mul(f, dx));
+            sy = df_add(sy, df_mul(f, dy));
+            sz = df_add(sz, df_mul(f, dz));
         }
+        elj += df_val(sl);
+        ec += df_val(sc);
+        gx += df_val(sx);
+        gy += df_val(sy);
+        gz += df_val(sz);
     }
     if (live) {
         if (blockIdx.y == 0) {

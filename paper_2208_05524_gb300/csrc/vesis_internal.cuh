@@ -258,7 +258,8 @@ void launch_pack_atoms(const double *xyz, const double *centre,
                        int n, double rho, double cfa, float4 *xyzq,
                        float2 *ab, float4 *fcoef, int *oob, const double *lo,
                        const double *hi, cudaStream_t st);
-// Solute-solute energy and gradient in FP64 (Eq. Gss) on a 2-D grid of
+// Solute-solute energy and gradient to FP64 accuracy (Eq. Gss; pair terms
+// in double-float arithmetic) on a 2-D grid of
 // (atom tile, j-chunk) blocks: e_part[block][3] (bond, LJ, Coulomb) and
 // g_part[chunk][n][3] (gradient partials, summed in chunk order later).
 struct SsPlan {
