@@ -200,6 +200,12 @@ def test_blsm_rounds_bit_exact(n, seed):
     O.blsm_parallel(ref2, U32.astype(np.float64), sc, max_rounds=k)
     assert r["rounds"] == k
     assert np.array_equal(chi.cpu().numpy(), ref2.reshape(-1))
+    for mode in (1, 0):      # the cap with the decide stamps forced on and off
+        S.set_sweep_stamps(mode)
+        chi = _dev(chi0.reshape(-1), torch.uint8)
+        r = S.blsm_relax(chi, U, max_rounds=k, terms=False)
+        assert r["rounds"] == k and np.array_equal(chi.cpu().numpy(), ref2.reshape(-1)), mode
+    S.set_sweep_stamps(-1)
 
 
 def test_blsm_single_ion_full_size():
