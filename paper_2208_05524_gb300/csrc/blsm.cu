@@ -542,39 +542,67 @@ __global__ void k_init_sphere(GridDesc g, float cx, float cy, float cz, float R,
     chi[p] = (sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) < R) ? 1 : 0;
 }
 
-constexpr int IT_TILE = 256;
+// Tight start (Sec. 3.1, Initial surfaces): chi = 1 where min_i(|x - r_i| -
+// d_i) < 0.  One block per tile of 4 x 8 x 8 cells: the block first keeps
+// the atoms whose ball, widened by kTightMargin, reaches the tile's box
+// (distance from the centre to the box at most d_i + margin), then every
+// cell takes the minimum over those.  A discarded atom's |x - r_i| - d_i is
+// at least the margin, far above the FP32 rounding of the distance, so it
+// could not have made the minimum negative: the labels are those of the
+// minimum over all atoms, in O(cells x nearby atoms) instead of O(cells x
+// atoms).
+constexpr int IT_X = 4, IT_Y = 8, IT_Z = 8;      // tile (IT_X * IT_Y * IT_Z = CT)
+constexpr int IT_LIST = 1024;                     // atoms examined per pass
+constexpr float kTightMargin = 1.0e-3f;           // Angstrom
+static_assert(IT_X * IT_Y * IT_Z == CT, "one cell per thread");
+
+static unsigned tight_blocks(const GridDesc &g)
+{
+    return (unsigned)(((g.nx + IT_X - 1) / IT_X) * ((g.ny + IT_Y - 1) / IT_Y) *
+                      ((g.nz + IT_Z - 1) / IT_Z));
+}
 
 __global__ void __launch_bounds__(CT)
 k_init_tight(GridDesc g, const float4 *__restrict__ xyzd, int n,
              uint8_t *__restrict__ chi)
 {
-    __shared__ float4 s_a[IT_TILE];
-    const long long nyz = (long long)g.ny * g.nz;
-    const long long G = nyz * g.nx;
-    const long long p = (long long)blockIdx.x * CT + threadIdx.x;
-    float x = 0.f, y = 0.f, z = 0.f;
-    if (p < G) {
-        const int i = (int)(p / nyz);
-        const long long rem = p - (long long)i * nyz;
-        const int j = (int)(rem / g.nz);
-        const int k = (int)(rem - (long long)j * g.nz);
-        x = cell_pos(i, g.cx, g.h);
-        y = cell_pos(j, g.cy, g.h);
-        z = cell_pos(k, g.cz, g.h);
-    }
+    __shared__ float4 s_a[IT_LIST];
+    __shared__ int s_cnt;
+    const int ntz = (g.nz + IT_Z - 1) / IT_Z, nty = (g.ny + IT_Y - 1) / IT_Y;
+    const int tz = blockIdx.x % ntz, ty = (blockIdx.x / ntz) % nty, tx = blockIdx.x / (ntz * nty);
+    const int i0 = tx * IT_X, j0 = ty * IT_Y, k0 = tz * IT_Z;
+    const int i = i0 + threadIdx.x / (IT_Y * IT_Z), j = j0 + (threadIdx.x / IT_Z) % IT_Y,
+              k = k0 + threadIdx.x % IT_Z;
+    const bool live = i < g.nx && j < g.ny && k < g.nz;
+    const float x = cell_pos(i, g.cx, g.h), y = cell_pos(j, g.cy, g.h), z = cell_pos(k, g.cz, g.h);
+    // the box of the tile's cells inside the grid
+    const float lx = cell_pos(i0, g.cx, g.h), hx = cell_pos(min(i0 + IT_X, g.nx) - 1, g.cx, g.h);
+    const float ly = cell_pos(j0, g.cy, g.h), hy = cell_pos(min(j0 + IT_Y, g.ny) - 1, g.cy, g.h);
+    const float lz = cell_pos(k0, g.cz, g.h), hz = cell_pos(min(k0 + IT_Z, g.nz) - 1, g.cz, g.h);
     float phi = 3.0e38f;
-    for (int base = 0; base < n; base += IT_TILE) {
-        const int cnt = min(IT_TILE, n - base);
+    for (int base = 0; base < n; base += IT_LIST) {
+        const int cnt = min(IT_LIST, n - base);
+        __syncthreads();          // the previous list is no longer read
+        if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
-        for (int m = threadIdx.x; m < cnt; m += CT) s_a[m] = xyzd[base + m];
+        for (int m = threadIdx.x; m < cnt; m += CT) {
+            const float4 A = xyzd[base + m];
+            const float gx = fmaxf(fmaxf(lx - A.x, A.x - hx), 0.f);
+            const float gy = fmaxf(fmaxf(ly - A.y, A.y - hy), 0.f);
+            const float gz = fmaxf(fmaxf(lz - A.z, A.z - hz), 0.f);
+            const float reach = A.w + kTightMargin;
+            if (reach > 0.f && fmaf(gx, gx, fmaf(gy, gy, gz * gz)) <= reach * reach)
+                s_a[atomicAdd(&s_cnt, 1)] = A;
+        }
         __syncthreads();
-        for (int m = 0; m < cnt; ++m) {
+        const int c = s_cnt;
+        for (int m = 0; m < c; ++m) {
             const float4 A = s_a[m];
             const float dx = x - A.x, dy = y - A.y, dz = z - A.z;
             phi = fminf(phi, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) - A.w);
         }
     }
-    if (p < G) chi[p] = (phi < 0.f) ? 1 : 0;
+    if (live) chi[((long long)i * g.ny + j) * g.nz + k] = (phi < 0.f) ? 1 : 0;
 }
 
 // ------------------------------------------------------------- launchers
@@ -666,7 +694,7 @@ void launch_init_tight(const GridDesc &g, const float4 *xyzd, int n,
                        uint8_t *chi, cudaStream_t st)
 {
     count_launch();
-    k_init_tight<<<cell_blocks(g), CT, 0, st>>>(g, xyzd, n, chi);
+    k_init_tight<<<tight_blocks(g), CT, 0, st>>>(g, xyzd, n, chi);
 }
 
 }  // namespace vesis
