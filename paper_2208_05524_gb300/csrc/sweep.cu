@@ -324,12 +324,15 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
             }
             bool lose = false;
             if (L != 0ull) {
+                // branch-free and unrolled, so that several shared-memory
+                // loads are in flight at once
+#pragma unroll 4
                 for (int q = sub; q < m; q += G) {
-                    if (M.d.cw[q] > L) {
-                        const unsigned c = M.d.cc[q];
-                        const int ox = c & 31, oy = (c >> 5) & 31, oz = (c >> 10) & 31;
-                        lose |= abs(ox - lx) <= r && abs(oy - ly) <= r && abs(oz - lz) <= r;
-                    }
+                    const unsigned long long w = M.d.cw[q];
+                    const unsigned c = M.d.cc[q];
+                    const int ox = c & 31, oy = (c >> 5) & 31, oz = (c >> 10) & 31;
+                    lose |= (w > L) & (abs(ox - lx) <= r) & (abs(oy - ly) <= r) &
+                            (abs(oz - lz) <= r);
                 }
             }
             const unsigned lb = __ballot_sync(0xffffffffu, lose);
