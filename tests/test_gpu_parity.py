@@ -268,6 +268,26 @@ def test_atom_forces_match_oracle(natoms, n, h):
 
 # ------------------------------------------------------------ relaxation
 
+def test_solute_solute_pair_terms_match_oracle():
+    """G_ss's bonds, LJ and Coulomb (Eq. Gss) on a charged, bonded 300-atom
+    solute: the GPU evaluates the pair terms in double-float arithmetic and
+    must agree with the FP64 oracle to near FP64 accuracy.  With rho_w = 0
+    and eps_w = eps_m the solvation forces vanish, so the gradient the
+    library returns is G_ss's alone."""
+    vs = _vs()
+    s = synth.protein_like(n_atoms=300, n=64, h=0.5, seed=5)
+    kw = dict(rho_w=0.0, eps_w=1.0)
+    S = vs.System(s, **kw)
+    t = S.ss_terms()
+    e, g = O.ss_terms(s, O.params(**kw))
+    assert t["bonds"] == pytest.approx(e[0], rel=1e-12)
+    assert t["lj"] == pytest.approx(e[1], rel=1e-12)
+    assert t["coulomb"] == pytest.approx(e[2], rel=1e-12)
+    chi = _dev(O.init_labels(s).reshape(-1), torch.uint8)
+    got = S.atom_forces(chi)
+    assert np.allclose(got, g, rtol=1e-10, atol=1e-12 * np.abs(g).max())
+
+
 def test_relax_two_atom_molecule_matches_oracle():
     vs = _vs()
     s = synth.two_atom_molecule(8.0, 7.0, n=32, h=0.5)
