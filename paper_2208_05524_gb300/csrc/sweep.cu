@@ -108,7 +108,8 @@ struct SweepArgs {
     double *dE;
     unsigned long long *PL;   // leader word per brick
     uint8_t *PO;              // leader cell within its brick: di | dj << 2 | dk << 4
-    unsigned *CB;             // labels, one bit per cell: row (i, j) is nzw words
+    unsigned *CB;             // labels, one bit per cell: word w of column (i, j)
+                              // at (w nx + i) ny + j (a tile's halo words adjoin)
     int nzw;
     uint8_t *post;            // posting area per tile (kPostBytes)
     uint8_t *upd;             // tile received a winner this round
@@ -241,6 +242,19 @@ __device__ __forceinline__ void red_add(unsigned *p, unsigned v)
     asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy through L2 (zero fill when
+// !valid), and the wait for this thread's copies.
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Labels, W, dE, leader words, postings and tile flags change under other
 // warps and blocks between phases: every read of them goes to L2
 // (ld.global.cg), never to a stale L1 line.
@@ -360,7 +374,7 @@ __device__ __forceinline__ void tile_decide(const SweepArgs &A, WarpMem &M, int 
         const long long p = (long long)(0xffffffffull - ((L >> 1) & 0xffffffffull));
         A.chi[p] = (uint8_t)(1u - (unsigned)(L & 1ull));
         asm volatile("red.relaxed.gpu.global.xor.b32 [%0], %1;"
-                     :: "l"(A.CB + ((long long)ci * g.ny + cj) * A.nzw + (ck >> 5)),
+                     :: "l"(A.CB + ((long long)(ck >> 5) * g.nx + ci) * g.ny + cj),
                         "r"(1u << (ck & 31)) : "memory");
         dv[h] = __ldcg(A.dE + p);
         n_lane += 1u;
@@ -424,38 +438,50 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
     // ---------------------------------------------------------- loads
     // All of a lane's loads are issued before the first use.  W and U of the
     // tile's own cells: rows rho = lane + 32 m, (x, y) = (rho >> 3, rho & 7).
+    // With 8-cell rows in 16-byte pieces (vec) they pass through the warp's
+    // candidate area in shared memory, consecutive lanes on consecutive
+    // pieces (two lanes per 32-byte row), so that each copy instruction
+    // reads whole sectors; otherwise each lane loads its rows itself.
     unsigned Wr[2][TS];
     float Ur[2][TS];
     bool rowok[2];
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
         const int rho = lane + 32 * m;
-        const int x = rho >> 3, y = rho & 7;
-        rowok[m] = (i0 + x < g.nx) && (j0 + y < g.ny);
+        rowok[m] = (i0 + (rho >> 3) < g.nx) && (j0 + (rho & 7) < g.ny);
 #pragma unroll
         for (int z = 0; z < TS; ++z) {
             Wr[m][z] = 0u;
             Ur[m][z] = 0.f;
         }
-        if (rowok[m]) {
-            const long long o = (long long)(i0 + x) * nyz + (long long)(j0 + y) * g.nz + k0;
-            if (A.vec) {
-                const uint4 *wp = reinterpret_cast<const uint4 *>(A.W + o);
-                const float4 *up = reinterpret_cast<const float4 *>(A.U + o);
-                const uint4 w0 = __ldcg(wp), w1 = __ldcg(wp + 1);
-                const float4 u0 = __ldg(up), u1 = __ldg(up + 1);
-                Wr[m][0] = w0.x; Wr[m][1] = w0.y; Wr[m][2] = w0.z; Wr[m][3] = w0.w;
-                Wr[m][4] = w1.x; Wr[m][5] = w1.y; Wr[m][6] = w1.z; Wr[m][7] = w1.w;
-                Ur[m][0] = u0.x; Ur[m][1] = u0.y; Ur[m][2] = u0.z; Ur[m][3] = u0.w;
-                Ur[m][4] = u1.x; Ur[m][5] = u1.y; Ur[m][6] = u1.z; Ur[m][7] = u1.w;
-            } else {
+    }
+    const unsigned sW = (unsigned)__cvta_generic_to_shared(M.u.cW);
+    const unsigned sU = (unsigned)__cvta_generic_to_shared(M.u.cU);
+    if (A.vec) {
 #pragma unroll
-                for (int z = 0; z < TS; ++z)
-                    if (z < zlim) {
-                        Wr[m][z] = __ldcg(A.W + o + z);
-                        Ur[m][z] = __ldg(A.U + o + z);
-                    }
-            }
+        for (int c4 = 0; c4 < 4; ++c4) {
+            const int c = lane + 32 * c4;            // piece c: row c >> 1, half c & 1
+            const int rho = c >> 1;
+            const bool ok = (i0 + (rho >> 3) < g.nx) && (j0 + (rho & 7) < g.ny);
+            const long long o = ok ? (long long)(i0 + (rho >> 3)) * nyz +
+                                         (long long)(j0 + (rho & 7)) * g.nz + k0 + 4 * (c & 1)
+                                   : 0;
+            cp_async16(sW + 16u * (unsigned)c, A.W + o, ok);
+            cp_async16(sU + 16u * (unsigned)c, A.U + o, ok);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int rho = lane + 32 * m;
+            if (!rowok[m]) continue;
+            const long long o = (long long)(i0 + (rho >> 3)) * nyz +
+                                (long long)(j0 + (rho & 7)) * g.nz + k0;
+#pragma unroll
+            for (int z = 0; z < TS; ++z)
+                if (z < zlim) {
+                    Wr[m][z] = __ldcg(A.W + o + z);
+                    Ur[m][z] = __ldg(A.U + o + z);
+                }
         }
     }
     // halo label rows from the bit copy: row h = hx * 10 + hy is the cell
@@ -474,10 +500,11 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
             if (h < kHaloRows) {
                 const int i = i0 - 1 + h / 10, j = j0 - 1 + h % 10;
                 if (i >= 0 && j >= 0 && i < g.nx && j < g.ny) {
-                    const unsigned *row = A.CB + ((long long)i * g.ny + j) * A.nzw;
-                    const unsigned vm = __ldcg(row + wm);
-                    const unsigned vl = need_lo ? __ldcg(row + wm - 1) : 0u;
-                    const unsigned vh = need_hi ? __ldcg(row + wm + 1) : 0u;
+                    const unsigned *col = A.CB + (long long)i * g.ny + j;
+                    const long long pl = (long long)g.nx * g.ny;     // words per plane
+                    const unsigned vm = __ldcg(col + wm * pl);
+                    const unsigned vl = need_lo ? __ldcg(col + (wm - 1) * pl) : 0u;
+                    const unsigned vh = need_hi ? __ldcg(col + (wm + 1) * pl) : 0u;
                     const unsigned lo = sh == 0 ? (vl >> 31) : ((vm >> (sh - 1)) & 1u);
                     const unsigned hi = sh == 24 ? (vh & 1u) : ((vm >> (sh + 8)) & 1u);
                     hb[u] = lo | (((vm >> sh) & 0xffu) << 1) | (hi << 9);
@@ -514,6 +541,23 @@ __device__ __forceinline__ bool tile_update(const SweepArgs &A, WarpMem &M, cons
     for (int u = 0; u < 4; ++u) {
         const int h = lane + 32 * u;
         if (h < kHaloRows) M.u.hr[h] = hb[u];
+    }
+    if (A.vec) {      // the staged rows into registers before the area is reused
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int rho = lane + 32 * m;
+            const uint4 w0 = reinterpret_cast<const uint4 *>(M.u.cW)[2 * rho];
+            const uint4 w1 = reinterpret_cast<const uint4 *>(M.u.cW)[2 * rho + 1];
+            const float4 u0 = reinterpret_cast<const float4 *>(M.u.cU)[2 * rho];
+            const float4 u1 = reinterpret_cast<const float4 *>(M.u.cU)[2 * rho + 1];
+            Wr[m][0] = w0.x; Wr[m][1] = w0.y; Wr[m][2] = w0.z; Wr[m][3] = w0.w;
+            Wr[m][4] = w1.x; Wr[m][5] = w1.y; Wr[m][6] = w1.z; Wr[m][7] = w1.w;
+            Ur[m][0] = u0.x; Ur[m][1] = u0.y; Ur[m][2] = u0.z; Ur[m][3] = u0.w;
+            Ur[m][4] = u1.x; Ur[m][5] = u1.y; Ur[m][6] = u1.z; Ur[m][7] = u1.w;
+        }
+        __syncwarp();
     }
 
     // ------------------------------------------------- posted winners
@@ -962,16 +1006,17 @@ size_t sweep_state_bytes(const GridDesc &g, int r)
            (size_t)g.nx * g.ny * nzw * 4;
 }
 
-// Label bits: word w of row (i, j) holds cells 32 w .. 32 w + 31 of the row
-// (bit = cell - 32 w), zero past the row's end.
-__global__ void k_pack_labels(const uint8_t *__restrict__ chi, int nz, int nzw,
+// Label bits: word w of column (i, j) holds cells 32 w .. 32 w + 31 of the
+// column (bit = cell - 32 w), zero past its end; the words are stored plane
+// by plane, word (w, i, j) at (w nx + i) ny + j.
+__global__ void k_pack_labels(const uint8_t *__restrict__ chi, int nz, long long nxy,
                               long long nwords, unsigned *__restrict__ CB)
 {
     const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nwords) return;
-    const long long row = w / nzw;
-    const int k0 = (int)(w - row * nzw) * 32;
-    const uint8_t *src = chi + row * nz + k0;
+    const long long wz = w / nxy, col = w - wz * nxy;
+    const int k0 = (int)wz * 32;
+    const uint8_t *src = chi + col * nz + k0;
     const int n = min(32, nz - k0);
     unsigned b = 0u;
     for (int k = 0; k < n; ++k) b |= (src[k] != 0 ? 1u : 0u) << k;
@@ -1070,8 +1115,8 @@ static SweepArgs sweep_setup(const GridDesc &g, const KernelW &kw, const int *k3
     {
         const long long nwords = (long long)g.nx * g.ny * A.nzw;
         count_launch();
-        k_pack_labels<<<(unsigned)((nwords + 255) / 256), 256, 0, st>>>(chi, g.nz, A.nzw,
-                                                                       nwords, A.CB);
+        k_pack_labels<<<(unsigned)((nwords + 255) / 256), 256, 0, st>>>(
+            chi, g.nz, (long long)g.nx * g.ny, nwords, A.CB);
     }
     return A;
 }
