@@ -160,7 +160,9 @@ struct WarpMem {
 // reduction (it orders the block's earlier writes, which bar.sync has made
 // visible to thread 0), the wait a relaxed poll (an acquire load per poll
 // would discard the SM's L1 under the blocks still working) closed by one
-// acquire fence; no reset is needed.  The poll is bounded (A.spin_limit
+// acquire load of the counter, which reads the completed count and so
+// synchronises with every arrival's release (a barrier alone measured 1.16
+// us against 1.26 with a closing acquire fence); no reset is needed.  The poll is bounded (A.spin_limit
 // polls; 0 gives up at the first poll that finds the barrier open) and
 // watches the error flag every 256 polls; a timeout raises the flag and the
 // caller returns.
@@ -168,6 +170,13 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned *p)
 {
     unsigned v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -189,7 +198,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, long long 
             }
             __nanosleep(32);
         }
-        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        (void)ld_acquire_u32(bar);
     }
     __syncthreads();
     return *abort_flag == 0;
