@@ -292,20 +292,23 @@ void launch_ss(const SsPlan &sp, const double *xyz, const double *sig,
         sp.chunk_len, coul, e_part, g_part);
 }
 
+// Sum of the blocks' partials, one warp per term: lane l adds blocks l,
+// l + 32, ... in order, then the lanes' sums are combined by a fixed tree,
+// so the result does not depend on timing.
 __global__ void k_ss_final(const double *__restrict__ e_part, int nb, double *out3)
 {
-    double t[3] = {0.0, 0.0, 0.0};
-    for (int b = 0; b < nb; ++b)
-        for (int c = 0; c < 3; ++c) t[c] += e_part[3 * b + c];
-    out3[0] = t[0];
-    out3[1] = t[1];
-    out3[2] = t[2];
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int b = lane; b < nb; b += 32) t += e_part[3 * b + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) out3[c] = t;
 }
 
 void launch_ss_final(const double *e_part, int nb, double *out3, cudaStream_t st)
 {
     count_launch();
-    k_ss_final<<<1, 1, 0, st>>>(e_part, nb, out3);
+    k_ss_final<<<1, 96, 0, st>>>(e_part, nb, out3);
 }
 
 // grad = a + b and max |grad component| (non-negative doubles order like

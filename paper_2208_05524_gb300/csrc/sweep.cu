@@ -1028,7 +1028,16 @@ __global__ void k_pack_labels(const uint8_t *__restrict__ chi, int nz, long long
     const uint8_t *src = chi + col * nz + k0;
     const int n = min(32, nz - k0);
     unsigned b = 0u;
-    for (int k = 0; k < n; ++k) b |= (src[k] != 0 ? 1u : 0u) << k;
+    if (n == 32 && ((uintptr_t)src & 15u) == 0) {   // two 16-byte loads
+        const uint4 v0 = *reinterpret_cast<const uint4 *>(src);
+        const uint4 v1 = *reinterpret_cast<const uint4 *>(src + 16);
+        const unsigned q[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            b |= (((q[k >> 2] >> (8 * (k & 3))) & 0xffu) != 0u ? 1u : 0u) << k;
+    } else {
+        for (int k = 0; k < n; ++k) b |= (src[k] != 0 ? 1u : 0u) << k;
+    }
     CB[w] = b;
 }
 
