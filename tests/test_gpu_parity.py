@@ -524,6 +524,7 @@ def test_two_domain_complex_full_size_sampled():
     assert np.array_equal(W.cpu().numpy().astype(np.int64),
                           O.conv(chin.reshape(n), sc["q"]).reshape(-1))
     del W
+    chi0 = chi.clone()
     r = S.blsm_relax(chi, U, E)
     assert r["status"] == 0 and r["rounds"] > 0
     assert r["terms"]["total"] - T0["total"] == pytest.approx(r["dE_sum"], rel=1e-6, abs=1e-6)
@@ -533,6 +534,28 @@ def test_two_domain_complex_full_size_sampled():
     m = cand.bool()
     assert int(m.sum()) > 0
     assert float(dE[m].min()) >= 0.0
+    del dE, cand
+    # the same rounds and labels with every leader tile decided every round
+    # (these blocks own 728 tiles each: the multi-pass tile lists), and
+    # through the multi-system kernel's global tile numbering
+    S.set_sweep_stamps(0)
+    c2 = chi0.clone()
+    r2 = S.blsm_relax(c2, U, E, terms=False)
+    S.set_sweep_stamps(-1)
+    assert (r2["rounds"], r2["flips"]) == (r["rounds"], r["flips"]) and torch.equal(c2, chi)
+    c3 = chi0.clone()
+    r3 = vs.blsm_relax_batch([S], [c3], [U])[0]
+    assert (r3["rounds"], r3["flips"]) == (r["rounds"], r["flips"]) and torch.equal(c3, chi)
+    del c2, c3
+    # one outer iteration with the sweep on 19 blocks (more than 2,048 tiles
+    # per block: several listing passes per phase) against the default grid
+    xyz = np.ascontiguousarray(s["xyz"])
+    a = chi0.clone()
+    ra = S.relax(a, xyz, max_outer=1)
+    b = chi0.clone()
+    rb = vs.relax_batch([S], [b], [xyz], threads=1, sweep_slots=8, max_outer=1)[0]
+    assert (rb["flip_rounds"], rb["flips"]) == (ra["flip_rounds"], ra["flips"])
+    assert torch.equal(a, b) and rb["G"] == ra["G"]
     S.close()
 
 
