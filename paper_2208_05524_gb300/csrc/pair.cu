@@ -350,7 +350,27 @@ ForcePlan plan_pair_force(long long G, int natoms, int nsm, int apt)
 {
     ForcePlan fp;
     fp.apt = apt == 2 ? 2 : 4;
-    fp.atom_tiles = (natoms + PF_THREADS * fp.apt - 1) / (PF_THREADS * fp.apt);
+    // Cell groups: a small solute fills few of a block's 512 atom slots, so
+    // the block splits into cg groups of 128 / cg threads that hold the same
+    // atoms and share each staged set of cells.  cg depends only on the atom
+    // count (the fill of 512 / cg-atom tiles against the staging a block
+    // then spreads over fewer atoms), so both atom tiles sum every atom's
+    // cells in the same groups and order and stay bit-identical.
+    fp.cg = 1;
+    {
+        double best = 0.0;
+        for (int cg = 1; cg <= 4; cg *= 2) {
+            const long long slots = PF_ATOMS / cg;
+            const double fill = (double)natoms / (double)(slots * ((natoms + slots - 1) / slots));
+            const double score = fill / (1.0 + 0.05 * cg);
+            if (score > best + 1e-12) {
+                best = score;
+                fp.cg = cg;
+            }
+        }
+    }
+    const int per_tile = PF_THREADS / fp.cg * fp.apt;
+    fp.atom_tiles = (natoms + per_tile - 1) / per_tile;
     // The cell chunks are sized from the 512-atom tile count whatever the
     // atom tile, so every atom sums the same stages in the same order and
     // both variants give bit-identical gradients.
@@ -449,7 +469,7 @@ __device__ __forceinline__ void force_pair2(const CellPairs &c, f2 ax, f2 ay, f2
 
 // APT (atoms per thread, 2 or 4, in packed pairs) is the atom tile the
 // autotuner picks per system.
-template <int APT>
+template <int APT, int CG>
 __global__ void __launch_bounds__(PF_THREADS)
 k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
                   const uint8_t *__restrict__ chi, const float *__restrict__ Ex,
@@ -459,7 +479,11 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
 {
     static_assert(APT % 2 == 0, "a thread's atoms form packed pairs");
     constexpr int PAIRS = APT / 2;
-    constexpr int ATOMS = PF_THREADS * APT;
+    // CG groups of T threads: thread lt of group grp holds the tile's atoms
+    // lt, lt + T, ... and visits the cells grp, grp + CG, ... of each stage
+    constexpr int T = PF_THREADS / CG;
+    const int grp = threadIdx.x / T, lt = threadIdx.x - grp * T;
+    constexpr int ATOMS = T * APT;
     __shared__ __align__(16) CellPairs s_c[PF_STAGE];
     __shared__ int s_wc[2 * PF_THREADS / 32];
     __shared__ float s_box[6 * (PF_THREADS / 32)];
@@ -478,7 +502,7 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
     const float4 A0 = a.xyzq[tile * ATOMS];   // exists: tiles are non-empty
 #pragma unroll
     for (int u = 0; u < APT; ++u) {
-        an[u] = tile * ATOMS + u * PF_THREADS + threadIdx.x;
+        an[u] = tile * ATOMS + u * T + lt;
         if (an[u] < a.n) {
             const float4 A = a.xyzq[an[u]];
             const float4 F = a.fcoef[an[u]];
@@ -590,7 +614,7 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         for (int pp = 0; pp < PAIRS; ++pp) fx[pp] = fy[pp] = fz[pp] = zero2;
         if (clamp) {
 #pragma unroll 2
-            for (int p = 0; p < tot; ++p) {
+            for (int p = grp; p < tot; p += CG) {
                 const CellPairs c = s_c[p];
 #pragma unroll
                 for (int pp = 0; pp < PAIRS; ++pp)
@@ -599,7 +623,7 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             }
         } else {
 #pragma unroll 2
-            for (int p = 0; p < tot; ++p) {
+            for (int p = grp; p < tot; p += CG) {
                 const CellPairs c = s_c[p];
 #pragma unroll
                 for (int pp = 0; pp < PAIRS; ++pp)
@@ -621,13 +645,33 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             acc[2 * pp + 1][2] += (double)f1;
         }
     }
+    if (CG > 1) {     // the groups' sums, added in group order
+        __shared__ double s_acc[PF_THREADS * 4 * 3];
 #pragma unroll
-    for (int u = 0; u < APT; ++u) {
-        if (an[u] < a.n) {
-            double *o = part + ((long long)chunk * a.n + an[u]) * 3;
-            o[0] = acc[u][0];
-            o[1] = acc[u][1];
-            o[2] = acc[u][2];
+        for (int u = 0; u < APT; ++u)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) s_acc[(threadIdx.x * APT + u) * 3 + c] = acc[u][c];
+        __syncthreads();
+        if (grp == 0) {
+#pragma unroll
+            for (int u = 0; u < APT; ++u)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    double t = 0.0;
+                    for (int q = 0; q < CG; ++q) t += s_acc[((q * T + lt) * APT + u) * 3 + c];
+                    acc[u][c] = t;
+                }
+        }
+    }
+    if (grp == 0) {
+#pragma unroll
+        for (int u = 0; u < APT; ++u) {
+            if (an[u] < a.n) {
+                double *o = part + ((long long)chunk * a.n + an[u]) * 3;
+                o[0] = acc[u][0];
+                o[1] = acc[u][1];
+                o[2] = acc[u][2];
+            }
         }
     }
     if (nsolvent && tile == 0 && threadIdx.x == 0) atomicAdd(nsolvent, seen);
@@ -642,18 +686,27 @@ void launch_pair_force_grid(const GridDesc &g, const ForcePlan &fp,
     const long long G = (long long)g.nx * g.ny * g.nz;
     dim3 grid(fp.atom_tiles, fp.nchunk);
     count_launch();
-    if (fp.apt == 2)
-        k_pair_force_grid<2><<<grid, PF_THREADS, 0, st>>>(g, G, fp.chunk_len, chi, Ex, Ey, Ez,
-                                                          a, rmin2, part, nsolvent);
-    else
-        k_pair_force_grid<4><<<grid, PF_THREADS, 0, st>>>(g, G, fp.chunk_len, chi, Ex, Ey, Ez,
-                                                          a, rmin2, part, nsolvent);
+#define VESIS_FORCE_LAUNCH(A, C)                                                            \
+    k_pair_force_grid<A, C><<<grid, PF_THREADS, 0, st>>>(g, G, fp.chunk_len, chi, Ex, Ey, Ez, a, \
+                                                         rmin2, part, nsolvent)
+    if (fp.apt == 2) {
+        if (fp.cg == 4) VESIS_FORCE_LAUNCH(2, 4);
+        else if (fp.cg == 2) VESIS_FORCE_LAUNCH(2, 2);
+        else VESIS_FORCE_LAUNCH(2, 1);
+    } else {
+        if (fp.cg == 4) VESIS_FORCE_LAUNCH(4, 4);
+        else if (fp.cg == 2) VESIS_FORCE_LAUNCH(4, 2);
+        else VESIS_FORCE_LAUNCH(4, 1);
+    }
+#undef VESIS_FORCE_LAUNCH
 }
 
 // Far-field nodes -> atoms: weighted points, all of them solvent.
 ForcePlan plan_point_force(int np, int natoms, int nsm)
 {
     ForcePlan fp;
+    fp.apt = PF_APT;
+    fp.cg = 1;
     fp.atom_tiles = (natoms + PF_ATOMS - 1) / PF_ATOMS;
     long long nchunk = ((long long)nsm * 8) / fp.atom_tiles;
     const long long maxc = (np + PF_STAGE - 1) / PF_STAGE;

@@ -71,6 +71,8 @@ struct ForcePlan {
     long long chunk_len;
     int atom_tiles;
     int apt;          // atoms per thread of the grid kernel (2 or 4)
+    int cg;           // cell groups of a block: 128 / cg threads hold the tile's atoms,
+                      // and each group takes every cg-th cell of a stage (1, 2 or 4)
 };
 ForcePlan plan_pair_force(long long G, int natoms, int nsm, int apt);
 void launch_pair_force_grid(const GridDesc &g, const ForcePlan &fp,
