@@ -75,7 +75,7 @@ enum {
 struct GdState {
     double M;
     int ncnt;
-    int decision;   // 0 accept, 1 reject
+    int decision;   // 0 accept, 1 reject, 2 the gradient test ends the relaxation
     double dG;
 };
 
@@ -89,10 +89,20 @@ __global__ void k_total(double *bank)
 // dG* = frac |G_old|; a rejection shrinks M by alpha and resets N_cnt, an
 // acceptance increments N_cnt.  A non-finite trial energy or an atom that
 // left the box is rejected like an energy increase.
+// Step 3.4's accept/shrink test of a trial step.  The first trial of an
+// iteration is enqueued before the host has seen the gradient: when Step
+// 3.2's test (max |dG/dr| below Tol1, or not finite) ends the relaxation
+// instead, the trial is void and M and N_cnt are left as they are.
 __global__ void k_gd_decide(GdState *s, const double *bank_old,
                             const double *bank_new, const int *oob,
-                            int ncnt_star, double frac, double alpha)
+                            int ncnt_star, double frac, double alpha,
+                            const unsigned long long *gmax_bits, double tol_grad)
 {
+    const double gmax = __longlong_as_double((long long)*gmax_bits);
+    if (!(gmax == gmax) || gmax >= 1.0e308 || gmax < tol_grad) {
+        s->decision = 2;
+        return;
+    }
     const double Gold = bank_old[S_TOTAL], Gnew = bank_new[S_TOTAL];
     const double dG = Gnew - Gold;
     const double dGs = frac * fabs(Gold);
@@ -263,6 +273,7 @@ struct vesis_system_t {
 
     // pinned host mirrors
     double *h_scal = nullptr;
+    double *h_scal2 = nullptr;    // a second bank (the trial's, read with the current one)
     RoundState *h_rs = nullptr;
     GdState *h_gd = nullptr;
     int *h_int = nullptr;
@@ -454,8 +465,13 @@ void enq_terms(vesis_system s, const uint8_t *chi, const float *U,
     k_total<<<1, 1, 0, s->st>>>(bk);
 }
 
+// The flip sweep to a local minimum.  defer: the sweep's record and error
+// flag are copied out but not waited for; the caller waits with its next
+// read and then calls finish_blsm (not with a sweep gate: a gated sweep
+// holds its slot until it has ended).
+int finish_blsm(vesis_system s, int sp, RoundState *out);
 int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
-             RoundState *out, bool w_current = false)
+             RoundState *out, bool w_current = false, int *defer_sp = nullptr)
 {
     // exact integer convolution of the starting labels (unless d_W holds it
     // already); the sweep keeps it current with every flip
@@ -486,7 +502,18 @@ int run_blsm(vesis_system s, uint8_t *chi, const float *U, int max_rounds,
                         cudaMemcpyDeviceToHost, s->st));
     VCK(cudaMemcpyAsync(s->h_int, s->d_err, sizeof(int), cudaMemcpyDeviceToHost,
                         s->st));
+    if (defer_sp && !s->gate) {
+        *defer_sp = sp;
+        return VESIS_OK;
+    }
     VCK(cudaStreamSynchronize(s->st));
+    if (defer_sp) *defer_sp = -2;    // already finished
+    return finish_blsm(s, sp, out);
+}
+
+// The sweep's outcome once its copies have landed (after a synchronisation).
+int finish_blsm(vesis_system s, int sp, RoundState *out)
+{
     if (*s->h_int) return fail(VESIS_E_CUDA, "flip sweep grid barrier timed out");
     if (sp >= 0) {
         // the rounds include the last one, which found nothing to flip
@@ -661,6 +688,7 @@ int vesis_destroy(vesis_system s)
     for (void *p : s->allocs) cudaFree(p);
     for (void *p : s->bonded_allocs) cudaFree(p);
     if (s->h_scal) cudaFreeHost(s->h_scal);
+    if (s->h_scal2) cudaFreeHost(s->h_scal2);
     if (s->h_rs) cudaFreeHost(s->h_rs);
     if (s->h_gd) cudaFreeHost(s->h_gd);
     if (s->h_int) cudaFreeHost(s->h_int);
@@ -935,6 +963,7 @@ static int init_impl(vesis_system s, const vesis_params *p, int n,
     VTRY(dalloc(s, &s->d_gd, 1));
     VCK(cudaMemset(s->d_scal, 0, 2 * S_BANK * sizeof(double)));
     VCK(cudaMallocHost(&s->h_scal, S_BANK * sizeof(double)));
+    VCK(cudaMallocHost(&s->h_scal2, S_BANK * sizeof(double)));
     VCK(cudaMallocHost(&s->h_rs, sizeof(RoundState)));
     VCK(cudaMallocHost(&s->h_gd, sizeof(GdState)));
     VCK(cudaMallocHost(&s->h_int, sizeof(int)));
@@ -1405,14 +1434,34 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
     int k = o.resume ? from.k : 0, stable = o.resume ? from.stable : 0;
     int reason = 2, status = VESIS_OK;
     double gmax = 0.0;
+    // One outer iteration waits on the host once: the sweep, the gradient
+    // and the first trial step are enqueued together, and their records
+    // come back with one synchronisation (a rejected trial costs one more).
+    auto enq_trial = [&]() {
+        launch_mobility(s->d_xyz, s->d_grad, s->d_gmax, &s->d_gd->M, s->d_xyz_new, 3 * s->n,
+                        s->st);
+        enq_pack(s, s->d_xyz_new);
+        enq_fields(s, s->d_U[trial], s->d_E[trial], bank(s, trial));
+        enq_ss(s, s->d_xyz_new, bank(s, trial));
+        enq_terms(s, chi_dev, s->d_U[trial], s->d_E[trial], bank(s, trial), true);
+        count_launch();
+        k_gd_decide<<<1, 1, 0, s->st>>>(s->d_gd, bank(s, cur), bank(s, trial), s->d_oob,
+                                        o.ncnt_star, o.dgstar_frac, o.alpha, s->d_gmax,
+                                        o.tol_grad);
+    };
+    auto copy_trial = [&]() -> int {
+        VCK(cudaMemcpyAsync(s->h_gd, s->d_gd, sizeof(GdState), cudaMemcpyDeviceToHost, s->st));
+        VCK(cudaMemcpyAsync(s->h_scal2, bank(s, trial), S_BANK * sizeof(double),
+                            cudaMemcpyDeviceToHost, s->st));
+        return VESIS_OK;
+    };
     while (k < o.max_outer) {
         RoundState rs;
+        int sweep_sp = -2;
         {
             NvtxRange range("vesis: flip sweep");
-            VTRY(run_blsm(s, chi_dev, s->d_U[cur], o.max_flip_rounds, &rs, true));
+            VTRY(run_blsm(s, chi_dev, s->d_U[cur], o.max_flip_rounds, &rs, true, &sweep_sp));
         }
-        st.flip_rounds += rs.round;
-        st.flips += (long long)rs.total_flips;
         // Step 3.1-3.2: gradient and G_old at (Gamma^{k+1}, R^k); the
         // solute-solute terms at R^k are current (the start or the accepted
         // trial evaluated them last)
@@ -1420,51 +1469,54 @@ int vesis_relax(vesis_system s, uint8_t *chi_dev, double *xyz_inout,
             NvtxRange range("vesis: gradient");
             enq_gradient(s, chi_dev, s->d_E[cur], s->d_xyz, bank(s, cur), true);
             enq_terms(s, chi_dev, s->d_U[cur], s->d_E[cur], bank(s, cur), true);
-            VTRY(last_launch("relax gradient"));
-            VCK(cudaMemcpyAsync(s->h_u64, s->d_gmax, sizeof(unsigned long long),
-                                cudaMemcpyDeviceToHost, s->st));
-            VTRY(read_bank(s, bank(s, cur)));
         }
-        const double G_old = s->h_scal[S_TOTAL];
-        std::memcpy(&gmax, s->h_u64, sizeof(double));
-        st.pair_evals += (s->G - (long long)s->h_scal[S_NSOL]) * s->n + FN;
-        if (!std::isfinite(gmax) || gmax >= 1.0e308) {
-            status = fail(VESIS_E_NAN, "non-finite gradient");
-            break;
-        }
-        if (gmax < o.tol_grad) {
-            reason = 0;
-            break;
-        }
-        // Step 3.3-3.4: trial steps until one is accepted
+        // Step 3.3-3.4: the first trial step, enqueued before the gradient
+        // test is known here (void if that test ends the relaxation)
         int retries = 0;
         bool accepted = false;
         double G_new = 0.0;
         {
             NvtxRange range("vesis: trial steps");
-            while (!accepted) {
-                launch_mobility(s->d_xyz, s->d_grad, s->d_gmax, &s->d_gd->M,
-                                s->d_xyz_new, 3 * s->n, s->st);
-                enq_pack(s, s->d_xyz_new);
-                enq_fields(s, s->d_U[trial], s->d_E[trial], bank(s, trial));
-                enq_ss(s, s->d_xyz_new, bank(s, trial));
-                enq_terms(s, chi_dev, s->d_U[trial], s->d_E[trial], bank(s, trial), true);
-                count_launch();
-                k_gd_decide<<<1, 1, 0, s->st>>>(s->d_gd, bank(s, cur), bank(s, trial),
-                                                s->d_oob, o.ncnt_star, o.dgstar_frac,
-                                                o.alpha);
-                VTRY(last_launch("relax trial"));
-                VCK(cudaMemcpyAsync(s->h_gd, s->d_gd, sizeof(GdState),
-                                    cudaMemcpyDeviceToHost, s->st));
-                VTRY(read_bank(s, bank(s, trial)));
+            enq_trial();
+            VTRY(last_launch("relax iteration"));
+            VCK(cudaMemcpyAsync(s->h_u64, s->d_gmax, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, s->st));
+            VCK(cudaMemcpyAsync(s->h_scal, bank(s, cur), S_BANK * sizeof(double),
+                                cudaMemcpyDeviceToHost, s->st));
+            VTRY(copy_trial());
+            VCK(cudaStreamSynchronize(s->st));
+        }
+        if (sweep_sp != -2) VTRY(finish_blsm(s, sweep_sp, &rs));
+        st.flip_rounds += rs.round;
+        st.flips += (long long)rs.total_flips;
+        const double G_old = s->h_scal[S_TOTAL];
+        std::memcpy(&gmax, s->h_u64, sizeof(double));
+        st.pair_evals += (s->G - (long long)s->h_scal[S_NSOL]) * s->n + FN;
+        if (!std::isfinite(gmax) || gmax >= 1.0e308) {
+            enq_pack(s, s->d_xyz);   // the void trial moved the packed atoms
+            status = fail(VESIS_E_NAN, "non-finite gradient");
+            break;
+        }
+        if (gmax < o.tol_grad) {
+            enq_pack(s, s->d_xyz);
+            reason = 0;
+            break;
+        }
+        {
+            NvtxRange range("vesis: trial steps");
+            for (;;) {
                 st.gd_trials += 1;
                 st.pair_evals += GN + FN + NN;
                 if (s->h_gd->decision == 0) {
                     accepted = true;
-                    G_new = s->h_scal[S_TOTAL];
-                } else if (++retries > o.max_gd_retries) {
+                    G_new = s->h_scal2[S_TOTAL];
                     break;
                 }
+                if (++retries > o.max_gd_retries) break;
+                enq_trial();
+                VTRY(last_launch("relax trial"));
+                VTRY(copy_trial());
+                VCK(cudaStreamSynchronize(s->st));
             }
         }
         if (!accepted) {
