@@ -38,9 +38,9 @@ METRIC = "atom-grid pair-evals/s"
 # capture of the default workload (dram__bytes_read.sum and
 # dram__bytes_write.sum), valid only for the source they were taken on:
 # reported as null once pair.cu changes.
-TRAFFIC = {"sha256_16": "57fdf408ed2bbff3", "workload": "complex20000_grid384",
-           "pair_energy_grid": 29906432 + 861332480,
-           "pair_force_grid": 703815936 + 58457856}
+TRAFFIC = {"sha256_16": "43d6e8b4069459d0", "workload": "complex20000_grid384",
+           "pair_energy_grid": 34590208 + 863972352,
+           "pair_force_grid": 703297024 + 58215936}
 # FP32 lane operations per energy pair in the inner loop of the pair kernel:
 # dz, r^2, r^-2, r^-3, r^-6, two LJ FMAs, Q r^-3, three field FMAs (the
 # reciprocal square root runs on the SFU and is not counted; the x/y parts of

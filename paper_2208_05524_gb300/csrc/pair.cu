@@ -377,7 +377,15 @@ ForcePlan plan_pair_force(long long G, int natoms, int nsm, int apt)
     const long long tiles512 = (natoms + PF_ATOMS - 1) / PF_ATOMS;
     const long long target = (long long)nsm * 8 * 4;
     long long nchunk = target / tiles512;
-    const long long maxc = (G + PF_STAGE - 1) / PF_STAGE;
+    // Every chunk writes an FP64 partial per atom.  On small grids one-stage
+    // chunks made those partials (and their reduction) cost more than the
+    // pairs, so a chunk spans at least 8 stages - unless that leaves fewer
+    // than two waves of blocks (counted with the 4-atom tiles, so that the
+    // plan depends on the atom count alone).
+    const long long tiles_ref = (natoms + PF_ATOMS / fp.cg - 1) / (PF_ATOMS / fp.cg);
+    const long long fill = ((long long)nsm * 8 + tiles_ref - 1) / tiles_ref;
+    const long long maxc = std::min((G + PF_STAGE - 1) / PF_STAGE,
+                                    std::max(fill, G / ((long long)PF_STAGE * 8)));
     if (nchunk < 1) nchunk = 1;
     if (nchunk > maxc) nchunk = maxc;
     long long len = (G + nchunk - 1) / nchunk;
