@@ -38,17 +38,20 @@ METRIC = "atom-grid pair-evals/s"
 # capture of the default workload (dram__bytes_read.sum and
 # dram__bytes_write.sum), valid only for the source they were taken on:
 # reported as null once pair.cu changes.
-TRAFFIC = {"sha256_16": "43d6e8b4069459d0", "workload": "complex20000_grid384",
-           "pair_energy_grid": 34590208 + 863972352,
-           "pair_force_grid": 703297024 + 58215936}
+TRAFFIC = {"sha256_16": "eb8ec2dae05bd457", "workload": "complex20000_grid384",
+           "pair_energy_grid": 34425600 + 864290304,
+           "pair_force_grid": 702819840 + 57329408}
 # FP32 lane operations per energy pair in the inner loop of the pair kernel:
 # dz, r^2, r^-2, r^-3, r^-6, two LJ FMAs, Q r^-3, three field FMAs (the
 # reciprocal square root runs on the SFU and is not counted; the x/y parts of
 # the distance are formed once per atom for 8 cells and not counted either).
 OPS_PER_PAIR = 11
-# The same for a gradient pair: d (3), r^2 (3), r^-2, r^-3, r^-6, r^-8, the
-# LJ factor (2), d.E (3), kq r^-3, the d d^T factor (3), six accumulations.
-FORCE_OPS_PER_PAIR = 25
+# The same for a gradient pair, whose cells come in z-pencils: dz, r^2,
+# r^-2, r^-3, r^-5, r^-6, the LJ factor, d.E (3), the d d^T factor (2), the
+# pair's factor, its sum and d_z term, and r^-3 E (3).  dx, dy and their
+# squares are formed once per pencil and atom, and the pencil's x/y terms are
+# dx and dy times its sum of factors (not counted).
+FORCE_OPS_PER_PAIR = 18
 FP32_LANES_PER_SM = 128
 L2_BYTES = 129 * 1024 * 1024
 
@@ -405,7 +408,8 @@ def run_vesis(args, world, rank, local):
                  "peak": peak_ops / 1e12, "unit": "Tops/s (FP32 lane-ops)",
                  "frac": fpairs * FORCE_OPS_PER_PAIR / fs / peak_ops,
                  "traffic": pair_traffic(args.workload, "pair_force_grid"),
-                 "ops_per_pair": FORCE_OPS_PER_PAIR}
+                 "ops_per_pair": FORCE_OPS_PER_PAIR,
+                 "frac_at_28_ops_per_pair": fpairs * 28 / fs / peak_ops}
 
     if rank == 0:
         cpu = None

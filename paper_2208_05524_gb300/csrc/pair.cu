@@ -432,47 +432,82 @@ __device__ __forceinline__ void force_pair(float px, float py, float pz,
     fz = fmaf(cd, dz, fmaf(am, E.z, fz));
 }
 
-// The same for the thread's two atoms at once (packed pairs; nk3 = -3 kq).
-// The clamped form goes through the halves one by one.
-struct CellPairs {
-    f2 x, y, z;      // cell position, duplicated into both halves
-    f2 ex, ey, ez;   // field at the cell, duplicated
+// The grid kernel's form of the same pair, for the thread's two atoms at
+// once (packed pairs; nk3 = -3 kq).  The cells of one z-pencil share x and
+// y, so dx, dy and dx^2 + dy^2 come in once per pencil, and the pencil's sum
+// of cd d_x is dx times its sum of cd.  With r^-8 (c1 r^-6 + c2) + nk3 r^-5
+// (d.E) = r^-5 [r^-3 (c1 r^-6 + c2) + nk3 (d.E)], a pair adds
+//   sc += cd,  fz += cd dz,  g += r^-3 E     (the E part times kq at the end)
+// in 18 packed operations.  Clamped pairs keep only r^-3 E.
+struct CellQuad {
+    f2 z, ex, ey, ez;   // cell z and field, each duplicated into both halves
 };
 
-template <bool CLAMP>
-__device__ __forceinline__ void force_pair2(const CellPairs &c, f2 ax, f2 ay, f2 az, f2 c1,
-                                            f2 c2, f2 kq, f2 nk3, float rmin2, f2 &fx,
-                                            f2 &fy, f2 &fz)
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
 {
-    const f2 dx = sub2(c.x, ax), dy = sub2(c.y, ay), dz = sub2(c.z, az);
-    const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+template <bool CLAMP>
+__device__ __forceinline__ void grad_pair2(const CellQuad &c, f2 dx, f2 dy, f2 dxy2, f2 az,
+                                           f2 c1, f2 c2, f2 nk3, float rmin2, f2 &sc,
+                                           f2 &fz, f2 &gx, f2 &gy, f2 &gz)
+{
+    const f2 dz = sub2(c.z, az);
+    const f2 r2 = fma2(dz, dz, dxy2);
     float ra, rb;
     upk2(r2, ra, rb);
-    f2 ri, c1m = c1, c2m = c2, k3m = nk3;
+    f2 ri;
+    bool ua = true, ub = true;   // not clamped
     if (CLAMP) {
-        const bool ua = ra >= rmin2, ub = rb >= rmin2;   // not clamped
+        ua = ra >= rmin2;
+        ub = rb >= rmin2;
         ri = pk2(rsqrt_ftz(fmaxf(ra, rmin2)), rsqrt_ftz(fmaxf(rb, rmin2)));
-        float s0, s1;
-        upk2(c1, s0, s1);
-        c1m = pk2(ua ? s0 : 0.f, ub ? s1 : 0.f);
-        upk2(c2, s0, s1);
-        c2m = pk2(ua ? s0 : 0.f, ub ? s1 : 0.f);
-        upk2(nk3, s0, s1);
-        k3m = pk2(ua ? s0 : 0.f, ub ? s1 : 0.f);
     } else {
         ri = pk2(rsqrt_ftz(ra), rsqrt_ftz(rb));
     }
     const f2 ri2 = mul2(ri, ri);
     const f2 ri3 = mul2(ri2, ri);
     const f2 ri6 = mul2(ri3, ri3);
-    const f2 ri8 = mul2(ri6, ri2);
-    const f2 glj = mul2(fma2(c1m, ri6, c2m), ri8);
+    const f2 ri5 = mul2(ri3, ri2);
+    const f2 t1 = fma2(c1, ri6, c2);
     const f2 dE = fma2(dx, c.ex, fma2(dy, c.ey, mul2(dz, c.ez)));
-    const f2 am = mul2(kq, ri3);
-    const f2 cd = fma2(mul2(k3m, ri3), mul2(dE, ri2), glj);
-    fx = fma2(cd, dx, fma2(am, c.ex, fx));
-    fy = fma2(cd, dy, fma2(am, c.ey, fy));
-    fz = fma2(cd, dz, fma2(am, c.ez, fz));
+    f2 cd = mul2(ri5, fma2(ri3, t1, mul2(nk3, dE)));
+    if (CLAMP) {
+        float ca, cb;
+        upk2(cd, ca, cb);
+        cd = pk2(ua ? ca : 0.f, ub ? cb : 0.f);
+    }
+    sc = add2(sc, cd);
+    fz = fma2(cd, dz, fz);
+    gx = fma2(ri3, c.ex, gx);
+    gy = fma2(ri3, c.ey, gy);
+    gz = fma2(ri3, c.ez, gz);
+}
+
+// hi + lo += v with the rounding error of the addition kept in lo (Knuth's
+// two-sum, both halves of the pairs at once)
+__device__ __forceinline__ void two_sum_acc(f2 &hi, f2 &lo, f2 v)
+{
+    const f2 s = add2(hi, v);
+    const f2 bb = sub2(s, hi);
+    lo = add2(lo, add2(sub2(hi, sub2(s, bb)), sub2(v, bb)));
+    hi = s;
+}
+
+// Number of solvent cells among the first n slots of a stage, from the
+// stage's per-warp ballots (slot order) and their counts.
+__device__ __forceinline__ int stage_rank(int n, const int *wc, const unsigned *bal)
+{
+    constexpr int NWORD = 2 * PF_THREADS / 32;
+    const int w = n >> 5;
+    int r = 0;
+#pragma unroll
+    for (int v = 0; v < NWORD; ++v) r += v < w ? wc[v] : 0;
+    if (w < NWORD) r += __popc(bal[w] & ((1u << (n & 31)) - 1u));
+    return r;
 }
 
 // APT (atoms per thread, 2 or 4, in packed pairs) is the atom tile the
@@ -492,8 +527,9 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
     constexpr int T = PF_THREADS / CG;
     const int grp = threadIdx.x / T, lt = threadIdx.x - grp * T;
     constexpr int ATOMS = T * APT;
-    __shared__ __align__(16) CellPairs s_c[PF_STAGE];
+    __shared__ __align__(16) CellQuad s_c[PF_STAGE];
     __shared__ int s_wc[2 * PF_THREADS / 32];
+    __shared__ unsigned s_bal[2 * PF_THREADS / 32];
     __shared__ float s_box[6 * (PF_THREADS / 32)];
     // the atom tile varies fastest in launch order: the blocks of one cell
     // chunk run together and its labels and field come from DRAM once
@@ -535,8 +571,8 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
             ahi[c] = fmaxf(ahi[c], hi2[c]);
         }
     }
-    f2 ax2[PAIRS], ay2[PAIRS], az2[PAIRS], c12[PAIRS], c22[PAIRS],
-        kq2[PAIRS], nk32[PAIRS];
+    f2 ax2[PAIRS], ay2[PAIRS], az2[PAIRS], c12[PAIRS], c22[PAIRS], kq2[PAIRS],
+        nk32[PAIRS];
 #pragma unroll
     for (int pp = 0; pp < PAIRS; ++pp) {
         const int u = 2 * pp;
@@ -549,9 +585,14 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         nk32[pp] = pk2(-kq3[u], -kq3[u + 1]);
     }
     const f2 zero2 = pk2(0.f, 0.f);
-    double acc[APT][3];
+    // the stage sums add into double-float (hi + lo) accumulators: exact
+    // FP32 error-free additions instead of FP64 arithmetic, which this part
+    // runs at a small fraction of the FP32 rate
+    f2 shi[PAIRS][3], slo[PAIRS][3];
 #pragma unroll
-    for (int u = 0; u < APT; ++u) acc[u][0] = acc[u][1] = acc[u][2] = 0.0;
+    for (int pp = 0; pp < PAIRS; ++pp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) shi[pp][c] = slo[pp][c] = zero2;
 
     const long long nyz = (long long)g.ny * g.nz;
     unsigned long long seen = 0;
@@ -591,6 +632,8 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         if (lane == 0) {
             s_wc[warp] = __popc(b0);
             s_wc[NW + warp] = __popc(b1);
+            s_bal[warp] = b0;
+            s_bal[NW + warp] = b1;
         }
         __syncthreads();
         int off0 = 0, off1 = 0, tot = 0;
@@ -606,9 +649,7 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         for (int hlf = 0; hlf < 2; ++hlf) {
             if (!v[hlf]) continue;
             const int pos = (hlf ? off1 + __popc(b1 & lt) : off0 + __popc(b0 & lt));
-            CellPairs cp;
-            cp.x = pk2(P[hlf].x, P[hlf].x);
-            cp.y = pk2(P[hlf].y, P[hlf].y);
+            CellQuad cp;
             cp.z = pk2(P[hlf].z, P[hlf].z);
             cp.ex = pk2(Ev[hlf].x, Ev[hlf].x);
             cp.ey = pk2(Ev[hlf].y, Ev[hlf].y);
@@ -617,42 +658,73 @@ k_pair_force_grid(GridDesc g, long long G, long long chunk_len,
         }
         __syncthreads();
         seen += (unsigned long long)tot;
-        f2 fx[PAIRS], fy[PAIRS], fz[PAIRS];
+        f2 fx[PAIRS], fy[PAIRS], fz[PAIRS], gx[PAIRS], gy[PAIRS], gz[PAIRS];
 #pragma unroll
-        for (int pp = 0; pp < PAIRS; ++pp) fx[pp] = fy[pp] = fz[pp] = zero2;
-        if (clamp) {
-#pragma unroll 2
-            for (int p = grp; p < tot; p += CG) {
-                const CellPairs c = s_c[p];
+        for (int pp = 0; pp < PAIRS; ++pp) fx[pp] = fy[pp] = fz[pp] = gx[pp] = gy[pp] = gz[pp] = zero2;
+        // the stage's cells by z-pencil: the solvent cells of pencil pen sit
+        // at positions [st, en) of the compacted list
+        const long long lim = min((long long)PF_STAGE, c1 - s);
+        const long long pen_end = (s + lim - 1) / g.nz;
+        for (long long pen = s / g.nz; pen <= pen_end; ++pen) {
+            const int st = stage_rank((int)max(pen * g.nz - s, 0LL), s_wc, s_bal);
+            const int en = stage_rank((int)min((pen + 1) * g.nz - s, lim), s_wc, s_bal);
+            if (st == en) continue;
+            const int i = (int)(pen / g.ny);
+            const int j = (int)(pen - (long long)i * g.ny);
+            const float x = cell_pos(i, g.cx, g.h), y = cell_pos(j, g.cy, g.h);
+            const f2 x2 = pk2(x, x), y2 = pk2(y, y);
+            f2 dx[PAIRS], dy[PAIRS], dxy2[PAIRS], sc[PAIRS];
 #pragma unroll
-                for (int pp = 0; pp < PAIRS; ++pp)
-                    force_pair2<true>(c, ax2[pp], ay2[pp], az2[pp], c12[pp], c22[pp], kq2[pp],
-                                      nk32[pp], rmin2, fx[pp], fy[pp], fz[pp]);
+            for (int pp = 0; pp < PAIRS; ++pp) {
+                dx[pp] = sub2(x2, ax2[pp]);
+                dy[pp] = sub2(y2, ay2[pp]);
+                dxy2[pp] = fma2(dx[pp], dx[pp], mul2(dy[pp], dy[pp]));
+                sc[pp] = zero2;
             }
-        } else {
-#pragma unroll 2
-            for (int p = grp; p < tot; p += CG) {
-                const CellPairs c = s_c[p];
+            const int first = st + ((grp - st) & (CG - 1));
+            if (clamp) {
+#pragma unroll 4
+                for (int p = first; p < en; p += CG) {
+                    const CellQuad c = s_c[p];
 #pragma unroll
-                for (int pp = 0; pp < PAIRS; ++pp)
-                    force_pair2<false>(c, ax2[pp], ay2[pp], az2[pp], c12[pp], c22[pp], kq2[pp],
-                                       nk32[pp], rmin2, fx[pp], fy[pp], fz[pp]);
+                    for (int pp = 0; pp < PAIRS; ++pp)
+                        grad_pair2<true>(c, dx[pp], dy[pp], dxy2[pp], az2[pp], c12[pp], c22[pp],
+                                         nk32[pp], rmin2, sc[pp], fz[pp], gx[pp], gy[pp], gz[pp]);
+                }
+            } else {
+#pragma unroll 4
+                for (int p = first; p < en; p += CG) {
+                    const CellQuad c = s_c[p];
+#pragma unroll
+                    for (int pp = 0; pp < PAIRS; ++pp)
+                        grad_pair2<false>(c, dx[pp], dy[pp], dxy2[pp], az2[pp], c12[pp], c22[pp],
+                                          nk32[pp], rmin2, sc[pp], fz[pp], gx[pp], gy[pp], gz[pp]);
+                }
+            }
+#pragma unroll
+            for (int pp = 0; pp < PAIRS; ++pp) {
+                fx[pp] = fma2(sc[pp], dx[pp], fx[pp]);
+                fy[pp] = fma2(sc[pp], dy[pp], fy[pp]);
             }
         }
 #pragma unroll
         for (int pp = 0; pp < PAIRS; ++pp) {
-            float f0, f1;
-            upk2(fx[pp], f0, f1);
-            acc[2 * pp][0] += (double)f0;
-            acc[2 * pp + 1][0] += (double)f1;
-            upk2(fy[pp], f0, f1);
-            acc[2 * pp][1] += (double)f0;
-            acc[2 * pp + 1][1] += (double)f1;
-            upk2(fz[pp], f0, f1);
-            acc[2 * pp][2] += (double)f0;
-            acc[2 * pp + 1][2] += (double)f1;
+            two_sum_acc(shi[pp][0], slo[pp][0], fma2(kq2[pp], gx[pp], fx[pp]));
+            two_sum_acc(shi[pp][1], slo[pp][1], fma2(kq2[pp], gy[pp], fy[pp]));
+            two_sum_acc(shi[pp][2], slo[pp][2], fma2(kq2[pp], gz[pp], fz[pp]));
         }
     }
+    double acc[APT][3];
+#pragma unroll
+    for (int pp = 0; pp < PAIRS; ++pp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float h0, h1, l0, l1;
+            upk2(shi[pp][c], h0, h1);
+            upk2(slo[pp][c], l0, l1);
+            acc[2 * pp][c] = (double)h0 + (double)l0;
+            acc[2 * pp + 1][c] = (double)h1 + (double)l1;
+        }
     if (CG > 1) {     // the groups' sums, added in group order
         __shared__ double s_acc[PF_THREADS * 4 * 3];
 #pragma unroll
