@@ -266,6 +266,61 @@ def test_atom_forces_match_oracle(natoms, n, h):
     assert e == pytest.approx(To["total"], rel=1e-6)
 
 
+def _pencil_case(n, natoms, seed, h=0.5):
+    """Atoms on a jittered lattice of about 5 A that fills the box (no bonds,
+    so the solute-solute terms stay moderate) and labels with half of the
+    cells farther than 2.5 A from every atom solvent, at random, so that
+    solvent runs are broken inside every z-pencil."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(n, np.float64) * h
+    s = synth.random_cluster(natoms, 8, h, seed=seed, net_charge=1.0)
+    m = np.maximum(np.floor(L / 5.0), 1).astype(int)
+    cells = np.stack(np.meshgrid(*[np.arange(k) for k in m], indexing="ij"), -1).reshape(-1, 3)
+    assert len(cells) >= natoms
+    pick = cells[rng.permutation(len(cells))[:natoms]]
+    step = L / m
+    jitter = (rng.random((natoms, 3)) - 0.5) * 0.3 * step
+    s["xyz"] = -0.5 * L + (pick + 0.5) * step + jitter
+    s["bonds"] = np.zeros((0, 2), np.int32)
+    s["bond_k"] = np.zeros(0)
+    s["bond_r0"] = np.zeros(0)
+    s["n"] = np.array(n)
+    s["origin"] = -0.5 * L
+    axes = [-0.5 * L[c] + (np.arange(n[c]) + 0.5) * h for c in range(3)]
+    X = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    from scipy.spatial import cKDTree
+    near = cKDTree(s["xyz"]).query(X, distance_upper_bound=2.5)[0] < 2.5
+    solvent = ~near & (rng.random(len(X)) < 0.5)
+    return s, (~solvent).astype(np.uint8).reshape(tuple(n))
+
+
+@pytest.mark.parametrize("n,natoms", [((40, 34, 1), 12),      # one cell per pencil, 4 groups
+                                      ((340, 320, 3), 1000),  # short pencils, 1 group, 2 tiles
+                                      ((240, 230, 3), 520),   # short pencils, 4 groups
+                                      ((4, 5, 300), 28)])     # pencils cut by the stages
+def test_atom_forces_by_pencil_match_oracle(n, natoms):
+    """The gradient kernel takes the solvent cells of each 256-cell stage by
+    z-pencil (dx, dy once per pencil and atom, the pencil's x/y terms from
+    its summed pair factor).  Gradient (Eq. GradientG) against the oracle's
+    on grids that stress that split: nz = 1, nz = 3 with two atom tiles, and
+    nz = 300 (a pencil spans two stages), with one and with four groups of
+    threads sharing the staged cells; random labels, so the solvent
+    cells of a pencil are not contiguous.  The far field is off on both
+    sides: these boxes are thinner than an atom, and the solvent it places
+    just outside them would dwarf the grid's terms being tested."""
+    vs = _vs()
+    s, chi0 = _pencil_case(n, natoms, seed=natoms)
+    p = O.params(far_field=False)
+    S = vs.System(s, far_field=0)
+    chi = _dev(chi0.reshape(-1), torch.uint8)
+    g = S.atom_forces(chi)
+    go = O.gradient(s, p, chi0)
+    nb, worst = _close(g, go)
+    assert nb == 0, worst
+    S.set_tiles(8, 2)     # the other atom tile: bit-identical
+    assert np.array_equal(S.atom_forces(chi), g)
+
+
 # ------------------------------------------------------------ relaxation
 
 def test_solute_solute_pair_terms_match_oracle():
